@@ -1,0 +1,259 @@
+"""FP64 CPU oracle (test infrastructure only).
+
+Only the test suite, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  It wraps ``liboracle.so`` (built from
+``oracle.cpp`` and ``mlp.cpp`` with g++; see ``build()``) through ctypes and
+marshals the seeded scenes of ``paper_2202_01284_gb300.scenes`` into the
+oracle's own input records.  Nothing here touches the CUDA library.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "liboracle.so")
+_SOURCES = [os.path.join(_HERE, "oracle.cpp"), os.path.join(_HERE, "mlp.cpp")]
+_lib = None
+_lock = threading.Lock()
+
+
+def build(force: bool = False) -> str:
+    """Compile liboracle.so in place (plain g++ -O2, no architecture flags)."""
+    srcs = [s for s in _SOURCES if os.path.exists(s)]
+    newest = max(os.path.getmtime(s) for s in srcs)
+    if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= newest:
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-shared", "-pthread", "-o", tmp] + srcs
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+class SceneIn(C.Structure):
+    _fields_ = [
+        ("n_tris", C.c_int), ("vertices", C.c_void_p), ("uvs", C.c_void_p), ("tri_shape", C.c_void_p),
+        ("n_shapes", C.c_int), ("bsdf", C.c_void_p), ("tex", C.c_void_p), ("albedo_index", C.c_void_p),
+        ("rough_index", C.c_void_p), ("alpha", C.c_void_p), ("f0", C.c_void_p), ("eta", C.c_void_p),
+        ("emission", C.c_void_p), ("diffuse_weight", C.c_void_p),
+        ("n_albedo", C.c_int), ("albedo", C.c_void_p),
+        ("n_tex", C.c_int), ("tex_data", C.c_void_p), ("tex_w", C.c_void_p), ("tex_h", C.c_void_p),
+        ("n_rough", C.c_int), ("roughness", C.c_void_p),
+        ("env_w", C.c_int), ("env_h", C.c_int), ("env", C.c_void_p),
+    ]
+
+
+class RenderIn(C.Structure):
+    _fields_ = [
+        ("origin", C.c_double * 3), ("target", C.c_double * 3), ("up", C.c_double * 3),
+        ("vfov_deg", C.c_double), ("width", C.c_int), ("height", C.c_int),
+        ("spp", C.c_int), ("max_depth", C.c_int), ("rr_depth", C.c_int), ("nee", C.c_int),
+        ("seed", C.c_uint64), ("cam_index", C.c_int),
+        ("crop_x0", C.c_int), ("crop_y0", C.c_int), ("crop_w", C.c_int), ("crop_h", C.c_int),
+    ]
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            L = C.CDLL(_LIB_PATH)
+            vp, ip, dp = C.c_void_p, C.c_int, C.c_double
+            L.oracle_scene_new.restype = vp
+            L.oracle_scene_new.argtypes = [C.POINTER(SceneIn)]
+            L.oracle_scene_free.argtypes = [vp]
+            L.oracle_render.argtypes = [vp, C.POINTER(RenderIn), vp, vp, vp, ip]
+            L.oracle_grad_tape.argtypes = [vp, C.POINTER(RenderIn), vp, vp, vp, vp, ip]
+            L.oracle_grad_dual.argtypes = [vp, C.POINTER(RenderIn), vp, ip, vp, vp, ip]
+            L.oracle_pcg32.argtypes = [C.c_uint64, C.c_uint64, ip, vp]
+            L.oracle_trace.argtypes = [vp, ip, vp, vp, ip, vp, vp]
+            L.oracle_bsdf_eval.argtypes = [ip, vp, vp, vp, vp, vp]
+            L.oracle_bsdf_sample.argtypes = [ip, vp, vp, dp, dp, dp, vp]
+            L.oracle_bsdf_sample.restype = ip
+            L.oracle_bsdf_dfactors.argtypes = [ip, vp, vp, vp, vp]
+            L.oracle_fresnel.argtypes = [dp, dp]
+            L.oracle_fresnel.restype = dp
+            L.oracle_env_pdf.argtypes = [vp, vp]
+            L.oracle_env_pdf.restype = dp
+            L.oracle_frame.argtypes = [vp, vp, vp]
+            if hasattr(L, "oracle_mlp_forward"):
+                L.oracle_mlp_forward.argtypes = [vp, ip, vp, ip, vp, vp]
+                L.oracle_mlp_loss_grad.argtypes = [vp, ip, vp, vp, ip, vp, vp]
+                L.oracle_mlp_loss_grad.restype = dp
+                L.oracle_mlp_adam.argtypes = [vp, vp, vp, vp, ip, dp, dp, dp, dp, ip]
+                L.oracle_nrc_encode.argtypes = [ip, vp, vp]
+            _lib = L
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(C.c_void_p) if a is not None else None
+
+
+class OracleScene:
+    """Oracle-side copy of a `scenes.Scene` (FP64, its own BVH and CDFs)."""
+
+    def __init__(self, scene):
+        L = lib()
+        self._keep = []
+
+        def arr(a, dt):
+            a = np.ascontiguousarray(a, dtype=dt)
+            self._keep.append(a)
+            return a
+        s = scene
+        si = SceneIn()
+        si.n_tris = s.n_tris
+        si.vertices = _ptr(arr(s.vertices, np.float32))
+        si.uvs = _ptr(arr(s.uvs, np.float32))
+        si.tri_shape = _ptr(arr(s.tri_shape, np.int32))
+        si.n_shapes = s.n_shapes
+        si.bsdf = _ptr(arr(s.bsdf, np.int32))
+        si.tex = _ptr(arr(s.tex, np.int32))
+        si.albedo_index = _ptr(arr(s.albedo_index, np.int32))
+        si.rough_index = _ptr(arr(s.rough_index, np.int32))
+        si.alpha = _ptr(arr(s.alpha, np.float32))
+        si.f0 = _ptr(arr(s.f0, np.float32))
+        si.eta = _ptr(arr(s.eta, np.float32))
+        si.emission = _ptr(arr(s.emission, np.float32))
+        si.diffuse_weight = _ptr(arr(s.diffuse_weight, np.float32))
+        si.n_albedo = int(s.albedo.shape[0])
+        si.albedo = _ptr(arr(s.albedo.reshape(-1, 3) if s.albedo.size else np.zeros((0, 3)), np.float32))
+        texs = [arr(t, np.float32) for t in s.textures]
+        ptrs = (C.c_void_p * max(1, len(texs)))(*[t.ctypes.data for t in texs])
+        self._keep.append(ptrs)
+        si.n_tex = len(texs)
+        si.tex_data = C.cast(ptrs, C.c_void_p)
+        si.tex_w = _ptr(arr([t.shape[1] for t in texs] or [0], np.int32))
+        si.tex_h = _ptr(arr([t.shape[0] for t in texs] or [0], np.int32))
+        si.n_rough = int(s.roughness.shape[0])
+        si.roughness = _ptr(arr(s.roughness if s.roughness.size else np.zeros(1), np.float32))
+        if s.env is not None:
+            si.env_w, si.env_h = int(s.env.shape[1]), int(s.env.shape[0])
+            si.env = _ptr(arr(s.env, np.float32))
+        else:
+            si.env_w = si.env_h = 0
+            si.env = None
+        self.handle = L.oracle_scene_new(C.byref(si))
+        self._keep = []  # the oracle copied everything
+        self.scene = scene
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.oracle_scene_free(self.handle)
+            self.handle = None
+
+
+def render_in(cam, spp, max_depth, seed, rr_depth=-1, nee=True, cam_index=0, crop=None) -> RenderIn:
+    r = RenderIn()
+    r.origin[:] = cam.origin
+    r.target[:] = cam.target
+    r.up[:] = cam.up
+    r.vfov_deg = cam.vfov_deg
+    r.width, r.height = cam.width, cam.height
+    r.spp, r.max_depth, r.rr_depth, r.nee = spp, max_depth, rr_depth, int(bool(nee))
+    r.seed = seed
+    r.cam_index = cam_index
+    if crop is not None:
+        r.crop_x0, r.crop_y0, r.crop_w, r.crop_h = crop
+    return r
+
+
+def _crop_shape(r: RenderIn):
+    return (r.crop_h, r.crop_w) if r.crop_w > 0 else (r.height, r.width)
+
+
+def render(osc: OracleScene, r: RenderIn, per_sample=False, threads=0):
+    """Image [h][w][3] (FP64); with per_sample also [h][w][spp][3] radiance and hashes."""
+    h, w = _crop_shape(r)
+    img = np.zeros((h, w, 3))
+    sl = np.zeros((h, w, r.spp, 3)) if per_sample else None
+    sh = np.zeros((h, w, r.spp), np.uint32) if per_sample else None
+    lib().oracle_render(osc.handle, C.byref(r), _ptr(img), _ptr(sl), _ptr(sh), threads)
+    return (img, sl, sh) if per_sample else img
+
+
+def grad_tape(osc: OracleScene, r: RenderIn, grad_image: np.ndarray, threads=0):
+    """Gradients (albedo [A,3], textures list [h,w,4], roughness [R]) by the stored tape."""
+    s = osc.scene
+    gi = np.ascontiguousarray(grad_image, dtype=np.float64)
+    ga = np.zeros((s.albedo.shape[0], 3))
+    gt = [np.zeros(t.shape) for t in s.textures]
+    gr = np.zeros(s.roughness.shape[0])
+    tp = (C.c_void_p * max(1, len(gt)))(*[t.ctypes.data for t in gt])
+    lib().oracle_grad_tape(osc.handle, C.byref(r), _ptr(gi), _ptr(ga), C.cast(tp, C.c_void_p), _ptr(gr), threads)
+    return ga, gt, gr
+
+
+def grad_dual(osc: OracleScene, r: RenderIn, grad_image: np.ndarray, sel, threads=0):
+    """Gradients of the selected parameters by forward-mode duals.
+
+    sel: list of (kind, a, b, c): (0,row,ch,0) albedo, (1,tex,texel,ch) texel, (2,idx,0,0) roughness.
+    """
+    gi = np.ascontiguousarray(grad_image, dtype=np.float64)
+    s = np.ascontiguousarray(np.asarray(sel, np.int32).reshape(-1, 4))
+    out = np.zeros(s.shape[0])
+    lib().oracle_grad_dual(osc.handle, C.byref(r), _ptr(gi), s.shape[0], _ptr(s), _ptr(out), threads)
+    return out
+
+
+def pcg32(initstate: int, initseq: int, n: int) -> np.ndarray:
+    out = np.zeros(n, np.uint32)
+    lib().oracle_pcg32(initstate, initseq, n, _ptr(out))
+    return out
+
+
+def trace(osc: OracleScene, o: np.ndarray, d: np.ndarray, brute=False):
+    o = np.ascontiguousarray(o, np.float64)
+    d = np.ascontiguousarray(d, np.float64)
+    n = o.shape[0]
+    t = np.zeros(n)
+    p = np.zeros(n, np.int32)
+    lib().oracle_trace(osc.handle, n, _ptr(o), _ptr(d), int(brute), _ptr(t), _ptr(p))
+    return t, p
+
+
+def bsdf_params(albedo=(0.5, 0.5, 0.5), alpha=0.3, f0=(0.04, 0.04, 0.04), eta=1.5, wd=0.8):
+    return np.array(list(albedo) + [alpha] + list(f0) + [eta, wd], np.float64)
+
+
+def bsdf_eval(bsdf, params, wi, wo):
+    f = np.zeros(3)
+    pdf = np.zeros(1)
+    lib().oracle_bsdf_eval(bsdf, _ptr(params), _ptr(np.asarray(wi, np.float64)),
+                           _ptr(np.asarray(wo, np.float64)), _ptr(f), _ptr(pdf))
+    return f, pdf[0]
+
+
+def bsdf_sample(bsdf, params, wi, u3, u4, u5):
+    wo = np.zeros(3)
+    ok = lib().oracle_bsdf_sample(bsdf, _ptr(params), _ptr(np.asarray(wi, np.float64)), u3, u4, u5, _ptr(wo))
+    return bool(ok), wo
+
+
+def bsdf_dfactors(bsdf, params, wi, wo):
+    out = np.zeros(6)
+    lib().oracle_bsdf_dfactors(bsdf, _ptr(params), _ptr(np.asarray(wi, np.float64)),
+                               _ptr(np.asarray(wo, np.float64)), _ptr(out))
+    return out[:3], out[3:]
+
+
+def fresnel(cos_i, eta):
+    return lib().oracle_fresnel(cos_i, eta)
+
+
+def env_pdf(osc: OracleScene, d):
+    return lib().oracle_env_pdf(osc.handle, _ptr(np.asarray(d, np.float64)))
+
+
+def frame(n):
+    s = np.zeros(3)
+    t = np.zeros(3)
+    lib().oracle_frame(_ptr(np.asarray(n, np.float64)), _ptr(s), _ptr(t))
+    return s, t

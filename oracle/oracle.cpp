@@ -1,0 +1,1250 @@
+// FP64 CPU oracle for the path-tracing megakernel and its reverse-mode derivative.
+//
+// TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the
+// benchmark's CPU-baseline leg may load this library.  It shares no code with
+// the CUDA path: its own PCG32, camera, BVH, intersection, BSDFs, emitter
+// sampling and gradient code, all in double precision, written for clarity.
+//
+// What it computes (Dr.Jit paper, Sec. 4.1 and Fig. 7): the Monte Carlo
+// estimate of a unidirectional path tracer with next-event estimation and
+// multiple importance sampling, pixel by pixel, with the same random numbers
+// the GPU kernel draws; and the derivative of that estimate with respect to
+// albedos, texels and roughness values with every random number fixed and the
+// sampling detached (Sec. 4.9: only BSDF *values* carry derivatives).  The
+// derivative is computed two ways, neither of which uses path replay:
+//   * oracle_grad_tape : reverse mode over a stored per-path vertex tape
+//                        (the "shadow memory" approach that PRB avoids, Sec. 2),
+//                        derivative factors written out analytically;
+//   * oracle_grad_dual : forward mode with dual numbers, derivative factors
+//                        obtained by automatic differentiation of the BSDF code.
+// The conventions the paper leaves open (RNG seeding, random-number layout,
+// depth convention, ray offsets, Fresnel, MIS, roulette) are fixed in
+// `render_sample` below and restated on the GPU side independently.
+//
+// Parity notes: no function here is "parity unpinned"; the pins are the
+// closed forms and finite-difference tests under tests/.
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+
+// ---------------------------------------------------------------- vectors
+struct V3 {
+  double x = 0, y = 0, z = 0;
+  V3() = default;
+  V3(double a, double b, double c) : x(a), y(b), z(c) {}
+  double operator[](int i) const { return i == 0 ? x : (i == 1 ? y : z); }
+  double& operator[](int i) { return i == 0 ? x : (i == 1 ? y : z); }
+};
+inline V3 operator+(V3 a, V3 b) { return {a.x + b.x, a.y + b.y, a.z + b.z}; }
+inline V3 operator-(V3 a, V3 b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
+inline V3 operator-(V3 a) { return {-a.x, -a.y, -a.z}; }
+inline V3 operator*(V3 a, double s) { return {a.x * s, a.y * s, a.z * s}; }
+inline V3 operator*(double s, V3 a) { return a * s; }
+inline V3 mul(V3 a, V3 b) { return {a.x * b.x, a.y * b.y, a.z * b.z}; }
+inline double dot(V3 a, V3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+inline V3 cross(V3 a, V3 b) {
+  return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+inline double length(V3 a) { return std::sqrt(dot(a, a)); }
+inline V3 normalize(V3 a) { return a * (1.0 / length(a)); }
+inline double max3(V3 a) { return std::max(a.x, std::max(a.y, a.z)); }
+
+// ---------------------------------------------------------------- PCG32
+// O'Neill (2014), "PCG: A family of simple fast space-efficient statistically
+// good algorithms for random number generation": 64-bit LCG state with the
+// XSH-RR output function; the paper uses it as its per-lane sampler (Sec. 3.1).
+struct Pcg32 {
+  uint64_t state = 0, inc = 0;
+  void seed(uint64_t initstate, uint64_t initseq) {
+    state = 0;
+    inc = (initseq << 1u) | 1u;
+    next_u32();
+    state += initstate;
+    next_u32();
+  }
+  uint32_t next_u32() {
+    uint64_t old = state;
+    state = old * 6364136223846793005ULL + inc;
+    uint32_t xorshifted = (uint32_t)(((old >> 18u) ^ old) >> 27u);
+    uint32_t rot = (uint32_t)(old >> 59u);
+    return (xorshifted >> rot) | (xorshifted << ((0u - rot) & 31u));
+  }
+  // 24 high bits -> [0,1): exact in both single and double precision.
+  double uniform() { return (double)(next_u32() >> 8) * (1.0 / 16777216.0); }
+};
+
+// ---------------------------------------------------------------- dual numbers
+// Forward-mode AD value with a fixed number of tangent slots.
+struct Dual {
+  double v = 0;
+  std::vector<double> d;
+  Dual() = default;
+  Dual(double val, size_t n) : v(val), d(n, 0.0) {}
+};
+inline size_t nd(const Dual& a, const Dual& b) { return std::max(a.d.size(), b.d.size()); }
+inline double tg(const Dual& a, size_t i) { return i < a.d.size() ? a.d[i] : 0.0; }
+inline Dual operator+(const Dual& a, const Dual& b) {
+  Dual r(a.v + b.v, nd(a, b));
+  for (size_t i = 0; i < r.d.size(); ++i) r.d[i] = tg(a, i) + tg(b, i);
+  return r;
+}
+inline Dual operator-(const Dual& a, const Dual& b) {
+  Dual r(a.v - b.v, nd(a, b));
+  for (size_t i = 0; i < r.d.size(); ++i) r.d[i] = tg(a, i) - tg(b, i);
+  return r;
+}
+inline Dual operator*(const Dual& a, const Dual& b) {
+  Dual r(a.v * b.v, nd(a, b));
+  for (size_t i = 0; i < r.d.size(); ++i) r.d[i] = tg(a, i) * b.v + a.v * tg(b, i);
+  return r;
+}
+inline Dual operator/(const Dual& a, const Dual& b) {
+  Dual r(a.v / b.v, nd(a, b));
+  for (size_t i = 0; i < r.d.size(); ++i) r.d[i] = (tg(a, i) * b.v - a.v * tg(b, i)) / (b.v * b.v);
+  return r;
+}
+inline Dual operator+(const Dual& a, double b) { Dual r = a; r.v += b; return r; }
+inline Dual operator+(double b, const Dual& a) { return a + b; }
+inline Dual operator-(const Dual& a, double b) { Dual r = a; r.v -= b; return r; }
+inline Dual operator-(double b, const Dual& a) { Dual r = a; r.v = b - a.v; for (auto& x : r.d) x = -x; return r; }
+inline Dual operator*(const Dual& a, double b) { Dual r = a; r.v *= b; for (auto& x : r.d) x *= b; return r; }
+inline Dual operator*(double b, const Dual& a) { return a * b; }
+inline Dual operator/(const Dual& a, double b) { return a * (1.0 / b); }
+inline Dual operator/(double b, const Dual& a) { return Dual(b, a.d.size()) / a; }
+inline Dual dsqrt(const Dual& a) {
+  Dual r = a;
+  r.v = std::sqrt(a.v);
+  for (auto& x : r.d) x = x / (2.0 * r.v);
+  return r;
+}
+inline double dsqrt(double a) { return std::sqrt(a); }
+inline double val(double a) { return a; }
+inline double val(const Dual& a) { return a.v; }
+
+// ---------------------------------------------------------------- scene
+enum { BSDF_NONE = 0, BSDF_DIFFUSE = 1, BSDF_CONDUCTOR = 2, BSDF_DIELECTRIC = 3, BSDF_BLEND = 4 };
+
+struct Shape {
+  int bsdf, tex, albedo_index, rough_index;
+  double alpha, eta, diffuse_weight;
+  V3 f0, emission;
+  bool emitter;
+};
+
+struct Texture {
+  int w = 0, h = 0;
+  std::vector<double> rgba;  // [h][w][4]
+};
+
+struct Node {  // binary BVH node of the oracle's own (median-split) tree
+  V3 lo, hi;
+  int left = -1, right = -1;  // children, or -1 for a leaf
+  int first = 0, count = 0;   // leaf: range into `order`
+};
+
+struct Scene {
+  int n_tris = 0;
+  std::vector<V3> v0, v1, v2;        // vertices (FP32 inputs widened to FP64)
+  std::vector<double> uv;            // [n][3][2]
+  std::vector<int> tri_shape;
+  std::vector<Shape> shapes;
+  std::vector<double> albedo;        // [A][3]
+  std::vector<Texture> tex;
+  std::vector<double> roughness;
+  // emitters (area lights): triangle ids and area CDF
+  std::vector<int> light_tris;
+  std::vector<double> light_cdf;     // normalised, size n+1
+  double light_area = 0;
+  // environment map
+  int env_w = 0, env_h = 0;
+  std::vector<double> env;           // [h][w][4]
+  std::vector<double> env_marg;      // normalised, size h+1
+  std::vector<double> env_cond;      // normalised per row, [h][w+1]
+  std::vector<double> env_p;         // pixel probability [h][w]
+  // BVH
+  std::vector<Node> nodes;
+  std::vector<int> order;
+};
+
+// oracle-side input record (plain pointers, host memory)
+}  // namespace
+
+extern "C" {
+typedef struct {
+  int n_tris;
+  const float* vertices;   // [n][3][3]
+  const float* uvs;        // [n][3][2]
+  const int* tri_shape;    // [n]
+  int n_shapes;
+  const int* bsdf;
+  const int* tex;
+  const int* albedo_index;
+  const int* rough_index;
+  const float* alpha;
+  const float* f0;         // [s][3]
+  const float* eta;
+  const float* emission;   // [s][3]
+  const float* diffuse_weight;
+  int n_albedo;
+  const float* albedo;     // [a][3]
+  int n_tex;
+  const float* const* tex_data;  // each [h][w][4]
+  const int* tex_w;
+  const int* tex_h;
+  int n_rough;
+  const float* roughness;
+  int env_w, env_h;
+  const float* env;        // [h][w][4] or NULL
+} oracle_scene_in;
+
+typedef struct {
+  double origin[3], target[3], up[3];
+  double vfov_deg;
+  int width, height;
+  int spp, max_depth, rr_depth, nee;
+  uint64_t seed;
+  int cam_index;
+  int crop_x0, crop_y0, crop_w, crop_h;  // crop_w == 0: whole image
+} oracle_render_in;
+}
+
+namespace {
+
+// ---------------------------------------------------------------- BVH (own, simple)
+// Object-median split on the longest centroid axis, leaves of <= 4 triangles.
+// Quality is irrelevant here; it only has to find the same closest hit as
+// brute force (pinned by tests).
+void tri_bounds(const Scene& s, int t, V3& lo, V3& hi) {
+  for (int k = 0; k < 3; ++k) {
+    double a = s.v0[t][k], b = s.v1[t][k], c = s.v2[t][k];
+    lo[k] = std::min(a, std::min(b, c));
+    hi[k] = std::max(a, std::max(b, c));
+  }
+}
+
+int build_node(Scene& s, int first, int count) {
+  Node n;
+  n.lo = V3(1e300, 1e300, 1e300);
+  n.hi = V3(-1e300, -1e300, -1e300);
+  for (int i = first; i < first + count; ++i) {
+    V3 lo, hi;
+    tri_bounds(s, s.order[i], lo, hi);
+    for (int k = 0; k < 3; ++k) {
+      n.lo[k] = std::min(n.lo[k], lo[k]);
+      n.hi[k] = std::max(n.hi[k], hi[k]);
+    }
+  }
+  // inflate slightly so that slab tests never reject a boundary hit
+  for (int k = 0; k < 3; ++k) {
+    double pad = 1e-9 * (1.0 + std::fabs(n.lo[k]) + std::fabs(n.hi[k]));
+    n.lo[k] -= pad;
+    n.hi[k] += pad;
+  }
+  int id = (int)s.nodes.size();
+  s.nodes.push_back(n);
+  if (count <= 4) {
+    s.nodes[id].first = first;
+    s.nodes[id].count = count;
+    return id;
+  }
+  V3 clo(1e300, 1e300, 1e300), chi(-1e300, -1e300, -1e300);
+  auto centroid = [&](int t) { return (s.v0[t] + s.v1[t] + s.v2[t]) * (1.0 / 3.0); };
+  for (int i = first; i < first + count; ++i) {
+    V3 c = centroid(s.order[i]);
+    for (int k = 0; k < 3; ++k) {
+      clo[k] = std::min(clo[k], c[k]);
+      chi[k] = std::max(chi[k], c[k]);
+    }
+  }
+  V3 ext = chi - clo;
+  int axis = (ext.x >= ext.y && ext.x >= ext.z) ? 0 : (ext.y >= ext.z ? 1 : 2);
+  int mid = first + count / 2;
+  std::nth_element(s.order.begin() + first, s.order.begin() + mid, s.order.begin() + first + count,
+                   [&](int a, int b) {
+                     double ca = centroid(a)[axis], cb = centroid(b)[axis];
+                     return ca < cb || (ca == cb && a < b);
+                   });
+  int l = build_node(s, first, mid - first);
+  int r = build_node(s, mid, first + count - mid);
+  s.nodes[id].left = l;
+  s.nodes[id].right = r;
+  return id;
+}
+
+bool hit_box(const Node& n, V3 o, V3 inv_d, double tmax) {
+  double t0 = 0.0, t1 = tmax;
+  for (int k = 0; k < 3; ++k) {
+    double a = (n.lo[k] - o[k]) * inv_d[k];
+    double b = (n.hi[k] - o[k]) * inv_d[k];
+    if (std::isnan(a) || std::isnan(b)) {  // 0 * inf: ray parallel and on the slab plane
+      if (o[k] < n.lo[k] || o[k] > n.hi[k]) return false;
+      continue;
+    }
+    if (a > b) std::swap(a, b);
+    t0 = std::max(t0, a);
+    t1 = std::min(t1, b);
+    if (t0 > t1) return false;
+  }
+  return true;
+}
+
+// Moller-Trumbore ray/triangle test in FP64.  Edges inclusive; det == 0 misses.
+bool intersect_tri(const Scene& s, int t, V3 o, V3 d, double& th, double& bu, double& bv) {
+  V3 e1 = s.v1[t] - s.v0[t];
+  V3 e2 = s.v2[t] - s.v0[t];
+  V3 p = cross(d, e2);
+  double det = dot(e1, p);
+  if (det == 0.0) return false;
+  double inv = 1.0 / det;
+  V3 sv = o - s.v0[t];
+  double u = dot(sv, p) * inv;
+  if (u < 0.0 || u > 1.0) return false;
+  V3 q = cross(sv, e1);
+  double v = dot(d, q) * inv;
+  if (v < 0.0 || u + v > 1.0) return false;
+  double tt = dot(e2, q) * inv;
+  if (!(tt > 0.0)) return false;
+  th = tt;
+  bu = u;
+  bv = v;
+  return true;
+}
+
+struct Hit {
+  int prim = -1;
+  double t = 0, u = 0, v = 0;
+};
+
+// Closest hit with t in (0, tmax); ties broken by the smaller triangle index.
+Hit closest_hit(const Scene& s, V3 o, V3 d, double tmax, bool brute) {
+  Hit h;
+  double best = tmax;
+  auto test = [&](int t) {
+    double th, u, v;
+    if (!intersect_tri(s, t, o, d, th, u, v)) return;
+    if (th < best || (h.prim >= 0 && th == best && t < h.prim)) {
+      best = th;
+      h.prim = t;
+      h.t = th;
+      h.u = u;
+      h.v = v;
+    }
+  };
+  if (brute || s.nodes.empty()) {
+    for (int t = 0; t < s.n_tris; ++t) test(t);
+    return h;
+  }
+  V3 inv(1.0 / d.x, 1.0 / d.y, 1.0 / d.z);
+  std::vector<int> stack;
+  stack.push_back(0);
+  while (!stack.empty()) {
+    int ni = stack.back();
+    stack.pop_back();
+    const Node& n = s.nodes[ni];
+    if (!hit_box(n, o, inv, best)) continue;
+    if (n.left < 0) {
+      for (int i = n.first; i < n.first + n.count; ++i) test(s.order[i]);
+    } else {
+      stack.push_back(n.left);
+      stack.push_back(n.right);
+    }
+  }
+  return h;
+}
+
+bool occluded(const Scene& s, V3 o, V3 d, double tmax) {
+  Hit h = closest_hit(s, o, d, tmax, false);
+  return h.prim >= 0;
+}
+
+V3 geo_normal(const Scene& s, int t) { return normalize(cross(s.v1[t] - s.v0[t], s.v2[t] - s.v0[t])); }
+
+// Ray origin offset: p + n_g * sign(n_g . d) * eps, eps = 1e-4 * max(1, max|p_i|).
+V3 offset_origin(V3 p, V3 ng, V3 d) {
+  double eps = 1e-4 * std::max(1.0, std::max(std::fabs(p.x), std::max(std::fabs(p.y), std::fabs(p.z))));
+  return p + ng * (dot(ng, d) >= 0.0 ? eps : -eps);
+}
+
+// ---------------------------------------------------------------- frames
+// Orthonormal basis around n (Duff et al. 2017, "Building an orthonormal basis,
+// revisited"), with the branch taken on n.z >= 0 so that +0 and -0 agree.
+struct Frame {
+  V3 s, t, n;
+  V3 to_local(V3 w) const { return {dot(w, s), dot(w, t), dot(w, n)}; }
+  V3 to_world(V3 v) const { return s * v.x + t * v.y + n * v.z; }
+};
+Frame make_frame(V3 n) {
+  double sign = n.z >= 0.0 ? 1.0 : -1.0;
+  double a = -1.0 / (sign + n.z);
+  double b = n.x * n.y * a;
+  Frame f;
+  f.n = n;
+  f.s = V3(1.0 + sign * n.x * n.x * a, sign * b, -sign * n.x);
+  f.t = V3(b, sign + n.y * n.y * a, -n.y);
+  return f;
+}
+
+// ---------------------------------------------------------------- BSDFs
+// Local shading space: the normal is +z and faces the incident direction wi.
+// Derivative-carrying inputs (albedo, alpha) are templated on T = double/Dual.
+template <class T>
+T ggx_D(const T& alpha, double cos_h) {
+  T a2 = alpha * alpha;
+  T den = (cos_h * cos_h) * (a2 - 1.0) + 1.0;
+  return a2 / (kPi * (den * den));
+}
+template <class T>
+T ggx_G1(const T& alpha, double cos_w) {
+  double tan2 = (1.0 - cos_w * cos_w) / (cos_w * cos_w);
+  return 2.0 / (1.0 + dsqrt(1.0 + (alpha * alpha) * tan2));
+}
+double schlick(double f0, double cos_d) {
+  double m = 1.0 - cos_d;
+  return f0 + (1.0 - f0) * m * m * m * m * m;
+}
+template <class T>
+void ggx_eval(const T& alpha, V3 f0, V3 wi, V3 wo, T out[3]) {
+  V3 h = normalize(wi + wo);
+  T D = ggx_D(alpha, h.z);
+  T G = ggx_G1(alpha, wi.z) * ggx_G1(alpha, wo.z);
+  double cd = dot(wi, h);
+  for (int c = 0; c < 3; ++c) out[c] = D * G * (schlick(f0[c], cd) / (4.0 * wi.z * wo.z));
+}
+double ggx_pdf(double alpha, V3 wi, V3 wo) {
+  V3 h = normalize(wi + wo);
+  double D = ggx_D<double>(alpha, h.z);
+  return D * h.z / (4.0 * std::fabs(dot(wo, h)));
+}
+// Walter et al. 2007 half-vector sampling: phi = 2 pi u4, tan^2 theta_h = a^2 u5 / (1 - u5)
+bool ggx_sample(double alpha, V3 wi, double u4, double u5, V3& wo) {
+  double phi = 2.0 * kPi * u4;
+  double tan2 = alpha * alpha * u5 / (1.0 - u5);
+  double cos_t = 1.0 / std::sqrt(1.0 + tan2);
+  double sin_t = std::sqrt(std::max(0.0, 1.0 - cos_t * cos_t));
+  V3 h(sin_t * std::cos(phi), sin_t * std::sin(phi), cos_t);
+  wo = h * (2.0 * dot(wi, h)) - wi;
+  return wo.z > 0.0;
+}
+
+// Cosine-weighted hemisphere, mapping of the ambient-occlusion example (Sec. 3.1):
+// phi = 2 pi u4, sin^2 theta = u5.
+V3 cosine_sample(double u4, double u5) {
+  double phi = 2.0 * kPi * u4;
+  double r = std::sqrt(u5);
+  return {std::cos(phi) * r, std::sin(phi) * r, std::sqrt(1.0 - u5)};
+}
+
+// The material seen at one vertex, with its differentiable inputs resolved.
+struct Mat {
+  int bsdf;
+  V3 albedo;        // diffuse / blend albedo
+  double alpha;     // GGX roughness
+  V3 f0;
+  double eta, wd;
+  // parameter references for gradients
+  int alb_kind;     // 0 none, 1 constant row, 2 texel
+  int alb_row, tex_id;
+  long long texel;  // linear texel index y*w + x
+  int rough;        // roughness entry or -1
+};
+
+template <class T>
+void bsdf_eval_t(const Mat& m, const T alb[3], const T& alpha, V3 wi, V3 wo, T out[3]) {
+  for (int c = 0; c < 3; ++c) out[c] = alb[c] * 0.0;
+  if (wi.z <= 0.0 || wo.z <= 0.0) return;
+  if (m.bsdf == BSDF_DIFFUSE) {
+    for (int c = 0; c < 3; ++c) out[c] = alb[c] * (1.0 / kPi);
+  } else if (m.bsdf == BSDF_CONDUCTOR) {
+    ggx_eval(alpha, m.f0, wi, wo, out);
+  } else if (m.bsdf == BSDF_BLEND) {
+    T g[3];
+    ggx_eval(alpha, m.f0, wi, wo, g);
+    for (int c = 0; c < 3; ++c) out[c] = alb[c] * (m.wd / kPi) + g[c] * (1.0 - m.wd);
+  }
+}
+V3 bsdf_eval(const Mat& m, V3 wi, V3 wo) {
+  double alb[3] = {m.albedo.x, m.albedo.y, m.albedo.z}, out[3];
+  bsdf_eval_t<double>(m, alb, m.alpha, wi, wo, out);
+  return {out[0], out[1], out[2]};
+}
+double bsdf_pdf(const Mat& m, V3 wi, V3 wo) {
+  if (wi.z <= 0.0 || wo.z <= 0.0) return 0.0;
+  if (m.bsdf == BSDF_DIFFUSE) return wo.z / kPi;
+  if (m.bsdf == BSDF_CONDUCTOR) return ggx_pdf(m.alpha, wi, wo);
+  if (m.bsdf == BSDF_BLEND) return m.wd * wo.z / kPi + (1.0 - m.wd) * ggx_pdf(m.alpha, wi, wo);
+  return 0.0;
+}
+
+// Analytic derivative factors (d f_c / d theta) / f_c for the stored-tape method.
+struct DFactors {
+  V3 d_alb;    // per channel: (d f_c / d albedo_c) / f_c
+  V3 d_alpha;  // per channel: (d f_c / d alpha) / f_c
+};
+DFactors bsdf_dfactors(const Mat& m, V3 wi, V3 wo) {
+  DFactors r;
+  V3 f = bsdf_eval(m, wi, wo);
+  if (wi.z <= 0.0 || wo.z <= 0.0) return r;
+  // d ln f_ggx / d alpha = 2/a - 4 a c^2 / (c^2 (a^2-1) + 1) - sum_w (a T_w / s_w) / (1 + s_w)
+  auto dlog_ggx = [&](double a) {
+    V3 h = normalize(wi + wo);
+    double c2 = h.z * h.z;
+    double r0 = 2.0 / a - 4.0 * a * c2 / (c2 * (a * a - 1.0) + 1.0);
+    for (double cw : {wi.z, wo.z}) {
+      double T = (1.0 - cw * cw) / (cw * cw);
+      double sw = std::sqrt(1.0 + a * a * T);
+      r0 -= (a * T / sw) / (1.0 + sw);
+    }
+    return r0;
+  };
+  if (m.bsdf == BSDF_DIFFUSE) {
+    for (int c = 0; c < 3; ++c) r.d_alb[c] = f[c] > 0 ? (1.0 / kPi) / f[c] : 0.0;
+  } else if (m.bsdf == BSDF_CONDUCTOR) {
+    double dl = dlog_ggx(m.alpha);
+    for (int c = 0; c < 3; ++c) r.d_alpha[c] = f[c] > 0 ? dl : 0.0;
+  } else if (m.bsdf == BSDF_BLEND) {
+    double alb0[3] = {0, 0, 0}, g[3];
+    Mat mg = m;
+    mg.bsdf = BSDF_CONDUCTOR;
+    bsdf_eval_t<double>(mg, alb0, m.alpha, wi, wo, g);
+    double dl = dlog_ggx(m.alpha);
+    for (int c = 0; c < 3; ++c) {
+      if (f[c] <= 0) continue;
+      r.d_alb[c] = (m.wd / kPi) / f[c];
+      r.d_alpha[c] = (1.0 - m.wd) * g[c] * dl / f[c];
+    }
+  }
+  return r;
+}
+
+// Exact unpolarised Fresnel reflectance of a smooth dielectric interface.
+// eta = n_t / n_i, cos_i >= 0.  Returns F and cos_t (0 on total internal reflection).
+double fresnel_dielectric(double cos_i, double eta, double& cos_t) {
+  double sin2_t = (1.0 - cos_i * cos_i) / (eta * eta);
+  if (sin2_t >= 1.0) {
+    cos_t = 0.0;
+    return 1.0;
+  }
+  cos_t = std::sqrt(1.0 - sin2_t);
+  double rs = (cos_i - eta * cos_t) / (cos_i + eta * cos_t);
+  double rp = (eta * cos_i - cos_t) / (eta * cos_i + cos_t);
+  return 0.5 * (rs * rs + rp * rp);
+}
+
+// ---------------------------------------------------------------- emitters
+V3 env_lookup(const Scene& s, V3 d, int& px, int& py) {
+  double phi = std::atan2(d.z, d.x);
+  if (phi < 0.0) phi += 2.0 * kPi;
+  double theta = std::acos(std::min(1.0, std::max(-1.0, d.y)));
+  double u = phi / (2.0 * kPi), v = theta / kPi;
+  px = std::min((int)(u * s.env_w), s.env_w - 1);
+  py = std::min((int)(v * s.env_h), s.env_h - 1);
+  const double* e = &s.env[((size_t)py * s.env_w + px) * 4];
+  return {e[0], e[1], e[2]};
+}
+// Solid-angle density of the environment sampler at direction d.
+double env_pdf(const Scene& s, V3 d) {
+  int px, py;
+  env_lookup(s, d, px, py);
+  double sin_t = std::sqrt(std::max(0.0, 1.0 - d.y * d.y));
+  if (sin_t == 0.0) return 0.0;
+  double p = s.env_p[(size_t)py * s.env_w + px] * s.env_w * s.env_h;
+  return p / (2.0 * kPi * kPi * sin_t);
+}
+// first index i with u < cdf[i+1]; cdf normalised, size n+1
+int cdf_pick(const double* cdf, int n, double u) {
+  int i = (int)(std::upper_bound(cdf + 1, cdf + n + 1, u) - (cdf + 1));
+  return std::min(std::max(i, 0), n - 1);
+}
+
+double power_heuristic(double a, double b) {
+  double a2 = a * a, b2 = b * b;
+  return (a2 + b2) > 0.0 ? a2 / (a2 + b2) : 0.0;
+}
+
+Mat resolve_material(const Scene& s, int shape, double tu, double tv) {
+  const Shape& sh = s.shapes[shape];
+  Mat m{};
+  m.bsdf = sh.bsdf;
+  m.alpha = sh.rough_index >= 0 ? s.roughness[sh.rough_index] : sh.alpha;
+  m.rough = sh.rough_index;
+  m.f0 = sh.f0;
+  m.eta = sh.eta;
+  m.wd = sh.diffuse_weight;
+  m.alb_kind = 0;
+  if (sh.bsdf == BSDF_DIFFUSE || sh.bsdf == BSDF_BLEND) {
+    if (sh.tex >= 0) {
+      // nearest lookup as in the paper's closure example (App. B):
+      // pos = min(uint(uv * res), res - 1), texel [pos.y, pos.x]
+      const Texture& t = s.tex[sh.tex];
+      int x = std::min((int)(std::max(tu, 0.0) * t.w), t.w - 1);
+      int y = std::min((int)(std::max(tv, 0.0) * t.h), t.h - 1);
+      const double* p = &t.rgba[((size_t)y * t.w + x) * 4];
+      m.albedo = V3(p[0], p[1], p[2]);
+      m.alb_kind = 2;
+      m.tex_id = sh.tex;
+      m.texel = (long long)y * t.w + x;
+    } else if (sh.albedo_index >= 0) {
+      const double* p = &s.albedo[(size_t)sh.albedo_index * 3];
+      m.albedo = V3(p[0], p[1], p[2]);
+      m.alb_kind = 1;
+      m.alb_row = sh.albedo_index;
+    }
+  }
+  return m;
+}
+
+// ---------------------------------------------------------------- integrator
+// FNV-1a over 32-bit words: a fingerprint of the discrete decisions of a path
+// (hit triangles, light picks, visibility, lobes, texels, roulette).
+struct DecisionHash {
+  uint32_t h = 2166136261u;
+  void add(uint32_t w) { h = (h ^ w) * 16777619u; }
+};
+
+struct Camera {
+  V3 o, fwd, right, up;
+  double tan_half, aspect;
+  int w, h;
+};
+Camera make_camera(const oracle_render_in& r) {
+  Camera c;
+  c.o = V3(r.origin[0], r.origin[1], r.origin[2]);
+  V3 t(r.target[0], r.target[1], r.target[2]);
+  V3 up(r.up[0], r.up[1], r.up[2]);
+  c.fwd = normalize(t - c.o);
+  c.right = normalize(cross(c.fwd, up));
+  c.up = cross(c.right, c.fwd);
+  c.tan_half = std::tan(0.5 * r.vfov_deg * kPi / 180.0);
+  c.w = r.width;
+  c.h = r.height;
+  c.aspect = (double)r.width / (double)r.height;
+  return c;
+}
+
+// Events reported by the integrator to an accumulator.  `scatter` is called
+// for every continued vertex with the throughput factor of the sampled
+// direction; the accumulators decide what to do with derivative information.
+struct VertexInfo {
+  Mat m;
+  V3 wi;        // local incident direction (toward the previous vertex)
+};
+
+template <class Acc>
+V3 render_sample(const Scene& s, const Camera& cam, const oracle_render_in& r, int px, int py,
+                 int spp_index, Acc& acc, uint32_t* hash_out) {
+  // RNG stream of this sample: (camera << 40) | (pixel << 12) | sample
+  Pcg32 rng;
+  uint64_t pixel = (uint64_t)py * (uint64_t)r.width + (uint64_t)px;
+  uint64_t stream = ((uint64_t)r.cam_index << 40) | (pixel << 12) | (uint64_t)spp_index;
+  rng.seed(r.seed, stream);
+  DecisionHash dh;
+
+  double j0 = rng.uniform(), j1 = rng.uniform();
+  double sx = (2.0 * (px + j0) / cam.w - 1.0) * cam.tan_half * cam.aspect;
+  double sy = (1.0 - 2.0 * (py + j1) / cam.h) * cam.tan_half;
+  V3 ro = cam.o;
+  V3 rd = normalize(cam.fwd + cam.right * sx + cam.up * sy);
+
+  bool has_area = !s.light_tris.empty();
+  bool has_env = s.env_w > 0;
+  double p_env = has_env ? (has_area ? 0.5 : 1.0) : 0.0;
+  double p_area = has_area ? 1.0 - p_env : 0.0;
+
+  V3 beta(1, 1, 1), L(0, 0, 0);
+  bool prev_delta = true;
+  double prev_pdf = 0.0;
+  for (int depth = 1;; ++depth) {
+    Hit hit = closest_hit(s, ro, rd, INFINITY, false);
+    dh.add(hit.prim < 0 ? 0xffffffffu : (uint32_t)hit.prim);
+    if (hit.prim < 0) {
+      if (has_env) {
+        int ex, ey;
+        V3 Le = env_lookup(s, rd, ex, ey);
+        double w = (prev_delta || !r.nee) ? 1.0 : power_heuristic(prev_pdf, p_env * env_pdf(s, rd));
+        V3 c = mul(beta, Le) * w;
+        L = L + c;
+        acc.emission(c, Le * w);
+      }
+      break;
+    }
+    int t = hit.prim;
+    const Shape& sh = s.shapes[s.tri_shape[t]];
+    V3 ng = geo_normal(s, t);
+    V3 wi_w = -rd;
+    double cos_front = dot(ng, wi_w);
+    if (sh.emitter && cos_front > 0.0) {
+      double w = 1.0;  // no MIS without light sampling or after a delta lobe
+      if (!prev_delta && r.nee) {
+        double pdf_l = p_area * hit.t * hit.t / (cos_front * s.light_area);
+        w = power_heuristic(prev_pdf, pdf_l);
+      }
+      V3 c = mul(beta, sh.emission) * w;
+      L = L + c;
+      acc.emission(c, sh.emission * w);
+    }
+    if (depth >= r.max_depth) break;
+    double u[8];
+    for (int k = 0; k < 8; ++k) u[k] = rng.uniform();
+    if (sh.bsdf == BSDF_NONE) break;
+
+    V3 p = ro + rd * hit.t;
+    const double* tuv = &s.uv[(size_t)t * 6];
+    double b0 = 1.0 - hit.u - hit.v;
+    double tu = b0 * tuv[0] + hit.u * tuv[2] + hit.v * tuv[4];
+    double tv = b0 * tuv[1] + hit.u * tuv[3] + hit.v * tuv[5];
+    VertexInfo vi;
+    vi.m = resolve_material(s, s.tri_shape[t], tu, tv);
+    dh.add(vi.m.alb_kind == 2 ? (uint32_t)vi.m.texel : 0xffffffffu);
+
+    if (sh.bsdf == BSDF_DIELECTRIC) {
+      bool entering = cos_front > 0.0;
+      V3 n = entering ? ng : -ng;
+      double eta = entering ? sh.eta : 1.0 / sh.eta;
+      double cos_i = dot(n, wi_w), cos_t;
+      double F = fresnel_dielectric(cos_i, eta, cos_t);
+      V3 wo;
+      double weight;
+      if (u[3] < F) {
+        wo = n * (2.0 * cos_i) - wi_w;
+        weight = 1.0;
+        dh.add(2);
+      } else {
+        wo = -wi_w * (1.0 / eta) + n * (cos_i / eta - cos_t);
+        weight = 1.0 / (eta * eta);
+        dh.add(3);
+      }
+      dh.add(0xfffffffeu);  // no light sample at a delta vertex
+      beta = beta * weight;
+      acc.scatter_delta(weight);
+      prev_delta = true;
+      prev_pdf = 0.0;
+      ro = offset_origin(p, ng, wo);
+      rd = wo;
+    } else {
+      V3 n = cos_front > 0.0 ? ng : -ng;
+      Frame fr = make_frame(n);
+      vi.wi = fr.to_local(wi_w);
+      // ---- next-event estimation
+      if (r.nee && (has_area || has_env)) {
+        bool pick_env = has_env && (!has_area || u[7] < 0.5);
+        V3 dir, Le;
+        double pdf_l = 0.0, dist = INFINITY;
+        bool valid = false;
+        if (pick_env) {
+          int y = cdf_pick(s.env_marg.data(), s.env_h, u[1]);
+          const double* cond = &s.env_cond[(size_t)y * (s.env_w + 1)];
+          int x = cdf_pick(cond, s.env_w, u[2]);
+          double fv = (u[1] - s.env_marg[y]) / (s.env_marg[y + 1] - s.env_marg[y]);
+          double fu = (u[2] - cond[x]) / (cond[x + 1] - cond[x]);
+          double theta = kPi * (y + fv) / s.env_h, phi = 2.0 * kPi * (x + fu) / s.env_w;
+          double st = std::sin(theta);
+          dir = V3(st * std::cos(phi), std::cos(theta), st * std::sin(phi));
+          const double* e = &s.env[((size_t)y * s.env_w + x) * 4];
+          Le = V3(e[0], e[1], e[2]);
+          double pdf_uv = s.env_p[(size_t)y * s.env_w + x] * s.env_w * s.env_h;
+          pdf_l = st > 0.0 ? p_env * pdf_uv / (2.0 * kPi * kPi * st) : 0.0;
+          valid = pdf_l > 0.0;
+          dh.add(0x80000000u | (uint32_t)(y * s.env_w + x));
+        } else {
+          int k = cdf_pick(s.light_cdf.data(), (int)s.light_tris.size(), u[0]);
+          int lt = s.light_tris[k];
+          double su = std::sqrt(u[1]);
+          double lb0 = 1.0 - su, lb1 = u[2] * su;
+          V3 q = s.v0[lt] * lb0 + s.v1[lt] * lb1 + s.v2[lt] * (1.0 - lb0 - lb1);
+          V3 dv = q - p;
+          dist = length(dv);
+          dir = dv * (1.0 / dist);
+          V3 nl = geo_normal(s, lt);
+          double cos_l = -dot(nl, dir);
+          Le = s.shapes[s.tri_shape[lt]].emission;
+          if (cos_l > 0.0 && dist > 0.0) {
+            pdf_l = p_area * dist * dist / (cos_l * s.light_area);
+            valid = true;
+          }
+          dh.add((uint32_t)lt);
+        }
+        V3 wl = fr.to_local(dir);
+        V3 f = bsdf_eval(vi.m, vi.wi, wl);
+        uint32_t vis_code = 2;
+        if (valid && wl.z > 0.0 && max3(f) > 0.0) {
+          V3 so = offset_origin(p, ng, dir);
+          double tmax = pick_env ? INFINITY : dist * (1.0 - 1e-3);
+          bool occ = occluded(s, so, dir, tmax);
+          vis_code = occ ? 1 : 0;
+          if (!occ) {
+            double w = power_heuristic(pdf_l, bsdf_pdf(vi.m, vi.wi, wl));
+            V3 scale = Le * (wl.z * w / pdf_l);  // everything but beta and f
+            V3 c = mul(mul(beta, f), scale);
+            L = L + c;
+            acc.nee(vi, wl, scale, c);
+          }
+        }
+        dh.add(vis_code);
+      }
+      // ---- BSDF sampling
+      V3 wo_l;
+      bool ok = true;
+      int lobe;
+      if (vi.m.bsdf == BSDF_DIFFUSE) {
+        wo_l = cosine_sample(u[4], u[5]);
+        lobe = 0;
+      } else if (vi.m.bsdf == BSDF_CONDUCTOR) {
+        ok = ggx_sample(vi.m.alpha, vi.wi, u[4], u[5], wo_l);
+        lobe = 1;
+      } else {  // blend
+        if (u[3] < vi.m.wd) {
+          wo_l = cosine_sample(u[4], u[5]);
+          lobe = 0;
+        } else {
+          ok = ggx_sample(vi.m.alpha, vi.wi, u[4], u[5], wo_l);
+          lobe = 1;
+        }
+      }
+      dh.add((uint32_t)lobe);
+      if (!ok) break;
+      double pdf = bsdf_pdf(vi.m, vi.wi, wo_l);
+      V3 f = bsdf_eval(vi.m, vi.wi, wo_l);
+      if (!(pdf > 0.0) || max3(f) <= 0.0) break;
+      double k = wo_l.z / pdf;
+      beta = mul(beta, f) * k;
+      acc.scatter(vi, wo_l, k);
+      prev_delta = false;
+      prev_pdf = pdf;
+      V3 wo = fr.to_world(wo_l);
+      ro = offset_origin(p, ng, wo);
+      rd = wo;
+    }
+    // ---- Russian roulette from depth rr_depth on
+    if (r.rr_depth >= 0 && depth >= r.rr_depth) {
+      double q = std::min(max3(beta), 0.95);
+      bool cont = u[6] < q;
+      dh.add(cont ? 1u : 0u);
+      if (!cont) break;
+      beta = beta * (1.0 / q);
+      acc.roulette(q);
+    }
+  }
+  if (hash_out) *hash_out = dh.h;
+  return L;
+}
+
+// Accumulator for the plain render: ignores events.
+struct NullAcc {
+  void emission(V3, V3) {}
+  void nee(const VertexInfo&, V3, V3, V3) {}
+  void scatter(const VertexInfo&, V3, double) {}
+  void scatter_delta(double) {}
+  void roulette(double) {}
+};
+
+// Stored-tape accumulator: keeps every vertex record, then runs a reverse sweep.
+struct TapeAcc {
+  struct Rec {
+    int kind;      // 0 emission, 1 nee, 2 scatter
+    V3 c;          // contribution (emission / nee)
+    Mat m;
+    V3 wi, wo;
+  };
+  std::vector<Rec> recs;
+  void emission(V3 c, V3) { recs.push_back({0, c, Mat{}, V3(), V3()}); }
+  void nee(const VertexInfo& v, V3 wl, V3, V3 c) { recs.push_back({1, c, v.m, v.wi, wl}); }
+  void scatter(const VertexInfo& v, V3 wo, double) { recs.push_back({2, V3(), v.m, v.wi, wo}); }
+  void scatter_delta(double) {}
+  void roulette(double) {}
+};
+
+struct GradOut {
+  std::vector<double> albedo;                 // [A][3]
+  std::vector<std::vector<double>> tex;       // each [h][w][4]
+  std::vector<double> rough;                  // [R]
+};
+
+void add_param_grad(GradOut& g, const Mat& m, V3 contrib, const DFactors& df, V3 dl) {
+  if (m.alb_kind == 1) {
+    for (int c = 0; c < 3; ++c) g.albedo[(size_t)m.alb_row * 3 + c] += dl[c] * contrib[c] * df.d_alb[c];
+  } else if (m.alb_kind == 2) {
+    for (int c = 0; c < 3; ++c) g.tex[m.tex_id][(size_t)m.texel * 4 + c] += dl[c] * contrib[c] * df.d_alb[c];
+  }
+  if (m.rough >= 0 && (m.bsdf == BSDF_CONDUCTOR || m.bsdf == BSDF_BLEND)) {
+    double s = 0.0;
+    for (int c = 0; c < 3; ++c) s += dl[c] * contrib[c] * df.d_alpha[c];
+    g.rough[m.rough] += s;
+  }
+}
+
+// Forward-mode accumulator: RGB dual throughput, dual radiance.
+struct SelParam {
+  int kind, a, b, c;  // 0: albedo (row a, channel b); 1: texel (tex a, texel b, channel c); 2: roughness a
+};
+struct DualAcc {
+  const std::vector<SelParam>* sel;
+  Dual beta[3], L[3];
+  size_t n;
+  void init(const std::vector<SelParam>* s) {
+    sel = s;
+    n = s->size();
+    for (int c = 0; c < 3; ++c) {
+      beta[c] = Dual(1.0, n);
+      L[c] = Dual(0.0, n);
+    }
+  }
+  void seeded_inputs(const Mat& m, Dual alb[3], Dual& alpha) const {
+    for (int c = 0; c < 3; ++c) alb[c] = Dual(m.albedo[c], n);
+    alpha = Dual(m.alpha, n);
+    for (size_t i = 0; i < n; ++i) {
+      const SelParam& p = (*sel)[i];
+      if (p.kind == 0 && m.alb_kind == 1 && m.alb_row == p.a) alb[p.b].d[i] = 1.0;
+      if (p.kind == 1 && m.alb_kind == 2 && m.tex_id == p.a && m.texel == p.b) alb[p.c].d[i] = 1.0;
+      if (p.kind == 2 && m.rough == p.a) alpha.d[i] = 1.0;
+    }
+  }
+  void emission(V3, V3 le_w) {
+    for (int c = 0; c < 3; ++c) L[c] = L[c] + beta[c] * le_w[c];
+  }
+  void nee(const VertexInfo& v, V3 wl, V3 scale, V3) {
+    Dual alb[3], alpha, f[3];
+    seeded_inputs(v.m, alb, alpha);
+    bsdf_eval_t<Dual>(v.m, alb, alpha, v.wi, wl, f);
+    for (int c = 0; c < 3; ++c) L[c] = L[c] + beta[c] * f[c] * scale[c];
+  }
+  void scatter(const VertexInfo& v, V3 wo, double k) {
+    Dual alb[3], alpha, f[3];
+    seeded_inputs(v.m, alb, alpha);
+    bsdf_eval_t<Dual>(v.m, alb, alpha, v.wi, wo, f);
+    for (int c = 0; c < 3; ++c) beta[c] = beta[c] * f[c] * k;
+  }
+  void scatter_delta(double w) {
+    for (int c = 0; c < 3; ++c) beta[c] = beta[c] * w;
+  }
+  void roulette(double q) {
+    for (int c = 0; c < 3; ++c) beta[c] = beta[c] * (1.0 / q);
+  }
+};
+
+// ---------------------------------------------------------------- parallel driver
+template <class F>
+void parallel_rows(int y0, int rows, int n_threads, F fn) {
+  if (n_threads <= 0) n_threads = (int)std::max(1u, std::thread::hardware_concurrency());
+  std::atomic<int> next(0);
+  std::vector<std::thread> ts;
+  for (int i = 0; i < n_threads; ++i)
+    ts.emplace_back([&]() {
+      for (;;) {
+        int r = next.fetch_add(1);
+        if (r >= rows) break;
+        fn(y0 + r);
+      }
+    });
+  for (auto& t : ts) t.join();
+}
+
+void crop_of(const oracle_render_in& r, int& x0, int& y0, int& cw, int& ch) {
+  x0 = r.crop_w > 0 ? r.crop_x0 : 0;
+  y0 = r.crop_w > 0 ? r.crop_y0 : 0;
+  cw = r.crop_w > 0 ? r.crop_w : r.width;
+  ch = r.crop_w > 0 ? r.crop_h : r.height;
+}
+
+}  // namespace
+
+extern "C" {
+
+// Copy the scene into FP64, build the oracle's BVH, the area-light CDF and the
+// environment-map distribution (luminance x sin(theta), marginal/conditional).
+void* oracle_scene_new(const oracle_scene_in* in) {
+  Scene* s = new Scene();
+  s->n_tris = in->n_tris;
+  for (int t = 0; t < in->n_tris; ++t) {
+    const float* v = in->vertices + (size_t)t * 9;
+    s->v0.emplace_back(v[0], v[1], v[2]);
+    s->v1.emplace_back(v[3], v[4], v[5]);
+    s->v2.emplace_back(v[6], v[7], v[8]);
+    for (int k = 0; k < 6; ++k) s->uv.push_back(in->uvs ? in->uvs[(size_t)t * 6 + k] : 0.0);
+    s->tri_shape.push_back(in->tri_shape[t]);
+  }
+  for (int i = 0; i < in->n_shapes; ++i) {
+    Shape sh;
+    sh.bsdf = in->bsdf[i];
+    sh.tex = in->tex[i];
+    sh.albedo_index = in->albedo_index[i];
+    sh.rough_index = in->rough_index[i];
+    sh.alpha = in->alpha[i];
+    sh.eta = in->eta[i];
+    sh.diffuse_weight = in->diffuse_weight[i];
+    sh.f0 = V3(in->f0[i * 3], in->f0[i * 3 + 1], in->f0[i * 3 + 2]);
+    sh.emission = V3(in->emission[i * 3], in->emission[i * 3 + 1], in->emission[i * 3 + 2]);
+    sh.emitter = max3(sh.emission) > 0.0;
+    s->shapes.push_back(sh);
+  }
+  s->albedo.assign(in->albedo, in->albedo + (size_t)in->n_albedo * 3);
+  for (int i = 0; i < in->n_tex; ++i) {
+    Texture t;
+    t.w = in->tex_w[i];
+    t.h = in->tex_h[i];
+    t.rgba.assign(in->tex_data[i], in->tex_data[i] + (size_t)t.w * t.h * 4);
+    s->tex.push_back(std::move(t));
+  }
+  s->roughness.assign(in->roughness, in->roughness + in->n_rough);
+  // area lights: every triangle of an emitting shape, picked proportionally to area
+  s->light_cdf.push_back(0.0);
+  for (int t = 0; t < s->n_tris; ++t) {
+    if (!s->shapes[s->tri_shape[t]].emitter) continue;
+    double a = 0.5 * length(cross(s->v1[t] - s->v0[t], s->v2[t] - s->v0[t]));
+    s->light_tris.push_back(t);
+    s->light_cdf.push_back(s->light_cdf.back() + a);
+  }
+  s->light_area = s->light_cdf.back();
+  for (auto& c : s->light_cdf) c = s->light_area > 0 ? c / s->light_area : 0.0;
+  // environment map
+  if (in->env && in->env_w > 0) {
+    s->env_w = in->env_w;
+    s->env_h = in->env_h;
+    size_t n = (size_t)s->env_w * s->env_h;
+    s->env.assign(in->env, in->env + n * 4);
+    std::vector<double> w(n);
+    double total = 0.0;
+    s->env_marg.assign(s->env_h + 1, 0.0);
+    s->env_cond.assign((size_t)s->env_h * (s->env_w + 1), 0.0);
+    for (int y = 0; y < s->env_h; ++y) {
+      double st = std::sin(kPi * (y + 0.5) / s->env_h);
+      double row = 0.0;
+      double* cond = &s->env_cond[(size_t)y * (s->env_w + 1)];
+      for (int x = 0; x < s->env_w; ++x) {
+        const double* e = &s->env[((size_t)y * s->env_w + x) * 4];
+        double lum = 0.2126 * e[0] + 0.7152 * e[1] + 0.0722 * e[2];
+        w[(size_t)y * s->env_w + x] = lum * st;
+        row += lum * st;
+        cond[x + 1] = row;
+      }
+      for (int x = 0; x <= s->env_w; ++x) cond[x] = row > 0 ? cond[x] / row : 0.0;
+      s->env_marg[y + 1] = s->env_marg[y] + row;
+      total += row;
+    }
+    for (auto& m : s->env_marg) m /= total;
+    s->env_p.resize(n);
+    for (size_t i = 0; i < n; ++i) s->env_p[i] = w[i] / total;
+  }
+  // BVH
+  s->order.resize(s->n_tris);
+  for (int t = 0; t < s->n_tris; ++t) s->order[t] = t;
+  if (s->n_tris > 0) build_node(*s, 0, s->n_tris);
+  return s;
+}
+
+void oracle_scene_free(void* sc) { delete (Scene*)sc; }
+
+// Mean over `spp` samples per pixel of the crop -> image [ch][cw][3].
+// Optional per-sample radiance [ch][cw][spp][3] and decision hashes [ch][cw][spp].
+int oracle_render(void* sc, const oracle_render_in* r, double* image, double* sample_L,
+                  uint32_t* sample_hash, int n_threads) {
+  const Scene& s = *(Scene*)sc;
+  Camera cam = make_camera(*r);
+  int x0, y0, cw, ch;
+  crop_of(*r, x0, y0, cw, ch);
+  parallel_rows(y0, ch, n_threads, [&](int py) {
+    for (int px = x0; px < x0 + cw; ++px) {
+      size_t pi = (size_t)(py - y0) * cw + (px - x0);
+      V3 sum(0, 0, 0);
+      for (int k = 0; k < r->spp; ++k) {
+        NullAcc acc;
+        uint32_t h;
+        V3 L = render_sample(s, cam, *r, px, py, k, acc, &h);
+        sum = sum + L;
+        size_t si = pi * r->spp + k;
+        if (sample_L)
+          for (int c = 0; c < 3; ++c) sample_L[si * 3 + c] = L[c];
+        if (sample_hash) sample_hash[si] = h;
+      }
+      for (int c = 0; c < 3; ++c) image[pi * 3 + c] = sum[c] / r->spp;
+    }
+  });
+  return 0;
+}
+
+// Gradient of sum(grad_image * image) by reverse mode over a stored per-path tape.
+// grad_image [ch][cw][3] is dLoss/dImage; each sample gets 1/spp of it.
+// Outputs are *overwritten*: g_albedo [A][3], g_tex[i] [h][w][4], g_rough [R] (any may be NULL).
+int oracle_grad_tape(void* sc, const oracle_render_in* r, const double* grad_image, double* g_albedo,
+                     double* const* g_tex, double* g_rough, int n_threads) {
+  const Scene& s = *(Scene*)sc;
+  Camera cam = make_camera(*r);
+  int x0, y0, cw, ch;
+  crop_of(*r, x0, y0, cw, ch);
+  GradOut total;
+  total.albedo.assign(s.albedo.size(), 0.0);
+  for (auto& t : s.tex) total.tex.emplace_back(t.rgba.size(), 0.0);
+  total.rough.assign(s.roughness.size(), 0.0);
+  std::mutex mu;
+  parallel_rows(y0, ch, n_threads, [&](int py) {
+    // one row's contributions, merged under the lock (texture buffers are shared)
+    GradOut row;
+    row.albedo.assign(s.albedo.size(), 0.0);
+    row.rough.assign(s.roughness.size(), 0.0);
+    struct TexAdd { int tex; size_t idx; double v; };
+    std::vector<TexAdd> tex_adds;
+    for (int px = x0; px < x0 + cw; ++px) {
+      size_t pi = (size_t)(py - y0) * cw + (px - x0);
+      V3 dl(grad_image[pi * 3] / r->spp, grad_image[pi * 3 + 1] / r->spp, grad_image[pi * 3 + 2] / r->spp);
+      for (int k = 0; k < r->spp; ++k) {
+        TapeAcc tape;
+        render_sample(s, cam, *r, px, py, k, tape, nullptr);
+        // reverse sweep: suffix sums of the recorded contributions give the
+        // radiance that flows through each sampled BSDF value (no subtraction);
+        // texel gradients go through a sparse list to keep per-row memory small
+        V3 suffix(0, 0, 0);
+        for (int i = (int)tape.recs.size() - 1; i >= 0; --i) {
+          const auto& rc = tape.recs[i];
+          if (rc.kind == 0) {
+            suffix = suffix + rc.c;
+            continue;
+          }
+          V3 contrib = rc.kind == 1 ? rc.c : suffix;
+          DFactors df = bsdf_dfactors(rc.m, rc.wi, rc.wo);
+          if (rc.m.alb_kind == 2) {
+            for (int c = 0; c < 3; ++c)
+              tex_adds.push_back({rc.m.tex_id, (size_t)rc.m.texel * 4 + c, dl[c] * contrib[c] * df.d_alb[c]});
+            Mat m2 = rc.m;
+            m2.alb_kind = 0;
+            add_param_grad(row, m2, contrib, df, dl);
+          } else {
+            add_param_grad(row, rc.m, contrib, df, dl);
+          }
+          if (rc.kind == 1) suffix = suffix + rc.c;
+        }
+      }
+    }
+    std::lock_guard<std::mutex> lk(mu);
+    for (size_t i = 0; i < row.albedo.size(); ++i) total.albedo[i] += row.albedo[i];
+    for (size_t i = 0; i < row.rough.size(); ++i) total.rough[i] += row.rough[i];
+    for (const auto& a : tex_adds) total.tex[a.tex][a.idx] += a.v;
+  });
+  if (g_albedo) std::memcpy(g_albedo, total.albedo.data(), total.albedo.size() * sizeof(double));
+  if (g_rough) std::memcpy(g_rough, total.rough.data(), total.rough.size() * sizeof(double));
+  if (g_tex)
+    for (size_t i = 0; i < total.tex.size(); ++i)
+      if (g_tex[i]) std::memcpy(g_tex[i], total.tex[i].data(), total.tex[i].size() * sizeof(double));
+  return 0;
+}
+
+// Gradient of sum(grad_image * image) w.r.t. a list of selected parameters by
+// forward-mode dual numbers.  sel: n_sel records of 4 ints (kind, a, b, c):
+//   kind 0 = albedo row a channel b; 1 = texture a, texel b, channel c; 2 = roughness a.
+int oracle_grad_dual(void* sc, const oracle_render_in* r, const double* grad_image, int n_sel,
+                     const int* sel, double* out, int n_threads) {
+  const Scene& s = *(Scene*)sc;
+  Camera cam = make_camera(*r);
+  int x0, y0, cw, ch;
+  crop_of(*r, x0, y0, cw, ch);
+  std::vector<SelParam> params;
+  for (int i = 0; i < n_sel; ++i) params.push_back({sel[i * 4], sel[i * 4 + 1], sel[i * 4 + 2], sel[i * 4 + 3]});
+  std::vector<double> total(n_sel, 0.0);
+  std::mutex mu;
+  parallel_rows(y0, ch, n_threads, [&](int py) {
+    std::vector<double> acc_row(n_sel, 0.0);
+    for (int px = x0; px < x0 + cw; ++px) {
+      size_t pi = (size_t)(py - y0) * cw + (px - x0);
+      for (int k = 0; k < r->spp; ++k) {
+        DualAcc acc;
+        acc.init(&params);
+        render_sample(s, cam, *r, px, py, k, acc, nullptr);
+        for (int c = 0; c < 3; ++c) {
+          double dl = grad_image[pi * 3 + c] / r->spp;
+          for (int i = 0; i < n_sel; ++i) acc_row[i] += dl * tg(acc.L[c], i);
+        }
+      }
+    }
+    std::lock_guard<std::mutex> lk(mu);
+    for (int i = 0; i < n_sel; ++i) total[i] += acc_row[i];
+  });
+  std::memcpy(out, total.data(), n_sel * sizeof(double));
+  return 0;
+}
+
+// ---------------------------------------------------------------- unit-test hooks
+void oracle_pcg32(uint64_t initstate, uint64_t initseq, int n, uint32_t* out) {
+  Pcg32 r;
+  r.seed(initstate, initseq);
+  for (int i = 0; i < n; ++i) out[i] = r.next_u32();
+}
+
+// Closest hits for n rays (o,d: [n][3]); prim = -1 on a miss.
+void oracle_trace(void* sc, int n, const double* o, const double* d, int brute, double* t_out, int* prim_out) {
+  const Scene& s = *(Scene*)sc;
+  for (int i = 0; i < n; ++i) {
+    Hit h = closest_hit(s, V3(o[i * 3], o[i * 3 + 1], o[i * 3 + 2]), V3(d[i * 3], d[i * 3 + 1], d[i * 3 + 2]),
+                        INFINITY, brute != 0);
+    t_out[i] = h.prim >= 0 ? h.t : INFINITY;
+    prim_out[i] = h.prim;
+  }
+}
+
+// BSDF hooks in local space (normal +z).  params: albedo[3], alpha, f0[3], eta, wd.
+static Mat hook_mat(int bsdf, const double* p) {
+  Mat m{};
+  m.bsdf = bsdf;
+  m.albedo = V3(p[0], p[1], p[2]);
+  m.alpha = p[3];
+  m.f0 = V3(p[4], p[5], p[6]);
+  m.eta = p[7];
+  m.wd = p[8];
+  m.rough = -1;
+  return m;
+}
+void oracle_bsdf_eval(int bsdf, const double* params, const double* wi, const double* wo, double* f_out,
+                      double* pdf_out) {
+  Mat m = hook_mat(bsdf, params);
+  V3 a(wi[0], wi[1], wi[2]), b(wo[0], wo[1], wo[2]);
+  V3 f = bsdf_eval(m, a, b);
+  for (int c = 0; c < 3; ++c) f_out[c] = f[c];
+  *pdf_out = bsdf_pdf(m, a, b);
+}
+// Returns 1 and wo if sampling succeeded (non-delta BSDFs).
+int oracle_bsdf_sample(int bsdf, const double* params, const double* wi, double u3, double u4, double u5,
+                       double* wo_out) {
+  Mat m = hook_mat(bsdf, params);
+  V3 a(wi[0], wi[1], wi[2]), wo;
+  bool ok = true;
+  if (bsdf == BSDF_DIFFUSE || (bsdf == BSDF_BLEND && u3 < m.wd)) {
+    wo = cosine_sample(u4, u5);
+  } else {
+    ok = ggx_sample(m.alpha, a, u4, u5, wo);
+  }
+  wo_out[0] = wo.x;
+  wo_out[1] = wo.y;
+  wo_out[2] = wo.z;
+  return ok ? 1 : 0;
+}
+// Analytic derivative factors: d_alb[3], d_alpha[3].
+void oracle_bsdf_dfactors(int bsdf, const double* params, const double* wi, const double* wo, double* out6) {
+  Mat m = hook_mat(bsdf, params);
+  DFactors df = bsdf_dfactors(m, V3(wi[0], wi[1], wi[2]), V3(wo[0], wo[1], wo[2]));
+  for (int c = 0; c < 3; ++c) {
+    out6[c] = df.d_alb[c];
+    out6[3 + c] = df.d_alpha[c];
+  }
+}
+double oracle_fresnel(double cos_i, double eta) {
+  double ct;
+  return fresnel_dielectric(cos_i, eta, ct);
+}
+double oracle_env_pdf(void* sc, const double* d) { return env_pdf(*(Scene*)sc, V3(d[0], d[1], d[2])); }
+int oracle_frame(const double* n, double* s_out, double* t_out) {
+  Frame f = make_frame(V3(n[0], n[1], n[2]));
+  for (int k = 0; k < 3; ++k) {
+    s_out[k] = f.s[k];
+    t_out[k] = f.t[k];
+  }
+  return 0;
+}
+
+}  // extern "C"
