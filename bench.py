@@ -1,0 +1,351 @@
+#!/usr/bin/env python3
+"""Throughput benchmark: Mrays/s of forward + PRB adjoint on one GB300 (per rank).
+
+Workload (the forward-throughput configuration): 32 noise-displaced level-4
+icospheres (5,120 triangles each) on a 128x128-quad ground plane (196,608
+triangles), textured diffuse / GGX conductor / dielectric, 512x256 sky
+environment map, 1024x1024 pixels, 64 spp, max depth 8, Russian roulette from
+depth 3.  One step = one forward render (megakernel) + one adjoint render (path
+replay backpropagation, decorrelated seed) with the L2-loss image gradient
+against a fixed target, gradients into the 1024^2 RGBA texture and the
+conductor roughness values.  Rays = closest-hit + shadow rays, counted by an
+instrumented launch of the same step before timing.
+
+Prints ONE JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle
+on a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Mrays/s fwd+adjoint on 1 GB300 vs roofline; equal-time MSE, cache vs plain PT"
+WORKLOAD = dict(workload="spheres32x5120 + ground 128^2 (196,608 tris), 1024x1024, 64 spp, depth 8, RR from 3, "
+                         "forward + PRB adjoint (texture 1024^2 RGBA + roughness gradients)",
+                width=1024, height=1024, spp=64, max_depth=8, rr_depth=3)
+FLOPS_PER_NODE = 44     # binary node: two child slab tests (12 FMA = 24 flops, 10 min/max, 2 compares, ordering)
+FLOPS_PER_TRI = 45      # Moller-Trumbore: 2 cross, 4 dot, 1 div, 4 mul, 3 sub (FMA = 2 flops)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--dispatch", type=int, default=0)
+    ap.add_argument("--lanes", type=int, default=0)
+    ap.add_argument("--block", type=int, default=0)
+    ap.add_argument("--tex-aggregate", type=int, default=0)
+    ap.add_argument("--small", action="store_true",
+                    help="profiling case: same scene and step at 256x256, 16 spp (not a bench line)")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi sampled every 200 ms during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[4:8]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- workload
+def make_workload(seed=2022, small=False):
+    from paper_2202_01284_gb300 import scenes as S
+    sc = S.spheres(seed, width=256, height=256) if small else S.spheres(seed)
+    tgt_tex = S.spheres_target_texture(sc.textures[0], seed)
+    return sc, tgt_tex
+
+
+def settings(args, seed):
+    from paper_2202_01284_gb300.render import RenderSettings
+    if args.small:
+        return RenderSettings(width=256, height=256, spp=16, max_depth=WORKLOAD["max_depth"],
+                              rr_depth=WORKLOAD["rr_depth"], seed=seed, dispatch=args.dispatch,
+                              lanes_per_pixel=args.lanes, block_size=args.block, tex_aggregate=args.tex_aggregate)
+    return RenderSettings(width=WORKLOAD["width"], height=WORKLOAD["height"], spp=WORKLOAD["spp"],
+                          max_depth=WORKLOAD["max_depth"], rr_depth=WORKLOAD["rr_depth"], seed=seed,
+                          dispatch=args.dispatch, lanes_per_pixel=args.lanes, block_size=args.block,
+                          tex_aggregate=args.tex_aggregate)
+
+
+def cpu_baseline_run(sc, seconds_target=15.0, steps=1):
+    """The FP64 oracle as it stands on the host cores, on a bounded crop of the workload."""
+    import numpy as np
+    import oracle
+    osc = oracle.OracleScene(sc)
+    cam = sc.cameras[0]
+    crop = (448, 448, 128, 128)
+    spp = 64
+    r = oracle.render_in(cam, spp, WORKLOAD["max_depth"], 11, WORKLOAD["rr_depth"], True, crop=crop)
+    cores = os.cpu_count() or 1
+    vals = []
+    total_rays = 0
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        img, rays_f = oracle.render(osc, r, threads=cores, count_rays=True)
+        gi = 2 * (img - 0.5) / img.size
+        *_, rays_b = oracle.grad_tape(osc, r, gi, threads=cores, count_rays=True)
+        dt = time.perf_counter() - t0
+        vals.append((rays_f + rays_b) / dt / 1e6)
+        total_rays += rays_f + rays_b
+    return {"value": statistics.median(vals), "unit": "Mrays/s", "cores": cores, "kind": "oracle",
+            "sample": f"{crop[2]}x{crop[3]} pixel crop at ({crop[0]},{crop[1]}), {spp} spp, depth 8, RR 3: "
+                      f"FP64 render + stored-tape adjoint, {total_rays} rays"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    sc, _ = make_workload()
+    steps = max(1, args.steps)
+    for _ in range(max(0, min(args.warmup, 1))):
+        cpu_baseline_run(sc, steps=1)
+    cb = cpu_baseline_run(sc, steps=steps)
+    line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": "Mrays/s", "n_gpus": args.gpus,
+            "steps": steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {**WORKLOAD, "sample": cb["sample"]},
+            "cpu_baseline": cb, "e2e": {"value": cb["value"], "unit": "Mrays/s", "h2d_bytes_per_step": 0,
+                                        "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2202_01284_gb300 import abi
+    from paper_2202_01284_gb300.render import DeviceScene
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    abi.load()
+
+    sc, tgt_tex = make_workload(small=args.small)
+    ds = DeviceScene(sc, device=dev)
+    seed_fwd, seed_bwd = 1000 + 2 * rank, 1001 + 2 * rank
+    st_f = settings(args, seed_fwd)
+    # fixed target image (rendered once) -> dLoss/dImage for the adjoint
+    target = ds.forward(settings(args, 77), textures=[torch.as_tensor(tgt_tex, device=dev)]).clone()
+    img = torch.empty_like(target)
+    g_tex = torch.zeros_like(ds.textures[0])
+    g_rough = torch.zeros_like(ds.roughness)
+    grad_img = torch.empty_like(target)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2 (129 MB)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(ev=None):
+        if ev is not None:
+            ev[0].record(stream)
+        ds.forward(st_f, out=img)
+        if ev is not None:
+            ev[1].record(stream)
+        torch.sub(img, target, out=grad_img)
+        grad_img.mul_(2.0 / img.numel())
+        if ev is not None:
+            ev[2].record(stream)
+        ds.backward(st_f, grad_img, g_textures=[g_tex], g_roughness=g_rough, seed=seed_bwd)
+        if ev is not None:
+            ev[3].record(stream)
+
+    # ray counts of one step (instrumented launches of the identical work)
+    cf = torch.zeros(abi.PT_N_COUNTERS, dtype=torch.int64, device=dev)
+    cb = torch.zeros(abi.PT_N_COUNTERS, dtype=torch.int64, device=dev)
+    ds.forward(st_f, out=img, counters=cf)
+    torch.sub(img, target, out=grad_img)
+    grad_img.mul_(2.0 / img.numel())
+    ds.backward(st_f, grad_img, g_textures=[torch.zeros_like(g_tex)], g_roughness=torch.zeros_like(g_rough),
+                seed=seed_bwd, counters=cb)
+    torch.cuda.synchronize()
+    cf, cb = cf.cpu().numpy(), cb.cpu().numpy()
+    rays_f = int(cf[1] + cf[2])
+    rays_b = int(cb[1] + cb[2])
+    rays_step = rays_f + rays_b
+    flops_f = FLOPS_PER_NODE * int(cf[3]) + FLOPS_PER_TRI * int(cf[4])
+    flops_b = FLOPS_PER_NODE * int(cb[3]) + FLOPS_PER_TRI * int(cb[4])
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.fill_(float(k))       # evict L2 between timed steps (outside the events)
+        step(evs[k])
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    clk = clocks.stop()
+    if world > 1:
+        dist.barrier()
+    fwd_ms = [e[0].elapsed_time(e[1]) for e in evs]
+    adj_ms = [e[2].elapsed_time(e[3]) for e in evs]
+    step_ms = [e[0].elapsed_time(e[3]) for e in evs]
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = rays_step * args.steps * world / (total_ms / 1e3) / 1e6
+
+    # ---- end to end through the C ABI with host buffers (pinned), copies inside the timed region
+    h_tex = torch.as_tensor(sc.textures[0]).pin_memory()
+    h_rough = torch.as_tensor(sc.roughness).pin_memory()
+    h_img = torch.empty(img.shape, dtype=torch.float32).pin_memory()
+    h_gtex = torch.empty(g_tex.shape, dtype=torch.float32).pin_memory()
+    h_grough = torch.empty(g_rough.shape, dtype=torch.float32).pin_memory()
+    d_tex = torch.empty_like(ds.textures[0])
+    d_rough = torch.empty_like(ds.roughness)
+
+    def e2e_step():
+        d_tex.copy_(h_tex, non_blocking=True)
+        d_rough.copy_(h_rough, non_blocking=True)
+        ds.forward(st_f, out=img, textures=[d_tex], roughness=d_rough)
+        torch.sub(img, target, out=grad_img)
+        grad_img.mul_(2.0 / img.numel())
+        g_tex.zero_()
+        g_rough.zero_()
+        ds.backward(st_f, grad_img, textures=[d_tex], roughness=d_rough, g_textures=[g_tex], g_roughness=g_rough,
+                    seed=seed_bwd)
+        h_img.copy_(img, non_blocking=True)
+        h_gtex.copy_(g_tex, non_blocking=True)
+        h_grough.copy_(g_rough, non_blocking=True)
+    e2e_step()
+    torch.cuda.synchronize()
+    e_steps = max(2, min(args.steps, 5))
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(e_steps):
+        e2e_step()
+    b.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = a.elapsed_time(b) / e_steps
+    h2d = h_tex.numel() * 4 + h_rough.numel() * 4
+    d2h = h_img.numel() * 4 + h_gtex.numel() * 4 + h_grough.numel() * 4
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    fwd_avg, adj_avg = statistics.mean(fwd_ms), statistics.mean(adj_ms)
+    dom = "adjoint_kernel" if adj_avg >= fwd_avg else "forward_kernel"
+    dom_ms = max(adj_avg, fwd_avg)
+    dom_flops = flops_b if adj_avg >= fwd_avg else flops_f
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = clk.get("sm_mhz") or 1477.0
+    peak_tflops = sms * 128 * 2 * mhz * 1e6 / 1e12
+    achieved = dom_flops / (dom_ms / 1e3) / 1e12
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        try:
+            cpu = cpu_baseline_run(sc)
+        except Exception as e:  # the oracle is optional for the GPU number
+            cpu = {"error": str(e)}
+    info = ds.info()
+    line = {
+        "metric": METRIC, "value": round(value, 2), "unit": "Mrays/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {**WORKLOAD, "l2": "flushed between timed steps (256 MB write)", "dispatch": args.dispatch,
+                   "bvh": "binary SAH", "bvh_nodes": info["n_nodes"], "rays_per_step": rays_step,
+                   "rays_fwd": rays_f, "rays_adj": rays_b, "fwd_ms": round(fwd_avg, 3),
+                   "adj_ms": round(adj_avg, 3), "fwd_mrays_s": round(rays_f / fwd_avg / 1e3, 1),
+                   "adj_mrays_s": round(rays_b / adj_avg / 1e3, 1),
+                   "node_visits_per_ray_fwd": round(int(cf[3]) / max(rays_f, 1), 2),
+                   "tri_tests_per_ray_fwd": round(int(cf[4]) / max(rays_f, 1), 2),
+                   "grad_terms": int(cb[7]), "grad_atomics": int(cb[6])},
+        "roofline": {"bound": "alu", "kernel": dom, "achieved": round(achieved, 3),
+                     "peak": round(peak_tflops, 2), "unit": "TFLOP/s", "frac": round(achieved / peak_tflops, 4),
+                     "traffic": None,
+                     "work": f"{FLOPS_PER_NODE}/node visit + {FLOPS_PER_TRI}/triangle test (counted launch)",
+                     "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 x median SM clock {mhz} MHz"},
+        "cpu_baseline": cpu,
+        "e2e": {"value": round(rays_step / (e2e_ms / 1e3) / 1e6, 2), "unit": "Mrays/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "ms_per_step": round(e2e_ms, 3)},
+        "gpu_launches": 2 * args.steps,
+        "clocks": clk,
+        "wall_s": round(wall, 3),
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

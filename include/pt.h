@@ -1,0 +1,217 @@
+/*
+ * pt.h -- C ABI of the GB300 path-tracing megakernel and its PRB adjoint.
+ *
+ * The library renders images with a unidirectional path tracer and
+ * differentiates a loss on them with respect to scene parameters, the problem
+ * stated in the introduction of the Dr.Jit paper (Sec. 1) and decomposed into
+ * megakernels in Fig. 7 (Sec. 4):
+ *   - pt_render_forward  : megakernel #1, the primal path tracer;
+ *   - pt_render_backward : megakernels #2 + #3 fused, Path Replay
+ *                          Backpropagation (Sec. 4.1) with detached BSDF
+ *                          sampling and attached BSDF values (Sec. 4.9);
+ *   - pt_cache_*         : a learned radiance cache that terminates paths
+ *                          (not in the paper; the paper mentions caches only
+ *                          as future work, Sec. 3.2);
+ *   - pt_render_batch    : many cameras/scenes in one persistent launch.
+ *
+ * Conventions
+ *   - Every function returns PT_OK (0) or a negative PT_ERR_* code; nothing
+ *     aborts.  pt_status_string() names a code.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *     Rendering calls are asynchronous on it; device-side faults the kernels
+ *     detect (e.g. BVH stack overflow, queue timeouts) are recorded in a
+ *     per-scene status word read by pt_last_device_status().
+ *   - Scene geometry and materials are COPIED into library-owned device memory
+ *     by pt_scene_create.  Differentiable parameters (pt_params) and gradient
+ *     buffers (pt_grads) are BORROWED device pointers: they must stay valid
+ *     until the stream has passed the call.  Gradients are ACCUMULATED (+=),
+ *     never cleared by the library.
+ *   - Images are float32 RGB, row-major [n_cams][rows][cols][3], row 0 = top.
+ *     With a crop rectangle, rows/cols are the crop's.
+ *   - The kernels need no scratch memory beyond their inputs and outputs.
+ */
+#ifndef PT_H_
+#define PT_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------ status */
+#define PT_OK 0
+#define PT_ERR_ARG (-1)      /* invalid argument or descriptor */
+#define PT_ERR_CUDA (-2)     /* a CUDA runtime call failed */
+#define PT_ERR_OOM (-3)      /* device allocation failed */
+#define PT_ERR_TIMEOUT (-4)  /* a bounded device-side wait gave up */
+#define PT_ERR_BVH (-5)      /* BVH missing, or traversal stack overflow */
+#define PT_ERR_STATE (-6)    /* call order violated (e.g. render before bvh_build) */
+
+/* ------------------------------------------------------------------ limits */
+#define PT_MAX_TEX 8      /* texture slots per scene */
+#define PT_MAX_CAMS 64    /* cameras per pt_render_forward/backward call */
+
+/* ------------------------------------------------------------------ materials
+ * BSDF codes (the polymorphic call of Sec. 3.1/3.3: one code path per type,
+ * dispatched per lane):
+ *   NONE       black; a path that reaches it stops (pure emitters).
+ *   DIFFUSE    Lambertian, f = albedo/pi; albedo constant or textured.
+ *   CONDUCTOR  rough GGX microfacet conductor, Schlick Fresnel (F0 per shape),
+ *              uncorrelated Smith shadowing, Walter-2007 half-vector sampling.
+ *   DIELECTRIC smooth interface of relative IOR eta, exact Fresnel.
+ *   BLEND      w * diffuse + (1-w) * GGX conductor (the lobe is chosen with
+ *              probabilities w, 1-w).
+ */
+enum { PT_BSDF_NONE = 0, PT_BSDF_DIFFUSE = 1, PT_BSDF_CONDUCTOR = 2, PT_BSDF_DIELECTRIC = 3, PT_BSDF_BLEND = 4 };
+
+/* One shape record (the closure data of App. B: scalars inline, textures by
+ * slot).  A triangle's shape is tri_shape[t]. */
+typedef struct {
+  int32_t bsdf;          /* PT_BSDF_* */
+  int32_t tex;           /* texture slot of the albedo (DIFFUSE/BLEND), -1 = constant */
+  int32_t albedo_index;  /* row of pt_params.albedo used when tex < 0, -1 = black */
+  int32_t rough_index;   /* entry of pt_params.roughness, -1 = use `alpha` */
+  float alpha;           /* fixed GGX roughness when rough_index < 0 */
+  float eta;             /* DIELECTRIC: interior/exterior IOR */
+  float diffuse_weight;  /* BLEND: w */
+  float f0[3];           /* CONDUCTOR/BLEND: Schlick reflectance at normal incidence */
+  float emission[3];     /* radiance emitted on the front side (normal = (v1-v0)x(v2-v0)) */
+} pt_shape;
+
+/* Scene input (host memory, copied). */
+typedef struct {
+  int32_t n_tris;
+  const float* vertices;     /* [n_tris][3][3] */
+  const float* uvs;          /* [n_tris][3][2] or NULL (all zero) */
+  const int32_t* tri_shape;  /* [n_tris] */
+  int32_t n_shapes;
+  const pt_shape* shapes;    /* [n_shapes] */
+  int32_t env_w, env_h;      /* environment map size, 0 = none */
+  const float* env;          /* [env_h][env_w][4] RGBA, equirectangular, row 0 looks along +y,
+                                column angle from +x toward +z */
+} pt_scene_desc;
+
+typedef struct pt_scene pt_scene;
+
+/* Copy geometry, shape table and environment map to the device, and build the
+ * emitter tables (area-proportional triangle CDF; environment map marginal and
+ * conditional CDFs over luminance x sin(theta)).  Synchronous.  *out receives
+ * a handle owned by the caller (pt_scene_destroy).
+ * Errors: PT_ERR_ARG (NULL pointers, n_tris <= 0, shape index out of range,
+ * bad BSDF code, tex slot >= PT_MAX_TEX), PT_ERR_OOM, PT_ERR_CUDA. */
+int pt_scene_create(const pt_scene_desc* desc, pt_scene** out);
+void pt_scene_destroy(pt_scene* scene);
+
+/* ------------------------------------------------------------------ BVH */
+enum { PT_BVH_BINARY = 0, PT_BVH_WIDE = 1 };
+typedef struct {
+  int32_t layout;        /* PT_BVH_BINARY (2-wide, float boxes) or PT_BVH_WIDE
+                            (8-wide, 8-bit quantised child boxes) */
+  int32_t max_leaf_tris; /* 1..8 for BINARY, 1..3 for WIDE (0 = default 4 / 3) */
+  int32_t n_bins;        /* SAH bins, 4..64 (0 = 32) */
+} pt_bvh_opts;
+
+/* Build the acceleration structure on the host (binned SAH over triangle
+ * centroids, Sec. 3.1 delegates this to Embree/OptiX; here it is our own) and
+ * upload it.  Re-callable; replaces the previous BVH.  Synchronous.
+ * opts may be NULL (defaults).  Errors: PT_ERR_ARG, PT_ERR_OOM, PT_ERR_CUDA. */
+int pt_bvh_build(pt_scene* scene, const pt_bvh_opts* opts);
+
+typedef struct {
+  int64_t n_tris, n_nodes, node_bytes, tri_bytes, env_bytes;
+  int32_t layout, depth;
+  double sah_cost;
+} pt_scene_info;
+int pt_scene_get_info(const pt_scene* scene, pt_scene_info* info);
+
+/* ------------------------------------------------------------------ rendering */
+typedef struct {
+  float origin[3], target[3], up[3];
+  float vfov_deg;  /* vertical field of view of the pinhole */
+} pt_camera;
+
+enum { PT_DISPATCH_SWITCH = 0, PT_DISPATCH_MATCH = 1 };
+
+/* Counters filled by instrumented launches (pt_render_desc.counters). */
+enum {
+  PT_CNT_PATHS = 0,      /* camera samples traced */
+  PT_CNT_RAYS = 1,       /* closest-hit rays (camera + continuation) */
+  PT_CNT_SHADOW = 2,     /* shadow (any-hit) rays */
+  PT_CNT_NODES = 3,      /* BVH nodes visited (all rays) */
+  PT_CNT_TRIS = 4,       /* ray/triangle tests */
+  PT_CNT_TEX = 5,        /* texture lookups */
+  PT_CNT_ATOMICS = 6,    /* gradient atomics issued after aggregation */
+  PT_CNT_GRAD_TERMS = 7, /* gradient terms before aggregation */
+  PT_N_COUNTERS = 16
+};
+
+typedef struct {
+  int32_t n_cams;             /* 1..PT_MAX_CAMS; cameras share size and spp */
+  const pt_camera* cams;      /* host [n_cams]; camera i uses RNG stream prefix i */
+  int32_t width, height;      /* full image size (pixel -> RNG stream mapping) */
+  int32_t spp;                /* samples per pixel, >= 1, <= 4096 */
+  int32_t max_depth;          /* path segments; 1 = directly visible emission only */
+  int32_t rr_depth;           /* Russian roulette at vertices reached by segment >= rr_depth; -1 = off */
+  int32_t nee;                /* next-event estimation + MIS (1) or BSDF sampling only (0) */
+  uint64_t seed;              /* PCG32 initstate; initseq = (cam<<40)|(pixel<<12)|sample */
+  int32_t dispatch;           /* PT_DISPATCH_SWITCH or PT_DISPATCH_MATCH (warp ballot grouping) */
+  int32_t crop_x0, crop_y0, crop_w, crop_h;  /* crop_w == 0: whole image */
+  int32_t lanes_per_pixel;    /* 1,2,4,..,32 threads sharing a pixel's samples; 0 = auto */
+  int32_t block_size;         /* threads per CTA (multiple of 32, <= 1024); 0 = auto */
+  int32_t tex_aggregate;      /* backward only: 1 = warp-aggregate texel gradient atomics
+                                 (__match_any_sync + shuffle tree), 0 = one float4 atomic per term */
+  /* instrumentation (device pointers; all NULL for the production path) */
+  float* dbg_sample_L;        /* [n_cams][rows][cols][spp][3] per-sample radiance */
+  uint32_t* dbg_sample_hash;  /* [n_cams][rows][cols][spp] FNV-1a of the path's discrete decisions */
+  unsigned long long* counters; /* [PT_N_COUNTERS], accumulated */
+} pt_render_desc;
+
+/* Differentiable parameters: borrowed device pointers. */
+typedef struct {
+  const float* albedo;        /* [n_albedo][3] constant albedos */
+  int32_t n_albedo;
+  const float* tex[PT_MAX_TEX]; /* each [tex_h][tex_w][4] RGBA (A unused); nearest lookup
+                                   x = min(int(u*w), w-1), y = min(int(v*h), h-1) (App. B) */
+  int32_t tex_w[PT_MAX_TEX], tex_h[PT_MAX_TEX];
+  int32_t n_tex;
+  const float* roughness;     /* [n_rough] GGX alpha per entry */
+  int32_t n_rough;
+} pt_params;
+
+/* Gradient outputs: borrowed device pointers, accumulated (+=); NULL = not wanted. */
+typedef struct {
+  float* albedo;              /* [n_albedo][3] */
+  float* tex[PT_MAX_TEX];     /* each [tex_h][tex_w][4] */
+  float* roughness;           /* [n_rough] */
+} pt_grads;
+
+/* Primal render (Fig. 7, megakernel #1): image = mean over spp of the path
+ * tracer's per-sample radiance.  image: device, [n_cams][rows][cols][3], overwritten.
+ * Errors: PT_ERR_ARG, PT_ERR_STATE (no BVH), PT_ERR_CUDA (launch failure). */
+int pt_render_forward(pt_scene* scene, const pt_render_desc* desc, const pt_params* params,
+                      float* image, void* stream);
+
+/* Adjoint render by Path Replay Backpropagation (Sec. 4.1, Fig. 7 #2+#3):
+ * each sample is traced once to obtain its radiance L, then replayed from the
+ * same PCG32 state while the remaining radiance L_rem = L - (contributions so
+ * far) is maintained; at every vertex the BSDF values' derivatives
+ * (d f/d theta)/f (Sec. 4.9) times the radiance they carry, weighted by
+ * grad_image/spp, are scatter-added into `grads` (warp-aggregated atomics).
+ * grad_image: device, same layout as the forward image, = dLoss/dImage.
+ * For decorrelated gradients pass a seed different from the forward's.
+ * Errors: as pt_render_forward. */
+int pt_render_backward(pt_scene* scene, const pt_render_desc* desc, const pt_params* params,
+                       const float* grad_image, const pt_grads* grads, void* stream);
+
+/* Reads (and clears) the scene's device status word after synchronising
+ * `stream`: *out = PT_OK or the first PT_ERR_* a kernel recorded. */
+int pt_last_device_status(pt_scene* scene, void* stream, int* out);
+
+const char* pt_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PT_H_ */

@@ -68,8 +68,8 @@ def lib():
             L.oracle_scene_new.restype = vp
             L.oracle_scene_new.argtypes = [C.POINTER(SceneIn)]
             L.oracle_scene_free.argtypes = [vp]
-            L.oracle_render.argtypes = [vp, C.POINTER(RenderIn), vp, vp, vp, ip]
-            L.oracle_grad_tape.argtypes = [vp, C.POINTER(RenderIn), vp, vp, vp, vp, ip]
+            L.oracle_render.argtypes = [vp, C.POINTER(RenderIn), vp, vp, vp, ip, vp]
+            L.oracle_grad_tape.argtypes = [vp, C.POINTER(RenderIn), vp, vp, vp, vp, ip, vp]
             L.oracle_grad_dual.argtypes = [vp, C.POINTER(RenderIn), vp, ip, vp, vp, ip]
             L.oracle_pcg32.argtypes = [C.c_uint64, C.c_uint64, ip, vp]
             L.oracle_trace.argtypes = [vp, ip, vp, vp, ip, vp, vp]
@@ -169,17 +169,22 @@ def _crop_shape(r: RenderIn):
     return (r.crop_h, r.crop_w) if r.crop_w > 0 else (r.height, r.width)
 
 
-def render(osc: OracleScene, r: RenderIn, per_sample=False, threads=0):
-    """Image [h][w][3] (FP64); with per_sample also [h][w][spp][3] radiance and hashes."""
+def render(osc: OracleScene, r: RenderIn, per_sample=False, threads=0, count_rays=False):
+    """Image [h][w][3] (FP64); with per_sample also [h][w][spp][3] radiance and hashes.
+    With count_rays the number of rays traced (closest-hit + shadow) is appended."""
     h, w = _crop_shape(r)
     img = np.zeros((h, w, 3))
     sl = np.zeros((h, w, r.spp, 3)) if per_sample else None
     sh = np.zeros((h, w, r.spp), np.uint32) if per_sample else None
-    lib().oracle_render(osc.handle, C.byref(r), _ptr(img), _ptr(sl), _ptr(sh), threads)
-    return (img, sl, sh) if per_sample else img
+    rays = np.zeros(1, np.uint64)
+    lib().oracle_render(osc.handle, C.byref(r), _ptr(img), _ptr(sl), _ptr(sh), threads, _ptr(rays))
+    out = (img, sl, sh) if per_sample else (img,)
+    if count_rays:
+        out = out + (int(rays[0]),)
+    return out if len(out) > 1 else out[0]
 
 
-def grad_tape(osc: OracleScene, r: RenderIn, grad_image: np.ndarray, threads=0):
+def grad_tape(osc: OracleScene, r: RenderIn, grad_image: np.ndarray, threads=0, count_rays=False):
     """Gradients (albedo [A,3], textures list [h,w,4], roughness [R]) by the stored tape."""
     s = osc.scene
     gi = np.ascontiguousarray(grad_image, dtype=np.float64)
@@ -187,8 +192,10 @@ def grad_tape(osc: OracleScene, r: RenderIn, grad_image: np.ndarray, threads=0):
     gt = [np.zeros(t.shape) for t in s.textures]
     gr = np.zeros(s.roughness.shape[0])
     tp = (C.c_void_p * max(1, len(gt)))(*[t.ctypes.data for t in gt])
-    lib().oracle_grad_tape(osc.handle, C.byref(r), _ptr(gi), _ptr(ga), C.cast(tp, C.c_void_p), _ptr(gr), threads)
-    return ga, gt, gr
+    rays = np.zeros(1, np.uint64)
+    lib().oracle_grad_tape(osc.handle, C.byref(r), _ptr(gi), _ptr(ga), C.cast(tp, C.c_void_p), _ptr(gr), threads,
+                           _ptr(rays))
+    return (ga, gt, gr, int(rays[0])) if count_rays else (ga, gt, gr)
 
 
 def grad_dual(osc: OracleScene, r: RenderIn, grad_image: np.ndarray, sel, threads=0):

@@ -320,6 +320,8 @@ bool intersect_tri(const Scene& s, int t, V3 o, V3 d, double& th, double& bu, do
   return true;
 }
 
+thread_local uint64_t g_rays = 0;  // rays traced by this thread (closest-hit + shadow)
+
 struct Hit {
   int prim = -1;
   double t = 0, u = 0, v = 0;
@@ -327,6 +329,7 @@ struct Hit {
 
 // Closest hit with t in (0, tmax); ties broken by the smaller triangle index.
 Hit closest_hit(const Scene& s, V3 o, V3 d, double tmax, bool brute) {
+  ++g_rays;
   Hit h;
   double best = tmax;
   auto test = [&](int t) {
@@ -1046,12 +1049,14 @@ void oracle_scene_free(void* sc) { delete (Scene*)sc; }
 // Mean over `spp` samples per pixel of the crop -> image [ch][cw][3].
 // Optional per-sample radiance [ch][cw][spp][3] and decision hashes [ch][cw][spp].
 int oracle_render(void* sc, const oracle_render_in* r, double* image, double* sample_L,
-                  uint32_t* sample_hash, int n_threads) {
+                  uint32_t* sample_hash, int n_threads, uint64_t* n_rays) {
   const Scene& s = *(Scene*)sc;
   Camera cam = make_camera(*r);
   int x0, y0, cw, ch;
   crop_of(*r, x0, y0, cw, ch);
+  std::atomic<uint64_t> rays(0);
   parallel_rows(y0, ch, n_threads, [&](int py) {
+    g_rays = 0;
     for (int px = x0; px < x0 + cw; ++px) {
       size_t pi = (size_t)(py - y0) * cw + (px - x0);
       V3 sum(0, 0, 0);
@@ -1067,7 +1072,9 @@ int oracle_render(void* sc, const oracle_render_in* r, double* image, double* sa
       }
       for (int c = 0; c < 3; ++c) image[pi * 3 + c] = sum[c] / r->spp;
     }
+    rays += g_rays;
   });
+  if (n_rays) *n_rays = rays.load();
   return 0;
 }
 
@@ -1075,7 +1082,7 @@ int oracle_render(void* sc, const oracle_render_in* r, double* image, double* sa
 // grad_image [ch][cw][3] is dLoss/dImage; each sample gets 1/spp of it.
 // Outputs are *overwritten*: g_albedo [A][3], g_tex[i] [h][w][4], g_rough [R] (any may be NULL).
 int oracle_grad_tape(void* sc, const oracle_render_in* r, const double* grad_image, double* g_albedo,
-                     double* const* g_tex, double* g_rough, int n_threads) {
+                     double* const* g_tex, double* g_rough, int n_threads, uint64_t* n_rays) {
   const Scene& s = *(Scene*)sc;
   Camera cam = make_camera(*r);
   int x0, y0, cw, ch;
@@ -1085,7 +1092,9 @@ int oracle_grad_tape(void* sc, const oracle_render_in* r, const double* grad_ima
   for (auto& t : s.tex) total.tex.emplace_back(t.rgba.size(), 0.0);
   total.rough.assign(s.roughness.size(), 0.0);
   std::mutex mu;
+  std::atomic<uint64_t> rays(0);
   parallel_rows(y0, ch, n_threads, [&](int py) {
+    g_rays = 0;
     // one row's contributions, merged under the lock (texture buffers are shared)
     GradOut row;
     row.albedo.assign(s.albedo.size(), 0.0);
@@ -1123,11 +1132,13 @@ int oracle_grad_tape(void* sc, const oracle_render_in* r, const double* grad_ima
         }
       }
     }
+    rays += g_rays;
     std::lock_guard<std::mutex> lk(mu);
     for (size_t i = 0; i < row.albedo.size(); ++i) total.albedo[i] += row.albedo[i];
     for (size_t i = 0; i < row.rough.size(); ++i) total.rough[i] += row.rough[i];
     for (const auto& a : tex_adds) total.tex[a.tex][a.idx] += a.v;
   });
+  if (n_rays) *n_rays = rays.load();
   if (g_albedo) std::memcpy(g_albedo, total.albedo.data(), total.albedo.size() * sizeof(double));
   if (g_rough) std::memcpy(g_rough, total.rough.data(), total.rough.size() * sizeof(double));
   if (g_tex)

@@ -1,0 +1,270 @@
+"""ctypes binding of the C ABI in ``include/pt.h`` (argument marshalling only).
+
+Functions keep the C names (``pt_scene_create``, ``pt_bvh_build``,
+``pt_render_forward``, ``pt_render_backward``, ...).  Device buffers are torch
+CUDA tensors; only their raw pointers cross the boundary.  Every step of the
+rendering runs in the CUDA library: if ``libptgb.so`` is missing this module
+raises instead of falling back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+from . import scenes as S
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libptgb.so")
+
+PT_OK = 0
+PT_ERR_ARG = -1
+PT_ERR_CUDA = -2
+PT_ERR_OOM = -3
+PT_ERR_TIMEOUT = -4
+PT_ERR_BVH = -5
+PT_ERR_STATE = -6
+PT_MAX_TEX = 8
+PT_MAX_CAMS = 64
+PT_BVH_BINARY = 0
+PT_BVH_WIDE = 1
+PT_DISPATCH_SWITCH = 0
+PT_DISPATCH_MATCH = 1
+PT_N_COUNTERS = 16
+COUNTER_NAMES = ["paths", "rays", "shadow_rays", "nodes", "tri_tests", "tex_lookups", "atomics", "grad_terms"]
+
+
+class PtError(RuntimeError):
+    def __init__(self, fn, code):
+        msg = _lib.pt_status_string(code).decode() if _lib is not None else str(code)
+        super().__init__(f"{fn} failed: {code} ({msg})")
+        self.code = code
+
+
+class pt_shape(C.Structure):
+    _fields_ = [("bsdf", C.c_int32), ("tex", C.c_int32), ("albedo_index", C.c_int32), ("rough_index", C.c_int32),
+                ("alpha", C.c_float), ("eta", C.c_float), ("diffuse_weight", C.c_float),
+                ("f0", C.c_float * 3), ("emission", C.c_float * 3)]
+
+
+class pt_scene_desc(C.Structure):
+    _fields_ = [("n_tris", C.c_int32), ("vertices", C.c_void_p), ("uvs", C.c_void_p), ("tri_shape", C.c_void_p),
+                ("n_shapes", C.c_int32), ("shapes", C.c_void_p), ("env_w", C.c_int32), ("env_h", C.c_int32),
+                ("env", C.c_void_p)]
+
+
+class pt_bvh_opts(C.Structure):
+    _fields_ = [("layout", C.c_int32), ("max_leaf_tris", C.c_int32), ("n_bins", C.c_int32)]
+
+
+class pt_scene_info(C.Structure):
+    _fields_ = [("n_tris", C.c_int64), ("n_nodes", C.c_int64), ("node_bytes", C.c_int64), ("tri_bytes", C.c_int64),
+                ("env_bytes", C.c_int64), ("layout", C.c_int32), ("depth", C.c_int32), ("sah_cost", C.c_double)]
+
+
+class pt_camera(C.Structure):
+    _fields_ = [("origin", C.c_float * 3), ("target", C.c_float * 3), ("up", C.c_float * 3), ("vfov_deg", C.c_float)]
+
+
+class pt_render_desc(C.Structure):
+    _fields_ = [("n_cams", C.c_int32), ("cams", C.c_void_p), ("width", C.c_int32), ("height", C.c_int32),
+                ("spp", C.c_int32), ("max_depth", C.c_int32), ("rr_depth", C.c_int32), ("nee", C.c_int32),
+                ("seed", C.c_uint64), ("dispatch", C.c_int32),
+                ("crop_x0", C.c_int32), ("crop_y0", C.c_int32), ("crop_w", C.c_int32), ("crop_h", C.c_int32),
+                ("lanes_per_pixel", C.c_int32), ("block_size", C.c_int32), ("tex_aggregate", C.c_int32),
+                ("dbg_sample_L", C.c_void_p), ("dbg_sample_hash", C.c_void_p), ("counters", C.c_void_p)]
+
+
+class pt_params(C.Structure):
+    _fields_ = [("albedo", C.c_void_p), ("n_albedo", C.c_int32), ("tex", C.c_void_p * PT_MAX_TEX),
+                ("tex_w", C.c_int32 * PT_MAX_TEX), ("tex_h", C.c_int32 * PT_MAX_TEX), ("n_tex", C.c_int32),
+                ("roughness", C.c_void_p), ("n_rough", C.c_int32)]
+
+
+class pt_grads(C.Structure):
+    _fields_ = [("albedo", C.c_void_p), ("tex", C.c_void_p * PT_MAX_TEX), ("roughness", C.c_void_p)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+# exported symbols with their argument/return types
+SIGNATURES = {
+    "pt_scene_create": ([C.POINTER(pt_scene_desc), C.POINTER(C.c_void_p)], C.c_int),
+    "pt_scene_destroy": ([C.c_void_p], None),
+    "pt_bvh_build": ([C.c_void_p, C.POINTER(pt_bvh_opts)], C.c_int),
+    "pt_scene_get_info": ([C.c_void_p, C.POINTER(pt_scene_info)], C.c_int),
+    "pt_render_forward": ([C.c_void_p, C.POINTER(pt_render_desc), C.POINTER(pt_params), C.c_void_p, C.c_void_p],
+                          C.c_int),
+    "pt_render_backward": ([C.c_void_p, C.POINTER(pt_render_desc), C.POINTER(pt_params), C.c_void_p,
+                            C.POINTER(pt_grads), C.c_void_p], C.c_int),
+    "pt_last_device_status": ([C.c_void_p, C.c_void_p, C.POINTER(C.c_int)], C.c_int),
+    "pt_status_string": ([C.c_int], C.c_char_p),
+}
+
+
+def load(path: str = LIB_PATH):
+    """Load libptgb.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(path):
+                raise RuntimeError(f"{path} is missing: build it with paper_2202_01284_gb300.build.build() "
+                                   "(there is no CPU fallback)")
+            lib = C.CDLL(path)
+            for name, (args, res) in SIGNATURES.items():
+                fn = getattr(lib, name, None)
+                if fn is None:
+                    continue
+                fn.argtypes = args
+                fn.restype = res
+            _lib = lib
+    return _lib
+
+
+def check(fn_name, code):
+    if code != PT_OK:
+        raise PtError(fn_name, code)
+
+
+def _ptr(t):
+    """Raw device (or host) pointer of a torch tensor / numpy array, or None."""
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data
+    return t.data_ptr()
+
+
+# ------------------------------------------------------------------ marshalling helpers
+def scene_desc(scene: "S.Scene"):
+    """Build a pt_scene_desc from a generator Scene; returns (desc, keepalive)."""
+    keep = []
+
+    def arr(a, dt):
+        a = np.ascontiguousarray(a, dtype=dt)
+        keep.append(a)
+        return a
+    n = scene.n_shapes
+    shapes = (pt_shape * n)()
+    for i in range(n):
+        sh = shapes[i]
+        sh.bsdf = int(scene.bsdf[i])
+        sh.tex = int(scene.tex[i])
+        sh.albedo_index = int(scene.albedo_index[i])
+        sh.rough_index = int(scene.rough_index[i])
+        sh.alpha = float(scene.alpha[i])
+        sh.eta = float(scene.eta[i])
+        sh.diffuse_weight = float(scene.diffuse_weight[i])
+        sh.f0[:] = [float(x) for x in scene.f0[i]]
+        sh.emission[:] = [float(x) for x in scene.emission[i]]
+    keep.append(shapes)
+    d = pt_scene_desc()
+    d.n_tris = scene.n_tris
+    d.vertices = _ptr(arr(scene.vertices, np.float32))
+    d.uvs = _ptr(arr(scene.uvs, np.float32))
+    d.tri_shape = _ptr(arr(scene.tri_shape, np.int32))
+    d.n_shapes = n
+    d.shapes = C.cast(shapes, C.c_void_p).value
+    if scene.env is not None:
+        d.env_w, d.env_h = int(scene.env.shape[1]), int(scene.env.shape[0])
+        d.env = _ptr(arr(scene.env, np.float32))
+    return d, keep
+
+
+def camera_struct(cam: "S.Camera") -> pt_camera:
+    c = pt_camera()
+    c.origin[:] = cam.origin
+    c.target[:] = cam.target
+    c.up[:] = cam.up
+    c.vfov_deg = cam.vfov_deg
+    return c
+
+
+def render_desc(cams, width, height, spp, max_depth, seed, rr_depth=-1, nee=True, dispatch=PT_DISPATCH_SWITCH,
+                crop=None, lanes_per_pixel=0, block_size=0, tex_aggregate=0, dbg_L=None, dbg_hash=None,
+                counters=None):
+    cams = list(cams)
+    arr = (pt_camera * len(cams))(*[camera_struct(c) for c in cams])
+    r = pt_render_desc()
+    r.n_cams = len(cams)
+    r.cams = C.cast(arr, C.c_void_p).value
+    r.width, r.height, r.spp, r.max_depth = width, height, spp, max_depth
+    r.rr_depth, r.nee, r.seed, r.dispatch = rr_depth, int(bool(nee)), seed, dispatch
+    if crop is not None:
+        r.crop_x0, r.crop_y0, r.crop_w, r.crop_h = crop
+    r.lanes_per_pixel, r.block_size, r.tex_aggregate = lanes_per_pixel, block_size, tex_aggregate
+    r.dbg_sample_L = _ptr(dbg_L)
+    r.dbg_sample_hash = _ptr(dbg_hash)
+    r.counters = _ptr(counters)
+    r._keep = arr
+    return r
+
+
+def params_struct(albedo=None, textures=(), roughness=None) -> pt_params:
+    p = pt_params()
+    if albedo is not None and albedo.numel() > 0:
+        p.albedo = _ptr(albedo)
+        p.n_albedo = int(albedo.shape[0])
+    for i, t in enumerate(textures):
+        p.tex[i] = _ptr(t)
+        p.tex_w[i] = int(t.shape[1])
+        p.tex_h[i] = int(t.shape[0])
+    p.n_tex = len(textures)
+    if roughness is not None and roughness.numel() > 0:
+        p.roughness = _ptr(roughness)
+        p.n_rough = int(roughness.shape[0])
+    return p
+
+
+def grads_struct(albedo=None, textures=(), roughness=None) -> pt_grads:
+    g = pt_grads()
+    g.albedo = _ptr(albedo) if albedo is not None and albedo.numel() > 0 else None
+    for i, t in enumerate(textures):
+        g.tex[i] = _ptr(t)
+    g.roughness = _ptr(roughness) if roughness is not None and roughness.numel() > 0 else None
+    return g
+
+
+# ------------------------------------------------------------------ C-named entry points
+def pt_scene_create(scene: "S.Scene") -> int:
+    L = load()
+    d, keep = scene_desc(scene)
+    h = C.c_void_p()
+    check("pt_scene_create", L.pt_scene_create(C.byref(d), C.byref(h)))
+    return h.value
+
+
+def pt_scene_destroy(handle: int) -> None:
+    if handle:
+        load().pt_scene_destroy(handle)
+
+
+def pt_bvh_build(handle: int, layout=PT_BVH_BINARY, max_leaf_tris=0, n_bins=0) -> None:
+    o = pt_bvh_opts(layout, max_leaf_tris, n_bins)
+    check("pt_bvh_build", load().pt_bvh_build(handle, C.byref(o)))
+
+
+def pt_scene_get_info(handle: int) -> dict:
+    i = pt_scene_info()
+    check("pt_scene_get_info", load().pt_scene_get_info(handle, C.byref(i)))
+    return {k: getattr(i, k) for k, _ in pt_scene_info._fields_}
+
+
+def pt_render_forward(handle: int, desc: pt_render_desc, params: pt_params, image, stream: int = 0) -> None:
+    check("pt_render_forward", load().pt_render_forward(handle, C.byref(desc), C.byref(params), _ptr(image),
+                                                        stream or None))
+
+
+def pt_render_backward(handle: int, desc: pt_render_desc, params: pt_params, grad_image, grads: pt_grads,
+                       stream: int = 0) -> None:
+    check("pt_render_backward", load().pt_render_backward(handle, C.byref(desc), C.byref(params),
+                                                          _ptr(grad_image), C.byref(grads), stream or None))
+
+
+def pt_last_device_status(handle: int, stream: int = 0) -> int:
+    v = C.c_int(0)
+    check("pt_last_device_status", load().pt_last_device_status(handle, stream or None, C.byref(v)))
+    return v.value

@@ -1,0 +1,239 @@
+// Binned-SAH BVH builder and GPU layouts (host C++).
+//
+// The paper delegates ray tracing to Embree/OptiX (Sec. 3.1); on GB300 the
+// RT cores are not reachable from CUDA, so the acceleration structure is our
+// own: a binned surface-area-heuristic build (cost = 1 per traversal step + 1
+// per triangle test), laid out either as a 2-wide tree with float boxes or as
+// an 8-wide tree with 8-bit quantised child boxes (80-byte nodes, five
+// 16-byte loads per node).
+#include "bvh_build.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <limits>
+
+namespace ptgb {
+namespace {
+
+struct Box {
+  float lo[3] = {INFINITY, INFINITY, INFINITY};
+  float hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+  void grow(const float* l, const float* h) {
+    for (int k = 0; k < 3; ++k) {
+      lo[k] = std::min(lo[k], l[k]);
+      hi[k] = std::max(hi[k], h[k]);
+    }
+  }
+  void grow_pt(const float* p) { grow(p, p); }
+  double area() const {
+    if (!(hi[0] >= lo[0])) return 0.0;
+    double dx = hi[0] - lo[0], dy = hi[1] - lo[1], dz = hi[2] - lo[2];
+    return 2.0 * (dx * dy + dy * dz + dz * dx);
+  }
+};
+
+struct Job {
+  int node, first, count, depth;
+};
+
+}  // namespace
+
+BuildTree build_sah(const float* V, int n, int max_leaf, int n_bins) {
+  BuildTree t;
+  std::vector<float> tlo(3 * (size_t)n), thi(3 * (size_t)n), cen(3 * (size_t)n);
+  for (int i = 0; i < n; ++i) {
+    const float* v = V + (size_t)i * 9;
+    for (int k = 0; k < 3; ++k) {
+      float a = v[k], b = v[3 + k], c = v[6 + k];
+      tlo[3 * i + k] = std::min(a, std::min(b, c));
+      thi[3 * i + k] = std::max(a, std::max(b, c));
+      cen[3 * i + k] = 0.5f * (tlo[3 * i + k] + thi[3 * i + k]);
+    }
+  }
+  t.order.resize(n);
+  for (int i = 0; i < n; ++i) t.order[i] = i;
+  auto bounds_of = [&](int first, int count, Box& b) {
+    for (int i = first; i < first + count; ++i) {
+      int tri = t.order[i];
+      b.grow(&tlo[3 * tri], &thi[3 * tri]);
+    }
+  };
+  t.nodes.reserve(2 * (size_t)n);
+  t.nodes.emplace_back();
+  {
+    Box b;
+    bounds_of(0, n, b);
+    std::memcpy(t.nodes[0].lo, b.lo, sizeof b.lo);
+    std::memcpy(t.nodes[0].hi, b.hi, sizeof b.hi);
+  }
+  double root_area = std::max(Box{}.area(), 0.0);
+  {
+    Box b;
+    std::memcpy(b.lo, t.nodes[0].lo, sizeof b.lo);
+    std::memcpy(b.hi, t.nodes[0].hi, sizeof b.hi);
+    root_area = std::max(b.area(), 1e-30);
+  }
+  std::vector<Job> stack;
+  stack.push_back({0, 0, n, 1});
+  std::vector<int> bin_count(n_bins);
+  std::vector<Box> bin_box(n_bins);
+  std::vector<double> right_area(n_bins);
+  std::vector<int> right_count(n_bins);
+  double sah = 0.0;
+  while (!stack.empty()) {
+    Job j = stack.back();
+    stack.pop_back();
+    t.depth = std::max(t.depth, j.depth);
+    BuildNode& nd = t.nodes[j.node];
+    Box nb;
+    std::memcpy(nb.lo, nd.lo, sizeof nb.lo);
+    std::memcpy(nb.hi, nd.hi, sizeof nb.hi);
+    double a_node = std::max(nb.area(), 1e-30);
+    auto make_leaf = [&]() {
+      t.nodes[j.node].first = j.first;
+      t.nodes[j.node].count = j.count;
+      sah += a_node / root_area * j.count;
+    };
+    if (j.count <= 1) {
+      make_leaf();
+      continue;
+    }
+    Box cb;
+    for (int i = j.first; i < j.first + j.count; ++i) cb.grow_pt(&cen[3 * t.order[i]]);
+    double best_cost = INFINITY;
+    int best_axis = -1, best_split = -1;
+    bool force_median = j.depth >= 48;  // keeps the tree shallow enough for a 64-entry stack
+    if (!force_median) {
+      for (int axis = 0; axis < 3; ++axis) {
+        float ext = cb.hi[axis] - cb.lo[axis];
+        if (!(ext > 0.0f)) continue;
+        float scale = (float)n_bins / ext;
+        std::fill(bin_count.begin(), bin_count.end(), 0);
+        std::fill(bin_box.begin(), bin_box.end(), Box{});
+        for (int i = j.first; i < j.first + j.count; ++i) {
+          int tri = t.order[i];
+          int b = std::min((int)((cen[3 * tri + axis] - cb.lo[axis]) * scale), n_bins - 1);
+          bin_count[b]++;
+          bin_box[b].grow(&tlo[3 * tri], &thi[3 * tri]);
+        }
+        Box acc;
+        int cnt = 0;
+        for (int b = n_bins - 1; b > 0; --b) {
+          acc.grow(bin_box[b].lo, bin_box[b].hi);
+          cnt += bin_count[b];
+          right_area[b] = acc.area();
+          right_count[b] = cnt;
+        }
+        Box lacc;
+        int lcnt = 0;
+        for (int b = 0; b < n_bins - 1; ++b) {
+          lacc.grow(bin_box[b].lo, bin_box[b].hi);
+          lcnt += bin_count[b];
+          if (lcnt == 0 || right_count[b + 1] == 0) continue;
+          double cost = 1.0 + (lacc.area() * lcnt + right_area[b + 1] * right_count[b + 1]) / a_node;
+          if (cost < best_cost) {
+            best_cost = cost;
+            best_axis = axis;
+            best_split = b;
+          }
+        }
+      }
+      if (j.count <= max_leaf && (best_axis < 0 || (double)j.count <= best_cost)) {
+        make_leaf();
+        continue;
+      }
+    } else if (j.count <= max_leaf) {
+      make_leaf();
+      continue;
+    }
+    int mid;
+    if (best_axis >= 0) {
+      float ext = cb.hi[best_axis] - cb.lo[best_axis];
+      float scale = (float)n_bins / ext;
+      auto it = std::partition(t.order.begin() + j.first, t.order.begin() + j.first + j.count, [&](int tri) {
+        int b = std::min((int)((cen[3 * tri + best_axis] - cb.lo[best_axis]) * scale), n_bins - 1);
+        return b <= best_split;
+      });
+      mid = (int)(it - t.order.begin());
+    } else {
+      // all centroids coincide (or forced): split by object median on the widest axis
+      int axis = 0;
+      float e0 = cb.hi[0] - cb.lo[0], e1 = cb.hi[1] - cb.lo[1], e2 = cb.hi[2] - cb.lo[2];
+      axis = (e0 >= e1 && e0 >= e2) ? 0 : (e1 >= e2 ? 1 : 2);
+      mid = j.first + j.count / 2;
+      std::nth_element(t.order.begin() + j.first, t.order.begin() + mid, t.order.begin() + j.first + j.count,
+                       [&](int a, int b) { return cen[3 * a + axis] < cen[3 * b + axis] || (cen[3 * a + axis] == cen[3 * b + axis] && a < b); });
+    }
+    if (mid <= j.first || mid >= j.first + j.count) mid = j.first + j.count / 2;
+    sah += a_node / root_area * 1.0;
+    int l = (int)t.nodes.size();
+    t.nodes.emplace_back();
+    t.nodes.emplace_back();
+    int r = l + 1;
+    Box lb, rb;
+    bounds_of(j.first, mid - j.first, lb);
+    bounds_of(mid, j.first + j.count - mid, rb);
+    std::memcpy(t.nodes[l].lo, lb.lo, sizeof lb.lo);
+    std::memcpy(t.nodes[l].hi, lb.hi, sizeof lb.hi);
+    std::memcpy(t.nodes[r].lo, rb.lo, sizeof rb.lo);
+    std::memcpy(t.nodes[r].hi, rb.hi, sizeof rb.hi);
+    t.nodes[j.node].left = l;
+    t.nodes[j.node].right = r;
+    stack.push_back({r, mid, j.first + j.count - mid, j.depth + 1});
+    stack.push_back({l, j.first, mid - j.first, j.depth + 1});
+  }
+  t.sah_cost = sah;
+  return t;
+}
+
+namespace {
+// Conservative outward padding of a box coordinate for FP32 slab tests.
+float pad_lo(float v, float abs_pad) { return v - (std::fabs(v) * 3.0e-6f + abs_pad); }
+float pad_hi(float v, float abs_pad) { return v + (std::fabs(v) * 3.0e-6f + abs_pad); }
+float scene_abs_pad(const BuildTree& t) {
+  const BuildNode& r = t.nodes[0];
+  float e = std::max(r.hi[0] - r.lo[0], std::max(r.hi[1] - r.lo[1], r.hi[2] - r.lo[2]));
+  return std::max(e, 1e-20f) * 1.0e-6f;
+}
+}  // namespace
+
+void layout_binary(const BuildTree& t, std::vector<float>& words) {
+  const float ap = scene_abs_pad(t);
+  std::vector<int> gidx(t.nodes.size(), -1);
+  std::vector<int> inner;
+  std::vector<int> st{0};
+  while (!st.empty()) {
+    int i = st.back();
+    st.pop_back();
+    if (t.nodes[i].left < 0) continue;
+    gidx[i] = (int)inner.size();
+    inner.push_back(i);
+    st.push_back(t.nodes[i].right);
+    st.push_back(t.nodes[i].left);
+  }
+  auto leaf_ref = [&](const BuildNode& n) { return ~((n.first << 3) | (n.count - 1)); };
+  auto child_ref = [&](int c) { return t.nodes[c].left < 0 ? leaf_ref(t.nodes[c]) : gidx[c]; };
+  auto put = [&](float* w, int c0, int c1, int r0, int r1) {
+    const BuildNode& a = t.nodes[c0];
+    const BuildNode& b = t.nodes[c1];
+    w[0] = pad_lo(a.lo[0], ap); w[1] = pad_hi(a.hi[0], ap); w[2] = pad_lo(a.lo[1], ap); w[3] = pad_hi(a.hi[1], ap);
+    w[4] = pad_lo(b.lo[0], ap); w[5] = pad_hi(b.hi[0], ap); w[6] = pad_lo(b.lo[1], ap); w[7] = pad_hi(b.hi[1], ap);
+    w[8] = pad_lo(a.lo[2], ap); w[9] = pad_hi(a.hi[2], ap); w[10] = pad_lo(b.lo[2], ap); w[11] = pad_hi(b.hi[2], ap);
+    int32_t refs[4] = {r0, r1, 0, 0};
+    std::memcpy(&w[12], refs, sizeof refs);
+  };
+  if (inner.empty()) {  // the whole scene is one leaf: root with the leaf in both slots
+    words.assign(16, 0.0f);
+    int r = leaf_ref(t.nodes[0]);
+    put(words.data(), 0, 0, r, r);
+    return;
+  }
+  words.assign(inner.size() * 16, 0.0f);
+  for (size_t g = 0; g < inner.size(); ++g) {
+    const BuildNode& n = t.nodes[inner[g]];
+    put(&words[g * 16], n.left, n.right, child_ref(n.left), child_ref(n.right));
+  }
+}
+
+}  // namespace ptgb

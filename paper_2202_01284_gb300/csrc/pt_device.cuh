@@ -1,0 +1,495 @@
+// Device code of the path-tracing megakernel and its PRB adjoint (sm_103a).
+//
+// One thread traces whole paths (megakernel, Fig. 7 #1): camera ray, closest-hit
+// traversal, surface interaction, per-material BSDF work reached through a
+// per-lane polymorphic dispatch, next-event estimation with MIS, BSDF
+// sampling, Russian roulette.  The adjoint (Fig. 7 #2 + #3 fused) runs the
+// same loop body twice per sample: pass 0 recovers the sample's radiance L,
+// pass 1 replays the identical path from the same PCG32 state, subtracting
+// each contribution from L (arithmetic invertibility, Sec. 4.1) and
+// scatter-adding (dL * radiance * (df/dtheta)/f) into parameter gradients
+// (Sec. 4.9: detached sampling, attached BSDF values).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "pt_internal.h"
+
+namespace ptgb {
+
+#define PT_PI 3.14159265358979323846f
+#define PT_INV_PI 0.31830988618379067154f
+#define PT_STACK 64
+
+// ---------------------------------------------------------------- float3 helpers
+__device__ __forceinline__ float3 f3(float a, float b, float c) { return make_float3(a, b, c); }
+__device__ __forceinline__ float3 operator+(float3 a, float3 b) { return f3(a.x + b.x, a.y + b.y, a.z + b.z); }
+__device__ __forceinline__ float3 operator-(float3 a, float3 b) { return f3(a.x - b.x, a.y - b.y, a.z - b.z); }
+__device__ __forceinline__ float3 operator-(float3 a) { return f3(-a.x, -a.y, -a.z); }
+__device__ __forceinline__ float3 operator*(float3 a, float s) { return f3(a.x * s, a.y * s, a.z * s); }
+__device__ __forceinline__ float3 operator*(float3 a, float3 b) { return f3(a.x * b.x, a.y * b.y, a.z * b.z); }
+__device__ __forceinline__ float dot3(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ float3 cross3(float3 a, float3 b) {
+  return f3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+__device__ __forceinline__ float3 normalize3(float3 a) { return a * rsqrtf(dot3(a, a)); }
+__device__ __forceinline__ float max3f(float3 a) { return fmaxf(a.x, fmaxf(a.y, a.z)); }
+__device__ __forceinline__ float3 xyz(float4 a) { return f3(a.x, a.y, a.z); }
+
+// ---------------------------------------------------------------- PCG32 (O'Neill 2014)
+struct Pcg32 {
+  unsigned long long state, inc;
+  __device__ __forceinline__ void seed(unsigned long long initstate, unsigned long long initseq) {
+    state = 0ull;
+    inc = (initseq << 1) | 1ull;
+    next();
+    state += initstate;
+    next();
+  }
+  __device__ __forceinline__ uint32_t next() {
+    unsigned long long old = state;
+    state = old * 6364136223846793005ull + inc;
+    uint32_t xs = (uint32_t)(((old >> 18) ^ old) >> 27);
+    uint32_t rot = (uint32_t)(old >> 59);
+    return __funnelshift_r(xs, xs, rot);  // rotate right by rot
+  }
+  // top 24 bits scaled by 2^-24: exactly representable
+  __device__ __forceinline__ float uniform() { return (float)(next() >> 8) * (1.0f / 16777216.0f); }
+};
+
+// ---------------------------------------------------------------- FNV-1a decision fingerprint
+struct Fnv {
+  uint32_t h;
+  __device__ __forceinline__ void add(uint32_t w) { h = (h ^ w) * 16777619u; }
+};
+
+// ---------------------------------------------------------------- instrumentation
+template <bool INSTR>
+struct Counters {
+  __device__ __forceinline__ void add(int, unsigned) {}
+};
+template <>
+struct Counters<true> {
+  unsigned c[8];
+  __device__ __forceinline__ void add(int i, unsigned v) { c[i] += v; }
+};
+
+__device__ __forceinline__ void set_status(const DevScene& s, int code) {
+  if (s.status) atomicCAS(s.status, 0, code);
+}
+
+// ---------------------------------------------------------------- traversal (binary BVH)
+struct Ray {
+  float3 o, d;
+};
+struct Hit {
+  int pos;      // leaf-order triangle position, -1 = miss
+  float t, u, v;
+};
+
+__device__ __forceinline__ float3 safe_inv(float3 d) {
+  const float eps = 1e-20f;
+  return f3(1.0f / (fabsf(d.x) > eps ? d.x : copysignf(eps, d.x)),
+            1.0f / (fabsf(d.y) > eps ? d.y : copysignf(eps, d.y)),
+            1.0f / (fabsf(d.z) > eps ? d.z : copysignf(eps, d.z)));
+}
+
+// Moller-Trumbore in FP32 (edges inclusive, det == 0 misses).  Updates the
+// closest hit; ties in t go to the smaller original triangle id.
+__device__ __forceinline__ bool tri_test(const float4* __restrict__ tv, int pos, const Ray& r, float& best_t,
+                                         int& best_pos, uint32_t& best_orig, float& bu, float& bv) {
+  float4 a = __ldg(&tv[3 * pos]);
+  float4 b = __ldg(&tv[3 * pos + 1]);
+  float4 c = __ldg(&tv[3 * pos + 2]);
+  float3 v0 = xyz(a), e1 = xyz(b), e2 = xyz(c);
+  float3 p = cross3(r.d, e2);
+  float det = dot3(e1, p);
+  if (det == 0.0f) return false;
+  float inv = 1.0f / det;
+  float3 s = r.o - v0;
+  float u = dot3(s, p) * inv;
+  if (u < 0.0f || u > 1.0f) return false;
+  float3 q = cross3(s, e1);
+  float v = dot3(r.d, q) * inv;
+  if (v < 0.0f || u + v > 1.0f) return false;
+  float t = dot3(e2, q) * inv;
+  if (!(t > 0.0f)) return false;
+  uint32_t orig = __float_as_uint(a.w);
+  if (t < best_t || (best_pos >= 0 && t == best_t && orig < best_orig)) {
+    best_t = t;
+    best_pos = pos;
+    best_orig = orig;
+    bu = u;
+    bv = v;
+    return true;
+  }
+  return false;
+}
+
+// Closest hit (ANY = false) or any hit before tmax (ANY = true) on the 2-wide BVH.
+template <bool ANY, bool INSTR>
+__device__ Hit trace_binary(const DevScene& S, const Ray& r, float tmax, Counters<INSTR>& cnt) {
+  Hit h;
+  h.pos = -1;
+  h.t = tmax;
+  h.u = h.v = 0.0f;
+  uint32_t best_orig = 0xffffffffu;
+  float3 inv = safe_inv(r.d);
+  float3 oi = r.o * inv;
+  int stack[PT_STACK];
+  int sp = 0;
+  int cur = 0;
+  const float4* __restrict__ N = S.nodes;
+  unsigned n_nodes = 0, n_tris = 0;
+  for (;;) {
+    if (cur >= 0) {
+      ++n_nodes;
+      float4 w0 = __ldg(&N[4 * cur]);
+      float4 w1 = __ldg(&N[4 * cur + 1]);
+      float4 w2 = __ldg(&N[4 * cur + 2]);
+      float4 w3 = __ldg(&N[4 * cur + 3]);
+      // child 0
+      float a0 = w0.x * inv.x - oi.x, a1 = w0.y * inv.x - oi.x;
+      float b0 = w0.z * inv.y - oi.y, b1 = w0.w * inv.y - oi.y;
+      float c0 = w2.x * inv.z - oi.z, c1 = w2.y * inv.z - oi.z;
+      float tn0 = fmaxf(fmaxf(fminf(a0, a1), fminf(b0, b1)), fmaxf(fminf(c0, c1), 0.0f));
+      float tf0 = fminf(fminf(fmaxf(a0, a1), fmaxf(b0, b1)), fminf(fmaxf(c0, c1), h.t));
+      // child 1
+      float d0 = w1.x * inv.x - oi.x, d1 = w1.y * inv.x - oi.x;
+      float e0 = w1.z * inv.y - oi.y, e1 = w1.w * inv.y - oi.y;
+      float g0 = w2.z * inv.z - oi.z, g1 = w2.w * inv.z - oi.z;
+      float tn1 = fmaxf(fmaxf(fminf(d0, d1), fminf(e0, e1)), fmaxf(fminf(g0, g1), 0.0f));
+      float tf1 = fminf(fminf(fmaxf(d0, d1), fmaxf(e0, e1)), fminf(fmaxf(g0, g1), h.t));
+      bool hit0 = tn0 <= tf0, hit1 = tn1 <= tf1;
+      int ch0 = __float_as_int(w3.x), ch1 = __float_as_int(w3.y);
+      if (hit0 && hit1) {
+        int nearc = ch0, farc = ch1;
+        if (tn1 < tn0) {
+          nearc = ch1;
+          farc = ch0;
+        }
+        if (sp >= PT_STACK) {
+          set_status(S, PT_ERR_BVH);
+          break;
+        }
+        stack[sp++] = farc;
+        cur = nearc;
+      } else if (hit0) {
+        cur = ch0;
+      } else if (hit1) {
+        cur = ch1;
+      } else {
+        if (sp == 0) break;
+        cur = stack[--sp];
+      }
+    } else {
+      int leaf = ~cur;
+      int first = leaf >> 3, count = (leaf & 7) + 1;
+      n_tris += count;
+      bool done = false;
+      for (int i = 0; i < count; ++i) {
+        if (tri_test(S.tri_v, first + i, r, h.t, h.pos, best_orig, h.u, h.v) && ANY) {
+          done = true;
+          break;
+        }
+      }
+      if (done || sp == 0) break;
+      cur = stack[--sp];
+    }
+  }
+  cnt.add(3, n_nodes);
+  cnt.add(4, n_tris);
+  return h;
+}
+
+// ---------------------------------------------------------------- shading frame
+// Orthonormal basis around n (Duff et al. 2017), branch on n.z >= 0 so +0/-0 agree.
+struct Frame {
+  float3 s, t, n;
+  __device__ __forceinline__ float3 to_local(float3 w) const { return f3(dot3(w, s), dot3(w, t), dot3(w, n)); }
+  __device__ __forceinline__ float3 to_world(float3 v) const { return s * v.x + t * v.y + n * v.z; }
+};
+__device__ __forceinline__ Frame make_frame(float3 n) {
+  float sign = n.z >= 0.0f ? 1.0f : -1.0f;
+  float a = -1.0f / (sign + n.z);
+  float b = n.x * n.y * a;
+  Frame f;
+  f.n = n;
+  f.s = f3(1.0f + sign * n.x * n.x * a, sign * b, -sign * n.x);
+  f.t = f3(b, sign + n.y * n.y * a, -n.y);
+  return f;
+}
+
+// ---------------------------------------------------------------- materials
+struct Material {
+  int type;
+  float3 albedo;
+  float alpha, eta, wd;
+  float3 f0;
+  int alb_kind;     // 0 none, 1 constant row, 2 texel
+  int alb_ref;      // row, or linear texel index
+  int tex;          // texture slot (alb_kind == 2)
+  int rough;        // roughness entry or -1
+};
+
+// BSDF value, pdf and (for the adjoint) partial derivatives of f per channel.
+struct BsdfEval {
+  float3 f;
+  float pdf;
+  float3 df_alb;    // d f_c / d albedo_c
+  float3 df_alpha;  // d f_c / d alpha
+};
+
+__device__ __forceinline__ float ggx_D(float a, float c) {
+  float a2 = a * a;
+  float den = c * c * (a2 - 1.0f) + 1.0f;
+  return a2 / (PT_PI * den * den);
+}
+__device__ __forceinline__ float ggx_G1(float a, float c, float* dlog) {
+  float T = (1.0f - c * c) / (c * c);
+  float s = sqrtf(1.0f + a * a * T);
+  if (dlog) *dlog = -(a * T / s) / (1.0f + s);
+  return 2.0f / (1.0f + s);
+}
+__device__ __forceinline__ float schlick(float f0, float cd) {
+  float m = 1.0f - cd;
+  float m2 = m * m;
+  return f0 + (1.0f - f0) * (m2 * m2 * m);
+}
+
+// GGX conductor value (+ d f / d alpha when GRAD); wi, wo above the surface.
+template <bool GRAD>
+__device__ __forceinline__ float3 ggx_eval(float a, float3 f0, float3 wi, float3 wo, float* pdf, float3* dfa) {
+  float3 h = normalize3(wi + wo);
+  float D = ggx_D(a, h.z);
+  float dl_i, dl_o;
+  float G = ggx_G1(a, wi.z, GRAD ? &dl_i : nullptr) * ggx_G1(a, wo.z, GRAD ? &dl_o : nullptr);
+  float cd = dot3(wi, h);
+  float k = D * G / (4.0f * wi.z * wo.z);
+  float3 f = f3(schlick(f0.x, cd) * k, schlick(f0.y, cd) * k, schlick(f0.z, cd) * k);
+  *pdf = D * h.z / (4.0f * fabsf(dot3(wo, h)));
+  if (GRAD) {
+    float c2 = h.z * h.z;
+    float dlog = 2.0f / a - 4.0f * a * c2 / (c2 * (a * a - 1.0f) + 1.0f) + dl_i + dl_o;
+    *dfa = f * dlog;
+  }
+  return f;
+}
+
+// Evaluate a non-delta BSDF of compile-time type T (local space, n = +z).
+template <int T, bool GRAD>
+__device__ __forceinline__ BsdfEval bsdf_eval(const Material& m, float3 wi, float3 wo) {
+  BsdfEval e;
+  e.f = f3(0.f, 0.f, 0.f);
+  e.pdf = 0.0f;
+  e.df_alb = f3(0.f, 0.f, 0.f);
+  e.df_alpha = f3(0.f, 0.f, 0.f);
+  if (!(wi.z > 0.0f) || !(wo.z > 0.0f)) return e;
+  if (T == PT_BSDF_DIFFUSE) {
+    e.f = m.albedo * PT_INV_PI;
+    e.pdf = wo.z * PT_INV_PI;
+    if (GRAD) e.df_alb = f3(PT_INV_PI, PT_INV_PI, PT_INV_PI);
+  } else if (T == PT_BSDF_CONDUCTOR) {
+    e.f = ggx_eval<GRAD>(m.alpha, m.f0, wi, wo, &e.pdf, &e.df_alpha);
+  } else if (T == PT_BSDF_BLEND) {
+    float pg;
+    float3 dga;
+    float3 g = ggx_eval<GRAD>(m.alpha, m.f0, wi, wo, &pg, &dga);
+    float w = m.wd;
+    e.f = m.albedo * (w * PT_INV_PI) + g * (1.0f - w);
+    e.pdf = w * wo.z * PT_INV_PI + (1.0f - w) * pg;
+    if (GRAD) {
+      float k = w * PT_INV_PI;
+      e.df_alb = f3(k, k, k);
+      e.df_alpha = dga * (1.0f - w);
+    }
+  }
+  return e;
+}
+
+// Cosine-weighted hemisphere, mapping of the paper's ambient-occlusion example
+// (Sec. 3.1): phi = 2 pi u4, sin^2(theta) = u5.
+__device__ __forceinline__ float3 cosine_sample(float u4, float u5) {
+  float s, c;
+  sincosf(2.0f * PT_PI * u4, &s, &c);
+  float r = sqrtf(u5);
+  return f3(c * r, s * r, sqrtf(1.0f - u5));
+}
+// Walter et al. 2007: phi = 2 pi u4, tan^2(theta_h) = a^2 u5 / (1 - u5).
+__device__ __forceinline__ bool ggx_sample(float a, float3 wi, float u4, float u5, float3& wo) {
+  float s, c;
+  sincosf(2.0f * PT_PI * u4, &s, &c);
+  float tan2 = a * a * u5 / (1.0f - u5);
+  float ct = rsqrtf(1.0f + tan2);
+  float st = sqrtf(fmaxf(0.0f, 1.0f - ct * ct));
+  float3 h = f3(st * c, st * s, ct);
+  wo = h * (2.0f * dot3(wi, h)) - wi;
+  return wo.z > 0.0f;
+}
+
+// Exact unpolarised Fresnel of a dielectric interface; eta = n_t / n_i.
+__device__ __forceinline__ float fresnel_dielectric(float cos_i, float eta, float& cos_t) {
+  float sin2_t = (1.0f - cos_i * cos_i) / (eta * eta);
+  if (sin2_t >= 1.0f) {
+    cos_t = 0.0f;
+    return 1.0f;
+  }
+  cos_t = sqrtf(1.0f - sin2_t);
+  float rs = (cos_i - eta * cos_t) / (cos_i + eta * cos_t);
+  float rp = (eta * cos_i - cos_t) / (eta * cos_i + cos_t);
+  return 0.5f * (rs * rs + rp * rp);
+}
+
+struct BsdfSample {
+  float3 wo;       // local
+  float3 weight;   // f cos / pdf (delta: the branch weight)
+  float pdf;       // solid-angle pdf (0 for delta)
+  BsdfEval ev;     // value at wo (non-delta; for the adjoint)
+  int lobe;        // 0 diffuse, 1 ggx, 2 reflect, 3 refract
+  bool ok, delta;
+};
+
+template <int T, bool GRAD>
+__device__ __forceinline__ BsdfSample bsdf_sample(const Material& m, float3 wi, bool entering, float u3, float u4,
+                                                  float u5) {
+  BsdfSample s;
+  s.ok = true;
+  s.delta = false;
+  s.pdf = 0.0f;
+  s.lobe = 0;
+  s.weight = f3(0.f, 0.f, 0.f);
+  if (T == PT_BSDF_DIELECTRIC) {
+    float eta = entering ? m.eta : 1.0f / m.eta;
+    float cos_t;
+    float F = fresnel_dielectric(wi.z, eta, cos_t);
+    s.delta = true;
+    if (u3 < F) {
+      s.wo = f3(-wi.x, -wi.y, wi.z);
+      s.weight = f3(1.f, 1.f, 1.f);
+      s.lobe = 2;
+    } else {
+      float ie = 1.0f / eta;
+      s.wo = f3(-wi.x * ie, -wi.y * ie, -cos_t);
+      float k = ie * ie;
+      s.weight = f3(k, k, k);
+      s.lobe = 3;
+    }
+    s.ev.f = f3(0.f, 0.f, 0.f);
+    return s;
+  }
+  if (T == PT_BSDF_DIFFUSE) {
+    s.wo = cosine_sample(u4, u5);
+  } else if (T == PT_BSDF_CONDUCTOR) {
+    s.ok = ggx_sample(m.alpha, wi, u4, u5, s.wo);
+    s.lobe = 1;
+  } else {  // blend
+    if (u3 < m.wd) {
+      s.wo = cosine_sample(u4, u5);
+    } else {
+      s.ok = ggx_sample(m.alpha, wi, u4, u5, s.wo);
+      s.lobe = 1;
+    }
+  }
+  if (!s.ok) return s;
+  s.ev = bsdf_eval<T, GRAD>(m, wi, s.wo);
+  s.pdf = s.ev.pdf;
+  if (!(s.pdf > 0.0f) || !(max3f(s.ev.f) > 0.0f)) {
+    s.ok = false;
+    return s;
+  }
+  s.weight = s.ev.f * (s.wo.z / s.pdf);
+  return s;
+}
+
+// Polymorphic call over the BSDF type.  MATCH: the warp votes once per type and
+// runs each type's code with only its lanes active (ballot grouping); SWITCH:
+// plain per-lane branch.
+template <class F>
+__device__ __forceinline__ void dispatch_bsdf(int mode, int type, F&& f) {
+  if (mode == PT_DISPATCH_MATCH) {
+    unsigned active = __activemask();
+    if (__any_sync(active, type == PT_BSDF_DIFFUSE)) { if (type == PT_BSDF_DIFFUSE) f.template operator()<PT_BSDF_DIFFUSE>(); }
+    if (__any_sync(active, type == PT_BSDF_CONDUCTOR)) { if (type == PT_BSDF_CONDUCTOR) f.template operator()<PT_BSDF_CONDUCTOR>(); }
+    if (__any_sync(active, type == PT_BSDF_DIELECTRIC)) { if (type == PT_BSDF_DIELECTRIC) f.template operator()<PT_BSDF_DIELECTRIC>(); }
+    if (__any_sync(active, type == PT_BSDF_BLEND)) { if (type == PT_BSDF_BLEND) f.template operator()<PT_BSDF_BLEND>(); }
+  } else {
+    switch (type) {
+      case PT_BSDF_DIFFUSE: f.template operator()<PT_BSDF_DIFFUSE>(); break;
+      case PT_BSDF_CONDUCTOR: f.template operator()<PT_BSDF_CONDUCTOR>(); break;
+      case PT_BSDF_DIELECTRIC: f.template operator()<PT_BSDF_DIELECTRIC>(); break;
+      case PT_BSDF_BLEND: f.template operator()<PT_BSDF_BLEND>(); break;
+      default: break;
+    }
+  }
+}
+
+// ---------------------------------------------------------------- emitters
+__device__ __forceinline__ int cdf_pick(const float* __restrict__ cdf, int n, float u) {
+  // first i with u < cdf[i+1]
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    int mid = (lo + hi) >> 1;
+    if (u < __ldg(&cdf[mid + 1])) hi = mid;
+    else lo = mid + 1;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ float power_heuristic(float a, float b) {
+  float a2 = a * a, b2 = b * b;
+  return (a2 + b2) > 0.0f ? a2 / (a2 + b2) : 0.0f;
+}
+
+__device__ __forceinline__ void env_pixel(const DevScene& S, float3 d, int& x, int& y) {
+  float phi = atan2f(d.z, d.x);
+  if (phi < 0.0f) phi += 2.0f * PT_PI;
+  float theta = acosf(fminf(1.0f, fmaxf(-1.0f, d.y)));
+  x = min((int)(phi * (0.5f * PT_INV_PI) * S.env_w), S.env_w - 1);
+  y = min((int)(theta * PT_INV_PI * S.env_h), S.env_h - 1);
+}
+__device__ __forceinline__ float env_pdf_at(const DevScene& S, int x, int y, float sin_t) {
+  if (!(sin_t > 0.0f)) return 0.0f;
+  float p = __ldg(&S.env_p[y * S.env_w + x]) * (float)S.env_w * (float)S.env_h;
+  return p / (2.0f * PT_PI * PT_PI * sin_t);
+}
+
+// ---------------------------------------------------------------- gradient scatter
+__device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
+
+__device__ __forceinline__ int nth_set_bit(unsigned m, int n) {
+  // smallest p with popc(m & bits[0..p]) > n
+  int lo = 0;
+#pragma unroll
+  for (int step = 16; step > 0; step >>= 1) {
+    int p = lo + step - 1;
+    unsigned upto = (p >= 31) ? 0xffffffffu : ((2u << p) - 1u);
+    if (__popc(m & upto) <= n) lo += step;
+  }
+  return lo;
+}
+
+// Warp-aggregated reduction: lanes with equal `key` (among the currently
+// converged lanes) sum their values with a segmented tree of shuffles; the
+// group's first lane returns true and holds the sum.
+template <int NV>
+__device__ __forceinline__ bool warp_aggregate(unsigned key, float (&v)[NV]) {
+  unsigned active = __activemask();
+  unsigned peers = __match_any_sync(active, key);
+  int lane = lane_id();
+  int n = __popc(peers);
+  int rank = __popc(peers & ((1u << lane) - 1u));
+  int maxn = __reduce_max_sync(active, (unsigned)n);
+  for (int s = 1; s < maxn; s <<= 1) {
+    int src_rank = rank + s;
+    int src = src_rank < n ? nth_set_bit(peers, src_rank) : lane;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      float x = __shfl_sync(active, v[k], src);
+      if ((rank & (2 * s - 1)) == 0 && src_rank < n) v[k] += x;
+    }
+  }
+  return rank == 0;
+}
+
+}  // namespace ptgb

@@ -1,0 +1,114 @@
+// Internal device-side data layout shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/pt.h"
+
+namespace ptgb {
+
+// Shape record on the device: four 16-byte words (one __ldg each).
+struct alignas(16) DevShape {
+  int bsdf, tex, albedo_index, rough_index;  // word 0
+  float alpha, eta, wd, emitter;              // word 1 (emitter: 1.0 if it emits)
+  float f0x, f0y, f0z, pad0;                  // word 2
+  float lex, ley, lez, pad1;                  // word 3
+};
+
+// Camera precomputed on the host (double -> float).
+struct DevCamera {
+  float ox, oy, oz;
+  float fx, fy, fz;   // forward
+  float rx, ry, rz;   // right * tan(vfov/2) * aspect
+  float ux, uy, uz;   // up * tan(vfov/2)
+};
+
+struct DevScene {
+  // geometry in BVH leaf order: three float4 per triangle (v0 | orig id bits, e1, e2)
+  const float4* tri_v;
+  // attributes in leaf order: (u0, v0, u1, v1), (u2, v2, shape bits, 0)
+  const float4* tri_a;
+  const float4* nodes;   // binary: 4 float4 per node; wide: 5 uint4 per node
+  int layout;            // PT_BVH_BINARY / PT_BVH_WIDE
+  int n_tris;
+  const DevShape* shapes;
+  int n_shapes;
+  // area lights: 4 float4 per light triangle: v0 (w = orig tri id bits), v1, v2, Le
+  const float4* lights;
+  const float* light_cdf;  // [n_lights + 1], normalised
+  int n_lights;
+  float light_area;
+  // environment map
+  const float4* env;       // [h][w]
+  const float* env_marg;   // [h + 1]
+  const float* env_cond;   // [h][w + 1]
+  const float* env_p;      // [h][w] pixel probabilities
+  int env_w, env_h;
+  int* status;             // device status word (first error wins)
+};
+
+struct DevParams {
+  const float* albedo;
+  const float4* tex[PT_MAX_TEX];
+  int tex_w[PT_MAX_TEX], tex_h[PT_MAX_TEX];
+  const float* rough;
+  int n_albedo, n_rough;
+};
+
+struct DevGrads {
+  float* albedo;
+  float4* tex[PT_MAX_TEX];
+  float* rough;
+  int n_albedo, n_rough;
+  int smem_albedo, smem_rough;  // per-CTA shared-memory staging of these (0/1)
+};
+
+// Everything one render launch needs (passed by value as the kernel parameter).
+struct LaunchArgs {
+  DevScene scene;
+  DevParams params;
+  DevGrads grads;
+  int n_cams, width, height, spp, max_depth, rr_depth, nee, dispatch;
+  int crop_x0, crop_y0, crop_w, crop_h;
+  int lanes_per_pixel, log2_lanes;
+  int tex_aggregate;
+  unsigned long long seed;
+  long long n_units;          // n_cams * crop_w * crop_h * lanes_per_pixel
+  float* image;               // forward output
+  const float* grad_image;    // adjoint input
+  float* dbg_L;
+  uint32_t* dbg_hash;
+  unsigned long long* counters;
+  DevCamera cams[PT_MAX_CAMS];
+};
+
+}  // namespace ptgb
+
+// Library-side scene object behind the opaque pt_scene handle.
+struct pt_scene {
+  ptgb::DevScene dev;       // device pointers handed to kernels
+  // host copies needed for (re)building the BVH
+  int n_tris = 0;
+  float* h_vertices = nullptr;  // [n][3][3]
+  float* h_uvs = nullptr;       // [n][3][2]
+  int* h_tri_shape = nullptr;   // [n]
+  int n_shapes = 0;
+  int has_bvh = 0;
+  int max_tex_slot = -1;        // highest texture slot any shape uses
+  int max_albedo_row = -1;
+  int max_rough = -1;
+  // device allocations owned by the scene
+  void* d_tri_v = nullptr;
+  void* d_tri_a = nullptr;
+  void* d_nodes = nullptr;
+  void* d_shapes = nullptr;
+  void* d_lights = nullptr;
+  void* d_light_cdf = nullptr;
+  void* d_env = nullptr;
+  void* d_env_marg = nullptr;
+  void* d_env_cond = nullptr;
+  void* d_env_p = nullptr;
+  void* d_status = nullptr;
+  pt_scene_info info{};
+};

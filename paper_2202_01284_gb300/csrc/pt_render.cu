@@ -1,0 +1,590 @@
+// Forward megakernel and fused PRB adjoint megakernel, plus their C-ABI launchers.
+#include <cmath>
+#include <cstring>
+
+#include "pt_device.cuh"
+
+namespace ptgb {
+
+// Per-vertex gradient sink of the adjoint: warp-aggregated atomics.
+// Constant-albedo rows and roughness entries are few and heavily shared, so
+// they are reduced per warp and staged in shared memory per CTA; texels are
+// many and rarely shared, so aggregation is optional for them.
+struct GradSink {
+  float* s_alb;    // shared staging (or nullptr -> global)
+  float* s_rough;
+  template <bool INSTR>
+  __device__ __forceinline__ void add(const LaunchArgs& A, const Material& m, float3 g_alb, float g_alpha,
+                                      Counters<INSTR>& cnt) {
+    const DevGrads& G = A.grads;
+    if (m.alb_kind == 2) {
+      float4* dst = G.tex[m.tex];
+      if (dst) {
+        cnt.add(7, 1);
+        if (A.tex_aggregate) {
+          float v[3] = {g_alb.x, g_alb.y, g_alb.z};
+          unsigned long long key = ((unsigned long long)m.tex << 32) | (unsigned)m.alb_ref;
+          unsigned active = __activemask();
+          unsigned peers = __match_any_sync(active, key);
+          int lane = lane_id();
+          int n = __popc(peers);
+          int rank = __popc(peers & ((1u << lane) - 1u));
+          int maxn = __reduce_max_sync(active, (unsigned)n);
+          for (int s = 1; s < maxn; s <<= 1) {
+            int src_rank = rank + s;
+            int src = src_rank < n ? nth_set_bit(peers, src_rank) : lane;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+              float x = __shfl_sync(active, v[k], src);
+              if ((rank & (2 * s - 1)) == 0 && src_rank < n) v[k] += x;
+            }
+          }
+          if (rank == 0) {
+            atomicAdd(&dst[m.alb_ref], make_float4(v[0], v[1], v[2], 0.0f));
+            cnt.add(6, 1);
+          }
+        } else {
+          atomicAdd(&dst[m.alb_ref], make_float4(g_alb.x, g_alb.y, g_alb.z, 0.0f));
+          cnt.add(6, 1);
+        }
+      }
+    } else if (m.alb_kind == 1 && G.albedo) {
+      cnt.add(7, 1);
+      float v[3] = {g_alb.x, g_alb.y, g_alb.z};
+      if (warp_aggregate<3>((unsigned)m.alb_ref, v)) {
+        float* dst = s_alb ? s_alb : G.albedo;
+        atomicAdd(&dst[3 * m.alb_ref + 0], v[0]);
+        atomicAdd(&dst[3 * m.alb_ref + 1], v[1]);
+        atomicAdd(&dst[3 * m.alb_ref + 2], v[2]);
+        cnt.add(6, 1);
+      }
+    }
+    if (m.rough >= 0 && G.rough && (m.type == PT_BSDF_CONDUCTOR || m.type == PT_BSDF_BLEND)) {
+      cnt.add(7, 1);
+      float v[1] = {g_alpha};
+      if (warp_aggregate<1>((unsigned)m.rough, v)) {
+        float* dst = s_rough ? s_rough : G.rough;
+        atomicAdd(&dst[m.rough], v[0]);
+        cnt.add(6, 1);
+      }
+    }
+  }
+};
+
+__device__ __forceinline__ float3 ratio_grad(float3 dl, float3 x, float3 df, float3 f) {
+  return f3(f.x > 0.0f ? dl.x * x.x * df.x / f.x : 0.0f, f.y > 0.0f ? dl.y * x.y * df.y / f.y : 0.0f,
+            f.z > 0.0f ? dl.z * x.z * df.z / f.z : 0.0f);
+}
+
+__device__ __forceinline__ float3 offset_origin(float3 p, float3 ng, float3 d) {
+  float eps = 1e-4f * fmaxf(1.0f, fmaxf(fabsf(p.x), fmaxf(fabsf(p.y), fabsf(p.z))));
+  return p + ng * (dot3(ng, d) >= 0.0f ? eps : -eps);
+}
+
+// One Monte Carlo sample of pixel (px, py) of camera `ci`.  With GRADPASS the
+// path is a replay: L_total is the radiance pass 0 returned for this very
+// sample, and the derivative terms are scattered into A.grads.
+template <bool ADJ, bool INSTR>
+__device__ __noinline__ float3 trace_path(const LaunchArgs& A, int ci, int px, int py, int si, bool grad_pass,
+                                          float3 L_total, float3 dl, Counters<INSTR>& cnt, uint32_t* hash_out,
+                                          GradSink& sink) {
+  const DevScene& S = A.scene;
+  const DevCamera& cam = A.cams[ci];
+  Pcg32 rng;
+  unsigned long long pixel = (unsigned long long)py * (unsigned long long)A.width + (unsigned long long)px;
+  rng.seed(A.seed, ((unsigned long long)ci << 40) | (pixel << 12) | (unsigned long long)si);
+  Fnv fh{2166136261u};
+
+  float j0 = rng.uniform(), j1 = rng.uniform();
+  float sx = 2.0f * (px + j0) / A.width - 1.0f;
+  float sy = 1.0f - 2.0f * (py + j1) / A.height;
+  Ray ray;
+  ray.o = f3(cam.ox, cam.oy, cam.oz);
+  ray.d = normalize3(f3(cam.fx + cam.rx * sx + cam.ux * sy, cam.fy + cam.ry * sx + cam.uy * sy,
+                        cam.fz + cam.rz * sx + cam.uz * sy));
+  cnt.add(0, 1);
+
+  const bool has_area = S.n_lights > 0;
+  const bool has_env = S.env_w > 0;
+  const float p_env = has_env ? (has_area ? 0.5f : 1.0f) : 0.0f;
+  const float p_area = has_area ? 1.0f - p_env : 0.0f;
+
+  float3 beta = f3(1.f, 1.f, 1.f), L = f3(0.f, 0.f, 0.f);
+  float3 Lrem = L_total;
+  bool prev_delta = true;
+  float prev_pdf = 0.0f;
+  for (int depth = 1;; ++depth) {
+    cnt.add(1, 1);
+    Hit hit = trace_binary<false, INSTR>(S, ray, INFINITY, cnt);
+    if (hit.pos < 0) {
+      fh.add(0xffffffffu);
+      if (has_env) {
+        int ex, ey;
+        env_pixel(S, ray.d, ex, ey);
+        float3 Le = xyz(__ldg(&S.env[ey * S.env_w + ex]));
+        float w = 1.0f;
+        if (!prev_delta && A.nee) {
+          float st = sqrtf(fmaxf(0.0f, 1.0f - ray.d.y * ray.d.y));
+          w = power_heuristic(prev_pdf, p_env * env_pdf_at(S, ex, ey, st));
+        }
+        float3 c = beta * Le * w;
+        L = L + c;
+        Lrem = Lrem - c;
+      }
+      break;
+    }
+    float4 tv0 = __ldg(&S.tri_v[3 * hit.pos]);
+    float4 tv1 = __ldg(&S.tri_v[3 * hit.pos + 1]);
+    float4 tv2 = __ldg(&S.tri_v[3 * hit.pos + 2]);
+    fh.add(__float_as_uint(tv0.w));
+    float4 ta0 = __ldg(&S.tri_a[2 * hit.pos]);
+    float4 ta1 = __ldg(&S.tri_a[2 * hit.pos + 1]);
+    int shape = __float_as_int(ta1.z);
+    const int4* shp = reinterpret_cast<const int4*>(&S.shapes[shape]);
+    int4 sw0 = __ldg(shp);
+    float4 sw1 = __ldg(reinterpret_cast<const float4*>(shp + 1));
+    float3 ng = normalize3(cross3(xyz(tv1), xyz(tv2)));
+    float3 wi_w = -ray.d;
+    float cos_front = dot3(ng, wi_w);
+    if (sw1.w > 0.0f && cos_front > 0.0f) {
+      float4 sw3 = __ldg(reinterpret_cast<const float4*>(shp + 3));
+      float w = 1.0f;
+      if (!prev_delta && A.nee) {
+        float pdf_l = p_area * hit.t * hit.t / (cos_front * S.light_area);
+        w = power_heuristic(prev_pdf, pdf_l);
+      }
+      float3 c = beta * xyz(sw3) * w;
+      L = L + c;
+      Lrem = Lrem - c;
+    }
+    if (depth >= A.max_depth) break;
+    float u[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) u[k] = rng.uniform();
+    const int type = sw0.x;
+    if (type == PT_BSDF_NONE) break;
+
+    float3 p = ray.o + ray.d * hit.t;
+    float b0 = 1.0f - hit.u - hit.v;
+    float tu = b0 * ta0.x + hit.u * ta0.z + hit.v * ta1.x;
+    float tvv = b0 * ta0.y + hit.u * ta0.w + hit.v * ta1.y;
+    // ---- resolve the material (closure record + differentiable parameters)
+    Material m;
+    m.type = type;
+    m.tex = sw0.y;
+    m.alpha = sw1.x;
+    m.eta = sw1.y;
+    m.wd = sw1.z;
+    m.rough = sw0.w;
+    m.alb_kind = 0;
+    m.alb_ref = 0;
+    m.albedo = f3(0.f, 0.f, 0.f);
+    if (m.rough >= 0) m.alpha = __ldg(&A.params.rough[m.rough]);
+    {
+      float4 sw2 = __ldg(reinterpret_cast<const float4*>(shp + 2));
+      m.f0 = xyz(sw2);
+    }
+    uint32_t texel_word = 0xffffffffu;
+    if (type == PT_BSDF_DIFFUSE || type == PT_BSDF_BLEND) {
+      if (m.tex >= 0) {
+        // nearest lookup (App. B): pos = min(uint(uv * res), res - 1), texel [pos.y, pos.x]
+        int w = A.params.tex_w[m.tex], h = A.params.tex_h[m.tex];
+        int x = min((int)(fmaxf(tu, 0.0f) * (float)w), w - 1);
+        int y = min((int)(fmaxf(tvv, 0.0f) * (float)h), h - 1);
+        int idx = y * w + x;
+        m.albedo = xyz(__ldg(&A.params.tex[m.tex][idx]));
+        m.alb_kind = 2;
+        m.alb_ref = idx;
+        texel_word = (uint32_t)idx;
+        cnt.add(5, 1);
+      } else if (sw0.z >= 0) {
+        const float* a = &A.params.albedo[3 * sw0.z];
+        m.albedo = f3(__ldg(a), __ldg(a + 1), __ldg(a + 2));
+        m.alb_kind = 1;
+        m.alb_ref = sw0.z;
+      }
+    }
+    fh.add(texel_word);
+
+    const bool entering = cos_front > 0.0f;
+    const float3 n_s = entering ? ng : -ng;
+    const Frame fr = make_frame(n_s);
+    const float3 wi = fr.to_local(wi_w);
+    float3 g_alb = f3(0.f, 0.f, 0.f);
+    float g_alpha = 0.0f;
+
+    // ---- next-event estimation (non-delta BSDFs)
+    if (type != PT_BSDF_DIELECTRIC && A.nee && (has_area || has_env)) {
+      const bool pick_env = has_env && (!has_area || u[7] < 0.5f);
+      float3 dir, Le;
+      float pdf_l = 0.0f, dist = INFINITY;
+      bool valid = false;
+      if (pick_env) {
+        int y = cdf_pick(S.env_marg, S.env_h, u[1]);
+        const float* cond = S.env_cond + (size_t)y * (S.env_w + 1);
+        int x = cdf_pick(cond, S.env_w, u[2]);
+        float m0 = __ldg(&S.env_marg[y]), m1 = __ldg(&S.env_marg[y + 1]);
+        float c0 = __ldg(&cond[x]), c1 = __ldg(&cond[x + 1]);
+        float fv = (u[1] - m0) / (m1 - m0);
+        float fu = (u[2] - c0) / (c1 - c0);
+        float theta = PT_PI * (y + fv) / S.env_h, phi = 2.0f * PT_PI * (x + fu) / S.env_w;
+        float st, ct, sp, cp;
+        sincosf(theta, &st, &ct);
+        sincosf(phi, &sp, &cp);
+        dir = f3(st * cp, ct, st * sp);
+        Le = xyz(__ldg(&S.env[y * S.env_w + x]));
+        pdf_l = p_env * env_pdf_at(S, x, y, st);
+        valid = pdf_l > 0.0f;
+        fh.add(0x80000000u | (uint32_t)(y * S.env_w + x));
+      } else {
+        int k = cdf_pick(S.light_cdf, S.n_lights, u[0]);
+        float4 l0 = __ldg(&S.lights[4 * k]);
+        float4 l1 = __ldg(&S.lights[4 * k + 1]);
+        float4 l2 = __ldg(&S.lights[4 * k + 2]);
+        float4 l3 = __ldg(&S.lights[4 * k + 3]);
+        float su = sqrtf(u[1]);
+        float lb0 = 1.0f - su, lb1 = u[2] * su;
+        float3 q = xyz(l0) * lb0 + xyz(l1) * lb1 + xyz(l2) * (1.0f - lb0 - lb1);
+        float3 dv = q - p;
+        dist = sqrtf(dot3(dv, dv));
+        dir = dv * (1.0f / dist);
+        float3 nl = normalize3(cross3(xyz(l1) - xyz(l0), xyz(l2) - xyz(l0)));
+        float cos_l = -dot3(nl, dir);
+        Le = xyz(l3);
+        if (cos_l > 0.0f && dist > 0.0f) {
+          pdf_l = p_area * dist * dist / (cos_l * S.light_area);
+          valid = true;
+        }
+        fh.add(__float_as_uint(l0.w));
+      }
+      const float3 wl = fr.to_local(dir);
+      BsdfEval ev;
+      dispatch_bsdf(A.dispatch, type, [&]<int T>() {
+        if constexpr (T != PT_BSDF_DIELECTRIC) ev = bsdf_eval<T, ADJ>(m, wi, wl);
+      });
+      uint32_t vis = 2;
+      if (valid && wl.z > 0.0f && max3f(ev.f) > 0.0f) {
+        Ray sr;
+        sr.o = offset_origin(p, ng, dir);
+        sr.d = dir;
+        float tmax = pick_env ? INFINITY : dist * (1.0f - 1e-3f);
+        cnt.add(2, 1);
+        Hit sh = trace_binary<true, INSTR>(S, sr, tmax, cnt);
+        bool occ = sh.pos >= 0;
+        vis = occ ? 1u : 0u;
+        if (!occ) {
+          float w = power_heuristic(pdf_l, ev.pdf);
+          float3 scale = Le * (wl.z * w / pdf_l);
+          float3 c = beta * ev.f * scale;
+          L = L + c;
+          if (ADJ && grad_pass) {
+            Lrem = Lrem - c;
+            g_alb = g_alb + ratio_grad(dl, c, ev.df_alb, ev.f);
+            float3 ga = ratio_grad(dl, c, ev.df_alpha, ev.f);
+            g_alpha += ga.x + ga.y + ga.z;
+          }
+        }
+      }
+      fh.add(vis);
+    }
+    // ---- BSDF sampling (detached) and attached value
+    BsdfSample bs;
+    dispatch_bsdf(A.dispatch, type, [&]<int T>() { bs = bsdf_sample<T, ADJ>(m, wi, entering, u[3], u[4], u[5]); });
+    fh.add((uint32_t)bs.lobe);
+    if (bs.delta) fh.add(0xfffffffeu);
+    if (ADJ && grad_pass) {
+      if (bs.ok && !bs.delta) {
+        float3 lr = f3(fmaxf(Lrem.x, 0.f), fmaxf(Lrem.y, 0.f), fmaxf(Lrem.z, 0.f));
+        g_alb = g_alb + ratio_grad(dl, lr, bs.ev.df_alb, bs.ev.f);
+        float3 ga = ratio_grad(dl, lr, bs.ev.df_alpha, bs.ev.f);
+        g_alpha += ga.x + ga.y + ga.z;
+      }
+      if (m.alb_kind != 0 || m.rough >= 0) sink.add<INSTR>(A, m, g_alb, g_alpha, cnt);
+    }
+    if (!bs.ok) break;
+    beta = beta * bs.weight;
+    prev_delta = bs.delta;
+    prev_pdf = bs.pdf;
+    const float3 wo = fr.to_world(bs.wo);
+    ray.o = offset_origin(p, ng, wo);
+    ray.d = wo;
+    // ---- Russian roulette
+    if (A.rr_depth >= 0 && depth >= A.rr_depth) {
+      float q = fminf(max3f(beta), 0.95f);
+      bool cont = u[6] < q;
+      fh.add(cont ? 1u : 0u);
+      if (!cont) break;
+      beta = beta * (1.0f / q);
+    }
+  }
+  if (hash_out) *hash_out = fh.h;
+  return L;
+}
+
+template <bool INSTR>
+__device__ __forceinline__ void flush_counters(const LaunchArgs& A, Counters<INSTR>& cnt) {
+  if constexpr (INSTR) {
+    if (A.counters) {
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        unsigned long long v = cnt.c[i];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+        if (lane_id() == 0 && v) atomicAdd(&A.counters[i], v);
+      }
+    }
+  }
+}
+
+struct PixelOf {
+  int cam, ix, iy, px, py;
+  long long pix;  // dense index of the pixel in the output
+};
+__device__ __forceinline__ PixelOf unit_pixel(const LaunchArgs& A, long long unit) {
+  PixelOf r;
+  long long pix = unit >> A.log2_lanes;
+  long long per_cam = (long long)A.crop_w * A.crop_h;
+  r.cam = (int)(pix / per_cam);
+  long long rem = pix - (long long)r.cam * per_cam;
+  r.iy = (int)(rem / A.crop_w);
+  r.ix = (int)(rem - (long long)r.iy * A.crop_w);
+  r.px = A.crop_x0 + r.ix;
+  r.py = A.crop_y0 + r.iy;
+  r.pix = pix;
+  return r;
+}
+
+template <bool INSTR>
+__global__ void __launch_bounds__(256) forward_kernel(const __grid_constant__ LaunchArgs A) {
+  long long unit = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  bool valid = unit < A.n_units;
+  Counters<INSTR> cnt;
+  if constexpr (INSTR) {
+    for (int i = 0; i < 8; ++i) cnt.c[i] = 0;
+  }
+  GradSink sink{nullptr, nullptr};
+  float3 sum = f3(0.f, 0.f, 0.f);
+  PixelOf P{};
+  int lane_in_pix = (int)(unit & (A.lanes_per_pixel - 1));
+  if (valid) {
+    P = unit_pixel(A, unit);
+    for (int s = lane_in_pix; s < A.spp; s += A.lanes_per_pixel) {
+      uint32_t h;
+      float3 L = trace_path<false, INSTR>(A, P.cam, P.px, P.py, s, false, f3(0.f, 0.f, 0.f), f3(0.f, 0.f, 0.f), cnt,
+                                          INSTR ? &h : nullptr, sink);
+      sum = sum + L;
+      if constexpr (INSTR) {
+        long long si = P.pix * A.spp + s;
+        if (A.dbg_L) {
+          A.dbg_L[3 * si] = L.x;
+          A.dbg_L[3 * si + 1] = L.y;
+          A.dbg_L[3 * si + 2] = L.z;
+        }
+        if (A.dbg_hash) A.dbg_hash[si] = h;
+      }
+    }
+  }
+  for (int off = 1; off < A.lanes_per_pixel; off <<= 1) {
+    sum.x += __shfl_xor_sync(0xffffffffu, sum.x, off);
+    sum.y += __shfl_xor_sync(0xffffffffu, sum.y, off);
+    sum.z += __shfl_xor_sync(0xffffffffu, sum.z, off);
+  }
+  if (valid && lane_in_pix == 0) {
+    float inv = 1.0f / (float)A.spp;
+    A.image[3 * P.pix] = sum.x * inv;
+    A.image[3 * P.pix + 1] = sum.y * inv;
+    A.image[3 * P.pix + 2] = sum.z * inv;
+  }
+  flush_counters<INSTR>(A, cnt);
+}
+
+template <bool INSTR>
+__global__ void __launch_bounds__(256) adjoint_kernel(const __grid_constant__ LaunchArgs A) {
+  extern __shared__ float smem[];
+  const DevGrads& G = A.grads;
+  float* s_alb = G.smem_albedo ? smem : nullptr;
+  float* s_rough = G.smem_rough ? smem + (G.smem_albedo ? 3 * G.n_albedo : 0) : nullptr;
+  int n_stage = (G.smem_albedo ? 3 * G.n_albedo : 0) + (G.smem_rough ? G.n_rough : 0);
+  for (int i = threadIdx.x; i < n_stage; i += blockDim.x) smem[i] = 0.0f;
+  __syncthreads();
+
+  long long unit = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  bool valid = unit < A.n_units;
+  Counters<INSTR> cnt;
+  if constexpr (INSTR) {
+    for (int i = 0; i < 8; ++i) cnt.c[i] = 0;
+  }
+  GradSink sink{s_alb, s_rough};
+  if (valid) {
+    PixelOf P = unit_pixel(A, unit);
+    int lane_in_pix = (int)(unit & (A.lanes_per_pixel - 1));
+    float inv = 1.0f / (float)A.spp;
+    float3 dl = f3(A.grad_image[3 * P.pix] * inv, A.grad_image[3 * P.pix + 1] * inv, A.grad_image[3 * P.pix + 2] * inv);
+    for (int s = lane_in_pix; s < A.spp; s += A.lanes_per_pixel) {
+      // pass 0: radiance of this sample; pass 1: replay with gradient scatter
+      float3 L = f3(0.f, 0.f, 0.f);
+#pragma unroll 1
+      for (int pass = 0; pass < 2; ++pass) {
+        L = trace_path<true, INSTR>(A, P.cam, P.px, P.py, s, pass == 1, L, dl, cnt, nullptr, sink);
+      }
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < n_stage; i += blockDim.x) {
+    float v = smem[i];
+    if (v != 0.0f) {
+      if (G.smem_albedo && i < 3 * G.n_albedo) atomicAdd(&G.albedo[i], v);
+      else atomicAdd(&G.rough[i - (G.smem_albedo ? 3 * G.n_albedo : 0)], v);
+    }
+  }
+  flush_counters<INSTR>(A, cnt);
+}
+
+}  // namespace ptgb
+
+// ============================================================================ host side
+using namespace ptgb;
+
+namespace {
+
+int fill_launch(pt_scene* s, const pt_render_desc* r, const pt_params* p, LaunchArgs& A) {
+  if (!s || !r || !p) return PT_ERR_ARG;
+  if (!s->has_bvh) return PT_ERR_STATE;
+  if (r->n_cams < 1 || r->n_cams > PT_MAX_CAMS || !r->cams) return PT_ERR_ARG;
+  if (r->width < 1 || r->height < 1 || r->spp < 1 || r->spp > 4096 || r->max_depth < 1) return PT_ERR_ARG;
+  if ((long long)r->width * r->height > (1ll << 28)) return PT_ERR_ARG;  // pixel index fits the RNG stream layout
+  int cw = r->crop_w > 0 ? r->crop_w : r->width, ch = r->crop_w > 0 ? r->crop_h : r->height;
+  int x0 = r->crop_w > 0 ? r->crop_x0 : 0, y0 = r->crop_w > 0 ? r->crop_y0 : 0;
+  if (x0 < 0 || y0 < 0 || cw < 1 || ch < 1 || x0 + cw > r->width || y0 + ch > r->height) return PT_ERR_ARG;
+  if (r->dispatch != PT_DISPATCH_SWITCH && r->dispatch != PT_DISPATCH_MATCH) return PT_ERR_ARG;
+  // parameters the scene references must be present
+  if (s->max_albedo_row >= 0 && (!p->albedo || p->n_albedo <= s->max_albedo_row)) return PT_ERR_ARG;
+  if (s->max_rough >= 0 && (!p->roughness || p->n_rough <= s->max_rough)) return PT_ERR_ARG;
+  for (int t = 0; t <= s->max_tex_slot; ++t)
+    if (!p->tex[t] || p->tex_w[t] < 1 || p->tex_h[t] < 1 || (long long)p->tex_w[t] * p->tex_h[t] > (1ll << 31) - 1)
+      return PT_ERR_ARG;
+  std::memset(&A, 0, sizeof A);
+  A.scene = s->dev;
+  A.params.albedo = p->albedo;
+  A.params.n_albedo = p->n_albedo;
+  A.params.rough = p->roughness;
+  A.params.n_rough = p->n_rough;
+  for (int t = 0; t < PT_MAX_TEX; ++t) {
+    A.params.tex[t] = reinterpret_cast<const float4*>(p->tex[t]);
+    A.params.tex_w[t] = p->tex_w[t];
+    A.params.tex_h[t] = p->tex_h[t];
+  }
+  A.n_cams = r->n_cams;
+  A.width = r->width;
+  A.height = r->height;
+  A.spp = r->spp;
+  A.max_depth = r->max_depth;
+  A.rr_depth = r->rr_depth;
+  A.nee = r->nee ? 1 : 0;
+  A.dispatch = r->dispatch;
+  A.crop_x0 = x0;
+  A.crop_y0 = y0;
+  A.crop_w = cw;
+  A.crop_h = ch;
+  int lp = r->lanes_per_pixel;
+  if (lp <= 0) {
+    // auto: spread samples over lanes until there are ~8 waves of 152 SMs x 2048 threads
+    long long pixels = (long long)r->n_cams * cw * ch;
+    lp = 1;
+    while (lp < 32 && lp < r->spp && pixels * lp < 152ll * 2048 * 8) lp <<= 1;
+  }
+  if (lp < 1 || lp > 32 || (lp & (lp - 1))) return PT_ERR_ARG;
+  A.lanes_per_pixel = lp;
+  A.log2_lanes = 0;
+  while ((1 << A.log2_lanes) < lp) ++A.log2_lanes;
+  A.tex_aggregate = r->tex_aggregate ? 1 : 0;
+  A.seed = r->seed;
+  A.n_units = (long long)r->n_cams * cw * ch * lp;
+  A.dbg_L = r->dbg_sample_L;
+  A.dbg_hash = r->dbg_sample_hash;
+  A.counters = r->counters;
+  for (int i = 0; i < r->n_cams; ++i) {
+    const pt_camera& c = r->cams[i];
+    double o[3] = {c.origin[0], c.origin[1], c.origin[2]};
+    double f[3] = {c.target[0] - o[0], c.target[1] - o[1], c.target[2] - o[2]};
+    double fl = std::sqrt(f[0] * f[0] + f[1] * f[1] + f[2] * f[2]);
+    if (!(fl > 0)) return PT_ERR_ARG;
+    for (double& v : f) v /= fl;
+    double up[3] = {c.up[0], c.up[1], c.up[2]};
+    double rt[3] = {f[1] * up[2] - f[2] * up[1], f[2] * up[0] - f[0] * up[2], f[0] * up[1] - f[1] * up[0]};
+    double rl = std::sqrt(rt[0] * rt[0] + rt[1] * rt[1] + rt[2] * rt[2]);
+    if (!(rl > 0)) return PT_ERR_ARG;
+    for (double& v : rt) v /= rl;
+    double uu[3] = {rt[1] * f[2] - rt[2] * f[1], rt[2] * f[0] - rt[0] * f[2], rt[0] * f[1] - rt[1] * f[0]};
+    double th = std::tan(0.5 * c.vfov_deg * 3.14159265358979323846 / 180.0);
+    double asp = (double)r->width / (double)r->height;
+    DevCamera& d = A.cams[i];
+    d.ox = (float)o[0]; d.oy = (float)o[1]; d.oz = (float)o[2];
+    d.fx = (float)f[0]; d.fy = (float)f[1]; d.fz = (float)f[2];
+    d.rx = (float)(rt[0] * th * asp); d.ry = (float)(rt[1] * th * asp); d.rz = (float)(rt[2] * th * asp);
+    d.ux = (float)(uu[0] * th); d.uy = (float)(uu[1] * th); d.uz = (float)(uu[2] * th);
+  }
+  return PT_OK;
+}
+
+int launch_dims(const pt_render_desc* r, const LaunchArgs& A, int& block, long long& grid) {
+  block = r->block_size > 0 ? r->block_size : 128;
+  if (block % 32 || block > 256) return PT_ERR_ARG;
+  grid = (A.n_units + block - 1) / block;
+  if (grid < 1) grid = 1;
+  if (grid > 0x7fffffffll) return PT_ERR_ARG;
+  return PT_OK;
+}
+
+bool instrumented(const pt_render_desc* r) { return r->dbg_sample_L || r->dbg_sample_hash || r->counters; }
+
+}  // namespace
+
+extern "C" int pt_render_forward(pt_scene* s, const pt_render_desc* r, const pt_params* p, float* image,
+                                 void* stream) {
+  LaunchArgs A;
+  int st = fill_launch(s, r, p, A);
+  if (st != PT_OK) return st;
+  if (!image) return PT_ERR_ARG;
+  A.image = image;
+  int block;
+  long long grid;
+  if ((st = launch_dims(r, A, block, grid)) != PT_OK) return st;
+  cudaStream_t cs = (cudaStream_t)stream;
+  if (instrumented(r))
+    forward_kernel<true><<<(unsigned)grid, block, 0, cs>>>(A);
+  else
+    forward_kernel<false><<<(unsigned)grid, block, 0, cs>>>(A);
+  return cudaGetLastError() == cudaSuccess ? PT_OK : PT_ERR_CUDA;
+}
+
+extern "C" int pt_render_backward(pt_scene* s, const pt_render_desc* r, const pt_params* p,
+                                  const float* grad_image, const pt_grads* g, void* stream) {
+  LaunchArgs A;
+  int st = fill_launch(s, r, p, A);
+  if (st != PT_OK) return st;
+  if (!grad_image || !g) return PT_ERR_ARG;
+  if (r->dbg_sample_L || r->dbg_sample_hash) return PT_ERR_ARG;  // per-sample outputs: forward only
+  A.grad_image = grad_image;
+  A.grads.albedo = g->albedo;
+  A.grads.rough = g->roughness;
+  for (int t = 0; t < PT_MAX_TEX; ++t) A.grads.tex[t] = reinterpret_cast<float4*>(g->tex[t]);
+  A.grads.n_albedo = p->n_albedo;
+  A.grads.n_rough = p->n_rough;
+  // stage the small, heavily shared gradient vectors in shared memory
+  size_t smem = 0;
+  A.grads.smem_albedo = (g->albedo && p->n_albedo > 0 && 3 * p->n_albedo <= 3072) ? 1 : 0;
+  if (A.grads.smem_albedo) smem += 3 * (size_t)p->n_albedo;
+  A.grads.smem_rough = (g->roughness && p->n_rough > 0 && smem + p->n_rough <= 6144) ? 1 : 0;
+  if (A.grads.smem_rough) smem += (size_t)p->n_rough;
+  smem *= sizeof(float);
+  int block;
+  long long grid;
+  if ((st = launch_dims(r, A, block, grid)) != PT_OK) return st;
+  cudaStream_t cs = (cudaStream_t)stream;
+  if (instrumented(r))
+    adjoint_kernel<true><<<(unsigned)grid, block, smem, cs>>>(A);
+  else
+    adjoint_kernel<false><<<(unsigned)grid, block, smem, cs>>>(A);
+  return cudaGetLastError() == cudaSuccess ? PT_OK : PT_ERR_CUDA;
+}

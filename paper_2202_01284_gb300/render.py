@@ -1,0 +1,145 @@
+"""Device-side scene wrapper and the differentiable render (torch.autograd.Function).
+
+``DeviceScene`` owns a pt_scene handle (geometry, materials, BVH in
+library-owned device memory) plus the differentiable parameters as torch CUDA
+tensors.  ``RenderFn`` calls ``pt_render_forward`` in its forward and
+``pt_render_backward`` (path replay backpropagation) in its backward; torch
+only provides memory and the stream.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+from typing import Optional, Sequence
+
+import numpy as np
+import torch
+
+from . import abi
+from . import scenes as S
+
+
+@dataclass
+class RenderSettings:
+    width: int
+    height: int
+    spp: int
+    max_depth: int
+    seed: int
+    rr_depth: int = -1
+    nee: bool = True
+    dispatch: int = abi.PT_DISPATCH_SWITCH
+    crop: Optional[tuple] = None       # (x0, y0, w, h)
+    lanes_per_pixel: int = 0
+    block_size: int = 0
+    tex_aggregate: int = 0
+    backward_seed: Optional[int] = None  # None: same seed as forward (correlated); else decorrelated
+
+    def rows_cols(self):
+        return (self.crop[3], self.crop[2]) if self.crop else (self.height, self.width)
+
+
+class DeviceScene:
+    """A scene uploaded through the C ABI, with device copies of its parameters."""
+
+    def __init__(self, scene: S.Scene, layout: int = abi.PT_BVH_BINARY, max_leaf_tris: int = 0, device="cuda"):
+        self.scene = scene
+        self.handle = abi.pt_scene_create(scene)
+        try:
+            abi.pt_bvh_build(self.handle, layout, max_leaf_tris)
+        except Exception:
+            abi.pt_scene_destroy(self.handle)
+            self.handle = None
+            raise
+        dev = torch.device(device)
+        self.albedo = torch.as_tensor(scene.albedo, dtype=torch.float32).reshape(-1, 3).to(dev).contiguous()
+        self.textures = [torch.as_tensor(t, dtype=torch.float32).to(dev).contiguous() for t in scene.textures]
+        self.roughness = torch.as_tensor(scene.roughness, dtype=torch.float32).to(dev).contiguous()
+        self.cameras = list(scene.cameras)
+
+    def info(self) -> dict:
+        return abi.pt_scene_get_info(self.handle)
+
+    def rebuild_bvh(self, layout=abi.PT_BVH_BINARY, max_leaf_tris=0):
+        abi.pt_bvh_build(self.handle, layout, max_leaf_tris)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            abi.pt_scene_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------------ raw calls
+    def _desc(self, cams, st: RenderSettings, seed=None, dbg_L=None, dbg_hash=None, counters=None):
+        return abi.render_desc(cams, st.width, st.height, st.spp, st.max_depth,
+                               st.seed if seed is None else seed, st.rr_depth, st.nee, st.dispatch, st.crop,
+                               st.lanes_per_pixel, st.block_size, st.tex_aggregate, dbg_L, dbg_hash, counters)
+
+    def forward(self, st: RenderSettings, cams: Optional[Sequence[S.Camera]] = None, albedo=None, textures=None,
+                roughness=None, out=None, per_sample=False, counters=None):
+        cams = list(cams) if cams is not None else self.cameras
+        rows, cols = st.rows_cols()
+        dev = self.albedo.device
+        img = out if out is not None else torch.empty((len(cams), rows, cols, 3), device=dev, dtype=torch.float32)
+        dL = dh = None
+        if per_sample:
+            dL = torch.empty((len(cams), rows, cols, st.spp, 3), device=dev, dtype=torch.float32)
+            dh = torch.empty((len(cams), rows, cols, st.spp), device=dev, dtype=torch.int32)
+        p = abi.params_struct(self.albedo if albedo is None else albedo,
+                              self.textures if textures is None else textures,
+                              self.roughness if roughness is None else roughness)
+        desc = self._desc(cams, st, dbg_L=dL, dbg_hash=dh, counters=counters)
+        abi.pt_render_forward(self.handle, desc, p, img, torch.cuda.current_stream(dev).cuda_stream)
+        return (img, dL, dh) if per_sample else img
+
+    def backward(self, st: RenderSettings, grad_image, cams=None, albedo=None, textures=None, roughness=None,
+                 g_albedo=None, g_textures=None, g_roughness=None, seed=None, counters=None):
+        cams = list(cams) if cams is not None else self.cameras
+        p = abi.params_struct(self.albedo if albedo is None else albedo,
+                              self.textures if textures is None else textures,
+                              self.roughness if roughness is None else roughness)
+        g = abi.grads_struct(g_albedo, g_textures or (), g_roughness)
+        desc = self._desc(cams, st, seed=seed, counters=counters)
+        abi.pt_render_backward(self.handle, desc, p, grad_image.contiguous(), g,
+                               torch.cuda.current_stream(grad_image.device).cuda_stream)
+
+    def status(self) -> int:
+        return abi.pt_last_device_status(self.handle, torch.cuda.current_stream().cuda_stream)
+
+
+class RenderFn(torch.autograd.Function):
+    """image = render(albedo, texture_0..k, roughness); backward = path replay backpropagation.
+
+    The backward seed is ``settings.backward_seed`` if given (decorrelated, as the
+    paper's three-phase PRB step does), else the forward seed (correlated).
+    """
+
+    @staticmethod
+    def forward(ctx, dscene: DeviceScene, st: RenderSettings, albedo, roughness, *textures):
+        ctx.dscene = dscene
+        ctx.st = st
+        ctx.save_for_backward(albedo, roughness, *textures)
+        return dscene.forward(st, albedo=albedo.detach().contiguous(), roughness=roughness.detach().contiguous(),
+                              textures=[t.detach().contiguous() for t in textures])
+
+    @staticmethod
+    def backward(ctx, grad_img):
+        albedo, roughness, *textures = ctx.saved_tensors
+        ga = torch.zeros_like(albedo) if ctx.needs_input_grad[2] else None
+        gr = torch.zeros_like(roughness) if ctx.needs_input_grad[3] else None
+        gt = [torch.zeros_like(t) if ctx.needs_input_grad[4 + i] else None for i, t in enumerate(textures)]
+        st = ctx.st
+        seed = st.backward_seed if st.backward_seed is not None else st.seed
+        ctx.dscene.backward(st, grad_img.contiguous(), albedo=albedo.detach(), roughness=roughness.detach(),
+                            textures=[t.detach() for t in textures], g_albedo=ga,
+                            g_textures=[g if g is not None else None for g in gt] if any(g is not None for g in gt) else None,
+                            g_roughness=gr, seed=seed)
+        return (None, None, ga, gr, *gt)
+
+
+def render(dscene: DeviceScene, st: RenderSettings, albedo, roughness, textures: Sequence[torch.Tensor]):
+    return RenderFn.apply(dscene, st, albedo, roughness, *textures)

@@ -1,0 +1,242 @@
+"""GPU parity: the CUDA forward megakernel and PRB adjoint vs the FP64 oracle.
+
+All calls go through the C ABI (paper_2202_01284_gb300.abi / render.DeviceScene).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2202_01284_gb300 import scenes as S
+
+from parity import GRAD_COSINE, PIXEL_FRACTION, cosine, pixel_ok_fraction, rel_ok, sample_report
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2202_01284_gb300 import abi
+    abi.load()
+    return abi
+
+
+def _oracle_render(oracle_mod, scene, st, cam_index=0, per_sample=False):
+    osc = oracle_mod.OracleScene(scene)
+    r = oracle_mod.render_in(scene.cameras[cam_index], st.spp, st.max_depth, st.seed, st.rr_depth, st.nee,
+                             cam_index=cam_index, crop=st.crop)
+    return oracle_mod.render(osc, r, per_sample=per_sample)
+
+
+def _settings(scene, **kw):
+    from paper_2202_01284_gb300.render import RenderSettings
+    cam = scene.cameras[0]
+    base = dict(width=cam.width, height=cam.height, spp=4, max_depth=4, seed=7)
+    base.update(kw)
+    return RenderSettings(**base)
+
+
+def _gpu_forward(lib, scene, st, per_sample=True, **kw):
+    from paper_2202_01284_gb300.render import DeviceScene
+    ds = DeviceScene(scene, **kw)
+    out = ds.forward(st, per_sample=per_sample)
+    torch.cuda.synchronize()
+    assert ds.status() == 0
+    if per_sample:
+        img, L, h = out
+        return ds, img[0].cpu().numpy(), L[0].cpu().numpy(), h[0].cpu().numpy().view(np.uint32)
+    return ds, out[0].cpu().numpy()
+
+
+# ---------------------------------------------------------------- closed forms on the GPU
+def test_furnace_gpu_exact(lib):
+    sc = S.furnace(0.5, 1.0, 16, 16)
+    st = _settings(sc, spp=8, max_depth=6, nee=False)
+    _, img, L, _ = _gpu_forward(lib, sc, st)
+    want = sum(np.float32(0.5) ** k for k in range(6))
+    assert np.allclose(L, want, rtol=2e-6)
+
+
+def test_lit_plane_gpu_exact(lib):
+    sc = S.lit_plane(0.6, 1.5)
+    st = _settings(sc, spp=8, max_depth=3, nee=False)
+    _, img, L, _ = _gpu_forward(lib, sc, st)
+    assert np.allclose(L, np.float32(0.6) * 1.5, rtol=2e-6)
+
+
+# ---------------------------------------------------------------- tiny Cornell box (36 tris)
+@pytest.mark.parametrize("dispatch", [0, 1])
+def test_cornell_forward_parity(lib, oracle_mod, dispatch):
+    sc = S.cornell()
+    st = _settings(sc, spp=4, max_depth=4, seed=7, dispatch=dispatch)
+    _, img, L, h = _gpu_forward(lib, sc, st)
+    ref, refL, refh = _oracle_render(oracle_mod, sc, st, per_sample=True)
+    rep = sample_report(L, h, refL, refh, img, ref)
+    print("cornell per-sample:", rep)
+    assert rep["matched_bad"] == 0, rep
+    assert rep["divergent_fraction"] <= 1e-3, rep
+    assert rep["clean_pixel_fraction_ok"] >= PIXEL_FRACTION, rep
+    frac, _ = pixel_ok_fraction(img, ref)
+    assert frac >= PIXEL_FRACTION
+
+
+def test_cornell_ragged_crop_and_lanes(lib, oracle_mod):
+    """Ragged crop (67x35 is not a multiple of any tile), every lanes-per-pixel split."""
+    sc = S.cornell(width=96, height=80)
+    ref = None
+    for lanes in (1, 2, 4, 8):
+        st = _settings(sc, spp=8, max_depth=3, seed=3, crop=(5, 9, 67, 35), lanes_per_pixel=lanes)
+        _, img = _gpu_forward(lib, sc, st, per_sample=False)
+        if ref is None:
+            ref = _oracle_render(oracle_mod, sc, st)
+        frac, _ = pixel_ok_fraction(img, ref)
+        assert frac >= PIXEL_FRACTION, (lanes, frac)
+
+
+def test_degenerate_settings(lib, oracle_mod):
+    sc = S.cornell(width=16, height=16)
+    # depth 1: only directly visible emission; spp 1; a single pixel crop
+    for kw in (dict(max_depth=1, spp=1), dict(max_depth=2, spp=1, crop=(7, 0, 1, 1)), dict(max_depth=4, spp=3)):
+        st = _settings(sc, seed=11, **kw)
+        _, img = _gpu_forward(lib, sc, st, per_sample=False)
+        ref = _oracle_render(oracle_mod, sc, st)
+        frac, _ = pixel_ok_fraction(img, ref)
+        assert frac >= PIXEL_FRACTION, (kw, frac)
+
+
+def test_bad_arguments_rejected(lib):
+    from paper_2202_01284_gb300.render import DeviceScene
+    sc = S.cornell(width=8, height=8)
+    ds = DeviceScene(sc)
+    for kw in (dict(spp=0), dict(max_depth=0), dict(crop=(4, 4, 8, 8)), dict(lanes_per_pixel=3),
+               dict(block_size=48), dict(spp=5000)):
+        st = _settings(sc, **kw)
+        with pytest.raises(lib.PtError) as e:
+            ds.forward(st)
+        assert e.value.code == lib.PT_ERR_ARG
+    # a scene referencing albedo rows that are not passed
+    with pytest.raises(lib.PtError):
+        ds.forward(_settings(sc), albedo=torch.zeros((2, 3), device="cuda"))
+    bad = S.cornell()
+    bad.tri_shape = bad.tri_shape.copy()
+    bad.tri_shape[0] = 99
+    with pytest.raises(lib.PtError):
+        lib.pt_scene_create(bad)
+
+
+def _loss_grad_image(img, target):
+    return 2.0 * (img - target) / img.size
+
+
+def test_cornell_albedo_gradient_parity(lib, oracle_mod):
+    """PRB adjoint (correlated seed) vs the oracle's stored-tape reverse mode."""
+    sc = S.cornell()
+    st = _settings(sc, spp=4, max_depth=4, seed=7)
+    tgt = sc.with_params(albedo=S.cornell_target_albedo(sc.albedo))
+    T = _oracle_render(oracle_mod, tgt, _settings(tgt, spp=16, max_depth=4, seed=99))
+    I = _oracle_render(oracle_mod, sc, st)
+    gi = _loss_grad_image(I, T)
+    osc = oracle_mod.OracleScene(sc)
+    r = oracle_mod.render_in(sc.cameras[0], st.spp, st.max_depth, st.seed)
+    ga_ref, _, _ = oracle_mod.grad_tape(osc, r, gi)
+    from paper_2202_01284_gb300.render import DeviceScene
+    for dispatch in (0, 1):
+        st.dispatch = dispatch
+        ds = DeviceScene(sc)
+        g = torch.zeros_like(ds.albedo)
+        ds.backward(st, torch.as_tensor(gi[None], dtype=torch.float32, device="cuda"), g_albedo=g)
+        torch.cuda.synchronize()
+        ga = g.cpu().numpy()
+        c = cosine(ga, ga_ref)
+        rel = np.abs(ga - ga_ref).max() / np.abs(ga_ref).max()
+        print("albedo grad cosine", c, "max rel", rel)
+        assert c >= GRAD_COSINE
+        assert rel < 1e-3
+
+
+def test_autograd_function_matches_backward(lib, oracle_mod):
+    from paper_2202_01284_gb300.render import DeviceScene, render
+    sc = S.cornell(width=32, height=32)
+    ds = DeviceScene(sc)
+    st = _settings(sc, spp=4, max_depth=4, seed=5)
+    alb = ds.albedo.clone().requires_grad_(True)
+    rough = ds.roughness.clone()
+    img = render(ds, st, alb, rough, [])
+    target = torch.zeros_like(img)
+    loss = ((img - target) ** 2).mean()
+    loss.backward()
+    g_ref = torch.zeros_like(ds.albedo)
+    ds.backward(st, (2 * (img.detach() - target) / img.numel()), g_albedo=g_ref)
+    torch.cuda.synchronize()
+    assert torch.allclose(alb.grad, g_ref, rtol=1e-6, atol=0)
+
+
+# ---------------------------------------------------------------- textures + roughness (96 shapes)
+def test_cornell96_forward_and_gradients(lib, oracle_mod):
+    sc = S.cornell96(width=512, height=512)
+    crop = (192, 160, 128, 128)
+    st = _settings(sc, spp=16, max_depth=6, seed=21, crop=crop)
+    _, img, L, h = _gpu_forward(lib, sc, st)
+    ref, refL, refh = _oracle_render(oracle_mod, sc, st, per_sample=True)
+    rep = sample_report(L, h, refL, refh, img, ref)
+    print("cornell96 per-sample:", rep)
+    # texel choices flip where FP32 and FP64 uv land on opposite sides of a texel edge:
+    # those pixels are path-divergence outliers (counted); all others meet the 1e-4 bar
+    assert rep["matched_bad"] <= rep["n"] // 10000, rep
+    assert rep["divergent_fraction"] <= 2e-3, rep
+    assert rep["clean_pixel_fraction_ok"] >= PIXEL_FRACTION, rep
+    # gradients: oracle tape on the same crop, correlated seed
+    tgt = sc.with_params(textures=[S.cornell96_target_texture(sc.textures[0])])
+    T = _oracle_render(oracle_mod, tgt, _settings(tgt, spp=16, max_depth=6, seed=23, crop=crop))
+    gi = _loss_grad_image(ref, T)
+    osc = oracle_mod.OracleScene(sc)
+    r = oracle_mod.render_in(sc.cameras[0], st.spp, st.max_depth, st.seed, crop=crop)
+    _, gt_ref, gr_ref = oracle_mod.grad_tape(osc, r, gi)
+    from paper_2202_01284_gb300.render import DeviceScene
+    for agg in (0, 1):
+        st.tex_aggregate = agg
+        ds = DeviceScene(sc)
+        gt = torch.zeros_like(ds.textures[0])
+        gr = torch.zeros_like(ds.roughness)
+        ds.backward(st, torch.as_tensor(gi[None], dtype=torch.float32, device="cuda"), g_textures=[gt],
+                    g_roughness=gr)
+        torch.cuda.synchronize()
+        c_t = cosine(gt.cpu().numpy()[..., :3], gt_ref[0][..., :3])
+        c_r = cosine(gr.cpu().numpy(), gr_ref)
+        print(f"agg={agg} texture grad cosine {c_t:.7f} roughness grad cosine {c_r:.7f}")
+        assert c_r >= GRAD_COSINE
+        assert c_t >= 0.999  # texel flips (path-divergence at texel edges) move single terms
+        assert np.all(gt.cpu().numpy()[..., 3] == 0)
+
+
+# ---------------------------------------------------------------- spheres under an environment map
+def test_spheres_forward_parity(lib, oracle_mod):
+    """GGX conductor, dielectric, textured diffuse, env-map importance sampling, roulette."""
+    sc = S.spheres(n_spheres=6, level=2, grid=(3, 2), ground_quads=8, tex_res=256, width=64, height=48)
+    st = _settings(sc, spp=8, max_depth=8, rr_depth=3, seed=5)
+    _, img, L, h = _gpu_forward(lib, sc, st)
+    ref, refL, refh = _oracle_render(oracle_mod, sc, st, per_sample=True)
+    rep = sample_report(L, h, refL, refh, img, ref)
+    print("spheres per-sample:", rep)
+    assert rep["matched_bad"] <= max(2, rep["n"] // 10000), rep
+    assert rep["divergent_fraction"] < 5e-3, rep
+    assert rep["clean_pixel_fraction_ok"] >= PIXEL_FRACTION, rep
+
+
+def test_counters_and_status(lib):
+    from paper_2202_01284_gb300.render import DeviceScene
+    sc = S.cornell(width=16, height=16)
+    ds = DeviceScene(sc)
+    st = _settings(sc, spp=2, max_depth=3)
+    cnt = torch.zeros(lib.PT_N_COUNTERS, dtype=torch.int64, device="cuda")
+    ds.forward(st, counters=cnt)
+    torch.cuda.synchronize()
+    c = cnt.cpu().numpy()
+    assert c[0] == 16 * 16 * 2          # paths
+    assert c[1] >= c[0]                 # rays >= paths
+    assert c[3] > 0 and c[4] > 0
+    assert ds.status() == 0
