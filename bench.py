@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--tex-aggregate", type=int, default=0)
     ap.add_argument("--small", action="store_true",
-                    help="profiling case: same scene and step at 256x256, 16 spp (not a bench line)")
+                    help="profiling case: same scene and step at 256x256, 64 spp (not a bench line)")
     return ap.parse_args()
 
 
@@ -116,7 +116,7 @@ def make_workload(seed=2022, small=False):
 def settings(args, seed):
     from paper_2202_01284_gb300.render import RenderSettings
     if args.small:
-        return RenderSettings(width=256, height=256, spp=16, max_depth=WORKLOAD["max_depth"],
+        return RenderSettings(width=256, height=256, spp=64, max_depth=WORKLOAD["max_depth"],
                               rr_depth=WORKLOAD["rr_depth"], seed=seed, dispatch=args.dispatch,
                               lanes_per_pixel=args.lanes, block_size=args.block, tex_aggregate=args.tex_aggregate)
     return RenderSettings(width=WORKLOAD["width"], height=WORKLOAD["height"], spp=WORKLOAD["spp"],

@@ -127,42 +127,49 @@ __device__ __forceinline__ bool tri_test(const float4* __restrict__ tv, int pos,
   return false;
 }
 
-// Closest hit (ANY = false) or any hit before tmax (ANY = true) on the 2-wide BVH.
-template <bool ANY, bool INSTR>
-__device__ Hit trace_binary(const DevScene& S, const Ray& r, float tmax, Counters<INSTR>& cnt) {
+// Closest hit (any_hit = false) or any hit before tmax (any_hit = true) on the
+// 2-wide BVH.  "While-while" structure (Aila & Laine 2009): an inner loop walks
+// inner nodes until the lane holds a leaf, a second loop intersects leaves, so
+// lanes of a warp stay in the same phase longer than with one if/else loop.
+template <bool INSTR>
+__device__ __forceinline__ Hit trace_binary(const DevScene& S, float3 ro, float3 rd, float tmax, bool any_hit,
+                                         Counters<INSTR>& cnt) {
   Hit h;
   h.pos = -1;
   h.t = tmax;
   h.u = h.v = 0.0f;
+  Ray r;
+  r.o = ro;
+  r.d = rd;
   uint32_t best_orig = 0xffffffffu;
-  float3 inv = safe_inv(r.d);
-  float3 oi = r.o * inv;
+  const float3 inv = safe_inv(rd);
+  const float3 oi = ro * inv;
   int stack[PT_STACK];
   int sp = 0;
   int cur = 0;
   const float4* __restrict__ N = S.nodes;
   unsigned n_nodes = 0, n_tris = 0;
-  for (;;) {
-    if (cur >= 0) {
+  const int kDone = 0x7fffffff;
+  while (cur != kDone) {
+    // ---- inner nodes
+    while (cur >= 0 && cur != kDone) {
       ++n_nodes;
-      float4 w0 = __ldg(&N[4 * cur]);
-      float4 w1 = __ldg(&N[4 * cur + 1]);
-      float4 w2 = __ldg(&N[4 * cur + 2]);
-      float4 w3 = __ldg(&N[4 * cur + 3]);
-      // child 0
-      float a0 = w0.x * inv.x - oi.x, a1 = w0.y * inv.x - oi.x;
-      float b0 = w0.z * inv.y - oi.y, b1 = w0.w * inv.y - oi.y;
-      float c0 = w2.x * inv.z - oi.z, c1 = w2.y * inv.z - oi.z;
-      float tn0 = fmaxf(fmaxf(fminf(a0, a1), fminf(b0, b1)), fmaxf(fminf(c0, c1), 0.0f));
-      float tf0 = fminf(fminf(fmaxf(a0, a1), fmaxf(b0, b1)), fminf(fmaxf(c0, c1), h.t));
-      // child 1
-      float d0 = w1.x * inv.x - oi.x, d1 = w1.y * inv.x - oi.x;
-      float e0 = w1.z * inv.y - oi.y, e1 = w1.w * inv.y - oi.y;
-      float g0 = w2.z * inv.z - oi.z, g1 = w2.w * inv.z - oi.z;
-      float tn1 = fmaxf(fmaxf(fminf(d0, d1), fminf(e0, e1)), fmaxf(fminf(g0, g1), 0.0f));
-      float tf1 = fminf(fminf(fmaxf(d0, d1), fmaxf(e0, e1)), fminf(fmaxf(g0, g1), h.t));
-      bool hit0 = tn0 <= tf0, hit1 = tn1 <= tf1;
-      int ch0 = __float_as_int(w3.x), ch1 = __float_as_int(w3.y);
+      const float4 w0 = __ldg(&N[4 * cur]);
+      const float4 w1 = __ldg(&N[4 * cur + 1]);
+      const float4 w2 = __ldg(&N[4 * cur + 2]);
+      const float4 w3 = __ldg(&N[4 * cur + 3]);
+      const float a0 = w0.x * inv.x - oi.x, a1 = w0.y * inv.x - oi.x;
+      const float b0 = w0.z * inv.y - oi.y, b1 = w0.w * inv.y - oi.y;
+      const float c0 = w2.x * inv.z - oi.z, c1 = w2.y * inv.z - oi.z;
+      const float tn0 = fmaxf(fmaxf(fminf(a0, a1), fminf(b0, b1)), fmaxf(fminf(c0, c1), 0.0f));
+      const float tf0 = fminf(fminf(fmaxf(a0, a1), fmaxf(b0, b1)), fminf(fmaxf(c0, c1), h.t));
+      const float d0 = w1.x * inv.x - oi.x, d1 = w1.y * inv.x - oi.x;
+      const float e0 = w1.z * inv.y - oi.y, e1 = w1.w * inv.y - oi.y;
+      const float g0 = w2.z * inv.z - oi.z, g1 = w2.w * inv.z - oi.z;
+      const float tn1 = fmaxf(fmaxf(fminf(d0, d1), fminf(e0, e1)), fmaxf(fminf(g0, g1), 0.0f));
+      const float tf1 = fminf(fminf(fmaxf(d0, d1), fmaxf(e0, e1)), fminf(fmaxf(g0, g1), h.t));
+      const bool hit0 = tn0 <= tf0, hit1 = tn1 <= tf1;
+      const int ch0 = __float_as_int(w3.x), ch1 = __float_as_int(w3.y);
       if (hit0 && hit1) {
         int nearc = ch0, farc = ch1;
         if (tn1 < tn0) {
@@ -171,6 +178,7 @@ __device__ Hit trace_binary(const DevScene& S, const Ray& r, float tmax, Counter
         }
         if (sp >= PT_STACK) {
           set_status(S, PT_ERR_BVH);
+          cur = kDone;
           break;
         }
         stack[sp++] = farc;
@@ -180,22 +188,21 @@ __device__ Hit trace_binary(const DevScene& S, const Ray& r, float tmax, Counter
       } else if (hit1) {
         cur = ch1;
       } else {
-        if (sp == 0) break;
-        cur = stack[--sp];
+        cur = sp > 0 ? stack[--sp] : kDone;
       }
-    } else {
-      int leaf = ~cur;
-      int first = leaf >> 3, count = (leaf & 7) + 1;
+    }
+    // ---- leaves
+    while (cur < 0) {
+      const int leaf = ~cur;
+      const int first = leaf >> 3, count = (leaf & 7) + 1;
       n_tris += count;
-      bool done = false;
-      for (int i = 0; i < count; ++i) {
-        if (tri_test(S.tri_v, first + i, r, h.t, h.pos, best_orig, h.u, h.v) && ANY) {
-          done = true;
-          break;
-        }
+      bool found = false;
+      for (int i = 0; i < count; ++i) found |= tri_test(S.tri_v, first + i, r, h.t, h.pos, best_orig, h.u, h.v);
+      if (found && any_hit) {
+        cur = kDone;
+        break;
       }
-      if (done || sp == 0) break;
-      cur = stack[--sp];
+      cur = sp > 0 ? stack[--sp] : kDone;
     }
   }
   cnt.add(3, n_nodes);

@@ -81,244 +81,290 @@ __device__ __forceinline__ float3 offset_origin(float3 p, float3 ng, float3 d) {
   return p + ng * (dot3(ng, d) >= 0.0f ? eps : -eps);
 }
 
-// One Monte Carlo sample of pixel (px, py) of camera `ci`.  With GRADPASS the
-// path is a replay: L_total is the radiance pass 0 returned for this very
-// sample, and the derivative terms are scattered into A.grads.
-template <bool ADJ, bool INSTR>
-__device__ __noinline__ float3 trace_path(const LaunchArgs& A, int ci, int px, int py, int si, bool grad_pass,
-                                          float3 L_total, float3 dl, Counters<INSTR>& cnt, uint32_t* hash_out,
-                                          GradSink& sink) {
-  const DevScene& S = A.scene;
-  const DevCamera& cam = A.cams[ci];
+// State of one lane's current path.  The megakernel loop below advances every
+// lane by one path vertex per iteration (closest hit -> shading + light sample +
+// BSDF sample -> shadow ray -> finish), and a lane whose path ended starts its
+// next sample in the same iteration ("path regeneration"), so the warp keeps
+// traversing together instead of waiting for its longest path.
+struct PathState {
   Pcg32 rng;
-  unsigned long long pixel = (unsigned long long)py * (unsigned long long)A.width + (unsigned long long)px;
-  rng.seed(A.seed, ((unsigned long long)ci << 40) | (pixel << 12) | (unsigned long long)si);
-  Fnv fh{2166136261u};
+  float3 ro, rd;      // current ray
+  float3 beta, L, Lrem;
+  float prev_pdf;
+  int depth;
+  bool prev_delta;
+  Fnv fh;
+  // ---- pending vertex (between the shading step and the shadow ray)
+  float3 so, sd;      // shadow ray
+  float stmax;
+  float3 c_nee;       // NEE contribution if unoccluded
+  float3 r_nee_alb, r_bsdf_alb;  // (df/dalbedo)/f per channel (NEE / sampled direction)
+  float3 r_nee_a, r_bsdf_a;      // (df/dalpha)/f per channel
+  float3 w_next;      // throughput factor of the sampled direction
+  float3 no, nd;      // continuation ray
+  float pdf_next;
+  float u6;
+  int lobe;
+  int alb_kind, alb_ref, tex, rough, mtype;
+  bool has_shadow, ok_next, delta_next, has_params;
+};
 
-  float j0 = rng.uniform(), j1 = rng.uniform();
+template <bool INSTR>
+__device__ __forceinline__ void path_start(const LaunchArgs& A, PathState& P, int ci, int px, int py, int si,
+                                           Counters<INSTR>& cnt) {
+  const DevCamera& cam = A.cams[ci];
+  unsigned long long pixel = (unsigned long long)py * (unsigned long long)A.width + (unsigned long long)px;
+  P.rng.seed(A.seed, ((unsigned long long)ci << 40) | (pixel << 12) | (unsigned long long)si);
+  P.fh.h = 2166136261u;
+  float j0 = P.rng.uniform(), j1 = P.rng.uniform();
   float sx = 2.0f * (px + j0) / A.width - 1.0f;
   float sy = 1.0f - 2.0f * (py + j1) / A.height;
-  Ray ray;
-  ray.o = f3(cam.ox, cam.oy, cam.oz);
-  ray.d = normalize3(f3(cam.fx + cam.rx * sx + cam.ux * sy, cam.fy + cam.ry * sx + cam.uy * sy,
-                        cam.fz + cam.rz * sx + cam.uz * sy));
+  P.ro = f3(cam.ox, cam.oy, cam.oz);
+  P.rd = normalize3(f3(cam.fx + cam.rx * sx + cam.ux * sy, cam.fy + cam.ry * sx + cam.uy * sy,
+                       cam.fz + cam.rz * sx + cam.uz * sy));
+  P.beta = f3(1.f, 1.f, 1.f);
+  P.L = f3(0.f, 0.f, 0.f);
+  P.prev_delta = true;
+  P.prev_pdf = 0.0f;
+  P.depth = 1;
   cnt.add(0, 1);
+}
 
+// Shading step after the closest hit.  Returns false if the path ended here.
+template <bool ADJ, bool INSTR>
+__device__ __forceinline__ bool path_shade(const LaunchArgs& A, PathState& P, const Hit& hit, bool grad_pass,
+                                           Counters<INSTR>& cnt) {
+  const DevScene& S = A.scene;
   const bool has_area = S.n_lights > 0;
   const bool has_env = S.env_w > 0;
   const float p_env = has_env ? (has_area ? 0.5f : 1.0f) : 0.0f;
   const float p_area = has_area ? 1.0f - p_env : 0.0f;
-
-  float3 beta = f3(1.f, 1.f, 1.f), L = f3(0.f, 0.f, 0.f);
-  float3 Lrem = L_total;
-  bool prev_delta = true;
-  float prev_pdf = 0.0f;
-  for (int depth = 1;; ++depth) {
-    cnt.add(1, 1);
-    Hit hit = trace_binary<false, INSTR>(S, ray, INFINITY, cnt);
-    if (hit.pos < 0) {
-      fh.add(0xffffffffu);
-      if (has_env) {
-        int ex, ey;
-        env_pixel(S, ray.d, ex, ey);
-        float3 Le = xyz(__ldg(&S.env[ey * S.env_w + ex]));
-        float w = 1.0f;
-        if (!prev_delta && A.nee) {
-          float st = sqrtf(fmaxf(0.0f, 1.0f - ray.d.y * ray.d.y));
-          w = power_heuristic(prev_pdf, p_env * env_pdf_at(S, ex, ey, st));
-        }
-        float3 c = beta * Le * w;
-        L = L + c;
-        Lrem = Lrem - c;
-      }
-      break;
-    }
-    float4 tv0 = __ldg(&S.tri_v[3 * hit.pos]);
-    float4 tv1 = __ldg(&S.tri_v[3 * hit.pos + 1]);
-    float4 tv2 = __ldg(&S.tri_v[3 * hit.pos + 2]);
-    fh.add(__float_as_uint(tv0.w));
-    float4 ta0 = __ldg(&S.tri_a[2 * hit.pos]);
-    float4 ta1 = __ldg(&S.tri_a[2 * hit.pos + 1]);
-    int shape = __float_as_int(ta1.z);
-    const int4* shp = reinterpret_cast<const int4*>(&S.shapes[shape]);
-    int4 sw0 = __ldg(shp);
-    float4 sw1 = __ldg(reinterpret_cast<const float4*>(shp + 1));
-    float3 ng = normalize3(cross3(xyz(tv1), xyz(tv2)));
-    float3 wi_w = -ray.d;
-    float cos_front = dot3(ng, wi_w);
-    if (sw1.w > 0.0f && cos_front > 0.0f) {
-      float4 sw3 = __ldg(reinterpret_cast<const float4*>(shp + 3));
+  P.has_shadow = false;
+  if (hit.pos < 0) {
+    P.fh.add(0xffffffffu);
+    if (has_env) {
+      int ex, ey;
+      env_pixel(S, P.rd, ex, ey);
+      float3 Le = xyz(__ldg(&S.env[ey * S.env_w + ex]));
       float w = 1.0f;
-      if (!prev_delta && A.nee) {
-        float pdf_l = p_area * hit.t * hit.t / (cos_front * S.light_area);
-        w = power_heuristic(prev_pdf, pdf_l);
+      if (!P.prev_delta && A.nee) {
+        float st = sqrtf(fmaxf(0.0f, 1.0f - P.rd.y * P.rd.y));
+        w = power_heuristic(P.prev_pdf, p_env * env_pdf_at(S, ex, ey, st));
       }
-      float3 c = beta * xyz(sw3) * w;
-      L = L + c;
-      Lrem = Lrem - c;
+      float3 c = P.beta * Le * w;
+      P.L = P.L + c;
+      P.Lrem = P.Lrem - c;
     }
-    if (depth >= A.max_depth) break;
-    float u[8];
+    return false;
+  }
+  const float4 tv0 = __ldg(&S.tri_v[3 * hit.pos]);
+  const float4 tv1 = __ldg(&S.tri_v[3 * hit.pos + 1]);
+  const float4 tv2 = __ldg(&S.tri_v[3 * hit.pos + 2]);
+  P.fh.add(__float_as_uint(tv0.w));
+  const float4 ta0 = __ldg(&S.tri_a[2 * hit.pos]);
+  const float4 ta1 = __ldg(&S.tri_a[2 * hit.pos + 1]);
+  const int shape = __float_as_int(ta1.z);
+  const int4* shp = reinterpret_cast<const int4*>(&S.shapes[shape]);
+  const int4 sw0 = __ldg(shp);
+  const float4 sw1 = __ldg(reinterpret_cast<const float4*>(shp + 1));
+  const float3 ng = normalize3(cross3(xyz(tv1), xyz(tv2)));
+  const float3 wi_w = -P.rd;
+  const float cos_front = dot3(ng, wi_w);
+  if (sw1.w > 0.0f && cos_front > 0.0f) {
+    const float4 sw3 = __ldg(reinterpret_cast<const float4*>(shp + 3));
+    float w = 1.0f;
+    if (!P.prev_delta && A.nee) {
+      float pdf_l = p_area * hit.t * hit.t / (cos_front * S.light_area);
+      w = power_heuristic(P.prev_pdf, pdf_l);
+    }
+    float3 c = P.beta * xyz(sw3) * w;
+    P.L = P.L + c;
+    P.Lrem = P.Lrem - c;
+  }
+  if (P.depth >= A.max_depth) return false;
+  float u[8];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) u[k] = rng.uniform();
-    const int type = sw0.x;
-    if (type == PT_BSDF_NONE) break;
+  for (int k = 0; k < 8; ++k) u[k] = P.rng.uniform();
+  const int type = sw0.x;
+  if (type == PT_BSDF_NONE) return false;
 
-    float3 p = ray.o + ray.d * hit.t;
-    float b0 = 1.0f - hit.u - hit.v;
-    float tu = b0 * ta0.x + hit.u * ta0.z + hit.v * ta1.x;
-    float tvv = b0 * ta0.y + hit.u * ta0.w + hit.v * ta1.y;
-    // ---- resolve the material (closure record + differentiable parameters)
-    Material m;
-    m.type = type;
-    m.tex = sw0.y;
-    m.alpha = sw1.x;
-    m.eta = sw1.y;
-    m.wd = sw1.z;
-    m.rough = sw0.w;
-    m.alb_kind = 0;
-    m.alb_ref = 0;
-    m.albedo = f3(0.f, 0.f, 0.f);
-    if (m.rough >= 0) m.alpha = __ldg(&A.params.rough[m.rough]);
-    {
-      float4 sw2 = __ldg(reinterpret_cast<const float4*>(shp + 2));
-      m.f0 = xyz(sw2);
-    }
-    uint32_t texel_word = 0xffffffffu;
-    if (type == PT_BSDF_DIFFUSE || type == PT_BSDF_BLEND) {
-      if (m.tex >= 0) {
-        // nearest lookup (App. B): pos = min(uint(uv * res), res - 1), texel [pos.y, pos.x]
-        int w = A.params.tex_w[m.tex], h = A.params.tex_h[m.tex];
-        int x = min((int)(fmaxf(tu, 0.0f) * (float)w), w - 1);
-        int y = min((int)(fmaxf(tvv, 0.0f) * (float)h), h - 1);
-        int idx = y * w + x;
-        m.albedo = xyz(__ldg(&A.params.tex[m.tex][idx]));
-        m.alb_kind = 2;
-        m.alb_ref = idx;
-        texel_word = (uint32_t)idx;
-        cnt.add(5, 1);
-      } else if (sw0.z >= 0) {
-        const float* a = &A.params.albedo[3 * sw0.z];
-        m.albedo = f3(__ldg(a), __ldg(a + 1), __ldg(a + 2));
-        m.alb_kind = 1;
-        m.alb_ref = sw0.z;
-      }
-    }
-    fh.add(texel_word);
-
-    const bool entering = cos_front > 0.0f;
-    const float3 n_s = entering ? ng : -ng;
-    const Frame fr = make_frame(n_s);
-    const float3 wi = fr.to_local(wi_w);
-    float3 g_alb = f3(0.f, 0.f, 0.f);
-    float g_alpha = 0.0f;
-
-    // ---- next-event estimation (non-delta BSDFs)
-    if (type != PT_BSDF_DIELECTRIC && A.nee && (has_area || has_env)) {
-      const bool pick_env = has_env && (!has_area || u[7] < 0.5f);
-      float3 dir, Le;
-      float pdf_l = 0.0f, dist = INFINITY;
-      bool valid = false;
-      if (pick_env) {
-        int y = cdf_pick(S.env_marg, S.env_h, u[1]);
-        const float* cond = S.env_cond + (size_t)y * (S.env_w + 1);
-        int x = cdf_pick(cond, S.env_w, u[2]);
-        float m0 = __ldg(&S.env_marg[y]), m1 = __ldg(&S.env_marg[y + 1]);
-        float c0 = __ldg(&cond[x]), c1 = __ldg(&cond[x + 1]);
-        float fv = (u[1] - m0) / (m1 - m0);
-        float fu = (u[2] - c0) / (c1 - c0);
-        float theta = PT_PI * (y + fv) / S.env_h, phi = 2.0f * PT_PI * (x + fu) / S.env_w;
-        float st, ct, sp, cp;
-        sincosf(theta, &st, &ct);
-        sincosf(phi, &sp, &cp);
-        dir = f3(st * cp, ct, st * sp);
-        Le = xyz(__ldg(&S.env[y * S.env_w + x]));
-        pdf_l = p_env * env_pdf_at(S, x, y, st);
-        valid = pdf_l > 0.0f;
-        fh.add(0x80000000u | (uint32_t)(y * S.env_w + x));
-      } else {
-        int k = cdf_pick(S.light_cdf, S.n_lights, u[0]);
-        float4 l0 = __ldg(&S.lights[4 * k]);
-        float4 l1 = __ldg(&S.lights[4 * k + 1]);
-        float4 l2 = __ldg(&S.lights[4 * k + 2]);
-        float4 l3 = __ldg(&S.lights[4 * k + 3]);
-        float su = sqrtf(u[1]);
-        float lb0 = 1.0f - su, lb1 = u[2] * su;
-        float3 q = xyz(l0) * lb0 + xyz(l1) * lb1 + xyz(l2) * (1.0f - lb0 - lb1);
-        float3 dv = q - p;
-        dist = sqrtf(dot3(dv, dv));
-        dir = dv * (1.0f / dist);
-        float3 nl = normalize3(cross3(xyz(l1) - xyz(l0), xyz(l2) - xyz(l0)));
-        float cos_l = -dot3(nl, dir);
-        Le = xyz(l3);
-        if (cos_l > 0.0f && dist > 0.0f) {
-          pdf_l = p_area * dist * dist / (cos_l * S.light_area);
-          valid = true;
-        }
-        fh.add(__float_as_uint(l0.w));
-      }
-      const float3 wl = fr.to_local(dir);
-      BsdfEval ev;
-      dispatch_bsdf(A.dispatch, type, [&]<int T>() {
-        if constexpr (T != PT_BSDF_DIELECTRIC) ev = bsdf_eval<T, ADJ>(m, wi, wl);
-      });
-      uint32_t vis = 2;
-      if (valid && wl.z > 0.0f && max3f(ev.f) > 0.0f) {
-        Ray sr;
-        sr.o = offset_origin(p, ng, dir);
-        sr.d = dir;
-        float tmax = pick_env ? INFINITY : dist * (1.0f - 1e-3f);
-        cnt.add(2, 1);
-        Hit sh = trace_binary<true, INSTR>(S, sr, tmax, cnt);
-        bool occ = sh.pos >= 0;
-        vis = occ ? 1u : 0u;
-        if (!occ) {
-          float w = power_heuristic(pdf_l, ev.pdf);
-          float3 scale = Le * (wl.z * w / pdf_l);
-          float3 c = beta * ev.f * scale;
-          L = L + c;
-          if (ADJ && grad_pass) {
-            Lrem = Lrem - c;
-            g_alb = g_alb + ratio_grad(dl, c, ev.df_alb, ev.f);
-            float3 ga = ratio_grad(dl, c, ev.df_alpha, ev.f);
-            g_alpha += ga.x + ga.y + ga.z;
-          }
-        }
-      }
-      fh.add(vis);
-    }
-    // ---- BSDF sampling (detached) and attached value
-    BsdfSample bs;
-    dispatch_bsdf(A.dispatch, type, [&]<int T>() { bs = bsdf_sample<T, ADJ>(m, wi, entering, u[3], u[4], u[5]); });
-    fh.add((uint32_t)bs.lobe);
-    if (bs.delta) fh.add(0xfffffffeu);
-    if (ADJ && grad_pass) {
-      if (bs.ok && !bs.delta) {
-        float3 lr = f3(fmaxf(Lrem.x, 0.f), fmaxf(Lrem.y, 0.f), fmaxf(Lrem.z, 0.f));
-        g_alb = g_alb + ratio_grad(dl, lr, bs.ev.df_alb, bs.ev.f);
-        float3 ga = ratio_grad(dl, lr, bs.ev.df_alpha, bs.ev.f);
-        g_alpha += ga.x + ga.y + ga.z;
-      }
-      if (m.alb_kind != 0 || m.rough >= 0) sink.add<INSTR>(A, m, g_alb, g_alpha, cnt);
-    }
-    if (!bs.ok) break;
-    beta = beta * bs.weight;
-    prev_delta = bs.delta;
-    prev_pdf = bs.pdf;
-    const float3 wo = fr.to_world(bs.wo);
-    ray.o = offset_origin(p, ng, wo);
-    ray.d = wo;
-    // ---- Russian roulette
-    if (A.rr_depth >= 0 && depth >= A.rr_depth) {
-      float q = fminf(max3f(beta), 0.95f);
-      bool cont = u[6] < q;
-      fh.add(cont ? 1u : 0u);
-      if (!cont) break;
-      beta = beta * (1.0f / q);
+  const float3 p = P.ro + P.rd * hit.t;
+  const float b0 = 1.0f - hit.u - hit.v;
+  const float tu = b0 * ta0.x + hit.u * ta0.z + hit.v * ta1.x;
+  const float tvv = b0 * ta0.y + hit.u * ta0.w + hit.v * ta1.y;
+  // ---- material: closure record + differentiable parameters
+  Material m;
+  m.type = type;
+  m.tex = sw0.y;
+  m.alpha = sw1.x;
+  m.eta = sw1.y;
+  m.wd = sw1.z;
+  m.rough = sw0.w;
+  m.alb_kind = 0;
+  m.alb_ref = 0;
+  m.albedo = f3(0.f, 0.f, 0.f);
+  if (m.rough >= 0) m.alpha = __ldg(&A.params.rough[m.rough]);
+  m.f0 = xyz(__ldg(reinterpret_cast<const float4*>(shp + 2)));
+  uint32_t texel_word = 0xffffffffu;
+  if (type == PT_BSDF_DIFFUSE || type == PT_BSDF_BLEND) {
+    if (m.tex >= 0) {
+      // nearest lookup (App. B): pos = min(uint(uv * res), res - 1), texel [pos.y, pos.x]
+      const int w = A.params.tex_w[m.tex], h = A.params.tex_h[m.tex];
+      const int x = min((int)(fmaxf(tu, 0.0f) * (float)w), w - 1);
+      const int y = min((int)(fmaxf(tvv, 0.0f) * (float)h), h - 1);
+      const int idx = y * w + x;
+      m.albedo = xyz(__ldg(&A.params.tex[m.tex][idx]));
+      m.alb_kind = 2;
+      m.alb_ref = idx;
+      texel_word = (uint32_t)idx;
+      cnt.add(5, 1);
+    } else if (sw0.z >= 0) {
+      const float* a = &A.params.albedo[3 * sw0.z];
+      m.albedo = f3(__ldg(a), __ldg(a + 1), __ldg(a + 2));
+      m.alb_kind = 1;
+      m.alb_ref = sw0.z;
     }
   }
-  if (hash_out) *hash_out = fh.h;
-  return L;
+  P.fh.add(texel_word);
+
+  const bool entering = cos_front > 0.0f;
+  const float3 n_s = entering ? ng : -ng;
+  const Frame fr = make_frame(n_s);
+  const float3 wi = fr.to_local(wi_w);
+  P.c_nee = f3(0.f, 0.f, 0.f);
+  P.r_nee_alb = P.r_nee_a = P.r_bsdf_alb = P.r_bsdf_a = f3(0.f, 0.f, 0.f);
+
+  // ---- next-event estimation: light sample + BSDF value toward it
+  if (type != PT_BSDF_DIELECTRIC && A.nee && (has_area || has_env)) {
+    const bool pick_env = has_env && (!has_area || u[7] < 0.5f);
+    float3 dir, Le;
+    float pdf_l = 0.0f, dist = INFINITY;
+    bool valid = false;
+    if (pick_env) {
+      const int y = cdf_pick(S.env_marg, S.env_h, u[1]);
+      const float* cond = S.env_cond + (size_t)y * (S.env_w + 1);
+      const int x = cdf_pick(cond, S.env_w, u[2]);
+      const float m0 = __ldg(&S.env_marg[y]), m1 = __ldg(&S.env_marg[y + 1]);
+      const float c0 = __ldg(&cond[x]), c1 = __ldg(&cond[x + 1]);
+      const float fv = (u[1] - m0) / (m1 - m0);
+      const float fu = (u[2] - c0) / (c1 - c0);
+      const float theta = PT_PI * (y + fv) / S.env_h, phi = 2.0f * PT_PI * (x + fu) / S.env_w;
+      float st, ct, sp, cp;
+      sincosf(theta, &st, &ct);
+      sincosf(phi, &sp, &cp);
+      dir = f3(st * cp, ct, st * sp);
+      Le = xyz(__ldg(&S.env[y * S.env_w + x]));
+      pdf_l = p_env * env_pdf_at(S, x, y, st);
+      valid = pdf_l > 0.0f;
+      P.fh.add(0x80000000u | (uint32_t)(y * S.env_w + x));
+    } else {
+      const int k = cdf_pick(S.light_cdf, S.n_lights, u[0]);
+      const float4 l0 = __ldg(&S.lights[4 * k]);
+      const float4 l1 = __ldg(&S.lights[4 * k + 1]);
+      const float4 l2 = __ldg(&S.lights[4 * k + 2]);
+      const float4 l3 = __ldg(&S.lights[4 * k + 3]);
+      const float su = sqrtf(u[1]);
+      const float lb0 = 1.0f - su, lb1 = u[2] * su;
+      const float3 q = xyz(l0) * lb0 + xyz(l1) * lb1 + xyz(l2) * (1.0f - lb0 - lb1);
+      const float3 dv = q - p;
+      dist = sqrtf(dot3(dv, dv));
+      dir = dv * (1.0f / dist);
+      const float3 nl = normalize3(cross3(xyz(l1) - xyz(l0), xyz(l2) - xyz(l0)));
+      const float cos_l = -dot3(nl, dir);
+      Le = xyz(l3);
+      if (cos_l > 0.0f && dist > 0.0f) {
+        pdf_l = p_area * dist * dist / (cos_l * S.light_area);
+        valid = true;
+      }
+      P.fh.add(__float_as_uint(l0.w));
+    }
+    const float3 wl = fr.to_local(dir);
+    BsdfEval ev;
+    dispatch_bsdf(A.dispatch, type, [&]<int T>() {
+      if constexpr (T != PT_BSDF_DIELECTRIC) ev = bsdf_eval<T, ADJ>(m, wi, wl);
+    });
+    if (valid && wl.z > 0.0f && max3f(ev.f) > 0.0f) {
+      P.has_shadow = true;
+      P.so = offset_origin(p, ng, dir);
+      P.sd = dir;
+      P.stmax = pick_env ? INFINITY : dist * (1.0f - 1e-3f);
+      const float w = power_heuristic(pdf_l, ev.pdf);
+      P.c_nee = P.beta * ev.f * (Le * (wl.z * w / pdf_l));
+      if (ADJ && grad_pass) {
+        P.r_nee_alb = ratio_grad(f3(1.f, 1.f, 1.f), f3(1.f, 1.f, 1.f), ev.df_alb, ev.f);
+        P.r_nee_a = ratio_grad(f3(1.f, 1.f, 1.f), f3(1.f, 1.f, 1.f), ev.df_alpha, ev.f);
+      }
+    }
+  }
+  // ---- BSDF sampling (detached) with its attached value
+  BsdfSample bs;
+  dispatch_bsdf(A.dispatch, type, [&]<int T>() { bs = bsdf_sample<T, ADJ>(m, wi, entering, u[3], u[4], u[5]); });
+  P.lobe = bs.lobe;
+  P.ok_next = bs.ok;
+  P.delta_next = bs.delta;
+  P.w_next = bs.weight;
+  P.pdf_next = bs.pdf;
+  P.u6 = u[6];
+  if (ADJ && grad_pass && bs.ok && !bs.delta) {
+    P.r_bsdf_alb = ratio_grad(f3(1.f, 1.f, 1.f), f3(1.f, 1.f, 1.f), bs.ev.df_alb, bs.ev.f);
+    P.r_bsdf_a = ratio_grad(f3(1.f, 1.f, 1.f), f3(1.f, 1.f, 1.f), bs.ev.df_alpha, bs.ev.f);
+  }
+  if (bs.ok) {
+    const float3 wo = fr.to_world(bs.wo);
+    P.no = offset_origin(p, ng, wo);
+    P.nd = wo;
+  }
+  P.alb_kind = m.alb_kind;
+  P.alb_ref = m.alb_ref;
+  P.tex = m.tex;
+  P.rough = m.rough;
+  P.mtype = type;
+  P.has_params = m.alb_kind != 0 || m.rough >= 0;
+  return true;
+}
+
+// Finish the vertex once the shadow ray is resolved.  Returns false if the path ended.
+template <bool ADJ, bool INSTR>
+__device__ __forceinline__ bool path_finish(const LaunchArgs& A, PathState& P, bool occluded, bool grad_pass,
+                                            float3 dl, GradSink& sink, Counters<INSTR>& cnt) {
+  if (A.nee && P.mtype != PT_BSDF_DIELECTRIC && (A.scene.n_lights > 0 || A.scene.env_w > 0))
+    P.fh.add(P.has_shadow ? (occluded ? 1u : 0u) : 2u);
+  const bool lit = P.has_shadow && !occluded;
+  if (lit) {
+    P.L = P.L + P.c_nee;
+    P.Lrem = P.Lrem - P.c_nee;
+  }
+  P.fh.add((uint32_t)P.lobe);
+  if (P.delta_next) P.fh.add(0xfffffffeu);
+  if (ADJ && grad_pass && P.has_params) {
+    const float3 cn = lit ? P.c_nee : f3(0.f, 0.f, 0.f);
+    const float3 lr = P.ok_next ? f3(fmaxf(P.Lrem.x, 0.f), fmaxf(P.Lrem.y, 0.f), fmaxf(P.Lrem.z, 0.f))
+                                : f3(0.f, 0.f, 0.f);
+    const float3 g_alb = dl * (cn * P.r_nee_alb + lr * P.r_bsdf_alb);
+    const float3 ga = dl * (cn * P.r_nee_a + lr * P.r_bsdf_a);
+    Material m;
+    m.type = P.mtype;
+    m.alb_kind = P.alb_kind;
+    m.alb_ref = P.alb_ref;
+    m.tex = P.tex;
+    m.rough = P.rough;
+    sink.add<INSTR>(A, m, g_alb, ga.x + ga.y + ga.z, cnt);
+  }
+  if (!P.ok_next) return false;
+  P.beta = P.beta * P.w_next;
+  P.prev_delta = P.delta_next;
+  P.prev_pdf = P.pdf_next;
+  P.ro = P.no;
+  P.rd = P.nd;
+  if (A.rr_depth >= 0 && P.depth >= A.rr_depth) {
+    const float q = fminf(max3f(P.beta), 0.95f);
+    const bool cont = P.u6 < q;
+    P.fh.add(cont ? 1u : 0u);
+    if (!cont) return false;
+    P.beta = P.beta * (1.0f / q);
+  }
+  ++P.depth;
+  return true;
 }
 
 template <bool INSTR>
@@ -354,90 +400,140 @@ __device__ __forceinline__ PixelOf unit_pixel(const LaunchArgs& A, long long uni
   return r;
 }
 
-template <bool INSTR>
-__global__ void __launch_bounds__(256) forward_kernel(const __grid_constant__ LaunchArgs A) {
-  long long unit = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  bool valid = unit < A.n_units;
-  Counters<INSTR> cnt;
-  if constexpr (INSTR) {
-    for (int i = 0; i < 8; ++i) cnt.c[i] = 0;
-  }
-  GradSink sink{nullptr, nullptr};
-  float3 sum = f3(0.f, 0.f, 0.f);
-  PixelOf P{};
-  int lane_in_pix = (int)(unit & (A.lanes_per_pixel - 1));
-  if (valid) {
-    P = unit_pixel(A, unit);
-    for (int s = lane_in_pix; s < A.spp; s += A.lanes_per_pixel) {
-      uint32_t h;
-      float3 L = trace_path<false, INSTR>(A, P.cam, P.px, P.py, s, false, f3(0.f, 0.f, 0.f), f3(0.f, 0.f, 0.f), cnt,
-                                          INSTR ? &h : nullptr, sink);
-      sum = sum + L;
-      if constexpr (INSTR) {
-        long long si = P.pix * A.spp + s;
-        if (A.dbg_L) {
-          A.dbg_L[3 * si] = L.x;
-          A.dbg_L[3 * si + 1] = L.y;
-          A.dbg_L[3 * si + 2] = L.z;
-        }
-        if (A.dbg_hash) A.dbg_hash[si] = h;
-      }
-    }
-  }
-  for (int off = 1; off < A.lanes_per_pixel; off <<= 1) {
-    sum.x += __shfl_xor_sync(0xffffffffu, sum.x, off);
-    sum.y += __shfl_xor_sync(0xffffffffu, sum.y, off);
-    sum.z += __shfl_xor_sync(0xffffffffu, sum.z, off);
-  }
-  if (valid && lane_in_pix == 0) {
-    float inv = 1.0f / (float)A.spp;
-    A.image[3 * P.pix] = sum.x * inv;
-    A.image[3 * P.pix + 1] = sum.y * inv;
-    A.image[3 * P.pix + 2] = sum.z * inv;
-  }
-  flush_counters<INSTR>(A, cnt);
-}
-
-template <bool INSTR>
-__global__ void __launch_bounds__(256) adjoint_kernel(const __grid_constant__ LaunchArgs A) {
-  extern __shared__ float smem[];
+// The megakernel: forward (ADJ = false) or fused PRB adjoint (ADJ = true).
+// Each thread owns the samples s = lane_in_pixel + k * lanes_per_pixel of one
+// pixel; in the adjoint every sample is traced twice (pass 0: radiance L,
+// pass 1: replay with L_rem and gradient scatter) by the same code.
+template <bool ADJ, bool INSTR>
+__device__ __forceinline__ void megakernel(const LaunchArgs& A, float* smem) {
   const DevGrads& G = A.grads;
-  float* s_alb = G.smem_albedo ? smem : nullptr;
-  float* s_rough = G.smem_rough ? smem + (G.smem_albedo ? 3 * G.n_albedo : 0) : nullptr;
-  int n_stage = (G.smem_albedo ? 3 * G.n_albedo : 0) + (G.smem_rough ? G.n_rough : 0);
-  for (int i = threadIdx.x; i < n_stage; i += blockDim.x) smem[i] = 0.0f;
-  __syncthreads();
-
-  long long unit = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  bool valid = unit < A.n_units;
+  float* s_alb = nullptr;
+  float* s_rough = nullptr;
+  int n_stage = 0;
+  if constexpr (ADJ) {
+    s_alb = G.smem_albedo ? smem : nullptr;
+    s_rough = G.smem_rough ? smem + (G.smem_albedo ? 3 * G.n_albedo : 0) : nullptr;
+    n_stage = (G.smem_albedo ? 3 * G.n_albedo : 0) + (G.smem_rough ? G.n_rough : 0);
+    for (int i = threadIdx.x; i < n_stage; i += blockDim.x) smem[i] = 0.0f;
+    __syncthreads();
+  }
+  const long long unit = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool valid = unit < A.n_units;
   Counters<INSTR> cnt;
   if constexpr (INSTR) {
     for (int i = 0; i < 8; ++i) cnt.c[i] = 0;
   }
   GradSink sink{s_alb, s_rough};
+  const int lane_in_pix = (int)(unit & (A.lanes_per_pixel - 1));
+  PixelOf px{};
+  float3 dl = f3(0.f, 0.f, 0.f);
   if (valid) {
-    PixelOf P = unit_pixel(A, unit);
-    int lane_in_pix = (int)(unit & (A.lanes_per_pixel - 1));
-    float inv = 1.0f / (float)A.spp;
-    float3 dl = f3(A.grad_image[3 * P.pix] * inv, A.grad_image[3 * P.pix + 1] * inv, A.grad_image[3 * P.pix + 2] * inv);
-    for (int s = lane_in_pix; s < A.spp; s += A.lanes_per_pixel) {
-      // pass 0: radiance of this sample; pass 1: replay with gradient scatter
-      float3 L = f3(0.f, 0.f, 0.f);
-#pragma unroll 1
-      for (int pass = 0; pass < 2; ++pass) {
-        L = trace_path<true, INSTR>(A, P.cam, P.px, P.py, s, pass == 1, L, dl, cnt, nullptr, sink);
+    px = unit_pixel(A, unit);
+    if constexpr (ADJ) {
+      const float inv = 1.0f / (float)A.spp;
+      dl = f3(A.grad_image[3 * px.pix] * inv, A.grad_image[3 * px.pix + 1] * inv, A.grad_image[3 * px.pix + 2] * inv);
+    }
+  }
+  float3 pix_sum = f3(0.f, 0.f, 0.f);
+  float3 L_pass0 = f3(0.f, 0.f, 0.f);
+  int next_s = lane_in_pix;
+  int pass = 0;
+  bool has_path = false;
+  bool want_shadow = false;  // the lane's next traversal is its pending shadow ray
+  PathState P;
+  for (;;) {
+    if (!has_path && valid && next_s < A.spp) {
+      // one call site for both passes: the replay starts from identical code
+      path_start<INSTR>(A, P, px.cam, px.px, px.py, next_s, cnt);
+      P.Lrem = L_pass0;
+      has_path = true;
+      want_shadow = false;
+    }
+    if (!__any_sync(0xffffffffu, has_path)) break;
+    if (has_path) {
+      // one traversal per lane per iteration: its path ray or its shadow ray
+      cnt.add(want_shadow ? 2 : 1, 1);
+      const Hit hit = trace_binary<INSTR>(A.scene, want_shadow ? P.so : P.ro, want_shadow ? P.sd : P.rd,
+                                          want_shadow ? P.stmax : INFINITY, want_shadow, cnt);
+      const bool grad_pass = ADJ && pass == 1;
+      bool alive = true, finish = true, occ = false;
+      if (!want_shadow) {
+        alive = path_shade<ADJ, INSTR>(A, P, hit, grad_pass, cnt);
+        finish = alive && !P.has_shadow;
+        want_shadow = alive && P.has_shadow;
+      } else {
+        occ = hit.pos >= 0;
+        want_shadow = false;
+      }
+      if (finish) alive = path_finish<ADJ, INSTR>(A, P, occ, grad_pass, dl, sink, cnt);
+      if (!alive) {
+        has_path = false;
+        if (ADJ && pass == 0) {
+          L_pass0 = P.L;  // replay the same sample next: L_rem starts from its radiance
+          pass = 1;
+        } else {
+          pix_sum = pix_sum + P.L;
+          if constexpr (INSTR && !ADJ) {
+            const long long si = px.pix * A.spp + next_s;
+            if (A.dbg_L) {
+              A.dbg_L[3 * si] = P.L.x;
+              A.dbg_L[3 * si + 1] = P.L.y;
+              A.dbg_L[3 * si + 2] = P.L.z;
+            }
+            if (A.dbg_hash) A.dbg_hash[si] = P.fh.h;
+          }
+          next_s += A.lanes_per_pixel;
+          pass = 0;
+          L_pass0 = f3(0.f, 0.f, 0.f);
+        }
       }
     }
   }
-  __syncthreads();
-  for (int i = threadIdx.x; i < n_stage; i += blockDim.x) {
-    float v = smem[i];
-    if (v != 0.0f) {
-      if (G.smem_albedo && i < 3 * G.n_albedo) atomicAdd(&G.albedo[i], v);
-      else atomicAdd(&G.rough[i - (G.smem_albedo ? 3 * G.n_albedo : 0)], v);
+  if constexpr (!ADJ) {
+    for (int off = 1; off < A.lanes_per_pixel; off <<= 1) {
+      pix_sum.x += __shfl_xor_sync(0xffffffffu, pix_sum.x, off);
+      pix_sum.y += __shfl_xor_sync(0xffffffffu, pix_sum.y, off);
+      pix_sum.z += __shfl_xor_sync(0xffffffffu, pix_sum.z, off);
+    }
+    if (valid && lane_in_pix == 0) {
+      const float inv = 1.0f / (float)A.spp;
+      A.image[3 * px.pix] = pix_sum.x * inv;
+      A.image[3 * px.pix + 1] = pix_sum.y * inv;
+      A.image[3 * px.pix + 2] = pix_sum.z * inv;
+    }
+  } else {
+    __syncthreads();
+    for (int i = threadIdx.x; i < n_stage; i += blockDim.x) {
+      const float v = smem[i];
+      if (v != 0.0f) {
+        if (G.smem_albedo && i < 3 * G.n_albedo) atomicAdd(&G.albedo[i], v);
+        else atomicAdd(&G.rough[i - (G.smem_albedo ? 3 * G.n_albedo : 0)], v);
+      }
     }
   }
   flush_counters<INSTR>(A, cnt);
+}
+
+// Minimum resident CTAs of 256 threads per SM requested from ptxas (register cap).
+// Two CTAs of 256 threads per SM cap both kernels at 128 registers; measured on
+// the 196k-triangle sphere workload this is faster than uncapped (the adjoint
+// would otherwise take ~190 registers and run at half the occupancy).
+#ifndef PT_FWD_MIN_BLOCKS
+#define PT_FWD_MIN_BLOCKS 2
+#endif
+#ifndef PT_ADJ_MIN_BLOCKS
+#define PT_ADJ_MIN_BLOCKS 2
+#endif
+
+template <bool INSTR>
+__global__ void __launch_bounds__(256, PT_FWD_MIN_BLOCKS) forward_kernel(const __grid_constant__ LaunchArgs A) {
+  megakernel<false, INSTR>(A, nullptr);
+}
+
+template <bool INSTR>
+__global__ void __launch_bounds__(256, PT_ADJ_MIN_BLOCKS) adjoint_kernel(const __grid_constant__ LaunchArgs A) {
+  extern __shared__ float smem[];
+  megakernel<true, INSTR>(A, smem);
 }
 
 }  // namespace ptgb
@@ -488,10 +584,13 @@ int fill_launch(pt_scene* s, const pt_render_desc* r, const pt_params* p, Launch
   A.crop_h = ch;
   int lp = r->lanes_per_pixel;
   if (lp <= 0) {
-    // auto: spread samples over lanes until there are ~8 waves of 152 SMs x 2048 threads
+    // auto: 8 lanes per pixel (measured best on the sphere workload: coherent
+    // primary rays within a warp, several samples per lane for regeneration),
+    // more if the image is too small to fill ~4 waves of 152 SMs x 512 threads
     long long pixels = (long long)r->n_cams * cw * ch;
     lp = 1;
-    while (lp < 32 && lp < r->spp && pixels * lp < 152ll * 2048 * 8) lp <<= 1;
+    while (lp < 8 && lp < r->spp) lp <<= 1;
+    while (lp < 32 && lp < r->spp && pixels * lp < 152ll * 512 * 4) lp <<= 1;
   }
   if (lp < 1 || lp > 32 || (lp & (lp - 1))) return PT_ERR_ARG;
   A.lanes_per_pixel = lp;
