@@ -32,7 +32,9 @@ METRIC = "Mrays/s fwd+adjoint on 1 GB300 vs roofline; equal-time MSE, cache vs p
 WORKLOAD = dict(workload="spheres32x5120 + ground 128^2 (196,608 tris), 1024x1024, 64 spp, depth 8, RR from 3, "
                          "forward + PRB adjoint (texture 1024^2 RGBA + roughness gradients)",
                 width=1024, height=1024, spp=64, max_depth=8, rr_depth=3)
-FLOPS_PER_NODE = 44     # binary node: two child slab tests (12 FMA = 24 flops, 10 min/max, 2 compares, ordering)
+FLOPS_PER_NODE = {"binary": 44,   # two child slab tests: 12 FMA (24 flops), 10 min/max, 2 compares, ordering
+                  "wide": 140}    # eight child slab tests: 48 FMA (96 flops), 40 min/max, 8 compares (per-node
+                                  # decode: 3 scale + 3 offset products excluded)
 FLOPS_PER_TRI = 45      # Moller-Trumbore: 2 cross, 4 dot, 1 div, 4 mul, 3 sub (FMA = 2 flops)
 
 
@@ -47,6 +49,7 @@ def parse():
     ap.add_argument("--lanes", type=int, default=0)
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--tex-aggregate", type=int, default=0)
+    ap.add_argument("--bvh", default="wide", choices=["wide", "binary"])
     ap.add_argument("--small", action="store_true",
                     help="profiling case: same scene and step at 256x256, 64 spp (not a bench line)")
     return ap.parse_args()
@@ -186,7 +189,8 @@ def run_ours(args):
     abi.load()
 
     sc, tgt_tex = make_workload(small=args.small)
-    ds = DeviceScene(sc, device=dev)
+    layout = abi.PT_BVH_WIDE if args.bvh == "wide" else abi.PT_BVH_BINARY
+    ds = DeviceScene(sc, layout=layout, device=dev)
     seed_fwd, seed_bwd = 1000 + 2 * rank, 1001 + 2 * rank
     st_f = settings(args, seed_fwd)
     # fixed target image (rendered once) -> dLoss/dImage for the adjoint
@@ -225,8 +229,9 @@ def run_ours(args):
     rays_f = int(cf[1] + cf[2])
     rays_b = int(cb[1] + cb[2])
     rays_step = rays_f + rays_b
-    flops_f = FLOPS_PER_NODE * int(cf[3]) + FLOPS_PER_TRI * int(cf[4])
-    flops_b = FLOPS_PER_NODE * int(cb[3]) + FLOPS_PER_TRI * int(cb[4])
+    fpn = FLOPS_PER_NODE[args.bvh]
+    flops_f = fpn * int(cf[3]) + FLOPS_PER_TRI * int(cf[4])
+    flops_b = fpn * int(cb[3]) + FLOPS_PER_TRI * int(cb[4])
 
     for _ in range(args.warmup):
         step()
@@ -315,7 +320,7 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {**WORKLOAD, "l2": "flushed between timed steps (256 MB write)", "dispatch": args.dispatch,
-                   "bvh": "binary SAH", "bvh_nodes": info["n_nodes"], "rays_per_step": rays_step,
+                   "bvh": f"{args.bvh} SAH", "bvh_nodes": info["n_nodes"], "rays_per_step": rays_step,
                    "rays_fwd": rays_f, "rays_adj": rays_b, "fwd_ms": round(fwd_avg, 3),
                    "adj_ms": round(adj_avg, 3), "fwd_mrays_s": round(rays_f / fwd_avg / 1e3, 1),
                    "adj_mrays_s": round(rays_b / adj_avg / 1e3, 1),
@@ -325,7 +330,7 @@ def run_ours(args):
         "roofline": {"bound": "alu", "kernel": dom, "achieved": round(achieved, 3),
                      "peak": round(peak_tflops, 2), "unit": "TFLOP/s", "frac": round(achieved / peak_tflops, 4),
                      "traffic": None,
-                     "work": f"{FLOPS_PER_NODE}/node visit + {FLOPS_PER_TRI}/triangle test (counted launch)",
+                     "work": f"{FLOPS_PER_NODE[args.bvh]}/node visit + {FLOPS_PER_TRI}/triangle test (counted launch)",
                      "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 x median SM clock {mhz} MHz"},
         "cpu_baseline": cpu,
         "e2e": {"value": round(rays_step / (e2e_ms / 1e3) / 1e6, 2), "unit": "Mrays/s", "h2d_bytes_per_step": h2d,

@@ -9,6 +9,7 @@
 #include "bvh_build.h"
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstring>
 #include <limits>
@@ -233,6 +234,170 @@ void layout_binary(const BuildTree& t, std::vector<float>& words) {
   for (size_t g = 0; g < inner.size(); ++g) {
     const BuildNode& n = t.nodes[inner[g]];
     put(&words[g * 16], n.left, n.right, child_ref(n.left), child_ref(n.right));
+  }
+}
+
+namespace {
+
+// Children of one 8-wide node: collapse the binary tree greedily by opening the
+// inner child with the largest surface area while at most 8 children result.
+void collapse_children(const BuildTree& t, int b, std::vector<int>& out) {
+  out.clear();
+  const BuildNode& n = t.nodes[b];
+  if (n.left < 0) {  // a leaf as the whole (root) node
+    out.push_back(b);
+    return;
+  }
+  out.push_back(n.left);
+  out.push_back(n.right);
+  while (out.size() < 8) {
+    int best = -1;
+    double best_area = -1.0;
+    for (size_t i = 0; i < out.size(); ++i) {
+      const BuildNode& c = t.nodes[out[i]];
+      if (c.left < 0) continue;
+      Box bx;
+      std::memcpy(bx.lo, c.lo, sizeof bx.lo);
+      std::memcpy(bx.hi, c.hi, sizeof bx.hi);
+      double a = bx.area();
+      if (a > best_area) {
+        best_area = a;
+        best = (int)i;
+      }
+    }
+    if (best < 0) break;
+    int c = out[best];
+    out[best] = t.nodes[c].left;
+    out.push_back(t.nodes[c].right);
+  }
+}
+
+uint32_t pack4(const uint8_t* b) {
+  return (uint32_t)b[0] | ((uint32_t)b[1] << 8) | ((uint32_t)b[2] << 16) | ((uint32_t)b[3] << 24);
+}
+
+}  // namespace
+
+void layout_wide(const BuildTree& t, std::vector<uint32_t>& words, std::vector<int>& order_out, int max_leaf) {
+  (void)max_leaf;
+  const float ap = scene_abs_pad(t);
+  struct Item {
+    int b, w;
+  };
+  std::vector<Item> queue{{0, 0}};
+  size_t head = 0;
+  int n_wide = 1;
+  words.assign(20, 0u);
+  order_out.clear();
+  std::vector<int> kids;
+  while (head < queue.size()) {
+    Item it = queue[head++];
+    collapse_children(t, it.b, kids);
+    // node box = union of the (padded) child boxes
+    float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    std::vector<std::array<float, 6>> cb(kids.size());
+    for (size_t i = 0; i < kids.size(); ++i) {
+      const BuildNode& c = t.nodes[kids[i]];
+      for (int k = 0; k < 3; ++k) {
+        cb[i][k] = pad_lo(c.lo[k], ap);
+        cb[i][3 + k] = pad_hi(c.hi[k], ap);
+        lo[k] = std::min(lo[k], cb[i][k]);
+        hi[k] = std::max(hi[k], cb[i][3 + k]);
+      }
+    }
+    // slot assignment: slot bit k set = child centroid on the negative side of axis k
+    float ctr[3] = {0.5f * (lo[0] + hi[0]), 0.5f * (lo[1] + hi[1]), 0.5f * (lo[2] + hi[2])};
+    int slot_of[8];
+    bool used[8] = {false, false, false, false, false, false, false, false};
+    std::vector<bool> done(kids.size(), false);
+    for (size_t round = 0; round < kids.size(); ++round) {
+      double best = -INFINITY;
+      int bc = -1, bs = -1;
+      for (size_t i = 0; i < kids.size(); ++i) {
+        if (done[i]) continue;
+        double off[3];
+        for (int k = 0; k < 3; ++k) off[k] = 0.5 * ((double)cb[i][k] + cb[i][3 + k]) - ctr[k];
+        for (int sl = 0; sl < 8; ++sl) {
+          if (used[sl]) continue;
+          double score = 0.0;
+          for (int k = 0; k < 3; ++k) score += ((sl >> k) & 1) ? -off[k] : off[k];
+          if (score > best) {
+            best = score;
+            bc = (int)i;
+            bs = sl;
+          }
+        }
+      }
+      done[bc] = true;
+      used[bs] = true;
+      slot_of[bc] = bs;
+    }
+    int slot_child[8];
+    for (int sl = 0; sl < 8; ++sl) slot_child[sl] = -1;
+    for (size_t i = 0; i < kids.size(); ++i) slot_child[slot_of[i]] = (int)i;
+    // quantisation frame: power-of-two step per axis, 8-bit coordinates
+    int ebits[3];
+    float scale[3];
+    for (int k = 0; k < 3; ++k) {
+      float ext = std::max(hi[k] - lo[k], 1e-30f);
+      int e = (int)std::ceil(std::log2(ext / 254.0f));
+      e = std::min(std::max(e, -126), 127);
+      ebits[k] = e + 127;
+      scale[k] = std::ldexp(1.0f, e);
+    }
+    uint8_t meta[8] = {0}, qlo[3][8] = {{0}}, qhi[3][8] = {{0}};
+    uint8_t imask = 0;
+    uint32_t child_base = (uint32_t)n_wide;
+    uint32_t tri_base = (uint32_t)order_out.size();
+    int inner_rank = 0;
+    for (int sl = 0; sl < 8; ++sl) {
+      int i = slot_child[sl];
+      if (i < 0) continue;
+      const BuildNode& c = t.nodes[kids[i]];
+      for (int k = 0; k < 3; ++k) {
+        int q0 = (int)std::floor((cb[i][k] - lo[k]) / scale[k]);
+        int q1 = (int)std::ceil((cb[i][3 + k] - lo[k]) / scale[k]);
+        q0 = std::min(std::max(q0, 0), 255);
+        q1 = std::min(std::max(q1, 0), 255);
+        while (q0 > 0 && lo[k] + (float)q0 * scale[k] > cb[i][k]) --q0;
+        while (q1 < 255 && lo[k] + (float)q1 * scale[k] < cb[i][3 + k]) ++q1;
+        qlo[k][sl] = (uint8_t)q0;
+        qhi[k][sl] = (uint8_t)q1;
+      }
+      if (c.left >= 0) {
+        imask |= (uint8_t)(1u << sl);
+        meta[sl] = (uint8_t)(0x20 | sl);  // non-zero marker; the child index comes from imask ranks
+        queue.push_back({kids[i], (int)child_base + inner_rank});
+        ++inner_rank;
+      } else {
+        int off = (int)(order_out.size() - tri_base);
+        for (int k = 0; k < c.count; ++k) order_out.push_back(t.order[c.first + k]);
+        meta[sl] = (uint8_t)((c.count << 5) | off);
+      }
+    }
+    n_wide += inner_rank;
+    words.resize((size_t)n_wide * 20, 0u);
+    uint32_t* w = &words[(size_t)it.w * 20];
+    std::memcpy(&w[0], &lo[0], 4);
+    std::memcpy(&w[1], &lo[1], 4);
+    std::memcpy(&w[2], &lo[2], 4);
+    w[3] = (uint32_t)ebits[0] | ((uint32_t)ebits[1] << 8) | ((uint32_t)ebits[2] << 16) | ((uint32_t)imask << 24);
+    w[4] = child_base;
+    w[5] = tri_base;
+    w[6] = pack4(meta);
+    w[7] = pack4(meta + 4);
+    w[8] = pack4(qlo[0]);
+    w[9] = pack4(qlo[0] + 4);
+    w[10] = pack4(qlo[1]);
+    w[11] = pack4(qlo[1] + 4);
+    w[12] = pack4(qlo[2]);
+    w[13] = pack4(qlo[2] + 4);
+    w[14] = pack4(qhi[0]);
+    w[15] = pack4(qhi[0] + 4);
+    w[16] = pack4(qhi[1]);
+    w[17] = pack4(qhi[1] + 4);
+    w[18] = pack4(qhi[2]);
+    w[19] = pack4(qhi[2] + 4);
   }
 }
 

@@ -210,6 +210,113 @@ __device__ __forceinline__ Hit trace_binary(const DevScene& S, float3 ro, float3
   return h;
 }
 
+// Closest hit / any hit on the 8-wide compressed BVH (80-byte nodes: origin,
+// per-axis power-of-two steps, inner-child mask, child and triangle bases, and
+// 8-bit child box planes; see bvh_build.h).  Each visited node tests its eight
+// child boxes with one FMA per plane (near/far planes picked once per node from
+// the ray direction), intersects the triangles of hit leaf children at once, and
+// pushes the remaining hit inner children as one (base, mask) group.  Children
+// are visited in the order of the slot octants relative to the ray direction.
+template <bool INSTR>
+__device__ __forceinline__ Hit trace_wide(const DevScene& S, float3 ro, float3 rd, float tmax, bool any_hit,
+                                          Counters<INSTR>& cnt) {
+  Hit h;
+  h.pos = -1;
+  h.t = tmax;
+  h.u = h.v = 0.0f;
+  Ray r;
+  r.o = ro;
+  r.d = rd;
+  uint32_t best_orig = 0xffffffffu;
+  const float3 inv = safe_inv(rd);
+  const uint32_t flip = (rd.x >= 0.0f ? 1u : 0u) | (rd.y >= 0.0f ? 2u : 0u) | (rd.z >= 0.0f ? 4u : 0u);
+  const uint4* __restrict__ N = reinterpret_cast<const uint4*>(S.nodes);
+  uint2 stack[32];
+  int sp = 0;
+  int node = 0;
+  unsigned n_nodes = 0, n_tris = 0;
+  for (;;) {
+    ++n_nodes;
+    const uint4 w0 = __ldg(&N[5 * node]);
+    const uint4 w1 = __ldg(&N[5 * node + 1]);
+    const uint4 w2 = __ldg(&N[5 * node + 2]);
+    const uint4 w3 = __ldg(&N[5 * node + 3]);
+    const uint4 w4 = __ldg(&N[5 * node + 4]);
+    const uint32_t ex = w0.w & 0xffu, ey = (w0.w >> 8) & 0xffu, ez = (w0.w >> 16) & 0xffu;
+    const uint32_t imask = w0.w >> 24;
+    const float ax = __uint_as_float(ex << 23) * inv.x;
+    const float ay = __uint_as_float(ey << 23) * inv.y;
+    const float az = __uint_as_float(ez << 23) * inv.z;
+    const float bx = (__uint_as_float(w0.x) - ro.x) * inv.x;
+    const float by = (__uint_as_float(w0.y) - ro.y) * inv.y;
+    const float bz = (__uint_as_float(w0.z) - ro.z) * inv.z;
+    // near / far plane bytes per axis (lo planes are near for a positive direction)
+    const uint32_t nx0 = rd.x >= 0.0f ? w2.x : w3.z, nx1 = rd.x >= 0.0f ? w2.y : w3.w;
+    const uint32_t fx0 = rd.x >= 0.0f ? w3.z : w2.x, fx1 = rd.x >= 0.0f ? w3.w : w2.y;
+    const uint32_t ny0 = rd.y >= 0.0f ? w2.z : w4.x, ny1 = rd.y >= 0.0f ? w2.w : w4.y;
+    const uint32_t fy0 = rd.y >= 0.0f ? w4.x : w2.z, fy1 = rd.y >= 0.0f ? w4.y : w2.w;
+    const uint32_t nz0 = rd.z >= 0.0f ? w3.x : w4.z, nz1 = rd.z >= 0.0f ? w3.y : w4.w;
+    const uint32_t fz0 = rd.z >= 0.0f ? w4.z : w3.x, fz1 = rd.z >= 0.0f ? w4.w : w3.y;
+    uint32_t inner_hits = 0, leaf_hits = 0;
+#pragma unroll
+    for (int sl = 0; sl < 8; ++sl) {
+      const int sh = 8 * (sl & 3);
+      const uint32_t meta = ((sl < 4 ? w1.z : w1.w) >> sh) & 0xffu;
+      const float qnx = (float)(((sl < 4 ? nx0 : nx1) >> sh) & 0xffu);
+      const float qfx = (float)(((sl < 4 ? fx0 : fx1) >> sh) & 0xffu);
+      const float qny = (float)(((sl < 4 ? ny0 : ny1) >> sh) & 0xffu);
+      const float qfy = (float)(((sl < 4 ? fy0 : fy1) >> sh) & 0xffu);
+      const float qnz = (float)(((sl < 4 ? nz0 : nz1) >> sh) & 0xffu);
+      const float qfz = (float)(((sl < 4 ? fz0 : fz1) >> sh) & 0xffu);
+      const float tn = fmaxf(fmaxf(fmaf(qnx, ax, bx), fmaf(qny, ay, by)), fmaxf(fmaf(qnz, az, bz), 0.0f));
+      const float tf = fminf(fminf(fmaf(qfx, ax, bx), fmaf(qfy, ay, by)), fminf(fmaf(qfz, az, bz), h.t));
+      if (meta != 0u && tn <= tf) {
+        if ((imask >> sl) & 1u) inner_hits |= 1u << (sl ^ flip);
+        else leaf_hits |= 1u << sl;
+      }
+    }
+    // triangles of the hit leaf children
+    bool stop = false;
+    while (leaf_hits) {
+      const int sl = __ffs(leaf_hits) - 1;
+      leaf_hits &= leaf_hits - 1;
+      const uint32_t meta = ((sl < 4 ? w1.z : w1.w) >> (8 * (sl & 3))) & 0xffu;
+      const int count = (int)(meta >> 5), first = (int)w1.y + (int)(meta & 31u);
+      n_tris += count;
+      bool found = false;
+      for (int i = 0; i < count; ++i) found |= tri_test(S.tri_v, first + i, r, h.t, h.pos, best_orig, h.u, h.v);
+      if (found && any_hit) {
+        stop = true;
+        break;
+      }
+    }
+    if (stop) break;
+    // next node: nearest-octant hit child, the rest stays on the stack as one group
+    uint32_t base = w1.x, gmask = imask, hits = inner_hits;
+    if (hits == 0u) {
+      if (sp == 0) break;
+      base = stack[sp - 1].x;
+      gmask = stack[sp - 1].y & 0xffu;
+      hits = stack[sp - 1].y >> 8;
+      --sp;
+    }
+    const int k = __ffs(hits) - 1;
+    hits &= hits - 1;
+    const int sl = k ^ (int)flip;
+    node = (int)base + __popc(gmask & ((1u << sl) - 1u));
+    if (hits) {
+      if (sp >= 32) {
+        set_status(S, PT_ERR_BVH);
+        break;
+      }
+      stack[sp++] = make_uint2(base, gmask | (hits << 8));
+    }
+  }
+  cnt.add(3, n_nodes);
+  cnt.add(4, n_tris);
+  return h;
+}
+
 // ---------------------------------------------------------------- shading frame
 // Orthonormal basis around n (Duff et al. 2017), branch on n.z >= 0 so +0/-0 agree.
 struct Frame {
@@ -435,6 +542,19 @@ __device__ __forceinline__ void dispatch_bsdf(int mode, int type, F&& f) {
 __device__ __forceinline__ int cdf_pick(const float* __restrict__ cdf, int n, float u) {
   // first i with u < cdf[i+1]
   int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    int mid = (lo + hi) >> 1;
+    if (u < __ldg(&cdf[mid + 1])) hi = mid;
+    else lo = mid + 1;
+  }
+  return lo;
+}
+
+// Same rule with a guide table: the search is confined to [guide[g], guide[g+1]].
+__device__ __forceinline__ int cdf_pick_guided(const float* __restrict__ cdf, const int* __restrict__ guide, int G,
+                                               float u) {
+  const int g = min((int)(u * (float)G), G - 1);
+  int lo = __ldg(&guide[g]), hi = __ldg(&guide[g + 1]);
   while (lo < hi) {
     int mid = (lo + hi) >> 1;
     if (u < __ldg(&cdf[mid + 1])) hi = mid;

@@ -37,6 +37,8 @@ struct DevScene {
   // area lights: 4 float4 per light triangle: v0 (w = orig tri id bits), v1, v2, Le
   const float4* lights;
   const float* light_cdf;  // [n_lights + 1], normalised
+  const int* light_guide;  // [light_g + 1]: first index picked for u = g / light_g
+  int light_g;
   int n_lights;
   float light_area;
   // environment map
@@ -44,6 +46,9 @@ struct DevScene {
   const float* env_marg;   // [h + 1]
   const float* env_cond;   // [h][w + 1]
   const float* env_p;      // [h][w] pixel probabilities
+  const int* env_marg_guide;  // [env_gm + 1]
+  const int* env_cond_guide;  // [h][env_gc + 1]
+  int env_gm, env_gc;
   int env_w, env_h;
   int* status;             // device status word (first error wins)
 };
@@ -109,6 +114,9 @@ struct pt_scene {
   void* d_env_marg = nullptr;
   void* d_env_cond = nullptr;
   void* d_env_p = nullptr;
+  void* d_light_guide = nullptr;
+  void* d_env_marg_guide = nullptr;
+  void* d_env_cond_guide = nullptr;
   void* d_status = nullptr;
   pt_scene_info info{};
 };

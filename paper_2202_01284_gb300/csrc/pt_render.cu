@@ -241,9 +241,9 @@ __device__ __forceinline__ bool path_shade(const LaunchArgs& A, PathState& P, co
     float pdf_l = 0.0f, dist = INFINITY;
     bool valid = false;
     if (pick_env) {
-      const int y = cdf_pick(S.env_marg, S.env_h, u[1]);
+      const int y = cdf_pick_guided(S.env_marg, S.env_marg_guide, S.env_gm, u[1]);
       const float* cond = S.env_cond + (size_t)y * (S.env_w + 1);
-      const int x = cdf_pick(cond, S.env_w, u[2]);
+      const int x = cdf_pick_guided(cond, S.env_cond_guide + (size_t)y * (S.env_gc + 1), S.env_gc, u[2]);
       const float m0 = __ldg(&S.env_marg[y]), m1 = __ldg(&S.env_marg[y + 1]);
       const float c0 = __ldg(&cond[x]), c1 = __ldg(&cond[x + 1]);
       const float fv = (u[1] - m0) / (m1 - m0);
@@ -258,7 +258,7 @@ __device__ __forceinline__ bool path_shade(const LaunchArgs& A, PathState& P, co
       valid = pdf_l > 0.0f;
       P.fh.add(0x80000000u | (uint32_t)(y * S.env_w + x));
     } else {
-      const int k = cdf_pick(S.light_cdf, S.n_lights, u[0]);
+      const int k = cdf_pick_guided(S.light_cdf, S.light_guide, S.light_g, u[0]);
       const float4 l0 = __ldg(&S.lights[4 * k]);
       const float4 l1 = __ldg(&S.lights[4 * k + 1]);
       const float4 l2 = __ldg(&S.lights[4 * k + 2]);
@@ -404,7 +404,7 @@ __device__ __forceinline__ PixelOf unit_pixel(const LaunchArgs& A, long long uni
 // Each thread owns the samples s = lane_in_pixel + k * lanes_per_pixel of one
 // pixel; in the adjoint every sample is traced twice (pass 0: radiance L,
 // pass 1: replay with L_rem and gradient scatter) by the same code.
-template <bool ADJ, bool INSTR>
+template <bool ADJ, bool INSTR, int LAYOUT>
 __device__ __forceinline__ void megakernel(const LaunchArgs& A, float* smem) {
   const DevGrads& G = A.grads;
   float* s_alb = nullptr;
@@ -453,8 +453,10 @@ __device__ __forceinline__ void megakernel(const LaunchArgs& A, float* smem) {
     if (has_path) {
       // one traversal per lane per iteration: its path ray or its shadow ray
       cnt.add(want_shadow ? 2 : 1, 1);
-      const Hit hit = trace_binary<INSTR>(A.scene, want_shadow ? P.so : P.ro, want_shadow ? P.sd : P.rd,
-                                          want_shadow ? P.stmax : INFINITY, want_shadow, cnt);
+      const float3 o = want_shadow ? P.so : P.ro, d = want_shadow ? P.sd : P.rd;
+      const float tmax = want_shadow ? P.stmax : INFINITY;
+      const Hit hit = LAYOUT == PT_BVH_WIDE ? trace_wide<INSTR>(A.scene, o, d, tmax, want_shadow, cnt)
+                                            : trace_binary<INSTR>(A.scene, o, d, tmax, want_shadow, cnt);
       const bool grad_pass = ADJ && pass == 1;
       bool alive = true, finish = true, occ = false;
       if (!want_shadow) {
@@ -525,15 +527,15 @@ __device__ __forceinline__ void megakernel(const LaunchArgs& A, float* smem) {
 #define PT_ADJ_MIN_BLOCKS 2
 #endif
 
-template <bool INSTR>
+template <bool INSTR, int LAYOUT>
 __global__ void __launch_bounds__(256, PT_FWD_MIN_BLOCKS) forward_kernel(const __grid_constant__ LaunchArgs A) {
-  megakernel<false, INSTR>(A, nullptr);
+  megakernel<false, INSTR, LAYOUT>(A, nullptr);
 }
 
-template <bool INSTR>
+template <bool INSTR, int LAYOUT>
 __global__ void __launch_bounds__(256, PT_ADJ_MIN_BLOCKS) adjoint_kernel(const __grid_constant__ LaunchArgs A) {
   extern __shared__ float smem[];
-  megakernel<true, INSTR>(A, smem);
+  megakernel<true, INSTR, LAYOUT>(A, smem);
 }
 
 }  // namespace ptgb
@@ -650,10 +652,11 @@ extern "C" int pt_render_forward(pt_scene* s, const pt_render_desc* r, const pt_
   long long grid;
   if ((st = launch_dims(r, A, block, grid)) != PT_OK) return st;
   cudaStream_t cs = (cudaStream_t)stream;
-  if (instrumented(r))
-    forward_kernel<true><<<(unsigned)grid, block, 0, cs>>>(A);
-  else
-    forward_kernel<false><<<(unsigned)grid, block, 0, cs>>>(A);
+  const bool ins = instrumented(r), wide = s->dev.layout == PT_BVH_WIDE;
+  if (ins && wide) forward_kernel<true, PT_BVH_WIDE><<<(unsigned)grid, block, 0, cs>>>(A);
+  else if (ins) forward_kernel<true, PT_BVH_BINARY><<<(unsigned)grid, block, 0, cs>>>(A);
+  else if (wide) forward_kernel<false, PT_BVH_WIDE><<<(unsigned)grid, block, 0, cs>>>(A);
+  else forward_kernel<false, PT_BVH_BINARY><<<(unsigned)grid, block, 0, cs>>>(A);
   return cudaGetLastError() == cudaSuccess ? PT_OK : PT_ERR_CUDA;
 }
 
@@ -681,9 +684,10 @@ extern "C" int pt_render_backward(pt_scene* s, const pt_render_desc* r, const pt
   long long grid;
   if ((st = launch_dims(r, A, block, grid)) != PT_OK) return st;
   cudaStream_t cs = (cudaStream_t)stream;
-  if (instrumented(r))
-    adjoint_kernel<true><<<(unsigned)grid, block, smem, cs>>>(A);
-  else
-    adjoint_kernel<false><<<(unsigned)grid, block, smem, cs>>>(A);
+  const bool ins = instrumented(r), wide = s->dev.layout == PT_BVH_WIDE;
+  if (ins && wide) adjoint_kernel<true, PT_BVH_WIDE><<<(unsigned)grid, block, smem, cs>>>(A);
+  else if (ins) adjoint_kernel<true, PT_BVH_BINARY><<<(unsigned)grid, block, smem, cs>>>(A);
+  else if (wide) adjoint_kernel<false, PT_BVH_WIDE><<<(unsigned)grid, block, smem, cs>>>(A);
+  else adjoint_kernel<false, PT_BVH_BINARY><<<(unsigned)grid, block, smem, cs>>>(A);
   return cudaGetLastError() == cudaSuccess ? PT_OK : PT_ERR_CUDA;
 }

@@ -29,6 +29,24 @@ int upload(void** dst, const T* src, size_t count) {
   return PT_OK;
 }
 
+// Guide table of a normalised CDF (Chen & Asau 1974 style "cutpoints"):
+// guide[g] = the index the inversion rule (first i with u < cdf[i+1]) picks for
+// u = g / G.  The pick for any u in [g/G, (g+1)/G) lies in [guide[g], guide[g+1]],
+// so a binary search in that range returns exactly the full search's answer.
+int guide_size(int n) {
+  int g = 1;
+  while (g < n && g < 4096) g <<= 1;
+  return g;
+}
+void make_guide(const float* cdf, int n, int G, int* guide) {
+  int i = 0;
+  for (int g = 0; g <= G; ++g) {
+    float u = (float)g / (float)G;
+    while (i < n - 1 && !(u < cdf[i + 1])) ++i;
+    guide[g] = i;
+  }
+}
+
 void free_dev(void*& p) {
   if (p) cudaFree(p);
   p = nullptr;
@@ -45,6 +63,9 @@ void scene_free_all(pt_scene* s) {
   free_dev(s->d_env_marg);
   free_dev(s->d_env_cond);
   free_dev(s->d_env_p);
+  free_dev(s->d_light_guide);
+  free_dev(s->d_env_marg_guide);
+  free_dev(s->d_env_cond_guide);
   free_dev(s->d_status);
   std::free(s->h_vertices);
   std::free(s->h_uvs);
@@ -147,6 +168,13 @@ extern "C" int pt_scene_create(const pt_scene_desc* d, pt_scene** out) {
   if (!cdf_f.empty()) cdf_f.back() = 1.0f;
   if (st == PT_OK) st = upload(&s->d_lights, lights.data(), lights.size());
   if (st == PT_OK && !lights.empty()) st = upload(&s->d_light_cdf, cdf_f.data(), cdf_f.size());
+  if (st == PT_OK && !lights.empty()) {
+    int n = (int)(lights.size() / 4), G = guide_size(n);
+    std::vector<int> guide(G + 1);
+    make_guide(cdf_f.data(), n, G, guide.data());
+    st = upload(&s->d_light_guide, guide.data(), guide.size());
+    s->dev.light_g = G;
+  }
   s->dev.n_lights = (int)(lights.size() / 4);
   s->dev.light_area = (float)total_area;
   // environment map: pixel weights luminance x sin(theta_center), marginal + conditional CDFs
@@ -186,7 +214,15 @@ extern "C" int pt_scene_create(const pt_scene_desc* d, pt_scene** out) {
     }
     marg[H] = 1.0f;
     for (size_t i = 0; i < n; ++i) prob[i] = (float)(w[i] / total);
+    int gm = guide_size(H), gc = guide_size(W);
+    std::vector<int> mguide(gm + 1), cguide((size_t)H * (gc + 1));
+    make_guide(marg.data(), H, gm, mguide.data());
+    for (int y = 0; y < H; ++y) make_guide(&cond[(size_t)y * (W + 1)], W, gc, &cguide[(size_t)y * (gc + 1)]);
+    s->dev.env_gm = gm;
+    s->dev.env_gc = gc;
     st = upload(&s->d_env, reinterpret_cast<const float4*>(d->env), n);
+    if (st == PT_OK) st = upload(&s->d_env_marg_guide, mguide.data(), mguide.size());
+    if (st == PT_OK) st = upload(&s->d_env_cond_guide, cguide.data(), cguide.size());
     if (st == PT_OK) st = upload(&s->d_env_marg, marg.data(), marg.size());
     if (st == PT_OK) st = upload(&s->d_env_cond, cond.data(), cond.size());
     if (st == PT_OK) st = upload(&s->d_env_p, prob.data(), prob.size());
@@ -208,6 +244,9 @@ extern "C" int pt_scene_create(const pt_scene_desc* d, pt_scene** out) {
   s->dev.n_shapes = d->n_shapes;
   s->dev.lights = (const float4*)s->d_lights;
   s->dev.light_cdf = (const float*)s->d_light_cdf;
+  s->dev.light_guide = (const int*)s->d_light_guide;
+  s->dev.env_marg_guide = (const int*)s->d_env_marg_guide;
+  s->dev.env_cond_guide = (const int*)s->d_env_cond_guide;
   s->dev.env = (const float4*)s->d_env;
   s->dev.env_marg = (const float*)s->d_env_marg;
   s->dev.env_cond = (const float*)s->d_env_cond;
@@ -243,7 +282,8 @@ extern "C" int pt_bvh_build(pt_scene* s, const pt_bvh_opts* o) {
   if (opts.layout == PT_BVH_BINARY) {
     layout_binary(tree, node_words);
   } else {
-    return PT_ERR_ARG;
+    layout_wide(tree, wide_words, order, max_leaf);
+    if ((int)order.size() != s->n_tris) return PT_ERR_BVH;
   }
   // triangles and attributes in layout order
   std::vector<float4> tv(3 * (size_t)s->n_tris), ta(2 * (size_t)s->n_tris);

@@ -69,11 +69,11 @@ def test_lit_plane_gpu_exact(lib):
 
 
 # ---------------------------------------------------------------- tiny Cornell box (36 tris)
-@pytest.mark.parametrize("dispatch", [0, 1])
-def test_cornell_forward_parity(lib, oracle_mod, dispatch):
+@pytest.mark.parametrize("dispatch,layout", [(0, 0), (1, 0), (0, 1), (1, 1)])
+def test_cornell_forward_parity(lib, oracle_mod, dispatch, layout):
     sc = S.cornell()
     st = _settings(sc, spp=4, max_depth=4, seed=7, dispatch=dispatch)
-    _, img, L, h = _gpu_forward(lib, sc, st)
+    _, img, L, h = _gpu_forward(lib, sc, st, layout=layout)
     ref, refL, refh = _oracle_render(oracle_mod, sc, st, per_sample=True)
     rep = sample_report(L, h, refL, refh, img, ref)
     print("cornell per-sample:", rep)
@@ -176,11 +176,12 @@ def test_autograd_function_matches_backward(lib, oracle_mod):
 
 
 # ---------------------------------------------------------------- textures + roughness (96 shapes)
-def test_cornell96_forward_and_gradients(lib, oracle_mod):
+@pytest.mark.parametrize("layout", [0, 1])
+def test_cornell96_forward_and_gradients(lib, oracle_mod, layout):
     sc = S.cornell96(width=512, height=512)
     crop = (192, 160, 128, 128)
     st = _settings(sc, spp=16, max_depth=6, seed=21, crop=crop)
-    _, img, L, h = _gpu_forward(lib, sc, st)
+    _, img, L, h = _gpu_forward(lib, sc, st, layout=layout)
     ref, refL, refh = _oracle_render(oracle_mod, sc, st, per_sample=True)
     rep = sample_report(L, h, refL, refh, img, ref)
     print("cornell96 per-sample:", rep)
@@ -199,7 +200,7 @@ def test_cornell96_forward_and_gradients(lib, oracle_mod):
     from paper_2202_01284_gb300.render import DeviceScene
     for agg in (0, 1):
         st.tex_aggregate = agg
-        ds = DeviceScene(sc)
+        ds = DeviceScene(sc, layout=layout)
         gt = torch.zeros_like(ds.textures[0])
         gr = torch.zeros_like(ds.roughness)
         ds.backward(st, torch.as_tensor(gi[None], dtype=torch.float32, device="cuda"), g_textures=[gt],
@@ -214,11 +215,12 @@ def test_cornell96_forward_and_gradients(lib, oracle_mod):
 
 
 # ---------------------------------------------------------------- spheres under an environment map
-def test_spheres_forward_parity(lib, oracle_mod):
+@pytest.mark.parametrize("layout", [0, 1])
+def test_spheres_forward_parity(lib, oracle_mod, layout):
     """GGX conductor, dielectric, textured diffuse, env-map importance sampling, roulette."""
     sc = S.spheres(n_spheres=6, level=2, grid=(3, 2), ground_quads=8, tex_res=256, width=64, height=48)
     st = _settings(sc, spp=8, max_depth=8, rr_depth=3, seed=5)
-    _, img, L, h = _gpu_forward(lib, sc, st)
+    _, img, L, h = _gpu_forward(lib, sc, st, layout=layout)
     ref, refL, refh = _oracle_render(oracle_mod, sc, st, per_sample=True)
     rep = sample_report(L, h, refL, refh, img, ref)
     print("spheres per-sample:", rep)
