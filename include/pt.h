@@ -211,6 +211,50 @@ int pt_last_device_status(pt_scene* scene, void* stream, int* out);
 
 const char* pt_status_string(int status);
 
+/* ------------------------------------------------------------------ radiance cache
+ * A small MLP that predicts the radiance reflected at a surface point toward a
+ * direction (Mueller et al. 2021, "Real-time Neural Radiance Caching"); the paper
+ * itself names caches only as an open direction (Sec. 3.2).  Input: raw records
+ * of 10 floats (position[3], unit direction toward the previous vertex[3], shading
+ * normal[3], GGX roughness or 1 for diffuse), encoded in-kernel into 64 features:
+ * position normalised to [box_lo, box_hi] with sin/cos(2^k pi x), k < 6; direction
+ * and normal mapped to [0,1] with k < 2; roughness; three constant ones.  Network:
+ * five 64x64 ReLU layers and a 64x3 linear head, no biases; BF16 weights and
+ * activations, FP32 accumulation (tensor cores).  Loss: relative L2,
+ * sum_c (y_c - t_c)^2 / (y_c^2 + 0.01) (denominator not differentiated), mean over
+ * the batch.  Optimiser: Adam.  Weight layout (FP32, PT_CACHE_N_PARAMS): layer l
+ * (0..4) at l*4096 as [out 64][in 64], then the head [3][64]. */
+#define PT_CACHE_N_PARAMS 20672
+
+typedef struct pt_cache pt_cache;
+
+typedef struct {
+  float box_lo[3], box_hi[3];   /* position-encoding box (scene bounds) */
+  int32_t batch;                /* training batch, multiple of 64 (e.g. 65536) */
+  int32_t max_queries;          /* capacity of cache-terminated samples per render call */
+  int32_t max_records;          /* capacity of training records per pt_cache_train call */
+  int32_t max_paths;            /* capacity of training paths per pt_cache_train call */
+  float lr, beta1, beta2, eps;  /* Adam */
+  const float* init_weights;    /* host [PT_CACHE_N_PARAMS] or NULL (uniform +-sqrt(6/64) from `seed`) */
+  uint64_t seed;
+} pt_cache_desc;
+
+/* Allocate weights, Adam state and all buffers on the current device (synchronous).
+ * Errors: PT_ERR_ARG (batch not a positive multiple of 64, empty box, negative
+ * capacities), PT_ERR_OOM, PT_ERR_CUDA. */
+int pt_cache_create(const pt_cache_desc* desc, pt_cache** out);
+void pt_cache_destroy(pt_cache* cache);
+/* Synchronous copies of the FP32 master weights; set also resets Adam. */
+int pt_cache_get_weights(pt_cache* cache, float* host_out);
+int pt_cache_set_weights(pt_cache* cache, const float* host_in);
+/* rgb[i] = MLP(encode(raw[i])), device pointers raw [n][10], rgb [n][3]; async on stream. */
+int pt_cache_query(pt_cache* cache, const float* raw, float* rgb, int n, void* stream);
+/* `steps` Adam steps on batches taken in order from device records raw [n][10],
+ * target [n][3] (wrapping); async on stream. */
+int pt_cache_train_records(pt_cache* cache, const float* raw, const float* target, int n, int steps, void* stream);
+/* Relative-L2 loss of the last optimisation step (synchronises the stream). */
+int pt_cache_last_loss(pt_cache* cache, void* stream, float* out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -82,12 +82,13 @@ def lib():
             L.oracle_env_pdf.argtypes = [vp, vp]
             L.oracle_env_pdf.restype = dp
             L.oracle_frame.argtypes = [vp, vp, vp]
-            if hasattr(L, "oracle_mlp_forward"):
-                L.oracle_mlp_forward.argtypes = [vp, ip, vp, ip, vp, vp]
-                L.oracle_mlp_loss_grad.argtypes = [vp, ip, vp, vp, ip, vp, vp]
-                L.oracle_mlp_loss_grad.restype = dp
-                L.oracle_mlp_adam.argtypes = [vp, vp, vp, vp, ip, dp, dp, dp, dp, ip]
-                L.oracle_nrc_encode.argtypes = [ip, vp, vp]
+            L.oracle_mlp_n_params.restype = ip
+            L.oracle_mlp_set_rounding.argtypes = [ip]
+            L.oracle_mlp_forward.argtypes = [vp, ip, vp, vp]
+            L.oracle_mlp_loss_grad.argtypes = [vp, ip, vp, vp, vp, vp]
+            L.oracle_mlp_loss_grad.restype = dp
+            L.oracle_mlp_adam.argtypes = [vp, vp, vp, vp, ip, dp, dp, dp, dp, ip]
+            L.oracle_nrc_encode.argtypes = [ip, vp, vp, vp]
             _lib = L
     return _lib
 
@@ -264,3 +265,46 @@ def frame(n):
     t = np.zeros(3)
     lib().oracle_frame(_ptr(np.asarray(n, np.float64)), _ptr(s), _ptr(t))
     return s, t
+
+
+# ---------------------------------------------------------------- radiance-cache MLP
+def mlp_n_params() -> int:
+    return lib().oracle_mlp_n_params()
+
+
+def mlp_set_rounding(on: bool) -> None:
+    """BF16 rounding of weights/activations (on by default; off = plain FP64 network)."""
+    lib().oracle_mlp_set_rounding(int(bool(on)))
+
+
+def nrc_encode(raw: np.ndarray, box_lo, box_hi) -> np.ndarray:
+    raw = np.ascontiguousarray(raw, np.float64).reshape(-1, 10)
+    box = np.ascontiguousarray(list(box_lo) + list(box_hi), np.float64)
+    out = np.zeros((raw.shape[0], 64))
+    lib().oracle_nrc_encode(raw.shape[0], _ptr(raw), _ptr(box), _ptr(out))
+    return out
+
+
+def mlp_forward(W: np.ndarray, enc: np.ndarray) -> np.ndarray:
+    W = np.ascontiguousarray(W, np.float64)
+    enc = np.ascontiguousarray(enc, np.float64).reshape(-1, 64)
+    out = np.zeros((enc.shape[0], 3))
+    lib().oracle_mlp_forward(_ptr(W), enc.shape[0], _ptr(enc), _ptr(out))
+    return out
+
+
+def mlp_loss_grad(W: np.ndarray, enc: np.ndarray, target: np.ndarray):
+    """(loss, grad [n_params], outputs [n,3]) of the relative-L2 loss."""
+    W = np.ascontiguousarray(W, np.float64)
+    enc = np.ascontiguousarray(enc, np.float64).reshape(-1, 64)
+    t = np.ascontiguousarray(target, np.float64).reshape(-1, 3)
+    g = np.zeros(W.shape[0])
+    out = np.zeros((enc.shape[0], 3))
+    loss = lib().oracle_mlp_loss_grad(_ptr(W), enc.shape[0], _ptr(enc), _ptr(t), _ptr(g), _ptr(out))
+    return loss, g, out
+
+
+def mlp_adam(W, grad, m, v, t, lr=5e-3, b1=0.9, b2=0.99, eps=1e-8):
+    """In-place Adam step on FP64 arrays."""
+    lib().oracle_mlp_adam(_ptr(W), _ptr(np.ascontiguousarray(grad, np.float64)), _ptr(m), _ptr(v), t, lr, b1, b2,
+                          eps, W.shape[0])

@@ -87,6 +87,16 @@ class pt_grads(C.Structure):
     _fields_ = [("albedo", C.c_void_p), ("tex", C.c_void_p * PT_MAX_TEX), ("roughness", C.c_void_p)]
 
 
+PT_CACHE_N_PARAMS = 20672
+
+
+class pt_cache_desc(C.Structure):
+    _fields_ = [("box_lo", C.c_float * 3), ("box_hi", C.c_float * 3), ("batch", C.c_int32),
+                ("max_queries", C.c_int32), ("max_records", C.c_int32), ("max_paths", C.c_int32),
+                ("lr", C.c_float), ("beta1", C.c_float), ("beta2", C.c_float), ("eps", C.c_float),
+                ("init_weights", C.c_void_p), ("seed", C.c_uint64)]
+
+
 _lib = None
 _lock = threading.Lock()
 
@@ -102,6 +112,13 @@ SIGNATURES = {
                             C.POINTER(pt_grads), C.c_void_p], C.c_int),
     "pt_last_device_status": ([C.c_void_p, C.c_void_p, C.POINTER(C.c_int)], C.c_int),
     "pt_status_string": ([C.c_int], C.c_char_p),
+    "pt_cache_create": ([C.POINTER(pt_cache_desc), C.POINTER(C.c_void_p)], C.c_int),
+    "pt_cache_destroy": ([C.c_void_p], None),
+    "pt_cache_get_weights": ([C.c_void_p, C.c_void_p], C.c_int),
+    "pt_cache_set_weights": ([C.c_void_p, C.c_void_p], C.c_int),
+    "pt_cache_query": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p], C.c_int),
+    "pt_cache_train_records": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p], C.c_int),
+    "pt_cache_last_loss": ([C.c_void_p, C.c_void_p, C.POINTER(C.c_float)], C.c_int),
 }
 
 
@@ -267,4 +284,55 @@ def pt_render_backward(handle: int, desc: pt_render_desc, params: pt_params, gra
 def pt_last_device_status(handle: int, stream: int = 0) -> int:
     v = C.c_int(0)
     check("pt_last_device_status", load().pt_last_device_status(handle, stream or None, C.byref(v)))
+    return v.value
+
+
+# ------------------------------------------------------------------ radiance cache
+def pt_cache_create(box_lo, box_hi, batch=65536, max_queries=0, max_records=0, max_paths=0, lr=5e-3,
+                    beta1=0.9, beta2=0.99, eps=1e-8, init_weights=None, seed=0) -> int:
+    d = pt_cache_desc()
+    d.box_lo[:] = [float(x) for x in box_lo]
+    d.box_hi[:] = [float(x) for x in box_hi]
+    d.batch, d.max_queries, d.max_records, d.max_paths = batch, max_queries, max_records, max_paths
+    d.lr, d.beta1, d.beta2, d.eps = lr, beta1, beta2, eps
+    w = None
+    if init_weights is not None:
+        w = np.ascontiguousarray(init_weights, np.float32)
+        assert w.size == PT_CACHE_N_PARAMS
+        d.init_weights = w.ctypes.data
+    d.seed = seed
+    h = C.c_void_p()
+    check("pt_cache_create", load().pt_cache_create(C.byref(d), C.byref(h)))
+    return h.value
+
+
+def pt_cache_destroy(handle: int) -> None:
+    if handle:
+        load().pt_cache_destroy(handle)
+
+
+def pt_cache_get_weights(handle: int) -> np.ndarray:
+    w = np.zeros(PT_CACHE_N_PARAMS, np.float32)
+    check("pt_cache_get_weights", load().pt_cache_get_weights(handle, w.ctypes.data))
+    return w
+
+
+def pt_cache_set_weights(handle: int, w) -> None:
+    w = np.ascontiguousarray(w, np.float32)
+    assert w.size == PT_CACHE_N_PARAMS
+    check("pt_cache_set_weights", load().pt_cache_set_weights(handle, w.ctypes.data))
+
+
+def pt_cache_query(handle: int, raw, rgb, n: int, stream: int = 0) -> None:
+    check("pt_cache_query", load().pt_cache_query(handle, _ptr(raw), _ptr(rgb), n, stream or None))
+
+
+def pt_cache_train_records(handle: int, raw, target, n: int, steps: int, stream: int = 0) -> None:
+    check("pt_cache_train_records",
+          load().pt_cache_train_records(handle, _ptr(raw), _ptr(target), n, steps, stream or None))
+
+
+def pt_cache_last_loss(handle: int, stream: int = 0) -> float:
+    v = C.c_float(0)
+    check("pt_cache_last_loss", load().pt_cache_last_loss(handle, stream or None, C.byref(v)))
     return v.value

@@ -584,3 +584,37 @@ def batch_scenes(seed=2022, sizes=("10k", "200k", "2M")) -> List[Scene]:
         else:
             raise ValueError(s)
     return out
+
+
+# ----------------------------------------------------------------------------
+# radiance-cache inputs: initial weights and synthetic records
+# ----------------------------------------------------------------------------
+
+MLP_N_PARAMS = 5 * 64 * 64 + 3 * 64
+
+
+def mlp_init_weights(seed: int = 2022) -> np.ndarray:
+    """Uniform +-sqrt(6/64) initial weights in the flat layout (layer l at l*4096 as
+    [out][in], then the [3][64] head)."""
+    rng = np.random.default_rng(seed)
+    a = math.sqrt(6.0 / 64.0)
+    return rng.uniform(-a, a, size=MLP_N_PARAMS).astype(np.float32)
+
+
+def random_cache_records(n: int, seed: int, box_lo=(-1, 0, -1), box_hi=(1, 2, 1)):
+    """Raw records (position in the box, unit direction, unit normal, roughness) and
+    smooth synthetic RGB targets (a fixed function of the inputs, for training tests)."""
+    rng = np.random.default_rng(seed)
+    lo, hi = np.asarray(box_lo, np.float64), np.asarray(box_hi, np.float64)
+    p = lo + (hi - lo) * rng.random((n, 3))
+    d = rng.normal(size=(n, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    nn = rng.normal(size=(n, 3))
+    nn /= np.linalg.norm(nn, axis=1, keepdims=True)
+    a = rng.uniform(0.1, 1.0, size=(n, 1))
+    raw = np.concatenate([p, d, nn, a], 1).astype(np.float32)
+    x = (p - lo) / (hi - lo)
+    t = np.stack([0.5 + 0.4 * np.sin(3 * x[:, 0] + d[:, 1]),
+                  0.4 + 0.3 * np.cos(2 * x[:, 1] - nn[:, 2]),
+                  0.3 + 0.2 * x[:, 2] * (1 + d[:, 0])], 1)
+    return raw, t.astype(np.float32)

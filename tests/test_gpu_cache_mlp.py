@@ -1,0 +1,105 @@
+"""GPU parity of the radiance-cache MLP kernels (BF16 tensor cores) vs the FP64 oracle."""
+import numpy as np
+import pytest
+
+from paper_2202_01284_gb300 import scenes as S
+
+from parity import cosine
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+BOX = ((-1.0, 0.0, -1.0), (1.0, 2.0, 1.0))
+
+
+@pytest.fixture(scope="module")
+def abi():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2202_01284_gb300 import abi
+    abi.load()
+    return abi
+
+
+def _rel_err(a, b):
+    scale = np.abs(b).mean()
+    return np.abs(a - b) / (np.abs(b) + 0.05 * scale)
+
+
+@pytest.mark.parametrize("n", [1, 17, 5000])
+def test_inference_matches_oracle(abi, oracle_mod, n):
+    """Ragged sizes (1, 17 = one full tile + 1 row, 5000) through the C ABI."""
+    raw, _ = S.random_cache_records(n, 11)
+    W = S.mlp_init_weights(12)
+    h = abi.pt_cache_create(*BOX, batch=64, init_weights=W)
+    try:
+        d_raw = torch.as_tensor(raw, device="cuda")
+        d_out = torch.full((n, 3), float("nan"), device="cuda")
+        abi.pt_cache_query(h, d_raw, d_out, n)
+        torch.cuda.synchronize()
+        got = d_out.cpu().numpy().astype(np.float64)
+    finally:
+        abi.pt_cache_destroy(h)
+    enc = oracle_mod.nrc_encode(raw, *BOX)
+    ref = oracle_mod.mlp_forward(W.astype(np.float64), enc)
+    err = _rel_err(got, ref)
+    print(f"n={n} median rel err {np.median(err):.2e} p99 {np.quantile(err, 0.99):.2e} max {err.max():.2e}")
+    assert np.all(np.isfinite(got))
+    assert np.median(err) < 2e-3
+    assert np.quantile(err, 0.99) < 2e-2
+
+
+def test_gradient_and_loss_match_oracle(abi, oracle_mod):
+    """One optimisation step with beta1 = beta2 = 0, lr = eps = 1e6 turns Adam into
+    w1 = w0 - g * 1e6 / (|g| + 1e6), exposing the kernels' weight gradient."""
+    n = 4096
+    raw, tgt = S.random_cache_records(n, 13)
+    W0 = S.mlp_init_weights(14)
+    h = abi.pt_cache_create(*BOX, batch=n, lr=1e6, beta1=0.0, beta2=0.0, eps=1e6, init_weights=W0)
+    try:
+        d_raw = torch.as_tensor(raw, device="cuda")
+        d_t = torch.as_tensor(tgt, device="cuda")
+        abi.pt_cache_train_records(h, d_raw, d_t, n, 1)
+        loss_gpu = abi.pt_cache_last_loss(h)
+        W1 = abi.pt_cache_get_weights(h)
+    finally:
+        abi.pt_cache_destroy(h)
+    g_gpu = (W0.astype(np.float64) - W1.astype(np.float64))
+    enc = oracle_mod.nrc_encode(raw, *BOX)
+    loss_ref, g_ref, _ = oracle_mod.mlp_loss_grad(W0.astype(np.float64), enc, tgt)
+    g_gpu = g_gpu * (np.abs(g_ref) + 1e6) / 1e6
+    c = cosine(g_gpu, g_ref)
+    print(f"loss gpu {loss_gpu:.6f} oracle {loss_ref:.6f}; gradient cosine {c:.6f}")
+    assert abs(loss_gpu - loss_ref) < 1e-2 * loss_ref
+    assert c > 0.999
+    for l in range(6):
+        sl = slice(l * 4096, (l + 1) * 4096) if l < 5 else slice(5 * 4096, None)
+        assert cosine(g_gpu[sl], g_ref[sl]) > 0.995, l
+
+
+def test_training_converges_like_oracle(abi, oracle_mod):
+    n = 1024
+    raw, tgt = S.random_cache_records(n, 15)
+    W0 = S.mlp_init_weights(16)
+    h = abi.pt_cache_create(*BOX, batch=n, lr=5e-3, init_weights=W0)
+    losses = []
+    try:
+        d_raw = torch.as_tensor(raw, device="cuda")
+        d_t = torch.as_tensor(tgt, device="cuda")
+        for _ in range(40):
+            abi.pt_cache_train_records(h, d_raw, d_t, n, 1)
+            losses.append(abi.pt_cache_last_loss(h))
+    finally:
+        abi.pt_cache_destroy(h)
+    enc = oracle_mod.nrc_encode(raw, *BOX)
+    W = W0.astype(np.float64)
+    m, v = np.zeros_like(W), np.zeros_like(W)
+    ref = []
+    for t in range(1, 41):
+        loss, g, _ = oracle_mod.mlp_loss_grad(W, enc, tgt)
+        ref.append(loss)
+        oracle_mod.mlp_adam(W, g, m, v, t, lr=5e-3)
+    print("gpu", losses[0], losses[-1], "oracle", ref[0], ref[-1])
+    assert abs(losses[0] - ref[0]) < 1e-2 * ref[0]
+    assert losses[-1] < 0.5 * losses[0]
+    assert losses[-1] < 1.5 * ref[-1] + 1e-3
