@@ -94,6 +94,7 @@ typedef struct {
 } pt_scene_desc;
 
 typedef struct pt_scene pt_scene;
+typedef struct pt_cache pt_cache;
 
 /* Copy geometry, shape table and environment map to the device, and build the
  * emitter tables (area-proportional triangle CDF; environment map marginal and
@@ -166,6 +167,14 @@ typedef struct {
   float* dbg_sample_L;        /* [n_cams][rows][cols][spp][3] per-sample radiance */
   uint32_t* dbg_sample_hash;  /* [n_cams][rows][cols][spp] FNV-1a of the path's discrete decisions */
   unsigned long long* counters; /* [PT_N_COUNTERS], accumulated */
+  /* radiance cache (NULL = plain path tracing).  Paths end at the first non-delta
+   * vertex reached by segment >= cache_bounce: emission there is added as usual,
+   * then beta * max(cache(x, w_o, n, alpha), 0) replaces the rest of the path
+   * (the cache predicts reflected radiance).  Needs cache max_queries >=
+   * n_cams * rows * cols * spp.  The backward pass uses the cache radiance as a
+   * detached incident radiance at that vertex. */
+  struct pt_cache* cache;
+  int32_t cache_bounce;         /* >= 1 */
 } pt_render_desc;
 
 /* Differentiable parameters: borrowed device pointers. */
@@ -226,8 +235,6 @@ const char* pt_status_string(int status);
  * (0..4) at l*4096 as [out 64][in 64], then the head [3][64]. */
 #define PT_CACHE_N_PARAMS 20672
 
-typedef struct pt_cache pt_cache;
-
 typedef struct {
   float box_lo[3], box_hi[3];   /* position-encoding box (scene bounds) */
   int32_t batch;                /* training batch, multiple of 64 (e.g. 65536) */
@@ -254,6 +261,20 @@ int pt_cache_query(pt_cache* cache, const float* raw, float* rgb, int n, void* s
 int pt_cache_train_records(pt_cache* cache, const float* raw, const float* target, int n, int steps, void* stream);
 /* Relative-L2 loss of the last optimisation step (synchronises the stream). */
 int pt_cache_last_loss(pt_cache* cache, void* stream, float* out);
+/* Online training step: trace the samples of `desc` as full-length training paths
+ * (desc->cache is ignored), record at every non-delta vertex below max_depth the
+ * raw features and the reflected radiance the rest of the path carried,
+ * (L_path - L_up_to_vertex) / throughput, then run `steps` optimisation steps on
+ * those records.  Needs max_paths >= samples of desc; records beyond max_records
+ * are dropped.  Synchronises the stream once (to read the record count).
+ * *n_records (optional) receives the number of records used. */
+int pt_cache_train(pt_cache* cache, pt_scene* scene, const pt_render_desc* desc, const pt_params* params, int steps,
+                   void* stream, int* n_records);
+/* Synchronous host copy of the records of the last pt_cache_train call (for
+ * inspection): raw [n][10], target [n][3], meta [n][2] = (sample index
+ * pixel * spp + sample, depth of the vertex); any pointer may be NULL.
+ * *n_out = min(cap, records kept). */
+int pt_cache_read_records(pt_cache* cache, int cap, float* raw, float* target, int* meta, int* n_out);
 
 #ifdef __cplusplus
 }

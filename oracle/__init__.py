@@ -82,6 +82,10 @@ def lib():
             L.oracle_env_pdf.argtypes = [vp, vp]
             L.oracle_env_pdf.restype = dp
             L.oracle_frame.argtypes = [vp, vp, vp]
+            L.oracle_render_cached.argtypes = [vp, C.POINTER(RenderIn), vp, vp, ip, vp, ip]
+            L.oracle_grad_dual_cached.argtypes = [vp, C.POINTER(RenderIn), vp, vp, ip, vp, ip, vp, vp, ip]
+            L.oracle_train_records.argtypes = [vp, C.POINTER(RenderIn), ip, vp, vp, vp]
+            L.oracle_train_records.restype = ip
             L.oracle_mlp_n_params.restype = ip
             L.oracle_mlp_set_rounding.argtypes = [ip]
             L.oracle_mlp_forward.argtypes = [vp, ip, vp, vp]
@@ -308,3 +312,33 @@ def mlp_adam(W, grad, m, v, t, lr=5e-3, b1=0.9, b2=0.99, eps=1e-8):
     """In-place Adam step on FP64 arrays."""
     lib().oracle_mlp_adam(_ptr(W), _ptr(np.ascontiguousarray(grad, np.float64)), _ptr(m), _ptr(v), t, lr, b1, b2,
                           eps, W.shape[0])
+
+
+# ---------------------------------------------------------------- cache-terminated rendering
+def render_cached(osc: OracleScene, r: RenderIn, W, box_lo, box_hi, bounce: int, threads=0):
+    h, w = _crop_shape(r)
+    img = np.zeros((h, w, 3))
+    Wd = np.ascontiguousarray(W, np.float64)
+    box = np.ascontiguousarray(list(box_lo) + list(box_hi), np.float64)
+    lib().oracle_render_cached(osc.handle, C.byref(r), _ptr(Wd), _ptr(box), bounce, _ptr(img), threads)
+    return img
+
+
+def grad_dual_cached(osc: OracleScene, r: RenderIn, W, box_lo, box_hi, bounce, grad_image, sel, threads=0):
+    Wd = np.ascontiguousarray(W, np.float64)
+    box = np.ascontiguousarray(list(box_lo) + list(box_hi), np.float64)
+    gi = np.ascontiguousarray(grad_image, dtype=np.float64)
+    s = np.ascontiguousarray(np.asarray(sel, np.int32).reshape(-1, 4))
+    out = np.zeros(s.shape[0])
+    lib().oracle_grad_dual_cached(osc.handle, C.byref(r), _ptr(Wd), _ptr(box), bounce, _ptr(gi), s.shape[0],
+                                  _ptr(s), _ptr(out), threads)
+    return out
+
+
+def train_records(osc: OracleScene, r: RenderIn, cap: int):
+    """(raw [n,10], target [n,3], meta [n,2] = (sample index, depth)) of full-length paths."""
+    raw = np.zeros((cap, 10))
+    tgt = np.zeros((cap, 3))
+    meta = np.zeros((cap, 2), np.int32)
+    n = lib().oracle_train_records(osc.handle, C.byref(r), cap, _ptr(raw), _ptr(tgt), _ptr(meta))
+    return raw[:n], tgt[:n], meta[:n]

@@ -642,9 +642,29 @@ struct VertexInfo {
   V3 wi;        // local incident direction (toward the previous vertex)
 };
 
+// Radiance-cache termination for the oracle: the MLP of mlp.cpp evaluated on
+// the raw features of the termination vertex (same definition as the kernels:
+// paths end at the first non-delta vertex reached by segment >= bounce).
+struct CacheModel {
+  const double* W = nullptr;  // NULL: no cache
+  double box[6];
+  int bounce = 0;
+};
+struct TrainRecord {
+  double raw[10];
+  V3 beta, L_before;
+  int depth;
+};
+
+}  // namespace
+extern "C" void oracle_nrc_encode(int n, const double* raw, const double* box, double* enc_out);
+extern "C" void oracle_mlp_forward(const double* W, int n, const double* enc, double* out);
+namespace {
+
 template <class Acc>
 V3 render_sample(const Scene& s, const Camera& cam, const oracle_render_in& r, int px, int py,
-                 int spp_index, Acc& acc, uint32_t* hash_out) {
+                 int spp_index, Acc& acc, uint32_t* hash_out, const CacheModel* cache = nullptr,
+                 std::vector<TrainRecord>* records = nullptr) {
   // RNG stream of this sample: (camera << 40) | (pixel << 12) | sample
   Pcg32 rng;
   uint64_t pixel = (uint64_t)py * (uint64_t)r.width + (uint64_t)px;
@@ -708,6 +728,30 @@ V3 render_sample(const Scene& s, const Camera& cam, const oracle_render_in& r, i
     VertexInfo vi;
     vi.m = resolve_material(s, s.tri_shape[t], tu, tv);
     dh.add(vi.m.alb_kind == 2 ? (uint32_t)vi.m.texel : 0xffffffffu);
+    if ((cache && cache->W) || records) {
+      if (sh.bsdf != BSDF_DIELECTRIC) {
+        V3 n = cos_front > 0.0 ? ng : -ng;
+        double rough = (sh.bsdf == BSDF_CONDUCTOR || sh.bsdf == BSDF_BLEND) ? vi.m.alpha : 1.0;
+        double raw[10] = {p.x, p.y, p.z, wi_w.x, wi_w.y, wi_w.z, n.x, n.y, n.z, rough};
+        if (records) {
+          TrainRecord rec;
+          std::memcpy(rec.raw, raw, sizeof raw);
+          rec.beta = beta;
+          rec.L_before = L;
+          rec.depth = depth;
+          records->push_back(rec);
+        } else if (depth >= cache->bounce) {
+          double enc[64], y[3];
+          oracle_nrc_encode(1, raw, cache->box, enc);
+          oracle_mlp_forward(cache->W, 1, enc, y);
+          V3 Lc(std::max(y[0], 0.0), std::max(y[1], 0.0), std::max(y[2], 0.0));
+          V3 c = mul(beta, Lc);
+          L = L + c;
+          acc.emission(c, Lc);
+          break;
+        }
+      }
+    }
 
     if (sh.bsdf == BSDF_DIELECTRIC) {
       bool entering = cos_front > 0.0;
@@ -951,6 +995,14 @@ void parallel_rows(int y0, int rows, int n_threads, F fn) {
   for (auto& t : ts) t.join();
 }
 
+CacheModel make_cache(const double* W, const double* box, int bounce) {
+  CacheModel c;
+  c.W = W;
+  if (box) std::memcpy(c.box, box, sizeof c.box);
+  c.bounce = bounce;
+  return c;
+}
+
 void crop_of(const oracle_render_in& r, int& x0, int& y0, int& cw, int& ch) {
   x0 = r.crop_w > 0 ? r.crop_x0 : 0;
   y0 = r.crop_w > 0 ? r.crop_y0 : 0;
@@ -1179,6 +1231,93 @@ int oracle_grad_dual(void* sc, const oracle_render_in* r, const double* grad_ima
   });
   std::memcpy(out, total.data(), n_sel * sizeof(double));
   return 0;
+}
+
+// Cache-terminated render (W: MLP weights [20672], box: lo[3], hi[3]).
+int oracle_render_cached(void* sc, const oracle_render_in* r, const double* W, const double* box, int bounce,
+                         double* image, int n_threads) {
+  const Scene& s = *(Scene*)sc;
+  Camera cam = make_camera(*r);
+  CacheModel cm = make_cache(W, box, bounce);
+  int x0, y0, cw, ch;
+  crop_of(*r, x0, y0, cw, ch);
+  parallel_rows(y0, ch, n_threads, [&](int py) {
+    for (int px = x0; px < x0 + cw; ++px) {
+      size_t pi = (size_t)(py - y0) * cw + (px - x0);
+      V3 sum(0, 0, 0);
+      for (int k = 0; k < r->spp; ++k) {
+        NullAcc acc;
+        sum = sum + render_sample(s, cam, *r, px, py, k, acc, nullptr, &cm);
+      }
+      for (int c = 0; c < 3; ++c) image[pi * 3 + c] = sum[c] / r->spp;
+    }
+  });
+  return 0;
+}
+
+// Albedo gradient (rows [A][3]) of the cache-terminated estimator by forward-mode
+// duals; the cache radiance is a detached incident radiance.
+int oracle_grad_dual_cached(void* sc, const oracle_render_in* r, const double* W, const double* box, int bounce,
+                            const double* grad_image, int n_sel, const int* sel, double* out, int n_threads) {
+  const Scene& s = *(Scene*)sc;
+  Camera cam = make_camera(*r);
+  CacheModel cm = make_cache(W, box, bounce);
+  int x0, y0, cw, ch;
+  crop_of(*r, x0, y0, cw, ch);
+  std::vector<SelParam> params;
+  for (int i = 0; i < n_sel; ++i) params.push_back({sel[i * 4], sel[i * 4 + 1], sel[i * 4 + 2], sel[i * 4 + 3]});
+  std::vector<double> total(n_sel, 0.0);
+  std::mutex mu;
+  parallel_rows(y0, ch, n_threads, [&](int py) {
+    std::vector<double> acc_row(n_sel, 0.0);
+    for (int px = x0; px < x0 + cw; ++px) {
+      size_t pi = (size_t)(py - y0) * cw + (px - x0);
+      for (int k = 0; k < r->spp; ++k) {
+        DualAcc acc;
+        acc.init(&params);
+        render_sample(s, cam, *r, px, py, k, acc, nullptr, &cm);
+        for (int c = 0; c < 3; ++c) {
+          double dl = grad_image[pi * 3 + c] / r->spp;
+          for (int i = 0; i < n_sel; ++i) acc_row[i] += dl * tg(acc.L[c], i);
+        }
+      }
+    }
+    std::lock_guard<std::mutex> lk(mu);
+    for (int i = 0; i < n_sel; ++i) total[i] += acc_row[i];
+  });
+  std::memcpy(out, total.data(), n_sel * sizeof(double));
+  return 0;
+}
+
+// Training records of full-length paths: per non-delta vertex below max_depth,
+// raw features and the target (L_path - L_up_to_vertex) / beta.  Returns the
+// number of records (<= cap); out_raw [cap][10], out_target [cap][3],
+// out_meta [cap][2] = (sample index pixel*spp + s within the crop, depth).
+int oracle_train_records(void* sc, const oracle_render_in* r, int cap, double* out_raw, double* out_target,
+                         int* out_meta) {
+  const Scene& s = *(Scene*)sc;
+  Camera cam = make_camera(*r);
+  int x0, y0, cw, ch;
+  crop_of(*r, x0, y0, cw, ch);
+  int n = 0;
+  for (int py = y0; py < y0 + ch; ++py)
+    for (int px = x0; px < x0 + cw; ++px)
+      for (int k = 0; k < r->spp; ++k) {
+        NullAcc acc;
+        std::vector<TrainRecord> recs;
+        V3 L = render_sample(s, cam, *r, px, py, k, acc, nullptr, nullptr, &recs);
+        long long slot = ((long long)(py - y0) * cw + (px - x0)) * r->spp + k;
+        for (const auto& rc : recs) {
+          if (n >= cap) return n;
+          std::memcpy(out_raw + 10 * (size_t)n, rc.raw, sizeof rc.raw);
+          for (int c = 0; c < 3; ++c)
+            out_target[3 * (size_t)n + c] = rc.beta[c] > 1e-12 ? std::max(L[c] - rc.L_before[c], 0.0) / rc.beta[c] : 0.0;
+          out_meta[2 * n] = (int)slot;
+          out_meta[2 * n + 1] = rc.depth;
+          ++n;
+        }
+      }
+  return n;
 }
 
 // ---------------------------------------------------------------- unit-test hooks

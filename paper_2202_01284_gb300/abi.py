@@ -74,7 +74,8 @@ class pt_render_desc(C.Structure):
                 ("seed", C.c_uint64), ("dispatch", C.c_int32),
                 ("crop_x0", C.c_int32), ("crop_y0", C.c_int32), ("crop_w", C.c_int32), ("crop_h", C.c_int32),
                 ("lanes_per_pixel", C.c_int32), ("block_size", C.c_int32), ("tex_aggregate", C.c_int32),
-                ("dbg_sample_L", C.c_void_p), ("dbg_sample_hash", C.c_void_p), ("counters", C.c_void_p)]
+                ("dbg_sample_L", C.c_void_p), ("dbg_sample_hash", C.c_void_p), ("counters", C.c_void_p),
+                ("cache", C.c_void_p), ("cache_bounce", C.c_int32)]
 
 
 class pt_params(C.Structure):
@@ -119,6 +120,10 @@ SIGNATURES = {
     "pt_cache_query": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p], C.c_int),
     "pt_cache_train_records": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p], C.c_int),
     "pt_cache_last_loss": ([C.c_void_p, C.c_void_p, C.POINTER(C.c_float)], C.c_int),
+    "pt_cache_train": ([C.c_void_p, C.c_void_p, C.POINTER(pt_render_desc), C.POINTER(pt_params), C.c_int,
+                        C.c_void_p, C.POINTER(C.c_int)], C.c_int),
+    "pt_cache_read_records": ([C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_int)],
+                              C.c_int),
 }
 
 
@@ -202,7 +207,7 @@ def camera_struct(cam: "S.Camera") -> pt_camera:
 
 def render_desc(cams, width, height, spp, max_depth, seed, rr_depth=-1, nee=True, dispatch=PT_DISPATCH_SWITCH,
                 crop=None, lanes_per_pixel=0, block_size=0, tex_aggregate=0, dbg_L=None, dbg_hash=None,
-                counters=None):
+                counters=None, cache=None, cache_bounce=1):
     cams = list(cams)
     arr = (pt_camera * len(cams))(*[camera_struct(c) for c in cams])
     r = pt_render_desc()
@@ -216,6 +221,8 @@ def render_desc(cams, width, height, spp, max_depth, seed, rr_depth=-1, nee=True
     r.dbg_sample_L = _ptr(dbg_L)
     r.dbg_sample_hash = _ptr(dbg_hash)
     r.counters = _ptr(counters)
+    r.cache = cache
+    r.cache_bounce = cache_bounce
     r._keep = arr
     return r
 
@@ -336,3 +343,21 @@ def pt_cache_last_loss(handle: int, stream: int = 0) -> float:
     v = C.c_float(0)
     check("pt_cache_last_loss", load().pt_cache_last_loss(handle, stream or None, C.byref(v)))
     return v.value
+
+
+def pt_cache_train(cache: int, scene: int, desc: pt_render_desc, params: pt_params, steps: int,
+                   stream: int = 0) -> int:
+    n = C.c_int(0)
+    check("pt_cache_train", load().pt_cache_train(cache, scene, C.byref(desc), C.byref(params), steps,
+                                                  stream or None, C.byref(n)))
+    return n.value
+
+
+def pt_cache_read_records(cache: int, cap: int):
+    raw = np.zeros((cap, 10), np.float32)
+    tgt = np.zeros((cap, 3), np.float32)
+    meta = np.zeros((cap, 2), np.int32)
+    n = C.c_int(0)
+    check("pt_cache_read_records", load().pt_cache_read_records(cache, cap, raw.ctypes.data, tgt.ctypes.data,
+                                                                meta.ctypes.data, C.byref(n)))
+    return raw[:n.value], tgt[:n.value], meta[:n.value]

@@ -85,8 +85,29 @@ struct LaunchArgs {
   float* dbg_L;
   uint32_t* dbg_hash;
   unsigned long long* counters;
+  // radiance cache: 0 off, 1 terminate + write queries, 2 terminate + read cache
+  // radiance (adjoint), 3 full-length training paths writing records
+  int cache_mode, cache_bounce;
+  float* q_raw;        // [slots][10]
+  float* q_beta;       // [slots][3]
+  const float* q_rgb;  // [slots][3]
+  float* r_raw;        // [max_records][10]
+  float* r_aux;        // [max_records][8]: beta(3), L_before(3), path id bits, pad
+  float* path_L;       // [slots][3]
+  unsigned* r_count;   // records written (may exceed max_records: extra ones dropped)
+  long long max_records;
   DevCamera cams[PT_MAX_CAMS];
 };
+
+// Implemented in pt_nrc.cu (radiance-cache kernels used by the render launchers).
+int cache_infer(pt_cache* c, const float* raw, float* rgb, long long n, cudaStream_t st);
+int cache_optimise(pt_cache* c, const float* raw, const float* target, long long n, int steps, cudaStream_t st);
+struct CacheBuffers {
+  float *q_raw, *q_beta, *q_rgb, *r_raw, *r_aux, *r_target, *path_L;
+  unsigned* r_count;
+  long long max_queries, max_records, max_paths;
+};
+CacheBuffers cache_buffers(pt_cache* c);
 
 }  // namespace ptgb
 

@@ -146,7 +146,7 @@ struct NrcBox {
 };
 
 // ---------------------------------------------------------------- inference
-// out[r][c] = MLP(encode(raw[r])); optionally fused resolve: image[pix] += beta * max(out, 0) / spp.
+// out[r][c] = MLP(encode(raw[r])).
 __global__ void __launch_bounds__(128) nrc_infer_kernel(const float* __restrict__ raw, long long n, NrcBox box,
                                                         const __nv_bfloat16* __restrict__ W, float* __restrict__ out) {
   extern __shared__ __align__(16) unsigned char nrc_smem[];
@@ -581,6 +581,24 @@ int cache_optimise(pt_cache* c, const float* raw, const float* target, long long
 }
 }  // namespace ptgb
 
+namespace ptgb {
+CacheBuffers cache_buffers(pt_cache* c) {
+  CacheBuffers b;
+  b.q_raw = c->q_raw;
+  b.q_beta = c->q_beta;
+  b.q_rgb = c->q_rgb;
+  b.r_raw = c->r_raw;
+  b.r_aux = c->r_aux;
+  b.r_target = c->r_target;
+  b.path_L = c->path_L;
+  b.r_count = c->r_count;
+  b.max_queries = c->desc.max_queries;
+  b.max_records = c->desc.max_records;
+  b.max_paths = c->desc.max_paths;
+  return b;
+}
+}  // namespace ptgb
+
 extern "C" int pt_cache_query(pt_cache* c, const float* raw, float* rgb, int n, void* stream) {
   if (!c || n < 0 || (n > 0 && (!raw || !rgb))) return PT_ERR_ARG;
   return cache_infer(c, raw, rgb, n, (cudaStream_t)stream);
@@ -596,4 +614,27 @@ extern "C" int pt_cache_last_loss(pt_cache* c, void* stream, float* out) {
   if (!c || !out) return PT_ERR_ARG;
   if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return PT_ERR_CUDA;
   return cudaMemcpy(out, c->loss, 4, cudaMemcpyDeviceToHost) == cudaSuccess ? PT_OK : PT_ERR_CUDA;
+}
+
+extern "C" int pt_cache_read_records(pt_cache* c, int cap, float* raw, float* target, int* meta, int* n_out) {
+  if (!c || cap < 0 || !n_out) return PT_ERR_ARG;
+  if (cudaDeviceSynchronize() != cudaSuccess) return PT_ERR_CUDA;
+  unsigned count = 0;
+  if (cudaMemcpy(&count, c->r_count, sizeof(unsigned), cudaMemcpyDeviceToHost) != cudaSuccess) return PT_ERR_CUDA;
+  long long n = count;
+  if (n > c->desc.max_records) n = c->desc.max_records;
+  if (n > cap) n = cap;
+  *n_out = (int)n;
+  if (n == 0) return PT_OK;
+  std::vector<float> aux((size_t)n * 8);
+  bool ok = (!raw || cudaMemcpy(raw, c->r_raw, (size_t)n * 40, cudaMemcpyDeviceToHost) == cudaSuccess) &&
+            (!target || cudaMemcpy(target, c->r_target, (size_t)n * 12, cudaMemcpyDeviceToHost) == cudaSuccess) &&
+            cudaMemcpy(aux.data(), c->r_aux, (size_t)n * 32, cudaMemcpyDeviceToHost) == cudaSuccess;
+  if (!ok) return PT_ERR_CUDA;
+  if (meta)
+    for (long long i = 0; i < n; ++i) {
+      std::memcpy(&meta[2 * i], &aux[i * 8 + 6], 4);
+      std::memcpy(&meta[2 * i + 1], &aux[i * 8 + 7], 4);
+    }
+  return PT_OK;
 }

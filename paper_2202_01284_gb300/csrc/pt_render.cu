@@ -107,11 +107,15 @@ struct PathState {
   int lobe;
   int alb_kind, alb_ref, tex, rough, mtype;
   bool has_shadow, ok_next, delta_next, has_params;
+  long long slot;     // sample index (pixel * spp + sample): radiance-cache query / path id
+  bool cache_done;    // a cache query was written for this sample
 };
 
 template <bool INSTR>
 __device__ __forceinline__ void path_start(const LaunchArgs& A, PathState& P, int ci, int px, int py, int si,
-                                           Counters<INSTR>& cnt) {
+                                           long long pix, Counters<INSTR>& cnt) {
+  P.slot = pix * A.spp + si;
+  P.cache_done = false;
   const DevCamera& cam = A.cams[ci];
   unsigned long long pixel = (unsigned long long)py * (unsigned long long)A.width + (unsigned long long)px;
   P.rng.seed(A.seed, ((unsigned long long)ci << 40) | (pixel << 12) | (unsigned long long)si);
@@ -229,6 +233,47 @@ __device__ __forceinline__ bool path_shade(const LaunchArgs& A, PathState& P, co
 
   const bool entering = cos_front > 0.0f;
   const float3 n_s = entering ? ng : -ng;
+  // ---- radiance cache: terminate into the cache, or record training data
+  if (A.cache_mode != 0 && type != PT_BSDF_DIELECTRIC) {
+    const float rough = (type == PT_BSDF_CONDUCTOR || type == PT_BSDF_BLEND) ? m.alpha : 1.0f;
+    if (A.cache_mode == 3) {
+      const unsigned active = __activemask();
+      const int lane = lane_id(), leader = __ffs(active) - 1;
+      unsigned base = 0;
+      if (lane == leader) base = atomicAdd(A.r_count, (unsigned)__popc(active));
+      base = __shfl_sync(active, base, leader);
+      const long long idx = (long long)base + __popc(active & ((1u << lane) - 1u));
+      if (idx < A.max_records) {
+        float* r = A.r_raw + idx * 10;
+        r[0] = p.x; r[1] = p.y; r[2] = p.z;
+        r[3] = wi_w.x; r[4] = wi_w.y; r[5] = wi_w.z;
+        r[6] = n_s.x; r[7] = n_s.y; r[8] = n_s.z;
+        r[9] = rough;
+        float* a = A.r_aux + idx * 8;
+        a[0] = P.beta.x; a[1] = P.beta.y; a[2] = P.beta.z;
+        a[3] = P.L.x; a[4] = P.L.y; a[5] = P.L.z;
+        a[6] = __int_as_float((int)P.slot);
+        a[7] = __int_as_float(P.depth);
+      }
+    } else if (P.depth >= A.cache_bounce) {
+      if (A.cache_mode == 1) {
+        float* r = A.q_raw + P.slot * 10;
+        r[0] = p.x; r[1] = p.y; r[2] = p.z;
+        r[3] = wi_w.x; r[4] = wi_w.y; r[5] = wi_w.z;
+        r[6] = n_s.x; r[7] = n_s.y; r[8] = n_s.z;
+        r[9] = rough;
+        float* b = A.q_beta + P.slot * 3;
+        b[0] = P.beta.x; b[1] = P.beta.y; b[2] = P.beta.z;
+        P.cache_done = true;
+      } else {
+        const float* q = A.q_rgb + P.slot * 3;
+        const float3 c = P.beta * f3(fmaxf(q[0], 0.f), fmaxf(q[1], 0.f), fmaxf(q[2], 0.f));
+        P.L = P.L + c;
+        P.Lrem = P.Lrem - c;
+      }
+      return false;
+    }
+  }
   const Frame fr = make_frame(n_s);
   const float3 wi = fr.to_local(wi_w);
   P.c_nee = f3(0.f, 0.f, 0.f);
@@ -444,7 +489,7 @@ __device__ __forceinline__ void megakernel(const LaunchArgs& A, float* smem) {
   for (;;) {
     if (!has_path && valid && next_s < A.spp) {
       // one call site for both passes: the replay starts from identical code
-      path_start<INSTR>(A, P, px.cam, px.px, px.py, next_s, cnt);
+      path_start<INSTR>(A, P, px.cam, px.px, px.py, next_s, px.pix, cnt);
       P.Lrem = L_pass0;
       has_path = true;
       want_shadow = false;
@@ -470,6 +515,20 @@ __device__ __forceinline__ void megakernel(const LaunchArgs& A, float* smem) {
       if (finish) alive = path_finish<ADJ, INSTR>(A, P, occ, grad_pass, dl, sink, cnt);
       if (!alive) {
         has_path = false;
+        if constexpr (!ADJ) {
+          if (A.cache_mode == 1 && !P.cache_done) {  // no cache query for this sample
+            float* r = A.q_raw + P.slot * 10;
+#pragma unroll
+            for (int k = 0; k < 10; ++k) r[k] = 0.0f;
+            float* b = A.q_beta + P.slot * 3;
+            b[0] = b[1] = b[2] = 0.0f;
+          } else if (A.cache_mode == 3) {
+            float* pl = A.path_L + P.slot * 3;
+            pl[0] = P.L.x;
+            pl[1] = P.L.y;
+            pl[2] = P.L.z;
+          }
+        }
         if (ADJ && pass == 0) {
           L_pass0 = P.L;  // replay the same sample next: L_rem starts from its radiance
           pass = 1;
@@ -497,7 +556,7 @@ __device__ __forceinline__ void megakernel(const LaunchArgs& A, float* smem) {
       pix_sum.y += __shfl_xor_sync(0xffffffffu, pix_sum.y, off);
       pix_sum.z += __shfl_xor_sync(0xffffffffu, pix_sum.z, off);
     }
-    if (valid && lane_in_pix == 0) {
+    if (valid && lane_in_pix == 0 && A.image) {
       const float inv = 1.0f / (float)A.spp;
       A.image[3 * px.pix] = pix_sum.x * inv;
       A.image[3 * px.pix + 1] = pix_sum.y * inv;
@@ -536,6 +595,41 @@ template <bool INSTR, int LAYOUT>
 __global__ void __launch_bounds__(256, PT_ADJ_MIN_BLOCKS) adjoint_kernel(const __grid_constant__ LaunchArgs A) {
   extern __shared__ float smem[];
   megakernel<true, INSTR, LAYOUT>(A, smem);
+}
+
+// image[pix] += sum_s q_beta[slot] * max(q_rgb[slot], 0) / spp  (cache-terminated render)
+__global__ void cache_resolve_kernel(float* __restrict__ image, const float* __restrict__ q_beta,
+                                     const float* __restrict__ q_rgb, long long n_pix, int spp) {
+  const long long pix = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (pix >= n_pix) return;
+  float3 acc = f3(0.f, 0.f, 0.f);
+  for (int s = 0; s < spp; ++s) {
+    const long long slot = pix * spp + s;
+    const float* b = q_beta + slot * 3;
+    if (b[0] == 0.f && b[1] == 0.f && b[2] == 0.f) continue;
+    const float* q = q_rgb + slot * 3;
+    acc = acc + f3(b[0] * fmaxf(q[0], 0.f), b[1] * fmaxf(q[1], 0.f), b[2] * fmaxf(q[2], 0.f));
+  }
+  const float inv = 1.0f / (float)spp;
+  image[3 * pix] += acc.x * inv;
+  image[3 * pix + 1] += acc.y * inv;
+  image[3 * pix + 2] += acc.z * inv;
+}
+
+// Training targets: reflected radiance carried by the rest of the path,
+// (L_path - L_up_to_vertex) / throughput, per channel.
+__global__ void cache_targets_kernel(const float* __restrict__ aux, const float* __restrict__ path_L,
+                                     float* __restrict__ target, long long n) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float* a = aux + i * 8;
+  const long long pid = (long long)(unsigned)__float_as_int(a[6]);
+  const float* L = path_L + pid * 3;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const float beta = a[c];
+    target[i * 3 + c] = beta > 1e-12f ? fmaxf(L[c] - a[3 + c], 0.0f) / beta : 0.0f;
+  }
 }
 
 }  // namespace ptgb
@@ -639,6 +733,36 @@ int launch_dims(const pt_render_desc* r, const LaunchArgs& A, int& block, long l
 
 bool instrumented(const pt_render_desc* r) { return r->dbg_sample_L || r->dbg_sample_hash || r->counters; }
 
+long long sample_slots(const LaunchArgs& A) { return (long long)A.n_cams * A.crop_w * A.crop_h * A.spp; }
+
+int launch_forward(pt_scene* s, const pt_render_desc* r, const LaunchArgs& A, cudaStream_t cs) {
+  int block;
+  long long grid;
+  int st = launch_dims(r, A, block, grid);
+  if (st != PT_OK) return st;
+  const bool ins = instrumented(r), wide = s->dev.layout == PT_BVH_WIDE;
+  if (ins && wide) forward_kernel<true, PT_BVH_WIDE><<<(unsigned)grid, block, 0, cs>>>(A);
+  else if (ins) forward_kernel<true, PT_BVH_BINARY><<<(unsigned)grid, block, 0, cs>>>(A);
+  else if (wide) forward_kernel<false, PT_BVH_WIDE><<<(unsigned)grid, block, 0, cs>>>(A);
+  else forward_kernel<false, PT_BVH_BINARY><<<(unsigned)grid, block, 0, cs>>>(A);
+  return cudaGetLastError() == cudaSuccess ? PT_OK : PT_ERR_CUDA;
+}
+
+// Query pass of a cache-terminated render: write one query per sample, then infer.
+int cache_query_pass(pt_scene* s, const pt_render_desc* r, LaunchArgs A, float* image, cudaStream_t cs) {
+  CacheBuffers b = cache_buffers(r->cache);
+  const long long slots = sample_slots(A);
+  if (r->cache_bounce < 1 || slots > b.max_queries) return PT_ERR_ARG;
+  A.cache_mode = 1;
+  A.cache_bounce = r->cache_bounce;
+  A.q_raw = b.q_raw;
+  A.q_beta = b.q_beta;
+  A.image = image;
+  int st = launch_forward(s, r, A, cs);
+  if (st != PT_OK) return st;
+  return cache_infer(r->cache, b.q_raw, b.q_rgb, slots, cs);
+}
+
 }  // namespace
 
 extern "C" int pt_render_forward(pt_scene* s, const pt_render_desc* r, const pt_params* p, float* image,
@@ -648,15 +772,13 @@ extern "C" int pt_render_forward(pt_scene* s, const pt_render_desc* r, const pt_
   if (st != PT_OK) return st;
   if (!image) return PT_ERR_ARG;
   A.image = image;
-  int block;
-  long long grid;
-  if ((st = launch_dims(r, A, block, grid)) != PT_OK) return st;
   cudaStream_t cs = (cudaStream_t)stream;
-  const bool ins = instrumented(r), wide = s->dev.layout == PT_BVH_WIDE;
-  if (ins && wide) forward_kernel<true, PT_BVH_WIDE><<<(unsigned)grid, block, 0, cs>>>(A);
-  else if (ins) forward_kernel<true, PT_BVH_BINARY><<<(unsigned)grid, block, 0, cs>>>(A);
-  else if (wide) forward_kernel<false, PT_BVH_WIDE><<<(unsigned)grid, block, 0, cs>>>(A);
-  else forward_kernel<false, PT_BVH_BINARY><<<(unsigned)grid, block, 0, cs>>>(A);
+  if (!r->cache) return launch_forward(s, r, A, cs);
+  if (r->dbg_sample_L || r->dbg_sample_hash) return PT_ERR_ARG;
+  if ((st = cache_query_pass(s, r, A, image, cs)) != PT_OK) return st;
+  const long long n_pix = (long long)A.n_cams * A.crop_w * A.crop_h;
+  CacheBuffers b = cache_buffers(r->cache);
+  cache_resolve_kernel<<<(unsigned)((n_pix + 255) / 256), 256, 0, cs>>>(image, b.q_beta, b.q_rgb, n_pix, A.spp);
   return cudaGetLastError() == cudaSuccess ? PT_OK : PT_ERR_CUDA;
 }
 
@@ -684,10 +806,49 @@ extern "C" int pt_render_backward(pt_scene* s, const pt_render_desc* r, const pt
   long long grid;
   if ((st = launch_dims(r, A, block, grid)) != PT_OK) return st;
   cudaStream_t cs = (cudaStream_t)stream;
+  if (r->cache) {
+    // cache radiance of every sample first (same seed and slots as the replay)
+    if ((st = cache_query_pass(s, r, A, nullptr, cs)) != PT_OK) return st;
+    A.cache_mode = 2;
+    A.cache_bounce = r->cache_bounce;
+    A.q_rgb = cache_buffers(r->cache).q_rgb;
+  }
   const bool ins = instrumented(r), wide = s->dev.layout == PT_BVH_WIDE;
   if (ins && wide) adjoint_kernel<true, PT_BVH_WIDE><<<(unsigned)grid, block, smem, cs>>>(A);
   else if (ins) adjoint_kernel<true, PT_BVH_BINARY><<<(unsigned)grid, block, smem, cs>>>(A);
   else if (wide) adjoint_kernel<false, PT_BVH_WIDE><<<(unsigned)grid, block, smem, cs>>>(A);
   else adjoint_kernel<false, PT_BVH_BINARY><<<(unsigned)grid, block, smem, cs>>>(A);
   return cudaGetLastError() == cudaSuccess ? PT_OK : PT_ERR_CUDA;
+}
+
+extern "C" int pt_cache_train(pt_cache* c, pt_scene* s, const pt_render_desc* r, const pt_params* p, int steps,
+                              void* stream, int* n_records) {
+  if (!c || steps < 0) return PT_ERR_ARG;
+  LaunchArgs A;
+  int st = fill_launch(s, r, p, A);
+  if (st != PT_OK) return st;
+  if (r->dbg_sample_L || r->dbg_sample_hash) return PT_ERR_ARG;
+  CacheBuffers b = cache_buffers(c);
+  const long long slots = sample_slots(A);
+  if (slots > b.max_paths || b.max_records <= 0) return PT_ERR_ARG;
+  cudaStream_t cs = (cudaStream_t)stream;
+  A.cache_mode = 3;
+  A.r_raw = b.r_raw;
+  A.r_aux = b.r_aux;
+  A.path_L = b.path_L;
+  A.r_count = b.r_count;
+  A.max_records = b.max_records;
+  A.image = nullptr;
+  if (cudaMemsetAsync(b.r_count, 0, sizeof(unsigned), cs) != cudaSuccess) return PT_ERR_CUDA;
+  if ((st = launch_forward(s, r, A, cs)) != PT_OK) return st;
+  unsigned count = 0;
+  if (cudaMemcpyAsync(&count, b.r_count, sizeof(unsigned), cudaMemcpyDeviceToHost, cs) != cudaSuccess ||
+      cudaStreamSynchronize(cs) != cudaSuccess)
+    return PT_ERR_CUDA;
+  const long long n = count < (unsigned long long)b.max_records ? (long long)count : b.max_records;
+  if (n_records) *n_records = (int)n;
+  if (n == 0) return PT_OK;
+  cache_targets_kernel<<<(unsigned)((n + 255) / 256), 256, 0, cs>>>(b.r_aux, b.path_L, b.r_target, n);
+  if (cudaGetLastError() != cudaSuccess) return PT_ERR_CUDA;
+  return cache_optimise(c, b.r_raw, b.r_target, n, steps, cs);
 }

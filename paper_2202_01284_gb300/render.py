@@ -33,6 +33,8 @@ class RenderSettings:
     block_size: int = 0
     tex_aggregate: int = 0
     backward_seed: Optional[int] = None  # None: same seed as forward (correlated); else decorrelated
+    cache: Optional[int] = None          # pt_cache handle: cache-terminated paths
+    cache_bounce: int = 1
 
     def rows_cols(self):
         return (self.crop[3], self.crop[2]) if self.crop else (self.height, self.width)
@@ -77,7 +79,8 @@ class DeviceScene:
     def _desc(self, cams, st: RenderSettings, seed=None, dbg_L=None, dbg_hash=None, counters=None):
         return abi.render_desc(cams, st.width, st.height, st.spp, st.max_depth,
                                st.seed if seed is None else seed, st.rr_depth, st.nee, st.dispatch, st.crop,
-                               st.lanes_per_pixel, st.block_size, st.tex_aggregate, dbg_L, dbg_hash, counters)
+                               st.lanes_per_pixel, st.block_size, st.tex_aggregate, dbg_L, dbg_hash, counters,
+                               st.cache, st.cache_bounce)
 
     def forward(self, st: RenderSettings, cams: Optional[Sequence[S.Camera]] = None, albedo=None, textures=None,
                 roughness=None, out=None, per_sample=False, counters=None):
@@ -143,3 +146,53 @@ class RenderFn(torch.autograd.Function):
 
 def render(dscene: DeviceScene, st: RenderSettings, albedo, roughness, textures: Sequence[torch.Tensor]):
     return RenderFn.apply(dscene, st, albedo, roughness, *textures)
+
+
+class RadianceCache:
+    """Owner of a pt_cache (MLP weights, Adam state, query/record buffers)."""
+
+    def __init__(self, box_lo, box_hi, batch=65536, max_queries=0, max_records=0, max_paths=0, lr=5e-3,
+                 init_weights=None, seed=0, **adam):
+        self.handle = abi.pt_cache_create(box_lo, box_hi, batch, max_queries, max_records, max_paths, lr,
+                                          init_weights=init_weights, seed=seed, **adam)
+
+    def weights(self):
+        return abi.pt_cache_get_weights(self.handle)
+
+    def set_weights(self, w):
+        abi.pt_cache_set_weights(self.handle, w)
+
+    def query(self, raw, out=None):
+        n = raw.shape[0]
+        out = out if out is not None else torch.empty((n, 3), device=raw.device, dtype=torch.float32)
+        abi.pt_cache_query(self.handle, raw.contiguous(), out, n, torch.cuda.current_stream(raw.device).cuda_stream)
+        return out
+
+    def train_records(self, raw, target, steps=1):
+        abi.pt_cache_train_records(self.handle, raw.contiguous(), target.contiguous(), raw.shape[0], steps,
+                                   torch.cuda.current_stream(raw.device).cuda_stream)
+
+    def train(self, dscene: "DeviceScene", st: RenderSettings, steps=1, cams=None) -> int:
+        cams = list(cams) if cams is not None else dscene.cameras
+        p = abi.params_struct(dscene.albedo, dscene.textures, dscene.roughness)
+        desc = dscene._desc(cams, st)
+        desc.cache = None
+        return abi.pt_cache_train(self.handle, dscene.handle, desc, p, steps,
+                                  torch.cuda.current_stream(dscene.albedo.device).cuda_stream)
+
+    def last_loss(self) -> float:
+        return abi.pt_cache_last_loss(self.handle, torch.cuda.current_stream().cuda_stream)
+
+    def read_records(self, cap):
+        return abi.pt_cache_read_records(self.handle, cap)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            abi.pt_cache_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
