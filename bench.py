@@ -50,6 +50,9 @@ def parse():
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--tex-aggregate", type=int, default=0)
     ap.add_argument("--bvh", default="wide", choices=["wide", "binary"])
+    ap.add_argument("--cache", action="store_true",
+                    help="radiance-cache experiment: equal-time MSE, cache-terminated vs plain PT (own JSON line)")
+    ap.add_argument("--cache-warmup-frames", type=int, default=300)
     ap.add_argument("--small", action="store_true",
                     help="profiling case: same scene and step at 256x256, 64 spp (not a bench line)")
     return ap.parse_args()
@@ -344,10 +347,110 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_cache_experiment(args):
+    """Cornell box at 1024^2, depth 4: plain PT at 64 spp vs cache-terminated PT (bounce 1
+    and 2) at the spp that fits the same per-frame time including one online training
+    update, after a warm-up of online training frames.  Reference: 4096-spp plain PT,
+    itself checked against the FP64 oracle on a 64^2 crop at 64 spp."""
+    import numpy as np
+    import torch
+
+    import oracle
+    from paper_2202_01284_gb300 import abi, scenes as S
+    from paper_2202_01284_gb300.render import DeviceScene, RadianceCache, RenderSettings
+
+    torch.cuda.set_device(0)
+    W, H, D = 1024, 1024, 4
+    sc = S.cornell(width=W, height=H)
+    ds = DeviceScene(sc, layout=abi.PT_BVH_WIDE)
+    box = ((-1.0, 0.0, -1.0), (1.0, 2.0, 1.0))
+
+    def st(spp, seed, **kw):
+        return RenderSettings(width=W, height=H, spp=spp, max_depth=D, seed=seed, **kw)
+
+    def timed(fn, reps=3):
+        ts = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(True), torch.cuda.Event(True)
+            a.record()
+            out = fn()
+            b.record()
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        return statistics.median(ts), out
+
+    # reference: 4096 spp as 16 x 256 spp with distinct seeds
+    ref = torch.zeros((1, H, W, 3), device="cuda")
+    for k in range(16):
+        ref += ds.forward(st(256, 50000 + k))
+    ref /= 16
+    # reference checked against the oracle on a 64^2 crop at 64 spp (same seed, same estimator)
+    crop = (480, 400, 64, 64)
+    g_crop = ds.forward(RenderSettings(width=W, height=H, spp=64, max_depth=D, seed=4242, crop=crop))[0].cpu().numpy()
+    o_crop = oracle.render(oracle.OracleScene(sc), oracle.render_in(sc.cameras[0], 64, D, 4242, crop=crop))
+    tau = 1e-3 * np.abs(o_crop).mean()
+    crop_frac = float(np.mean((np.abs(g_crop - o_crop) <= 1e-4 * np.maximum(np.abs(o_crop), tau)).all(-1)))
+
+    # pixels that do not see the emitter (reference below 1): the light's edge pixels carry
+    # anti-aliasing variance (radiance 15 vs ~0.2) that no cache can remove
+    indirect = (ref.amax(dim=-1, keepdim=True) < 1.0).float()
+    n_ind = float(indirect.sum()) * 3
+
+    def mse(img):
+        d2 = (img - ref) ** 2
+        return float(d2.mean()), float((d2 * indirect).sum()) / n_ind
+
+    t_plain, img_plain = timed(lambda: ds.forward(st(64, 7)))
+    mp, mpi = mse(img_plain)
+    out = {"metric": "equal-time MSE vs 4096-spp reference, radiance cache vs plain PT",
+           "workload": f"cornell36, {W}x{H}, depth {D}", "reference_spp": 4096,
+           "reference_vs_oracle_crop": {"crop": crop, "spp": 64, "pixels_within_1e-4": crop_frac},
+           "indirect_pixel_fraction": n_ind / (3 * W * H),
+           "plain": {"spp": 64, "ms": round(t_plain, 3), "mse": mp, "mse_indirect": mpi}}
+    for bounce in (1, 2):
+        cache = RadianceCache(*box, batch=65536, max_queries=W * H * 192, max_records=2_000_000,
+                              max_paths=256 * 256, lr=5e-3, init_weights=S.mlp_init_weights(2022))
+        train_st = RenderSettings(width=256, height=256, spp=1, max_depth=D, seed=0)
+        train_cam = [S.cornell_camera(256, 256)]
+
+        def train_frame(i):
+            train_st.seed = 900000 + i
+            return cache.train(ds, train_st, steps=4, cams=train_cam)
+        t0 = time.perf_counter()
+        for i in range(args.cache_warmup_frames):
+            train_frame(i)
+        torch.cuda.synchronize()
+        warm_s = time.perf_counter() - t0
+        loss = cache.last_loss()
+        res = {}
+        best = None
+        for spp in (1, 2, 4, 8, 16, 32, 64, 96, 128, 192):
+            if W * H * spp > W * H * 64 * 3:
+                break
+            t_frame, img = timed(lambda: (train_frame(10 ** 6 + spp),
+                                          ds.forward(st(spp, 8, cache=cache.handle, cache_bounce=bounce)))[1])
+            m_all, m_ind = mse(img)
+            res[spp] = {"ms": round(t_frame, 3), "mse": m_all, "mse_indirect": m_ind}
+            if t_frame <= t_plain:
+                best = spp
+        eq = res[best] if best else None
+        out[f"cache_bounce{bounce}"] = {
+            "warmup_frames": args.cache_warmup_frames, "warmup_s": round(warm_s, 2), "train_loss": loss,
+            "per_frame": "one pt_cache_train (256^2 training paths, 1 spp, 4 Adam steps of 65,536) + render",
+            "equal_time_spp": best, "equal_time": eq,
+            "mse_ratio_plain_over_cache": (out["plain"]["mse"] / eq["mse"]) if eq else None,
+            "mse_indirect_ratio_plain_over_cache": (out["plain"]["mse_indirect"] / eq["mse_indirect"]) if eq else None,
+            "sweep": res}
+        cache.close()
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.cache:
+        run_cache_experiment(args)
     else:
         run_ours(args)
 

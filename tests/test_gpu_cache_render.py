@@ -48,7 +48,9 @@ def test_zero_cache_equals_truncated_paths(R, oracle_mod, bounce):
 @pytest.mark.parametrize("bounce", [1, 2])
 def test_cache_render_matches_oracle(R, oracle_mod, bounce):
     sc = S.cornell()
-    W = S.mlp_init_weights(31) * 0.5
+    # non-negative weights of mean ~1/64 keep every activation and output positive
+    # and of order one, so relative errors are well conditioned (no ReLU/clamp flips)
+    W = np.abs(S.mlp_init_weights(31)) * 0.1
     ds = R.DeviceScene(sc)
     cache = R.RadianceCache(*BOX, batch=64, max_queries=64 * 64 * 4, init_weights=W)
     img = ds.forward(_settings(R, sc, cache=cache.handle, cache_bounce=bounce))[0].cpu().numpy()
@@ -125,7 +127,10 @@ def test_trained_cache_lowers_error_at_equal_spp(R):
         cache.train(ds, _settings(R, sc, spp=1, max_depth=4, seed=1000 + it), steps=4)
     plain = ds.forward(_settings(R, sc, spp=4, max_depth=4, seed=77))[0]
     cached = ds.forward(_settings(R, sc, spp=4, max_depth=4, seed=77, cache=cache.handle, cache_bounce=1))[0]
-    mse_plain = float(((plain - ref) ** 2).mean())
-    mse_cache = float(((cached - ref) ** 2).mean())
-    print(f"loss {cache.last_loss():.4f}  MSE plain {mse_plain:.5f} cache {mse_cache:.5f}")
-    assert mse_cache < mse_plain
+    # pixels that do not see the light: its edge pixels carry anti-aliasing variance
+    # (radiance 15) that is the same for both estimators
+    m = (ref.amax(dim=-1, keepdim=True) < 1.0).float()
+    mse_plain = float((((plain - ref) ** 2) * m).sum() / (3 * m.sum()))
+    mse_cache = float((((cached - ref) ** 2) * m).sum() / (3 * m.sum()))
+    print(f"loss {cache.last_loss():.4f}  MSE (indirect pixels) plain {mse_plain:.6f} cache {mse_cache:.6f}")
+    assert mse_cache < 0.5 * mse_plain
