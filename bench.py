@@ -53,6 +53,9 @@ def parse():
     ap.add_argument("--cache", action="store_true",
                     help="radiance-cache experiment: equal-time MSE, cache-terminated vs plain PT (own JSON line)")
     ap.add_argument("--cache-warmup-frames", type=int, default=300)
+    ap.add_argument("--batch", action="store_true",
+                    help="batching experiment: 64 cameras over 10k/200k/2M-triangle scenes, forward + adjoint "
+                         "in one persistent graph-captured launch vs 64 separate launches (own JSON line)")
     ap.add_argument("--small", action="store_true",
                     help="profiling case: same scene and step at 256x256, 64 spp (not a bench line)")
     return ap.parse_args()
@@ -445,12 +448,100 @@ def run_cache_experiment(args):
     print(json.dumps(out), flush=True)
 
 
+def run_batch_experiment(args):
+    """64 cameras (128^2..1024^2, 4..64 spp) over three sphere scenes of ~10k, ~200k and
+    ~2M triangles: forward + PRB adjoint (L2 loss vs a constant 0.3 target, gradients into
+    each scene's texture and roughness) as one persistent launch replayed from a CUDA
+    graph with autotuned tiles, vs 64 x (forward, loss gradient, backward) launches."""
+    import torch
+
+    from paper_2202_01284_gb300 import abi, batch as B, scenes as S
+    from paper_2202_01284_gb300.render import DeviceScene, RenderSettings
+
+    torch.cuda.set_device(0)
+    t0 = time.perf_counter()
+    scenes = [DeviceScene(sc, layout=abi.PT_BVH_WIDE) for sc in S.batch_scenes()]
+    setup_s = time.perf_counter() - t0
+    cams = S.batch_cameras(64)
+    g_tex = [[torch.zeros_like(t) for t in ds.textures] for ds in scenes]
+    g_rough = [torch.zeros_like(ds.roughness) for ds in scenes]
+
+    def reset():
+        for gl in g_tex:
+            for g in gl:
+                g.zero_()
+        for g in g_rough:
+            g.zero_()
+    jobs = []
+    for k, bc in enumerate(cams):
+        tgt = torch.full((bc.camera.height, bc.camera.width, 3), 0.3, device="cuda")
+        jobs.append(B.Job(scenes[bc.scene], bc.camera, bc.spp, seed=10 + k, backward_seed=5000 + k, target=tgt,
+                          g_textures=g_tex[bc.scene], g_roughness=g_rough[bc.scene]))
+    samples = sum(j.camera.width * j.camera.height * j.spp for j in jobs)
+    grad_bufs = {(j.camera.height, j.camera.width): torch.empty((j.camera.height, j.camera.width, 3), device="cuda")
+                 for j in jobs}
+    # rays of the whole workload (instrumented separate launches of the same jobs)
+    cnt_f = torch.zeros(abi.PT_N_COUNTERS, dtype=torch.int64, device="cuda")
+    cnt_b = torch.zeros(abi.PT_N_COUNTERS, dtype=torch.int64, device="cuda")
+
+    def st_of(j):
+        return RenderSettings(width=j.camera.width, height=j.camera.height, spp=j.spp, max_depth=j.max_depth,
+                              rr_depth=j.rr_depth, seed=j.seed, lanes_per_pixel=min(8, j.spp))
+
+    def separate(counters=False):
+        for j in jobs:
+            st = st_of(j)
+            img = j.dscene.forward(st, cams=[j.camera], out=j.image[None], counters=cnt_f if counters else None)
+            torch.sub(img[0], j.target, out=grad_bufs[j.camera.height, j.camera.width])
+            gi = grad_bufs[j.camera.height, j.camera.width]
+            gi.mul_(2.0 / img.numel())
+            j.dscene.backward(st, gi[None], cams=[j.camera], g_textures=j.g_textures,
+                              g_roughness=j.g_roughness, seed=j.backward_seed, counters=cnt_b if counters else None)
+    separate(counters=True)
+    torch.cuda.synchronize()
+    rays = int(cnt_f[1] + cnt_f[2] + cnt_b[1] + cnt_b[2])
+    reset()
+
+    def timed(fn, reps=3):
+        fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            a, e = torch.cuda.Event(True), torch.cuda.Event(True)
+            a.record()
+            fn()
+            e.record()
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(e))
+        return statistics.median(ts)
+    sep_ms = timed(separate)
+    reset()
+    best = B.autotune(jobs, candidates=[(t, l, c) for t in (2, 4, 8) for l in (2, 4, 8) for c in (4, 8)],
+                      use_cache=False, reset_grads=reset)
+    b = B.Batch(jobs, tile=best["tile"], lanes_per_pixel=best["lanes_per_pixel"], ctas_per_sm=best["ctas_per_sm"])
+    b.capture()
+    graph_ms = timed(b.replay)
+    direct_ms = timed(b.run)
+    out = {"metric": "batched forward + adjoint: one persistent CUDA-graph launch vs 64 separate launches",
+           "jobs": len(jobs), "scenes_tris": [ds.scene.n_tris for ds in scenes], "samples": samples, "rays": rays,
+           "work_items": b.n_items, "scene_setup_s": round(setup_s, 2),
+           "persistent_graph_ms": round(graph_ms, 3), "persistent_direct_ms": round(direct_ms, 3),
+           "separate_ms": round(sep_ms, 3), "speedup": round(sep_ms / graph_ms, 3),
+           "mrays_s_persistent": round(rays / graph_ms / 1e3, 1), "mrays_s_separate": round(rays / sep_ms / 1e3, 1),
+           "gpu_launches": {"persistent": 2, "separate": 2 * len(jobs), "graph_launches": 1},
+           "autotune": {k: v for k, v in best.items() if k != "candidates"},
+           "autotune_candidates": best["candidates"]}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
     elif args.cache:
         run_cache_experiment(args)
+    elif args.batch:
+        run_batch_experiment(args)
     else:
         run_ours(args)
 

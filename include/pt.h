@@ -214,6 +214,49 @@ int pt_render_forward(pt_scene* scene, const pt_render_desc* desc, const pt_para
 int pt_render_backward(pt_scene* scene, const pt_render_desc* desc, const pt_params* params,
                        const float* grad_image, const pt_grads* grads, void* stream);
 
+/* ------------------------------------------------------------------ batching
+ * Many cameras over several scenes, of uneven size and spp, in one persistent
+ * pass per phase: the (job, tile) work items are sorted longest first and handed,
+ * one per warp, to the warps of grid = ctas_per_sm x SMs resident CTAs by a global
+ * atomic counter.  The forward kernel renders every tile; the adjoint kernel,
+ * launched right after it on the same stream, replays every tile of the jobs with
+ * a target using the job's backward seed and dLoss/dI = 2 (I - T) / (3 W H),
+ * accumulating into the job's gradient buffers.
+ * Not in the paper (its megakernels render one image at a time). */
+typedef struct {
+  pt_scene* scene;             /* all jobs of a batch must use the same BVH layout */
+  pt_camera camera;
+  int32_t width, height, spp, max_depth, rr_depth, nee;
+  uint64_t seed, backward_seed;
+  pt_params params;            /* borrowed device pointers */
+  pt_grads grads;              /* accumulated (+=); NULL members are skipped */
+  float* image;                /* device [height][width][3], written */
+  const float* target;         /* device [height][width][3]; NULL = forward only */
+} pt_job;
+
+typedef struct {
+  int32_t tile;                /* tile side in pixels (one warp's work item), 1..256 */
+  int32_t lanes_per_pixel;     /* threads per pixel (power of two <= 32; capped at spp) */
+  int32_t ctas_per_sm;         /* resident CTAs per SM, 1..8 */
+  int32_t block_size;          /* threads per CTA, multiple of 32, <= 256 */
+} pt_batch_opts;
+
+typedef struct pt_batch pt_batch;
+
+/* Validate the jobs, build and upload the job table and the sorted work list
+ * (synchronous; device memory owned by the batch).  opts may be NULL
+ * (tile 4, 4 lanes, 4 CTAs/SM, 128 threads).  Errors: PT_ERR_ARG (bad job or
+ * option, mixed BVH layouts), PT_ERR_STATE (scene without BVH), PT_ERR_OOM. */
+int pt_batch_create(const pt_job* jobs, int n_jobs, const pt_batch_opts* opts, pt_batch** out);
+/* Reset the work counters and launch the two persistent kernels on `stream`: one
+ * memset and two launches, no allocation or host synchronisation, so the call can
+ * be captured into one CUDA graph and replayed with a single graph launch. */
+int pt_batch_run(pt_batch* batch, void* stream);
+int pt_batch_info(const pt_batch* batch, int* n_items);
+void pt_batch_destroy(pt_batch* batch);
+/* create + run + synchronise + destroy. */
+int pt_render_batch(const pt_job* jobs, int n_jobs, const pt_batch_opts* opts, void* stream);
+
 /* Reads (and clears) the scene's device status word after synchronising
  * `stream`: *out = PT_OK or the first PT_ERR_* a kernel recorded. */
 int pt_last_device_status(pt_scene* scene, void* stream, int* out);

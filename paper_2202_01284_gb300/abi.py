@@ -98,6 +98,18 @@ class pt_cache_desc(C.Structure):
                 ("init_weights", C.c_void_p), ("seed", C.c_uint64)]
 
 
+class pt_job(C.Structure):
+    _fields_ = [("scene", C.c_void_p), ("camera", pt_camera), ("width", C.c_int32), ("height", C.c_int32),
+                ("spp", C.c_int32), ("max_depth", C.c_int32), ("rr_depth", C.c_int32), ("nee", C.c_int32),
+                ("seed", C.c_uint64), ("backward_seed", C.c_uint64), ("params", pt_params), ("grads", pt_grads),
+                ("image", C.c_void_p), ("target", C.c_void_p)]
+
+
+class pt_batch_opts(C.Structure):
+    _fields_ = [("tile", C.c_int32), ("lanes_per_pixel", C.c_int32), ("ctas_per_sm", C.c_int32),
+                ("block_size", C.c_int32)]
+
+
 _lib = None
 _lock = threading.Lock()
 
@@ -122,6 +134,11 @@ SIGNATURES = {
     "pt_cache_last_loss": ([C.c_void_p, C.c_void_p, C.POINTER(C.c_float)], C.c_int),
     "pt_cache_train": ([C.c_void_p, C.c_void_p, C.POINTER(pt_render_desc), C.POINTER(pt_params), C.c_int,
                         C.c_void_p, C.POINTER(C.c_int)], C.c_int),
+    "pt_batch_create": ([C.c_void_p, C.c_int, C.POINTER(pt_batch_opts), C.POINTER(C.c_void_p)], C.c_int),
+    "pt_batch_run": ([C.c_void_p, C.c_void_p], C.c_int),
+    "pt_batch_info": ([C.c_void_p, C.POINTER(C.c_int)], C.c_int),
+    "pt_batch_destroy": ([C.c_void_p], None),
+    "pt_render_batch": ([C.c_void_p, C.c_int, C.POINTER(pt_batch_opts), C.c_void_p], C.c_int),
     "pt_cache_read_records": ([C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_int)],
                               C.c_int),
 }
@@ -361,3 +378,26 @@ def pt_cache_read_records(cache: int, cap: int):
     check("pt_cache_read_records", load().pt_cache_read_records(cache, cap, raw.ctypes.data, tgt.ctypes.data,
                                                                 meta.ctypes.data, C.byref(n)))
     return raw[:n.value], tgt[:n.value], meta[:n.value]
+
+
+# ------------------------------------------------------------------ batching
+def pt_batch_create(jobs, opts) -> int:
+    arr = (pt_job * len(jobs))(*jobs)
+    h = C.c_void_p()
+    check("pt_batch_create", load().pt_batch_create(C.cast(arr, C.c_void_p), len(jobs), C.byref(opts), C.byref(h)))
+    return h.value
+
+
+def pt_batch_run(handle: int, stream: int = 0) -> None:
+    check("pt_batch_run", load().pt_batch_run(handle, stream or None))
+
+
+def pt_batch_info(handle: int) -> int:
+    n = C.c_int(0)
+    check("pt_batch_info", load().pt_batch_info(handle, C.byref(n)))
+    return n.value
+
+
+def pt_batch_destroy(handle: int) -> None:
+    if handle:
+        load().pt_batch_destroy(handle)

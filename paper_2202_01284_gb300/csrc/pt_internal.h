@@ -78,10 +78,12 @@ struct LaunchArgs {
   int crop_x0, crop_y0, crop_w, crop_h;
   int lanes_per_pixel, log2_lanes;
   int tex_aggregate;
-  unsigned long long seed;
+  unsigned long long seed, seed_adj;  // forward / adjoint PCG32 initstate
   long long n_units;          // n_cams * crop_w * crop_h * lanes_per_pixel
   float* image;               // forward output
   const float* grad_image;    // adjoint input
+  const float* target;        // batched jobs: L2-loss target image (NULL = forward only)
+  float loss_scale;           // batched jobs: dLoss/dI = 2 * (I - T) * loss_scale
   float* dbg_L;
   uint32_t* dbg_hash;
   unsigned long long* counters;

@@ -1,6 +1,10 @@
 // Forward megakernel and fused PRB adjoint megakernel, plus their C-ABI launchers.
+#include <algorithm>
 #include <cmath>
+#include <cstddef>
 #include <cstring>
+#include <new>
+#include <vector>
 
 #include "pt_device.cuh"
 
@@ -112,13 +116,13 @@ struct PathState {
 };
 
 template <bool INSTR>
-__device__ __forceinline__ void path_start(const LaunchArgs& A, PathState& P, int ci, int px, int py, int si,
-                                           long long pix, Counters<INSTR>& cnt) {
+__device__ __forceinline__ void path_start(const LaunchArgs& A, PathState& P, unsigned long long seed, int ci, int px,
+                                           int py, int si, long long pix, Counters<INSTR>& cnt) {
   P.slot = pix * A.spp + si;
   P.cache_done = false;
   const DevCamera& cam = A.cams[ci];
   unsigned long long pixel = (unsigned long long)py * (unsigned long long)A.width + (unsigned long long)px;
-  P.rng.seed(A.seed, ((unsigned long long)ci << 40) | (pixel << 12) | (unsigned long long)si);
+  P.rng.seed(seed, ((unsigned long long)ci << 40) | (pixel << 12) | (unsigned long long)si);
   P.fh.h = 2166136261u;
   float j0 = P.rng.uniform(), j1 = P.rng.uniform();
   float sx = 2.0f * (px + j0) / A.width - 1.0f;
@@ -428,21 +432,28 @@ __device__ __forceinline__ void flush_counters(const LaunchArgs& A, Counters<INS
 }
 
 struct PixelOf {
-  int cam, ix, iy, px, py;
-  long long pix;  // dense index of the pixel in the output
+  int cam, px, py;
+  long long pix;  // dense index of the pixel in the output image
 };
-__device__ __forceinline__ PixelOf unit_pixel(const LaunchArgs& A, long long unit) {
-  PixelOf r;
-  long long pix = unit >> A.log2_lanes;
-  long long per_cam = (long long)A.crop_w * A.crop_h;
+// A rectangle of pixels (of n_cams cameras) processed by one launch or one work item.
+struct Tile {
+  int x0, y0, w, h, n_cams;
+};
+// Pixel of `unit` (pixel-major, lanes_per_pixel consecutive units per pixel) inside
+// the tile; false if the unit lies outside the tile or outside the image crop.
+__device__ __forceinline__ bool unit_pixel(const LaunchArgs& A, long long unit, const Tile& t, PixelOf& r) {
+  const long long pix = unit >> A.log2_lanes;
+  const long long per_cam = (long long)t.w * t.h;
+  if (unit < 0 || pix >= per_cam * t.n_cams) return false;
   r.cam = (int)(pix / per_cam);
-  long long rem = pix - (long long)r.cam * per_cam;
-  r.iy = (int)(rem / A.crop_w);
-  r.ix = (int)(rem - (long long)r.iy * A.crop_w);
-  r.px = A.crop_x0 + r.ix;
-  r.py = A.crop_y0 + r.iy;
-  r.pix = pix;
-  return r;
+  const long long rem = pix - (long long)r.cam * per_cam;
+  const int iy = (int)(rem / t.w);
+  const int ix = (int)(rem - (long long)iy * t.w);
+  r.px = t.x0 + ix;
+  r.py = t.y0 + iy;
+  if (r.px >= A.crop_x0 + A.crop_w || r.py >= A.crop_y0 + A.crop_h) return false;
+  r.pix = ((long long)r.cam * A.crop_h + (r.py - A.crop_y0)) * A.crop_w + (r.px - A.crop_x0);
+  return true;
 }
 
 // The megakernel: forward (ADJ = false) or fused PRB adjoint (ADJ = true).
@@ -450,7 +461,7 @@ __device__ __forceinline__ PixelOf unit_pixel(const LaunchArgs& A, long long uni
 // pixel; in the adjoint every sample is traced twice (pass 0: radiance L,
 // pass 1: replay with L_rem and gradient scatter) by the same code.
 template <bool ADJ, bool INSTR, int LAYOUT>
-__device__ __forceinline__ void megakernel(const LaunchArgs& A, float* smem) {
+__device__ __forceinline__ void megakernel(const LaunchArgs& A, float* smem, long long unit, const Tile& tile) {
   const DevGrads& G = A.grads;
   float* s_alb = nullptr;
   float* s_rough = nullptr;
@@ -459,24 +470,30 @@ __device__ __forceinline__ void megakernel(const LaunchArgs& A, float* smem) {
     s_alb = G.smem_albedo ? smem : nullptr;
     s_rough = G.smem_rough ? smem + (G.smem_albedo ? 3 * G.n_albedo : 0) : nullptr;
     n_stage = (G.smem_albedo ? 3 * G.n_albedo : 0) + (G.smem_rough ? G.n_rough : 0);
-    for (int i = threadIdx.x; i < n_stage; i += blockDim.x) smem[i] = 0.0f;
-    __syncthreads();
+    if (n_stage > 0) {  // uniform over the CTA
+      for (int i = threadIdx.x; i < n_stage; i += blockDim.x) smem[i] = 0.0f;
+      __syncthreads();
+    }
   }
-  const long long unit = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const bool valid = unit < A.n_units;
+  PixelOf px{};
+  const bool valid = unit_pixel(A, unit, tile, px);
   Counters<INSTR> cnt;
   if constexpr (INSTR) {
     for (int i = 0; i < 8; ++i) cnt.c[i] = 0;
   }
   GradSink sink{s_alb, s_rough};
   const int lane_in_pix = (int)(unit & (A.lanes_per_pixel - 1));
-  PixelOf px{};
   float3 dl = f3(0.f, 0.f, 0.f);
   if (valid) {
-    px = unit_pixel(A, unit);
     if constexpr (ADJ) {
       const float inv = 1.0f / (float)A.spp;
-      dl = f3(A.grad_image[3 * px.pix] * inv, A.grad_image[3 * px.pix + 1] * inv, A.grad_image[3 * px.pix + 2] * inv);
+      if (A.target) {  // batched jobs: L2 loss against the job's target
+        const float k = 2.0f * A.loss_scale * inv;
+        dl = f3((A.image[3 * px.pix] - A.target[3 * px.pix]) * k, (A.image[3 * px.pix + 1] - A.target[3 * px.pix + 1]) * k,
+                (A.image[3 * px.pix + 2] - A.target[3 * px.pix + 2]) * k);
+      } else {
+        dl = f3(A.grad_image[3 * px.pix] * inv, A.grad_image[3 * px.pix + 1] * inv, A.grad_image[3 * px.pix + 2] * inv);
+      }
     }
   }
   float3 pix_sum = f3(0.f, 0.f, 0.f);
@@ -489,7 +506,7 @@ __device__ __forceinline__ void megakernel(const LaunchArgs& A, float* smem) {
   for (;;) {
     if (!has_path && valid && next_s < A.spp) {
       // one call site for both passes: the replay starts from identical code
-      path_start<INSTR>(A, P, px.cam, px.px, px.py, next_s, px.pix, cnt);
+      path_start<INSTR>(A, P, ADJ ? A.seed_adj : A.seed, px.cam, px.px, px.py, next_s, px.pix, cnt);
       P.Lrem = L_pass0;
       has_path = true;
       want_shadow = false;
@@ -562,7 +579,7 @@ __device__ __forceinline__ void megakernel(const LaunchArgs& A, float* smem) {
       A.image[3 * px.pix + 1] = pix_sum.y * inv;
       A.image[3 * px.pix + 2] = pix_sum.z * inv;
     }
-  } else {
+  } else if (n_stage > 0) {
     __syncthreads();
     for (int i = threadIdx.x; i < n_stage; i += blockDim.x) {
       const float v = smem[i];
@@ -586,15 +603,19 @@ __device__ __forceinline__ void megakernel(const LaunchArgs& A, float* smem) {
 #define PT_ADJ_MIN_BLOCKS 2
 #endif
 
+__device__ __forceinline__ Tile crop_tile(const LaunchArgs& A) {
+  return Tile{A.crop_x0, A.crop_y0, A.crop_w, A.crop_h, A.n_cams};
+}
+
 template <bool INSTR, int LAYOUT>
 __global__ void __launch_bounds__(256, PT_FWD_MIN_BLOCKS) forward_kernel(const __grid_constant__ LaunchArgs A) {
-  megakernel<false, INSTR, LAYOUT>(A, nullptr);
+  megakernel<false, INSTR, LAYOUT>(A, nullptr, (long long)blockIdx.x * blockDim.x + threadIdx.x, crop_tile(A));
 }
 
 template <bool INSTR, int LAYOUT>
 __global__ void __launch_bounds__(256, PT_ADJ_MIN_BLOCKS) adjoint_kernel(const __grid_constant__ LaunchArgs A) {
   extern __shared__ float smem[];
-  megakernel<true, INSTR, LAYOUT>(A, smem);
+  megakernel<true, INSTR, LAYOUT>(A, smem, (long long)blockIdx.x * blockDim.x + threadIdx.x, crop_tile(A));
 }
 
 // image[pix] += sum_s q_beta[slot] * max(q_rgb[slot], 0) / spp  (cache-terminated render)
@@ -629,6 +650,51 @@ __global__ void cache_targets_kernel(const float* __restrict__ aux, const float*
   for (int c = 0; c < 3; ++c) {
     const float beta = a[c];
     target[i * 3 + c] = beta > 1e-12f ? fmaxf(L[c] - a[3 + c], 0.0f) / beta : 0.0f;
+  }
+}
+
+// ---------------------------------------------------------------- batched persistent launch
+struct BatchItem {
+  int job, x0, y0;
+};
+
+// Bytes of a job record the megakernel reads for single-camera jobs (all fields up
+// to and including cams[0]), copied per warp into shared memory.
+constexpr int kJobBytes = (int)((offsetof(LaunchArgs, cams) + sizeof(DevCamera) + 15) / 16 * 16);
+
+// Persistent kernel over a queue of (job, tile) work items taken per WARP from a
+// global atomic counter (nothing waits on it: it only hands out work).  The
+// forward instance renders each tile; the adjoint instance (launched after it on
+// the same stream) replays each tile with the job's backward seed, taking
+// dLoss/dI = 2 (I - T) / (3 W H) straight from the image and the job's target.
+// Two kernels rather than one keep each at the register footprint of its
+// single-job counterpart (one kernel holding both megakernels spills).
+template <bool ADJ, int LAYOUT>
+__global__ void __launch_bounds__(256, PT_ADJ_MIN_BLOCKS)
+    batch_kernel(const LaunchArgs* __restrict__ jobs, const BatchItem* __restrict__ items, int n_items, int tile,
+                 unsigned* __restrict__ queue) {
+  extern __shared__ __align__(16) unsigned char job_smem[];
+  const int lane = lane_id();
+  unsigned char* slot = job_smem + (threadIdx.x >> 5) * kJobBytes;
+  const LaunchArgs& A = *reinterpret_cast<const LaunchArgs*>(slot);
+  int cur_job = -1;
+  for (;;) {
+    int it = 0;
+    if (lane == 0) it = (int)atomicAdd(queue, 1u);
+    it = __shfl_sync(0xffffffffu, it, 0);
+    if (it >= n_items) break;
+    const BatchItem bi = items[it];
+    if (bi.job != cur_job) {
+      __syncwarp();
+      const uint4* src = reinterpret_cast<const uint4*>(&jobs[bi.job]);
+      uint4* dst = reinterpret_cast<uint4*>(slot);
+      for (int k = lane; k < kJobBytes / 16; k += 32) dst[k] = src[k];
+      __syncwarp();
+      cur_job = bi.job;
+    }
+    const Tile t{bi.x0, bi.y0, tile, tile, 1};
+    const long long units = (long long)tile * tile * A.lanes_per_pixel;
+    for (long long b = 0; b < units; b += 32) megakernel<ADJ, false, LAYOUT>(A, nullptr, b + lane, t);
   }
 }
 
@@ -694,6 +760,7 @@ int fill_launch(pt_scene* s, const pt_render_desc* r, const pt_params* p, Launch
   while ((1 << A.log2_lanes) < lp) ++A.log2_lanes;
   A.tex_aggregate = r->tex_aggregate ? 1 : 0;
   A.seed = r->seed;
+  A.seed_adj = r->seed;
   A.n_units = (long long)r->n_cams * cw * ch * lp;
   A.dbg_L = r->dbg_sample_L;
   A.dbg_hash = r->dbg_sample_hash;
@@ -851,4 +918,154 @@ extern "C" int pt_cache_train(pt_cache* c, pt_scene* s, const pt_render_desc* r,
   cache_targets_kernel<<<(unsigned)((n + 255) / 256), 256, 0, cs>>>(b.r_aux, b.path_L, b.r_target, n);
   if (cudaGetLastError() != cudaSuccess) return PT_ERR_CUDA;
   return cache_optimise(c, b.r_raw, b.r_target, n, steps, cs);
+}
+
+// ---------------------------------------------------------------- batch ABI
+struct pt_batch {
+  LaunchArgs* d_jobs = nullptr;
+  BatchItem* d_items = nullptr;   // forward items, then adjoint items
+  unsigned* d_queue = nullptr;    // [2] work counters (forward, adjoint)
+  int n_items = 0, n_adj_items = 0, tile = 4, block = 128, grid = 152, layout = PT_BVH_WIDE;
+};
+
+extern "C" int pt_batch_create(const pt_job* jobs, int n_jobs, const pt_batch_opts* o, pt_batch** out) {
+  if (!jobs || n_jobs <= 0 || !out) return PT_ERR_ARG;
+  *out = nullptr;
+  pt_batch_opts opts{4, 4, 4, 128};
+  if (o) opts = *o;
+  if (opts.tile < 1 || opts.tile > 256 || opts.ctas_per_sm < 1 || opts.ctas_per_sm > 8) return PT_ERR_ARG;
+  if (opts.block_size <= 0) opts.block_size = 128;
+  if (opts.block_size % 32 || opts.block_size > 256) return PT_ERR_ARG;
+  int lp = opts.lanes_per_pixel > 0 ? opts.lanes_per_pixel : 8;
+  if (lp > 32 || (lp & (lp - 1))) return PT_ERR_ARG;
+  std::vector<LaunchArgs> args(n_jobs);
+  std::vector<BatchItem> items;
+  std::vector<long long> cost;
+  int layout = -1;
+  for (int j = 0; j < n_jobs; ++j) {
+    const pt_job& jb = jobs[j];
+    if (!jb.scene || !jb.image) return PT_ERR_ARG;
+    pt_render_desc r;
+    std::memset(&r, 0, sizeof r);
+    r.n_cams = 1;
+    r.cams = &jb.camera;
+    r.width = jb.width;
+    r.height = jb.height;
+    r.spp = jb.spp;
+    r.max_depth = jb.max_depth;
+    r.rr_depth = jb.rr_depth;
+    r.nee = jb.nee;
+    r.seed = jb.seed;
+    r.lanes_per_pixel = std::min(lp, std::max(1, jb.spp));
+    while (r.lanes_per_pixel & (r.lanes_per_pixel - 1)) --r.lanes_per_pixel;
+    LaunchArgs& A = args[j];
+    int st = fill_launch(jb.scene, &r, &jb.params, A);
+    if (st != PT_OK) return st;
+    if (layout < 0) layout = jb.scene->dev.layout;
+    if (jb.scene->dev.layout != layout) return PT_ERR_ARG;
+    A.seed_adj = jb.backward_seed;
+    A.image = jb.image;
+    A.target = jb.target;
+    A.grad_image = nullptr;
+    A.loss_scale = 1.0f / (3.0f * jb.width * jb.height);
+    A.grads.albedo = jb.grads.albedo;
+    A.grads.rough = jb.grads.roughness;
+    for (int t = 0; t < PT_MAX_TEX; ++t) A.grads.tex[t] = reinterpret_cast<float4*>(jb.grads.tex[t]);
+    A.grads.n_albedo = jb.params.n_albedo;
+    A.grads.n_rough = jb.params.n_rough;
+    // no shared-memory staging of gradients in the persistent kernel: it would put two
+    // CTA barriers into every tile; warp-aggregated global atomics are used instead
+    A.grads.smem_albedo = 0;
+    A.grads.smem_rough = 0;
+    for (int y0 = 0; y0 < jb.height; y0 += opts.tile)
+      for (int x0 = 0; x0 < jb.width; x0 += opts.tile) {
+        items.push_back({j, x0, y0});
+        cost.push_back((long long)jb.spp * std::min(opts.tile, jb.width - x0) * std::min(opts.tile, jb.height - y0) *
+                       (jb.target ? 3 : 1));
+      }
+  }
+  // longest work first (list scheduling onto the persistent warps); the adjoint list
+  // holds the items of the jobs that have a target
+  std::vector<int> order(items.size());
+  for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+  std::vector<BatchItem> sorted;
+  sorted.reserve(2 * items.size());
+  for (size_t i = 0; i < order.size(); ++i) sorted.push_back(items[order[i]]);
+  const int n_fwd = (int)sorted.size();
+  for (size_t i = 0; i < order.size(); ++i)
+    if (jobs[items[order[i]].job].target) sorted.push_back(items[order[i]]);
+  pt_batch* b = new (std::nothrow) pt_batch();
+  if (!b) return PT_ERR_OOM;
+  int dev = 0, sms = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  b->n_items = n_fwd;
+  b->n_adj_items = (int)sorted.size() - n_fwd;
+  b->tile = opts.tile;
+  b->block = opts.block_size;
+  b->grid = sms * opts.ctas_per_sm;
+  b->layout = layout;
+  bool ok = cudaMalloc(&b->d_jobs, sizeof(LaunchArgs) * n_jobs) == cudaSuccess &&
+            cudaMalloc(&b->d_items, sizeof(BatchItem) * sorted.size()) == cudaSuccess &&
+            cudaMalloc(&b->d_queue, 2 * sizeof(unsigned)) == cudaSuccess;
+  ok = ok && cudaMemcpy(b->d_jobs, args.data(), sizeof(LaunchArgs) * n_jobs, cudaMemcpyHostToDevice) == cudaSuccess &&
+       cudaMemcpy(b->d_items, sorted.data(), sizeof(BatchItem) * sorted.size(), cudaMemcpyHostToDevice) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    if (b->d_jobs) cudaFree(b->d_jobs);
+    if (b->d_items) cudaFree(b->d_items);
+    if (b->d_queue) cudaFree(b->d_queue);
+    delete b;
+    return PT_ERR_OOM;
+  }
+  *out = b;
+  return PT_OK;
+}
+
+extern "C" int pt_batch_run(pt_batch* b, void* stream) {
+  if (!b) return PT_ERR_ARG;
+  cudaStream_t cs = (cudaStream_t)stream;
+  if (cudaMemsetAsync(b->d_queue, 0, 2 * sizeof(unsigned), cs) != cudaSuccess) return PT_ERR_CUDA;
+  const size_t smem = (size_t)(b->block / 32) * kJobBytes;
+  const BatchItem* adj_items = b->d_items + b->n_items;
+  if (b->layout == PT_BVH_WIDE) {
+    batch_kernel<false, PT_BVH_WIDE><<<b->grid, b->block, smem, cs>>>(b->d_jobs, b->d_items, b->n_items, b->tile,
+                                                                        b->d_queue);
+    if (b->n_adj_items)
+      batch_kernel<true, PT_BVH_WIDE><<<b->grid, b->block, smem, cs>>>(b->d_jobs, adj_items, b->n_adj_items, b->tile,
+                                                                         b->d_queue + 1);
+  } else {
+    batch_kernel<false, PT_BVH_BINARY><<<b->grid, b->block, smem, cs>>>(b->d_jobs, b->d_items, b->n_items, b->tile,
+                                                                          b->d_queue);
+    if (b->n_adj_items)
+      batch_kernel<true, PT_BVH_BINARY><<<b->grid, b->block, smem, cs>>>(b->d_jobs, adj_items, b->n_adj_items,
+                                                                           b->tile, b->d_queue + 1);
+  }
+  return cudaGetLastError() == cudaSuccess ? PT_OK : PT_ERR_CUDA;
+}
+
+extern "C" int pt_batch_info(const pt_batch* b, int* n_items) {
+  if (!b || !n_items) return PT_ERR_ARG;
+  *n_items = b->n_items;
+  return PT_OK;
+}
+
+extern "C" void pt_batch_destroy(pt_batch* b) {
+  if (!b) return;
+  cudaDeviceSynchronize();
+  cudaFree(b->d_jobs);
+  cudaFree(b->d_items);
+  cudaFree(b->d_queue);
+  delete b;
+}
+
+extern "C" int pt_render_batch(const pt_job* jobs, int n_jobs, const pt_batch_opts* o, void* stream) {
+  pt_batch* b = nullptr;
+  int st = pt_batch_create(jobs, n_jobs, o, &b);
+  if (st != PT_OK) return st;
+  st = pt_batch_run(b, stream);
+  if (st == PT_OK && cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) st = PT_ERR_CUDA;
+  pt_batch_destroy(b);
+  return st;
 }
