@@ -257,6 +257,33 @@ void pt_batch_destroy(pt_batch* batch);
 /* create + run + synchronise + destroy. */
 int pt_render_batch(const pt_job* jobs, int n_jobs, const pt_batch_opts* opts, void* stream);
 
+/* Batched render that allocates no device memory (no counterpart in the paper).
+ * For callers that may not call cudaMalloc: code running inside a host application
+ * or framework that owns the whole device-memory budget, or that forbids device
+ * allocation once it has started.  It does the work of pt_batch_create +
+ * pt_batch_run, but its scratch -- the job table, the forward and adjoint work lists
+ * and the two work counters -- lives in one file-scope device array of about
+ * PT_NOALLOC_MAX_JOBS * 3.6 KB + 2 * PT_NOALLOC_MAX_ITEMS * 12 B (~1.8 MB), which
+ * every GPU that loads the library holds until the process exits.  The caller
+ * still passes inputs and outputs (jobs, with their images, targets, parameters and
+ * gradient buffers).
+ *   - Limits: n_jobs <= PT_NOALLOC_MAX_JOBS and at most PT_NOALLOC_MAX_ITEMS tiles
+ *     in total (ceil(w/tile) * ceil(h/tile) summed over jobs); larger requests
+ *     return PT_ERR_ARG before anything is launched (use a larger tile, or
+ *     pt_batch_create).
+ *   - The first call on a device (with that device current) looks up the array's
+ *     device address with cudaGetSymbolAddress; make that first call before any
+ *     stream capture.
+ *   - Every call reuses the same array, which keeps the last call's contents; the
+ *     work counters are cleared on `stream` before each launch.  Calls whose work
+ *     overlaps on the GPU (other streams, or other host threads) race on the array:
+ *     serialise them.
+ *   - Asynchronous on `stream`; the host-side tables are copied with
+ *     cudaMemcpyAsync from pageable memory, which returns once they are consumed. */
+#define PT_NOALLOC_MAX_JOBS 64
+#define PT_NOALLOC_MAX_ITEMS 65536
+int pt_render_batch_noalloc(const pt_job* jobs, int n_jobs, const pt_batch_opts* opts, void* stream);
+
 /* Reads (and clears) the scene's device status word after synchronising
  * `stream`: *out = PT_OK or the first PT_ERR_* a kernel recorded. */
 int pt_last_device_status(pt_scene* scene, void* stream, int* out);

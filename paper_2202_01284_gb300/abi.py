@@ -139,6 +139,7 @@ SIGNATURES = {
     "pt_batch_info": ([C.c_void_p, C.POINTER(C.c_int)], C.c_int),
     "pt_batch_destroy": ([C.c_void_p], None),
     "pt_render_batch": ([C.c_void_p, C.c_int, C.POINTER(pt_batch_opts), C.c_void_p], C.c_int),
+    "pt_render_batch_noalloc": ([C.c_void_p, C.c_int, C.POINTER(pt_batch_opts), C.c_void_p], C.c_int),
     "pt_cache_read_records": ([C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_int)],
                               C.c_int),
 }
@@ -401,3 +402,16 @@ def pt_batch_info(handle: int) -> int:
 def pt_batch_destroy(handle: int) -> None:
     if handle:
         load().pt_batch_destroy(handle)
+
+
+def pt_render_batch(jobs, opts, stream: int = 0) -> None:
+    arr = (pt_job * len(jobs))(*jobs)
+    check("pt_render_batch", load().pt_render_batch(C.cast(arr, C.c_void_p), len(jobs), C.byref(opts),
+                                                    stream or None))
+
+
+def pt_render_batch_noalloc(jobs, opts, stream: int = 0) -> None:
+    """Batched render whose scratch is a static device array (no device allocation)."""
+    arr = (pt_job * len(jobs))(*jobs)
+    check("pt_render_batch_noalloc", load().pt_render_batch_noalloc(C.cast(arr, C.c_void_p), len(jobs),
+                                                                    C.byref(opts), stream or None))

@@ -3,6 +3,7 @@
 #include <cmath>
 #include <cstddef>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -1068,4 +1069,140 @@ extern "C" int pt_render_batch(const pt_job* jobs, int n_jobs, const pt_batch_op
   if (st == PT_OK && cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) st = PT_ERR_CUDA;
   pt_batch_destroy(b);
   return st;
+}
+
+// ---------------------------------------------------------------- batch without device allocation
+// Scratch of pt_render_batch_noalloc: work counters, the job table and the
+// forward / adjoint work lists, in one file-scope device array.  Every GPU that
+// loads the library holds it until the process exits.
+namespace {
+constexpr size_t kNoAllocQueueBytes = 256;
+constexpr size_t kNoAllocJobsBytes = (size_t)PT_NOALLOC_MAX_JOBS * sizeof(LaunchArgs);
+constexpr size_t kNoAllocItemsBytes = (size_t)2 * PT_NOALLOC_MAX_ITEMS * sizeof(BatchItem);
+constexpr size_t kNoAllocBytes = kNoAllocQueueBytes + (kNoAllocJobsBytes + 255) / 256 * 256 + kNoAllocItemsBytes;
+}  // namespace
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+namespace {
+// Device address of g_noalloc_scratch per device, looked up on the first call made
+// with that device current (host code only sees a stand-in symbol).
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[64] = {nullptr};
+
+int noalloc_scratch(void** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return PT_ERR_CUDA;
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+      cudaGetLastError();
+      return PT_ERR_CUDA;
+    }
+    g_noalloc_addr[dev] = p;
+  }
+  *out = g_noalloc_addr[dev];
+  return PT_OK;
+}
+}  // namespace
+
+extern "C" int pt_render_batch_noalloc(const pt_job* jobs, int n_jobs, const pt_batch_opts* o, void* stream) {
+  if (!jobs || n_jobs <= 0) return PT_ERR_ARG;
+  if (n_jobs > PT_NOALLOC_MAX_JOBS) return PT_ERR_ARG;
+  pt_batch_opts opts{4, 4, 4, 128};
+  if (o) opts = *o;
+  if (opts.tile < 1 || opts.tile > 256 || opts.ctas_per_sm < 1 || opts.ctas_per_sm > 8) return PT_ERR_ARG;
+  if (opts.block_size <= 0) opts.block_size = 128;
+  if (opts.block_size % 32 || opts.block_size > 256) return PT_ERR_ARG;
+  const int lp = opts.lanes_per_pixel > 0 ? opts.lanes_per_pixel : 8;
+  if (lp > 32 || (lp & (lp - 1))) return PT_ERR_ARG;
+  // job table and work lists on the host, exactly as pt_batch_create builds them
+  std::vector<LaunchArgs> args(n_jobs);
+  std::vector<BatchItem> items;
+  std::vector<long long> cost;
+  int layout = -1;
+  for (int j = 0; j < n_jobs; ++j) {
+    const pt_job& jb = jobs[j];
+    if (!jb.scene || !jb.image) return PT_ERR_ARG;
+    pt_render_desc r;
+    std::memset(&r, 0, sizeof r);
+    r.n_cams = 1;
+    r.cams = &jb.camera;
+    r.width = jb.width;
+    r.height = jb.height;
+    r.spp = jb.spp;
+    r.max_depth = jb.max_depth;
+    r.rr_depth = jb.rr_depth;
+    r.nee = jb.nee;
+    r.seed = jb.seed;
+    r.lanes_per_pixel = std::min(lp, std::max(1, jb.spp));
+    while (r.lanes_per_pixel & (r.lanes_per_pixel - 1)) --r.lanes_per_pixel;
+    LaunchArgs& A = args[j];
+    const int st = fill_launch(jb.scene, &r, &jb.params, A);
+    if (st != PT_OK) return st;
+    if (layout < 0) layout = jb.scene->dev.layout;
+    if (jb.scene->dev.layout != layout) return PT_ERR_ARG;
+    A.seed_adj = jb.backward_seed;
+    A.image = jb.image;
+    A.target = jb.target;
+    A.grad_image = nullptr;
+    A.loss_scale = 1.0f / (3.0f * jb.width * jb.height);
+    A.grads.albedo = jb.grads.albedo;
+    A.grads.rough = jb.grads.roughness;
+    for (int t = 0; t < PT_MAX_TEX; ++t) A.grads.tex[t] = reinterpret_cast<float4*>(jb.grads.tex[t]);
+    A.grads.n_albedo = jb.params.n_albedo;
+    A.grads.n_rough = jb.params.n_rough;
+    A.grads.smem_albedo = 0;
+    A.grads.smem_rough = 0;
+    for (int y0 = 0; y0 < jb.height; y0 += opts.tile)
+      for (int x0 = 0; x0 < jb.width; x0 += opts.tile) {
+        items.push_back({j, x0, y0});
+        cost.push_back((long long)jb.spp * std::min(opts.tile, jb.width - x0) * std::min(opts.tile, jb.height - y0) *
+                       (jb.target ? 3 : 1));
+      }
+  }
+  if ((long long)items.size() > PT_NOALLOC_MAX_ITEMS) return PT_ERR_ARG;
+  std::vector<int> order(items.size());
+  for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+  std::vector<BatchItem> sorted;
+  sorted.reserve(2 * items.size());
+  for (size_t i = 0; i < order.size(); ++i) sorted.push_back(items[order[i]]);
+  const int n_fwd = (int)sorted.size();
+  for (size_t i = 0; i < order.size(); ++i)
+    if (jobs[items[order[i]].job].target) sorted.push_back(items[order[i]]);
+  const int n_adj = (int)sorted.size() - n_fwd;
+  // scratch: the static array, no allocation
+  void* base = nullptr;
+  int st = noalloc_scratch(&base);
+  if (st != PT_OK) return st;
+  unsigned char* p = static_cast<unsigned char*>(base);
+  unsigned* d_queue = reinterpret_cast<unsigned*>(p);
+  LaunchArgs* d_jobs = reinterpret_cast<LaunchArgs*>(p + kNoAllocQueueBytes);
+  BatchItem* d_items = reinterpret_cast<BatchItem*>(p + kNoAllocQueueBytes + (kNoAllocJobsBytes + 255) / 256 * 256);
+  cudaStream_t cs = (cudaStream_t)stream;
+  // pageable sources: each copy returns once the host buffer has been consumed
+  if (cudaMemcpyAsync(d_jobs, args.data(), sizeof(LaunchArgs) * n_jobs, cudaMemcpyHostToDevice, cs) != cudaSuccess ||
+      cudaMemcpyAsync(d_items, sorted.data(), sizeof(BatchItem) * sorted.size(), cudaMemcpyHostToDevice, cs) !=
+          cudaSuccess ||
+      cudaMemsetAsync(d_queue, 0, 2 * sizeof(unsigned), cs) != cudaSuccess)
+    return PT_ERR_CUDA;
+  int dev = 0, sms = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int grid = sms * opts.ctas_per_sm;
+  const size_t smem = (size_t)(opts.block_size / 32) * kJobBytes;
+  if (layout == PT_BVH_WIDE) {
+    batch_kernel<false, PT_BVH_WIDE><<<grid, opts.block_size, smem, cs>>>(d_jobs, d_items, n_fwd, opts.tile, d_queue);
+    if (n_adj)
+      batch_kernel<true, PT_BVH_WIDE><<<grid, opts.block_size, smem, cs>>>(d_jobs, d_items + n_fwd, n_adj, opts.tile,
+                                                                             d_queue + 1);
+  } else {
+    batch_kernel<false, PT_BVH_BINARY><<<grid, opts.block_size, smem, cs>>>(d_jobs, d_items, n_fwd, opts.tile,
+                                                                              d_queue);
+    if (n_adj)
+      batch_kernel<true, PT_BVH_BINARY><<<grid, opts.block_size, smem, cs>>>(d_jobs, d_items + n_fwd, n_adj,
+                                                                               opts.tile, d_queue + 1);
+  }
+  return cudaGetLastError() == cudaSuccess ? PT_OK : PT_ERR_CUDA;
 }
