@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--batch", action="store_true",
                     help="batching experiment: 64 cameras over 10k/200k/2M-triangle scenes, forward + adjoint "
                          "in one persistent graph-captured launch vs 64 separate launches (own JSON line)")
+    ap.add_argument("--peaks", action="store_true",
+                    help="microbenchmarks of the memory-side roofs (L2-resident reads, atomics) as a JSON line")
     ap.add_argument("--small", action="store_true",
                     help="profiling case: same scene and step at 256x256, 64 spp (not a bench line)")
     return ap.parse_args()
@@ -185,6 +187,8 @@ def run_ours(args):
     from paper_2202_01284_gb300 import abi
     from paper_2202_01284_gb300.render import DeviceScene
 
+    from paper_2202_01284_gb300 import dist as D
+
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -197,7 +201,7 @@ def run_ours(args):
     sc, tgt_tex = make_workload(small=args.small)
     layout = abi.PT_BVH_WIDE if args.bvh == "wide" else abi.PT_BVH_BINARY
     ds = DeviceScene(sc, layout=layout, device=dev)
-    seed_fwd, seed_bwd = 1000 + 2 * rank, 1001 + 2 * rank
+    seed_fwd, seed_bwd = D.rank_seeds(rank)  # replicas: every rank renders its own samples
     st_f = settings(args, seed_fwd)
     # fixed target image (rendered once) -> dLoss/dImage for the adjoint
     target = ds.forward(settings(args, 77), textures=[torch.as_tensor(tgt_tex, device=dev)]).clone()
@@ -260,11 +264,7 @@ def run_ours(args):
     fwd_ms = [e[0].elapsed_time(e[1]) for e in evs]
     adj_ms = [e[2].elapsed_time(e[3]) for e in evs]
     step_ms = [e[0].elapsed_time(e[3]) for e in evs]
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = D.max_over_ranks(sum(step_ms), device=dev)
     value = rays_step * args.steps * world / (total_ms / 1e3) / 1e6
 
     # ---- end to end through the C ABI with host buffers (pinned), copies inside the timed region
@@ -534,8 +534,49 @@ def run_batch_experiment(args):
     print(json.dumps(out), flush=True)
 
 
+def run_peaks(args):
+    """L2-resident read bandwidth and float atomic throughput (spread vs colliding
+    addresses), measured with torch's reduction and index_add_ kernels."""
+    import torch
+    torch.cuda.set_device(0)
+
+    def t_ms(fn, reps=20):
+        fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(True), torch.cuda.Event(True)
+        a.record()
+        for _ in range(reps):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+    out = {"metric": "memory-side roofs (own microbenchmarks)"}
+    x = torch.rand(16 * 1024 * 1024, device="cuda")            # 64 MB: L2 resident after the first pass
+    ms = t_ms(lambda: x.sum())
+    out["l2_read_gbs"] = round(x.numel() * 4 / ms / 1e6, 1)
+    big = torch.rand(1024 * 1024 * 1024 // 4 * 2, device="cuda")  # 2 GB: HBM
+    ms = t_ms(lambda: big.sum(), reps=5)
+    out["hbm_read_gbs"] = round(big.numel() * 4 / ms / 1e6, 1)
+    del big
+    n = 1 << 24
+    vals = torch.rand(n, device="cuda")
+    for name, m in (("spread_16M_targets", n), ("spread_1M_targets", 1 << 20), ("colliding_96_targets", 96),
+                    ("colliding_15_targets", 15)):
+        idx = torch.randint(0, m, (n,), device="cuda")
+        dst = torch.zeros(m, device="cuda")
+        ms = t_ms(lambda: dst.index_add_(0, idx, vals))
+        out[f"atomic_add_f32_{name}_gops"] = round(n / ms / 1e6, 2)
+    props = torch.cuda.get_device_properties(0)
+    out["sms"] = props.multi_processor_count
+    out["fp32_peak_tflops_at_2070mhz"] = round(props.multi_processor_count * 128 * 2 * 2070e6 / 1e12, 2)
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
+    if args.peaks:
+        run_peaks(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     elif args.cache:
