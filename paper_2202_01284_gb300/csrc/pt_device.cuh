@@ -516,12 +516,12 @@ __device__ __forceinline__ BsdfSample bsdf_sample(const Material& m, float3 wi, 
   return s;
 }
 
-// Polymorphic call over the BSDF type.  MATCH: the warp votes once per type and
-// runs each type's code with only its lanes active (ballot grouping); SWITCH:
-// plain per-lane branch.
-template <class F>
-__device__ __forceinline__ void dispatch_bsdf(int mode, int type, F&& f) {
-  if (mode == PT_DISPATCH_MATCH) {
+// Polymorphic call over the BSDF type (compile-time dispatch mode).  MATCH: the
+// warp votes once per type and runs each type's code with only its lanes active
+// (ballot grouping); SWITCH: plain per-lane branch.
+template <int MODE, class F>
+__device__ __forceinline__ void dispatch_bsdf(int type, F&& f) {
+  if constexpr (MODE == PT_DISPATCH_MATCH) {
     unsigned active = __activemask();
     if (__any_sync(active, type == PT_BSDF_DIFFUSE)) { if (type == PT_BSDF_DIFFUSE) f.template operator()<PT_BSDF_DIFFUSE>(); }
     if (__any_sync(active, type == PT_BSDF_CONDUCTOR)) { if (type == PT_BSDF_CONDUCTOR) f.template operator()<PT_BSDF_CONDUCTOR>(); }

@@ -66,11 +66,12 @@ struct DevGrads {
   float4* tex[PT_MAX_TEX];
   float* rough;
   int n_albedo, n_rough;
-  int smem_albedo, smem_rough;  // per-CTA shared-memory staging of these (0/1)
 };
 
-// Everything one render launch needs (passed by value as the kernel parameter).
-struct LaunchArgs {
+// Everything one render launch needs (passed by value as the kernel parameter;
+// batched launches keep arrays of them in device memory and copy records with
+// 16-byte loads, hence the alignment).
+struct alignas(16) LaunchArgs {
   DevScene scene;
   DevParams params;
   DevGrads grads;
@@ -100,6 +101,7 @@ struct LaunchArgs {
   long long max_records;
   DevCamera cams[PT_MAX_CAMS];
 };
+static_assert(sizeof(LaunchArgs) % 16 == 0, "job records are copied with 16-byte loads");
 
 // Implemented in pt_nrc.cu (radiance-cache kernels used by the render launchers).
 int cache_infer(pt_cache* c, const float* raw, float* rgb, long long n, cudaStream_t st);

@@ -12,12 +12,12 @@
 namespace ptgb {
 
 // Per-vertex gradient sink of the adjoint: warp-aggregated atomics.
-// Constant-albedo rows and roughness entries are few and heavily shared, so
-// they are reduced per warp and staged in shared memory per CTA; texels are
-// many and rarely shared, so aggregation is optional for them.
+// Constant-albedo rows and roughness entries are few and heavily shared, so the
+// lanes of a warp that hit the same entry are reduced with a shuffle tree and one
+// lane issues the atomic; texels are many and rarely shared, so aggregation is
+// optional for them.  (No per-CTA shared-memory staging: its end-of-CTA barrier
+// kept finished warps resident and cost more than the atomics it saved.)
 struct GradSink {
-  float* s_alb;    // shared staging (or nullptr -> global)
-  float* s_rough;
   template <bool INSTR>
   __device__ __forceinline__ void add(const LaunchArgs& A, const Material& m, float3 g_alb, float g_alpha,
                                       Counters<INSTR>& cnt) {
@@ -57,10 +57,9 @@ struct GradSink {
       cnt.add(7, 1);
       float v[3] = {g_alb.x, g_alb.y, g_alb.z};
       if (warp_aggregate<3>((unsigned)m.alb_ref, v)) {
-        float* dst = s_alb ? s_alb : G.albedo;
-        atomicAdd(&dst[3 * m.alb_ref + 0], v[0]);
-        atomicAdd(&dst[3 * m.alb_ref + 1], v[1]);
-        atomicAdd(&dst[3 * m.alb_ref + 2], v[2]);
+        atomicAdd(&G.albedo[3 * m.alb_ref + 0], v[0]);
+        atomicAdd(&G.albedo[3 * m.alb_ref + 1], v[1]);
+        atomicAdd(&G.albedo[3 * m.alb_ref + 2], v[2]);
         cnt.add(6, 1);
       }
     }
@@ -68,8 +67,7 @@ struct GradSink {
       cnt.add(7, 1);
       float v[1] = {g_alpha};
       if (warp_aggregate<1>((unsigned)m.rough, v)) {
-        float* dst = s_rough ? s_rough : G.rough;
-        atomicAdd(&dst[m.rough], v[0]);
+        atomicAdd(&G.rough[m.rough], v[0]);
         cnt.add(6, 1);
       }
     }
@@ -140,7 +138,7 @@ __device__ __forceinline__ void path_start(const LaunchArgs& A, PathState& P, un
 }
 
 // Shading step after the closest hit.  Returns false if the path ended here.
-template <bool ADJ, bool INSTR>
+template <bool ADJ, bool INSTR, int DISPATCH>
 __device__ __forceinline__ bool path_shade(const LaunchArgs& A, PathState& P, const Hit& hit, bool grad_pass,
                                            Counters<INSTR>& cnt) {
   const DevScene& S = A.scene;
@@ -330,7 +328,7 @@ __device__ __forceinline__ bool path_shade(const LaunchArgs& A, PathState& P, co
     }
     const float3 wl = fr.to_local(dir);
     BsdfEval ev;
-    dispatch_bsdf(A.dispatch, type, [&]<int T>() {
+    dispatch_bsdf<DISPATCH>(type, [&]<int T>() {
       if constexpr (T != PT_BSDF_DIELECTRIC) ev = bsdf_eval<T, ADJ>(m, wi, wl);
     });
     if (valid && wl.z > 0.0f && max3f(ev.f) > 0.0f) {
@@ -348,7 +346,7 @@ __device__ __forceinline__ bool path_shade(const LaunchArgs& A, PathState& P, co
   }
   // ---- BSDF sampling (detached) with its attached value
   BsdfSample bs;
-  dispatch_bsdf(A.dispatch, type, [&]<int T>() { bs = bsdf_sample<T, ADJ>(m, wi, entering, u[3], u[4], u[5]); });
+  dispatch_bsdf<DISPATCH>(type, [&]<int T>() { bs = bsdf_sample<T, ADJ>(m, wi, entering, u[3], u[4], u[5]); });
   P.lobe = bs.lobe;
   P.ok_next = bs.ok;
   P.delta_next = bs.delta;
@@ -461,28 +459,15 @@ __device__ __forceinline__ bool unit_pixel(const LaunchArgs& A, long long unit, 
 // Each thread owns the samples s = lane_in_pixel + k * lanes_per_pixel of one
 // pixel; in the adjoint every sample is traced twice (pass 0: radiance L,
 // pass 1: replay with L_rem and gradient scatter) by the same code.
-template <bool ADJ, bool INSTR, int LAYOUT>
-__device__ __forceinline__ void megakernel(const LaunchArgs& A, float* smem, long long unit, const Tile& tile) {
-  const DevGrads& G = A.grads;
-  float* s_alb = nullptr;
-  float* s_rough = nullptr;
-  int n_stage = 0;
-  if constexpr (ADJ) {
-    s_alb = G.smem_albedo ? smem : nullptr;
-    s_rough = G.smem_rough ? smem + (G.smem_albedo ? 3 * G.n_albedo : 0) : nullptr;
-    n_stage = (G.smem_albedo ? 3 * G.n_albedo : 0) + (G.smem_rough ? G.n_rough : 0);
-    if (n_stage > 0) {  // uniform over the CTA
-      for (int i = threadIdx.x; i < n_stage; i += blockDim.x) smem[i] = 0.0f;
-      __syncthreads();
-    }
-  }
+template <bool ADJ, bool INSTR, int LAYOUT, int DISPATCH>
+__device__ __forceinline__ void megakernel(const LaunchArgs& A, long long unit, const Tile& tile) {
   PixelOf px{};
   const bool valid = unit_pixel(A, unit, tile, px);
   Counters<INSTR> cnt;
   if constexpr (INSTR) {
     for (int i = 0; i < 8; ++i) cnt.c[i] = 0;
   }
-  GradSink sink{s_alb, s_rough};
+  GradSink sink;
   const int lane_in_pix = (int)(unit & (A.lanes_per_pixel - 1));
   float3 dl = f3(0.f, 0.f, 0.f);
   if (valid) {
@@ -523,7 +508,7 @@ __device__ __forceinline__ void megakernel(const LaunchArgs& A, float* smem, lon
       const bool grad_pass = ADJ && pass == 1;
       bool alive = true, finish = true, occ = false;
       if (!want_shadow) {
-        alive = path_shade<ADJ, INSTR>(A, P, hit, grad_pass, cnt);
+        alive = path_shade<ADJ, INSTR, DISPATCH>(A, P, hit, grad_pass, cnt);
         finish = alive && !P.has_shadow;
         want_shadow = alive && P.has_shadow;
       } else {
@@ -580,15 +565,6 @@ __device__ __forceinline__ void megakernel(const LaunchArgs& A, float* smem, lon
       A.image[3 * px.pix + 1] = pix_sum.y * inv;
       A.image[3 * px.pix + 2] = pix_sum.z * inv;
     }
-  } else if (n_stage > 0) {
-    __syncthreads();
-    for (int i = threadIdx.x; i < n_stage; i += blockDim.x) {
-      const float v = smem[i];
-      if (v != 0.0f) {
-        if (G.smem_albedo && i < 3 * G.n_albedo) atomicAdd(&G.albedo[i], v);
-        else atomicAdd(&G.rough[i - (G.smem_albedo ? 3 * G.n_albedo : 0)], v);
-      }
-    }
   }
   flush_counters<INSTR>(A, cnt);
 }
@@ -608,15 +584,14 @@ __device__ __forceinline__ Tile crop_tile(const LaunchArgs& A) {
   return Tile{A.crop_x0, A.crop_y0, A.crop_w, A.crop_h, A.n_cams};
 }
 
-template <bool INSTR, int LAYOUT>
+template <bool INSTR, int LAYOUT, int DISPATCH>
 __global__ void __launch_bounds__(256, PT_FWD_MIN_BLOCKS) forward_kernel(const __grid_constant__ LaunchArgs A) {
-  megakernel<false, INSTR, LAYOUT>(A, nullptr, (long long)blockIdx.x * blockDim.x + threadIdx.x, crop_tile(A));
+  megakernel<false, INSTR, LAYOUT, DISPATCH>(A, (long long)blockIdx.x * blockDim.x + threadIdx.x, crop_tile(A));
 }
 
-template <bool INSTR, int LAYOUT>
+template <bool INSTR, int LAYOUT, int DISPATCH>
 __global__ void __launch_bounds__(256, PT_ADJ_MIN_BLOCKS) adjoint_kernel(const __grid_constant__ LaunchArgs A) {
-  extern __shared__ float smem[];
-  megakernel<true, INSTR, LAYOUT>(A, smem, (long long)blockIdx.x * blockDim.x + threadIdx.x, crop_tile(A));
+  megakernel<true, INSTR, LAYOUT, DISPATCH>(A, (long long)blockIdx.x * blockDim.x + threadIdx.x, crop_tile(A));
 }
 
 // image[pix] += sum_s q_beta[slot] * max(q_rgb[slot], 0) / spp  (cache-terminated render)
@@ -695,7 +670,7 @@ __global__ void __launch_bounds__(256, PT_ADJ_MIN_BLOCKS)
     }
     const Tile t{bi.x0, bi.y0, tile, tile, 1};
     const long long units = (long long)tile * tile * A.lanes_per_pixel;
-    for (long long b = 0; b < units; b += 32) megakernel<ADJ, false, LAYOUT>(A, nullptr, b + lane, t);
+    for (long long b = 0; b < units; b += 32) megakernel<ADJ, false, LAYOUT, PT_DISPATCH_SWITCH>(A, b + lane, t);
   }
 }
 
@@ -808,11 +783,18 @@ int launch_forward(pt_scene* s, const pt_render_desc* r, const LaunchArgs& A, cu
   long long grid;
   int st = launch_dims(r, A, block, grid);
   if (st != PT_OK) return st;
-  const bool ins = instrumented(r), wide = s->dev.layout == PT_BVH_WIDE;
-  if (ins && wide) forward_kernel<true, PT_BVH_WIDE><<<(unsigned)grid, block, 0, cs>>>(A);
-  else if (ins) forward_kernel<true, PT_BVH_BINARY><<<(unsigned)grid, block, 0, cs>>>(A);
-  else if (wide) forward_kernel<false, PT_BVH_WIDE><<<(unsigned)grid, block, 0, cs>>>(A);
-  else forward_kernel<false, PT_BVH_BINARY><<<(unsigned)grid, block, 0, cs>>>(A);
+  const int v = (instrumented(r) ? 4 : 0) | (s->dev.layout == PT_BVH_WIDE ? 2 : 0) | (A.dispatch == PT_DISPATCH_MATCH ? 1 : 0);
+  const dim3 g((unsigned)grid), b(block);
+  switch (v) {
+    case 0: forward_kernel<false, PT_BVH_BINARY, PT_DISPATCH_SWITCH><<<g, b, 0, cs>>>(A); break;
+    case 1: forward_kernel<false, PT_BVH_BINARY, PT_DISPATCH_MATCH><<<g, b, 0, cs>>>(A); break;
+    case 2: forward_kernel<false, PT_BVH_WIDE, PT_DISPATCH_SWITCH><<<g, b, 0, cs>>>(A); break;
+    case 3: forward_kernel<false, PT_BVH_WIDE, PT_DISPATCH_MATCH><<<g, b, 0, cs>>>(A); break;
+    case 4: forward_kernel<true, PT_BVH_BINARY, PT_DISPATCH_SWITCH><<<g, b, 0, cs>>>(A); break;
+    case 5: forward_kernel<true, PT_BVH_BINARY, PT_DISPATCH_MATCH><<<g, b, 0, cs>>>(A); break;
+    case 6: forward_kernel<true, PT_BVH_WIDE, PT_DISPATCH_SWITCH><<<g, b, 0, cs>>>(A); break;
+    default: forward_kernel<true, PT_BVH_WIDE, PT_DISPATCH_MATCH><<<g, b, 0, cs>>>(A); break;
+  }
   return cudaGetLastError() == cudaSuccess ? PT_OK : PT_ERR_CUDA;
 }
 
@@ -863,13 +845,6 @@ extern "C" int pt_render_backward(pt_scene* s, const pt_render_desc* r, const pt
   for (int t = 0; t < PT_MAX_TEX; ++t) A.grads.tex[t] = reinterpret_cast<float4*>(g->tex[t]);
   A.grads.n_albedo = p->n_albedo;
   A.grads.n_rough = p->n_rough;
-  // stage the small, heavily shared gradient vectors in shared memory
-  size_t smem = 0;
-  A.grads.smem_albedo = (g->albedo && p->n_albedo > 0 && 3 * p->n_albedo <= 3072) ? 1 : 0;
-  if (A.grads.smem_albedo) smem += 3 * (size_t)p->n_albedo;
-  A.grads.smem_rough = (g->roughness && p->n_rough > 0 && smem + p->n_rough <= 6144) ? 1 : 0;
-  if (A.grads.smem_rough) smem += (size_t)p->n_rough;
-  smem *= sizeof(float);
   int block;
   long long grid;
   if ((st = launch_dims(r, A, block, grid)) != PT_OK) return st;
@@ -881,11 +856,18 @@ extern "C" int pt_render_backward(pt_scene* s, const pt_render_desc* r, const pt
     A.cache_bounce = r->cache_bounce;
     A.q_rgb = cache_buffers(r->cache).q_rgb;
   }
-  const bool ins = instrumented(r), wide = s->dev.layout == PT_BVH_WIDE;
-  if (ins && wide) adjoint_kernel<true, PT_BVH_WIDE><<<(unsigned)grid, block, smem, cs>>>(A);
-  else if (ins) adjoint_kernel<true, PT_BVH_BINARY><<<(unsigned)grid, block, smem, cs>>>(A);
-  else if (wide) adjoint_kernel<false, PT_BVH_WIDE><<<(unsigned)grid, block, smem, cs>>>(A);
-  else adjoint_kernel<false, PT_BVH_BINARY><<<(unsigned)grid, block, smem, cs>>>(A);
+  const int v = (instrumented(r) ? 4 : 0) | (s->dev.layout == PT_BVH_WIDE ? 2 : 0) | (A.dispatch == PT_DISPATCH_MATCH ? 1 : 0);
+  const dim3 gd((unsigned)grid), bd(block);
+  switch (v) {
+    case 0: adjoint_kernel<false, PT_BVH_BINARY, PT_DISPATCH_SWITCH><<<gd, bd, 0, cs>>>(A); break;
+    case 1: adjoint_kernel<false, PT_BVH_BINARY, PT_DISPATCH_MATCH><<<gd, bd, 0, cs>>>(A); break;
+    case 2: adjoint_kernel<false, PT_BVH_WIDE, PT_DISPATCH_SWITCH><<<gd, bd, 0, cs>>>(A); break;
+    case 3: adjoint_kernel<false, PT_BVH_WIDE, PT_DISPATCH_MATCH><<<gd, bd, 0, cs>>>(A); break;
+    case 4: adjoint_kernel<true, PT_BVH_BINARY, PT_DISPATCH_SWITCH><<<gd, bd, 0, cs>>>(A); break;
+    case 5: adjoint_kernel<true, PT_BVH_BINARY, PT_DISPATCH_MATCH><<<gd, bd, 0, cs>>>(A); break;
+    case 6: adjoint_kernel<true, PT_BVH_WIDE, PT_DISPATCH_SWITCH><<<gd, bd, 0, cs>>>(A); break;
+    default: adjoint_kernel<true, PT_BVH_WIDE, PT_DISPATCH_MATCH><<<gd, bd, 0, cs>>>(A); break;
+  }
   return cudaGetLastError() == cudaSuccess ? PT_OK : PT_ERR_CUDA;
 }
 
@@ -974,10 +956,6 @@ extern "C" int pt_batch_create(const pt_job* jobs, int n_jobs, const pt_batch_op
     for (int t = 0; t < PT_MAX_TEX; ++t) A.grads.tex[t] = reinterpret_cast<float4*>(jb.grads.tex[t]);
     A.grads.n_albedo = jb.params.n_albedo;
     A.grads.n_rough = jb.params.n_rough;
-    // no shared-memory staging of gradients in the persistent kernel: it would put two
-    // CTA barriers into every tile; warp-aggregated global atomics are used instead
-    A.grads.smem_albedo = 0;
-    A.grads.smem_rough = 0;
     for (int y0 = 0; y0 < jb.height; y0 += opts.tile)
       for (int x0 = 0; x0 < jb.width; x0 += opts.tile) {
         items.push_back({j, x0, y0});
@@ -1152,8 +1130,6 @@ extern "C" int pt_render_batch_noalloc(const pt_job* jobs, int n_jobs, const pt_
     for (int t = 0; t < PT_MAX_TEX; ++t) A.grads.tex[t] = reinterpret_cast<float4*>(jb.grads.tex[t]);
     A.grads.n_albedo = jb.params.n_albedo;
     A.grads.n_rough = jb.params.n_rough;
-    A.grads.smem_albedo = 0;
-    A.grads.smem_rough = 0;
     for (int y0 = 0; y0 < jb.height; y0 += opts.tile)
       for (int x0 = 0; x0 < jb.width; x0 += opts.tile) {
         items.push_back({j, x0, y0});
