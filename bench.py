@@ -136,13 +136,19 @@ def settings(args, seed):
                           tex_aggregate=args.tex_aggregate)
 
 
-def cpu_baseline_run(sc, seconds_target=15.0, steps=1):
+# Bounded samples of the workload for the FP64 oracle on the host cores: the
+# CPU-baseline leg of our arm (~10 s on 16 Grace cores) and one step of the
+# reference arm (~3 s, so that --steps 5 --warmup 3 stays well under a minute).
+CPU_BASELINE_CROP = (256, 320, 512, 384)
+REFERENCE_STEP_CROP = (384, 384, 256, 256)
+
+
+def cpu_baseline_run(sc, steps=1, crop=CPU_BASELINE_CROP):
     """The FP64 oracle as it stands on the host cores, on a bounded crop of the workload."""
     import numpy as np
     import oracle
     osc = oracle.OracleScene(sc)
     cam = sc.cameras[0]
-    crop = (448, 448, 128, 128)
     spp = 64
     r = oracle.render_in(cam, spp, WORKLOAD["max_depth"], 11, WORKLOAD["rr_depth"], True, crop=crop)
     cores = os.cpu_count() or 1
@@ -167,9 +173,9 @@ def run_reference(args):
         return
     sc, _ = make_workload()
     steps = max(1, args.steps)
-    for _ in range(max(0, min(args.warmup, 1))):
-        cpu_baseline_run(sc, steps=1)
-    cb = cpu_baseline_run(sc, steps=steps)
+    for _ in range(max(0, args.warmup)):
+        cpu_baseline_run(sc, steps=1, crop=REFERENCE_STEP_CROP)
+    cb = cpu_baseline_run(sc, steps=steps, crop=REFERENCE_STEP_CROP)
     line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": "Mrays/s", "n_gpus": args.gpus,
             "steps": steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
