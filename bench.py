@@ -36,6 +36,10 @@ FLOPS_PER_NODE = {"binary": 44,   # two child slab tests: 12 FMA (24 flops), 10 
                   "wide": 140}    # eight child slab tests: 48 FMA (96 flops), 40 min/max, 8 compares (per-node
                                   # decode: 3 scale + 3 offset products excluded)
 FLOPS_PER_TRI = 45      # Moller-Trumbore: 2 cross, 4 dot, 1 div, 4 mul, 3 sub (FMA = 2 flops)
+# DRAM bytes (read + write) per full-size launch of the production kernels, from one
+# ncu capture of this step (profiles/launches_spheres196k_1024px_64spp.md); set to
+# None whenever the kernels change until they are captured again.
+DRAM_TRAFFIC_PER_LAUNCH = {"wide": {"adjoint_kernel": 105.59e6 + 355.88e6, "forward_kernel": 48.31e6 + 139.58e6}}
 
 
 def parse():
@@ -341,7 +345,7 @@ def run_ours(args):
                    "grad_terms": int(cb[7]), "grad_atomics": int(cb[6])},
         "roofline": {"bound": "alu", "kernel": dom, "achieved": round(achieved, 3),
                      "peak": round(peak_tflops, 2), "unit": "TFLOP/s", "frac": round(achieved / peak_tflops, 4),
-                     "traffic": None,
+                     "traffic": DRAM_TRAFFIC_PER_LAUNCH.get(args.bvh, {}).get(dom) if not args.small else None,
                      "work": f"{FLOPS_PER_NODE[args.bvh]}/node visit + {FLOPS_PER_TRI}/triangle test (counted launch)",
                      "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 x median SM clock {mhz} MHz"},
         "cpu_baseline": cpu,
