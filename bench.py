@@ -39,7 +39,7 @@ FLOPS_PER_TRI = 45      # Moller-Trumbore: 2 cross, 4 dot, 1 div, 4 mul, 3 sub (
 # DRAM bytes (read + write) per full-size launch of the production kernels, from one
 # ncu capture of this step (profiles/launches_spheres196k_1024px_64spp.md); set to
 # None whenever the kernels change until they are captured again.
-DRAM_TRAFFIC_PER_LAUNCH = {"wide": {"adjoint_kernel": 105.59e6 + 355.88e6, "forward_kernel": 48.31e6 + 139.58e6}}
+DRAM_TRAFFIC_PER_LAUNCH = {}
 
 
 def parse():

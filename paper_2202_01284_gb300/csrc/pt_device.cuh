@@ -260,14 +260,16 @@ __device__ __forceinline__ Hit trace_wide(const DevScene& S, float3 ro, float3 r
     uint32_t inner_hits = 0, leaf_hits = 0;
 #pragma unroll
     for (int sl = 0; sl < 8; ++sl) {
-      const int sh = 8 * (sl & 3);
-      const uint32_t meta = ((sl < 4 ? w1.z : w1.w) >> sh) & 0xffu;
-      const float qnx = (float)(((sl < 4 ? nx0 : nx1) >> sh) & 0xffu);
-      const float qfx = (float)(((sl < 4 ? fx0 : fx1) >> sh) & 0xffu);
-      const float qny = (float)(((sl < 4 ? ny0 : ny1) >> sh) & 0xffu);
-      const float qfy = (float)(((sl < 4 ? fy0 : fy1) >> sh) & 0xffu);
-      const float qnz = (float)(((sl < 4 ? nz0 : nz1) >> sh) & 0xffu);
-      const float qfz = (float)(((sl < 4 ? fz0 : fz1) >> sh) & 0xffu);
+      const uint32_t meta = ((sl < 4 ? w1.z : w1.w) >> (8 * (sl & 3))) & 0xffu;
+      // byte q of a plane word -> float q: one byte permute builds 2^23 + q, then
+      // subtract 2^23 (both exact), instead of a shift/mask and an int->float convert
+      const uint32_t sel = 0x7540u | (uint32_t)(sl & 3);
+      const float qnx = __uint_as_float(__byte_perm(sl < 4 ? nx0 : nx1, 0x4B000000u, sel)) - 8388608.0f;
+      const float qfx = __uint_as_float(__byte_perm(sl < 4 ? fx0 : fx1, 0x4B000000u, sel)) - 8388608.0f;
+      const float qny = __uint_as_float(__byte_perm(sl < 4 ? ny0 : ny1, 0x4B000000u, sel)) - 8388608.0f;
+      const float qfy = __uint_as_float(__byte_perm(sl < 4 ? fy0 : fy1, 0x4B000000u, sel)) - 8388608.0f;
+      const float qnz = __uint_as_float(__byte_perm(sl < 4 ? nz0 : nz1, 0x4B000000u, sel)) - 8388608.0f;
+      const float qfz = __uint_as_float(__byte_perm(sl < 4 ? fz0 : fz1, 0x4B000000u, sel)) - 8388608.0f;
       const float tn = fmaxf(fmaxf(fmaf(qnx, ax, bx), fmaf(qny, ay, by)), fmaxf(fmaf(qnz, az, bz), 0.0f));
       const float tf = fminf(fminf(fmaf(qfx, ax, bx), fmaf(qfy, ay, by)), fminf(fmaf(qfz, az, bz), h.t));
       if (meta != 0u && tn <= tf) {

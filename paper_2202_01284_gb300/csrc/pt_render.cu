@@ -573,14 +573,15 @@ __device__ __forceinline__ void megakernel(const LaunchArgs& A, long long unit, 
 }
 
 // Minimum resident CTAs of 256 threads per SM requested from ptxas (register cap).
-// Two CTAs of 256 threads per SM cap both kernels at 128 registers; measured on
-// the 196k-triangle sphere workload this is faster than uncapped (the adjoint
-// would otherwise take ~190 registers and run at half the occupancy).
+// Measured on the 196k-triangle sphere workload (forward + adjoint step): with the
+// per-vertex shading out of line, more resident warps beat fewer spills -- the
+// forward runs best at 4 CTAs (64 registers, 48 vs 62 ms at 128 registers), the
+// adjoint at 3 (85 registers, 135 vs 148 ms).
 #ifndef PT_FWD_MIN_BLOCKS
-#define PT_FWD_MIN_BLOCKS 2
+#define PT_FWD_MIN_BLOCKS 4
 #endif
 #ifndef PT_ADJ_MIN_BLOCKS
-#define PT_ADJ_MIN_BLOCKS 2
+#define PT_ADJ_MIN_BLOCKS 3
 #endif
 
 __device__ __forceinline__ Tile crop_tile(const LaunchArgs& A) {
@@ -649,7 +650,7 @@ constexpr int kJobBytes = (int)((offsetof(LaunchArgs, cams) + sizeof(DevCamera) 
 // Two kernels rather than one keep each at the register footprint of its
 // single-job counterpart (one kernel holding both megakernels spills).
 template <bool ADJ, int LAYOUT>
-__global__ void __launch_bounds__(256, PT_ADJ_MIN_BLOCKS)
+__global__ void __launch_bounds__(256, ADJ ? PT_ADJ_MIN_BLOCKS : PT_FWD_MIN_BLOCKS)
     batch_kernel(const LaunchArgs* __restrict__ jobs, const BatchItem* __restrict__ items, int n_items, int tile,
                  unsigned* __restrict__ queue) {
   extern __shared__ __align__(16) unsigned char job_smem[];
