@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--batch", action="store_true",
                     help="batching experiment: 64 cameras over 10k/200k/2M-triangle scenes, forward + adjoint "
                          "in one persistent graph-captured launch vs 64 separate launches (own JSON line)")
+    ap.add_argument("--jvp", action="store_true",
+                    help="forward-mode image derivative on the throughput workload vs the plain forward (own line)")
     ap.add_argument("--peaks", action="store_true",
                     help="microbenchmarks of the memory-side roofs (L2-resident reads, atomics) as a JSON line")
     ap.add_argument("--small", action="store_true",
@@ -360,6 +362,78 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_jvp_experiment(args):
+    """Forward-mode image derivative on the throughput workload: one pt_render_jvp
+    pass (image and d image / d eps along a direction over the 1024^2 texture and
+    the roughness values) against the plain forward render with the same seed,
+    i.e. the same rays.  Own JSON line."""
+    import torch
+
+    from paper_2202_01284_gb300 import abi
+    from paper_2202_01284_gb300.render import DeviceScene
+    abi.load()
+    dev = torch.device("cuda", 0)
+    sc, _ = make_workload(small=args.small)
+    layout = abi.PT_BVH_WIDE if args.bvh == "wide" else abi.PT_BVH_BINARY
+    ds = DeviceScene(sc, layout=layout, device=dev)
+    st = settings(args, 11)
+    g = torch.Generator(device=dev).manual_seed(5)
+    v_tex = torch.rand(ds.textures[0].shape, device=dev, generator=g)
+    v_tex[..., 3] = 0
+    v_rough = torch.randn(ds.roughness.shape, device=dev, generator=g)
+    img = torch.empty((1, st.height, st.width, 3), device=dev)
+    cf = torch.zeros(abi.PT_N_COUNTERS, dtype=torch.int64, device=dev)
+    ds.forward(st, out=img, counters=cf)
+    torch.cuda.synchronize()
+    cf = cf.cpu().numpy()
+    rays = int(cf[1] + cf[2])
+    flops = FLOPS_PER_NODE[args.bvh] * int(cf[3]) + FLOPS_PER_TRI * int(cf[4])
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def jvp():
+        return ds.jvp(st, t_textures=[v_tex], t_roughness=v_rough)
+    for _ in range(max(3, args.warmup)):
+        jvp()
+        ds.forward(st, out=img)
+    torch.cuda.synchronize()
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    clocks = ClockSampler(0)
+    clocks.start()
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        ev[k][0].record(stream)
+        jvp()
+        ev[k][1].record(stream)
+        flush.fill_(float(k) + 0.5)
+        ev[k][2].record(stream)
+        ds.forward(st, out=img)
+        ev[k][3].record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    jvp_ms = statistics.mean(e[0].elapsed_time(e[1]) for e in ev)
+    fwd_ms = statistics.mean(e[2].elapsed_time(e[3]) for e in ev)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = clk.get("sm_mhz") or 1477.0
+    peak = sms * 128 * 2 * mhz * 1e6 / 1e12
+    achieved = flops / (jvp_ms / 1e3) / 1e12
+    line = {"metric": "Mrays/s of the forward-mode image derivative (image + JVP along a parameter direction)",
+            "value": round(rays / jvp_ms / 1e3, 2), "unit": "Mrays/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": round(jvp_ms, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {**WORKLOAD, "workload": WORKLOAD["workload"].split(",")[0] + ", " +
+                       f"{st.width}x{st.height}, 64 spp, depth 8, RR from 3, JVP along texture + roughness",
+                       "width": st.width, "height": st.height, "l2": "flushed before each timed launch",
+                       "rays": rays, "jvp_ms": round(jvp_ms, 3), "forward_ms": round(fwd_ms, 3),
+                       "jvp_over_forward": round(jvp_ms / fwd_ms, 3),
+                       "forward_mrays_s": round(rays / fwd_ms / 1e3, 1)},
+            "roofline": {"bound": "alu", "kernel": "jvp_kernel", "achieved": round(achieved, 3), "peak": round(peak, 2),
+                         "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": None,
+                         "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 x median SM clock {mhz} MHz"},
+            "gpu_launches": 2 * args.steps, "clocks": clk}
+    print(json.dumps(line), flush=True)
+
+
 def run_cache_experiment(args):
     """Cornell box at 1024^2, depth 4: plain PT at 64 spp vs cache-terminated PT (bounce 1
     and 2) at the spp that fits the same per-frame time including one online training
@@ -593,6 +667,8 @@ def main():
         run_cache_experiment(args)
     elif args.batch:
         run_batch_experiment(args)
+    elif args.jvp:
+        run_jvp_experiment(args)
     else:
         run_ours(args)
 

@@ -284,6 +284,17 @@ int pt_render_batch(const pt_job* jobs, int n_jobs, const pt_batch_opts* opts, v
 #define PT_NOALLOC_MAX_ITEMS 65536
 int pt_render_batch_noalloc(const pt_job* jobs, int n_jobs, const pt_batch_opts* opts, void* stream);
 
+/* Forward-mode derivative of the render (the paper's forward-mode AD, Sec. 1 and
+ * Sec. 4: image-space derivatives "for debugging and visualization"): in one pass,
+ * image (as pt_render_forward) and image_dot = d image / d eps at eps = 0 of the
+ * render with parameters params + eps * tangent, with sampling detached exactly as
+ * in pt_render_backward (so sum(grad_image * image_dot) equals <gradient, tangent>
+ * of the backward pass with the same seed).  tangent: device pointers with the
+ * layouts of params (NULL members mean zero); texture sizes must match.
+ * No radiance cache, crop allowed.  Errors: as pt_render_forward. */
+int pt_render_jvp(pt_scene* scene, const pt_render_desc* desc, const pt_params* params, const pt_params* tangent,
+                  float* image, float* image_dot, void* stream);
+
 /* Reads (and clears) the scene's device status word after synchronising
  * `stream`: *out = PT_OK or the first PT_ERR_* a kernel recorded. */
 int pt_last_device_status(pt_scene* scene, void* stream, int* out);

@@ -71,6 +71,7 @@ def lib():
             L.oracle_render.argtypes = [vp, C.POINTER(RenderIn), vp, vp, vp, ip, vp]
             L.oracle_grad_tape.argtypes = [vp, C.POINTER(RenderIn), vp, vp, vp, vp, ip, vp]
             L.oracle_grad_dual.argtypes = [vp, C.POINTER(RenderIn), vp, ip, vp, vp, ip]
+            L.oracle_render_jvp.argtypes = [vp, C.POINTER(RenderIn), vp, vp, ip, vp, vp, vp, ip]
             L.oracle_pcg32.argtypes = [C.c_uint64, C.c_uint64, ip, vp]
             L.oracle_trace.argtypes = [vp, ip, vp, vp, ip, vp, vp]
             L.oracle_bsdf_eval.argtypes = [ip, vp, vp, vp, vp, vp]
@@ -213,6 +214,28 @@ def grad_dual(osc: OracleScene, r: RenderIn, grad_image: np.ndarray, sel, thread
     out = np.zeros(s.shape[0])
     lib().oracle_grad_dual(osc.handle, C.byref(r), _ptr(gi), s.shape[0], _ptr(s), _ptr(out), threads)
     return out
+
+
+def render_jvp(osc: OracleScene, r: RenderIn, t_albedo=None, t_textures=None, t_rough=None, threads=0):
+    """(image, image_dot): the render and its derivative along the direction
+    (t_albedo [A,3], t_textures [[H,W,4] or None, ...], t_rough [R]); None = zero."""
+    rows = r.crop_h if r.crop_w > 0 else r.height
+    cols = r.crop_w if r.crop_w > 0 else r.width
+    img = np.zeros((rows, cols, 3))
+    dot = np.zeros((rows, cols, 3))
+    keep = []
+
+    def dptr(a):
+        if a is None:
+            return None
+        a = np.ascontiguousarray(a, dtype=np.float64)
+        keep.append(a)
+        return _ptr(a)
+    tex = list(t_textures or [])
+    arr = (C.c_void_p * max(1, len(tex)))(*[(None if t is None else C.cast(dptr(t), C.c_void_p)) for t in tex])
+    lib().oracle_render_jvp(osc.handle, C.byref(r), dptr(t_albedo), C.cast(arr, C.c_void_p), len(tex),
+                            dptr(t_rough), _ptr(img), _ptr(dot), threads)
+    return img, dot
 
 
 def pcg32(initstate: int, initseq: int, n: int) -> np.ndarray:

@@ -15,6 +15,7 @@
 //   * oracle_grad_tape : reverse mode over a stored per-path vertex tape
 //                        (the "shadow memory" approach that PRB avoids, Sec. 2),
 //                        derivative factors written out analytically;
+//   * oracle_render_jvp: image and its derivative along one parameter direction
 //   * oracle_grad_dual : forward mode with dual numbers, derivative factors
 //                        obtained by automatic differentiation of the BSDF code.
 // The conventions the paper leaves open (RNG seeding, random-number layout,
@@ -978,6 +979,57 @@ struct DualAcc {
   }
 };
 
+// Forward-mode accumulator along one direction v of parameter space: one tangent
+// slot holds d/d eps at eps = 0 of the estimator evaluated at (params + eps v).
+// Sampling stays detached (the sampled directions do not move with eps), the
+// same convention as the adjoint (Sec. 4.9).
+struct Direction {
+  const double* albedo = nullptr;         // [A][3] or null (zero)
+  std::vector<const double*> tex;         // per texture [h][w][4] or null
+  const double* rough = nullptr;          // [R] or null
+};
+struct JvpAcc {
+  const Direction* v;
+  Dual beta[3], L[3];
+  void init(const Direction* dir) {
+    v = dir;
+    for (int c = 0; c < 3; ++c) {
+      beta[c] = Dual(1.0, 1);
+      L[c] = Dual(0.0, 1);
+    }
+  }
+  void seeded_inputs(const Mat& m, Dual alb[3], Dual& alpha) const {
+    for (int c = 0; c < 3; ++c) alb[c] = Dual(m.albedo[c], 1);
+    alpha = Dual(m.alpha, 1);
+    if (m.alb_kind == 1 && v->albedo)
+      for (int c = 0; c < 3; ++c) alb[c].d[0] = v->albedo[(size_t)m.alb_row * 3 + c];
+    if (m.alb_kind == 2 && m.tex_id < (int)v->tex.size() && v->tex[m.tex_id])
+      for (int c = 0; c < 3; ++c) alb[c].d[0] = v->tex[m.tex_id][(size_t)m.texel * 4 + c];
+    if (m.rough >= 0 && v->rough) alpha.d[0] = v->rough[m.rough];
+  }
+  void emission(V3, V3 le_w) {
+    for (int c = 0; c < 3; ++c) L[c] = L[c] + beta[c] * le_w[c];
+  }
+  void nee(const VertexInfo& vi, V3 wl, V3 scale, V3) {
+    Dual alb[3], alpha, f[3];
+    seeded_inputs(vi.m, alb, alpha);
+    bsdf_eval_t<Dual>(vi.m, alb, alpha, vi.wi, wl, f);
+    for (int c = 0; c < 3; ++c) L[c] = L[c] + beta[c] * f[c] * scale[c];
+  }
+  void scatter(const VertexInfo& vi, V3 wo, double k) {
+    Dual alb[3], alpha, f[3];
+    seeded_inputs(vi.m, alb, alpha);
+    bsdf_eval_t<Dual>(vi.m, alb, alpha, vi.wi, wo, f);
+    for (int c = 0; c < 3; ++c) beta[c] = beta[c] * f[c] * k;
+  }
+  void scatter_delta(double w) {
+    for (int c = 0; c < 3; ++c) beta[c] = beta[c] * w;
+  }
+  void roulette(double q) {
+    for (int c = 0; c < 3; ++c) beta[c] = beta[c] * (1.0 / q);
+  }
+};
+
 // ---------------------------------------------------------------- parallel driver
 template <class F>
 void parallel_rows(int y0, int rows, int n_threads, F fn) {
@@ -1230,6 +1282,41 @@ int oracle_grad_dual(void* sc, const oracle_render_in* r, const double* grad_ima
     for (int i = 0; i < n_sel; ++i) total[i] += acc_row[i];
   });
   std::memcpy(out, total.data(), n_sel * sizeof(double));
+  return 0;
+}
+
+// Forward-mode image derivative: image (as oracle_render) and image_dot =
+// d image / d eps of the render at params + eps v.  t_tex: n_tex pointers
+// (entries may be null), each [h][w][4] like the scene's textures.
+int oracle_render_jvp(void* sc, const oracle_render_in* r, const double* t_albedo, const double* const* t_tex,
+                      int n_tex, const double* t_rough, double* image, double* image_dot, int n_threads) {
+  const Scene& s = *(Scene*)sc;
+  Camera cam = make_camera(*r);
+  Direction dir;
+  dir.albedo = t_albedo;
+  for (int i = 0; i < n_tex; ++i) dir.tex.push_back(t_tex ? t_tex[i] : nullptr);
+  dir.rough = t_rough;
+  int x0, y0, cw, ch;
+  crop_of(*r, x0, y0, cw, ch);
+  parallel_rows(y0, ch, n_threads, [&](int py) {
+    for (int px = x0; px < x0 + cw; ++px) {
+      size_t pi = (size_t)(py - y0) * cw + (px - x0);
+      double sum[3] = {0, 0, 0}, sum_dot[3] = {0, 0, 0};
+      for (int k = 0; k < r->spp; ++k) {
+        JvpAcc acc;
+        acc.init(&dir);
+        V3 l = render_sample(s, cam, *r, px, py, k, acc, nullptr);
+        for (int c = 0; c < 3; ++c) {
+          sum[c] += l[c];
+          sum_dot[c] += tg(acc.L[c], 0);
+        }
+      }
+      for (int c = 0; c < 3; ++c) {
+        image[pi * 3 + c] = sum[c] / r->spp;
+        image_dot[pi * 3 + c] = sum_dot[c] / r->spp;
+      }
+    }
+  });
   return 0;
 }
 

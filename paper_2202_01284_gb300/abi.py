@@ -123,6 +123,8 @@ SIGNATURES = {
                           C.c_int),
     "pt_render_backward": ([C.c_void_p, C.POINTER(pt_render_desc), C.POINTER(pt_params), C.c_void_p,
                             C.POINTER(pt_grads), C.c_void_p], C.c_int),
+    "pt_render_jvp": ([C.c_void_p, C.POINTER(pt_render_desc), C.POINTER(pt_params), C.POINTER(pt_params),
+                       C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "pt_last_device_status": ([C.c_void_p, C.c_void_p, C.POINTER(C.c_int)], C.c_int),
     "pt_status_string": ([C.c_int], C.c_char_p),
     "pt_cache_create": ([C.POINTER(pt_cache_desc), C.POINTER(C.c_void_p)], C.c_int),
@@ -304,6 +306,12 @@ def pt_render_backward(handle: int, desc: pt_render_desc, params: pt_params, gra
                        stream: int = 0) -> None:
     check("pt_render_backward", load().pt_render_backward(handle, C.byref(desc), C.byref(params),
                                                           _ptr(grad_image), C.byref(grads), stream or None))
+
+
+def pt_render_jvp(handle: int, desc: pt_render_desc, params: pt_params, tangent: pt_params, image, image_dot,
+                  stream: int = 0) -> None:
+    check("pt_render_jvp", load().pt_render_jvp(handle, C.byref(desc), C.byref(params), C.byref(tangent),
+                                                _ptr(image), _ptr(image_dot), stream or None))
 
 
 def pt_last_device_status(handle: int, stream: int = 0) -> int:

@@ -74,6 +74,7 @@ struct DevGrads {
 struct alignas(16) LaunchArgs {
   DevScene scene;
   DevParams params;
+  DevParams tangent;          // forward mode: direction in parameter space (NULL members = 0)
   DevGrads grads;
   int n_cams, width, height, spp, max_depth, rr_depth, nee, dispatch;
   int crop_x0, crop_y0, crop_w, crop_h;
@@ -82,6 +83,7 @@ struct alignas(16) LaunchArgs {
   unsigned long long seed, seed_adj;  // forward / adjoint PCG32 initstate
   long long n_units;          // n_cams * crop_w * crop_h * lanes_per_pixel
   float* image;               // forward output
+  float* image_dot;           // forward mode: derivative of the image along `tangent`
   const float* grad_image;    // adjoint input
   const float* target;        // batched jobs: L2-loss target image (NULL = forward only)
   float loss_scale;           // batched jobs: dLoss/dI = 2 * (I - T) * loss_scale

@@ -112,6 +112,8 @@ struct PathState {
   bool has_shadow, ok_next, delta_next, has_params;
   long long slot;     // sample index (pixel * spp + sample): radiance-cache query / path id
   bool cache_done;    // a cache query was written for this sample
+  // forward-mode tangents (image derivative along a parameter direction)
+  float3 beta_dot, L_dot, c_nee_dot, w_next_dot;
 };
 
 template <bool INSTR>
@@ -131,6 +133,8 @@ __device__ __forceinline__ void path_start(const LaunchArgs& A, PathState& P, un
                        cam.fz + cam.rz * sx + cam.uz * sy));
   P.beta = f3(1.f, 1.f, 1.f);
   P.L = f3(0.f, 0.f, 0.f);
+  P.beta_dot = f3(0.f, 0.f, 0.f);
+  P.L_dot = f3(0.f, 0.f, 0.f);
   P.prev_delta = true;
   P.prev_pdf = 0.0f;
   P.depth = 1;
@@ -141,7 +145,7 @@ __device__ __forceinline__ void path_start(const LaunchArgs& A, PathState& P, un
 // Not inlined (nor is path_finish): with their own register allocation the
 // traversal loop of the megakernel keeps more registers (measured: adjoint -15 %,
 // forward -4 % on the 196k-triangle sphere workload).
-template <bool ADJ, bool INSTR, int DISPATCH>
+template <bool ADJ, bool JVP, bool INSTR, int DISPATCH>
 __device__ __noinline__ bool path_shade(const LaunchArgs& A, PathState& P, const Hit& hit, bool grad_pass,
                                            Counters<INSTR>& cnt) {
   const DevScene& S = A.scene;
@@ -164,6 +168,7 @@ __device__ __noinline__ bool path_shade(const LaunchArgs& A, PathState& P, const
       float3 c = P.beta * Le * w;
       P.L = P.L + c;
       P.Lrem = P.Lrem - c;
+      if (JVP) P.L_dot = P.L_dot + P.beta_dot * Le * w;
     }
     return false;
   }
@@ -190,6 +195,7 @@ __device__ __noinline__ bool path_shade(const LaunchArgs& A, PathState& P, const
     float3 c = P.beta * xyz(sw3) * w;
     P.L = P.L + c;
     P.Lrem = P.Lrem - c;
+    if (JVP) P.L_dot = P.L_dot + P.beta_dot * xyz(sw3) * w;
   }
   if (P.depth >= A.max_depth) return false;
   float u[8];
@@ -236,6 +242,17 @@ __device__ __noinline__ bool path_shade(const LaunchArgs& A, PathState& P, const
     }
   }
   P.fh.add(texel_word);
+  // tangent of the differentiable inputs along the JVP direction
+  float3 alb_dot = f3(0.f, 0.f, 0.f);
+  float alpha_dot = 0.0f;
+  if constexpr (JVP) {
+    if (m.alb_kind == 2 && A.tangent.tex[m.tex]) alb_dot = xyz(__ldg(&A.tangent.tex[m.tex][m.alb_ref]));
+    else if (m.alb_kind == 1 && A.tangent.albedo) {
+      const float* a = &A.tangent.albedo[3 * m.alb_ref];
+      alb_dot = f3(__ldg(a), __ldg(a + 1), __ldg(a + 2));
+    }
+    if (m.rough >= 0 && A.tangent.rough) alpha_dot = __ldg(&A.tangent.rough[m.rough]);
+  }
 
   const bool entering = cos_front > 0.0f;
   const float3 n_s = entering ? ng : -ng;
@@ -283,6 +300,7 @@ __device__ __noinline__ bool path_shade(const LaunchArgs& A, PathState& P, const
   const Frame fr = make_frame(n_s);
   const float3 wi = fr.to_local(wi_w);
   P.c_nee = f3(0.f, 0.f, 0.f);
+  if (JVP) P.c_nee_dot = f3(0.f, 0.f, 0.f);
   P.r_nee_alb = P.r_nee_a = P.r_bsdf_alb = P.r_bsdf_a = f3(0.f, 0.f, 0.f);
 
   // ---- next-event estimation: light sample + BSDF value toward it
@@ -332,7 +350,7 @@ __device__ __noinline__ bool path_shade(const LaunchArgs& A, PathState& P, const
     const float3 wl = fr.to_local(dir);
     BsdfEval ev;
     dispatch_bsdf<DISPATCH>(type, [&]<int T>() {
-      if constexpr (T != PT_BSDF_DIELECTRIC) ev = bsdf_eval<T, ADJ>(m, wi, wl);
+      if constexpr (T != PT_BSDF_DIELECTRIC) ev = bsdf_eval<T, ADJ || JVP>(m, wi, wl);
     });
     if (valid && wl.z > 0.0f && max3f(ev.f) > 0.0f) {
       P.has_shadow = true;
@@ -340,7 +358,12 @@ __device__ __noinline__ bool path_shade(const LaunchArgs& A, PathState& P, const
       P.sd = dir;
       P.stmax = pick_env ? INFINITY : dist * (1.0f - 1e-3f);
       const float w = power_heuristic(pdf_l, ev.pdf);
-      P.c_nee = P.beta * ev.f * (Le * (wl.z * w / pdf_l));
+      const float3 scale = Le * (wl.z * w / pdf_l);
+      P.c_nee = P.beta * ev.f * scale;
+      if (JVP) {
+        const float3 f_dot = ev.df_alb * alb_dot + ev.df_alpha * alpha_dot;
+        P.c_nee_dot = (P.beta_dot * ev.f + P.beta * f_dot) * scale;
+      }
       if (ADJ && grad_pass) {
         P.r_nee_alb = ratio_grad(f3(1.f, 1.f, 1.f), f3(1.f, 1.f, 1.f), ev.df_alb, ev.f);
         P.r_nee_a = ratio_grad(f3(1.f, 1.f, 1.f), f3(1.f, 1.f, 1.f), ev.df_alpha, ev.f);
@@ -349,7 +372,12 @@ __device__ __noinline__ bool path_shade(const LaunchArgs& A, PathState& P, const
   }
   // ---- BSDF sampling (detached) with its attached value
   BsdfSample bs;
-  dispatch_bsdf<DISPATCH>(type, [&]<int T>() { bs = bsdf_sample<T, ADJ>(m, wi, entering, u[3], u[4], u[5]); });
+  dispatch_bsdf<DISPATCH>(type, [&]<int T>() { bs = bsdf_sample<T, ADJ || JVP>(m, wi, entering, u[3], u[4], u[5]); });
+  if constexpr (JVP) {
+    P.w_next_dot = f3(0.f, 0.f, 0.f);
+    if (bs.ok && !bs.delta)
+      P.w_next_dot = (bs.ev.df_alb * alb_dot + bs.ev.df_alpha * alpha_dot) * (bs.wo.z / bs.pdf);
+  }
   P.lobe = bs.lobe;
   P.ok_next = bs.ok;
   P.delta_next = bs.delta;
@@ -375,7 +403,7 @@ __device__ __noinline__ bool path_shade(const LaunchArgs& A, PathState& P, const
 }
 
 // Finish the vertex once the shadow ray is resolved.  Returns false if the path ended.
-template <bool ADJ, bool INSTR>
+template <bool ADJ, bool JVP, bool INSTR>
 __device__ __noinline__ bool path_finish(const LaunchArgs& A, PathState& P, bool occluded, bool grad_pass,
                                             float3 dl, GradSink& sink, Counters<INSTR>& cnt) {
   if (A.nee && P.mtype != PT_BSDF_DIELECTRIC && (A.scene.n_lights > 0 || A.scene.env_w > 0))
@@ -384,6 +412,7 @@ __device__ __noinline__ bool path_finish(const LaunchArgs& A, PathState& P, bool
   if (lit) {
     P.L = P.L + P.c_nee;
     P.Lrem = P.Lrem - P.c_nee;
+    if (JVP) P.L_dot = P.L_dot + P.c_nee_dot;
   }
   P.fh.add((uint32_t)P.lobe);
   if (P.delta_next) P.fh.add(0xfffffffeu);
@@ -402,6 +431,7 @@ __device__ __noinline__ bool path_finish(const LaunchArgs& A, PathState& P, bool
     sink.add<INSTR>(A, m, g_alb, ga.x + ga.y + ga.z, cnt);
   }
   if (!P.ok_next) return false;
+  if (JVP) P.beta_dot = P.beta_dot * P.w_next + P.beta * P.w_next_dot;
   P.beta = P.beta * P.w_next;
   P.prev_delta = P.delta_next;
   P.prev_pdf = P.pdf_next;
@@ -413,6 +443,7 @@ __device__ __noinline__ bool path_finish(const LaunchArgs& A, PathState& P, bool
     P.fh.add(cont ? 1u : 0u);
     if (!cont) return false;
     P.beta = P.beta * (1.0f / q);
+    if (JVP) P.beta_dot = P.beta_dot * (1.0f / q);
   }
   ++P.depth;
   return true;
@@ -462,7 +493,7 @@ __device__ __forceinline__ bool unit_pixel(const LaunchArgs& A, long long unit, 
 // Each thread owns the samples s = lane_in_pixel + k * lanes_per_pixel of one
 // pixel; in the adjoint every sample is traced twice (pass 0: radiance L,
 // pass 1: replay with L_rem and gradient scatter) by the same code.
-template <bool ADJ, bool INSTR, int LAYOUT, int DISPATCH>
+template <bool ADJ, bool JVP, bool INSTR, int LAYOUT, int DISPATCH>
 __device__ __forceinline__ void megakernel(const LaunchArgs& A, long long unit, const Tile& tile) {
   PixelOf px{};
   const bool valid = unit_pixel(A, unit, tile, px);
@@ -486,6 +517,7 @@ __device__ __forceinline__ void megakernel(const LaunchArgs& A, long long unit, 
     }
   }
   float3 pix_sum = f3(0.f, 0.f, 0.f);
+  float3 pix_sum_dot = f3(0.f, 0.f, 0.f);
   float3 L_pass0 = f3(0.f, 0.f, 0.f);
   int next_s = lane_in_pix;
   int pass = 0;
@@ -511,14 +543,14 @@ __device__ __forceinline__ void megakernel(const LaunchArgs& A, long long unit, 
       const bool grad_pass = ADJ && pass == 1;
       bool alive = true, finish = true, occ = false;
       if (!want_shadow) {
-        alive = path_shade<ADJ, INSTR, DISPATCH>(A, P, hit, grad_pass, cnt);
+        alive = path_shade<ADJ, JVP, INSTR, DISPATCH>(A, P, hit, grad_pass, cnt);
         finish = alive && !P.has_shadow;
         want_shadow = alive && P.has_shadow;
       } else {
         occ = hit.pos >= 0;
         want_shadow = false;
       }
-      if (finish) alive = path_finish<ADJ, INSTR>(A, P, occ, grad_pass, dl, sink, cnt);
+      if (finish) alive = path_finish<ADJ, JVP, INSTR>(A, P, occ, grad_pass, dl, sink, cnt);
       if (!alive) {
         has_path = false;
         if constexpr (!ADJ) {
@@ -540,6 +572,7 @@ __device__ __forceinline__ void megakernel(const LaunchArgs& A, long long unit, 
           pass = 1;
         } else {
           pix_sum = pix_sum + P.L;
+          if (JVP) pix_sum_dot = pix_sum_dot + P.L_dot;
           if constexpr (INSTR && !ADJ) {
             const long long si = px.pix * A.spp + next_s;
             if (A.dbg_L) {
@@ -562,11 +595,23 @@ __device__ __forceinline__ void megakernel(const LaunchArgs& A, long long unit, 
       pix_sum.y += __shfl_xor_sync(0xffffffffu, pix_sum.y, off);
       pix_sum.z += __shfl_xor_sync(0xffffffffu, pix_sum.z, off);
     }
+    if constexpr (JVP) {
+      for (int off = 1; off < A.lanes_per_pixel; off <<= 1) {
+        pix_sum_dot.x += __shfl_xor_sync(0xffffffffu, pix_sum_dot.x, off);
+        pix_sum_dot.y += __shfl_xor_sync(0xffffffffu, pix_sum_dot.y, off);
+        pix_sum_dot.z += __shfl_xor_sync(0xffffffffu, pix_sum_dot.z, off);
+      }
+    }
     if (valid && lane_in_pix == 0 && A.image) {
       const float inv = 1.0f / (float)A.spp;
       A.image[3 * px.pix] = pix_sum.x * inv;
       A.image[3 * px.pix + 1] = pix_sum.y * inv;
       A.image[3 * px.pix + 2] = pix_sum.z * inv;
+      if (JVP) {
+        A.image_dot[3 * px.pix] = pix_sum_dot.x * inv;
+        A.image_dot[3 * px.pix + 1] = pix_sum_dot.y * inv;
+        A.image_dot[3 * px.pix + 2] = pix_sum_dot.z * inv;
+      }
     }
   }
   flush_counters<INSTR>(A, cnt);
@@ -590,12 +635,20 @@ __device__ __forceinline__ Tile crop_tile(const LaunchArgs& A) {
 
 template <bool INSTR, int LAYOUT, int DISPATCH>
 __global__ void __launch_bounds__(256, PT_FWD_MIN_BLOCKS) forward_kernel(const __grid_constant__ LaunchArgs A) {
-  megakernel<false, INSTR, LAYOUT, DISPATCH>(A, (long long)blockIdx.x * blockDim.x + threadIdx.x, crop_tile(A));
+  megakernel<false, false, INSTR, LAYOUT, DISPATCH>(A, (long long)blockIdx.x * blockDim.x + threadIdx.x, crop_tile(A));
+}
+
+// Forward mode (Sec. 4, forward-mode derivatives of the paper's AD layer): the
+// image and its derivative along a parameter direction in one pass.
+template <int LAYOUT>
+__global__ void __launch_bounds__(256, PT_ADJ_MIN_BLOCKS) jvp_kernel(const __grid_constant__ LaunchArgs A) {
+  megakernel<false, true, false, LAYOUT, PT_DISPATCH_SWITCH>(A, (long long)blockIdx.x * blockDim.x + threadIdx.x,
+                                                             crop_tile(A));
 }
 
 template <bool INSTR, int LAYOUT, int DISPATCH>
 __global__ void __launch_bounds__(256, PT_ADJ_MIN_BLOCKS) adjoint_kernel(const __grid_constant__ LaunchArgs A) {
-  megakernel<true, INSTR, LAYOUT, DISPATCH>(A, (long long)blockIdx.x * blockDim.x + threadIdx.x, crop_tile(A));
+  megakernel<true, false, INSTR, LAYOUT, DISPATCH>(A, (long long)blockIdx.x * blockDim.x + threadIdx.x, crop_tile(A));
 }
 
 // image[pix] += sum_s q_beta[slot] * max(q_rgb[slot], 0) / spp  (cache-terminated render)
@@ -674,7 +727,7 @@ __global__ void __launch_bounds__(256, ADJ ? PT_ADJ_MIN_BLOCKS : PT_FWD_MIN_BLOC
     }
     const Tile t{bi.x0, bi.y0, tile, tile, 1};
     const long long units = (long long)tile * tile * A.lanes_per_pixel;
-    for (long long b = 0; b < units; b += 32) megakernel<ADJ, false, LAYOUT, PT_DISPATCH_SWITCH>(A, b + lane, t);
+    for (long long b = 0; b < units; b += 32) megakernel<ADJ, false, false, LAYOUT, PT_DISPATCH_SWITCH>(A, b + lane, t);
   }
 }
 
@@ -1184,5 +1237,33 @@ extern "C" int pt_render_batch_noalloc(const pt_job* jobs, int n_jobs, const pt_
       batch_kernel<true, PT_BVH_BINARY><<<grid, opts.block_size, smem, cs>>>(d_jobs, d_items + n_fwd, n_adj,
                                                                                opts.tile, d_queue + 1);
   }
+  return cudaGetLastError() == cudaSuccess ? PT_OK : PT_ERR_CUDA;
+}
+
+extern "C" int pt_render_jvp(pt_scene* s, const pt_render_desc* r, const pt_params* p, const pt_params* tangent,
+                             float* image, float* image_dot, void* stream) {
+  LaunchArgs A;
+  int st = fill_launch(s, r, p, A);
+  if (st != PT_OK) return st;
+  if (!tangent || !image || !image_dot || r->cache || r->dbg_sample_L || r->dbg_sample_hash || r->counters)
+    return PT_ERR_ARG;
+  A.image = image;
+  A.image_dot = image_dot;
+  A.tangent.albedo = tangent->albedo;
+  A.tangent.n_albedo = tangent->n_albedo;
+  A.tangent.rough = tangent->roughness;
+  A.tangent.n_rough = tangent->n_rough;
+  if (s->max_albedo_row >= 0 && tangent->albedo && tangent->n_albedo <= s->max_albedo_row) return PT_ERR_ARG;
+  if (s->max_rough >= 0 && tangent->roughness && tangent->n_rough <= s->max_rough) return PT_ERR_ARG;
+  for (int t = 0; t <= s->max_tex_slot; ++t) {
+    A.tangent.tex[t] = reinterpret_cast<const float4*>(tangent->tex[t]);
+    if (tangent->tex[t] && (tangent->tex_w[t] != p->tex_w[t] || tangent->tex_h[t] != p->tex_h[t])) return PT_ERR_ARG;
+  }
+  int block;
+  long long grid;
+  if ((st = launch_dims(r, A, block, grid)) != PT_OK) return st;
+  cudaStream_t cs = (cudaStream_t)stream;
+  if (s->dev.layout == PT_BVH_WIDE) jvp_kernel<PT_BVH_WIDE><<<(unsigned)grid, block, 0, cs>>>(A);
+  else jvp_kernel<PT_BVH_BINARY><<<(unsigned)grid, block, 0, cs>>>(A);
   return cudaGetLastError() == cudaSuccess ? PT_OK : PT_ERR_CUDA;
 }

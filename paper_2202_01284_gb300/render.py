@@ -110,6 +110,30 @@ class DeviceScene:
         abi.pt_render_backward(self.handle, desc, p, grad_image.contiguous(), g,
                                torch.cuda.current_stream(grad_image.device).cuda_stream)
 
+    def jvp(self, st: RenderSettings, t_albedo=None, t_textures=None, t_roughness=None, cams=None, albedo=None,
+            textures=None, roughness=None):
+        """(image, image_dot): the render and its derivative along the parameter
+        direction (t_albedo, t_textures, t_roughness); None members are zero."""
+        cams = list(cams) if cams is not None else self.cameras
+        rows, cols = st.rows_cols()
+        dev = self.albedo.device
+        img = torch.empty((len(cams), rows, cols, 3), device=dev, dtype=torch.float32)
+        dot = torch.empty_like(img)
+        textures = self.textures if textures is None else textures
+        p = abi.params_struct(self.albedo if albedo is None else albedo, textures,
+                              self.roughness if roughness is None else roughness)
+        tt = list(t_textures) if t_textures is not None else []
+        t = abi.params_struct(t_albedo, [], t_roughness)
+        for i, x in enumerate(tt):
+            if x is not None:
+                t.tex[i] = abi._ptr(x.contiguous())
+                t.tex_w[i] = int(x.shape[1])
+                t.tex_h[i] = int(x.shape[0])
+        t.n_tex = len(tt)
+        desc = self._desc(cams, st)
+        abi.pt_render_jvp(self.handle, desc, p, t, img, dot, torch.cuda.current_stream(dev).cuda_stream)
+        return img, dot
+
     def status(self) -> int:
         return abi.pt_last_device_status(self.handle, torch.cuda.current_stream().cuda_stream)
 
@@ -126,8 +150,20 @@ class RenderFn(torch.autograd.Function):
         ctx.dscene = dscene
         ctx.st = st
         ctx.save_for_backward(albedo, roughness, *textures)
+        ctx.primal = (albedo.detach(), roughness.detach(), [t.detach() for t in textures])
         return dscene.forward(st, albedo=albedo.detach().contiguous(), roughness=roughness.detach().contiguous(),
                               textures=[t.detach().contiguous() for t in textures])
+
+    @staticmethod
+    def jvp(ctx, _scene, _st, t_albedo, t_roughness, *t_textures):
+        """Forward-mode derivative (torch.autograd.forward_ad): the image tangent
+        along the input tangents, from one pt_render_jvp pass."""
+        albedo, roughness, textures = ctx.primal
+        _, dot = ctx.dscene.jvp(ctx.st, t_albedo=t_albedo, t_roughness=t_roughness,
+                                t_textures=[t.contiguous() if t is not None else None for t in t_textures],
+                                albedo=albedo.detach().contiguous(), roughness=roughness.detach().contiguous(),
+                                textures=[t.detach().contiguous() for t in textures])
+        return dot
 
     @staticmethod
     def backward(ctx, grad_img):
