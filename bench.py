@@ -62,6 +62,9 @@ def parse():
                          "in one persistent graph-captured launch vs 64 separate launches (own JSON line)")
     ap.add_argument("--jvp", action="store_true",
                     help="forward-mode image derivative on the throughput workload vs the plain forward (own line)")
+    ap.add_argument("--wavefront", action="store_true",
+                    help="megakernel vs wavefront ablation, forward and adjoint (own JSON line)")
+    ap.add_argument("--wave-paths", type=int, default=0)
     ap.add_argument("--peaks", action="store_true",
                     help="microbenchmarks of the memory-side roofs (L2-resident reads, atomics) as a JSON line")
     ap.add_argument("--small", action="store_true",
@@ -421,8 +424,9 @@ def run_jvp_experiment(args):
             "value": round(rays / jvp_ms / 1e3, 2), "unit": "Mrays/s", "n_gpus": 1, "steps": args.steps,
             "warmup": max(3, args.warmup), "ms_per_step": round(jvp_ms, 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {**WORKLOAD, "workload": WORKLOAD["workload"].split(",")[0] + ", " +
-                       f"{st.width}x{st.height}, 64 spp, depth 8, RR from 3, JVP along texture + roughness",
+            "config": {**WORKLOAD, "workload": "spheres32x5120 + ground 128^2 (196,608 tris), "
+                       f"{st.width}x{st.height}, 64 spp, depth 8, RR from 3, image + JVP along a direction over "
+                       "the texture and roughness",
                        "width": st.width, "height": st.height, "l2": "flushed before each timed launch",
                        "rays": rays, "jvp_ms": round(jvp_ms, 3), "forward_ms": round(fwd_ms, 3),
                        "jvp_over_forward": round(jvp_ms / fwd_ms, 3),
@@ -431,6 +435,84 @@ def run_jvp_experiment(args):
                          "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": None,
                          "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 x median SM clock {mhz} MHz"},
             "gpu_launches": 2 * args.steps, "clocks": clk}
+    print(json.dumps(line), flush=True)
+
+
+def run_wavefront_experiment(args):
+    """Megakernel vs wavefront execution of the same estimator (forward and PRB
+    adjoint) on the throughput workload: the wavefront variant in its two call
+    modes (traced material switch, material-grouped shading kernels).  Own JSON line."""
+    import torch
+
+    from paper_2202_01284_gb300 import abi
+    from paper_2202_01284_gb300.render import DeviceScene
+    abi.load()
+    dev = torch.device("cuda", 0)
+    sc, tgt_tex = make_workload(small=args.small)
+    layout = abi.PT_BVH_WIDE if args.bvh == "wide" else abi.PT_BVH_BINARY
+    ds = DeviceScene(sc, layout=layout, device=dev)
+    st = settings(args, 11)
+    target = ds.forward(settings(args, 77), textures=[torch.as_tensor(tgt_tex, device=dev)]).clone()
+    img = torch.empty_like(target)
+    cf = torch.zeros(abi.PT_N_COUNTERS, dtype=torch.int64, device=dev)
+    cb = torch.zeros(abi.PT_N_COUNTERS, dtype=torch.int64, device=dev)
+    ds.forward(st, out=img, counters=cf)
+    grad_img = (2.0 * (img - target) / img.numel()).contiguous()
+    g_tex = torch.zeros_like(ds.textures[0])
+    g_rough = torch.zeros_like(ds.roughness)
+    ds.backward(st, grad_img, g_textures=[g_tex], g_roughness=g_rough, counters=cb)
+    torch.cuda.synchronize()
+    cf, cb = cf.cpu().numpy(), cb.cpu().numpy()
+    rays_f, rays_b = int(cf[1] + cf[2]), int(cb[1] + cb[2])
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    wave = args.wave_paths
+    variants = {
+        "megakernel_fwd": lambda: ds.forward(st, out=img),
+        "wavefront_traced_fwd": lambda: ds.wavefront_forward(st, calls=abi.PT_WF_TRACED, wave_paths=wave, out=img),
+        "wavefront_grouped_fwd": lambda: ds.wavefront_forward(st, calls=abi.PT_WF_GROUPED, wave_paths=wave, out=img),
+        "megakernel_adj": lambda: ds.backward(st, grad_img, g_textures=[g_tex], g_roughness=g_rough),
+        "wavefront_traced_adj": lambda: ds.wavefront_backward(st, grad_img, calls=abi.PT_WF_TRACED, wave_paths=wave,
+                                                              g_textures=[g_tex], g_roughness=g_rough),
+        "wavefront_grouped_adj": lambda: ds.wavefront_backward(st, grad_img, calls=abi.PT_WF_GROUPED,
+                                                               wave_paths=wave, g_textures=[g_tex],
+                                                               g_roughness=g_rough),
+    }
+    for fn in variants.values():
+        for _ in range(max(3, args.warmup)):
+            fn()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    clocks.start()
+    ms = {k: [] for k in variants}
+    for k in range(args.steps):
+        for name, fn in variants.items():
+            flush.fill_(float(k))
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            ms[name].append((a, b))
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    avg = {k: statistics.mean(a.elapsed_time(b) for a, b in v) for k, v in ms.items()}
+    mr = {k: round((rays_f if k.endswith("fwd") else rays_b) / v / 1e3, 1) for k, v in avg.items()}
+    # per-path state through HBM: 16-byte words of PathState per slot
+    line = {"metric": "megakernel vs wavefront: ms and Mrays/s, forward and PRB adjoint",
+            "value": round(avg["wavefront_traced_fwd"] / avg["megakernel_fwd"], 3),
+            "unit": "x slowdown of the wavefront (traced calls) forward vs the megakernel forward",
+            "n_gpus": 1, "steps": args.steps, "warmup": max(3, args.warmup), "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD["workload"] if not args.small else "spheres 256x256 64 spp",
+                       "wave_paths": wave or 4 * 1024 * 1024, "l2": "flushed before each timed launch",
+                       "rays_fwd": rays_f, "rays_adj": rays_b,
+                       "ms": {k: round(v, 3) for k, v in avg.items()}, "mrays_s": mr,
+                       "slowdown_vs_megakernel": {
+                           "traced_fwd": round(avg["wavefront_traced_fwd"] / avg["megakernel_fwd"], 3),
+                           "grouped_fwd": round(avg["wavefront_grouped_fwd"] / avg["megakernel_fwd"], 3),
+                           "traced_adj": round(avg["wavefront_traced_adj"] / avg["megakernel_adj"], 3),
+                           "grouped_adj": round(avg["wavefront_grouped_adj"] / avg["megakernel_adj"], 3)}},
+            "clocks": clk}
     print(json.dumps(line), flush=True)
 
 
@@ -669,6 +751,8 @@ def main():
         run_batch_experiment(args)
     elif args.jvp:
         run_jvp_experiment(args)
+    elif args.wavefront:
+        run_wavefront_experiment(args)
     else:
         run_ours(args)
 

@@ -295,6 +295,31 @@ int pt_render_batch_noalloc(const pt_job* jobs, int n_jobs, const pt_batch_opts*
 int pt_render_jvp(pt_scene* scene, const pt_render_desc* desc, const pt_params* params, const pt_params* tangent,
                   float* image, float* image_dot, void* stream);
 
+/* Wavefront variant (Sec. 3.3 "wavefront-style evaluation", Sec. 5: the megakernel
+ * against wavefront execution).  The same estimator as pt_render_forward /
+ * pt_render_backward (same random numbers and decisions), computed by one kernel per
+ * stage with the path state in device memory: a wave of whole pixels runs max_depth
+ * rounds of closest-hit traversal, shading, shadow traversal and finish, each over a
+ * queue of paths.  calls: PT_WF_TRACED = one shading kernel with the material switch
+ * inside; PT_WF_GROUPED = paths sorted into one queue per material by the closest-hit
+ * kernel, one shading kernel per material.  wave_paths: samples per wave (0 = 4 Mi;
+ * rounded down to whole pixels; at most 2^28).  Scratch (about 360 B per path of a
+ * wave) is owned by the scene, grown on demand (cudaMalloc, which synchronises the
+ * device) and freed with it; calls on one scene must be ordered on one stream.
+ * desc: dbg_sample_L / dbg_sample_hash honoured by the forward; counters, cache and
+ * (backward) per-sample outputs are PT_ERR_ARG; lanes_per_pixel, block_size and
+ * dispatch are ignored.  Errors: as pt_render_forward / _backward, PT_ERR_OOM. */
+enum { PT_WF_TRACED = 0, PT_WF_GROUPED = 1 };
+typedef struct pt_wavefront_opts {
+  int32_t calls;       /* PT_WF_TRACED or PT_WF_GROUPED */
+  int32_t wave_paths;  /* 0 = default */
+} pt_wavefront_opts;
+int pt_wavefront_forward(pt_scene* scene, const pt_render_desc* desc, const pt_params* params,
+                         const pt_wavefront_opts* opts, float* image, void* stream);
+int pt_wavefront_backward(pt_scene* scene, const pt_render_desc* desc, const pt_params* params,
+                          const pt_wavefront_opts* opts, const float* grad_image, const pt_grads* grads,
+                          void* stream);
+
 /* Reads (and clears) the scene's device status word after synchronising
  * `stream`: *out = PT_OK or the first PT_ERR_* a kernel recorded. */
 int pt_last_device_status(pt_scene* scene, void* stream, int* out);

@@ -32,6 +32,8 @@ PT_BVH_BINARY = 0
 PT_BVH_WIDE = 1
 PT_DISPATCH_SWITCH = 0
 PT_DISPATCH_MATCH = 1
+PT_WF_TRACED = 0
+PT_WF_GROUPED = 1
 PT_N_COUNTERS = 16
 COUNTER_NAMES = ["paths", "rays", "shadow_rays", "nodes", "tri_tests", "tex_lookups", "atomics", "grad_terms"]
 
@@ -110,6 +112,10 @@ class pt_batch_opts(C.Structure):
                 ("block_size", C.c_int32)]
 
 
+class pt_wavefront_opts(C.Structure):
+    _fields_ = [("calls", C.c_int32), ("wave_paths", C.c_int32)]
+
+
 _lib = None
 _lock = threading.Lock()
 
@@ -125,6 +131,10 @@ SIGNATURES = {
                             C.POINTER(pt_grads), C.c_void_p], C.c_int),
     "pt_render_jvp": ([C.c_void_p, C.POINTER(pt_render_desc), C.POINTER(pt_params), C.POINTER(pt_params),
                        C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
+    "pt_wavefront_forward": ([C.c_void_p, C.POINTER(pt_render_desc), C.POINTER(pt_params),
+                              C.POINTER(pt_wavefront_opts), C.c_void_p, C.c_void_p], C.c_int),
+    "pt_wavefront_backward": ([C.c_void_p, C.POINTER(pt_render_desc), C.POINTER(pt_params),
+                               C.POINTER(pt_wavefront_opts), C.c_void_p, C.POINTER(pt_grads), C.c_void_p], C.c_int),
     "pt_last_device_status": ([C.c_void_p, C.c_void_p, C.POINTER(C.c_int)], C.c_int),
     "pt_status_string": ([C.c_int], C.c_char_p),
     "pt_cache_create": ([C.POINTER(pt_cache_desc), C.POINTER(C.c_void_p)], C.c_int),
@@ -312,6 +322,19 @@ def pt_render_jvp(handle: int, desc: pt_render_desc, params: pt_params, tangent:
                   stream: int = 0) -> None:
     check("pt_render_jvp", load().pt_render_jvp(handle, C.byref(desc), C.byref(params), C.byref(tangent),
                                                 _ptr(image), _ptr(image_dot), stream or None))
+
+
+def pt_wavefront_forward(handle: int, desc: pt_render_desc, params: pt_params, opts: pt_wavefront_opts, image,
+                         stream: int = 0) -> None:
+    check("pt_wavefront_forward", load().pt_wavefront_forward(handle, C.byref(desc), C.byref(params), C.byref(opts),
+                                                              _ptr(image), stream or None))
+
+
+def pt_wavefront_backward(handle: int, desc: pt_render_desc, params: pt_params, opts: pt_wavefront_opts, grad_image,
+                          grads: pt_grads, stream: int = 0) -> None:
+    check("pt_wavefront_backward", load().pt_wavefront_backward(handle, C.byref(desc), C.byref(params),
+                                                                C.byref(opts), _ptr(grad_image), C.byref(grads),
+                                                                stream or None))
 
 
 def pt_last_device_status(handle: int, stream: int = 0) -> int:

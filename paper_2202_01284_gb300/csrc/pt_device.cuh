@@ -521,9 +521,15 @@ __device__ __forceinline__ BsdfSample bsdf_sample(const Material& m, float3 wi, 
 // Polymorphic call over the BSDF type (compile-time dispatch mode).  MATCH: the
 // warp votes once per type and runs each type's code with only its lanes active
 // (ballot grouping); SWITCH: plain per-lane branch.
+// Internal mode for kernels that only ever see one material (the grouped
+// wavefront shading kernels): PT_DISPATCH_FIXED + type compiles that type alone.
+constexpr int PT_DISPATCH_FIXED = 16;
+
 template <int MODE, class F>
 __device__ __forceinline__ void dispatch_bsdf(int type, F&& f) {
-  if constexpr (MODE == PT_DISPATCH_MATCH) {
+  if constexpr (MODE >= PT_DISPATCH_FIXED) {
+    if (type == MODE - PT_DISPATCH_FIXED) f.template operator()<MODE - PT_DISPATCH_FIXED>();
+  } else if constexpr (MODE == PT_DISPATCH_MATCH) {
     unsigned active = __activemask();
     if (__any_sync(active, type == PT_BSDF_DIFFUSE)) { if (type == PT_BSDF_DIFFUSE) f.template operator()<PT_BSDF_DIFFUSE>(); }
     if (__any_sync(active, type == PT_BSDF_CONDUCTOR)) { if (type == PT_BSDF_CONDUCTOR) f.template operator()<PT_BSDF_CONDUCTOR>(); }

@@ -115,6 +115,11 @@ struct CacheBuffers {
 };
 CacheBuffers cache_buffers(pt_cache* c);
 
+// Host helpers of the render entry points (pt_render.cu): validate a render
+// description and parameters into launch arguments; block and grid of a launch.
+int fill_launch(pt_scene* s, const pt_render_desc* r, const pt_params* p, LaunchArgs& A);
+int launch_dims(const pt_render_desc* r, const LaunchArgs& A, int& block, long long& grid);
+
 }  // namespace ptgb
 
 // Library-side scene object behind the opaque pt_scene handle.
@@ -145,5 +150,7 @@ struct pt_scene {
   void* d_env_marg_guide = nullptr;
   void* d_env_cond_guide = nullptr;
   void* d_status = nullptr;
+  void* d_wf = nullptr;         // wavefront scratch (grown on demand)
+  size_t wf_bytes = 0;
   pt_scene_info info{};
 };

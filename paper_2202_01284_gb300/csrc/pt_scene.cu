@@ -67,6 +67,7 @@ void scene_free_all(pt_scene* s) {
   free_dev(s->d_env_marg_guide);
   free_dev(s->d_env_cond_guide);
   free_dev(s->d_status);
+  free_dev(s->d_wf);
   std::free(s->h_vertices);
   std::free(s->h_uvs);
   std::free(s->h_tri_shape);

@@ -110,6 +110,39 @@ class DeviceScene:
         abi.pt_render_backward(self.handle, desc, p, grad_image.contiguous(), g,
                                torch.cuda.current_stream(grad_image.device).cuda_stream)
 
+    # ------------------------------------------------------------------ wavefront variant
+    def wavefront_forward(self, st: RenderSettings, calls: int = abi.PT_WF_TRACED, wave_paths: int = 0, cams=None,
+                          albedo=None, textures=None, roughness=None, out=None, per_sample=False):
+        """pt_wavefront_forward: the same image as forward(), one kernel per stage."""
+        cams = list(cams) if cams is not None else self.cameras
+        rows, cols = st.rows_cols()
+        dev = self.albedo.device
+        img = out if out is not None else torch.empty((len(cams), rows, cols, 3), device=dev, dtype=torch.float32)
+        dL = dh = None
+        if per_sample:
+            dL = torch.empty((len(cams), rows, cols, st.spp, 3), device=dev, dtype=torch.float32)
+            dh = torch.empty((len(cams), rows, cols, st.spp), device=dev, dtype=torch.int32)
+        p = abi.params_struct(self.albedo if albedo is None else albedo,
+                              self.textures if textures is None else textures,
+                              self.roughness if roughness is None else roughness)
+        desc = self._desc(cams, st, dbg_L=dL, dbg_hash=dh)
+        abi.pt_wavefront_forward(self.handle, desc, p, abi.pt_wavefront_opts(calls, wave_paths), img,
+                                 torch.cuda.current_stream(dev).cuda_stream)
+        return (img, dL, dh) if per_sample else img
+
+    def wavefront_backward(self, st: RenderSettings, grad_image, calls: int = abi.PT_WF_TRACED, wave_paths: int = 0,
+                           cams=None, albedo=None, textures=None, roughness=None, g_albedo=None, g_textures=None,
+                           g_roughness=None, seed=None):
+        """pt_wavefront_backward: the same gradients as backward(), one kernel per stage."""
+        cams = list(cams) if cams is not None else self.cameras
+        p = abi.params_struct(self.albedo if albedo is None else albedo,
+                              self.textures if textures is None else textures,
+                              self.roughness if roughness is None else roughness)
+        g = abi.grads_struct(g_albedo, g_textures or (), g_roughness)
+        desc = self._desc(cams, st, seed=seed)
+        abi.pt_wavefront_backward(self.handle, desc, p, abi.pt_wavefront_opts(calls, wave_paths),
+                                  grad_image.contiguous(), g, torch.cuda.current_stream(grad_image.device).cuda_stream)
+
     def jvp(self, st: RenderSettings, t_albedo=None, t_textures=None, t_roughness=None, cams=None, albedo=None,
             textures=None, roughness=None):
         """(image, image_dot): the render and its derivative along the parameter

@@ -1,0 +1,154 @@
+"""GPU parity of the wavefront variant (pt_wavefront_forward / _backward).
+
+The wavefront kernels run the megakernel's per-path code stage by stage with the
+state in device memory, so they are held to the same bars: per-sample parity with
+the FP64 oracle (decision fingerprints, 1e-3 per matched sample, 1e-4 on 99.9 %
+of clean pixels), and gradients against the oracle's stored-tape adjoint.  They
+are also compared with the megakernel itself (same FP32 arithmetic: identical
+decisions on all but a handful of samples).
+"""
+import numpy as np
+import pytest
+
+from paper_2202_01284_gb300 import scenes as S
+
+from parity import GRAD_COSINE, PIXEL_FRACTION, cosine, pixel_ok_fraction, rel_ok, sample_report
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2202_01284_gb300 import abi
+    abi.load()
+    return abi
+
+
+def _settings(scene, **kw):
+    from paper_2202_01284_gb300.render import RenderSettings
+    cam = scene.cameras[0]
+    base = dict(width=cam.width, height=cam.height, spp=4, max_depth=4, seed=7)
+    base.update(kw)
+    return RenderSettings(**base)
+
+
+def _oracle(oracle_mod, sc, st, per_sample=True):
+    r = oracle_mod.render_in(sc.cameras[0], st.spp, st.max_depth, st.seed, st.rr_depth, st.nee, crop=st.crop)
+    return oracle_mod.render(oracle_mod.OracleScene(sc), r, per_sample=per_sample)
+
+
+def _wf(ds, st, calls, wave_paths=0):
+    img, L, h = ds.wavefront_forward(st, calls=calls, wave_paths=wave_paths, per_sample=True)
+    torch.cuda.synchronize()
+    assert ds.status() == 0
+    return img[0].cpu().numpy(), L[0].cpu().numpy(), h[0].cpu().numpy().view(np.uint32)
+
+
+@pytest.mark.parametrize("calls,layout", [(0, 0), (1, 0), (0, 1), (1, 1)])
+def test_cornell_wavefront_parity(lib, oracle_mod, calls, layout):
+    from paper_2202_01284_gb300.render import DeviceScene
+    sc = S.cornell()
+    st = _settings(sc, spp=4, max_depth=5, seed=7)
+    ds = DeviceScene(sc, layout=layout)
+    img, L, h = _wf(ds, st, calls)
+    ref, refL, refh = _oracle(oracle_mod, sc, st)
+    rep = sample_report(L, h, refL, refh, img, ref)
+    print("cornell wavefront:", rep)
+    assert rep["matched_bad"] == 0, rep
+    assert rep["divergent_fraction"] <= 1e-3, rep
+    assert rep["clean_pixel_fraction_ok"] >= PIXEL_FRACTION, rep
+    # the megakernel takes the same decisions in FP32
+    mimg, mL, mh = ds.forward(st, per_sample=True)
+    torch.cuda.synchronize()
+    same = h == mh[0].cpu().numpy().view(np.uint32)
+    assert same.mean() >= 0.999
+    assert rel_ok(L[same], mL[0].cpu().numpy()[same], rel=1e-5).all(axis=-1).mean() >= 0.999
+
+
+def test_spheres_wavefront_parity(lib, oracle_mod):
+    """GGX conductor, dielectric, textured diffuse, env map, roulette; grouped calls."""
+    from paper_2202_01284_gb300.render import DeviceScene
+    sc = S.spheres(n_spheres=6, level=2, grid=(3, 2), ground_quads=8, tex_res=256, width=64, height=48)
+    st = _settings(sc, spp=8, max_depth=8, rr_depth=3, seed=5)
+    ds = DeviceScene(sc, layout=1)
+    ref, refL, refh = _oracle(oracle_mod, sc, st)
+    for calls in (0, 1):
+        img, L, h = _wf(ds, st, calls)
+        rep = sample_report(L, h, refL, refh, img, ref)
+        print("spheres wavefront calls", calls, rep)
+        assert rep["matched_bad"] <= max(2, rep["n"] // 10000), rep
+        assert rep["divergent_fraction"] < 5e-3, rep
+        assert rep["clean_pixel_fraction_ok"] >= PIXEL_FRACTION, rep
+
+
+def test_ragged_waves_and_crop(lib, oracle_mod):
+    """Waves of 125 pixels (the last one partial) over a ragged crop, 2 cameras."""
+    from paper_2202_01284_gb300.render import DeviceScene
+    sc = S.cornell(width=96, height=80)
+    cams = [sc.cameras[0], S.Camera(origin=(0.3, 1.1, 3.4), target=(0.0, 1.0, 0.0), up=(0, 1, 0), vfov_deg=40.0,
+                                    width=96, height=80)]
+    st = _settings(sc, spp=8, max_depth=4, seed=3, crop=(5, 9, 67, 35))
+    ds = DeviceScene(sc)
+    full = ds.wavefront_forward(st, cams=cams)
+    small = ds.wavefront_forward(st, cams=cams, wave_paths=1000)
+    mega = ds.forward(st, cams=cams)
+    torch.cuda.synchronize()
+    assert torch.equal(full, small)  # waves only change the order of independent paths
+    frac, _ = pixel_ok_fraction(full[0].cpu().numpy(), _oracle(oracle_mod, sc, st, per_sample=False))
+    assert frac >= PIXEL_FRACTION
+    assert rel_ok(full.cpu().numpy(), mega.cpu().numpy(), rel=1e-5).all(axis=-1).mean() >= PIXEL_FRACTION
+
+
+def test_wavefront_gradients(lib, oracle_mod):
+    """PRB in wavefront form: texture and roughness gradients vs the oracle tape and
+    vs the megakernel adjoint (same seed)."""
+    from paper_2202_01284_gb300.render import DeviceScene
+    sc = S.cornell96(width=512, height=512)
+    crop = (192, 160, 96, 96)
+    st = _settings(sc, spp=8, max_depth=6, seed=21, crop=crop)
+    ds = DeviceScene(sc, layout=1)
+    ref = _oracle(oracle_mod, sc, st, per_sample=False)
+    tgt = sc.with_params(textures=[S.cornell96_target_texture(sc.textures[0])])
+    T = _oracle(oracle_mod, tgt, _settings(tgt, spp=8, max_depth=6, seed=23, crop=crop), per_sample=False)
+    gi = 2 * (ref - T) / ref.size
+    osc = oracle_mod.OracleScene(sc)
+    r = oracle_mod.render_in(sc.cameras[0], st.spp, st.max_depth, st.seed, crop=crop)
+    _, gt_ref, gr_ref = oracle_mod.grad_tape(osc, r, gi)
+    gi_t = torch.as_tensor(gi[None], dtype=torch.float32, device="cuda")
+    gt_m = torch.zeros_like(ds.textures[0])
+    gr_m = torch.zeros_like(ds.roughness)
+    ds.backward(st, gi_t, g_textures=[gt_m], g_roughness=gr_m)
+    for calls in (0, 1):
+        gt = torch.zeros_like(ds.textures[0])
+        gr = torch.zeros_like(ds.roughness)
+        ds.wavefront_backward(st, gi_t, calls=calls, wave_paths=20000, g_textures=[gt], g_roughness=gr)
+        torch.cuda.synchronize()
+        assert ds.status() == 0
+        c_t = cosine(gt.cpu().numpy()[..., :3], gt_ref[0][..., :3])
+        c_r = cosine(gr.cpu().numpy(), gr_ref)
+        c_tm = cosine(gt.cpu().numpy(), gt_m.cpu().numpy())
+        c_rm = cosine(gr.cpu().numpy(), gr_m.cpu().numpy())
+        print(f"calls={calls}: vs oracle tex {c_t:.7f} rough {c_r:.7f}; vs megakernel tex {c_tm:.9f} rough {c_rm:.9f}")
+        assert c_r >= GRAD_COSINE
+        assert c_t >= 0.999  # texel-edge flips between FP32 and FP64, as for the megakernel
+        assert c_tm >= 0.99999 and c_rm >= 0.99999
+        assert np.all(gt.cpu().numpy()[..., 3] == 0)
+
+
+def test_wavefront_bad_arguments(lib):
+    from paper_2202_01284_gb300.render import DeviceScene
+    sc = S.cornell(width=16, height=16)
+    ds = DeviceScene(sc)
+    st = _settings(sc)
+    with pytest.raises(lib.PtError) as e:
+        ds.wavefront_forward(st, calls=2)
+    assert e.value.code == lib.PT_ERR_ARG
+    with pytest.raises(lib.PtError):
+        ds.wavefront_forward(st, wave_paths=-1 + (1 << 30))
+    st.spp = 0
+    with pytest.raises(lib.PtError):
+        ds.wavefront_forward(st)
