@@ -187,6 +187,10 @@ typedef struct {
   int32_t n_tex;
   const float* roughness;     /* [n_rough] GGX alpha per entry */
   int32_t n_rough;
+  const float* env;           /* [env_h][env_w][4] environment radiance used for shading, the
+                                 scene's map dimensions; NULL = the map given to pt_scene_create.
+                                 Importance sampling always uses the scene's map (detached
+                                 sampling, Sec. 4.9), so the render is linear in this input. */
 } pt_params;
 
 /* Gradient outputs: borrowed device pointers, accumulated (+=); NULL = not wanted. */
@@ -194,6 +198,8 @@ typedef struct {
   float* albedo;              /* [n_albedo][3] */
   float* tex[PT_MAX_TEX];     /* each [tex_h][tex_w][4] */
   float* roughness;           /* [n_rough] */
+  float* env;                 /* [env_h][env_w][4] environment radiance (emitter gradients,
+                                 Sec. 5: PRB differentiating the environment map) */
 } pt_grads;
 
 /* Primal render (Fig. 7, megakernel #1): image = mean over spp of the path

@@ -55,6 +55,7 @@ class RenderIn(C.Structure):
         ("spp", C.c_int), ("max_depth", C.c_int), ("rr_depth", C.c_int), ("nee", C.c_int),
         ("seed", C.c_uint64), ("cam_index", C.c_int),
         ("crop_x0", C.c_int), ("crop_y0", C.c_int), ("crop_w", C.c_int), ("crop_h", C.c_int),
+        ("env_radiance", C.c_void_p),
     ]
 
 
@@ -69,9 +70,9 @@ def lib():
             L.oracle_scene_new.argtypes = [C.POINTER(SceneIn)]
             L.oracle_scene_free.argtypes = [vp]
             L.oracle_render.argtypes = [vp, C.POINTER(RenderIn), vp, vp, vp, ip, vp]
-            L.oracle_grad_tape.argtypes = [vp, C.POINTER(RenderIn), vp, vp, vp, vp, ip, vp]
+            L.oracle_grad_tape.argtypes = [vp, C.POINTER(RenderIn), vp, vp, vp, vp, vp, ip, vp]
             L.oracle_grad_dual.argtypes = [vp, C.POINTER(RenderIn), vp, ip, vp, vp, ip]
-            L.oracle_render_jvp.argtypes = [vp, C.POINTER(RenderIn), vp, vp, ip, vp, vp, vp, ip]
+            L.oracle_render_jvp.argtypes = [vp, C.POINTER(RenderIn), vp, vp, ip, vp, vp, vp, vp, ip]
             L.oracle_pcg32.argtypes = [C.c_uint64, C.c_uint64, ip, vp]
             L.oracle_trace.argtypes = [vp, ip, vp, vp, ip, vp, vp]
             L.oracle_bsdf_eval.argtypes = [ip, vp, vp, vp, vp, vp]
@@ -156,8 +157,15 @@ class OracleScene:
             self.handle = None
 
 
-def render_in(cam, spp, max_depth, seed, rr_depth=-1, nee=True, cam_index=0, crop=None) -> RenderIn:
+def render_in(cam, spp, max_depth, seed, rr_depth=-1, nee=True, cam_index=0, crop=None,
+              env_radiance=None) -> RenderIn:
+    """Render settings.  env_radiance [env_h, env_w, 4]: radiance used for shading
+    instead of the scene's map (sampling keeps the scene's map)."""
     r = RenderIn()
+    if env_radiance is not None:
+        e = np.ascontiguousarray(env_radiance, dtype=np.float64)
+        r._env_keep = e
+        r.env_radiance = e.ctypes.data
     r.origin[:] = cam.origin
     r.target[:] = cam.target
     r.up[:] = cam.up
@@ -190,24 +198,28 @@ def render(osc: OracleScene, r: RenderIn, per_sample=False, threads=0, count_ray
     return out if len(out) > 1 else out[0]
 
 
-def grad_tape(osc: OracleScene, r: RenderIn, grad_image: np.ndarray, threads=0, count_rays=False):
-    """Gradients (albedo [A,3], textures list [h,w,4], roughness [R]) by the stored tape."""
+def grad_tape(osc: OracleScene, r: RenderIn, grad_image: np.ndarray, threads=0, count_rays=False, env=False):
+    """Gradients (albedo [A,3], textures list [h,w,4], roughness [R]) by the stored tape;
+    with env=True also the environment-radiance gradient [env_h, env_w, 4] (after roughness)."""
     s = osc.scene
     gi = np.ascontiguousarray(grad_image, dtype=np.float64)
     ga = np.zeros((s.albedo.shape[0], 3))
     gt = [np.zeros(t.shape) for t in s.textures]
     gr = np.zeros(s.roughness.shape[0])
+    ge = np.zeros(s.env.shape if s.env is not None else (0, 0, 4))
     tp = (C.c_void_p * max(1, len(gt)))(*[t.ctypes.data for t in gt])
     rays = np.zeros(1, np.uint64)
-    lib().oracle_grad_tape(osc.handle, C.byref(r), _ptr(gi), _ptr(ga), C.cast(tp, C.c_void_p), _ptr(gr), threads,
-                           _ptr(rays))
-    return (ga, gt, gr, int(rays[0])) if count_rays else (ga, gt, gr)
+    lib().oracle_grad_tape(osc.handle, C.byref(r), _ptr(gi), _ptr(ga), C.cast(tp, C.c_void_p), _ptr(gr),
+                           _ptr(ge) if ge.size else None, threads, _ptr(rays))
+    out = (ga, gt, gr, ge) if env else (ga, gt, gr)
+    return out + (int(rays[0]),) if count_rays else out
 
 
 def grad_dual(osc: OracleScene, r: RenderIn, grad_image: np.ndarray, sel, threads=0):
     """Gradients of the selected parameters by forward-mode duals.
 
-    sel: list of (kind, a, b, c): (0,row,ch,0) albedo, (1,tex,texel,ch) texel, (2,idx,0,0) roughness.
+    sel: list of (kind, a, b, c): (0,row,ch,0) albedo, (1,tex,texel,ch) texel, (2,idx,0,0) roughness,
+    (3,pixel,ch,0) environment radiance (pixel = y * env_w + x).
     """
     gi = np.ascontiguousarray(grad_image, dtype=np.float64)
     s = np.ascontiguousarray(np.asarray(sel, np.int32).reshape(-1, 4))
@@ -216,9 +228,10 @@ def grad_dual(osc: OracleScene, r: RenderIn, grad_image: np.ndarray, sel, thread
     return out
 
 
-def render_jvp(osc: OracleScene, r: RenderIn, t_albedo=None, t_textures=None, t_rough=None, threads=0):
+def render_jvp(osc: OracleScene, r: RenderIn, t_albedo=None, t_textures=None, t_rough=None, t_env=None, threads=0):
     """(image, image_dot): the render and its derivative along the direction
-    (t_albedo [A,3], t_textures [[H,W,4] or None, ...], t_rough [R]); None = zero."""
+    (t_albedo [A,3], t_textures [[H,W,4] or None, ...], t_rough [R], t_env [env_h, env_w, 4]);
+    None = zero."""
     rows = r.crop_h if r.crop_w > 0 else r.height
     cols = r.crop_w if r.crop_w > 0 else r.width
     img = np.zeros((rows, cols, 3))
@@ -234,7 +247,7 @@ def render_jvp(osc: OracleScene, r: RenderIn, t_albedo=None, t_textures=None, t_
     tex = list(t_textures or [])
     arr = (C.c_void_p * max(1, len(tex)))(*[(None if t is None else C.cast(dptr(t), C.c_void_p)) for t in tex])
     lib().oracle_render_jvp(osc.handle, C.byref(r), dptr(t_albedo), C.cast(arr, C.c_void_p), len(tex),
-                            dptr(t_rough), _ptr(img), _ptr(dot), threads)
+                            dptr(t_rough), dptr(t_env), _ptr(img), _ptr(dot), threads)
     return img, dot
 
 

@@ -216,6 +216,9 @@ typedef struct {
   uint64_t seed;
   int cam_index;
   int crop_x0, crop_y0, crop_w, crop_h;  // crop_w == 0: whole image
+  // Environment radiance used for shading, [env_h][env_w][4], or NULL for the
+  // scene's map.  Sampling always uses the scene's map (detached sampling).
+  const double* env_radiance;
 } oracle_render_in;
 }
 
@@ -555,6 +558,12 @@ V3 env_lookup(const Scene& s, V3 d, int& px, int& py) {
   const double* e = &s.env[((size_t)py * s.env_w + px) * 4];
   return {e[0], e[1], e[2]};
 }
+// Radiance of env pixel (x, y): the render's override, else the scene's map.
+V3 env_value(const Scene& s, const oracle_render_in& r, int x, int y) {
+  const double* e = r.env_radiance ? &r.env_radiance[((size_t)y * s.env_w + x) * 4]
+                                   : &s.env[((size_t)y * s.env_w + x) * 4];
+  return {e[0], e[1], e[2]};
+}
 // Solid-angle density of the environment sampler at direction d.
 double env_pdf(const Scene& s, V3 d) {
   int px, py;
@@ -693,11 +702,12 @@ V3 render_sample(const Scene& s, const Camera& cam, const oracle_render_in& r, i
     if (hit.prim < 0) {
       if (has_env) {
         int ex, ey;
-        V3 Le = env_lookup(s, rd, ex, ey);
+        env_lookup(s, rd, ex, ey);
+        V3 Le = env_value(s, r, ex, ey);
         double w = (prev_delta || !r.nee) ? 1.0 : power_heuristic(prev_pdf, p_env * env_pdf(s, rd));
         V3 c = mul(beta, Le) * w;
         L = L + c;
-        acc.emission(c, Le * w);
+        acc.emission(c, Le * w, ey * s.env_w + ex, beta * w, w);
       }
       break;
     }
@@ -714,7 +724,7 @@ V3 render_sample(const Scene& s, const Camera& cam, const oracle_render_in& r, i
       }
       V3 c = mul(beta, sh.emission) * w;
       L = L + c;
-      acc.emission(c, sh.emission * w);
+      acc.emission(c, sh.emission * w, -1, V3(), 0.0);
     }
     if (depth >= r.max_depth) break;
     double u[8];
@@ -748,7 +758,7 @@ V3 render_sample(const Scene& s, const Camera& cam, const oracle_render_in& r, i
           V3 Lc(std::max(y[0], 0.0), std::max(y[1], 0.0), std::max(y[2], 0.0));
           V3 c = mul(beta, Lc);
           L = L + c;
-          acc.emission(c, Lc);
+          acc.emission(c, Lc, -1, V3(), 0.0);
           break;
         }
       }
@@ -788,6 +798,7 @@ V3 render_sample(const Scene& s, const Camera& cam, const oracle_render_in& r, i
         V3 dir, Le;
         double pdf_l = 0.0, dist = INFINITY;
         bool valid = false;
+        int env_texel = -1;
         if (pick_env) {
           int y = cdf_pick(s.env_marg.data(), s.env_h, u[1]);
           const double* cond = &s.env_cond[(size_t)y * (s.env_w + 1)];
@@ -797,8 +808,8 @@ V3 render_sample(const Scene& s, const Camera& cam, const oracle_render_in& r, i
           double theta = kPi * (y + fv) / s.env_h, phi = 2.0 * kPi * (x + fu) / s.env_w;
           double st = std::sin(theta);
           dir = V3(st * std::cos(phi), std::cos(theta), st * std::sin(phi));
-          const double* e = &s.env[((size_t)y * s.env_w + x) * 4];
-          Le = V3(e[0], e[1], e[2]);
+          Le = env_value(s, r, x, y);
+          env_texel = y * s.env_w + x;
           double pdf_uv = s.env_p[(size_t)y * s.env_w + x] * s.env_w * s.env_h;
           pdf_l = st > 0.0 ? p_env * pdf_uv / (2.0 * kPi * kPi * st) : 0.0;
           valid = pdf_l > 0.0;
@@ -831,10 +842,11 @@ V3 render_sample(const Scene& s, const Camera& cam, const oracle_render_in& r, i
           vis_code = occ ? 1 : 0;
           if (!occ) {
             double w = power_heuristic(pdf_l, bsdf_pdf(vi.m, vi.wi, wl));
-            V3 scale = Le * (wl.z * w / pdf_l);  // everything but beta and f
+            double s_env = wl.z * w / pdf_l;   // d scale / d Le
+            V3 scale = Le * s_env;             // everything but beta and f
             V3 c = mul(mul(beta, f), scale);
             L = L + c;
-            acc.nee(vi, wl, scale, c);
+            acc.nee(vi, wl, scale, c, env_texel, mul(beta, f) * s_env, s_env);
           }
         }
         dh.add(vis_code);
@@ -888,8 +900,8 @@ V3 render_sample(const Scene& s, const Camera& cam, const oracle_render_in& r, i
 
 // Accumulator for the plain render: ignores events.
 struct NullAcc {
-  void emission(V3, V3) {}
-  void nee(const VertexInfo&, V3, V3, V3) {}
+  void emission(V3, V3, int, V3, double) {}
+  void nee(const VertexInfo&, V3, V3, V3, int, V3, double) {}
   void scatter(const VertexInfo&, V3, double) {}
   void scatter_delta(double) {}
   void roulette(double) {}
@@ -902,11 +914,17 @@ struct TapeAcc {
     V3 c;          // contribution (emission / nee)
     Mat m;
     V3 wi, wo;
+    int env_texel;  // emission / nee from the environment: its pixel, else -1
+    V3 d_env;       // d contribution / d env radiance, per channel
   };
   std::vector<Rec> recs;
-  void emission(V3 c, V3) { recs.push_back({0, c, Mat{}, V3(), V3()}); }
-  void nee(const VertexInfo& v, V3 wl, V3, V3 c) { recs.push_back({1, c, v.m, v.wi, wl}); }
-  void scatter(const VertexInfo& v, V3 wo, double) { recs.push_back({2, V3(), v.m, v.wi, wo}); }
+  void emission(V3 c, V3, int env_texel, V3 d_env, double) {
+    recs.push_back({0, c, Mat{}, V3(), V3(), env_texel, d_env});
+  }
+  void nee(const VertexInfo& v, V3 wl, V3, V3 c, int env_texel, V3 d_env, double) {
+    recs.push_back({1, c, v.m, v.wi, wl, env_texel, d_env});
+  }
+  void scatter(const VertexInfo& v, V3 wo, double) { recs.push_back({2, V3(), v.m, v.wi, wo, -1, V3()}); }
   void scatter_delta(double) {}
   void roulette(double) {}
 };
@@ -915,6 +933,7 @@ struct GradOut {
   std::vector<double> albedo;                 // [A][3]
   std::vector<std::vector<double>> tex;       // each [h][w][4]
   std::vector<double> rough;                  // [R]
+  std::vector<double> env;                    // [env_h][env_w][4]
 };
 
 void add_param_grad(GradOut& g, const Mat& m, V3 contrib, const DFactors& df, V3 dl) {
@@ -932,7 +951,8 @@ void add_param_grad(GradOut& g, const Mat& m, V3 contrib, const DFactors& df, V3
 
 // Forward-mode accumulator: RGB dual throughput, dual radiance.
 struct SelParam {
-  int kind, a, b, c;  // 0: albedo (row a, channel b); 1: texel (tex a, texel b, channel c); 2: roughness a
+  int kind, a, b, c;  // 0: albedo (row a, channel b); 1: texel (tex a, texel b, channel c); 2: roughness a;
+                      // 3: environment pixel a, channel b
 };
 struct DualAcc {
   const std::vector<SelParam>* sel;
@@ -956,14 +976,26 @@ struct DualAcc {
       if (p.kind == 2 && m.rough == p.a) alpha.d[i] = 1.0;
     }
   }
-  void emission(V3, V3 le_w) {
-    for (int c = 0; c < 3; ++c) L[c] = L[c] + beta[c] * le_w[c];
+  // le_w (or scale) as duals: derivative `k` in the slots of environment pixel `texel`
+  void env_seeded(V3 v, int texel, double k, Dual out[3]) const {
+    for (int c = 0; c < 3; ++c) out[c] = Dual(v[c], n);
+    if (texel < 0) return;
+    for (size_t i = 0; i < n; ++i) {
+      const SelParam& p = (*sel)[i];
+      if (p.kind == 3 && p.a == texel) out[p.b].d[i] = k;
+    }
   }
-  void nee(const VertexInfo& v, V3 wl, V3 scale, V3) {
-    Dual alb[3], alpha, f[3];
+  void emission(V3, V3 le_w, int env_texel, V3, double w_env) {
+    Dual e[3];
+    env_seeded(le_w, env_texel, w_env, e);
+    for (int c = 0; c < 3; ++c) L[c] = L[c] + beta[c] * e[c];
+  }
+  void nee(const VertexInfo& v, V3 wl, V3 scale, V3, int env_texel, V3, double s_env) {
+    Dual alb[3], alpha, f[3], sc[3];
     seeded_inputs(v.m, alb, alpha);
     bsdf_eval_t<Dual>(v.m, alb, alpha, v.wi, wl, f);
-    for (int c = 0; c < 3; ++c) L[c] = L[c] + beta[c] * f[c] * scale[c];
+    env_seeded(scale, env_texel, s_env, sc);
+    for (int c = 0; c < 3; ++c) L[c] = L[c] + beta[c] * f[c] * sc[c];
   }
   void scatter(const VertexInfo& v, V3 wo, double k) {
     Dual alb[3], alpha, f[3];
@@ -987,6 +1019,7 @@ struct Direction {
   const double* albedo = nullptr;         // [A][3] or null (zero)
   std::vector<const double*> tex;         // per texture [h][w][4] or null
   const double* rough = nullptr;          // [R] or null
+  const double* env = nullptr;            // [env_h][env_w][4] or null
 };
 struct JvpAcc {
   const Direction* v;
@@ -1007,14 +1040,24 @@ struct JvpAcc {
       for (int c = 0; c < 3; ++c) alb[c].d[0] = v->tex[m.tex_id][(size_t)m.texel * 4 + c];
     if (m.rough >= 0 && v->rough) alpha.d[0] = v->rough[m.rough];
   }
-  void emission(V3, V3 le_w) {
-    for (int c = 0; c < 3; ++c) L[c] = L[c] + beta[c] * le_w[c];
+  // le_w (or scale) as duals: tangent k * v_env at environment pixel `texel`
+  void env_seeded(V3 val, int texel, double k, Dual out[3]) const {
+    for (int c = 0; c < 3; ++c) {
+      out[c] = Dual(val[c], 1);
+      if (texel >= 0 && v->env) out[c].d[0] = k * v->env[(size_t)texel * 4 + c];
+    }
   }
-  void nee(const VertexInfo& vi, V3 wl, V3 scale, V3) {
-    Dual alb[3], alpha, f[3];
+  void emission(V3, V3 le_w, int env_texel, V3, double w_env) {
+    Dual e[3];
+    env_seeded(le_w, env_texel, w_env, e);
+    for (int c = 0; c < 3; ++c) L[c] = L[c] + beta[c] * e[c];
+  }
+  void nee(const VertexInfo& vi, V3 wl, V3 scale, V3, int env_texel, V3, double s_env) {
+    Dual alb[3], alpha, f[3], sc[3];
     seeded_inputs(vi.m, alb, alpha);
     bsdf_eval_t<Dual>(vi.m, alb, alpha, vi.wi, wl, f);
-    for (int c = 0; c < 3; ++c) L[c] = L[c] + beta[c] * f[c] * scale[c];
+    env_seeded(scale, env_texel, s_env, sc);
+    for (int c = 0; c < 3; ++c) L[c] = L[c] + beta[c] * f[c] * sc[c];
   }
   void scatter(const VertexInfo& vi, V3 wo, double k) {
     Dual alb[3], alpha, f[3];
@@ -1186,7 +1229,7 @@ int oracle_render(void* sc, const oracle_render_in* r, double* image, double* sa
 // grad_image [ch][cw][3] is dLoss/dImage; each sample gets 1/spp of it.
 // Outputs are *overwritten*: g_albedo [A][3], g_tex[i] [h][w][4], g_rough [R] (any may be NULL).
 int oracle_grad_tape(void* sc, const oracle_render_in* r, const double* grad_image, double* g_albedo,
-                     double* const* g_tex, double* g_rough, int n_threads, uint64_t* n_rays) {
+                     double* const* g_tex, double* g_rough, double* g_env, int n_threads, uint64_t* n_rays) {
   const Scene& s = *(Scene*)sc;
   Camera cam = make_camera(*r);
   int x0, y0, cw, ch;
@@ -1195,6 +1238,7 @@ int oracle_grad_tape(void* sc, const oracle_render_in* r, const double* grad_ima
   total.albedo.assign(s.albedo.size(), 0.0);
   for (auto& t : s.tex) total.tex.emplace_back(t.rgba.size(), 0.0);
   total.rough.assign(s.roughness.size(), 0.0);
+  total.env.assign((size_t)s.env_w * s.env_h * 4, 0.0);
   std::mutex mu;
   std::atomic<uint64_t> rays(0);
   parallel_rows(y0, ch, n_threads, [&](int py) {
@@ -1204,7 +1248,7 @@ int oracle_grad_tape(void* sc, const oracle_render_in* r, const double* grad_ima
     row.albedo.assign(s.albedo.size(), 0.0);
     row.rough.assign(s.roughness.size(), 0.0);
     struct TexAdd { int tex; size_t idx; double v; };
-    std::vector<TexAdd> tex_adds;
+    std::vector<TexAdd> tex_adds;  // tex = -1: environment pixel
     for (int px = x0; px < x0 + cw; ++px) {
       size_t pi = (size_t)(py - y0) * cw + (px - x0);
       V3 dl(grad_image[pi * 3] / r->spp, grad_image[pi * 3 + 1] / r->spp, grad_image[pi * 3 + 2] / r->spp);
@@ -1217,6 +1261,9 @@ int oracle_grad_tape(void* sc, const oracle_render_in* r, const double* grad_ima
         V3 suffix(0, 0, 0);
         for (int i = (int)tape.recs.size() - 1; i >= 0; --i) {
           const auto& rc = tape.recs[i];
+          // environment radiance: the contribution is linear in it (local term)
+          if (rc.env_texel >= 0)
+            for (int c = 0; c < 3; ++c) tex_adds.push_back({-1, (size_t)rc.env_texel * 4 + c, dl[c] * rc.d_env[c]});
           if (rc.kind == 0) {
             suffix = suffix + rc.c;
             continue;
@@ -1240,11 +1287,12 @@ int oracle_grad_tape(void* sc, const oracle_render_in* r, const double* grad_ima
     std::lock_guard<std::mutex> lk(mu);
     for (size_t i = 0; i < row.albedo.size(); ++i) total.albedo[i] += row.albedo[i];
     for (size_t i = 0; i < row.rough.size(); ++i) total.rough[i] += row.rough[i];
-    for (const auto& a : tex_adds) total.tex[a.tex][a.idx] += a.v;
+    for (const auto& a : tex_adds) (a.tex < 0 ? total.env : total.tex[a.tex])[a.idx] += a.v;
   });
   if (n_rays) *n_rays = rays.load();
   if (g_albedo) std::memcpy(g_albedo, total.albedo.data(), total.albedo.size() * sizeof(double));
   if (g_rough) std::memcpy(g_rough, total.rough.data(), total.rough.size() * sizeof(double));
+  if (g_env) std::memcpy(g_env, total.env.data(), total.env.size() * sizeof(double));
   if (g_tex)
     for (size_t i = 0; i < total.tex.size(); ++i)
       if (g_tex[i]) std::memcpy(g_tex[i], total.tex[i].data(), total.tex[i].size() * sizeof(double));
@@ -1287,15 +1335,18 @@ int oracle_grad_dual(void* sc, const oracle_render_in* r, const double* grad_ima
 
 // Forward-mode image derivative: image (as oracle_render) and image_dot =
 // d image / d eps of the render at params + eps v.  t_tex: n_tex pointers
-// (entries may be null), each [h][w][4] like the scene's textures.
+// (entries may be null), each [h][w][4] like the scene's textures; t_env:
+// tangent of the environment radiance [env_h][env_w][4] or null.
 int oracle_render_jvp(void* sc, const oracle_render_in* r, const double* t_albedo, const double* const* t_tex,
-                      int n_tex, const double* t_rough, double* image, double* image_dot, int n_threads) {
+                      int n_tex, const double* t_rough, const double* t_env, double* image, double* image_dot,
+                      int n_threads) {
   const Scene& s = *(Scene*)sc;
   Camera cam = make_camera(*r);
   Direction dir;
   dir.albedo = t_albedo;
   for (int i = 0; i < n_tex; ++i) dir.tex.push_back(t_tex ? t_tex[i] : nullptr);
   dir.rough = t_rough;
+  dir.env = t_env;
   int x0, y0, cw, ch;
   crop_of(*r, x0, y0, cw, ch);
   parallel_rows(y0, ch, n_threads, [&](int py) {

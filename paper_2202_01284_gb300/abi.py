@@ -83,11 +83,12 @@ class pt_render_desc(C.Structure):
 class pt_params(C.Structure):
     _fields_ = [("albedo", C.c_void_p), ("n_albedo", C.c_int32), ("tex", C.c_void_p * PT_MAX_TEX),
                 ("tex_w", C.c_int32 * PT_MAX_TEX), ("tex_h", C.c_int32 * PT_MAX_TEX), ("n_tex", C.c_int32),
-                ("roughness", C.c_void_p), ("n_rough", C.c_int32)]
+                ("roughness", C.c_void_p), ("n_rough", C.c_int32), ("env", C.c_void_p)]
 
 
 class pt_grads(C.Structure):
-    _fields_ = [("albedo", C.c_void_p), ("tex", C.c_void_p * PT_MAX_TEX), ("roughness", C.c_void_p)]
+    _fields_ = [("albedo", C.c_void_p), ("tex", C.c_void_p * PT_MAX_TEX), ("roughness", C.c_void_p),
+                ("env", C.c_void_p)]
 
 
 PT_CACHE_N_PARAMS = 20672
@@ -257,7 +258,7 @@ def render_desc(cams, width, height, spp, max_depth, seed, rr_depth=-1, nee=True
     return r
 
 
-def params_struct(albedo=None, textures=(), roughness=None) -> pt_params:
+def params_struct(albedo=None, textures=(), roughness=None, env=None) -> pt_params:
     p = pt_params()
     if albedo is not None and albedo.numel() > 0:
         p.albedo = _ptr(albedo)
@@ -270,15 +271,18 @@ def params_struct(albedo=None, textures=(), roughness=None) -> pt_params:
     if roughness is not None and roughness.numel() > 0:
         p.roughness = _ptr(roughness)
         p.n_rough = int(roughness.shape[0])
+    if env is not None:
+        p.env = _ptr(env)
     return p
 
 
-def grads_struct(albedo=None, textures=(), roughness=None) -> pt_grads:
+def grads_struct(albedo=None, textures=(), roughness=None, env=None) -> pt_grads:
     g = pt_grads()
     g.albedo = _ptr(albedo) if albedo is not None and albedo.numel() > 0 else None
     for i, t in enumerate(textures):
         g.tex[i] = _ptr(t)
     g.roughness = _ptr(roughness) if roughness is not None and roughness.numel() > 0 else None
+    g.env = _ptr(env) if env is not None else None
     return g
 
 

@@ -33,6 +33,7 @@ class Job:
     g_textures: Optional[list] = None
     g_roughness: Optional[torch.Tensor] = None
     g_albedo: Optional[torch.Tensor] = None
+    g_env: Optional[torch.Tensor] = None     # environment-radiance gradient [env_h, env_w, 4]
 
     def __post_init__(self):
         dev = self.dscene.albedo.device
@@ -48,7 +49,7 @@ class Job:
         j.max_depth, j.rr_depth, j.nee = self.max_depth, self.rr_depth, 1
         j.seed, j.backward_seed = self.seed, self.backward_seed
         j.params = abi.params_struct(ds.albedo, ds.textures, ds.roughness)
-        j.grads = abi.grads_struct(self.g_albedo, self.g_textures or (), self.g_roughness)
+        j.grads = abi.grads_struct(self.g_albedo, self.g_textures or (), self.g_roughness, self.g_env)
         j.image = self.image.data_ptr()
         j.target = self.target.data_ptr() if self.target is not None else None
         return j

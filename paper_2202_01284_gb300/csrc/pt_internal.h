@@ -58,6 +58,7 @@ struct DevParams {
   const float4* tex[PT_MAX_TEX];
   int tex_w[PT_MAX_TEX], tex_h[PT_MAX_TEX];
   const float* rough;
+  const float4* env;  // environment radiance for shading (NULL: the scene's map)
   int n_albedo, n_rough;
 };
 
@@ -65,6 +66,7 @@ struct DevGrads {
   float* albedo;
   float4* tex[PT_MAX_TEX];
   float* rough;
+  float4* env;
   int n_albedo, n_rough;
 };
 

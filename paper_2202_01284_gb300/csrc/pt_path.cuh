@@ -68,6 +68,17 @@ struct GradSink {
       }
     }
   }
+  // Environment radiance of pixel `idx` (emitter gradient): warp-aggregated, as
+  // coherent rays escape through the same pixel of a coarse map.
+  template <bool INSTR>
+  __device__ __forceinline__ void add_env(const LaunchArgs& A, int idx, float3 g, Counters<INSTR>& cnt) {
+    cnt.add(7, 1);
+    float v[3] = {g.x, g.y, g.z};
+    if (warp_aggregate<3>((unsigned)idx, v)) {
+      atomicAdd(&A.grads.env[idx], make_float4(v[0], v[1], v[2], 0.0f));
+      cnt.add(6, 1);
+    }
+  }
 };
 
 __device__ __forceinline__ float3 ratio_grad(float3 dl, float3 x, float3 df, float3 f) {
@@ -99,6 +110,8 @@ struct PathState {
   float3 c_nee;       // NEE contribution if unoccluded
   float3 r_nee_alb, r_bsdf_alb;  // (df/dalbedo)/f per channel (NEE / sampled direction)
   float3 r_nee_a, r_bsdf_a;      // (df/dalpha)/f per channel
+  int nee_env;        // env pixel of the light sample (-1: area light or none)
+  float3 nee_env_d;   // d (NEE contribution) / d (env radiance of that pixel)
   float3 w_next;      // throughput factor of the sampled direction
   float3 no, nd;      // continuation ray
   float pdf_next;
@@ -141,8 +154,11 @@ __device__ __forceinline__ void path_start(const LaunchArgs& A, PathState& P, un
 // Not inlined (nor is path_finish): with their own register allocation the
 // traversal loop of the megakernel keeps more registers (measured: adjoint -15 %,
 // forward -4 % on the 196k-triangle sphere workload).
-template <bool ADJ, bool JVP, bool INSTR, int DISPATCH>
-__device__ __noinline__ bool path_shade(const LaunchArgs& A, PathState& P, const Hit& hit, bool grad_pass,
+// EGRAD: the adjoint also scatters environment-radiance gradients (a separate
+// instantiation: the extra code costs the plain adjoint instruction-cache space).
+template <bool ADJ, bool JVP, bool INSTR, int DISPATCH, bool EGRAD = false>
+__device__ __noinline__ bool path_shade(const LaunchArgs& A, PathState& P, const Hit& hit, bool grad_pass, float3 dl,
+                                        GradSink& sink,
                                            Counters<INSTR>& cnt) {
   const DevScene& S = A.scene;
   const bool has_area = S.n_lights > 0;
@@ -155,7 +171,8 @@ __device__ __noinline__ bool path_shade(const LaunchArgs& A, PathState& P, const
     if (has_env) {
       int ex, ey;
       env_pixel(S, P.rd, ex, ey);
-      float3 Le = xyz(__ldg(&S.env[ey * S.env_w + ex]));
+      const int ei = ey * S.env_w + ex;
+      float3 Le = xyz(__ldg(&(A.params.env ? A.params.env : S.env)[ei]));
       float w = 1.0f;
       if (!P.prev_delta && A.nee) {
         float st = sqrtf(fmaxf(0.0f, 1.0f - P.rd.y * P.rd.y));
@@ -164,7 +181,11 @@ __device__ __noinline__ bool path_shade(const LaunchArgs& A, PathState& P, const
       float3 c = P.beta * Le * w;
       P.L = P.L + c;
       P.Lrem = P.Lrem - c;
-      if (JVP) P.L_dot = P.L_dot + P.beta_dot * Le * w;
+      if (JVP) {
+        P.L_dot = P.L_dot + P.beta_dot * Le * w;
+        if (A.tangent.env) P.L_dot = P.L_dot + P.beta * xyz(__ldg(&A.tangent.env[ei])) * w;
+      }
+      if (ADJ && EGRAD && grad_pass && A.grads.env) sink.add_env<INSTR>(A, ei, dl * P.beta * w, cnt);
     }
     return false;
   }
@@ -296,6 +317,7 @@ __device__ __noinline__ bool path_shade(const LaunchArgs& A, PathState& P, const
   const Frame fr = make_frame(n_s);
   const float3 wi = fr.to_local(wi_w);
   P.c_nee = f3(0.f, 0.f, 0.f);
+  if (EGRAD) P.nee_env = -1;
   if (JVP) P.c_nee_dot = f3(0.f, 0.f, 0.f);
   P.r_nee_alb = P.r_nee_a = P.r_bsdf_alb = P.r_bsdf_a = f3(0.f, 0.f, 0.f);
 
@@ -305,6 +327,7 @@ __device__ __noinline__ bool path_shade(const LaunchArgs& A, PathState& P, const
     float3 dir, Le;
     float pdf_l = 0.0f, dist = INFINITY;
     bool valid = false;
+    int env_i = -1;
     if (pick_env) {
       const int y = cdf_pick_guided(S.env_marg, S.env_marg_guide, S.env_gm, u[1]);
       const float* cond = S.env_cond + (size_t)y * (S.env_w + 1);
@@ -318,7 +341,8 @@ __device__ __noinline__ bool path_shade(const LaunchArgs& A, PathState& P, const
       sincosf(theta, &st, &ct);
       sincosf(phi, &sp, &cp);
       dir = f3(st * cp, ct, st * sp);
-      Le = xyz(__ldg(&S.env[y * S.env_w + x]));
+      env_i = y * S.env_w + x;
+      Le = xyz(__ldg(&(A.params.env ? A.params.env : S.env)[env_i]));
       pdf_l = p_env * env_pdf_at(S, x, y, st);
       valid = pdf_l > 0.0f;
       P.fh.add(0x80000000u | (uint32_t)(y * S.env_w + x));
@@ -354,11 +378,18 @@ __device__ __noinline__ bool path_shade(const LaunchArgs& A, PathState& P, const
       P.sd = dir;
       P.stmax = pick_env ? INFINITY : dist * (1.0f - 1e-3f);
       const float w = power_heuristic(pdf_l, ev.pdf);
-      const float3 scale = Le * (wl.z * w / pdf_l);
+      const float s_env = wl.z * w / pdf_l;  // d scale / d Le
+      const float3 scale = Le * s_env;
       P.c_nee = P.beta * ev.f * scale;
       if (JVP) {
         const float3 f_dot = ev.df_alb * alb_dot + ev.df_alpha * alpha_dot;
         P.c_nee_dot = (P.beta_dot * ev.f + P.beta * f_dot) * scale;
+        if (env_i >= 0 && A.tangent.env)
+          P.c_nee_dot = P.c_nee_dot + P.beta * ev.f * xyz(__ldg(&A.tangent.env[env_i])) * s_env;
+      }
+      if (ADJ && EGRAD && grad_pass && env_i >= 0 && A.grads.env) {
+        P.nee_env = env_i;
+        P.nee_env_d = P.beta * ev.f * s_env;
       }
       if (ADJ && grad_pass) {
         P.r_nee_alb = ratio_grad(f3(1.f, 1.f, 1.f), f3(1.f, 1.f, 1.f), ev.df_alb, ev.f);
@@ -399,7 +430,7 @@ __device__ __noinline__ bool path_shade(const LaunchArgs& A, PathState& P, const
 }
 
 // Finish the vertex once the shadow ray is resolved.  Returns false if the path ended.
-template <bool ADJ, bool JVP, bool INSTR>
+template <bool ADJ, bool JVP, bool INSTR, bool EGRAD = false>
 __device__ __noinline__ bool path_finish(const LaunchArgs& A, PathState& P, bool occluded, bool grad_pass,
                                             float3 dl, GradSink& sink, Counters<INSTR>& cnt) {
   if (A.nee && P.mtype != PT_BSDF_DIELECTRIC && (A.scene.n_lights > 0 || A.scene.env_w > 0))
@@ -409,6 +440,7 @@ __device__ __noinline__ bool path_finish(const LaunchArgs& A, PathState& P, bool
     P.L = P.L + P.c_nee;
     P.Lrem = P.Lrem - P.c_nee;
     if (JVP) P.L_dot = P.L_dot + P.c_nee_dot;
+    if (ADJ && EGRAD && grad_pass && P.nee_env >= 0) sink.add_env<INSTR>(A, P.nee_env, dl * P.nee_env_d, cnt);
   }
   P.fh.add((uint32_t)P.lobe);
   if (P.delta_next) P.fh.add(0xfffffffeu);

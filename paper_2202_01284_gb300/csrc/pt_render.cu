@@ -55,7 +55,7 @@ __device__ __forceinline__ bool unit_pixel(const LaunchArgs& A, long long unit, 
 // Each thread owns the samples s = lane_in_pixel + k * lanes_per_pixel of one
 // pixel; in the adjoint every sample is traced twice (pass 0: radiance L,
 // pass 1: replay with L_rem and gradient scatter) by the same code.
-template <bool ADJ, bool JVP, bool INSTR, int LAYOUT, int DISPATCH>
+template <bool ADJ, bool JVP, bool INSTR, int LAYOUT, int DISPATCH, bool EGRAD = false>
 __device__ __forceinline__ void megakernel(const LaunchArgs& A, long long unit, const Tile& tile) {
   PixelOf px{};
   const bool valid = unit_pixel(A, unit, tile, px);
@@ -105,14 +105,14 @@ __device__ __forceinline__ void megakernel(const LaunchArgs& A, long long unit, 
       const bool grad_pass = ADJ && pass == 1;
       bool alive = true, finish = true, occ = false;
       if (!want_shadow) {
-        alive = path_shade<ADJ, JVP, INSTR, DISPATCH>(A, P, hit, grad_pass, cnt);
+        alive = path_shade<ADJ, JVP, INSTR, DISPATCH, EGRAD>(A, P, hit, grad_pass, dl, sink, cnt);
         finish = alive && !P.has_shadow;
         want_shadow = alive && P.has_shadow;
       } else {
         occ = hit.pos >= 0;
         want_shadow = false;
       }
-      if (finish) alive = path_finish<ADJ, JVP, INSTR>(A, P, occ, grad_pass, dl, sink, cnt);
+      if (finish) alive = path_finish<ADJ, JVP, INSTR, EGRAD>(A, P, occ, grad_pass, dl, sink, cnt);
       if (!alive) {
         has_path = false;
         if constexpr (!ADJ) {
@@ -213,6 +213,13 @@ __global__ void __launch_bounds__(256, PT_ADJ_MIN_BLOCKS) adjoint_kernel(const _
   megakernel<true, false, INSTR, LAYOUT, DISPATCH>(A, (long long)blockIdx.x * blockDim.x + threadIdx.x, crop_tile(A));
 }
 
+// The adjoint with environment-radiance gradients as well (emitter gradients).
+template <int LAYOUT>
+__global__ void __launch_bounds__(256, PT_ADJ_MIN_BLOCKS) adjoint_env_kernel(const __grid_constant__ LaunchArgs A) {
+  megakernel<true, false, false, LAYOUT, PT_DISPATCH_SWITCH, true>(A, (long long)blockIdx.x * blockDim.x + threadIdx.x,
+                                                                   crop_tile(A));
+}
+
 // image[pix] += sum_s q_beta[slot] * max(q_rgb[slot], 0) / spp  (cache-terminated render)
 __global__ void cache_resolve_kernel(float* __restrict__ image, const float* __restrict__ q_beta,
                                      const float* __restrict__ q_rgb, long long n_pix, int spp) {
@@ -264,7 +271,7 @@ constexpr int kJobBytes = (int)((offsetof(LaunchArgs, cams) + sizeof(DevCamera) 
 // dLoss/dI = 2 (I - T) / (3 W H) straight from the image and the job's target.
 // Two kernels rather than one keep each at the register footprint of its
 // single-job counterpart (one kernel holding both megakernels spills).
-template <bool ADJ, int LAYOUT>
+template <bool ADJ, int LAYOUT, bool EGRAD = false>
 __global__ void __launch_bounds__(256, ADJ ? PT_ADJ_MIN_BLOCKS : PT_FWD_MIN_BLOCKS)
     batch_kernel(const LaunchArgs* __restrict__ jobs, const BatchItem* __restrict__ items, int n_items, int tile,
                  unsigned* __restrict__ queue) {
@@ -289,7 +296,7 @@ __global__ void __launch_bounds__(256, ADJ ? PT_ADJ_MIN_BLOCKS : PT_FWD_MIN_BLOC
     }
     const Tile t{bi.x0, bi.y0, tile, tile, 1};
     const long long units = (long long)tile * tile * A.lanes_per_pixel;
-    for (long long b = 0; b < units; b += 32) megakernel<ADJ, false, false, LAYOUT, PT_DISPATCH_SWITCH>(A, b + lane, t);
+    for (long long b = 0; b < units; b += 32) megakernel<ADJ, false, false, LAYOUT, PT_DISPATCH_SWITCH, EGRAD>(A, b + lane, t);
   }
 }
 
@@ -322,6 +329,8 @@ int fill_launch(pt_scene* s, const pt_render_desc* r, const pt_params* p, Launch
   A.params.n_albedo = p->n_albedo;
   A.params.rough = p->roughness;
   A.params.n_rough = p->n_rough;
+  if (p->env && s->dev.env_w <= 0) return PT_ERR_ARG;  // no environment map to override
+  A.params.env = reinterpret_cast<const float4*>(p->env);
   for (int t = 0; t < PT_MAX_TEX; ++t) {
     A.params.tex[t] = reinterpret_cast<const float4*>(p->tex[t]);
     A.params.tex_w[t] = p->tex_w[t];
@@ -466,6 +475,8 @@ extern "C" int pt_render_backward(pt_scene* s, const pt_render_desc* r, const pt
   A.grads.albedo = g->albedo;
   A.grads.rough = g->roughness;
   for (int t = 0; t < PT_MAX_TEX; ++t) A.grads.tex[t] = reinterpret_cast<float4*>(g->tex[t]);
+  if (g->env && s->dev.env_w <= 0) return PT_ERR_ARG;
+  A.grads.env = reinterpret_cast<float4*>(g->env);
   A.grads.n_albedo = p->n_albedo;
   A.grads.n_rough = p->n_rough;
   int block;
@@ -479,8 +490,14 @@ extern "C" int pt_render_backward(pt_scene* s, const pt_render_desc* r, const pt
     A.cache_bounce = r->cache_bounce;
     A.q_rgb = cache_buffers(r->cache).q_rgb;
   }
-  const int v = (instrumented(r) ? 4 : 0) | (s->dev.layout == PT_BVH_WIDE ? 2 : 0) | (A.dispatch == PT_DISPATCH_MATCH ? 1 : 0);
   const dim3 gd((unsigned)grid), bd(block);
+  if (A.grads.env) {  // emitter gradients: their own instantiation (switch dispatch, no counters)
+    if (instrumented(r)) return PT_ERR_ARG;
+    if (s->dev.layout == PT_BVH_WIDE) adjoint_env_kernel<PT_BVH_WIDE><<<gd, bd, 0, cs>>>(A);
+    else adjoint_env_kernel<PT_BVH_BINARY><<<gd, bd, 0, cs>>>(A);
+    return cudaGetLastError() == cudaSuccess ? PT_OK : PT_ERR_CUDA;
+  }
+  const int v = (instrumented(r) ? 4 : 0) | (s->dev.layout == PT_BVH_WIDE ? 2 : 0) | (A.dispatch == PT_DISPATCH_MATCH ? 1 : 0);
   switch (v) {
     case 0: adjoint_kernel<false, PT_BVH_BINARY, PT_DISPATCH_SWITCH><<<gd, bd, 0, cs>>>(A); break;
     case 1: adjoint_kernel<false, PT_BVH_BINARY, PT_DISPATCH_MATCH><<<gd, bd, 0, cs>>>(A); break;
@@ -532,7 +549,31 @@ struct pt_batch {
   BatchItem* d_items = nullptr;   // forward items, then adjoint items
   unsigned* d_queue = nullptr;    // [2] work counters (forward, adjoint)
   int n_items = 0, n_adj_items = 0, tile = 4, block = 128, grid = 152, layout = PT_BVH_WIDE;
+  bool egrad = false;             // some job wants environment-radiance gradients
 };
+
+namespace {
+bool any_env_grads(const pt_job* jobs, int n_jobs) {
+  for (int j = 0; j < n_jobs; ++j)
+    if (jobs[j].grads.env) return true;
+  return false;
+}
+
+// Forward then adjoint persistent kernels over the two item lists.
+void launch_batch(int layout, bool egrad, int grid, int block, size_t smem, const LaunchArgs* jobs,
+                  const BatchItem* items, int n_fwd, int n_adj, int tile, unsigned* queue, cudaStream_t cs) {
+  const BatchItem* adj = items + n_fwd;
+  if (layout == PT_BVH_WIDE) {
+    batch_kernel<false, PT_BVH_WIDE><<<grid, block, smem, cs>>>(jobs, items, n_fwd, tile, queue);
+    if (n_adj && egrad) batch_kernel<true, PT_BVH_WIDE, true><<<grid, block, smem, cs>>>(jobs, adj, n_adj, tile, queue + 1);
+    else if (n_adj) batch_kernel<true, PT_BVH_WIDE><<<grid, block, smem, cs>>>(jobs, adj, n_adj, tile, queue + 1);
+  } else {
+    batch_kernel<false, PT_BVH_BINARY><<<grid, block, smem, cs>>>(jobs, items, n_fwd, tile, queue);
+    if (n_adj && egrad) batch_kernel<true, PT_BVH_BINARY, true><<<grid, block, smem, cs>>>(jobs, adj, n_adj, tile, queue + 1);
+    else if (n_adj) batch_kernel<true, PT_BVH_BINARY><<<grid, block, smem, cs>>>(jobs, adj, n_adj, tile, queue + 1);
+  }
+}
+}  // namespace
 
 extern "C" int pt_batch_create(const pt_job* jobs, int n_jobs, const pt_batch_opts* o, pt_batch** out) {
   if (!jobs || n_jobs <= 0 || !out) return PT_ERR_ARG;
@@ -577,6 +618,8 @@ extern "C" int pt_batch_create(const pt_job* jobs, int n_jobs, const pt_batch_op
     A.grads.albedo = jb.grads.albedo;
     A.grads.rough = jb.grads.roughness;
     for (int t = 0; t < PT_MAX_TEX; ++t) A.grads.tex[t] = reinterpret_cast<float4*>(jb.grads.tex[t]);
+    if (jb.grads.env && jb.scene->dev.env_w <= 0) return PT_ERR_ARG;
+    A.grads.env = reinterpret_cast<float4*>(jb.grads.env);
     A.grads.n_albedo = jb.params.n_albedo;
     A.grads.n_rough = jb.params.n_rough;
     for (int y0 = 0; y0 < jb.height; y0 += opts.tile)
@@ -608,6 +651,7 @@ extern "C" int pt_batch_create(const pt_job* jobs, int n_jobs, const pt_batch_op
   b->block = opts.block_size;
   b->grid = sms * opts.ctas_per_sm;
   b->layout = layout;
+  b->egrad = any_env_grads(jobs, n_jobs);
   bool ok = cudaMalloc(&b->d_jobs, sizeof(LaunchArgs) * n_jobs) == cudaSuccess &&
             cudaMalloc(&b->d_items, sizeof(BatchItem) * sorted.size()) == cudaSuccess &&
             cudaMalloc(&b->d_queue, 2 * sizeof(unsigned)) == cudaSuccess;
@@ -630,20 +674,8 @@ extern "C" int pt_batch_run(pt_batch* b, void* stream) {
   cudaStream_t cs = (cudaStream_t)stream;
   if (cudaMemsetAsync(b->d_queue, 0, 2 * sizeof(unsigned), cs) != cudaSuccess) return PT_ERR_CUDA;
   const size_t smem = (size_t)(b->block / 32) * kJobBytes;
-  const BatchItem* adj_items = b->d_items + b->n_items;
-  if (b->layout == PT_BVH_WIDE) {
-    batch_kernel<false, PT_BVH_WIDE><<<b->grid, b->block, smem, cs>>>(b->d_jobs, b->d_items, b->n_items, b->tile,
-                                                                        b->d_queue);
-    if (b->n_adj_items)
-      batch_kernel<true, PT_BVH_WIDE><<<b->grid, b->block, smem, cs>>>(b->d_jobs, adj_items, b->n_adj_items, b->tile,
-                                                                         b->d_queue + 1);
-  } else {
-    batch_kernel<false, PT_BVH_BINARY><<<b->grid, b->block, smem, cs>>>(b->d_jobs, b->d_items, b->n_items, b->tile,
-                                                                          b->d_queue);
-    if (b->n_adj_items)
-      batch_kernel<true, PT_BVH_BINARY><<<b->grid, b->block, smem, cs>>>(b->d_jobs, adj_items, b->n_adj_items,
-                                                                           b->tile, b->d_queue + 1);
-  }
+  launch_batch(b->layout, b->egrad, b->grid, b->block, smem, b->d_jobs, b->d_items, b->n_items, b->n_adj_items,
+               b->tile, b->d_queue, cs);
   return cudaGetLastError() == cudaSuccess ? PT_OK : PT_ERR_CUDA;
 }
 
@@ -751,6 +783,8 @@ extern "C" int pt_render_batch_noalloc(const pt_job* jobs, int n_jobs, const pt_
     A.grads.albedo = jb.grads.albedo;
     A.grads.rough = jb.grads.roughness;
     for (int t = 0; t < PT_MAX_TEX; ++t) A.grads.tex[t] = reinterpret_cast<float4*>(jb.grads.tex[t]);
+    if (jb.grads.env && jb.scene->dev.env_w <= 0) return PT_ERR_ARG;
+    A.grads.env = reinterpret_cast<float4*>(jb.grads.env);
     A.grads.n_albedo = jb.params.n_albedo;
     A.grads.n_rough = jb.params.n_rough;
     for (int y0 = 0; y0 < jb.height; y0 += opts.tile)
@@ -791,18 +825,8 @@ extern "C" int pt_render_batch_noalloc(const pt_job* jobs, int n_jobs, const pt_
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int grid = sms * opts.ctas_per_sm;
   const size_t smem = (size_t)(opts.block_size / 32) * kJobBytes;
-  if (layout == PT_BVH_WIDE) {
-    batch_kernel<false, PT_BVH_WIDE><<<grid, opts.block_size, smem, cs>>>(d_jobs, d_items, n_fwd, opts.tile, d_queue);
-    if (n_adj)
-      batch_kernel<true, PT_BVH_WIDE><<<grid, opts.block_size, smem, cs>>>(d_jobs, d_items + n_fwd, n_adj, opts.tile,
-                                                                             d_queue + 1);
-  } else {
-    batch_kernel<false, PT_BVH_BINARY><<<grid, opts.block_size, smem, cs>>>(d_jobs, d_items, n_fwd, opts.tile,
-                                                                              d_queue);
-    if (n_adj)
-      batch_kernel<true, PT_BVH_BINARY><<<grid, opts.block_size, smem, cs>>>(d_jobs, d_items + n_fwd, n_adj,
-                                                                               opts.tile, d_queue + 1);
-  }
+  launch_batch(layout, any_env_grads(jobs, n_jobs), grid, opts.block_size, smem, d_jobs, d_items, n_fwd, n_adj,
+               opts.tile, d_queue, cs);
   return cudaGetLastError() == cudaSuccess ? PT_OK : PT_ERR_CUDA;
 }
 
@@ -819,6 +843,8 @@ extern "C" int pt_render_jvp(pt_scene* s, const pt_render_desc* r, const pt_para
   A.tangent.n_albedo = tangent->n_albedo;
   A.tangent.rough = tangent->roughness;
   A.tangent.n_rough = tangent->n_rough;
+  if (tangent->env && s->dev.env_w <= 0) return PT_ERR_ARG;
+  A.tangent.env = reinterpret_cast<const float4*>(tangent->env);
   if (s->max_albedo_row >= 0 && tangent->albedo && tangent->n_albedo <= s->max_albedo_row) return PT_ERR_ARG;
   if (s->max_rough >= 0 && tangent->roughness && tangent->n_rough <= s->max_rough) return PT_ERR_ARG;
   for (int t = 0; t <= s->max_tex_slot; ++t) {

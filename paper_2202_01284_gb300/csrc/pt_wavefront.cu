@@ -182,16 +182,14 @@ __global__ void __launch_bounds__(kBlock, kShadeMinBlocks) wf_shade(const __grid
     PathState P;
     load_state(W, i, P);
     const Hit h = W.hit[i];
-    bool alive = path_shade<ADJ, false, false, DISPATCH>(A, P, h, grad_pass, cnt);
+    const float3 dl = grad_pass ? pixel_dl(A, P) : f3(0.f, 0.f, 0.f);
+    bool alive = path_shade<ADJ, false, false, DISPATCH, ADJ>(A, P, h, grad_pass, dl, sink, cnt);
     if (alive && P.has_shadow) {
       store_state(W, i, P);
       push(W.sq, &c[C_SHADOW], i);
       continue;
     }
-    if (alive) {
-      const float3 dl = grad_pass ? pixel_dl(A, P) : f3(0.f, 0.f, 0.f);
-      alive = path_finish<ADJ, false, false>(A, P, false, grad_pass, dl, sink, cnt);
-    }
+    if (alive) alive = path_finish<ADJ, false, false, ADJ>(A, P, false, grad_pass, dl, sink, cnt);
     if (alive) {
       store_state(W, i, P);
       push(W.q[(round + 1) & 1], &cn[C_RAY], i);
@@ -216,7 +214,7 @@ __global__ void __launch_bounds__(kBlock, kShadeMinBlocks) wf_finish(const __gri
     PathState P;
     load_state(W, i, P);
     const float3 dl = grad_pass ? pixel_dl(A, P) : f3(0.f, 0.f, 0.f);
-    const bool alive = path_finish<ADJ, false, false>(A, P, W.occ[i] != 0, grad_pass, dl, sink, cnt);
+    const bool alive = path_finish<ADJ, false, false, ADJ>(A, P, W.occ[i] != 0, grad_pass, dl, sink, cnt);
     if (alive) {
       store_state(W, i, P);
       push(W.q[(round + 1) & 1], &cn[C_RAY], i);
@@ -368,6 +366,8 @@ extern "C" int pt_wavefront_backward(pt_scene* s, const pt_render_desc* r, const
   A.grads.albedo = g->albedo;
   A.grads.rough = g->roughness;
   for (int t = 0; t < PT_MAX_TEX; ++t) A.grads.tex[t] = reinterpret_cast<float4*>(g->tex[t]);
+  if (g->env && s->dev.env_w <= 0) return PT_ERR_ARG;
+  A.grads.env = reinterpret_cast<float4*>(g->env);
   A.grads.n_albedo = p->n_albedo;
   A.grads.n_rough = p->n_rough;
   return run_wavefront<true>(s, A, o, (cudaStream_t)stream);

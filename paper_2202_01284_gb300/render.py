@@ -56,6 +56,9 @@ class DeviceScene:
         self.albedo = torch.as_tensor(scene.albedo, dtype=torch.float32).reshape(-1, 3).to(dev).contiguous()
         self.textures = [torch.as_tensor(t, dtype=torch.float32).to(dev).contiguous() for t in scene.textures]
         self.roughness = torch.as_tensor(scene.roughness, dtype=torch.float32).to(dev).contiguous()
+        # environment radiance (a differentiable emitter; sampling keeps the scene's map)
+        self.env = (torch.as_tensor(scene.env, dtype=torch.float32).to(dev).contiguous()
+                    if scene.env is not None else None)
         self.cameras = list(scene.cameras)
 
     def info(self) -> dict:
@@ -83,7 +86,7 @@ class DeviceScene:
                                st.cache, st.cache_bounce)
 
     def forward(self, st: RenderSettings, cams: Optional[Sequence[S.Camera]] = None, albedo=None, textures=None,
-                roughness=None, out=None, per_sample=False, counters=None):
+                roughness=None, out=None, per_sample=False, counters=None, env=None):
         cams = list(cams) if cams is not None else self.cameras
         rows, cols = st.rows_cols()
         dev = self.albedo.device
@@ -94,25 +97,25 @@ class DeviceScene:
             dh = torch.empty((len(cams), rows, cols, st.spp), device=dev, dtype=torch.int32)
         p = abi.params_struct(self.albedo if albedo is None else albedo,
                               self.textures if textures is None else textures,
-                              self.roughness if roughness is None else roughness)
+                              self.roughness if roughness is None else roughness, env)
         desc = self._desc(cams, st, dbg_L=dL, dbg_hash=dh, counters=counters)
         abi.pt_render_forward(self.handle, desc, p, img, torch.cuda.current_stream(dev).cuda_stream)
         return (img, dL, dh) if per_sample else img
 
     def backward(self, st: RenderSettings, grad_image, cams=None, albedo=None, textures=None, roughness=None,
-                 g_albedo=None, g_textures=None, g_roughness=None, seed=None, counters=None):
+                 g_albedo=None, g_textures=None, g_roughness=None, seed=None, counters=None, env=None, g_env=None):
         cams = list(cams) if cams is not None else self.cameras
         p = abi.params_struct(self.albedo if albedo is None else albedo,
                               self.textures if textures is None else textures,
-                              self.roughness if roughness is None else roughness)
-        g = abi.grads_struct(g_albedo, g_textures or (), g_roughness)
+                              self.roughness if roughness is None else roughness, env)
+        g = abi.grads_struct(g_albedo, g_textures or (), g_roughness, g_env)
         desc = self._desc(cams, st, seed=seed, counters=counters)
         abi.pt_render_backward(self.handle, desc, p, grad_image.contiguous(), g,
                                torch.cuda.current_stream(grad_image.device).cuda_stream)
 
     # ------------------------------------------------------------------ wavefront variant
     def wavefront_forward(self, st: RenderSettings, calls: int = abi.PT_WF_TRACED, wave_paths: int = 0, cams=None,
-                          albedo=None, textures=None, roughness=None, out=None, per_sample=False):
+                          albedo=None, textures=None, roughness=None, out=None, per_sample=False, env=None):
         """pt_wavefront_forward: the same image as forward(), one kernel per stage."""
         cams = list(cams) if cams is not None else self.cameras
         rows, cols = st.rows_cols()
@@ -124,7 +127,7 @@ class DeviceScene:
             dh = torch.empty((len(cams), rows, cols, st.spp), device=dev, dtype=torch.int32)
         p = abi.params_struct(self.albedo if albedo is None else albedo,
                               self.textures if textures is None else textures,
-                              self.roughness if roughness is None else roughness)
+                              self.roughness if roughness is None else roughness, env)
         desc = self._desc(cams, st, dbg_L=dL, dbg_hash=dh)
         abi.pt_wavefront_forward(self.handle, desc, p, abi.pt_wavefront_opts(calls, wave_paths), img,
                                  torch.cuda.current_stream(dev).cuda_stream)
@@ -132,19 +135,19 @@ class DeviceScene:
 
     def wavefront_backward(self, st: RenderSettings, grad_image, calls: int = abi.PT_WF_TRACED, wave_paths: int = 0,
                            cams=None, albedo=None, textures=None, roughness=None, g_albedo=None, g_textures=None,
-                           g_roughness=None, seed=None):
+                           g_roughness=None, seed=None, env=None, g_env=None):
         """pt_wavefront_backward: the same gradients as backward(), one kernel per stage."""
         cams = list(cams) if cams is not None else self.cameras
         p = abi.params_struct(self.albedo if albedo is None else albedo,
                               self.textures if textures is None else textures,
-                              self.roughness if roughness is None else roughness)
-        g = abi.grads_struct(g_albedo, g_textures or (), g_roughness)
+                              self.roughness if roughness is None else roughness, env)
+        g = abi.grads_struct(g_albedo, g_textures or (), g_roughness, g_env)
         desc = self._desc(cams, st, seed=seed)
         abi.pt_wavefront_backward(self.handle, desc, p, abi.pt_wavefront_opts(calls, wave_paths),
                                   grad_image.contiguous(), g, torch.cuda.current_stream(grad_image.device).cuda_stream)
 
     def jvp(self, st: RenderSettings, t_albedo=None, t_textures=None, t_roughness=None, cams=None, albedo=None,
-            textures=None, roughness=None):
+            textures=None, roughness=None, t_env=None, env=None):
         """(image, image_dot): the render and its derivative along the parameter
         direction (t_albedo, t_textures, t_roughness); None members are zero."""
         cams = list(cams) if cams is not None else self.cameras
@@ -154,9 +157,9 @@ class DeviceScene:
         dot = torch.empty_like(img)
         textures = self.textures if textures is None else textures
         p = abi.params_struct(self.albedo if albedo is None else albedo, textures,
-                              self.roughness if roughness is None else roughness)
+                              self.roughness if roughness is None else roughness, env)
         tt = list(t_textures) if t_textures is not None else []
-        t = abi.params_struct(t_albedo, [], t_roughness)
+        t = abi.params_struct(t_albedo, [], t_roughness, t_env.contiguous() if t_env is not None else None)
         for i, x in enumerate(tt):
             if x is not None:
                 t.tex[i] = abi._ptr(x.contiguous())
@@ -172,49 +175,57 @@ class DeviceScene:
 
 
 class RenderFn(torch.autograd.Function):
-    """image = render(albedo, texture_0..k, roughness); backward = path replay backpropagation.
+    """image = render(albedo, roughness, env, texture_0..k); backward = path replay
+    backpropagation; forward-mode (torch.autograd.forward_ad) = pt_render_jvp.
 
-    The backward seed is ``settings.backward_seed`` if given (decorrelated, as the
+    env may be None (the scene's environment map, not differentiated).  The
+    backward seed is ``settings.backward_seed`` if given (decorrelated, as the
     paper's three-phase PRB step does), else the forward seed (correlated).
     """
 
     @staticmethod
-    def forward(ctx, dscene: DeviceScene, st: RenderSettings, albedo, roughness, *textures):
+    def forward(ctx, dscene: DeviceScene, st: RenderSettings, albedo, roughness, env, *textures):
         ctx.dscene = dscene
         ctx.st = st
-        ctx.save_for_backward(albedo, roughness, *textures)
-        ctx.primal = (albedo.detach(), roughness.detach(), [t.detach() for t in textures])
-        return dscene.forward(st, albedo=albedo.detach().contiguous(), roughness=roughness.detach().contiguous(),
-                              textures=[t.detach().contiguous() for t in textures])
+        ctx.has_env = env is not None
+        ctx.save_for_backward(albedo, roughness, *( [env] if env is not None else [] ), *textures)
+        ctx.primal = (albedo.detach().contiguous(), roughness.detach().contiguous(),
+                      env.detach().contiguous() if env is not None else None,
+                      [t.detach().contiguous() for t in textures])
+        a, r, e, tx = ctx.primal
+        return dscene.forward(st, albedo=a, roughness=r, textures=tx, env=e)
 
     @staticmethod
-    def jvp(ctx, _scene, _st, t_albedo, t_roughness, *t_textures):
-        """Forward-mode derivative (torch.autograd.forward_ad): the image tangent
-        along the input tangents, from one pt_render_jvp pass."""
-        albedo, roughness, textures = ctx.primal
+    def jvp(ctx, _scene, _st, t_albedo, t_roughness, t_env, *t_textures):
+        """The image tangent along the input tangents, from one pt_render_jvp pass."""
+        a, r, e, tx = ctx.primal
         _, dot = ctx.dscene.jvp(ctx.st, t_albedo=t_albedo, t_roughness=t_roughness,
                                 t_textures=[t.contiguous() if t is not None else None for t in t_textures],
-                                albedo=albedo.detach().contiguous(), roughness=roughness.detach().contiguous(),
-                                textures=[t.detach().contiguous() for t in textures])
+                                t_env=t_env if ctx.has_env else None,
+                                albedo=a, roughness=r, textures=tx, env=e)
         return dot
 
     @staticmethod
     def backward(ctx, grad_img):
-        albedo, roughness, *textures = ctx.saved_tensors
+        saved = ctx.saved_tensors
+        albedo, roughness = saved[0], saved[1]
+        env = saved[2] if ctx.has_env else None
+        textures = saved[3:] if ctx.has_env else saved[2:]
         ga = torch.zeros_like(albedo) if ctx.needs_input_grad[2] else None
         gr = torch.zeros_like(roughness) if ctx.needs_input_grad[3] else None
-        gt = [torch.zeros_like(t) if ctx.needs_input_grad[4 + i] else None for i, t in enumerate(textures)]
+        ge = torch.zeros_like(env) if ctx.has_env and ctx.needs_input_grad[4] else None
+        gt = [torch.zeros_like(t) if ctx.needs_input_grad[5 + i] else None for i, t in enumerate(textures)]
         st = ctx.st
         seed = st.backward_seed if st.backward_seed is not None else st.seed
-        ctx.dscene.backward(st, grad_img.contiguous(), albedo=albedo.detach(), roughness=roughness.detach(),
-                            textures=[t.detach() for t in textures], g_albedo=ga,
-                            g_textures=[g if g is not None else None for g in gt] if any(g is not None for g in gt) else None,
-                            g_roughness=gr, seed=seed)
-        return (None, None, ga, gr, *gt)
+        a, r, e, tx = ctx.primal
+        ctx.dscene.backward(st, grad_img.contiguous(), albedo=a, roughness=r, textures=tx, env=e, g_albedo=ga,
+                            g_textures=gt if any(g is not None for g in gt) else None, g_roughness=gr, g_env=ge,
+                            seed=seed)
+        return (None, None, ga, gr, ge, *gt)
 
 
-def render(dscene: DeviceScene, st: RenderSettings, albedo, roughness, textures: Sequence[torch.Tensor]):
-    return RenderFn.apply(dscene, st, albedo, roughness, *textures)
+def render(dscene: DeviceScene, st: RenderSettings, albedo, roughness, textures: Sequence[torch.Tensor], env=None):
+    return RenderFn.apply(dscene, st, albedo, roughness, env, *textures)
 
 
 class RadianceCache:
