@@ -65,6 +65,8 @@ def parse():
     ap.add_argument("--wavefront", action="store_true",
                     help="megakernel vs wavefront ablation, forward and adjoint (own JSON line)")
     ap.add_argument("--wave-paths", type=int, default=0)
+    ap.add_argument("--ckpt", action="store_true",
+                    help="PRB vs reverse mode with checkpoints, one gradient step each (own JSON line)")
     ap.add_argument("--peaks", action="store_true",
                     help="microbenchmarks of the memory-side roofs (L2-resident reads, atomics) as a JSON line")
     ap.add_argument("--small", action="store_true",
@@ -516,6 +518,83 @@ def run_wavefront_experiment(args):
     print(json.dumps(line), flush=True)
 
 
+def run_ckpt_experiment(args):
+    """PRB against reverse mode with checkpoints (one per path vertex) on the
+    throughput workload: one gradient step each (forward image, L2-loss image
+    gradient, reverse pass), plus the checkpoint memory.  Own JSON line."""
+    import torch
+
+    from paper_2202_01284_gb300 import abi
+    from paper_2202_01284_gb300.render import Checkpoints, DeviceScene, ckpt_backward, ckpt_forward
+    abi.load()
+    dev = torch.device("cuda", 0)
+    sc, tgt_tex = make_workload(small=args.small)
+    layout = abi.PT_BVH_WIDE if args.bvh == "wide" else abi.PT_BVH_BINARY
+    ds = DeviceScene(sc, layout=layout, device=dev)
+    st = settings(args, 11)
+    target = ds.forward(settings(args, 77), textures=[torch.as_tensor(tgt_tex, device=dev)]).clone()
+    img = torch.empty_like(target)
+    grad_img = torch.empty_like(target)
+    g_tex = torch.zeros_like(ds.textures[0])
+    g_rough = torch.zeros_like(ds.roughness)
+    ck = Checkpoints(st.width * st.height * st.spp, st.max_depth)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def prb(ev):
+        ev[0].record(stream)
+        ds.forward(st, out=img)
+        torch.sub(img, target, out=grad_img)
+        grad_img.mul_(2.0 / img.numel())
+        ev[1].record(stream)
+        ds.backward(st, grad_img, g_textures=[g_tex], g_roughness=g_rough, seed=12)
+        ev[2].record(stream)
+
+    def ckpt(ev):
+        ev[0].record(stream)
+        ckpt_forward(ds, st, ck, out=img)
+        torch.sub(img, target, out=grad_img)
+        grad_img.mul_(2.0 / img.numel())
+        ev[1].record(stream)
+        ckpt_backward(ds, st, ck, grad_img, g_textures=[g_tex], g_roughness=g_rough)
+        ev[2].record(stream)
+
+    dummy = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    for _ in range(max(3, args.warmup)):
+        prb(dummy)
+        ckpt(dummy)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    clocks.start()
+    res = {"prb": [], "ckpt": []}
+    for k in range(args.steps):
+        for name, fn in (("prb", prb), ("ckpt", ckpt)):
+            flush.fill_(float(k))
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            fn(ev)
+            res[name].append(ev)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+
+    def avg(name, a, b):
+        return statistics.mean(e[a].elapsed_time(e[b]) for e in res[name])
+    out = {k: {"forward_ms": round(avg(k, 0, 1), 3), "reverse_ms": round(avg(k, 1, 2), 3),
+               "step_ms": round(avg(k, 0, 2), 3)} for k in res}
+    line = {"metric": "gradient step: PRB vs reverse mode with checkpoints (ms, memory)",
+            "value": round(out["ckpt"]["step_ms"] / out["prb"]["step_ms"], 3),
+            "unit": "x time of the checkpointed step relative to the PRB step", "n_gpus": 1, "steps": args.steps,
+            "warmup": max(3, args.warmup), "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD["workload"] if not args.small else "spheres 256x256 64 spp",
+                       "l2": "flushed before each timed step", "prb": out["prb"], "ckpt": out["ckpt"],
+                       "ckpt_bytes": ck.nbytes, "prb_scratch_bytes": 0,
+                       "prb_seed": "decorrelated (radiance pass + replay)",
+                       "ckpt_seed": "the forward's (reverse sweep over stored vertices)"},
+            "clocks": clk}
+    print(json.dumps(line), flush=True)
+    ck.close()
+
+
 def run_cache_experiment(args):
     """Cornell box at 1024^2, depth 4: plain PT at 64 spp vs cache-terminated PT (bounce 1
     and 2) at the spp that fits the same per-frame time including one online training
@@ -753,6 +832,8 @@ def main():
         run_jvp_experiment(args)
     elif args.wavefront:
         run_wavefront_experiment(args)
+    elif args.ckpt:
+        run_ckpt_experiment(args)
     else:
         run_ours(args)
 

@@ -326,6 +326,31 @@ int pt_wavefront_backward(pt_scene* scene, const pt_render_desc* desc, const pt_
                           const pt_wavefront_opts* opts, const float* grad_image, const pt_grads* grads,
                           void* stream);
 
+/* Reverse mode with checkpoints (Sec. 5: differentiating a standard path tracer
+ * whose loop keeps one checkpoint per scattering event, against PRB).
+ * pt_ckpt_forward renders like pt_render_forward and stores, before every
+ * closest-hit ray, the loop state of the path (PCG32 state, ray, throughput, MIS
+ * state, depth: 64 B) plus each sample's vertex count.  pt_ckpt_backward, called
+ * with the same scene, desc and params, recomputes each sample's vertices from
+ * their checkpoints last to first and accumulates the gradients of
+ * sum(grad_image * image) like pt_render_backward with the forward's seed (the
+ * same estimator; no radiance pass, the radiance of the later vertices is summed
+ * on the way back).  Gradients as pt_render_backward, including env.
+ * The buffer holds max_samples (n_cams * rows * cols * spp of a call) x max_depth
+ * checkpoints; pt_ckpt_create allocates it (cudaMalloc, synchronous) and clears
+ * the counts.  Calls with more samples or depth than the buffer holds, counters,
+ * per-sample outputs or a cache are PT_ERR_ARG.  A backward call after a forward
+ * with a different desc reads whatever checkpoints are stored (vertex counts are
+ * clamped to the buffer, so it stays in bounds) and returns a wrong gradient. */
+typedef struct pt_ckpt pt_ckpt;
+int pt_ckpt_create(int64_t max_samples, int32_t max_depth, pt_ckpt** out);
+void pt_ckpt_destroy(pt_ckpt* ckpt);
+int pt_ckpt_bytes(const pt_ckpt* ckpt, int64_t* bytes);
+int pt_ckpt_forward(pt_scene* scene, const pt_render_desc* desc, const pt_params* params, pt_ckpt* ckpt,
+                    float* image, void* stream);
+int pt_ckpt_backward(pt_scene* scene, const pt_render_desc* desc, const pt_params* params, pt_ckpt* ckpt,
+                     const float* grad_image, const pt_grads* grads, void* stream);
+
 /* Reads (and clears) the scene's device status word after synchronising
  * `stream`: *out = PT_OK or the first PT_ERR_* a kernel recorded. */
 int pt_last_device_status(pt_scene* scene, void* stream, int* out);

@@ -136,6 +136,13 @@ SIGNATURES = {
                               C.POINTER(pt_wavefront_opts), C.c_void_p, C.c_void_p], C.c_int),
     "pt_wavefront_backward": ([C.c_void_p, C.POINTER(pt_render_desc), C.POINTER(pt_params),
                                C.POINTER(pt_wavefront_opts), C.c_void_p, C.POINTER(pt_grads), C.c_void_p], C.c_int),
+    "pt_ckpt_create": ([C.c_int64, C.c_int32, C.POINTER(C.c_void_p)], C.c_int),
+    "pt_ckpt_destroy": ([C.c_void_p], None),
+    "pt_ckpt_bytes": ([C.c_void_p, C.POINTER(C.c_int64)], C.c_int),
+    "pt_ckpt_forward": ([C.c_void_p, C.POINTER(pt_render_desc), C.POINTER(pt_params), C.c_void_p, C.c_void_p,
+                         C.c_void_p], C.c_int),
+    "pt_ckpt_backward": ([C.c_void_p, C.POINTER(pt_render_desc), C.POINTER(pt_params), C.c_void_p, C.c_void_p,
+                          C.POINTER(pt_grads), C.c_void_p], C.c_int),
     "pt_last_device_status": ([C.c_void_p, C.c_void_p, C.POINTER(C.c_int)], C.c_int),
     "pt_status_string": ([C.c_int], C.c_char_p),
     "pt_cache_create": ([C.POINTER(pt_cache_desc), C.POINTER(C.c_void_p)], C.c_int),
@@ -339,6 +346,33 @@ def pt_wavefront_backward(handle: int, desc: pt_render_desc, params: pt_params, 
     check("pt_wavefront_backward", load().pt_wavefront_backward(handle, C.byref(desc), C.byref(params),
                                                                 C.byref(opts), _ptr(grad_image), C.byref(grads),
                                                                 stream or None))
+
+
+def pt_ckpt_create(max_samples: int, max_depth: int) -> int:
+    h = C.c_void_p()
+    check("pt_ckpt_create", load().pt_ckpt_create(max_samples, max_depth, C.byref(h)))
+    return h.value
+
+
+def pt_ckpt_destroy(handle: int) -> None:
+    load().pt_ckpt_destroy(handle)
+
+
+def pt_ckpt_bytes(handle: int) -> int:
+    v = C.c_int64(0)
+    check("pt_ckpt_bytes", load().pt_ckpt_bytes(handle, C.byref(v)))
+    return v.value
+
+
+def pt_ckpt_forward(handle: int, desc: pt_render_desc, params: pt_params, ckpt: int, image, stream: int = 0) -> None:
+    check("pt_ckpt_forward", load().pt_ckpt_forward(handle, C.byref(desc), C.byref(params), ckpt, _ptr(image),
+                                                    stream or None))
+
+
+def pt_ckpt_backward(handle: int, desc: pt_render_desc, params: pt_params, ckpt: int, grad_image, grads: pt_grads,
+                     stream: int = 0) -> None:
+    check("pt_ckpt_backward", load().pt_ckpt_backward(handle, C.byref(desc), C.byref(params), ckpt,
+                                                      _ptr(grad_image), C.byref(grads), stream or None))
 
 
 def pt_last_device_status(handle: int, stream: int = 0) -> int:

@@ -103,6 +103,11 @@ struct alignas(16) LaunchArgs {
   float* path_L;       // [slots][3]
   unsigned* r_count;   // records written (may exceed max_records: extra ones dropped)
   long long max_records;
+  // reverse-mode checkpoints (one per path vertex): 4 words of 16 B per vertex,
+  // word-major [vertex][word][slot]; ck_count[slot] = vertices of the sample
+  uint4* ck_state;
+  int* ck_count;
+  long long ck_slots;
   DevCamera cams[PT_MAX_CAMS];
 };
 static_assert(sizeof(LaunchArgs) % 16 == 0, "job records are copied with 16-byte loads");

@@ -7,193 +7,10 @@
 #include <new>
 #include <vector>
 
-#include "pt_path.cuh"
+#include "pt_mega.cuh"
 
 namespace ptgb {
 
-template <bool INSTR>
-__device__ __forceinline__ void flush_counters(const LaunchArgs& A, Counters<INSTR>& cnt) {
-  if constexpr (INSTR) {
-    if (A.counters) {
-#pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        unsigned long long v = cnt.c[i];
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-        if (lane_id() == 0 && v) atomicAdd(&A.counters[i], v);
-      }
-    }
-  }
-}
-
-struct PixelOf {
-  int cam, px, py;
-  long long pix;  // dense index of the pixel in the output image
-};
-// A rectangle of pixels (of n_cams cameras) processed by one launch or one work item.
-struct Tile {
-  int x0, y0, w, h, n_cams;
-};
-// Pixel of `unit` (pixel-major, lanes_per_pixel consecutive units per pixel) inside
-// the tile; false if the unit lies outside the tile or outside the image crop.
-__device__ __forceinline__ bool unit_pixel(const LaunchArgs& A, long long unit, const Tile& t, PixelOf& r) {
-  const long long pix = unit >> A.log2_lanes;
-  const long long per_cam = (long long)t.w * t.h;
-  if (unit < 0 || pix >= per_cam * t.n_cams) return false;
-  r.cam = (int)(pix / per_cam);
-  const long long rem = pix - (long long)r.cam * per_cam;
-  const int iy = (int)(rem / t.w);
-  const int ix = (int)(rem - (long long)iy * t.w);
-  r.px = t.x0 + ix;
-  r.py = t.y0 + iy;
-  if (r.px >= A.crop_x0 + A.crop_w || r.py >= A.crop_y0 + A.crop_h) return false;
-  r.pix = ((long long)r.cam * A.crop_h + (r.py - A.crop_y0)) * A.crop_w + (r.px - A.crop_x0);
-  return true;
-}
-
-// The megakernel: forward (ADJ = false) or fused PRB adjoint (ADJ = true).
-// Each thread owns the samples s = lane_in_pixel + k * lanes_per_pixel of one
-// pixel; in the adjoint every sample is traced twice (pass 0: radiance L,
-// pass 1: replay with L_rem and gradient scatter) by the same code.
-template <bool ADJ, bool JVP, bool INSTR, int LAYOUT, int DISPATCH, bool EGRAD = false>
-__device__ __forceinline__ void megakernel(const LaunchArgs& A, long long unit, const Tile& tile) {
-  PixelOf px{};
-  const bool valid = unit_pixel(A, unit, tile, px);
-  Counters<INSTR> cnt;
-  if constexpr (INSTR) {
-    for (int i = 0; i < 8; ++i) cnt.c[i] = 0;
-  }
-  GradSink sink;
-  const int lane_in_pix = (int)(unit & (A.lanes_per_pixel - 1));
-  float3 dl = f3(0.f, 0.f, 0.f);
-  if (valid) {
-    if constexpr (ADJ) {
-      const float inv = 1.0f / (float)A.spp;
-      if (A.target) {  // batched jobs: L2 loss against the job's target
-        const float k = 2.0f * A.loss_scale * inv;
-        dl = f3((A.image[3 * px.pix] - A.target[3 * px.pix]) * k, (A.image[3 * px.pix + 1] - A.target[3 * px.pix + 1]) * k,
-                (A.image[3 * px.pix + 2] - A.target[3 * px.pix + 2]) * k);
-      } else {
-        dl = f3(A.grad_image[3 * px.pix] * inv, A.grad_image[3 * px.pix + 1] * inv, A.grad_image[3 * px.pix + 2] * inv);
-      }
-    }
-  }
-  float3 pix_sum = f3(0.f, 0.f, 0.f);
-  float3 pix_sum_dot = f3(0.f, 0.f, 0.f);
-  float3 L_pass0 = f3(0.f, 0.f, 0.f);
-  int next_s = lane_in_pix;
-  int pass = 0;
-  bool has_path = false;
-  bool want_shadow = false;  // the lane's next traversal is its pending shadow ray
-  PathState P;
-  for (;;) {
-    if (!has_path && valid && next_s < A.spp) {
-      // one call site for both passes: the replay starts from identical code
-      path_start<INSTR>(A, P, ADJ ? A.seed_adj : A.seed, px.cam, px.px, px.py, next_s, px.pix, cnt);
-      P.Lrem = L_pass0;
-      has_path = true;
-      want_shadow = false;
-    }
-    if (!__any_sync(0xffffffffu, has_path)) break;
-    if (has_path) {
-      // one traversal per lane per iteration: its path ray or its shadow ray
-      cnt.add(want_shadow ? 2 : 1, 1);
-      const float3 o = want_shadow ? P.so : P.ro, d = want_shadow ? P.sd : P.rd;
-      const float tmax = want_shadow ? P.stmax : INFINITY;
-      const Hit hit = LAYOUT == PT_BVH_WIDE ? trace_wide<INSTR>(A.scene, o, d, tmax, want_shadow, cnt)
-                                            : trace_binary<INSTR>(A.scene, o, d, tmax, want_shadow, cnt);
-      const bool grad_pass = ADJ && pass == 1;
-      bool alive = true, finish = true, occ = false;
-      if (!want_shadow) {
-        alive = path_shade<ADJ, JVP, INSTR, DISPATCH, EGRAD>(A, P, hit, grad_pass, dl, sink, cnt);
-        finish = alive && !P.has_shadow;
-        want_shadow = alive && P.has_shadow;
-      } else {
-        occ = hit.pos >= 0;
-        want_shadow = false;
-      }
-      if (finish) alive = path_finish<ADJ, JVP, INSTR, EGRAD>(A, P, occ, grad_pass, dl, sink, cnt);
-      if (!alive) {
-        has_path = false;
-        if constexpr (!ADJ) {
-          if (A.cache_mode == 1 && !P.cache_done) {  // no cache query for this sample
-            float* r = A.q_raw + P.slot * 10;
-#pragma unroll
-            for (int k = 0; k < 10; ++k) r[k] = 0.0f;
-            float* b = A.q_beta + P.slot * 3;
-            b[0] = b[1] = b[2] = 0.0f;
-          } else if (A.cache_mode == 3) {
-            float* pl = A.path_L + P.slot * 3;
-            pl[0] = P.L.x;
-            pl[1] = P.L.y;
-            pl[2] = P.L.z;
-          }
-        }
-        if (ADJ && pass == 0) {
-          L_pass0 = P.L;  // replay the same sample next: L_rem starts from its radiance
-          pass = 1;
-        } else {
-          pix_sum = pix_sum + P.L;
-          if (JVP) pix_sum_dot = pix_sum_dot + P.L_dot;
-          if constexpr (INSTR && !ADJ) {
-            const long long si = px.pix * A.spp + next_s;
-            if (A.dbg_L) {
-              A.dbg_L[3 * si] = P.L.x;
-              A.dbg_L[3 * si + 1] = P.L.y;
-              A.dbg_L[3 * si + 2] = P.L.z;
-            }
-            if (A.dbg_hash) A.dbg_hash[si] = P.fh.h;
-          }
-          next_s += A.lanes_per_pixel;
-          pass = 0;
-          L_pass0 = f3(0.f, 0.f, 0.f);
-        }
-      }
-    }
-  }
-  if constexpr (!ADJ) {
-    for (int off = 1; off < A.lanes_per_pixel; off <<= 1) {
-      pix_sum.x += __shfl_xor_sync(0xffffffffu, pix_sum.x, off);
-      pix_sum.y += __shfl_xor_sync(0xffffffffu, pix_sum.y, off);
-      pix_sum.z += __shfl_xor_sync(0xffffffffu, pix_sum.z, off);
-    }
-    if constexpr (JVP) {
-      for (int off = 1; off < A.lanes_per_pixel; off <<= 1) {
-        pix_sum_dot.x += __shfl_xor_sync(0xffffffffu, pix_sum_dot.x, off);
-        pix_sum_dot.y += __shfl_xor_sync(0xffffffffu, pix_sum_dot.y, off);
-        pix_sum_dot.z += __shfl_xor_sync(0xffffffffu, pix_sum_dot.z, off);
-      }
-    }
-    if (valid && lane_in_pix == 0 && A.image) {
-      const float inv = 1.0f / (float)A.spp;
-      A.image[3 * px.pix] = pix_sum.x * inv;
-      A.image[3 * px.pix + 1] = pix_sum.y * inv;
-      A.image[3 * px.pix + 2] = pix_sum.z * inv;
-      if (JVP) {
-        A.image_dot[3 * px.pix] = pix_sum_dot.x * inv;
-        A.image_dot[3 * px.pix + 1] = pix_sum_dot.y * inv;
-        A.image_dot[3 * px.pix + 2] = pix_sum_dot.z * inv;
-      }
-    }
-  }
-  flush_counters<INSTR>(A, cnt);
-}
-
-// Minimum resident CTAs of 256 threads per SM requested from ptxas (register cap).
-// Measured on the 196k-triangle sphere workload (forward + adjoint step): with the
-// per-vertex shading out of line, more resident warps beat fewer spills -- the
-// forward runs best at 4 CTAs (64 registers, 48 vs 62 ms at 128 registers), the
-// adjoint at 3 (85 registers, 135 vs 148 ms).
-#ifndef PT_FWD_MIN_BLOCKS
-#define PT_FWD_MIN_BLOCKS 4
-#endif
-#ifndef PT_ADJ_MIN_BLOCKS
-#define PT_ADJ_MIN_BLOCKS 3
-#endif
-
-__device__ __forceinline__ Tile crop_tile(const LaunchArgs& A) {
-  return Tile{A.crop_x0, A.crop_y0, A.crop_w, A.crop_h, A.n_cams};
-}
 
 template <bool INSTR, int LAYOUT, int DISPATCH>
 __global__ void __launch_bounds__(256, PT_FWD_MIN_BLOCKS) forward_kernel(const __grid_constant__ LaunchArgs A) {

@@ -174,6 +174,50 @@ class DeviceScene:
         return abi.pt_last_device_status(self.handle, torch.cuda.current_stream().cuda_stream)
 
 
+class Checkpoints:
+    """Owner of a pt_ckpt buffer (reverse mode with one checkpoint per path vertex)."""
+
+    def __init__(self, max_samples: int, max_depth: int):
+        self.handle = abi.pt_ckpt_create(max_samples, max_depth)
+
+    @property
+    def nbytes(self) -> int:
+        return abi.pt_ckpt_bytes(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            abi.pt_ckpt_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def ckpt_forward(dscene: DeviceScene, st: RenderSettings, ck: Checkpoints, cams=None, out=None, env=None):
+    """pt_ckpt_forward: the image, storing a checkpoint per path vertex in `ck`."""
+    cams = list(cams) if cams is not None else dscene.cameras
+    rows, cols = st.rows_cols()
+    dev = dscene.albedo.device
+    img = out if out is not None else torch.empty((len(cams), rows, cols, 3), device=dev, dtype=torch.float32)
+    p = abi.params_struct(dscene.albedo, dscene.textures, dscene.roughness, env)
+    abi.pt_ckpt_forward(dscene.handle, dscene._desc(cams, st), p, ck.handle, img,
+                        torch.cuda.current_stream(dev).cuda_stream)
+    return img
+
+
+def ckpt_backward(dscene: DeviceScene, st: RenderSettings, ck: Checkpoints, grad_image, cams=None, g_albedo=None,
+                  g_textures=None, g_roughness=None, g_env=None, env=None):
+    """pt_ckpt_backward: gradients from the checkpoints of the last ckpt_forward."""
+    cams = list(cams) if cams is not None else dscene.cameras
+    p = abi.params_struct(dscene.albedo, dscene.textures, dscene.roughness, env)
+    g = abi.grads_struct(g_albedo, g_textures or (), g_roughness, g_env)
+    abi.pt_ckpt_backward(dscene.handle, dscene._desc(cams, st), p, ck.handle, grad_image.contiguous(), g,
+                         torch.cuda.current_stream(grad_image.device).cuda_stream)
+
+
 class RenderFn(torch.autograd.Function):
     """image = render(albedo, roughness, env, texture_0..k); backward = path replay
     backpropagation; forward-mode (torch.autograd.forward_ad) = pt_render_jvp.
