@@ -27,12 +27,12 @@ namespace {
 
 template <int LAYOUT>
 __global__ void __launch_bounds__(256, PT_FWD_MIN_BLOCKS) ckpt_forward_kernel(const __grid_constant__ LaunchArgs A) {
-  megakernel<false, false, false, LAYOUT, PT_DISPATCH_SWITCH, false, true>(
+  megakernel<false, false, false, LAYOUT, PT_DISPATCH_SWITCH, FEAT_CKPT>(
       A, (long long)blockIdx.x * blockDim.x + threadIdx.x, crop_tile(A));
 }
 
 // Finish vertex k of the reverse sweep and fold its radiance into S.
-template <bool EGRAD>
+template <int FEAT>
 __device__ __forceinline__ void reverse_finish(const LaunchArgs& A, PathState& P, bool alive, bool occluded,
                                                float3& S, float3 dl, GradSink& sink, Counters<false>& cnt) {
   if (alive) {
@@ -40,7 +40,7 @@ __device__ __forceinline__ void reverse_finish(const LaunchArgs& A, PathState& P
     // radiance that flows through this vertex's sampled direction: everything the
     // later vertices contributed (path_finish removes the light sample again)
     P.Lrem = (lit ? P.c_nee : f3(0.f, 0.f, 0.f)) + S;
-    path_finish<true, false, false, EGRAD>(A, P, occluded, true, dl, sink, cnt);
+    path_finish<true, false, false, FEAT>(A, P, occluded, true, dl, sink, cnt);
   }
   S = S + P.L;  // this vertex's own emission and light sample
 }
@@ -49,6 +49,7 @@ __device__ __forceinline__ void reverse_finish(const LaunchArgs& A, PathState& P
 // are processed last to first, one traversal per lane per loop iteration.
 template <int LAYOUT, bool EGRAD>
 __global__ void __launch_bounds__(256, PT_ADJ_MIN_BLOCKS) ckpt_reverse_kernel(const __grid_constant__ LaunchArgs A) {
+  constexpr int FEAT = FEAT_TEXAGG | (EGRAD ? FEAT_EGRAD : 0);
   const long long unit = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   PixelOf px{};
   const bool valid = unit_pixel(A, unit, crop_tile(A), px);
@@ -81,18 +82,18 @@ __global__ void __launch_bounds__(256, PT_ADJ_MIN_BLOCKS) ckpt_reverse_kernel(co
       load_checkpoint(A, slot, k, P);
       const Hit hit = LAYOUT == PT_BVH_WIDE ? trace_wide<false>(A.scene, P.ro, P.rd, INFINITY, false, cnt)
                                             : trace_binary<false>(A.scene, P.ro, P.rd, INFINITY, false, cnt);
-      const bool alive = path_shade<true, false, false, PT_DISPATCH_SWITCH, EGRAD>(A, P, hit, true, dl, sink, cnt);
+      const bool alive = path_shade<true, false, false, PT_DISPATCH_SWITCH, FEAT>(A, P, hit, true, dl, sink, cnt);
       if (alive && P.has_shadow) {
         want_shadow = true;
       } else {
-        reverse_finish<EGRAD>(A, P, alive, false, S, dl, sink, cnt);
+        reverse_finish<FEAT>(A, P, alive, false, S, dl, sink, cnt);
         --k;
       }
     } else {
       const Hit hit = LAYOUT == PT_BVH_WIDE ? trace_wide<false>(A.scene, P.so, P.sd, P.stmax, true, cnt)
                                             : trace_binary<false>(A.scene, P.so, P.sd, P.stmax, true, cnt);
       want_shadow = false;
-      reverse_finish<EGRAD>(A, P, true, hit.pos >= 0, S, dl, sink, cnt);
+      reverse_finish<FEAT>(A, P, true, hit.pos >= 0, S, dl, sink, cnt);
       --k;
     }
   }

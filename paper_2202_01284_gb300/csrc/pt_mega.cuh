@@ -89,10 +89,11 @@ __device__ __forceinline__ void load_checkpoint(const LaunchArgs& A, long long s
   P.Lrem = f3(0.f, 0.f, 0.f);
 }
 
-// CKPT (forward only): store a checkpoint before every closest-hit ray and the
-// vertex count of every sample (reverse mode with checkpoints, Sec. 5).
-template <bool ADJ, bool JVP, bool INSTR, int LAYOUT, int DISPATCH, bool EGRAD = false, bool CKPT = false>
+// FEAT_CKPT (forward only): store a checkpoint before every closest-hit ray and
+// the vertex count of every sample (reverse mode with checkpoints, Sec. 5).
+template <bool ADJ, bool JVP, bool INSTR, int LAYOUT, int DISPATCH, int FEAT = 0>
 __device__ __forceinline__ void megakernel(const LaunchArgs& A, long long unit, const Tile& tile) {
+  constexpr bool CKPT = (FEAT & FEAT_CKPT) != 0;
   PixelOf px{};
   const bool valid = unit_pixel(A, unit, tile, px);
   Counters<INSTR> cnt;
@@ -144,18 +145,18 @@ __device__ __forceinline__ void megakernel(const LaunchArgs& A, long long unit, 
       const bool grad_pass = ADJ && pass == 1;
       bool alive = true, finish = true, occ = false;
       if (!want_shadow) {
-        alive = path_shade<ADJ, JVP, INSTR, DISPATCH, EGRAD>(A, P, hit, grad_pass, dl, sink, cnt);
+        alive = path_shade<ADJ, JVP, INSTR, DISPATCH, FEAT>(A, P, hit, grad_pass, dl, sink, cnt);
         finish = alive && !P.has_shadow;
         want_shadow = alive && P.has_shadow;
       } else {
         occ = hit.pos >= 0;
         want_shadow = false;
       }
-      if (finish) alive = path_finish<ADJ, JVP, INSTR, EGRAD>(A, P, occ, grad_pass, dl, sink, cnt);
+      if (finish) alive = path_finish<ADJ, JVP, INSTR, FEAT>(A, P, occ, grad_pass, dl, sink, cnt);
       if (!alive) {
         has_path = false;
         if constexpr (CKPT) A.ck_count[P.slot] = P.depth;
-        if constexpr (!ADJ) {
+        if constexpr (!ADJ && (FEAT & FEAT_CACHE) != 0) {
           if (A.cache_mode == 1 && !P.cache_done) {  // no cache query for this sample
             float* r = A.q_raw + P.slot * 10;
 #pragma unroll

@@ -7,6 +7,12 @@
 
 namespace ptgb {
 
+// Optional features compiled into an instantiation of the per-vertex code (each
+// costs the production kernels instruction-cache space when compiled in):
+// environment-radiance gradients, radiance-cache modes, warp-aggregated texel
+// atomics, reverse-mode checkpoints.
+enum : int { FEAT_EGRAD = 1, FEAT_CACHE = 2, FEAT_TEXAGG = 4, FEAT_CKPT = 8, FEAT_ALL = 7 };
+
 // Per-vertex gradient sink of the adjoint: warp-aggregated atomics.
 // Constant-albedo rows and roughness entries are few and heavily shared, so the
 // lanes of a warp that hit the same entry are reduced with a shuffle tree and one
@@ -14,7 +20,7 @@ namespace ptgb {
 // optional for them.  (No per-CTA shared-memory staging: its end-of-CTA barrier
 // kept finished warps resident and cost more than the atomics it saved.)
 struct GradSink {
-  template <bool INSTR>
+  template <bool INSTR, bool TEXAGG>
   __device__ __forceinline__ void add(const LaunchArgs& A, const Material& m, float3 g_alb, float g_alpha,
                                       Counters<INSTR>& cnt) {
     const DevGrads& G = A.grads;
@@ -22,7 +28,7 @@ struct GradSink {
       float4* dst = G.tex[m.tex];
       if (dst) {
         cnt.add(7, 1);
-        if (A.tex_aggregate) {
+        if (TEXAGG && A.tex_aggregate) {
           float v[3] = {g_alb.x, g_alb.y, g_alb.z};
           unsigned long long key = ((unsigned long long)m.tex << 32) | (unsigned)m.alb_ref;
           unsigned active = __activemask();
@@ -154,13 +160,12 @@ __device__ __forceinline__ void path_start(const LaunchArgs& A, PathState& P, un
 // Not inlined (nor is path_finish): with their own register allocation the
 // traversal loop of the megakernel keeps more registers (measured: adjoint -15 %,
 // forward -4 % on the 196k-triangle sphere workload).
-// EGRAD: the adjoint also scatters environment-radiance gradients (a separate
-// instantiation: the extra code costs the plain adjoint instruction-cache space).
-template <bool ADJ, bool JVP, bool INSTR, int DISPATCH, bool EGRAD = false>
+template <bool ADJ, bool JVP, bool INSTR, int DISPATCH, int FEAT = 0>
 __device__ __noinline__ bool path_shade(const LaunchArgs& A, PathState& P, const Hit& hit, bool grad_pass, float3 dl,
                                         GradSink& sink,
                                            Counters<INSTR>& cnt) {
   const DevScene& S = A.scene;
+  constexpr bool EGRAD = (FEAT & FEAT_EGRAD) != 0;
   const bool has_area = S.n_lights > 0;
   const bool has_env = S.env_w > 0;
   const float p_env = has_env ? (has_area ? 0.5f : 1.0f) : 0.0f;
@@ -274,7 +279,7 @@ __device__ __noinline__ bool path_shade(const LaunchArgs& A, PathState& P, const
   const bool entering = cos_front > 0.0f;
   const float3 n_s = entering ? ng : -ng;
   // ---- radiance cache: terminate into the cache, or record training data
-  if (A.cache_mode != 0 && type != PT_BSDF_DIELECTRIC) {
+  if ((FEAT & FEAT_CACHE) && A.cache_mode != 0 && type != PT_BSDF_DIELECTRIC) {
     const float rough = (type == PT_BSDF_CONDUCTOR || type == PT_BSDF_BLEND) ? m.alpha : 1.0f;
     if (A.cache_mode == 3) {
       const unsigned active = __activemask();
@@ -430,7 +435,7 @@ __device__ __noinline__ bool path_shade(const LaunchArgs& A, PathState& P, const
 }
 
 // Finish the vertex once the shadow ray is resolved.  Returns false if the path ended.
-template <bool ADJ, bool JVP, bool INSTR, bool EGRAD = false>
+template <bool ADJ, bool JVP, bool INSTR, int FEAT = 0>
 __device__ __noinline__ bool path_finish(const LaunchArgs& A, PathState& P, bool occluded, bool grad_pass,
                                             float3 dl, GradSink& sink, Counters<INSTR>& cnt) {
   if (A.nee && P.mtype != PT_BSDF_DIELECTRIC && (A.scene.n_lights > 0 || A.scene.env_w > 0))
@@ -440,7 +445,8 @@ __device__ __noinline__ bool path_finish(const LaunchArgs& A, PathState& P, bool
     P.L = P.L + P.c_nee;
     P.Lrem = P.Lrem - P.c_nee;
     if (JVP) P.L_dot = P.L_dot + P.c_nee_dot;
-    if (ADJ && EGRAD && grad_pass && P.nee_env >= 0) sink.add_env<INSTR>(A, P.nee_env, dl * P.nee_env_d, cnt);
+    if (ADJ && (FEAT & FEAT_EGRAD) && grad_pass && P.nee_env >= 0)
+      sink.add_env<INSTR>(A, P.nee_env, dl * P.nee_env_d, cnt);
   }
   P.fh.add((uint32_t)P.lobe);
   if (P.delta_next) P.fh.add(0xfffffffeu);
@@ -456,7 +462,7 @@ __device__ __noinline__ bool path_finish(const LaunchArgs& A, PathState& P, bool
     m.alb_ref = P.alb_ref;
     m.tex = P.tex;
     m.rough = P.rough;
-    sink.add<INSTR>(A, m, g_alb, ga.x + ga.y + ga.z, cnt);
+    sink.add<INSTR, (FEAT & FEAT_TEXAGG) != 0>(A, m, g_alb, ga.x + ga.y + ga.z, cnt);
   }
   if (!P.ok_next) return false;
   if (JVP) P.beta_dot = P.beta_dot * P.w_next + P.beta * P.w_next_dot;

@@ -12,9 +12,18 @@
 namespace ptgb {
 
 
+// Production instances carry no optional features; instrumented ones carry all.
 template <bool INSTR, int LAYOUT, int DISPATCH>
 __global__ void __launch_bounds__(256, PT_FWD_MIN_BLOCKS) forward_kernel(const __grid_constant__ LaunchArgs A) {
-  megakernel<false, false, INSTR, LAYOUT, DISPATCH>(A, (long long)blockIdx.x * blockDim.x + threadIdx.x, crop_tile(A));
+  megakernel<false, false, INSTR, LAYOUT, DISPATCH, INSTR ? FEAT_ALL : 0>(
+      A, (long long)blockIdx.x * blockDim.x + threadIdx.x, crop_tile(A));
+}
+
+// The forward with the radiance-cache modes compiled in.
+template <int LAYOUT>
+__global__ void __launch_bounds__(256, PT_FWD_MIN_BLOCKS) forward_full_kernel(const __grid_constant__ LaunchArgs A) {
+  megakernel<false, false, false, LAYOUT, PT_DISPATCH_SWITCH, FEAT_ALL>(
+      A, (long long)blockIdx.x * blockDim.x + threadIdx.x, crop_tile(A));
 }
 
 // Forward mode (Sec. 4, forward-mode derivatives of the paper's AD layer): the
@@ -27,14 +36,16 @@ __global__ void __launch_bounds__(256, PT_ADJ_MIN_BLOCKS) jvp_kernel(const __gri
 
 template <bool INSTR, int LAYOUT, int DISPATCH>
 __global__ void __launch_bounds__(256, PT_ADJ_MIN_BLOCKS) adjoint_kernel(const __grid_constant__ LaunchArgs A) {
-  megakernel<true, false, INSTR, LAYOUT, DISPATCH>(A, (long long)blockIdx.x * blockDim.x + threadIdx.x, crop_tile(A));
+  megakernel<true, false, INSTR, LAYOUT, DISPATCH, INSTR ? FEAT_ALL : 0>(
+      A, (long long)blockIdx.x * blockDim.x + threadIdx.x, crop_tile(A));
 }
 
-// The adjoint with environment-radiance gradients as well (emitter gradients).
+// The adjoint with every optional feature: environment-radiance (emitter)
+// gradients, the cache-terminated replay, warp-aggregated texel atomics.
 template <int LAYOUT>
-__global__ void __launch_bounds__(256, PT_ADJ_MIN_BLOCKS) adjoint_env_kernel(const __grid_constant__ LaunchArgs A) {
-  megakernel<true, false, false, LAYOUT, PT_DISPATCH_SWITCH, true>(A, (long long)blockIdx.x * blockDim.x + threadIdx.x,
-                                                                   crop_tile(A));
+__global__ void __launch_bounds__(256, PT_ADJ_MIN_BLOCKS) adjoint_full_kernel(const __grid_constant__ LaunchArgs A) {
+  megakernel<true, false, false, LAYOUT, PT_DISPATCH_SWITCH, FEAT_ALL>(
+      A, (long long)blockIdx.x * blockDim.x + threadIdx.x, crop_tile(A));
 }
 
 // image[pix] += sum_s q_beta[slot] * max(q_rgb[slot], 0) / spp  (cache-terminated render)
@@ -113,7 +124,7 @@ __global__ void __launch_bounds__(256, ADJ ? PT_ADJ_MIN_BLOCKS : PT_FWD_MIN_BLOC
     }
     const Tile t{bi.x0, bi.y0, tile, tile, 1};
     const long long units = (long long)tile * tile * A.lanes_per_pixel;
-    for (long long b = 0; b < units; b += 32) megakernel<ADJ, false, false, LAYOUT, PT_DISPATCH_SWITCH, EGRAD>(A, b + lane, t);
+    for (long long b = 0; b < units; b += 32) megakernel<ADJ, false, false, LAYOUT, PT_DISPATCH_SWITCH, EGRAD ? FEAT_EGRAD : 0>(A, b + lane, t);
   }
 }
 
@@ -232,8 +243,13 @@ int launch_forward(pt_scene* s, const pt_render_desc* r, const LaunchArgs& A, cu
   long long grid;
   int st = launch_dims(r, A, block, grid);
   if (st != PT_OK) return st;
-  const int v = (instrumented(r) ? 4 : 0) | (s->dev.layout == PT_BVH_WIDE ? 2 : 0) | (A.dispatch == PT_DISPATCH_MATCH ? 1 : 0);
   const dim3 g((unsigned)grid), b(block);
+  if (A.cache_mode != 0 && !instrumented(r)) {
+    if (s->dev.layout == PT_BVH_WIDE) forward_full_kernel<PT_BVH_WIDE><<<g, b, 0, cs>>>(A);
+    else forward_full_kernel<PT_BVH_BINARY><<<g, b, 0, cs>>>(A);
+    return cudaGetLastError() == cudaSuccess ? PT_OK : PT_ERR_CUDA;
+  }
+  const int v = (instrumented(r) ? 4 : 0) | (s->dev.layout == PT_BVH_WIDE ? 2 : 0) | (A.dispatch == PT_DISPATCH_MATCH ? 1 : 0);
   switch (v) {
     case 0: forward_kernel<false, PT_BVH_BINARY, PT_DISPATCH_SWITCH><<<g, b, 0, cs>>>(A); break;
     case 1: forward_kernel<false, PT_BVH_BINARY, PT_DISPATCH_MATCH><<<g, b, 0, cs>>>(A); break;
@@ -308,10 +324,10 @@ extern "C" int pt_render_backward(pt_scene* s, const pt_render_desc* r, const pt
     A.q_rgb = cache_buffers(r->cache).q_rgb;
   }
   const dim3 gd((unsigned)grid), bd(block);
-  if (A.grads.env) {  // emitter gradients: their own instantiation (switch dispatch, no counters)
-    if (instrumented(r)) return PT_ERR_ARG;
-    if (s->dev.layout == PT_BVH_WIDE) adjoint_env_kernel<PT_BVH_WIDE><<<gd, bd, 0, cs>>>(A);
-    else adjoint_env_kernel<PT_BVH_BINARY><<<gd, bd, 0, cs>>>(A);
+  if ((A.grads.env || A.cache_mode != 0 || A.tex_aggregate) && !instrumented(r)) {
+    // optional features: their own instantiation (switch dispatch)
+    if (s->dev.layout == PT_BVH_WIDE) adjoint_full_kernel<PT_BVH_WIDE><<<gd, bd, 0, cs>>>(A);
+    else adjoint_full_kernel<PT_BVH_BINARY><<<gd, bd, 0, cs>>>(A);
     return cudaGetLastError() == cudaSuccess ? PT_OK : PT_ERR_CUDA;
   }
   const int v = (instrumented(r) ? 4 : 0) | (s->dev.layout == PT_BVH_WIDE ? 2 : 0) | (A.dispatch == PT_DISPATCH_MATCH ? 1 : 0);

@@ -25,6 +25,9 @@ constexpr int kStateWords = (int)((sizeof(PathState) + 15) / 16);
 constexpr int kMaterials = 5;  // queue 0: misses and PT_BSDF_NONE; 1..4: the BSDF types
 enum { C_RAY = 0, C_SHADOW = 1, C_TYPE = 2, kCounts = 8 };
 constexpr int kBlock = 256;
+// adjoint stages: environment gradients and texel aggregation available
+template <bool ADJ>
+constexpr int kWfFeat = ADJ ? (FEAT_EGRAD | FEAT_TEXAGG) : 0;
 constexpr int kTraceMinBlocks = 4;  // 64 registers: latency-bound traversal wants occupancy
 constexpr int kShadeMinBlocks = 3;  // 85 registers, as the adjoint megakernel
 
@@ -183,13 +186,13 @@ __global__ void __launch_bounds__(kBlock, kShadeMinBlocks) wf_shade(const __grid
     load_state(W, i, P);
     const Hit h = W.hit[i];
     const float3 dl = grad_pass ? pixel_dl(A, P) : f3(0.f, 0.f, 0.f);
-    bool alive = path_shade<ADJ, false, false, DISPATCH, ADJ>(A, P, h, grad_pass, dl, sink, cnt);
+    bool alive = path_shade<ADJ, false, false, DISPATCH, kWfFeat<ADJ>>(A, P, h, grad_pass, dl, sink, cnt);
     if (alive && P.has_shadow) {
       store_state(W, i, P);
       push(W.sq, &c[C_SHADOW], i);
       continue;
     }
-    if (alive) alive = path_finish<ADJ, false, false, ADJ>(A, P, false, grad_pass, dl, sink, cnt);
+    if (alive) alive = path_finish<ADJ, false, false, kWfFeat<ADJ>>(A, P, false, grad_pass, dl, sink, cnt);
     if (alive) {
       store_state(W, i, P);
       push(W.q[(round + 1) & 1], &cn[C_RAY], i);
@@ -214,7 +217,7 @@ __global__ void __launch_bounds__(kBlock, kShadeMinBlocks) wf_finish(const __gri
     PathState P;
     load_state(W, i, P);
     const float3 dl = grad_pass ? pixel_dl(A, P) : f3(0.f, 0.f, 0.f);
-    const bool alive = path_finish<ADJ, false, false, ADJ>(A, P, W.occ[i] != 0, grad_pass, dl, sink, cnt);
+    const bool alive = path_finish<ADJ, false, false, kWfFeat<ADJ>>(A, P, W.occ[i] != 0, grad_pass, dl, sink, cnt);
     if (alive) {
       store_state(W, i, P);
       push(W.q[(round + 1) & 1], &cn[C_RAY], i);
