@@ -37,9 +37,11 @@ FLOPS_PER_NODE = {"binary": 44,   # two child slab tests: 12 FMA (24 flops), 10 
                                   # decode: 3 scale + 3 offset products excluded)
 FLOPS_PER_TRI = 45      # Moller-Trumbore: 2 cross, 4 dot, 1 div, 4 mul, 3 sub (FMA = 2 flops)
 # DRAM bytes (read + write) per full-size launch of the production kernels, from one
-# ncu capture of this step (profiles/launches_spheres196k_1024px_64spp.md); set to
-# None whenever the kernels change until they are captured again.
-DRAM_TRAFFIC_PER_LAUNCH = {}
+# one-pass ncu capture of this step (profiles/launches_spheres196k_1024px_64spp.md);
+# cleared whenever the kernels change until they are captured again.
+DRAM_TRAFFIC_PER_LAUNCH = {"wide": {"forward_kernel": 2_958_000_000 + 14_328_000_000,
+                                    "adjoint_kernel": 1_775_000_000 + 11_908_000_000,
+                                    "jvp_kernel": 1_325_000_000 + 7_153_000_000}}
 
 
 def parse():
@@ -434,7 +436,9 @@ def run_jvp_experiment(args):
                        "jvp_over_forward": round(jvp_ms / fwd_ms, 3),
                        "forward_mrays_s": round(rays / fwd_ms / 1e3, 1)},
             "roofline": {"bound": "alu", "kernel": "jvp_kernel", "achieved": round(achieved, 3), "peak": round(peak, 2),
-                         "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": None,
+                         "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
+                         "traffic": DRAM_TRAFFIC_PER_LAUNCH.get(args.bvh, {}).get("jvp_kernel")
+                         if not args.small else None,
                          "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 x median SM clock {mhz} MHz"},
             "gpu_launches": 2 * args.steps, "clocks": clk}
     print(json.dumps(line), flush=True)
