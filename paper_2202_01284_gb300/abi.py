@@ -147,6 +147,8 @@ SIGNATURES = {
     "pt_status_string": ([C.c_int], C.c_char_p),
     "pt_cache_create": ([C.POINTER(pt_cache_desc), C.POINTER(C.c_void_p)], C.c_int),
     "pt_cache_destroy": ([C.c_void_p], None),
+    "pt_cache_set_engine": ([C.c_void_p, C.c_int], C.c_int),
+    "pt_cache_status": ([C.c_void_p, C.c_void_p, C.POINTER(C.c_int)], C.c_int),
     "pt_cache_get_weights": ([C.c_void_p, C.c_void_p], C.c_int),
     "pt_cache_set_weights": ([C.c_void_p, C.c_void_p], C.c_int),
     "pt_cache_query": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p], C.c_int),
@@ -415,6 +417,20 @@ def pt_cache_set_weights(handle: int, w) -> None:
     w = np.ascontiguousarray(w, np.float32)
     assert w.size == PT_CACHE_N_PARAMS
     check("pt_cache_set_weights", load().pt_cache_set_weights(handle, w.ctypes.data))
+
+
+PT_CACHE_TCGEN05 = 0
+PT_CACHE_MMA_SYNC = 1
+
+
+def pt_cache_set_engine(handle: int, engine: int) -> None:
+    check("pt_cache_set_engine", load().pt_cache_set_engine(handle, engine))
+
+
+def pt_cache_status(handle: int, stream: int = 0) -> int:
+    v = C.c_int(0)
+    check("pt_cache_status", load().pt_cache_status(handle, stream or None, C.byref(v)))
+    return v.value
 
 
 def pt_cache_query(handle: int, raw, rgb, n: int, stream: int = 0) -> None:

@@ -141,10 +141,6 @@ __device__ __forceinline__ void head(float (&y)[4], const uint32_t (&A)[4][4], c
   }
 }
 
-struct NrcBox {
-  float lo[3], inv_ext[3];
-};
-
 // ---------------------------------------------------------------- inference
 // out[r][c] = MLP(encode(raw[r])).
 __global__ void __launch_bounds__(128) nrc_infer_kernel(const float* __restrict__ raw, long long n, NrcBox box,
@@ -419,6 +415,8 @@ struct pt_cache {
   float* r_target = nullptr;    // [max_records][3]
   float* path_L = nullptr;      // [max_paths][3] final radiance of training paths
   unsigned* r_count = nullptr;  // [2] records written, paths written
+  int* status = nullptr;        // [1] device-side error of the tensor-core kernels
+  int engine = PT_CACHE_TCGEN05;
   int step = 0;
 };
 
@@ -430,7 +428,7 @@ constexpr size_t kTrainSmem = (size_t)NrcSmem::W_ELEMS * 2 + (size_t)NRC_HIDDEN 
 
 void cache_free(pt_cache* c) {
   void* ptrs[] = {c->W32, c->m, c->v, c->dW, c->Wb, c->X, c->dZ, c->loss, c->q_raw, c->q_beta, c->q_rgb,
-                  c->r_raw, c->r_aux, c->r_target, c->path_L, c->r_count};
+                  c->r_raw, c->r_aux, c->r_target, c->path_L, c->r_count, c->status};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -483,7 +481,7 @@ extern "C" int pt_cache_create(const pt_cache_desc* d, pt_cache** out) {
             cudaMalloc(&c->v, NRC_PARAMS * 4) == cudaSuccess && cudaMalloc(&c->dW, NRC_PARAMS * 4) == cudaSuccess &&
             cudaMalloc(&c->Wb, nb * 2) == cudaSuccess && cudaMalloc(&c->X, act * 2) == cudaSuccess &&
             cudaMalloc(&c->dZ, act * 2) == cudaSuccess && cudaMalloc(&c->loss, 4) == cudaSuccess &&
-            cudaMalloc(&c->r_count, 8) == cudaSuccess;
+            cudaMalloc(&c->r_count, 8) == cudaSuccess && cudaMalloc(&c->status, 4) == cudaSuccess;
   if (ok && d->max_queries > 0)
     ok = cudaMalloc(&c->q_raw, (size_t)d->max_queries * NRC_RAW * 4) == cudaSuccess &&
          cudaMalloc(&c->q_beta, (size_t)d->max_queries * 12) == cudaSuccess &&
@@ -505,7 +503,8 @@ extern "C" int pt_cache_create(const pt_cache_desc* d, pt_cache** out) {
   ok = cudaMemcpy(c->W32, w.data(), NRC_PARAMS * 4, cudaMemcpyHostToDevice) == cudaSuccess &&
        cudaMemset(c->m, 0, NRC_PARAMS * 4) == cudaSuccess && cudaMemset(c->v, 0, NRC_PARAMS * 4) == cudaSuccess &&
        cudaMemset(c->dW, 0, NRC_PARAMS * 4) == cudaSuccess && cudaMemset(c->Wb, 0, nb * 2) == cudaSuccess &&
-       cudaMemset(c->loss, 0, 4) == cudaSuccess && cudaMemset(c->r_count, 0, 8) == cudaSuccess;
+       cudaMemset(c->loss, 0, 4) == cudaSuccess && cudaMemset(c->r_count, 0, 8) == cudaSuccess &&
+       cudaMemset(c->status, 0, 4) == cudaSuccess;
   if (ok) {
     nrc_to_bf16_kernel<<<(NRC_PARAMS + 255) / 256, 256>>>(c->W32, c->Wb);
     ok = cudaDeviceSynchronize() == cudaSuccess;
@@ -548,6 +547,7 @@ extern "C" int pt_cache_set_weights(pt_cache* c, const float* host_in) {
 namespace ptgb {
 int cache_infer(pt_cache* c, const float* raw, float* rgb, long long n, cudaStream_t st) {
   if (n <= 0) return PT_OK;
+  if (c->engine == PT_CACHE_TCGEN05) return cache_infer_tc(raw, rgb, n, c->box, c->Wb, c->status, st);
   const long long tiles = (n + 15) / 16;
   long long grid = (tiles + 3) / 4;
   if (grid > 152 * 8) grid = 152 * 8;
@@ -602,6 +602,19 @@ CacheBuffers cache_buffers(pt_cache* c) {
 extern "C" int pt_cache_query(pt_cache* c, const float* raw, float* rgb, int n, void* stream) {
   if (!c || n < 0 || (n > 0 && (!raw || !rgb))) return PT_ERR_ARG;
   return cache_infer(c, raw, rgb, n, (cudaStream_t)stream);
+}
+
+extern "C" int pt_cache_set_engine(pt_cache* c, int engine) {
+  if (!c || (engine != PT_CACHE_TCGEN05 && engine != PT_CACHE_MMA_SYNC)) return PT_ERR_ARG;
+  c->engine = engine;
+  return PT_OK;
+}
+
+extern "C" int pt_cache_status(pt_cache* c, void* stream, int* out) {
+  if (!c || !out) return PT_ERR_ARG;
+  if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return PT_ERR_CUDA;
+  if (cudaMemcpy(out, c->status, 4, cudaMemcpyDeviceToHost) != cudaSuccess) return PT_ERR_CUDA;
+  return cudaMemset(c->status, 0, 4) == cudaSuccess ? PT_OK : PT_ERR_CUDA;
 }
 
 extern "C" int pt_cache_train_records(pt_cache* c, const float* raw, const float* target, int n, int steps,

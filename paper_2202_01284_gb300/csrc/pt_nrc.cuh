@@ -16,6 +16,15 @@ constexpr int NRC_PARAMS = NRC_HIDDEN * NRC_W * NRC_W + NRC_OUT * NRC_W;  // 20,
 constexpr int NRC_RAW = 10;      // raw record: position[3], direction[3], normal[3], roughness
 constexpr int NRC_LD = 72;       // padded shared-memory row (bf16 elements): conflict-free fragment loads
 
+struct NrcBox {
+  float lo[3], inv_ext[3];
+};
+
+// Inference on the tcgen05 tensor cores (pt_nrc_tc.cu); `status` receives
+// PT_ERR_TIMEOUT if a bounded wait on the tensor core gave up.
+int cache_infer_tc(const float* raw, float* rgb, long long n, const NrcBox& box, const __nv_bfloat16* Wb, int* status,
+                   cudaStream_t st);
+
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
   __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
   return *reinterpret_cast<uint32_t*>(&v);

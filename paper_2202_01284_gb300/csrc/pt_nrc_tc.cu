@@ -1,0 +1,239 @@
+// Radiance-cache MLP inference on the 5th-generation tensor cores (tcgen05):
+// the MMAs are issued by one thread with operands in shared memory (UMMA
+// descriptors, K-major, no swizzle), accumulators live in tensor memory and are
+// read back with tcgen05.ld for the ReLU / BF16 epilogue, which writes the next
+// layer's operand tile.  128 queries per tile (M = 128), 64-wide layers (N = 64,
+// K = 64 as four K = 16 steps), a 16-wide head (3 outputs used).  Same network,
+// encoding and BF16 rounding points as the mma.sync kernel in pt_nrc.cu.
+#include <cuda_bf16.h>
+
+#include "pt_internal.h"
+#include "pt_nrc.cuh"
+
+namespace ptgb {
+namespace {
+
+// ---------------------------------------------------------------- PTX wrappers
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// Bounded wait on the barrier phase with the given parity; false if it gave up.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, unsigned limit) {
+  const uint32_t a = smem_addr(bar);
+  for (unsigned i = 0; i < limit; ++i) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+// generic-proxy shared-memory writes -> visible to the tensor core (async proxy)
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// Shared-memory matrix descriptor: start address, leading-dimension byte offset
+// (between core matrices along K), stride byte offset (between 8-row groups),
+// the fixed 0b001 at bits 46-48, no swizzle.
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)(lbo >> 4) << 16) | ((uint64_t)(sbo >> 4) << 32) |
+         (1ull << 46);
+}
+
+// Instruction descriptor, kind::f16: D FP32 (bits 4-5 = 1), A and B BF16 (bits 7-9,
+// 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 at bits 17-22, M >> 4 at 24-28.
+constexpr uint32_t idesc_bf16(uint32_t m, uint32_t n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((n >> 3) << 17) | ((m >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                          uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_addr(bar))
+               : "memory");
+}
+
+// 16 consecutive FP32 columns of this thread's TMEM lane (32x32b shape), waited on.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n tcgen05.wait::ld.sync.aligned;\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+               : "r"(taddr)
+               : "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// ---------------------------------------------------------------- operand layout
+// K-major, no swizzle, K = 64: 8x8 core matrices of 8 rows x 16 bytes, the eight
+// core matrices of an 8-row group adjacent along K (128 B apart), 8-row groups
+// 1024 B apart.  A K = 16 step covers two core matrices along K (256 B).
+constexpr uint32_t kLBO = 128, kSBO = 1024;
+__device__ __forceinline__ uint32_t core_off(int row, int k) {
+  return (uint32_t)((row >> 3) * 1024 + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2);
+}
+
+// shared memory: five 64x64 layer tiles (8 KB each), the 16x64 head tile,
+// the 128x64 activation tile, the barrier and the TMEM address slot
+constexpr uint32_t kSmW = 0, kSmH = 5 * 8192, kSmX = kSmH + 2048, kSmBar = kSmX + 16384, kSmSlot = kSmBar + 8;
+constexpr uint32_t kTcSmem = kSmSlot + 8 + 1024;  // + alignment slack
+constexpr uint32_t kTmemCols = 64;
+constexpr unsigned kWaitLimit = 1u << 22;
+
+__global__ void __launch_bounds__(128) nrc_infer_tc_kernel(const float* __restrict__ raw, long long n, NrcBox box,
+                                                           const __nv_bfloat16* __restrict__ W,
+                                                           float* __restrict__ out, int* __restrict__ status) {
+  extern __shared__ unsigned char tc_smem_raw[];
+  // 1024-byte aligned base for the operand tiles
+  unsigned char* sm = tc_smem_raw + ((1024u - (smem_addr(tc_smem_raw) & 1023u)) & 1023u);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sm + kSmBar);
+  uint32_t* slot = reinterpret_cast<uint32_t*>(sm + kSmSlot);
+  const int tid = threadIdx.x, warp = tid >> 5;
+
+  // weights into the operand layout: layer l is B = W_l[o][i] (N = o, K = i)
+  const unsigned short* g = reinterpret_cast<const unsigned short*>(W);
+  for (int idx = tid; idx < NRC_HIDDEN * NRC_W * NRC_W; idx += blockDim.x) {
+    const int l = idx >> 12, o = (idx >> 6) & 63, i = idx & 63;
+    *reinterpret_cast<unsigned short*>(sm + kSmW + l * 8192 + core_off(o, i)) = g[idx];
+  }
+  for (int idx = tid; idx < 16 * NRC_W; idx += blockDim.x) {
+    const int o = idx >> 6, i = idx & 63;
+    *reinterpret_cast<unsigned short*>(sm + kSmH + core_off(o, i)) =
+        o < NRC_OUT ? g[NRC_HIDDEN * NRC_W * NRC_W + o * NRC_W + i] : (unsigned short)0;
+  }
+  if (tid == 0) mbar_init(bar, 1);
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(slot)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_async_smem();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *slot;
+  const uint32_t x_s = smem_addr(sm + kSmX), w_s = smem_addr(sm + kSmW), h_s = smem_addr(sm + kSmH);
+  const uint32_t t_lane = tmem + ((uint32_t)(warp * 32) << 16);  // this warp's 32 TMEM lanes
+  uint32_t phase = 0;
+  bool ok = true;
+  const long long n_tiles = (n + 127) / 128;
+  for (long long tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
+    // ---- encode this thread's query (row tid) into the activation tile
+    const long long row = tile * 128 + tid;
+    float rr[NRC_RAW];
+#pragma unroll
+    for (int k = 0; k < NRC_RAW; ++k) rr[k] = row < n ? raw[row * NRC_RAW + k] : 0.0f;
+#pragma unroll
+    for (int c8 = 0; c8 < 8; ++c8) {
+      uint32_t q[4];
+#pragma unroll
+      for (int h = 0; h < 4; ++h) {
+        const int j = 8 * c8 + 2 * h;
+        q[h] = row < n ? pack_bf16(nrc_feature(j, rr, box.lo, box.inv_ext), nrc_feature(j + 1, rr, box.lo, box.inv_ext))
+                       : 0u;
+      }
+      *reinterpret_cast<uint4*>(sm + kSmX + core_off(tid, 8 * c8)) = make_uint4(q[0], q[1], q[2], q[3]);
+    }
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    // ---- five hidden layers and the head
+    for (int l = 0; l <= NRC_HIDDEN; ++l) {
+      const bool head = l == NRC_HIDDEN;
+      if (tid == 0) {
+        tc_fence_after();
+        const uint32_t b_s = head ? h_s : w_s + (uint32_t)l * 8192u;
+        const uint32_t idesc = head ? idesc_bf16(128, 16) : idesc_bf16(128, 64);
+#pragma unroll
+        for (int s = 0; s < 4; ++s)
+          umma_bf16(tmem, umma_desc(x_s + 256u * s, kLBO, kSBO), umma_desc(b_s + 256u * s, kLBO, kSBO), idesc,
+                    s > 0 ? 1u : 0u);
+        umma_commit(bar);
+      }
+      const bool done = mbar_wait(bar, phase, kWaitLimit);
+      phase ^= 1u;
+      ok = __syncthreads_and(done) != 0;
+      if (!ok) break;
+      tc_fence_after();
+      if (!head) {
+        // ReLU + BF16 of this thread's row -> next operand tile
+#pragma unroll
+        for (int c16 = 0; c16 < 4; ++c16) {
+          float v[16];
+          tmem_ld16(t_lane + 16u * c16, v);
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const float* p = v + 8 * h;
+            const uint4 q = make_uint4(pack_bf16(fmaxf(p[0], 0.f), fmaxf(p[1], 0.f)),
+                                       pack_bf16(fmaxf(p[2], 0.f), fmaxf(p[3], 0.f)),
+                                       pack_bf16(fmaxf(p[4], 0.f), fmaxf(p[5], 0.f)),
+                                       pack_bf16(fmaxf(p[6], 0.f), fmaxf(p[7], 0.f)));
+            *reinterpret_cast<uint4*>(sm + kSmX + core_off(tid, 16 * c16 + 8 * h)) = q;
+          }
+        }
+        fence_async_smem();
+      } else {
+        float v[16];
+        tmem_ld16(t_lane, v);
+        if (row < n) {
+          out[row * 3] = v[0];
+          out[row * 3 + 1] = v[1];
+          out[row * 3 + 2] = v[2];
+        }
+      }
+      tc_fence_before();
+      __syncthreads();
+    }
+  }
+  if (!ok) {
+    if (tid == 0) atomicCAS(status, 0, PT_ERR_TIMEOUT);
+    // let an MMA still in flight finish before its TMEM is released
+    mbar_wait(bar, phase, kWaitLimit);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+  }
+}
+
+}  // namespace
+
+int cache_infer_tc(const float* raw, float* rgb, long long n, const NrcBox& box, const __nv_bfloat16* Wb, int* status,
+                   cudaStream_t st) {
+  static int attr = 0;
+  if (!attr) {
+    if (cudaFuncSetAttribute(nrc_infer_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem) !=
+        cudaSuccess)
+      return PT_ERR_CUDA;
+    attr = 1;
+  }
+  const long long tiles = (n + 127) / 128;
+  int dev = 0, sms = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  long long grid = tiles < 3ll * sms ? tiles : 3ll * sms;  // 3 CTAs (58 KB each, 64 TMEM columns) per SM
+  if (grid < 1) grid = 1;
+  nrc_infer_tc_kernel<<<(unsigned)grid, 128, kTcSmem, st>>>(raw, n, box, Wb, rgb, status);
+  return cudaGetLastError() == cudaSuccess ? PT_OK : PT_ERR_CUDA;
+}
+
+}  // namespace ptgb

@@ -26,17 +26,21 @@ def _rel_err(a, b):
     return np.abs(a - b) / (np.abs(b) + 0.05 * scale)
 
 
-@pytest.mark.parametrize("n", [1, 17, 5000])
-def test_inference_matches_oracle(abi, oracle_mod, n):
-    """Ragged sizes (1, 17 = one full tile + 1 row, 5000) through the C ABI."""
+@pytest.mark.parametrize("engine", [0, 1])
+@pytest.mark.parametrize("n", [1, 17, 127, 128, 129, 5000])
+def test_inference_matches_oracle(abi, oracle_mod, n, engine):
+    """Ragged sizes (1, 17 = one mma.sync warp tile + 1 row, 127/128/129 around one
+    tcgen05 tile, 5000) through the C ABI, both inference engines."""
     raw, _ = S.random_cache_records(n, 11)
     W = S.mlp_init_weights(12)
     h = abi.pt_cache_create(*BOX, batch=64, init_weights=W)
     try:
+        abi.pt_cache_set_engine(h, engine)
         d_raw = torch.as_tensor(raw, device="cuda")
         d_out = torch.full((n, 3), float("nan"), device="cuda")
         abi.pt_cache_query(h, d_raw, d_out, n)
         torch.cuda.synchronize()
+        assert abi.pt_cache_status(h) == abi.PT_OK
         got = d_out.cpu().numpy().astype(np.float64)
     finally:
         abi.pt_cache_destroy(h)
@@ -103,3 +107,30 @@ def test_training_converges_like_oracle(abi, oracle_mod):
     assert abs(losses[0] - ref[0]) < 1e-2 * ref[0]
     assert losses[-1] < 0.5 * losses[0]
     assert losses[-1] < 1.5 * ref[-1] + 1e-3
+
+
+def test_engines_agree_on_large_batch(abi):
+    """tcgen05 and mma.sync inference on 300,001 queries (2,344 MMA tiles + a ragged
+    one): the same BF16 rounding points, FP32 accumulation in a different order."""
+    n = 300_001
+    raw, _ = S.random_cache_records(n, 21)
+    W = S.mlp_init_weights(13)
+    h = abi.pt_cache_create(*BOX, batch=64, init_weights=W)
+    try:
+        d_raw = torch.as_tensor(raw, device="cuda")
+        out = []
+        for engine in (abi.PT_CACHE_TCGEN05, abi.PT_CACHE_MMA_SYNC):
+            abi.pt_cache_set_engine(h, engine)
+            d_out = torch.full((n, 3), float("nan"), device="cuda")
+            abi.pt_cache_query(h, d_raw, d_out, n)
+            torch.cuda.synchronize()
+            assert abi.pt_cache_status(h) == abi.PT_OK
+            out.append(d_out.cpu().numpy().astype(np.float64))
+    finally:
+        abi.pt_cache_destroy(h)
+    a, b = out
+    assert np.all(np.isfinite(a))
+    err = _rel_err(a, b)
+    print(f"tcgen05 vs mma.sync: median {np.median(err):.2e} p99.9 {np.quantile(err, 0.999):.2e} max {err.max():.2e}")
+    assert np.median(err) < 1e-3
+    assert np.quantile(err, 0.999) < 2e-2
