@@ -132,5 +132,5 @@ def test_engines_agree_on_large_batch(abi):
     assert np.all(np.isfinite(a))
     err = _rel_err(a, b)
     print(f"tcgen05 vs mma.sync: median {np.median(err):.2e} p99.9 {np.quantile(err, 0.999):.2e} max {err.max():.2e}")
-    assert np.median(err) < 1e-3
-    assert np.quantile(err, 0.999) < 2e-2
+    assert np.median(err) < 1e-6  # same features and rounding points; FP32 accumulation order may differ
+    assert np.quantile(err, 0.999) < 1e-4
