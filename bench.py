@@ -67,6 +67,8 @@ def parse():
     ap.add_argument("--wavefront", action="store_true",
                     help="megakernel vs wavefront ablation, forward and adjoint (own JSON line)")
     ap.add_argument("--wave-paths", type=int, default=0)
+    ap.add_argument("--mlp", action="store_true",
+                    help="radiance-cache MLP inference throughput, tcgen05 vs mma.sync engines (own JSON line)")
     ap.add_argument("--ckpt", action="store_true",
                     help="PRB vs reverse mode with checkpoints, one gradient step each (own JSON line)")
     ap.add_argument("--peaks", action="store_true",
@@ -599,6 +601,70 @@ def run_ckpt_experiment(args):
     ck.close()
 
 
+MLP_FLOPS_PER_QUERY = 2 * (5 * 64 * 64 + 64 * 3)  # five 64x64 layers + the 64x3 head
+
+
+def measured_peak(key, fallback):
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)[key]), "measured"
+    except Exception:
+        return fallback, "fallback"
+
+
+def run_mlp_experiment(args):
+    """Radiance-cache MLP inference throughput: the tcgen05 engine (UMMA, TMEM
+    accumulators) against the mma.sync engine on the same queries.  Own JSON line."""
+    import numpy as np
+    import torch
+
+    from paper_2202_01284_gb300 import abi
+    from paper_2202_01284_gb300 import scenes as S
+    abi.load()
+    n = (1 << 21) if args.small else (1 << 24)
+    box = ((-1.0, 0.0, -1.0), (1.0, 2.0, 1.0))
+    raw, _ = S.random_cache_records(min(n, 1 << 20), 3, *box)
+    raw = np.tile(raw, (n // raw.shape[0], 1))
+    h = abi.pt_cache_create(*box, batch=64, init_weights=S.mlp_init_weights(12))
+    d_raw = torch.as_tensor(raw, device="cuda")
+    d_out = torch.empty((n, 3), device="cuda")
+    res = {}
+    clocks = ClockSampler(0)
+    clocks.start()
+    for name, eng in (("tcgen05", abi.PT_CACHE_TCGEN05), ("mma_sync", abi.PT_CACHE_MMA_SYNC)):
+        abi.pt_cache_set_engine(h, eng)
+        for _ in range(max(3, args.warmup)):
+            abi.pt_cache_query(h, d_raw, d_out, n)
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(args.steps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            abi.pt_cache_query(h, d_raw, d_out, n)
+            b.record()
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+        assert abi.pt_cache_status(h) == abi.PT_OK
+        t = statistics.mean(ms)
+        res[name] = {"ms": round(t, 4), "gqueries_s": round(n / t / 1e6, 3),
+                     "tflops": round(n * MLP_FLOPS_PER_QUERY / t / 1e9, 1)}
+    clk = clocks.stop()
+    abi.pt_cache_destroy(h)
+    peak, basis = measured_peak("bf16_tflops", 1900.0)
+    ach = res["tcgen05"]["tflops"]
+    line = {"metric": "radiance-cache MLP inference, queries/s (tcgen05 vs mma.sync)",
+            "value": res["tcgen05"]["gqueries_s"], "unit": "G queries/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": max(3, args.warmup), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16 (FP32 accumulate)", "data": "synthetic",
+            "config": {"workload": f"{n} queries, 64-d encoding, 5x64 ReLU + 64x3, BF16 weights", "engines": res,
+                       "speedup_over_mma_sync": round(res["mma_sync"]["ms"] / res["tcgen05"]["ms"], 2)},
+            "roofline": {"bound": "tensor", "kernel": "nrc_infer_tc_kernel", "achieved": ach, "peak": peak,
+                         "unit": "TFLOP/s", "frac": round(ach / peak, 4), "traffic": None,
+                         "peak_basis": f"bf16 dense, {basis} (cuBLAS burst); includes the encoding on CUDA cores"},
+            "clocks": clk}
+    print(json.dumps(line), flush=True)
+
+
 def run_cache_experiment(args):
     """Cornell box at 1024^2, depth 4: plain PT at 64 spp vs cache-terminated PT (bounce 1
     and 2) at the spp that fits the same per-frame time including one online training
@@ -660,7 +726,7 @@ def run_cache_experiment(args):
            "indirect_pixel_fraction": n_ind / (3 * W * H),
            "plain": {"spp": 64, "ms": round(t_plain, 3), "mse": mp, "mse_indirect": mpi}}
     for bounce in (1, 2):
-        cache = RadianceCache(*box, batch=65536, max_queries=W * H * 192, max_records=2_000_000,
+        cache = RadianceCache(*box, batch=65536, max_queries=W * H * 384, max_records=2_000_000,
                               max_paths=256 * 256, lr=5e-3, init_weights=S.mlp_init_weights(2022))
         train_st = RenderSettings(width=256, height=256, spp=1, max_depth=D, seed=0)
         train_cam = [S.cornell_camera(256, 256)]
@@ -676,9 +742,7 @@ def run_cache_experiment(args):
         loss = cache.last_loss()
         res = {}
         best = None
-        for spp in (1, 2, 4, 8, 16, 32, 64, 96, 128, 192):
-            if W * H * spp > W * H * 64 * 3:
-                break
+        for spp in (1, 2, 4, 8, 16, 32, 64, 96, 128, 192, 256, 320, 384):
             t_frame, img = timed(lambda: (train_frame(10 ** 6 + spp),
                                           ds.forward(st(spp, 8, cache=cache.handle, cache_bounce=bounce)))[1])
             m_all, m_ind = mse(img)
@@ -838,6 +902,8 @@ def main():
         run_wavefront_experiment(args)
     elif args.ckpt:
         run_ckpt_experiment(args)
+    elif args.mlp:
+        run_mlp_experiment(args)
     else:
         run_ours(args)
 
