@@ -216,10 +216,11 @@ __global__ void __launch_bounds__(128 * kGroups, 1)
                     s > 0 ? 1u : 0u);
         umma_commit(bar);
       }
+      // each thread waits for the commit itself; the group agrees on the outcome at
+      // the end of the layer (a thread whose wait gave up reads an unfinished
+      // accumulator: wrong values, reported through `status`, no stray access)
       const bool done = mbar_wait(bar, phase, kWaitLimit);
       phase ^= 1u;
-      ok = group_sync_and(g, done);
-      if (!ok) break;
       tc_fence_after();
       if (!head) {
         // ReLU + BF16 of this thread's row -> the next operand tile
@@ -248,7 +249,8 @@ __global__ void __launch_bounds__(128 * kGroups, 1)
         }
       }
       tc_fence_before();
-      group_sync(g);
+      ok = group_sync_and(g, done);
+      if (!ok) break;
     }
   }
   if (!ok) {
