@@ -566,8 +566,14 @@ int cache_optimise(pt_cache* c, const float* raw, const float* target, long long
     long long grid = (tiles + 3) / 4;
     if (grid > 152 * 4) grid = 152 * 4;
     cudaMemsetAsync(c->loss, 0, 4, st);
-    nrc_train_fb_kernel<<<(unsigned)grid, 128, kTrainSmem, st>>>(raw + off * NRC_RAW, target + off * 3, nb, c->box,
-                                                                 c->Wb, c->X, c->dZ, c->loss);
+    if (c->engine == PT_CACHE_TCGEN05) {
+      const int rc = cache_train_fb_tc(raw + off * NRC_RAW, target + off * 3, nb, c->box, c->Wb, c->X, c->dZ, c->loss,
+                                       c->status, st);
+      if (rc != PT_OK) return rc;
+    } else {
+      nrc_train_fb_kernel<<<(unsigned)grid, 128, kTrainSmem, st>>>(raw + off * NRC_RAW, target + off * 3, nb, c->box,
+                                                                   c->Wb, c->X, c->dZ, c->loss);
+    }
     const long long chunk = 512;
     dim3 g2((unsigned)((nb + chunk - 1) / chunk), NRC_HIDDEN + 1);
     nrc_wgrad_kernel<<<g2, 128, 0, st>>>(c->X, c->dZ, nb, chunk, c->dW);

@@ -24,6 +24,10 @@ struct NrcBox {
 // PT_ERR_TIMEOUT if a bounded wait on the tensor core gave up.
 int cache_infer_tc(const float* raw, float* rgb, long long n, const NrcBox& box, const __nv_bfloat16* Wb, int* status,
                    cudaStream_t st);
+// Training forward + backward deltas on tcgen05 (pt_nrc_tc.cu): writes X[6][n][64],
+// dZ[6][n][64] and adds the batch's loss, as nrc_train_fb_kernel.
+int cache_train_fb_tc(const float* raw, const float* target, long long n, const NrcBox& box, const __nv_bfloat16* Wb,
+                      __nv_bfloat16* X, __nv_bfloat16* dZ, float* loss, int* status, cudaStream_t st);
 
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
   __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);

@@ -266,6 +266,233 @@ __global__ void __launch_bounds__(128 * kGroups, 1)
   }
 }
 
+// ---------------------------------------------------------------- training: forward + backward deltas
+// The mma.sync training kernel's computation on tcgen05, group by group: per
+// 128-record tile, the forward chain writes X_0..X_5 (BF16, [n][64] per layer),
+// the head gives y, the relative-L2 loss and dy = 2 (y - t) / (y^2 + 0.01) / n
+// (rounded to BF16, written to dZ_5 columns 0..2), then
+//   dX_5 = dY Wh,  dZ_l = dX_{l+1} * [X_{l+1} > 0]  (BF16, written to dZ_l),
+//   dX_l = dZ_l W_l  (l = 4 .. 1).
+// The backward products use transposed weight tiles (B[n = i][k = o] = W[o][i]).
+constexpr int kTrGroups = 4;
+constexpr uint32_t kTrW = 0, kTrH = 40960, kTrWT = kTrH + 2048, kTrHT = kTrWT + 40960;
+constexpr uint32_t kTrX = kTrHT + 2048;                        // per group: 128x64 operand tile
+constexpr uint32_t kTrY = kTrX + kTrGroups * 16384;            // per group: 128x16 head-delta tile
+constexpr uint32_t kTrBar = kTrY + kTrGroups * 4096, kTrSlot = kTrBar + 8 * kTrGroups;
+constexpr uint32_t kTrSmem = kTrSlot + 8 + 1024;
+constexpr uint32_t kTrCols = 64 * kTrGroups;
+
+// K = 16 operand tile: two core matrices along K (128 B apart), 8-row groups 256 B apart.
+__device__ __forceinline__ uint32_t core16_off(int row, int k) {
+  return (uint32_t)((row >> 3) * 256 + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2);
+}
+
+// Issue D = A B^T over K = 64 (four K = 16 steps), or one step for K = 16 tiles.
+__device__ __forceinline__ void issue_k64(uint32_t d, uint32_t a_s, uint32_t b_s, uint32_t idesc, uint64_t* bar) {
+  tc_fence_after();
+#pragma unroll
+  for (int s = 0; s < 4; ++s)
+    umma_bf16(d, umma_desc(a_s + 256u * s, kLBO, kSBO), umma_desc(b_s + 256u * s, kLBO, kSBO), idesc,
+              s > 0 ? 1u : 0u);
+  umma_commit(bar);
+}
+__device__ __forceinline__ void issue_k16(uint32_t d, uint32_t a_s, uint32_t b_s, uint32_t idesc, uint64_t* bar) {
+  tc_fence_after();
+  umma_bf16(d, umma_desc(a_s, 128, 256), umma_desc(b_s, 128, 256), idesc, 0u);
+  umma_commit(bar);
+}
+
+// Writes 8 BF16 values (one 16-byte chunk k8 of row `row`) to the operand tile and
+// to the global row.
+__device__ __forceinline__ void put_chunk(unsigned char* tile, int row, int k8, uint4 q, __nv_bfloat16* grow) {
+  *reinterpret_cast<uint4*>(tile + core_off(row, 8 * k8)) = q;
+  if (grow) reinterpret_cast<uint4*>(grow)[k8] = q;
+}
+
+__global__ void __launch_bounds__(128 * kTrGroups, 1)
+    nrc_train_tc_kernel(const float* __restrict__ raw, const float* __restrict__ target, long long n, NrcBox box,
+                        const __nv_bfloat16* __restrict__ W, __nv_bfloat16* __restrict__ X,
+                        __nv_bfloat16* __restrict__ dZ, float* __restrict__ loss, int* __restrict__ status) {
+  extern __shared__ unsigned char tc_smem_raw[];
+  unsigned char* sm = tc_smem_raw + ((1024u - (smem_addr(tc_smem_raw) & 1023u)) & 1023u);
+  uint32_t* slot = reinterpret_cast<uint32_t*>(sm + kTrSlot);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int g = tid >> 7, r = tid & 127;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sm + kTrBar) + g;
+  unsigned char* Xt = sm + kTrX + g * 16384;
+  unsigned char* Yt = sm + kTrY + g * 4096;
+
+  // weights: forward tiles B[o][i] and transposed tiles B[i][o]; the head (3 rows used)
+  const unsigned short* gw = reinterpret_cast<const unsigned short*>(W);
+  for (int idx = tid; idx < NRC_HIDDEN * NRC_W * NRC_W; idx += blockDim.x) {
+    const int l = idx >> 12, o = (idx >> 6) & 63, i = idx & 63;
+    const unsigned short v = gw[idx];
+    *reinterpret_cast<unsigned short*>(sm + kTrW + l * 8192 + core_off(o, i)) = v;
+    *reinterpret_cast<unsigned short*>(sm + kTrWT + l * 8192 + core_off(i, o)) = v;
+  }
+  for (int idx = tid; idx < 16 * NRC_W; idx += blockDim.x) {
+    const int o = idx >> 6, i = idx & 63;
+    const unsigned short v = o < NRC_OUT ? gw[NRC_HIDDEN * NRC_W * NRC_W + o * NRC_W + i] : (unsigned short)0;
+    *reinterpret_cast<unsigned short*>(sm + kTrH + core_off(o, i)) = v;   // [o(16)][i(64)]
+    *reinterpret_cast<unsigned short*>(sm + kTrHT + core16_off(i, o)) = v;  // [i(64)][o(16)]
+  }
+  if (r == 0) mbar_init(bar, 1);
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(slot)),
+                 "r"(kTrCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_async_smem();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *slot + 64u * g;
+  const uint32_t x_s = smem_addr(Xt), y_s = smem_addr(Yt);
+  const uint32_t w_s = smem_addr(sm + kTrW), h_s = smem_addr(sm + kTrH);
+  const uint32_t wt_s = smem_addr(sm + kTrWT), ht_s = smem_addr(sm + kTrHT);
+  const uint32_t t_lane = tmem + ((uint32_t)((warp & 3) * 32) << 16);
+  const uint32_t id64 = idesc_bf16(128, 64), id16 = idesc_bf16(128, 16);
+  const long long plane = n * NRC_W;
+  const float inv_n = 1.0f / (float)n;
+  float loss_acc = 0.0f;
+  uint32_t phase = 0;
+  bool ok = true;
+  // one MMA step of the group: issue (thread 0 of the group), wait, agree
+  auto step = [&](auto&& issue) -> bool {
+    if (r == 0) issue();
+    const bool done = mbar_wait(bar, phase, kWaitLimit);
+    phase ^= 1u;
+    tc_fence_after();
+    return done;
+  };
+  const long long n_tiles = (n + 127) / 128;
+  for (long long tile = (long long)blockIdx.x * kTrGroups + g; tile < n_tiles && ok;
+       tile += (long long)gridDim.x * kTrGroups) {
+    const long long row = tile * 128 + r;
+    const bool live = row < n;
+    // ---- encoding -> X_0
+    {
+      float rr[NRC_RAW];
+#pragma unroll
+      for (int k = 0; k < NRC_RAW; ++k) rr[k] = live ? raw[row * NRC_RAW + k] : 0.0f;
+      float f[64];
+      encode_row(rr, box, f);
+#pragma unroll
+      for (int c8 = 0; c8 < 8; ++c8) {
+        const float* p = f + 8 * c8;
+        const uint4 q = live ? make_uint4(pack_bf16(p[0], p[1]), pack_bf16(p[2], p[3]), pack_bf16(p[4], p[5]),
+                                          pack_bf16(p[6], p[7]))
+                             : make_uint4(0u, 0u, 0u, 0u);
+        put_chunk(Xt, r, c8, q, live ? X + row * NRC_W : nullptr);
+      }
+    }
+    fence_async_smem();
+    tc_fence_before();
+    ok = group_sync_and(g, true);
+    // ---- forward: X_{l+1} = relu(X_l W_l^T), then the head
+    for (int l = 0; l < NRC_HIDDEN && ok; ++l) {
+      const bool done = step([&] { issue_k64(tmem, x_s, w_s + (uint32_t)l * 8192u, id64, bar); });
+#pragma unroll
+      for (int c16 = 0; c16 < 4; ++c16) {
+        float v[16];
+        tmem_ld16(t_lane + 16u * c16, v);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const float* p = v + 8 * h;
+          const uint4 q = make_uint4(pack_bf16(fmaxf(p[0], 0.f), fmaxf(p[1], 0.f)),
+                                     pack_bf16(fmaxf(p[2], 0.f), fmaxf(p[3], 0.f)),
+                                     pack_bf16(fmaxf(p[4], 0.f), fmaxf(p[5], 0.f)),
+                                     pack_bf16(fmaxf(p[6], 0.f), fmaxf(p[7], 0.f)));
+          put_chunk(Xt, r, 2 * c16 + h, q, live ? X + (l + 1) * plane + row * NRC_W : nullptr);
+        }
+      }
+      fence_async_smem();
+      tc_fence_before();
+      ok = group_sync_and(g, done);
+    }
+    if (!ok) break;
+    {
+      const bool done = step([&] { issue_k64(tmem, x_s, h_s, id16, bar); });
+      float y[16];
+      tmem_ld16(t_lane, y);
+      float dy[3] = {0.f, 0.f, 0.f};
+      if (live) {
+#pragma unroll
+        for (int c = 0; c < NRC_OUT; ++c) {
+          const float tv = target[row * 3 + c];
+          const float den = y[c] * y[c] + 0.01f;
+          const float diff = y[c] - tv;
+          loss_acc += diff * diff / den * inv_n;
+          dy[c] = 2.0f * diff / den * inv_n;
+        }
+      }
+      // head delta: the K = 16 operand tile (columns 0..2) and dZ_5 (64 columns, 3 used)
+      const uint4 q0 = make_uint4(pack_bf16(dy[0], dy[1]), pack_bf16(dy[2], 0.f), 0u, 0u);
+      *reinterpret_cast<uint4*>(Yt + core16_off(r, 0)) = q0;
+      *reinterpret_cast<uint4*>(Yt + core16_off(r, 8)) = make_uint4(0u, 0u, 0u, 0u);
+      if (live) {
+        uint4* d5 = reinterpret_cast<uint4*>(dZ + NRC_HIDDEN * plane + row * NRC_W);
+        d5[0] = q0;
+#pragma unroll
+        for (int k8 = 1; k8 < 8; ++k8) d5[k8] = make_uint4(0u, 0u, 0u, 0u);
+      }
+      fence_async_smem();
+      tc_fence_before();
+      ok = group_sync_and(g, done);
+    }
+    if (!ok) break;
+    // ---- backward: dX_5 = dY Wh, then dZ_l, dX_l for l = 4 .. 0
+    {
+      const bool done = step([&] { issue_k16(tmem, y_s, ht_s, id64, bar); });
+      ok = done;  // agreed below together with the first delta
+    }
+    for (int l = NRC_HIDDEN - 1; l >= 0; --l) {
+      // dZ_l = dX_{l+1} * [X_{l+1} > 0] (X_{l+1} as written by this thread above)
+      const uint4* xg = reinterpret_cast<const uint4*>(X + (l + 1) * plane + row * NRC_W);
+#pragma unroll
+      for (int c16 = 0; c16 < 4; ++c16) {
+        float v[16];
+        tmem_ld16(t_lane + 16u * c16, v);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int k8 = 2 * c16 + h;
+          const uint4 xq = live ? xg[k8] : make_uint4(0u, 0u, 0u, 0u);
+          const uint32_t xw[4] = {xq.x, xq.y, xq.z, xq.w};
+          uint32_t dq[4];
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const float d0 = bf16_lo(xw[e]) > 0.f ? v[8 * h + 2 * e] : 0.f;
+            const float d1 = bf16_hi(xw[e]) > 0.f ? v[8 * h + 2 * e + 1] : 0.f;
+            dq[e] = pack_bf16(d0, d1);
+          }
+          put_chunk(Xt, r, k8, make_uint4(dq[0], dq[1], dq[2], dq[3]),
+                    live ? dZ + l * plane + row * NRC_W : nullptr);
+        }
+      }
+      fence_async_smem();
+      tc_fence_before();
+      ok = group_sync_and(g, ok);
+      if (!ok || l == 0) break;
+      ok = step([&] { issue_k64(tmem, x_s, wt_s + (uint32_t)l * 8192u, id64, bar); });
+    }
+    if (!ok) break;
+  }
+  if (!ok) {
+    if (r == 0) atomicCAS(status, 0, PT_ERR_TIMEOUT);
+    mbar_wait(bar, phase, kWaitLimit);
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) loss_acc += __shfl_xor_sync(0xffffffffu, loss_acc, off);
+  if (lane == 0 && loss_acc != 0.0f) atomicAdd(loss, loss_acc);
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(*slot), "r"(kTrCols) : "memory");
+  }
+}
+
 }  // namespace
 
 int cache_infer_tc(const float* raw, float* rgb, long long n, const NrcBox& box, const __nv_bfloat16* Wb, int* status,
@@ -288,4 +515,26 @@ int cache_infer_tc(const float* raw, float* rgb, long long n, const NrcBox& box,
   return cudaGetLastError() == cudaSuccess ? PT_OK : PT_ERR_CUDA;
 }
 
+}  // namespace ptgb
+
+namespace ptgb {
+int cache_train_fb_tc(const float* raw, const float* target, long long n, const NrcBox& box, const __nv_bfloat16* Wb,
+                      __nv_bfloat16* X, __nv_bfloat16* dZ, float* loss, int* status, cudaStream_t st) {
+  static int attr = 0;
+  if (!attr) {
+    if (cudaFuncSetAttribute(nrc_train_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTrSmem) !=
+        cudaSuccess)
+      return PT_ERR_CUDA;
+    attr = 1;
+  }
+  const long long tiles = (n + 127) / 128;
+  int dev = 0, sms = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  long long grid = (tiles + kTrGroups - 1) / kTrGroups;
+  if (grid > sms) grid = sms;
+  if (grid < 1) grid = 1;
+  nrc_train_tc_kernel<<<(unsigned)grid, 128 * kTrGroups, kTrSmem, st>>>(raw, target, n, box, Wb, X, dZ, loss, status);
+  return cudaGetLastError() == cudaSuccess ? PT_OK : PT_ERR_CUDA;
+}
 }  // namespace ptgb

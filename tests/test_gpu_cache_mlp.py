@@ -134,3 +134,28 @@ def test_engines_agree_on_large_batch(abi):
     print(f"tcgen05 vs mma.sync: median {np.median(err):.2e} p99.9 {np.quantile(err, 0.999):.2e} max {err.max():.2e}")
     assert np.median(err) < 1e-6  # same features and rounding points; FP32 accumulation order may differ
     assert np.quantile(err, 0.999) < 1e-4
+
+
+def test_training_engines_agree(abi):
+    """One optimisation step (Adam turned into w - g * 1e6 / (|g| + 1e6)) with the
+    tcgen05 and the mma.sync forward/backward kernels from the same weights on a
+    ragged batch of 5,000 records: the same loss and weight gradients."""
+    n = 5000
+    raw, tgt = S.random_cache_records(n, 23)
+    W0 = S.mlp_init_weights(24)
+    res = []
+    for engine in (abi.PT_CACHE_TCGEN05, abi.PT_CACHE_MMA_SYNC):
+        h = abi.pt_cache_create(*BOX, batch=5056, lr=1e6, beta1=0.0, beta2=0.0, eps=1e6, init_weights=W0)
+        try:
+            abi.pt_cache_set_engine(h, engine)
+            abi.pt_cache_train_records(h, torch.as_tensor(raw, device="cuda"), torch.as_tensor(tgt, device="cuda"),
+                                       n, 1)
+            assert abi.pt_cache_status(h) == abi.PT_OK
+            res.append((abi.pt_cache_last_loss(h), W0.astype(np.float64) - abi.pt_cache_get_weights(h)))
+        finally:
+            abi.pt_cache_destroy(h)
+    (l_tc, g_tc), (l_mma, g_mma) = res
+    c = cosine(g_tc, g_mma)
+    print(f"loss tcgen05 {l_tc:.7f} mma.sync {l_mma:.7f}; update cosine {c:.9f}")
+    assert abs(l_tc - l_mma) <= 1e-5 * abs(l_mma)
+    assert c > 0.99999
