@@ -575,8 +575,13 @@ int cache_optimise(pt_cache* c, const float* raw, const float* target, long long
                                                                    c->Wb, c->X, c->dZ, c->loss);
     }
     const long long chunk = 512;
-    dim3 g2((unsigned)((nb + chunk - 1) / chunk), NRC_HIDDEN + 1);
-    nrc_wgrad_kernel<<<g2, 128, 0, st>>>(c->X, c->dZ, nb, chunk, c->dW);
+    if (c->engine == PT_CACHE_TCGEN05) {
+      const int rc = cache_wgrad_tc(c->X, c->dZ, nb, chunk, c->dW, c->status, st);
+      if (rc != PT_OK) return rc;
+    } else {
+      dim3 g2((unsigned)((nb + chunk - 1) / chunk), NRC_HIDDEN + 1);
+      nrc_wgrad_kernel<<<g2, 128, 0, st>>>(c->X, c->dZ, nb, chunk, c->dW);
+    }
     c->step += 1;
     const pt_cache_desc& d = c->desc;
     const float c1 = 1.0f - std::pow(d.beta1, (float)c->step), c2 = 1.0f - std::pow(d.beta2, (float)c->step);

@@ -493,6 +493,107 @@ __global__ void __launch_bounds__(128 * kTrGroups, 1)
   }
 }
 
+// ---------------------------------------------------------------- training: weight gradients
+// dW_l[o][i] += sum_b dZ_l[b][o] X_l[b][i]: split-K over blocks (blockIdx.y = layer,
+// the head is layer 5 with o < 3).  The batch is the K dimension: each 64-record
+// step loads dZ_l^T (A: o x b, rows 64..127 zero so that M = 128) and X_l^T
+// (B: i x b) transposed into K-major tiles and accumulates D (o x i, FP32) in
+// TMEM over the block's records; the block then adds D to dW.
+constexpr uint32_t kWgA = 0, kWgB = 16384, kWgBar = kWgB + 8192, kWgSlot = kWgBar + 8;
+constexpr uint32_t kWgSmem = 40 * 1024;  // > what is used: at most 5 blocks (320 TMEM columns) per SM
+
+__global__ void __launch_bounds__(128) nrc_wgrad_tc_kernel(const __nv_bfloat16* __restrict__ X,
+                                                           const __nv_bfloat16* __restrict__ dZ, long long n,
+                                                           long long chunk, float* __restrict__ dW,
+                                                           int* __restrict__ status) {
+  extern __shared__ unsigned char tc_smem_raw[];
+  unsigned char* sm = tc_smem_raw + ((1024u - (smem_addr(tc_smem_raw) & 1023u)) & 1023u);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sm + kWgBar);
+  uint32_t* slot = reinterpret_cast<uint32_t*>(sm + kWgSlot);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int l = blockIdx.y;
+  const long long plane = n * NRC_W;
+  const unsigned short* Zl = reinterpret_cast<const unsigned short*>(dZ + l * plane);
+  const unsigned short* Xl = reinterpret_cast<const unsigned short*>(X + l * plane);
+  const long long b_begin = (long long)blockIdx.x * chunk;
+  const long long b_end = b_begin + chunk < n ? b_begin + chunk : n;
+  // rows 64..127 of A stay zero
+  for (int idx = tid; idx < 16384 / 16; idx += blockDim.x) reinterpret_cast<uint4*>(sm + kWgA)[idx] = make_uint4(0, 0, 0, 0);
+  if (tid == 0) mbar_init(bar, 1);
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(slot)), "r"(64u)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *slot;
+  const uint32_t a_s = smem_addr(sm + kWgA), b_s = smem_addr(sm + kWgB);
+  uint32_t phase = 0;
+  bool ok = true, any = false;
+  for (long long b0 = b_begin; b0 < b_end && ok; b0 += 64) {
+    // record rb = tid / 2 of the step, half h = tid % 2 of its 64 columns
+    const int rb = tid >> 1, h = tid & 1;
+    const long long b = b0 + rb;
+    uint4 zq[4], xq[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      zq[q] = b < b_end ? reinterpret_cast<const uint4*>(Zl + b * NRC_W + 32 * h)[q] : make_uint4(0, 0, 0, 0);
+      xq[q] = b < b_end ? reinterpret_cast<const uint4*>(Xl + b * NRC_W + 32 * h)[q] : make_uint4(0, 0, 0, 0);
+    }
+    const unsigned short* zs = reinterpret_cast<const unsigned short*>(zq);
+    const unsigned short* xs = reinterpret_cast<const unsigned short*>(xq);
+#pragma unroll
+    for (int e = 0; e < 32; ++e) {
+      const int c = 32 * h + e;  // o for A, i for B
+      *reinterpret_cast<unsigned short*>(sm + kWgA + core_off(c, rb)) = zs[e];
+      *reinterpret_cast<unsigned short*>(sm + kWgB + core_off(c, rb)) = xs[e];
+    }
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    if (tid == 0) {
+      tc_fence_after();
+#pragma unroll
+      for (int s2 = 0; s2 < 4; ++s2)
+        umma_bf16(tmem, umma_desc(a_s + 256u * s2, kLBO, kSBO), umma_desc(b_s + 256u * s2, kLBO, kSBO),
+                  idesc_bf16(128, 64), (any || s2 > 0) ? 1u : 0u);
+      umma_commit(bar);
+    }
+    any = true;
+    const bool done = mbar_wait(bar, phase, kWaitLimit);
+    phase ^= 1u;
+    tc_fence_after();
+    tc_fence_before();
+    ok = __syncthreads_and(done) != 0;  // the tiles may be overwritten after this
+  }
+  if (!ok) {
+    if (tid == 0) atomicCAS(status, 0, PT_ERR_TIMEOUT);
+    mbar_wait(bar, phase, kWaitLimit);
+  } else if (any && warp < 2) {
+    // rows o = 32 warp + lane of D (lanes 0..63): add to dW_l
+    float* dWl = dW + (size_t)l * NRC_W * NRC_W;
+    const int o = 32 * warp + (tid & 31);
+    const int o_lim = l < NRC_HIDDEN ? NRC_W : NRC_OUT;
+#pragma unroll
+    for (int c16 = 0; c16 < 4; ++c16) {
+      float v[16];
+      tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + 16u * c16, v);
+      if (o < o_lim) {
+#pragma unroll
+        for (int e = 0; e < 16; ++e) atomicAdd(&dWl[o * NRC_W + 16 * c16 + e], v[e]);
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(64u) : "memory");
+  }
+}
+
 }  // namespace
 
 int cache_infer_tc(const float* raw, float* rgb, long long n, const NrcBox& box, const __nv_bfloat16* Wb, int* status,
@@ -535,6 +636,22 @@ int cache_train_fb_tc(const float* raw, const float* target, long long n, const 
   if (grid > sms) grid = sms;
   if (grid < 1) grid = 1;
   nrc_train_tc_kernel<<<(unsigned)grid, 128 * kTrGroups, kTrSmem, st>>>(raw, target, n, box, Wb, X, dZ, loss, status);
+  return cudaGetLastError() == cudaSuccess ? PT_OK : PT_ERR_CUDA;
+}
+}  // namespace ptgb
+
+namespace ptgb {
+int cache_wgrad_tc(const __nv_bfloat16* X, const __nv_bfloat16* dZ, long long n, long long chunk, float* dW,
+                   int* status, cudaStream_t st) {
+  static int attr = 0;
+  if (!attr) {
+    if (cudaFuncSetAttribute(nrc_wgrad_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWgSmem) !=
+        cudaSuccess)
+      return PT_ERR_CUDA;
+    attr = 1;
+  }
+  const dim3 grid((unsigned)((n + chunk - 1) / chunk), NRC_HIDDEN + 1);
+  nrc_wgrad_tc_kernel<<<grid, 128, kWgSmem, st>>>(X, dZ, n, chunk, dW, status);
   return cudaGetLastError() == cudaSuccess ? PT_OK : PT_ERR_CUDA;
 }
 }  // namespace ptgb
