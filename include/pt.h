@@ -326,13 +326,12 @@ int pt_wavefront_backward(pt_scene* scene, const pt_render_desc* desc, const pt_
                           const pt_wavefront_opts* opts, const float* grad_image, const pt_grads* grads,
                           void* stream);
 
-/* Tensor-core engine of the cache MLP: PT_CACHE_TCGEN05 (default) runs inference
- * and the training forward/backward chain on the 5th-generation tensor cores
- * (tcgen05.mma, accumulators in tensor memory, 128 records per MMA tile);
- * PT_CACHE_MMA_SYNC uses warp-level mma.sync (16 records per warp tile,
- * activations in registers), kept for comparison.  Both round inputs and
- * activations to BF16 and accumulate in FP32; the weight gradients (a split-K
- * reduction over the batch) use mma.sync with either engine. */
+/* Tensor-core engine of the cache MLP: PT_CACHE_TCGEN05 (default) runs inference,
+ * the training forward/backward chain and the weight gradients on the
+ * 5th-generation tensor cores (tcgen05.mma, accumulators in tensor memory, 128
+ * records per MMA tile); PT_CACHE_MMA_SYNC uses warp-level mma.sync (16 records
+ * per warp tile, activations in registers), kept for comparison.  Both round
+ * inputs and activations to BF16 and accumulate in FP32. */
 enum { PT_CACHE_TCGEN05 = 0, PT_CACHE_MMA_SYNC = 1 };
 int pt_cache_set_engine(pt_cache* cache, int engine);
 /* Reads (after synchronising `stream`) and clears the cache's device status word:
