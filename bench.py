@@ -55,6 +55,7 @@ def parse():
     ap.add_argument("--lanes", type=int, default=0)
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--tex-aggregate", type=int, default=0)
+    ap.add_argument("--prb-mode", type=int, default=0, help="backward: 0 auto (split), 1 fused PRB, 2 split")
     ap.add_argument("--bvh", default="wide", choices=["wide", "binary"])
     ap.add_argument("--cache", action="store_true",
                     help="radiance-cache experiment: equal-time MSE, cache-terminated vs plain PT (own JSON line)")
@@ -144,11 +145,12 @@ def settings(args, seed):
     if args.small:
         return RenderSettings(width=256, height=256, spp=64, max_depth=WORKLOAD["max_depth"],
                               rr_depth=WORKLOAD["rr_depth"], seed=seed, dispatch=args.dispatch,
-                              lanes_per_pixel=args.lanes, block_size=args.block, tex_aggregate=args.tex_aggregate)
+                              lanes_per_pixel=args.lanes, block_size=args.block, tex_aggregate=args.tex_aggregate,
+                              prb_mode=args.prb_mode)
     return RenderSettings(width=WORKLOAD["width"], height=WORKLOAD["height"], spp=WORKLOAD["spp"],
                           max_depth=WORKLOAD["max_depth"], rr_depth=WORKLOAD["rr_depth"], seed=seed,
                           dispatch=args.dispatch, lanes_per_pixel=args.lanes, block_size=args.block,
-                          tex_aggregate=args.tex_aggregate)
+                          tex_aggregate=args.tex_aggregate, prb_mode=args.prb_mode)
 
 
 # Bounded samples of the workload for the FP64 oracle on the host cores: the
@@ -328,9 +330,29 @@ def run_ours(args):
             dist.destroy_process_group()
         return
     fwd_avg, adj_avg = statistics.mean(fwd_ms), statistics.mean(adj_ms)
-    dom = "adjoint_kernel" if adj_avg >= fwd_avg else "forward_kernel"
-    dom_ms = max(adj_avg, fwd_avg)
-    dom_flops = flops_b if adj_avg >= fwd_avg else flops_f
+    split = args.prb_mode != abi.PT_PRB_FUSED
+    if split:
+        # the adjoint stage is a radiance pass (the forward megakernel with the adjoint
+        # seed, storing each sample's L) + the replay kernel: time that radiance pass
+        # on its own (after the timed region) to attribute the stage to its kernels
+        from dataclasses import replace
+        st_r = replace(st_f, seed=seed_bwd)
+        ev_r = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                for _ in range(args.steps)]
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            ev_r[k][0].record(stream)
+            ds.forward(st_r, out=img)
+            ev_r[k][1].record(stream)
+        torch.cuda.synchronize()
+        rad_avg = statistics.mean(a.elapsed_time(b) for a, b in ev_r)
+        replay_avg = adj_avg - rad_avg
+        kern = {"forward_kernel": (fwd_avg, flops_f), "replay_kernel": (replay_avg, flops_b / 2)}
+    else:
+        rad_avg = replay_avg = None
+        kern = {"forward_kernel": (fwd_avg, flops_f), "adjoint_kernel": (adj_avg, flops_b)}
+    dom = max(kern, key=lambda k: kern[k][0])
+    dom_ms, dom_flops = kern[dom]
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     mhz = clk.get("sm_mhz") or 1477.0
     peak_tflops = sms * 128 * 2 * mhz * 1e6 / 1e12
@@ -349,7 +371,10 @@ def run_ours(args):
         "config": {**WORKLOAD, "l2": "flushed between timed steps (256 MB write)", "dispatch": args.dispatch,
                    "bvh": f"{args.bvh} SAH", "bvh_nodes": info["n_nodes"], "rays_per_step": rays_step,
                    "rays_fwd": rays_f, "rays_adj": rays_b, "fwd_ms": round(fwd_avg, 3),
-                   "adj_ms": round(adj_avg, 3), "fwd_mrays_s": round(rays_f / fwd_avg / 1e3, 1),
+                   "adj_ms": round(adj_avg, 3), "prb": "split" if split else "fused",
+                   "adj_radiance_pass_ms": round(rad_avg, 3) if split else None,
+                   "adj_replay_ms": round(replay_avg, 3) if split else None,
+                   "fwd_mrays_s": round(rays_f / fwd_avg / 1e3, 1),
                    "adj_mrays_s": round(rays_b / adj_avg / 1e3, 1),
                    "node_visits_per_ray_fwd": round(int(cf[3]) / max(rays_f, 1), 2),
                    "tri_tests_per_ray_fwd": round(int(cf[4]) / max(rays_f, 1), 2),
@@ -357,12 +382,14 @@ def run_ours(args):
         "roofline": {"bound": "alu", "kernel": dom, "achieved": round(achieved, 3),
                      "peak": round(peak_tflops, 2), "unit": "TFLOP/s", "frac": round(achieved / peak_tflops, 4),
                      "traffic": DRAM_TRAFFIC_PER_LAUNCH.get(args.bvh, {}).get(dom) if not args.small else None,
-                     "work": f"{FLOPS_PER_NODE[args.bvh]}/node visit + {FLOPS_PER_TRI}/triangle test (counted launch)",
+                     "work": f"{FLOPS_PER_NODE[args.bvh]}/node visit + {FLOPS_PER_TRI}/triangle test (counted launch"
+                             + ("; replay = half of the counted fused adjoint, its time = adjoint stage minus "
+                                "the radiance pass timed alone)" if split else ")"),
                      "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 x median SM clock {mhz} MHz"},
         "cpu_baseline": cpu,
         "e2e": {"value": round(rays_step / (e2e_ms / 1e3) / 1e6, 2), "unit": "Mrays/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": round(e2e_ms, 3)},
-        "gpu_launches": 2 * args.steps,
+        "gpu_launches": (3 if split else 2) * args.steps,
         "clocks": clk,
         "wall_s": round(wall, 3),
     }

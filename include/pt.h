@@ -175,7 +175,16 @@ typedef struct {
    * detached incident radiance at that vertex. */
   struct pt_cache* cache;
   int32_t cache_bounce;         /* >= 1 */
+  /* pt_render_backward only, PT_PRB_*: SPLIT runs the paper's separate phases -- a
+   * forward kernel stores every sample's radiance (12 B per sample in scene-owned
+   * scratch grown with cudaMalloc, which synchronises the device), then a
+   * replay-only adjoint kernel; FUSED traces each sample for its radiance and
+   * replays it in one kernel (no scratch).  AUTO (0) = SPLIT.  SPLIT applies to the
+   * plain adjoint (no cache, env gradients, texel aggregation or counters); the
+   * others run fused. */
+  int32_t prb_mode;
 } pt_render_desc;
+enum { PT_PRB_AUTO = 0, PT_PRB_FUSED = 1, PT_PRB_SPLIT = 2 };
 
 /* Differentiable parameters: borrowed device pointers. */
 typedef struct {

@@ -32,6 +32,9 @@ PT_BVH_BINARY = 0
 PT_BVH_WIDE = 1
 PT_DISPATCH_SWITCH = 0
 PT_DISPATCH_MATCH = 1
+PT_PRB_AUTO = 0
+PT_PRB_FUSED = 1
+PT_PRB_SPLIT = 2
 PT_WF_TRACED = 0
 PT_WF_GROUPED = 1
 PT_N_COUNTERS = 16
@@ -77,7 +80,7 @@ class pt_render_desc(C.Structure):
                 ("crop_x0", C.c_int32), ("crop_y0", C.c_int32), ("crop_w", C.c_int32), ("crop_h", C.c_int32),
                 ("lanes_per_pixel", C.c_int32), ("block_size", C.c_int32), ("tex_aggregate", C.c_int32),
                 ("dbg_sample_L", C.c_void_p), ("dbg_sample_hash", C.c_void_p), ("counters", C.c_void_p),
-                ("cache", C.c_void_p), ("cache_bounce", C.c_int32)]
+                ("cache", C.c_void_p), ("cache_bounce", C.c_int32), ("prb_mode", C.c_int32)]
 
 
 class pt_params(C.Structure):
@@ -247,7 +250,7 @@ def camera_struct(cam: "S.Camera") -> pt_camera:
 
 def render_desc(cams, width, height, spp, max_depth, seed, rr_depth=-1, nee=True, dispatch=PT_DISPATCH_SWITCH,
                 crop=None, lanes_per_pixel=0, block_size=0, tex_aggregate=0, dbg_L=None, dbg_hash=None,
-                counters=None, cache=None, cache_bounce=1):
+                counters=None, cache=None, cache_bounce=1, prb_mode=0):
     cams = list(cams)
     arr = (pt_camera * len(cams))(*[camera_struct(c) for c in cams])
     r = pt_render_desc()
@@ -263,6 +266,7 @@ def render_desc(cams, width, height, spp, max_depth, seed, rr_depth=-1, nee=True
     r.counters = _ptr(counters)
     r.cache = cache
     r.cache_bounce = cache_bounce
+    r.prb_mode = prb_mode
     r._keep = arr
     return r
 

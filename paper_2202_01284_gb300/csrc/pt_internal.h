@@ -108,6 +108,7 @@ struct alignas(16) LaunchArgs {
   uint4* ck_state;
   int* ck_count;
   long long ck_slots;
+  float* sample_L;             // split PRB: [slots][3] radiance of each sample (adjoint seed)
   DevCamera cams[PT_MAX_CAMS];
 };
 static_assert(sizeof(LaunchArgs) % 16 == 0, "job records are copied with 16-byte loads");
@@ -159,5 +160,7 @@ struct pt_scene {
   void* d_status = nullptr;
   void* d_wf = nullptr;         // wavefront scratch (grown on demand)
   size_t wf_bytes = 0;
+  void* d_sample_L = nullptr;   // split PRB: per-sample radiance (grown on demand)
+  size_t sample_L_bytes = 0;
   pt_scene_info info{};
 };

@@ -119,7 +119,9 @@ __device__ __forceinline__ void megakernel(const LaunchArgs& A, long long unit, 
   float3 pix_sum_dot = f3(0.f, 0.f, 0.f);
   float3 L_pass0 = f3(0.f, 0.f, 0.f);
   int next_s = lane_in_pix;
-  int pass = 0;
+  // FEAT_REPLAY: every sample is replayed once from the radiance the forward stored
+  constexpr bool REPLAY = ADJ && (FEAT & FEAT_REPLAY) != 0;
+  int pass = REPLAY ? 1 : 0;
   bool has_path = false;
   bool want_shadow = false;  // the lane's next traversal is its pending shadow ray
   PathState P;
@@ -127,7 +129,12 @@ __device__ __forceinline__ void megakernel(const LaunchArgs& A, long long unit, 
     if (!has_path && valid && next_s < A.spp) {
       // one call site for both passes: the replay starts from identical code
       path_start<INSTR>(A, P, ADJ ? A.seed_adj : A.seed, px.cam, px.px, px.py, next_s, px.pix, cnt);
-      P.Lrem = L_pass0;
+      if constexpr (REPLAY) {
+        const float* l = A.sample_L + 3 * P.slot;
+        P.Lrem = f3(l[0], l[1], l[2]);
+      } else {
+        P.Lrem = L_pass0;
+      }
       has_path = true;
       want_shadow = false;
     }
@@ -170,7 +177,13 @@ __device__ __forceinline__ void megakernel(const LaunchArgs& A, long long unit, 
             pl[2] = P.L.z;
           }
         }
-        if (ADJ && pass == 0) {
+        if constexpr (!ADJ && (FEAT & FEAT_SAMPLE_L) != 0) {
+          float* l = A.sample_L + 3 * P.slot;
+          l[0] = P.L.x;
+          l[1] = P.L.y;
+          l[2] = P.L.z;
+        }
+        if (ADJ && !REPLAY && pass == 0) {
           L_pass0 = P.L;  // replay the same sample next: L_rem starts from its radiance
           pass = 1;
         } else {
@@ -186,7 +199,7 @@ __device__ __forceinline__ void megakernel(const LaunchArgs& A, long long unit, 
             if (A.dbg_hash) A.dbg_hash[si] = P.fh.h;
           }
           next_s += A.lanes_per_pixel;
-          pass = 0;
+          pass = REPLAY ? 1 : 0;
           L_pass0 = f3(0.f, 0.f, 0.f);
         }
       }

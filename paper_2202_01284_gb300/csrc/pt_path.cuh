@@ -10,8 +10,12 @@ namespace ptgb {
 // Optional features compiled into an instantiation of the per-vertex code (each
 // costs the production kernels instruction-cache space when compiled in):
 // environment-radiance gradients, radiance-cache modes, warp-aggregated texel
-// atomics, reverse-mode checkpoints.
-enum : int { FEAT_EGRAD = 1, FEAT_CACHE = 2, FEAT_TEXAGG = 4, FEAT_CKPT = 8, FEAT_ALL = 7 };
+// atomics, reverse-mode checkpoints; split PRB: the forward writes each sample's
+// radiance, the adjoint replays only (no radiance pass of its own).
+enum : int {
+  FEAT_EGRAD = 1, FEAT_CACHE = 2, FEAT_TEXAGG = 4, FEAT_CKPT = 8, FEAT_SAMPLE_L = 16, FEAT_REPLAY = 32,
+  FEAT_ALL = 7
+};
 
 // Per-vertex gradient sink of the adjoint: warp-aggregated atomics.
 // Constant-albedo rows and roughness entries are few and heavily shared, so the

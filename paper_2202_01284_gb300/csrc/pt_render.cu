@@ -40,6 +40,19 @@ __global__ void __launch_bounds__(256, PT_ADJ_MIN_BLOCKS) adjoint_kernel(const _
       A, (long long)blockIdx.x * blockDim.x + threadIdx.x, crop_tile(A));
 }
 
+// Split PRB: the radiance pass as a forward kernel storing each sample's L, and
+// the replay-only adjoint reading it.
+template <int LAYOUT>
+__global__ void __launch_bounds__(256, PT_FWD_MIN_BLOCKS) radiance_kernel(const __grid_constant__ LaunchArgs A) {
+  megakernel<false, false, false, LAYOUT, PT_DISPATCH_SWITCH, FEAT_SAMPLE_L>(
+      A, (long long)blockIdx.x * blockDim.x + threadIdx.x, crop_tile(A));
+}
+template <int LAYOUT>
+__global__ void __launch_bounds__(256, PT_ADJ_MIN_BLOCKS) replay_kernel(const __grid_constant__ LaunchArgs A) {
+  megakernel<true, false, false, LAYOUT, PT_DISPATCH_SWITCH, FEAT_REPLAY>(
+      A, (long long)blockIdx.x * blockDim.x + threadIdx.x, crop_tile(A));
+}
+
 // The adjoint with every optional feature: environment-radiance (emitter)
 // gradients, the cache-terminated replay, warp-aggregated texel atomics.
 template <int LAYOUT>
@@ -328,6 +341,33 @@ extern "C" int pt_render_backward(pt_scene* s, const pt_render_desc* r, const pt
     // optional features: their own instantiation (switch dispatch)
     if (s->dev.layout == PT_BVH_WIDE) adjoint_full_kernel<PT_BVH_WIDE><<<gd, bd, 0, cs>>>(A);
     else adjoint_full_kernel<PT_BVH_BINARY><<<gd, bd, 0, cs>>>(A);
+    return cudaGetLastError() == cudaSuccess ? PT_OK : PT_ERR_CUDA;
+  }
+  if (r->prb_mode < PT_PRB_AUTO || r->prb_mode > PT_PRB_SPLIT) return PT_ERR_ARG;
+  if (r->prb_mode != PT_PRB_FUSED && !instrumented(r)) {
+    // per-sample radiance scratch owned by the scene
+    const size_t need = (size_t)sample_slots(A) * 3 * sizeof(float);
+    if (s->sample_L_bytes < need) {
+      if (s->d_sample_L) cudaFree(s->d_sample_L);
+      s->d_sample_L = nullptr;
+      s->sample_L_bytes = 0;
+      if (cudaMalloc(&s->d_sample_L, need) != cudaSuccess) {
+        cudaGetLastError();
+        return PT_ERR_OOM;
+      }
+      s->sample_L_bytes = need;
+    }
+    LaunchArgs F = A;
+    F.seed = A.seed_adj;
+    F.image = nullptr;
+    F.sample_L = A.sample_L = static_cast<float*>(s->d_sample_L);
+    if (s->dev.layout == PT_BVH_WIDE) {
+      radiance_kernel<PT_BVH_WIDE><<<gd, bd, 0, cs>>>(F);
+      replay_kernel<PT_BVH_WIDE><<<gd, bd, 0, cs>>>(A);
+    } else {
+      radiance_kernel<PT_BVH_BINARY><<<gd, bd, 0, cs>>>(F);
+      replay_kernel<PT_BVH_BINARY><<<gd, bd, 0, cs>>>(A);
+    }
     return cudaGetLastError() == cudaSuccess ? PT_OK : PT_ERR_CUDA;
   }
   const int v = (instrumented(r) ? 4 : 0) | (s->dev.layout == PT_BVH_WIDE ? 2 : 0) | (A.dispatch == PT_DISPATCH_MATCH ? 1 : 0);

@@ -68,6 +68,7 @@ void scene_free_all(pt_scene* s) {
   free_dev(s->d_env_cond_guide);
   free_dev(s->d_status);
   free_dev(s->d_wf);
+  free_dev(s->d_sample_L);
   std::free(s->h_vertices);
   std::free(s->h_uvs);
   std::free(s->h_tri_shape);

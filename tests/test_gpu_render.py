@@ -242,3 +242,38 @@ def test_counters_and_status(lib):
     assert c[1] >= c[0]                 # rays >= paths
     assert c[3] > 0 and c[4] > 0
     assert ds.status() == 0
+
+
+# ---------------------------------------------------------------- split PRB (separate radiance pass)
+@pytest.mark.parametrize("layout", [0, 1])
+def test_split_prb_matches_fused_and_oracle(lib, oracle_mod, layout):
+    """PT_PRB_SPLIT: a forward kernel stores each sample's radiance (adjoint seed),
+    a replay-only adjoint consumes it.  Same estimator as the fused kernel."""
+    from dataclasses import replace
+    from paper_2202_01284_gb300.render import DeviceScene
+    sc = S.cornell96(width=512, height=512)
+    crop = (192, 160, 128, 128)
+    st = _settings(sc, spp=16, max_depth=6, seed=21, crop=crop)
+    ref = _oracle_render(oracle_mod, sc, st)
+    tgt = sc.with_params(textures=[S.cornell96_target_texture(sc.textures[0])])
+    T = _oracle_render(oracle_mod, tgt, _settings(tgt, spp=16, max_depth=6, seed=23, crop=crop))
+    gi = _loss_grad_image(ref, T)
+    osc = oracle_mod.OracleScene(sc)
+    r = oracle_mod.render_in(sc.cameras[0], st.spp, st.max_depth, st.seed, crop=crop)
+    _, gt_ref, gr_ref = oracle_mod.grad_tape(osc, r, gi)
+    ds = DeviceScene(sc, layout=layout)
+    gi_t = torch.as_tensor(gi[None], dtype=torch.float32, device="cuda")
+    out = []
+    for mode in (lib.PT_PRB_FUSED, lib.PT_PRB_SPLIT):
+        gt = torch.zeros_like(ds.textures[0])
+        gr = torch.zeros_like(ds.roughness)
+        ds.backward(replace(st, prb_mode=mode), gi_t, g_textures=[gt], g_roughness=gr)
+        torch.cuda.synchronize()
+        assert ds.status() == 0
+        out.append((gt.cpu().numpy(), gr.cpu().numpy()))
+    (gt0, gr0), (gt1, gr1) = out
+    c_t, c_r = cosine(gt1[..., :3], gt_ref[0][..., :3]), cosine(gr1, gr_ref)
+    c_tf, c_rf = cosine(gt1, gt0), cosine(gr1, gr0)
+    print(f"split PRB vs oracle: tex {c_t:.7f} rough {c_r:.7f}; vs fused: tex {c_tf:.9f} rough {c_rf:.9f}")
+    assert c_r >= GRAD_COSINE and c_t >= 0.999
+    assert c_tf >= 0.99999 and c_rf >= 0.99999
