@@ -49,12 +49,14 @@ def up_to_date() -> bool:
     return all(os.path.getmtime(d) <= t for d in _deps())
 
 
-def build(force: bool = False, verbose: bool = False, ptxas_verbose: bool = False) -> str:
-    if not force and up_to_date():
+def build(force: bool = False, verbose: bool = False, ptxas_verbose: bool = False, defines=()) -> str:
+    """defines: extra preprocessor definitions ("NAME=value"), e.g. the register caps
+    PT_FWD_MIN_BLOCKS / PT_ADJ_MIN_BLOCKS / PT_REPLAY_MIN_BLOCKS for tuning."""
+    if not force and not defines and up_to_date():
         return LIB
     nvcc = _nvcc()
     os.makedirs(OBJDIR, exist_ok=True)
-    common = ["-O3", "-std=c++20", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
+    common = ["-O3", "-std=c++20", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC] + [f"-D{d}" for d in defines]
 
     def compile_one(src):
         obj = os.path.join(OBJDIR, os.path.basename(src) + ".o")

@@ -47,8 +47,11 @@ __global__ void __launch_bounds__(256, PT_FWD_MIN_BLOCKS) radiance_kernel(const 
   megakernel<false, false, false, LAYOUT, PT_DISPATCH_SWITCH, FEAT_SAMPLE_L>(
       A, (long long)blockIdx.x * blockDim.x + threadIdx.x, crop_tile(A));
 }
+#ifndef PT_REPLAY_MIN_BLOCKS
+#define PT_REPLAY_MIN_BLOCKS PT_ADJ_MIN_BLOCKS
+#endif
 template <int LAYOUT>
-__global__ void __launch_bounds__(256, PT_ADJ_MIN_BLOCKS) replay_kernel(const __grid_constant__ LaunchArgs A) {
+__global__ void __launch_bounds__(256, PT_REPLAY_MIN_BLOCKS) replay_kernel(const __grid_constant__ LaunchArgs A) {
   megakernel<true, false, false, LAYOUT, PT_DISPATCH_SWITCH, FEAT_REPLAY>(
       A, (long long)blockIdx.x * blockDim.x + threadIdx.x, crop_tile(A));
 }
