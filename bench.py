@@ -39,7 +39,9 @@ FLOPS_PER_TRI = 45      # Moller-Trumbore: 2 cross, 4 dot, 1 div, 4 mul, 3 sub (
 # DRAM bytes (read + write) per full-size launch of the production kernels, from one
 # one-pass ncu capture of this step (profiles/launches_spheres196k_1024px_64spp.md);
 # cleared whenever the kernels change until they are captured again.
-DRAM_TRAFFIC_PER_LAUNCH = {"wide": {"forward_kernel": 2_958_000_000 + 14_328_000_000,
+DRAM_TRAFFIC_PER_LAUNCH = {"wide": {"forward_kernel": 2_960_000_000 + 14_310_000_000,
+                                    "replay_kernel": 2_030_000_000 + 4_620_000_000,
+                                    "radiance_kernel": 4_030_000_000 + 15_990_000_000,
                                     "adjoint_kernel": 1_775_000_000 + 11_908_000_000,
                                     "jvp_kernel": 1_325_000_000 + 7_153_000_000}}
 
