@@ -28,8 +28,11 @@ __global__ void __launch_bounds__(256, PT_FWD_MIN_BLOCKS) forward_full_kernel(co
 
 // Forward mode (Sec. 4, forward-mode derivatives of the paper's AD layer): the
 // image and its derivative along a parameter direction in one pass.
+#ifndef PT_JVP_MIN_BLOCKS
+#define PT_JVP_MIN_BLOCKS PT_ADJ_MIN_BLOCKS
+#endif
 template <int LAYOUT>
-__global__ void __launch_bounds__(256, PT_ADJ_MIN_BLOCKS) jvp_kernel(const __grid_constant__ LaunchArgs A) {
+__global__ void __launch_bounds__(256, PT_JVP_MIN_BLOCKS) jvp_kernel(const __grid_constant__ LaunchArgs A) {
   megakernel<false, true, false, LAYOUT, PT_DISPATCH_SWITCH>(A, (long long)blockIdx.x * blockDim.x + threadIdx.x,
                                                              crop_tile(A));
 }
