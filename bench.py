@@ -870,7 +870,7 @@ def run_batch_experiment(args):
            "persistent_graph_ms": round(graph_ms, 3), "persistent_direct_ms": round(direct_ms, 3),
            "separate_ms": round(sep_ms, 3), "speedup": round(sep_ms / graph_ms, 3),
            "mrays_s_persistent": round(rays / graph_ms / 1e3, 1), "mrays_s_separate": round(rays / sep_ms / 1e3, 1),
-           "gpu_launches": {"persistent": 2, "separate": 2 * len(jobs), "graph_launches": 1},
+           "gpu_launches": {"persistent": 3, "separate": 3 * len(jobs), "graph_launches": 1},
            "autotune": {k: v for k, v in best.items() if k != "candidates"},
            "autotune_candidates": best["candidates"]}
     print(json.dumps(out), flush=True)

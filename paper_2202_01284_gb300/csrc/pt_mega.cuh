@@ -128,7 +128,9 @@ __device__ __forceinline__ void megakernel(const LaunchArgs& A, long long unit, 
   for (;;) {
     if (!has_path && valid && next_s < A.spp) {
       // one call site for both passes: the replay starts from identical code
-      path_start<INSTR>(A, P, ADJ ? A.seed_adj : A.seed, px.cam, px.px, px.py, next_s, px.pix, cnt);
+      // the split-PRB radiance pass traces the adjoint's samples
+      path_start<INSTR>(A, P, (ADJ || (FEAT & FEAT_SAMPLE_L)) ? A.seed_adj : A.seed, px.cam, px.px, px.py, next_s,
+                        px.pix, cnt);
       if constexpr (REPLAY) {
         const float* l = A.sample_L + 3 * P.slot;
         P.Lrem = f3(l[0], l[1], l[2]);
@@ -218,7 +220,7 @@ __device__ __forceinline__ void megakernel(const LaunchArgs& A, long long unit, 
         pix_sum_dot.z += __shfl_xor_sync(0xffffffffu, pix_sum_dot.z, off);
       }
     }
-    if (valid && lane_in_pix == 0 && A.image) {
+    if (valid && lane_in_pix == 0 && A.image && (FEAT & FEAT_SAMPLE_L) == 0) {
       const float inv = 1.0f / (float)A.spp;
       A.image[3 * px.pix] = pix_sum.x * inv;
       A.image[3 * px.pix + 1] = pix_sum.y * inv;

@@ -118,7 +118,7 @@ constexpr int kJobBytes = (int)((offsetof(LaunchArgs, cams) + sizeof(DevCamera) 
 // dLoss/dI = 2 (I - T) / (3 W H) straight from the image and the job's target.
 // Two kernels rather than one keep each at the register footprint of its
 // single-job counterpart (one kernel holding both megakernels spills).
-template <bool ADJ, int LAYOUT, bool EGRAD = false>
+template <bool ADJ, int LAYOUT, int FEAT = 0>
 __global__ void __launch_bounds__(256, ADJ ? PT_ADJ_MIN_BLOCKS : PT_FWD_MIN_BLOCKS)
     batch_kernel(const LaunchArgs* __restrict__ jobs, const BatchItem* __restrict__ items, int n_items, int tile,
                  unsigned* __restrict__ queue) {
@@ -143,7 +143,7 @@ __global__ void __launch_bounds__(256, ADJ ? PT_ADJ_MIN_BLOCKS : PT_FWD_MIN_BLOC
     }
     const Tile t{bi.x0, bi.y0, tile, tile, 1};
     const long long units = (long long)tile * tile * A.lanes_per_pixel;
-    for (long long b = 0; b < units; b += 32) megakernel<ADJ, false, false, LAYOUT, PT_DISPATCH_SWITCH, EGRAD ? FEAT_EGRAD : 0>(A, b + lane, t);
+    for (long long b = 0; b < units; b += 32) megakernel<ADJ, false, false, LAYOUT, PT_DISPATCH_SWITCH, FEAT>(A, b + lane, t);
   }
 }
 
@@ -364,7 +364,6 @@ extern "C" int pt_render_backward(pt_scene* s, const pt_render_desc* r, const pt
       s->sample_L_bytes = need;
     }
     LaunchArgs F = A;
-    F.seed = A.seed_adj;
     F.image = nullptr;
     F.sample_L = A.sample_L = static_cast<float*>(s->d_sample_L);
     if (s->dev.layout == PT_BVH_WIDE) {
@@ -426,7 +425,8 @@ extern "C" int pt_cache_train(pt_cache* c, pt_scene* s, const pt_render_desc* r,
 struct pt_batch {
   LaunchArgs* d_jobs = nullptr;
   BatchItem* d_items = nullptr;   // forward items, then adjoint items
-  unsigned* d_queue = nullptr;    // [2] work counters (forward, adjoint)
+  unsigned* d_queue = nullptr;    // [3] work counters (forward, radiance pass, replay)
+  float* d_sample_L = nullptr;    // split PRB: per-sample radiance of the jobs with a target
   int n_items = 0, n_adj_items = 0, tile = 4, block = 128, grid = 152, layout = PT_BVH_WIDE;
   bool egrad = false;             // some job wants environment-radiance gradients
 };
@@ -438,19 +438,33 @@ bool any_env_grads(const pt_job* jobs, int n_jobs) {
   return false;
 }
 
-// Forward then adjoint persistent kernels over the two item lists.
-void launch_batch(int layout, bool egrad, int grid, int block, size_t smem, const LaunchArgs* jobs,
-                  const BatchItem* items, int n_fwd, int n_adj, int tile, unsigned* queue, cudaStream_t cs) {
+// The persistent kernels over the item lists: forward; then, for the jobs with a
+// target, either the fused adjoint, or (split PRB) the radiance pass storing each
+// sample's radiance followed by the replay.
+template <int LAYOUT>
+void launch_batch_layout(bool egrad, bool split, int grid, int block, size_t smem, const LaunchArgs* jobs,
+                         const BatchItem* items, int n_fwd, int n_adj, int tile, unsigned* queue, cudaStream_t cs) {
   const BatchItem* adj = items + n_fwd;
-  if (layout == PT_BVH_WIDE) {
-    batch_kernel<false, PT_BVH_WIDE><<<grid, block, smem, cs>>>(jobs, items, n_fwd, tile, queue);
-    if (n_adj && egrad) batch_kernel<true, PT_BVH_WIDE, true><<<grid, block, smem, cs>>>(jobs, adj, n_adj, tile, queue + 1);
-    else if (n_adj) batch_kernel<true, PT_BVH_WIDE><<<grid, block, smem, cs>>>(jobs, adj, n_adj, tile, queue + 1);
+  batch_kernel<false, LAYOUT><<<grid, block, smem, cs>>>(jobs, items, n_fwd, tile, queue);
+  if (!n_adj) return;
+  if (split) {
+    batch_kernel<false, LAYOUT, FEAT_SAMPLE_L><<<grid, block, smem, cs>>>(jobs, adj, n_adj, tile, queue + 1);
+    if (egrad)
+      batch_kernel<true, LAYOUT, FEAT_REPLAY | FEAT_EGRAD><<<grid, block, smem, cs>>>(jobs, adj, n_adj, tile, queue + 2);
+    else
+      batch_kernel<true, LAYOUT, FEAT_REPLAY><<<grid, block, smem, cs>>>(jobs, adj, n_adj, tile, queue + 2);
+  } else if (egrad) {
+    batch_kernel<true, LAYOUT, FEAT_EGRAD><<<grid, block, smem, cs>>>(jobs, adj, n_adj, tile, queue + 1);
   } else {
-    batch_kernel<false, PT_BVH_BINARY><<<grid, block, smem, cs>>>(jobs, items, n_fwd, tile, queue);
-    if (n_adj && egrad) batch_kernel<true, PT_BVH_BINARY, true><<<grid, block, smem, cs>>>(jobs, adj, n_adj, tile, queue + 1);
-    else if (n_adj) batch_kernel<true, PT_BVH_BINARY><<<grid, block, smem, cs>>>(jobs, adj, n_adj, tile, queue + 1);
+    batch_kernel<true, LAYOUT><<<grid, block, smem, cs>>>(jobs, adj, n_adj, tile, queue + 1);
   }
+}
+void launch_batch(int layout, bool egrad, bool split, int grid, int block, size_t smem, const LaunchArgs* jobs,
+                  const BatchItem* items, int n_fwd, int n_adj, int tile, unsigned* queue, cudaStream_t cs) {
+  if (layout == PT_BVH_WIDE)
+    launch_batch_layout<PT_BVH_WIDE>(egrad, split, grid, block, smem, jobs, items, n_fwd, n_adj, tile, queue, cs);
+  else
+    launch_batch_layout<PT_BVH_BINARY>(egrad, split, grid, block, smem, jobs, items, n_fwd, n_adj, tile, queue, cs);
 }
 }  // namespace
 
@@ -531,9 +545,20 @@ extern "C" int pt_batch_create(const pt_job* jobs, int n_jobs, const pt_batch_op
   b->grid = sms * opts.ctas_per_sm;
   b->layout = layout;
   b->egrad = any_env_grads(jobs, n_jobs);
+  // split PRB: one radiance slot per sample of every job with a target
+  long long n_slots = 0;
+  std::vector<long long> slot0(n_jobs, -1);
+  for (int j = 0; j < n_jobs; ++j)
+    if (jobs[j].target) {
+      slot0[j] = n_slots;
+      n_slots += (long long)jobs[j].width * jobs[j].height * jobs[j].spp;
+    }
   bool ok = cudaMalloc(&b->d_jobs, sizeof(LaunchArgs) * n_jobs) == cudaSuccess &&
             cudaMalloc(&b->d_items, sizeof(BatchItem) * sorted.size()) == cudaSuccess &&
-            cudaMalloc(&b->d_queue, 2 * sizeof(unsigned)) == cudaSuccess;
+            cudaMalloc(&b->d_queue, 3 * sizeof(unsigned)) == cudaSuccess &&
+            (n_slots == 0 || cudaMalloc(&b->d_sample_L, (size_t)n_slots * 3 * sizeof(float)) == cudaSuccess);
+  for (int j = 0; j < n_jobs && ok; ++j)
+    if (slot0[j] >= 0) args[j].sample_L = b->d_sample_L + 3 * slot0[j];
   ok = ok && cudaMemcpy(b->d_jobs, args.data(), sizeof(LaunchArgs) * n_jobs, cudaMemcpyHostToDevice) == cudaSuccess &&
        cudaMemcpy(b->d_items, sorted.data(), sizeof(BatchItem) * sorted.size(), cudaMemcpyHostToDevice) == cudaSuccess;
   if (!ok) {
@@ -541,6 +566,7 @@ extern "C" int pt_batch_create(const pt_job* jobs, int n_jobs, const pt_batch_op
     if (b->d_jobs) cudaFree(b->d_jobs);
     if (b->d_items) cudaFree(b->d_items);
     if (b->d_queue) cudaFree(b->d_queue);
+    if (b->d_sample_L) cudaFree(b->d_sample_L);
     delete b;
     return PT_ERR_OOM;
   }
@@ -551,10 +577,10 @@ extern "C" int pt_batch_create(const pt_job* jobs, int n_jobs, const pt_batch_op
 extern "C" int pt_batch_run(pt_batch* b, void* stream) {
   if (!b) return PT_ERR_ARG;
   cudaStream_t cs = (cudaStream_t)stream;
-  if (cudaMemsetAsync(b->d_queue, 0, 2 * sizeof(unsigned), cs) != cudaSuccess) return PT_ERR_CUDA;
+  if (cudaMemsetAsync(b->d_queue, 0, 3 * sizeof(unsigned), cs) != cudaSuccess) return PT_ERR_CUDA;
   const size_t smem = (size_t)(b->block / 32) * kJobBytes;
-  launch_batch(b->layout, b->egrad, b->grid, b->block, smem, b->d_jobs, b->d_items, b->n_items, b->n_adj_items,
-               b->tile, b->d_queue, cs);
+  launch_batch(b->layout, b->egrad, b->d_sample_L != nullptr, b->grid, b->block, smem, b->d_jobs, b->d_items,
+               b->n_items, b->n_adj_items, b->tile, b->d_queue, cs);
   return cudaGetLastError() == cudaSuccess ? PT_OK : PT_ERR_CUDA;
 }
 
@@ -570,6 +596,7 @@ extern "C" void pt_batch_destroy(pt_batch* b) {
   cudaFree(b->d_jobs);
   cudaFree(b->d_items);
   cudaFree(b->d_queue);
+  cudaFree(b->d_sample_L);
   delete b;
 }
 
@@ -704,7 +731,7 @@ extern "C" int pt_render_batch_noalloc(const pt_job* jobs, int n_jobs, const pt_
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int grid = sms * opts.ctas_per_sm;
   const size_t smem = (size_t)(opts.block_size / 32) * kJobBytes;
-  launch_batch(layout, any_env_grads(jobs, n_jobs), grid, opts.block_size, smem, d_jobs, d_items, n_fwd, n_adj,
+  launch_batch(layout, any_env_grads(jobs, n_jobs), false, grid, opts.block_size, smem, d_jobs, d_items, n_fwd, n_adj,
                opts.tile, d_queue, cs);
   return cudaGetLastError() == cudaSuccess ? PT_OK : PT_ERR_CUDA;
 }
