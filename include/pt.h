@@ -101,7 +101,10 @@ typedef struct pt_cache pt_cache;
  * conditional CDFs over luminance x sin(theta)).  Synchronous.  *out receives
  * a handle owned by the caller (pt_scene_destroy).
  * Errors: PT_ERR_ARG (NULL pointers, n_tris <= 0, shape index out of range,
- * bad BSDF code, tex slot >= PT_MAX_TEX), PT_ERR_OOM, PT_ERR_CUDA. */
+ * bad BSDF code, tex slot >= PT_MAX_TEX, non-finite vertices / uvs / shape
+ * scalars, negative or non-finite emission or environment radiance, emitting
+ * shapes of zero total area), PT_ERR_OOM, PT_ERR_CUDA.  All checks run before any
+ * device call. */
 int pt_scene_create(const pt_scene_desc* desc, pt_scene** out);
 void pt_scene_destroy(pt_scene* scene);
 

@@ -86,6 +86,34 @@ extern "C" int pt_scene_create(const pt_scene_desc* d, pt_scene** out) {
     if (d->tri_shape[i] < 0 || d->tri_shape[i] >= d->n_shapes) return PT_ERR_ARG;
   for (int i = 0; i < 9 * d->n_tris; ++i)
     if (!std::isfinite(d->vertices[i])) return PT_ERR_ARG;
+  if (d->uvs)
+    for (int i = 0; i < 6 * d->n_tris; ++i)
+      if (!std::isfinite(d->uvs[i])) return PT_ERR_ARG;
+  for (int i = 0; i < d->n_shapes; ++i) {
+    const pt_shape& p = d->shapes[i];
+    for (int c = 0; c < 3; ++c)
+      if (!(p.emission[c] >= 0.0f) || !std::isfinite(p.emission[c]) || !std::isfinite(p.f0[c])) return PT_ERR_ARG;
+    if (!std::isfinite(p.alpha) || !std::isfinite(p.eta) || !std::isfinite(p.diffuse_weight)) return PT_ERR_ARG;
+  }
+  if (d->env_w > 0)
+    for (size_t i = 0; i < 4 * (size_t)d->env_w * d->env_h; ++i)
+      if (!(d->env[i] >= 0.0f) || !std::isfinite(d->env[i])) return PT_ERR_ARG;
+  {
+    // emitters must have some area: light sampling divides by the total
+    bool any_emitter = false;
+    double area = 0.0;
+    for (int t = 0; t < d->n_tris; ++t) {
+      const pt_shape& p = d->shapes[d->tri_shape[t]];
+      if (!(p.emission[0] > 0 || p.emission[1] > 0 || p.emission[2] > 0)) continue;
+      any_emitter = true;
+      const float* v = d->vertices + 9 * (size_t)t;
+      const double e1[3] = {(double)v[3] - v[0], (double)v[4] - v[1], (double)v[5] - v[2]};
+      const double e2[3] = {(double)v[6] - v[0], (double)v[7] - v[1], (double)v[8] - v[2]};
+      const double c[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
+      area += std::sqrt(c[0] * c[0] + c[1] * c[1] + c[2] * c[2]);
+    }
+    if (any_emitter && !(area > 0.0)) return PT_ERR_ARG;
+  }
   pt_scene* s = new (std::nothrow) pt_scene();
   if (!s) return PT_ERR_OOM;
   s->n_tris = d->n_tris;
