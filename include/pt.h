@@ -350,6 +350,14 @@ int pt_cache_set_engine(pt_cache* cache, int engine);
  * PT_OK, or PT_ERR_TIMEOUT if a bounded wait on the tensor core gave up (the
  * outputs of that call are then incomplete). */
 int pt_cache_status(pt_cache* cache, void* stream, int* status);
+/* Failure injection for the bounded waits of the tcgen05 kernels (no counterpart in
+ * the paper): each MMA step polls its completion barrier at most `limit` times
+ * (default PT_CACHE_WAIT_LIMIT_DEFAULT) before the kernel gives up, records
+ * PT_ERR_TIMEOUT in the cache's status word (pt_cache_status) and returns after
+ * letting the MMA in flight finish (that last wait always uses the default).
+ * limit = 0 makes the timeout path run deterministically. */
+#define PT_CACHE_WAIT_LIMIT_DEFAULT (1u << 22)
+int pt_cache_set_wait_limit(pt_cache* cache, uint32_t limit);
 
 /* Reverse mode with checkpoints (Sec. 5: differentiating a standard path tracer
  * whose loop keeps one checkpoint per scattering event, against PRB).

@@ -152,6 +152,7 @@ SIGNATURES = {
     "pt_cache_destroy": ([C.c_void_p], None),
     "pt_cache_set_engine": ([C.c_void_p, C.c_int], C.c_int),
     "pt_cache_status": ([C.c_void_p, C.c_void_p, C.POINTER(C.c_int)], C.c_int),
+    "pt_cache_set_wait_limit": ([C.c_void_p, C.c_uint32], C.c_int),
     "pt_cache_get_weights": ([C.c_void_p, C.c_void_p], C.c_int),
     "pt_cache_set_weights": ([C.c_void_p, C.c_void_p], C.c_int),
     "pt_cache_query": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p], C.c_int),
@@ -429,6 +430,13 @@ PT_CACHE_MMA_SYNC = 1
 
 def pt_cache_set_engine(handle: int, engine: int) -> None:
     check("pt_cache_set_engine", load().pt_cache_set_engine(handle, engine))
+
+
+PT_CACHE_WAIT_LIMIT_DEFAULT = 1 << 22
+
+
+def pt_cache_set_wait_limit(handle: int, limit: int) -> None:
+    check("pt_cache_set_wait_limit", load().pt_cache_set_wait_limit(handle, limit))
 
 
 def pt_cache_status(handle: int, stream: int = 0) -> int:

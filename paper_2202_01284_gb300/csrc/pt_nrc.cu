@@ -417,6 +417,7 @@ struct pt_cache {
   unsigned* r_count = nullptr;  // [2] records written, paths written
   int* status = nullptr;        // [1] device-side error of the tensor-core kernels
   int engine = PT_CACHE_TCGEN05;
+  unsigned wait_limit = PT_CACHE_WAIT_LIMIT_DEFAULT;  // per-step bounded-wait polls of the tensor-core kernels
   int step = 0;
 };
 
@@ -547,7 +548,7 @@ extern "C" int pt_cache_set_weights(pt_cache* c, const float* host_in) {
 namespace ptgb {
 int cache_infer(pt_cache* c, const float* raw, float* rgb, long long n, cudaStream_t st) {
   if (n <= 0) return PT_OK;
-  if (c->engine == PT_CACHE_TCGEN05) return cache_infer_tc(raw, rgb, n, c->box, c->Wb, c->status, st);
+  if (c->engine == PT_CACHE_TCGEN05) return cache_infer_tc(raw, rgb, n, c->box, c->Wb, c->status, c->wait_limit, st);
   const long long tiles = (n + 15) / 16;
   long long grid = (tiles + 3) / 4;
   if (grid > 152 * 8) grid = 152 * 8;
@@ -568,7 +569,7 @@ int cache_optimise(pt_cache* c, const float* raw, const float* target, long long
     cudaMemsetAsync(c->loss, 0, 4, st);
     if (c->engine == PT_CACHE_TCGEN05) {
       const int rc = cache_train_fb_tc(raw + off * NRC_RAW, target + off * 3, nb, c->box, c->Wb, c->X, c->dZ, c->loss,
-                                       c->status, st);
+                                       c->status, c->wait_limit, st);
       if (rc != PT_OK) return rc;
     } else {
       nrc_train_fb_kernel<<<(unsigned)grid, 128, kTrainSmem, st>>>(raw + off * NRC_RAW, target + off * 3, nb, c->box,
@@ -576,7 +577,7 @@ int cache_optimise(pt_cache* c, const float* raw, const float* target, long long
     }
     const long long chunk = 512;
     if (c->engine == PT_CACHE_TCGEN05) {
-      const int rc = cache_wgrad_tc(c->X, c->dZ, nb, chunk, c->dW, c->status, st);
+      const int rc = cache_wgrad_tc(c->X, c->dZ, nb, chunk, c->dW, c->status, c->wait_limit, st);
       if (rc != PT_OK) return rc;
     } else {
       dim3 g2((unsigned)((nb + chunk - 1) / chunk), NRC_HIDDEN + 1);
@@ -618,6 +619,12 @@ extern "C" int pt_cache_query(pt_cache* c, const float* raw, float* rgb, int n, 
 extern "C" int pt_cache_set_engine(pt_cache* c, int engine) {
   if (!c || (engine != PT_CACHE_TCGEN05 && engine != PT_CACHE_MMA_SYNC)) return PT_ERR_ARG;
   c->engine = engine;
+  return PT_OK;
+}
+
+extern "C" int pt_cache_set_wait_limit(pt_cache* c, uint32_t limit) {
+  if (!c) return PT_ERR_ARG;
+  c->wait_limit = limit;
   return PT_OK;
 }
 

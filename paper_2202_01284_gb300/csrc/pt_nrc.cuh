@@ -23,15 +23,16 @@ struct NrcBox {
 // Inference on the tcgen05 tensor cores (pt_nrc_tc.cu); `status` receives
 // PT_ERR_TIMEOUT if a bounded wait on the tensor core gave up.
 int cache_infer_tc(const float* raw, float* rgb, long long n, const NrcBox& box, const __nv_bfloat16* Wb, int* status,
-                   cudaStream_t st);
+                   unsigned wait_limit, cudaStream_t st);
 // Training forward + backward deltas on tcgen05 (pt_nrc_tc.cu): writes X[6][n][64],
 // dZ[6][n][64] and adds the batch's loss, as nrc_train_fb_kernel.
 int cache_train_fb_tc(const float* raw, const float* target, long long n, const NrcBox& box, const __nv_bfloat16* Wb,
-                      __nv_bfloat16* X, __nv_bfloat16* dZ, float* loss, int* status, cudaStream_t st);
+                      __nv_bfloat16* X, __nv_bfloat16* dZ, float* loss, int* status, unsigned wait_limit,
+                      cudaStream_t st);
 // Weight gradients on tcgen05 (pt_nrc_tc.cu): dW_l += dZ_l^T X_l, split-K over
 // blocks of `chunk` records, as nrc_wgrad_kernel.
 int cache_wgrad_tc(const __nv_bfloat16* X, const __nv_bfloat16* dZ, long long n, long long chunk, float* dW,
-                   int* status, cudaStream_t st);
+                   int* status, unsigned wait_limit, cudaStream_t st);
 
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
   __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);

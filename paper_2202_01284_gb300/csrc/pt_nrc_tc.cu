@@ -99,7 +99,11 @@ constexpr uint32_t kSmW = 0, kSmH = 5 * 8192, kSmX = kSmH + 2048;
 constexpr uint32_t kSmBar = kSmX + kGroups * 16384, kSmSlot = kSmBar + 8 * kGroups;
 constexpr uint32_t kTcSmem = kSmSlot + 8 + 1024;  // + alignment slack
 constexpr uint32_t kTmemCols = 64 * kGroups;      // 512: the whole tensor memory of the SM
-constexpr unsigned kWaitLimit = 1u << 22;
+// Bounded waits: per MMA step `limit` polls (the cache's wait limit, by default
+// kWaitLimit; a smaller one is a failure-injection hook), and always kWaitLimit
+// for the final wait (on the parity of the wait that gave up) that lets an MMA in
+// flight finish before TMEM is released.
+constexpr unsigned kWaitLimit = PT_CACHE_WAIT_LIMIT_DEFAULT;
 
 // Barrier over the 128 threads of group g (named barrier 1 + g), AND of `pred`.
 __device__ __forceinline__ bool group_sync_and(int g, bool pred) {
@@ -143,7 +147,7 @@ __device__ __forceinline__ void encode_row(const float* rr, const NrcBox& box, f
 
 __global__ void __launch_bounds__(128 * kGroups, 1)
     nrc_infer_tc_kernel(const float* __restrict__ raw, long long n, NrcBox box, const __nv_bfloat16* __restrict__ W,
-                        float* __restrict__ out, int* __restrict__ status) {
+                        float* __restrict__ out, int* __restrict__ status, unsigned limit) {
   extern __shared__ unsigned char tc_smem_raw[];
   // 1024-byte aligned base for the operand tiles
   unsigned char* sm = tc_smem_raw + ((1024u - (smem_addr(tc_smem_raw) & 1023u)) & 1023u);
@@ -178,7 +182,7 @@ __global__ void __launch_bounds__(128 * kGroups, 1)
   const uint32_t tmem = *slot + 64u * g;  // this group's 64 columns
   const uint32_t x_s = smem_addr(X), w_s = smem_addr(sm + kSmW), h_s = smem_addr(sm + kSmH);
   const uint32_t t_lane = tmem + ((uint32_t)((warp & 3) * 32) << 16);  // this warp's 32 TMEM lanes
-  uint32_t phase = 0;
+  uint32_t phase = 0, last = 0;  // last: parity of the latest wait
   bool ok = true;
   const long long n_tiles = (n + 127) / 128;
   for (long long tile = (long long)blockIdx.x * kGroups + g; tile < n_tiles && ok;
@@ -216,13 +220,15 @@ __global__ void __launch_bounds__(128 * kGroups, 1)
                     s > 0 ? 1u : 0u);
         umma_commit(bar);
       }
-      // each thread waits for the commit itself; the group agrees on the outcome at
-      // the end of the layer (a thread whose wait gave up reads an unfinished
-      // accumulator: wrong values, reported through `status`, no stray access)
-      const bool done = mbar_wait(bar, phase, kWaitLimit);
+      // each thread waits for the commit itself (the warp takes the AND, so that the
+      // warp-collective TMEM loads below run in all of its lanes or in none); the
+      // group agrees on the outcome at the end of the layer
+      const bool done = __all_sync(0xffffffffu, mbar_wait(bar, last = phase, limit));
       phase ^= 1u;
       tc_fence_after();
-      if (!head) {
+      if (!done) {
+        // gave up: no TMEM read of an unfinished accumulator, outputs not written
+      } else if (!head) {
         // ReLU + BF16 of this thread's row -> the next operand tile
 #pragma unroll
         for (int c16 = 0; c16 < 4; ++c16) {
@@ -256,7 +262,7 @@ __global__ void __launch_bounds__(128 * kGroups, 1)
   if (!ok) {
     if (r == 0) atomicCAS(status, 0, PT_ERR_TIMEOUT);
     // let an MMA still in flight finish before the tensor memory is released
-    mbar_wait(bar, phase, kWaitLimit);
+    mbar_wait(bar, last, kWaitLimit);
   }
   tc_fence_before();
   __syncthreads();
@@ -312,7 +318,8 @@ __device__ __forceinline__ void put_chunk(unsigned char* tile, int row, int k8, 
 __global__ void __launch_bounds__(128 * kTrGroups, 1)
     nrc_train_tc_kernel(const float* __restrict__ raw, const float* __restrict__ target, long long n, NrcBox box,
                         const __nv_bfloat16* __restrict__ W, __nv_bfloat16* __restrict__ X,
-                        __nv_bfloat16* __restrict__ dZ, float* __restrict__ loss, int* __restrict__ status) {
+                        __nv_bfloat16* __restrict__ dZ, float* __restrict__ loss, int* __restrict__ status,
+                        unsigned limit) {
   extern __shared__ unsigned char tc_smem_raw[];
   unsigned char* sm = tc_smem_raw + ((1024u - (smem_addr(tc_smem_raw) & 1023u)) & 1023u);
   uint32_t* slot = reinterpret_cast<uint32_t*>(sm + kTrSlot);
@@ -356,12 +363,13 @@ __global__ void __launch_bounds__(128 * kTrGroups, 1)
   const long long plane = n * NRC_W;
   const float inv_n = 1.0f / (float)n;
   float loss_acc = 0.0f;
-  uint32_t phase = 0;
+  uint32_t phase = 0, last = 0;  // last: parity of the latest wait
   bool ok = true;
   // one MMA step of the group: issue (thread 0 of the group), wait, agree
   auto step = [&](auto&& issue) -> bool {
     if (r == 0) issue();
-    const bool done = mbar_wait(bar, phase, kWaitLimit);
+    // warp-uniform, so that the warp-collective TMEM loads run in all lanes or none
+    const bool done = __all_sync(0xffffffffu, mbar_wait(bar, last = phase, limit));
     phase ^= 1u;
     tc_fence_after();
     return done;
@@ -394,7 +402,7 @@ __global__ void __launch_bounds__(128 * kTrGroups, 1)
     for (int l = 0; l < NRC_HIDDEN && ok; ++l) {
       const bool done = step([&] { issue_k64(tmem, x_s, w_s + (uint32_t)l * 8192u, id64, bar); });
 #pragma unroll
-      for (int c16 = 0; c16 < 4; ++c16) {
+      for (int c16 = 0; c16 < 4 && done; ++c16) {
         float v[16];
         tmem_ld16(t_lane + 16u * c16, v);
 #pragma unroll
@@ -415,9 +423,9 @@ __global__ void __launch_bounds__(128 * kTrGroups, 1)
     {
       const bool done = step([&] { issue_k64(tmem, x_s, h_s, id16, bar); });
       float y[16];
-      tmem_ld16(t_lane, y);
+      if (done) tmem_ld16(t_lane, y);
       float dy[3] = {0.f, 0.f, 0.f};
-      if (live) {
+      if (live && done) {
 #pragma unroll
         for (int c = 0; c < NRC_OUT; ++c) {
           const float tv = target[row * 3 + c];
@@ -451,7 +459,7 @@ __global__ void __launch_bounds__(128 * kTrGroups, 1)
       // dZ_l = dX_{l+1} * [X_{l+1} > 0] (X_{l+1} as written by this thread above)
       const uint4* xg = reinterpret_cast<const uint4*>(X + (l + 1) * plane + row * NRC_W);
 #pragma unroll
-      for (int c16 = 0; c16 < 4; ++c16) {
+      for (int c16 = 0; c16 < 4 && ok; ++c16) {
         float v[16];
         tmem_ld16(t_lane + 16u * c16, v);
 #pragma unroll
@@ -480,7 +488,7 @@ __global__ void __launch_bounds__(128 * kTrGroups, 1)
   }
   if (!ok) {
     if (r == 0) atomicCAS(status, 0, PT_ERR_TIMEOUT);
-    mbar_wait(bar, phase, kWaitLimit);
+    mbar_wait(bar, last, kWaitLimit);
   }
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) loss_acc += __shfl_xor_sync(0xffffffffu, loss_acc, off);
@@ -505,7 +513,7 @@ constexpr uint32_t kWgSmem = 40 * 1024;  // > what is used: at most 5 blocks (32
 __global__ void __launch_bounds__(128) nrc_wgrad_tc_kernel(const __nv_bfloat16* __restrict__ X,
                                                            const __nv_bfloat16* __restrict__ dZ, long long n,
                                                            long long chunk, float* __restrict__ dW,
-                                                           int* __restrict__ status) {
+                                                           int* __restrict__ status, unsigned limit) {
   extern __shared__ unsigned char tc_smem_raw[];
   unsigned char* sm = tc_smem_raw + ((1024u - (smem_addr(tc_smem_raw) & 1023u)) & 1023u);
   uint64_t* bar = reinterpret_cast<uint64_t*>(sm + kWgBar);
@@ -530,7 +538,7 @@ __global__ void __launch_bounds__(128) nrc_wgrad_tc_kernel(const __nv_bfloat16* 
   tc_fence_after();
   const uint32_t tmem = *slot;
   const uint32_t a_s = smem_addr(sm + kWgA), b_s = smem_addr(sm + kWgB);
-  uint32_t phase = 0;
+  uint32_t phase = 0, last = 0;  // last: parity of the latest wait
   bool ok = true, any = false;
   for (long long b0 = b_begin; b0 < b_end && ok; b0 += 64) {
     // record rb = tid / 2 of the step, half h = tid % 2 of its 64 columns
@@ -562,7 +570,7 @@ __global__ void __launch_bounds__(128) nrc_wgrad_tc_kernel(const __nv_bfloat16* 
       umma_commit(bar);
     }
     any = true;
-    const bool done = mbar_wait(bar, phase, kWaitLimit);
+    const bool done = mbar_wait(bar, last = phase, limit);
     phase ^= 1u;
     tc_fence_after();
     tc_fence_before();
@@ -570,7 +578,7 @@ __global__ void __launch_bounds__(128) nrc_wgrad_tc_kernel(const __nv_bfloat16* 
   }
   if (!ok) {
     if (tid == 0) atomicCAS(status, 0, PT_ERR_TIMEOUT);
-    mbar_wait(bar, phase, kWaitLimit);
+    mbar_wait(bar, last, kWaitLimit);
   } else if (any && warp < 2) {
     // rows o = 32 warp + lane of D (lanes 0..63): add to dW_l
     float* dWl = dW + (size_t)l * NRC_W * NRC_W;
@@ -597,7 +605,7 @@ __global__ void __launch_bounds__(128) nrc_wgrad_tc_kernel(const __nv_bfloat16* 
 }  // namespace
 
 int cache_infer_tc(const float* raw, float* rgb, long long n, const NrcBox& box, const __nv_bfloat16* Wb, int* status,
-                   cudaStream_t st) {
+                   unsigned wait_limit, cudaStream_t st) {
   static int attr = 0;
   if (!attr) {
     if (cudaFuncSetAttribute(nrc_infer_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem) !=
@@ -612,7 +620,8 @@ int cache_infer_tc(const float* raw, float* rgb, long long n, const NrcBox& box,
   long long grid = (tiles + kGroups - 1) / kGroups;  // one CTA per SM at most (all of its TMEM)
   if (grid > sms) grid = sms;
   if (grid < 1) grid = 1;
-  nrc_infer_tc_kernel<<<(unsigned)grid, 128 * kGroups, kTcSmem, st>>>(raw, n, box, Wb, rgb, status);
+  nrc_infer_tc_kernel<<<(unsigned)grid, 128 * kGroups, kTcSmem, st>>>(raw, n, box, Wb, rgb, status,
+                                                                      wait_limit);
   return cudaGetLastError() == cudaSuccess ? PT_OK : PT_ERR_CUDA;
 }
 
@@ -620,7 +629,8 @@ int cache_infer_tc(const float* raw, float* rgb, long long n, const NrcBox& box,
 
 namespace ptgb {
 int cache_train_fb_tc(const float* raw, const float* target, long long n, const NrcBox& box, const __nv_bfloat16* Wb,
-                      __nv_bfloat16* X, __nv_bfloat16* dZ, float* loss, int* status, cudaStream_t st) {
+                      __nv_bfloat16* X, __nv_bfloat16* dZ, float* loss, int* status, unsigned wait_limit,
+                      cudaStream_t st) {
   static int attr = 0;
   if (!attr) {
     if (cudaFuncSetAttribute(nrc_train_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTrSmem) !=
@@ -635,14 +645,15 @@ int cache_train_fb_tc(const float* raw, const float* target, long long n, const 
   long long grid = (tiles + kTrGroups - 1) / kTrGroups;
   if (grid > sms) grid = sms;
   if (grid < 1) grid = 1;
-  nrc_train_tc_kernel<<<(unsigned)grid, 128 * kTrGroups, kTrSmem, st>>>(raw, target, n, box, Wb, X, dZ, loss, status);
+  nrc_train_tc_kernel<<<(unsigned)grid, 128 * kTrGroups, kTrSmem, st>>>(raw, target, n, box, Wb, X, dZ, loss, status,
+                                                                        wait_limit);
   return cudaGetLastError() == cudaSuccess ? PT_OK : PT_ERR_CUDA;
 }
 }  // namespace ptgb
 
 namespace ptgb {
 int cache_wgrad_tc(const __nv_bfloat16* X, const __nv_bfloat16* dZ, long long n, long long chunk, float* dW,
-                   int* status, cudaStream_t st) {
+                   int* status, unsigned wait_limit, cudaStream_t st) {
   static int attr = 0;
   if (!attr) {
     if (cudaFuncSetAttribute(nrc_wgrad_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWgSmem) !=
@@ -651,7 +662,7 @@ int cache_wgrad_tc(const __nv_bfloat16* X, const __nv_bfloat16* dZ, long long n,
     attr = 1;
   }
   const dim3 grid((unsigned)((n + chunk - 1) / chunk), NRC_HIDDEN + 1);
-  nrc_wgrad_tc_kernel<<<grid, 128, kWgSmem, st>>>(X, dZ, n, chunk, dW, status);
+  nrc_wgrad_tc_kernel<<<grid, 128, kWgSmem, st>>>(X, dZ, n, chunk, dW, status, wait_limit);
   return cudaGetLastError() == cudaSuccess ? PT_OK : PT_ERR_CUDA;
 }
 }  // namespace ptgb

@@ -159,3 +159,36 @@ def test_training_engines_agree(abi):
     print(f"loss tcgen05 {l_tc:.7f} mma.sync {l_mma:.7f}; update cosine {c:.9f}")
     assert abs(l_tc - l_mma) <= 1e-5 * abs(l_mma)
     assert c > 0.99999
+
+
+def test_bounded_wait_timeout_is_reported(abi, oracle_mod):
+    """Failure injection without a GPU fault: with a wait limit of 0 polls every
+    tcgen05 kernel gives up on its first MMA step, reports PT_ERR_TIMEOUT through
+    the status word, lets the MMA in flight finish and frees its tensor memory; the
+    next calls with the default limit are correct (the context is intact)."""
+    n = 1000
+    raw, tgt = S.random_cache_records(n, 31)
+    W = S.mlp_init_weights(32)
+    h = abi.pt_cache_create(*BOX, batch=1024, init_weights=W)
+    try:
+        d_raw = torch.as_tensor(raw, device="cuda")
+        d_t = torch.as_tensor(tgt, device="cuda")
+        abi.pt_cache_set_wait_limit(h, 0)
+        out = torch.full((n, 3), float("nan"), device="cuda")
+        abi.pt_cache_query(h, d_raw, out, n)
+        assert abi.pt_cache_status(h) == abi.PT_ERR_TIMEOUT
+        assert torch.isnan(out).all()  # nothing written past the failed step
+        abi.pt_cache_train_records(h, d_raw, d_t, n, 1)
+        assert abi.pt_cache_status(h) == abi.PT_ERR_TIMEOUT
+        # back to the default: correct results, status clear
+        abi.pt_cache_set_wait_limit(h, abi.PT_CACHE_WAIT_LIMIT_DEFAULT)
+        abi.pt_cache_set_weights(h, W)
+        out = torch.full((n, 3), float("nan"), device="cuda")
+        abi.pt_cache_query(h, d_raw, out, n)
+        assert abi.pt_cache_status(h) == abi.PT_OK
+        got = out.cpu().numpy().astype(np.float64)
+    finally:
+        abi.pt_cache_destroy(h)
+    ref = oracle_mod.mlp_forward(W.astype(np.float64), oracle_mod.nrc_encode(raw, *BOX))
+    err = _rel_err(got, ref)
+    assert np.median(err) < 2e-3
