@@ -350,6 +350,14 @@ int pt_cache_set_engine(pt_cache* cache, int engine);
  * PT_OK, or PT_ERR_TIMEOUT if a bounded wait on the tensor core gave up (the
  * outputs of that call are then incomplete). */
 int pt_cache_status(pt_cache* cache, void* stream, int* status);
+/* Checkpoint / resume of cache training (no counterpart in the paper): the FP32
+ * master weights, Adam's first and second moments (each PT_CACHE_N_PARAMS floats,
+ * host memory) and the Adam step count.  set_state restores all of them (the BF16
+ * weights are re-derived), so training continues exactly as if uninterrupted.
+ * Both synchronise the device. */
+int pt_cache_get_state(pt_cache* cache, float* weights, float* m, float* v, int32_t* step);
+int pt_cache_set_state(pt_cache* cache, const float* weights, const float* m, const float* v, int32_t step);
+
 /* Failure injection for the bounded waits of the tcgen05 kernels (no counterpart in
  * the paper): each MMA step polls its completion barrier at most `limit` times
  * (default PT_CACHE_WAIT_LIMIT_DEFAULT) before the kernel gives up, records

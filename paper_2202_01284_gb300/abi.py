@@ -153,6 +153,8 @@ SIGNATURES = {
     "pt_cache_set_engine": ([C.c_void_p, C.c_int], C.c_int),
     "pt_cache_status": ([C.c_void_p, C.c_void_p, C.POINTER(C.c_int)], C.c_int),
     "pt_cache_set_wait_limit": ([C.c_void_p, C.c_uint32], C.c_int),
+    "pt_cache_get_state": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_int32)], C.c_int),
+    "pt_cache_set_state": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32], C.c_int),
     "pt_cache_get_weights": ([C.c_void_p, C.c_void_p], C.c_int),
     "pt_cache_set_weights": ([C.c_void_p, C.c_void_p], C.c_int),
     "pt_cache_query": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p], C.c_int),
@@ -433,6 +435,21 @@ def pt_cache_set_engine(handle: int, engine: int) -> None:
 
 
 PT_CACHE_WAIT_LIMIT_DEFAULT = 1 << 22
+
+
+def pt_cache_get_state(handle: int):
+    """(weights, adam_m, adam_v, step): float32 arrays of PT_CACHE_N_PARAMS and the step."""
+    w, m, v = (np.zeros(PT_CACHE_N_PARAMS, np.float32) for _ in range(3))
+    step = C.c_int32(0)
+    check("pt_cache_get_state", load().pt_cache_get_state(handle, w.ctypes.data, m.ctypes.data, v.ctypes.data,
+                                                          C.byref(step)))
+    return w, m, v, step.value
+
+
+def pt_cache_set_state(handle: int, w, m, v, step: int) -> None:
+    arrs = [np.ascontiguousarray(x, np.float32) for x in (w, m, v)]
+    assert all(a.size == PT_CACHE_N_PARAMS for a in arrs)
+    check("pt_cache_set_state", load().pt_cache_set_state(handle, *(a.ctypes.data for a in arrs), int(step)))
 
 
 def pt_cache_set_wait_limit(handle: int, limit: int) -> None:

@@ -622,6 +622,30 @@ extern "C" int pt_cache_set_engine(pt_cache* c, int engine) {
   return PT_OK;
 }
 
+extern "C" int pt_cache_get_state(pt_cache* c, float* w, float* m, float* v, int32_t* step) {
+  if (!c || !w || !m || !v || !step) return PT_ERR_ARG;
+  if (cudaDeviceSynchronize() != cudaSuccess) return PT_ERR_CUDA;
+  const bool ok = cudaMemcpy(w, c->W32, NRC_PARAMS * 4, cudaMemcpyDeviceToHost) == cudaSuccess &&
+                  cudaMemcpy(m, c->m, NRC_PARAMS * 4, cudaMemcpyDeviceToHost) == cudaSuccess &&
+                  cudaMemcpy(v, c->v, NRC_PARAMS * 4, cudaMemcpyDeviceToHost) == cudaSuccess;
+  if (!ok) return PT_ERR_CUDA;
+  *step = c->step;
+  return PT_OK;
+}
+
+extern "C" int pt_cache_set_state(pt_cache* c, const float* w, const float* m, const float* v, int32_t step) {
+  if (!c || !w || !m || !v || step < 0) return PT_ERR_ARG;
+  if (cudaDeviceSynchronize() != cudaSuccess) return PT_ERR_CUDA;
+  const bool ok = cudaMemcpy(c->W32, w, NRC_PARAMS * 4, cudaMemcpyHostToDevice) == cudaSuccess &&
+                  cudaMemcpy(c->m, m, NRC_PARAMS * 4, cudaMemcpyHostToDevice) == cudaSuccess &&
+                  cudaMemcpy(c->v, v, NRC_PARAMS * 4, cudaMemcpyHostToDevice) == cudaSuccess &&
+                  cudaMemset(c->dW, 0, NRC_PARAMS * 4) == cudaSuccess;
+  if (!ok) return PT_ERR_CUDA;
+  c->step = step;
+  nrc_to_bf16_kernel<<<(NRC_PARAMS + 255) / 256, 256>>>(c->W32, c->Wb);
+  return cudaDeviceSynchronize() == cudaSuccess ? PT_OK : PT_ERR_CUDA;
+}
+
 extern "C" int pt_cache_set_wait_limit(pt_cache* c, uint32_t limit) {
   if (!c) return PT_ERR_ARG;
   c->wait_limit = limit;

@@ -311,6 +311,27 @@ class RadianceCache:
     def read_records(self, cap):
         return abi.pt_cache_read_records(self.handle, cap)
 
+    # ---- checkpoint / resume of training: weights, Adam moments and step in one file
+    _MAGIC = b"PTGBNRC1"
+
+    def save(self, path):
+        w, m, v, step = abi.pt_cache_get_state(self.handle)
+        with open(path, "wb") as f:
+            f.write(self._MAGIC)
+            f.write(np.array([abi.PT_CACHE_N_PARAMS, step], np.int64).tobytes())
+            for a in (w, m, v):
+                f.write(a.astype("<f4").tobytes())
+
+    def load(self, path):
+        with open(path, "rb") as f:
+            if f.read(8) != self._MAGIC:
+                raise ValueError(f"{path}: not a radiance-cache checkpoint")
+            n, step = np.frombuffer(f.read(16), np.int64)
+            if n != abi.PT_CACHE_N_PARAMS:
+                raise ValueError(f"{path}: {n} parameters, expected {abi.PT_CACHE_N_PARAMS}")
+            w, m, v = (np.frombuffer(f.read(4 * n), "<f4").astype(np.float32) for _ in range(3))
+        abi.pt_cache_set_state(self.handle, w, m, v, int(step))
+
     def close(self):
         if getattr(self, "handle", None):
             abi.pt_cache_destroy(self.handle)

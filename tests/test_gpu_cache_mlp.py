@@ -192,3 +192,35 @@ def test_bounded_wait_timeout_is_reported(abi, oracle_mod):
     ref = oracle_mod.mlp_forward(W.astype(np.float64), oracle_mod.nrc_encode(raw, *BOX))
     err = _rel_err(got, ref)
     assert np.median(err) < 2e-3
+
+
+def test_training_checkpoint_resume(abi, tmp_path):
+    """Save after 3 Adam steps, reload into a fresh cache, 3 more steps: the same as
+    6 uninterrupted steps (weights, moments and the step count are restored; the
+    split-K gradient sums are atomics, so equal up to FP32 summation order)."""
+    from paper_2202_01284_gb300.render import RadianceCache
+    n = 2048
+    raw, tgt = S.random_cache_records(n, 41)
+    W0 = S.mlp_init_weights(42)
+    d_raw, d_t = torch.as_tensor(raw, device="cuda"), torch.as_tensor(tgt, device="cuda")
+
+    def steps(c, k):
+        for _ in range(k):
+            c.train_records(d_raw, d_t, steps=1)
+        torch.cuda.synchronize()
+    a = RadianceCache(*BOX, batch=n, lr=5e-3, init_weights=W0)
+    steps(a, 6)
+    want = a.weights()
+    a.close()
+    b = RadianceCache(*BOX, batch=n, lr=5e-3, init_weights=W0)
+    steps(b, 3)
+    b.save(tmp_path / "cache.bin")
+    b.close()
+    c = RadianceCache(*BOX, batch=n, lr=5e-3, init_weights=S.mlp_init_weights(7))
+    c.load(tmp_path / "cache.bin")
+    assert abi.pt_cache_get_state(c.handle)[3] == 3
+    steps(c, 3)
+    got = c.weights()
+    assert abi.pt_cache_get_state(c.handle)[3] == 6
+    c.close()
+    assert np.allclose(got, want, rtol=1e-4, atol=1e-6), np.abs(got - want).max()
