@@ -36,6 +36,7 @@ FLOPS_PER_NODE = {"binary": 44,   # two child slab tests: 12 FMA (24 flops), 10 
                   "wide": 140}    # eight child slab tests: 48 FMA (96 flops), 40 min/max, 8 compares (per-node
                                   # decode: 3 scale + 3 offset products excluded)
 FLOPS_PER_TRI = 45      # Moller-Trumbore: 2 cross, 4 dot, 1 div, 4 mul, 3 sub (FMA = 2 flops)
+NODE_BYTES = {"binary": 64, "wide": 80}  # bytes fetched per node visit
 # DRAM bytes (read + write) per full-size launch of the production kernels, from one
 # one-pass ncu capture of this step (profiles/launches_spheres196k_1024px_64spp.md);
 # cleared whenever the kernels change until they are captured again.
@@ -355,6 +356,12 @@ def run_ours(args):
         kern = {"forward_kernel": (fwd_avg, flops_f), "adjoint_kernel": (adj_avg, flops_b)}
     dom = max(kern, key=lambda k: kern[k][0])
     dom_ms, dom_flops = kern[dom]
+    # memory side of the same kernel: node and triangle bytes the traversal must
+    # fetch (through L2; the scene is L2-resident), per the counted visits
+    node_b, tri_b = NODE_BYTES[args.bvh], 48
+    bytes_f = node_b * int(cf[3]) + tri_b * int(cf[4])
+    bytes_b = node_b * int(cb[3]) + tri_b * int(cb[4])
+    dom_bytes = {"forward_kernel": bytes_f, "replay_kernel": bytes_b / 2, "adjoint_kernel": bytes_b}[dom]
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     mhz = clk.get("sm_mhz") or 1477.0
     peak_tflops = sms * 128 * 2 * mhz * 1e6 / 1e12
@@ -387,7 +394,10 @@ def run_ours(args):
                      "work": f"{FLOPS_PER_NODE[args.bvh]}/node visit + {FLOPS_PER_TRI}/triangle test (counted launch"
                              + ("; replay = half of the counted fused adjoint, its time = adjoint stage minus "
                                 "the radiance pass timed alone)" if split else ")"),
-                     "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 x median SM clock {mhz} MHz"},
+                     "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 x median SM clock {mhz} MHz",
+                     "l2_algorithmic_gbs": round(dom_bytes / (dom_ms / 1e3) / 1e9, 1),
+                     "l2_basis": f"{node_b} B per node visit + {tri_b} B per triangle test; compare the "
+                                 "L2-resident read probe of bench.py --peaks (4254 GB/s)"},
         "cpu_baseline": cpu,
         "e2e": {"value": round(rays_step / (e2e_ms / 1e3) / 1e6, 2), "unit": "Mrays/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": round(e2e_ms, 3)},
