@@ -80,6 +80,14 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// BF16 pair (lo in the low half) of max(x, 0): one convert with ReLU, the same bits
+// as pack_bf16(fmaxf(lo, 0), fmaxf(hi, 0)) for finite inputs.
+__device__ __forceinline__ uint32_t pack_relu_bf16(float lo, float hi) {
+  uint32_t d;
+  asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+  return d;
+}
+
 // ---------------------------------------------------------------- operand layout
 // K-major, no swizzle, K = 64: 8x8 core matrices of 8 rows x 16 bytes, the eight
 // core matrices of an 8-row group adjacent along K (128 B apart), 8-row groups
@@ -237,10 +245,8 @@ __global__ void __launch_bounds__(128 * kGroups, 1)
 #pragma unroll
           for (int h = 0; h < 2; ++h) {
             const float* p = v + 8 * h;
-            const uint4 q = make_uint4(pack_bf16(fmaxf(p[0], 0.f), fmaxf(p[1], 0.f)),
-                                       pack_bf16(fmaxf(p[2], 0.f), fmaxf(p[3], 0.f)),
-                                       pack_bf16(fmaxf(p[4], 0.f), fmaxf(p[5], 0.f)),
-                                       pack_bf16(fmaxf(p[6], 0.f), fmaxf(p[7], 0.f)));
+            const uint4 q = make_uint4(pack_relu_bf16(p[0], p[1]), pack_relu_bf16(p[2], p[3]),
+                                       pack_relu_bf16(p[4], p[5]), pack_relu_bf16(p[6], p[7]));
             *reinterpret_cast<uint4*>(X + core_off(r, 16 * c16 + 8 * h)) = q;
           }
         }
@@ -408,10 +414,8 @@ __global__ void __launch_bounds__(128 * kTrGroups, 1)
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
           const float* p = v + 8 * h;
-          const uint4 q = make_uint4(pack_bf16(fmaxf(p[0], 0.f), fmaxf(p[1], 0.f)),
-                                     pack_bf16(fmaxf(p[2], 0.f), fmaxf(p[3], 0.f)),
-                                     pack_bf16(fmaxf(p[4], 0.f), fmaxf(p[5], 0.f)),
-                                     pack_bf16(fmaxf(p[6], 0.f), fmaxf(p[7], 0.f)));
+          const uint4 q = make_uint4(pack_relu_bf16(p[0], p[1]), pack_relu_bf16(p[2], p[3]),
+                                     pack_relu_bf16(p[4], p[5]), pack_relu_bf16(p[6], p[7]));
           put_chunk(Xt, r, 2 * c16 + h, q, live ? X + (l + 1) * plane + row * NRC_W : nullptr);
         }
       }
