@@ -59,6 +59,12 @@ class RenderIn(C.Structure):
     ]
 
 
+class ReparamIn(C.Structure):
+    _fields_ = [("n_aux", C.c_int), ("kappa", C.c_double), ("kernel_scale", C.c_double), ("power", C.c_double),
+                ("miss", C.c_double), ("eps", C.c_double), ("jackknife", C.c_int),
+                ("border", C.c_double)]
+
+
 def lib():
     global _lib
     with _lock:
@@ -95,6 +101,12 @@ def lib():
             L.oracle_mlp_loss_grad.restype = dp
             L.oracle_mlp_adam.argtypes = [vp, vp, vp, vp, ip, dp, dp, dp, dp, ip]
             L.oracle_nrc_encode.argtypes = [ip, vp, vp, vp]
+            L.oracle_grad_reparam.argtypes = [vp, C.POINTER(RenderIn), vp, C.POINTER(ReparamIn), vp, vp, ip, vp, ip]
+            L.oracle_grad_reparam.restype = ip
+            L.oracle_sphere_div.argtypes = [ip, vp, vp]
+            L.oracle_sphere_div.restype = dp
+            L.oracle_warp.argtypes = [vp, vp, vp, ip, vp, C.POINTER(ReparamIn), ip, vp, vp, vp, vp, vp]
+            L.oracle_warp.restype = ip
             _lib = L
     return _lib
 
@@ -249,6 +261,66 @@ def render_jvp(osc: OracleScene, r: RenderIn, t_albedo=None, t_textures=None, t_
     lib().oracle_render_jvp(osc.handle, C.byref(r), dptr(t_albedo), C.cast(arr, C.c_void_p), len(tex),
                             dptr(t_rough), dptr(t_env), _ptr(img), _ptr(dot), threads)
     return img, dot
+
+
+# Options of the reparameterized translation derivative: auxiliary rays per
+# traced ray, vMF concentration of their lobe, how much narrower the weighting
+# kernel is, depth-weight exponent, weight of escaping rays, normaliser floor,
+# leave-one-out correction on/off, width in pixels of the window that takes the
+# camera-ray warp to zero at the image border.
+REPARAM_DEFAULTS = dict(n_aux=16, kappa=1000.0, kernel_scale=8.0, power=2.0, miss=0.01, eps=1e-4,
+                        jackknife=1, border=4.0)
+
+
+def _reparam_in(opts) -> ReparamIn:
+    o = dict(REPARAM_DEFAULTS, **opts)
+    return ReparamIn(int(o["n_aux"]), float(o["kappa"]), float(o["kernel_scale"]), float(o["power"]),
+                     float(o["miss"]), float(o["eps"]), int(o["jackknife"]), float(o["border"]))
+
+
+def grad_reparam(osc: OracleScene, r: RenderIn, grad_image=None, dot_param=-1, threads=0, **opts):
+    """Translation gradients through reparameterized visibility, by forward mode.
+
+    Returns (g [n_shapes, 3], image [h, w, 3], image_dot [h, w, 3]): g = sum of
+    grad_image * d image / d tau (zeros without grad_image); image_dot = derivative
+    along parameter `dot_param` = 3 * shape + axis (zeros if < 0)."""
+    o = _reparam_in(opts)
+    h, w = _crop_shape(r)
+    gi = None if grad_image is None else np.ascontiguousarray(grad_image, dtype=np.float64).reshape(h, w, 3)
+    g = np.zeros((osc.scene.n_shapes, 3))
+    img = np.zeros((h, w, 3))
+    dot = np.zeros((h, w, 3))
+    rc = lib().oracle_grad_reparam(osc.handle, C.byref(r), _ptr(gi), C.byref(o), _ptr(g), _ptr(img),
+                                   int(dot_param), _ptr(dot), threads)
+    if rc != 0:
+        raise ValueError("oracle_grad_reparam: bad options")
+    return g, img, dot
+
+
+def sphere_div(kind: int, u, e) -> float:
+    """Divergence on the unit sphere at u of V = e (0), w x e (1), (I - w w^T) e (2)."""
+    u = np.ascontiguousarray(u, np.float64)
+    e = np.ascontiguousarray(e, np.float64)
+    return lib().oracle_sphere_div(kind, _ptr(u), _ptr(e))
+
+
+def warp(osc: OracleScene, o, u, s_o: int, uniforms, param: int, at=None, m=None, **opts):
+    """One warp field: (V at `at` (default u), div V at u, log-derivative with covector m, n_hits)."""
+    op = _reparam_in(opts)
+    o = np.ascontiguousarray(o, np.float64)
+    u = np.ascontiguousarray(u, np.float64)
+    uni = np.ascontiguousarray(uniforms, np.float64)
+    assert uni.size == 2 * op.n_aux
+    at_ = None if at is None else np.ascontiguousarray(at, np.float64)
+    m_ = None if m is None else np.ascontiguousarray(m, np.float64)
+    V = np.zeros(3)
+    div = np.zeros(1)
+    logd = np.zeros(1)
+    n = lib().oracle_warp(osc.handle, _ptr(o), _ptr(u), int(s_o), _ptr(uni), C.byref(op), int(param), _ptr(at_),
+                          _ptr(m_), _ptr(V), _ptr(div), _ptr(logd))
+    if n < 0:
+        raise ValueError("oracle_warp: bad options")
+    return V, float(div[0]), float(logd[0]), n
 
 
 def pcg32(initstate: int, initseq: int, n: int) -> np.ndarray:

@@ -220,6 +220,14 @@ typedef struct {
   // scene's map.  Sampling always uses the scene's map (detached sampling).
   const double* env_radiance;
 } oracle_render_in;
+
+// Options of the reparameterized translation derivative (see ReparamOpts).
+typedef struct {
+  int n_aux;
+  double kappa, kernel_scale, power, miss, eps;
+  int jackknife;
+  double border;
+} oracle_reparam_opts;
 }
 
 namespace {
@@ -647,6 +655,15 @@ Camera make_camera(const oracle_render_in& r) {
 // Events reported by the integrator to an accumulator.  `scatter` is called
 // for every continued vertex with the throughput factor of the sampled
 // direction; the accumulators decide what to do with derivative information.
+// The ray events (camera ray, the block of auxiliary random numbers a vertex
+// draws, the unoccluded light-sample ray and the sampled continuation ray) are
+// only used by the reparameterized derivative; the others inherit no-ops.
+struct NoRayEvents {
+  void camera_ray(uint64_t, V3, V3, V3) {}
+  void vertex_block() {}
+  void nee_ray(V3, V3, int, V3, int) {}
+  void bsdf_ray(V3, V3, int, V3, int) {}
+};
 struct VertexInfo {
   Mat m;
   V3 wi;        // local incident direction (toward the previous vertex)
@@ -687,6 +704,7 @@ V3 render_sample(const Scene& s, const Camera& cam, const oracle_render_in& r, i
   double sy = (1.0 - 2.0 * (py + j1) / cam.h) * cam.tan_half;
   V3 ro = cam.o;
   V3 rd = normalize(cam.fwd + cam.right * sx + cam.up * sy);
+  acc.camera_ray(stream, ro, rd, cam.fwd);
 
   bool has_area = !s.light_tris.empty();
   bool has_env = s.env_w > 0;
@@ -729,6 +747,7 @@ V3 render_sample(const Scene& s, const Camera& cam, const oracle_render_in& r, i
     if (depth >= r.max_depth) break;
     double u[8];
     for (int k = 0; k < 8; ++k) u[k] = rng.uniform();
+    acc.vertex_block();
     if (sh.bsdf == BSDF_NONE) break;
 
     V3 p = ro + rd * hit.t;
@@ -846,6 +865,7 @@ V3 render_sample(const Scene& s, const Camera& cam, const oracle_render_in& r, i
             V3 scale = Le * s_env;             // everything but beta and f
             V3 c = mul(mul(beta, f), scale);
             L = L + c;
+            acc.nee_ray(so, dir, s.tri_shape[t], n, vi.m.bsdf);
             acc.nee(vi, wl, scale, c, env_texel, mul(beta, f) * s_env, s_env);
           }
         }
@@ -877,11 +897,13 @@ V3 render_sample(const Scene& s, const Camera& cam, const oracle_render_in& r, i
       if (!(pdf > 0.0) || max3(f) <= 0.0) break;
       double k = wo_l.z / pdf;
       beta = mul(beta, f) * k;
+      V3 wo = fr.to_world(wo_l);
+      V3 ro_next = offset_origin(p, ng, wo);
+      acc.bsdf_ray(ro_next, wo, s.tri_shape[t], n, vi.m.bsdf);
       acc.scatter(vi, wo_l, k);
       prev_delta = false;
       prev_pdf = pdf;
-      V3 wo = fr.to_world(wo_l);
-      ro = offset_origin(p, ng, wo);
+      ro = ro_next;
       rd = wo;
     }
     // ---- Russian roulette from depth rr_depth on
@@ -899,7 +921,7 @@ V3 render_sample(const Scene& s, const Camera& cam, const oracle_render_in& r, i
 }
 
 // Accumulator for the plain render: ignores events.
-struct NullAcc {
+struct NullAcc : NoRayEvents {
   void emission(V3, V3, int, V3, double) {}
   void nee(const VertexInfo&, V3, V3, V3, int, V3, double) {}
   void scatter(const VertexInfo&, V3, double) {}
@@ -908,7 +930,7 @@ struct NullAcc {
 };
 
 // Stored-tape accumulator: keeps every vertex record, then runs a reverse sweep.
-struct TapeAcc {
+struct TapeAcc : NoRayEvents {
   struct Rec {
     int kind;      // 0 emission, 1 nee, 2 scatter
     V3 c;          // contribution (emission / nee)
@@ -954,7 +976,7 @@ struct SelParam {
   int kind, a, b, c;  // 0: albedo (row a, channel b); 1: texel (tex a, texel b, channel c); 2: roughness a;
                       // 3: environment pixel a, channel b
 };
-struct DualAcc {
+struct DualAcc : NoRayEvents {
   const std::vector<SelParam>* sel;
   Dual beta[3], L[3];
   size_t n;
@@ -1021,7 +1043,7 @@ struct Direction {
   const double* rough = nullptr;          // [R] or null
   const double* env = nullptr;            // [env_h][env_w][4] or null
 };
-struct JvpAcc {
+struct JvpAcc : NoRayEvents {
   const Direction* v;
   Dual beta[3], L[3];
   void init(const Direction* dir) {
@@ -1070,6 +1092,339 @@ struct JvpAcc {
   }
   void roulette(double q) {
     for (int c = 0; c < 3; ++c) beta[c] = beta[c] * (1.0 / q);
+  }
+};
+
+// ---------------------------------------------------------------- reparameterized derivatives
+// Derivatives with respect to shape translations through visibility (Sec. 4.7,
+// "Reparameterizations"; warp field after Bangaru et al. 2020).  Every ray the
+// integrator traces is reparameterized: in the primal the warp is the identity;
+// its derivative turns the ray direction by V(u) and multiplies the integrand by
+// the Jacobian determinant 1 + div V.  The parameters are one translation per
+// shape (all its vertices move together); a surface point keeps its barycentric
+// coordinates, so path vertices move with their shape's translation.
+//
+// The warp field of a ray (origin o, primal direction u, origin shape s_o; the
+// camera counts as static) is built from N auxiliary rays w_i drawn from the von
+// Mises-Fisher lobe of concentration kappa around u (Jakob 2012, "Numerically
+// stable sampling of the von Mises-Fisher distribution on S^2"), in the frame of u
+// (Duff et al. 2017), with uniforms from the sample's auxiliary PCG32 stream.  An
+// auxiliary ray that hits triangle i (plane n_i . (x - o) = d_i) says how a point
+// of that plane moves relative to the origin: seen along w, the plane point at
+// distance d_i / (n_i . w) moves with Delta_i = tau'(shape_i) - tau'(s_o), i.e. its
+// direction turns by (I - w w^T) Delta_i (n_i . w) / d_i.  The warp is the
+// kernel-weighted average of these velocities,
+//   V(w) = sum_i k(w, w_i) g_i c_i(w) / q_i  /  ( sum_i k(w, w_i) g_i / q_i + N eps K ),
+// with the vMF kernel k(w, w') = exp(kernel_scale kappa (w.w' - 1)) (narrower
+// than the sampling density q), depth weights g_i = (t0 / t_i)^m relative to the
+// ray's own hit distance t0 (1 if the ray escapes) so that the closer surface
+// dominates near its silhouette, and escaping auxiliary rays weighted `miss` with
+// velocity 0 (the environment does not move).  The samples are held fixed while V
+// is evaluated at other w, so V is smooth; its divergence on the sphere is taken
+// in the gnomonic chart around u with two-component dual numbers.  The ratio of
+// sample sums is biased by O(1/N); the leave-one-out (jackknife) combination
+// N f(all) - (N-1)/N sum_j f(all but j) removes the leading term.
+//
+// Each traced ray multiplies the integrand it carries by
+//   camera ray: 1 + theta (div(bV) - 3 f.(bV) / f.u), the image-plane measure of
+//               the pinhole (f = optical axis); b is a window that takes the warp
+//               to 0 within `border` pixels of the image border, where samples
+//               cannot be moved;
+//   light and BSDF rays at a diffuse vertex: 1 + theta (div V + n.V / n.u), the
+//               cosine term.
+// Rays leaving non-diffuse vertices are not reparameterized (their directional
+// terms stay detached).  The tangent of a sample is propagated forward along the
+// path like the throughput (no replay): the oracle's independent route to the
+// reverse-mode kernel's gradients.
+
+struct ReparamOpts {
+  int n_aux = 16;
+  double kappa = 1000.0;      // concentration of the auxiliary-ray lobe
+  double kernel_scale = 8.0;  // the weighting kernel is kernel_scale x narrower
+  double power = 2.0;         // depth-weight exponent m
+  double miss = 0.01;         // weight of an auxiliary ray that escapes (velocity 0)
+  double eps = 1e-4;          // floor of the normaliser
+  int jackknife = 1;          // leave-one-out correction of the ratio's 1/N bias
+  double border = 4.0;        // camera-ray warp window at the image border, pixels
+};
+
+// value and gradient in the two chart coordinates
+struct D2 {
+  double v = 0, a = 0, b = 0;
+};
+inline D2 operator+(D2 x, D2 y) { return {x.v + y.v, x.a + y.a, x.b + y.b}; }
+inline D2 operator-(D2 x, D2 y) { return {x.v - y.v, x.a - y.a, x.b - y.b}; }
+inline D2 operator*(D2 x, D2 y) { return {x.v * y.v, x.a * y.v + x.v * y.a, x.b * y.v + x.v * y.b}; }
+inline D2 operator*(D2 x, double k) { return {x.v * k, x.a * k, x.b * k}; }
+inline D2 operator/(D2 x, D2 y) {
+  double q = x.v / y.v;
+  return {q, (x.a - q * y.a) / y.v, (x.b - q * y.b) / y.v};
+}
+inline D2 d2exp(D2 x) {
+  double e = std::exp(x.v);
+  return {e, e * x.a, e * x.b};
+}
+inline D2 d2sqrt(D2 x) {
+  double r = std::sqrt(x.v);
+  return {r, x.a / (2.0 * r), x.b / (2.0 * r)};
+}
+struct VD {
+  D2 x, y, z;
+};
+inline D2 dotd(VD p, V3 q) { return p.x * q.x + p.y * q.y + p.z * q.z; }
+inline D2 dotd(VD p, VD q) { return p.x * q.x + p.y * q.y + p.z * q.z; }
+inline VD scaled(V3 q, D2 k) { return {k * q.x, k * q.y, k * q.z}; }
+inline VD operator+(VD p, VD q) { return {p.x + q.x, p.y + q.y, p.z + q.z}; }
+inline VD divided(VD p, D2 k) { return {p.x / k, p.y / k, p.z / k}; }
+inline VD constant(V3 q) { return {D2{q.x, 0, 0}, D2{q.y, 0, 0}, D2{q.z, 0, 0}}; }
+
+// Divergence on the unit sphere at u of the field F (a functor VD -> VD taking a
+// unit direction): in gnomonic coordinates x around u, w(x) = normalize(u + x1
+// t1 + x2 t2), the field's coordinates are U_a = d x_a / d theta =
+// [t_a.V (u.w) - (t_a.w)(u.V)] / (u.w)^2, and the chart's metric is Euclidean to
+// first order at x = 0, so div = dU_1/dx1 + dU_2/dx2 there.
+template <class F>
+double sphere_div(V3 u, F field) {
+  Frame fr = make_frame(u);
+  VD wr{D2{u.x, fr.s.x, fr.t.x}, D2{u.y, fr.s.y, fr.t.y}, D2{u.z, fr.s.z, fr.t.z}};
+  D2 len = d2sqrt(dotd(wr, wr));
+  VD w = divided(wr, len);
+  VD V = field(w);
+  D2 uw = dotd(w, u), uV = dotd(V, u);
+  D2 den = uw * uw;
+  D2 U1 = (dotd(V, fr.s) * uw - dotd(w, fr.s) * uV) / den;
+  D2 U2 = (dotd(V, fr.t) * uw - dotd(w, fr.t) * uV) / den;
+  return U1.a + U2.b;
+}
+
+// Auxiliary rays of one warp, traced once at the primal center u.
+struct AuxHit {
+  V3 w;
+  double t, g_over_q;
+  int shape;
+  V3 n;       // geometric normal of the hit triangle
+  double d;   // n . (hit point - origin): the plane is {x : n.(x - o) = d}
+};
+struct WarpSamples {
+  V3 u;
+  std::vector<AuxHit> hits;
+  int n = 0;
+  double kappa = 0, eps = 0, K = 0, kscale = 1.0;
+  int jackknife = 0;
+};
+
+// vMF direction (local z = lobe axis) from two uniforms: cos(theta) = 1 + log(xi +
+// (1 - xi) e^{-2 kappa}) / kappa with xi = 1 - u0 in (0, 1], phi = 2 pi u1.
+V3 vmf_local(double u0, double u1, double kappa) {
+  double xi = 1.0 - u0;
+  double c1 = std::log(xi + (1.0 - xi) * std::exp(-2.0 * kappa)) / kappa;  // cos(theta) - 1
+  double sin2 = std::max(0.0, -c1 * (2.0 + c1));
+  double st = std::sqrt(sin2), phi = 2.0 * kPi * u1;
+  return V3(st * std::cos(phi), st * std::sin(phi), 1.0 + c1);
+}
+
+WarpSamples warp_samples(const Scene& s, const ReparamOpts& op, V3 o, V3 u, const double* uni) {
+  WarpSamples ws;
+  ws.u = u;
+  ws.n = op.n_aux;
+  ws.kappa = op.kappa;
+  ws.eps = op.eps;
+  ws.kscale = op.kernel_scale;
+  ws.jackknife = op.jackknife;
+  ws.K = 2.0 * kPi * (1.0 - std::exp(-2.0 * op.kappa)) / op.kappa;  // integral of k
+  const double Cq = 1.0 / ws.K;                                       // vMF normalisation
+  Frame fr = make_frame(u);
+  for (int i = 0; i < op.n_aux; ++i) {
+    V3 w = normalize(fr.to_world(vmf_local(uni[2 * i], uni[2 * i + 1], op.kappa)));
+    Hit h = closest_hit(s, o, w, INFINITY, false);
+    if (h.prim < 0) {
+      if (op.miss > 0)
+        ws.hits.push_back({w, INFINITY, op.miss / (Cq * std::exp(op.kappa * (dot(u, w) - 1.0))), -1, V3(), 1.0});
+      continue;
+    }
+    double q = Cq * std::exp(op.kappa * (dot(u, w) - 1.0));
+    V3 n = geo_normal(s, h.prim);
+    ws.hits.push_back({w, h.t, 1.0 / q, s.tri_shape[h.prim], n, dot(n, w) * h.t});
+  }
+  // depth weights relative to the ray's own hit distance t0: g = (t0 / t)^m, so
+  // a closer surface dominates a farther one near its silhouette; if the ray
+  // itself escapes, every hit has g = 1
+  Hit h0 = closest_hit(s, o, u, INFINITY, false);
+  if (h0.prim >= 0)
+    for (AuxHit& h : ws.hits)
+      if (h.shape >= 0) h.g_over_q *= std::pow(h0.t / std::max(h.t, 1e-3 * h0.t), op.power);
+  return ws;
+}
+
+// Motion of auxiliary hit i relative to the origin for the unit tangent of
+// parameter (shape ps, axis pa): the hit's shape moves with tau[ps], the origin
+// with tau[s_o]; escaping rays (shape -1) see the static environment.
+V3 aux_motion(const AuxHit& h, int s_o, int ps, int pa) {
+  double m = (h.shape >= 0 && h.shape == ps ? 1.0 : 0.0) - (h.shape >= 0 && s_o == ps ? 1.0 : 0.0);
+  V3 e;
+  if (pa == 0) e.x = m;
+  else if (pa == 1) e.y = m;
+  else e.z = m;
+  return e;
+}
+
+// The warp field of parameter (ps, pa) at direction w (fixed samples).
+VD warp_field(const WarpSamples& ws, int s_o, int ps, int pa, VD w, int skip = -1) {
+  VD num = constant(V3());
+  D2 den{0, 0, 0};
+  int idx = -1;
+  for (const AuxHit& h : ws.hits) {
+    if (++idx == skip) continue;
+    D2 a = d2exp((dotd(w, h.w) - D2{1.0, 0, 0}) * (ws.kappa * ws.kscale)) * h.g_over_q;
+    // velocity seen along w of the point where w meets the plane of hit i
+    // (distance d_i / (n_i . w)), moving with the hit's shape relative to the origin
+    V3 e = aux_motion(h, s_o, ps, pa);
+    D2 inv_t = dotd(w, h.n) * (1.0 / h.d);
+    D2 we = dotd(w, e);
+    VD pc{(D2{e.x, 0, 0} - w.x * we) * inv_t, (D2{e.y, 0, 0} - w.y * we) * inv_t, (D2{e.z, 0, 0} - w.z * we) * inv_t};
+    num = num + VD{pc.x * a, pc.y * a, pc.z * a};
+    den = den + a;
+  }
+  const double inv_n = 1.0 / (skip != -1 ? ws.n - 1 : ws.n);
+  D2 d = den * inv_n + D2{ws.eps * ws.K, 0, 0};
+  return divided(VD{num.x * inv_n, num.y * inv_n, num.z * inv_n}, d);
+}
+
+// Log-derivative factor of one reparameterized ray for every translation
+// parameter that can move it: d/dtheta log(integrand * det) = m.(P u V) + div V,
+// with m the covector of the ray's measure/cosine term.  `out` gets (param, value).
+// Window of the camera-ray warp: 1 inside the image, falling to 0 at its border
+// over `border` pixels (smoothstep of the distance in pixels to the nearest image
+// edge), so that no sample is moved across the border of the image.
+struct CamWindow {
+  V3 fwd, right, up;
+  double tan_half = 1, aspect = 1, border = 4;
+  int w = 1, h = 1;
+};
+D2 window(const CamWindow& c, VD w) {
+  D2 fw = dotd(w, c.fwd);
+  D2 sx = dotd(w, c.right) / fw * (1.0 / (c.tan_half * c.aspect));
+  D2 sy = dotd(w, c.up) / fw * (1.0 / c.tan_half);
+  D2 px = (sx + D2{1, 0, 0}) * (0.5 * c.w), py = (D2{1, 0, 0} - sy) * (0.5 * c.h);
+  D2 d = px;
+  for (D2 x : {D2{c.w - px.v, -px.a, -px.b}, py, D2{c.h - py.v, -py.a, -py.b}})
+    if (x.v < d.v) d = x;
+  D2 t = d * (1.0 / c.border);
+  if (t.v >= 1.0) return D2{1, 0, 0};
+  if (t.v <= 0.0) return D2{0, 0, 0};
+  return t * t * (D2{3, 0, 0} - t * 2.0);
+}
+
+void warp_log_derivs(const WarpSamples& ws, int s_o, V3 m, std::vector<std::pair<int, double>>& out,
+                     const CamWindow* win = nullptr) {
+  out.clear();
+  std::vector<int> shapes;
+  for (const AuxHit& h : ws.hits)
+    if (h.shape >= 0 && h.shape != s_o && std::find(shapes.begin(), shapes.end(), h.shape) == shapes.end())
+      shapes.push_back(h.shape);
+  if (!shapes.empty() && s_o >= 0) shapes.push_back(s_o);
+  const V3 u = ws.u;
+  for (int ps : shapes)
+    for (int pa = 0; pa < 3; ++pa) {
+      auto ld = [&](int skip) {
+        auto field = [&](VD w) {
+          VD V = warp_field(ws, s_o, ps, pa, w, skip);
+          if (!win) return V;
+          D2 b = window(*win, w);
+          return VD{V.x * b, V.y * b, V.z * b};
+        };
+        double div = sphere_div(u, field);
+        VD V = field(constant(u));
+        V3 v(V.x.v, V.y.v, V.z.v);
+        V3 wdot = v - u * dot(u, v);
+        return dot(m, wdot) + div;
+      };
+      double full = ld(-1);
+      if (ws.jackknife && ws.n > 1) {
+        // leave-one-out over all N samples (misses without weight contribute the full value)
+        double loo = 0.0;
+        int nh = (int)ws.hits.size();
+        for (int j = 0; j < nh; ++j) loo += ld(j);
+        loo += (ws.n - nh) * ld(-2);
+        full = ws.n * full - (ws.n - 1.0) / ws.n * loo;
+      }
+      out.push_back({3 * ps + pa, full});
+    }
+}
+
+// Forward-mode accumulator of the translation derivatives (all shapes at once).
+struct ReparamAcc {
+  const Scene* s = nullptr;
+  const ReparamOpts* op = nullptr;
+  uint64_t seed = 0;
+  int np = 0;
+  Pcg32 aux;
+  std::vector<double> block;  // 4N uniforms of the current vertex: light ray, then BSDF ray
+  V3 beta;
+  std::vector<V3> bdot, ldot;
+  std::vector<std::pair<int, double>> lnee, lbsdf, tmp;
+  CamWindow win;
+  void init(const Scene* sc, const ReparamOpts* o, uint64_t sd, const Camera& cam) {
+    win.fwd = cam.fwd;
+    win.right = cam.right;
+    win.up = cam.up;
+    win.tan_half = cam.tan_half;
+    win.aspect = cam.aspect;
+    win.w = cam.w;
+    win.h = cam.h;
+    win.border = o->border;
+    s = sc;
+    op = o;
+    seed = sd;
+    np = 3 * (int)sc->shapes.size();
+    bdot.assign(np, V3());
+    ldot.assign(np, V3());
+    block.assign(4 * o->n_aux, 0.0);
+  }
+  void camera_ray(uint64_t stream, V3 o, V3 d, V3 fwd) {
+    aux.seed(seed, stream | (1ull << 62));
+    std::vector<double> uni(2 * op->n_aux);
+    for (double& x : uni) x = aux.uniform();
+    WarpSamples ws = warp_samples(*s, *op, o, d, uni.data());
+    warp_log_derivs(ws, -1, fwd * (-3.0 / dot(fwd, d)), tmp, &win);
+    beta = V3(1, 1, 1);
+    for (auto& pv : tmp) bdot[pv.first] = V3(1, 1, 1) * pv.second;
+  }
+  void vertex_block() {
+    for (double& x : block) x = aux.uniform();
+  }
+  void ray(V3 o, V3 d, int shape, V3 n, int bsdf, const double* uni, std::vector<std::pair<int, double>>& out) {
+    out.clear();
+    if (bsdf != BSDF_DIFFUSE) return;
+    WarpSamples ws = warp_samples(*s, *op, o, d, uni);
+    warp_log_derivs(ws, shape, n * (1.0 / dot(n, d)), out);
+  }
+  void nee_ray(V3 o, V3 d, int shape, V3 n, int bsdf) { ray(o, d, shape, n, bsdf, block.data(), lnee); }
+  void bsdf_ray(V3 o, V3 d, int shape, V3 n, int bsdf) {
+    ray(o, d, shape, n, bsdf, block.data() + 2 * op->n_aux, lbsdf);
+  }
+  void emission(V3, V3 le_w, int, V3, double) {
+    for (int p = 0; p < np; ++p) ldot[p] = ldot[p] + mul(bdot[p], le_w);
+  }
+  void nee(const VertexInfo& vi, V3 wl, V3 scale, V3 c, int, V3, double) {
+    V3 f = bsdf_eval(vi.m, vi.wi, wl);
+    for (int p = 0; p < np; ++p) ldot[p] = ldot[p] + mul(mul(bdot[p], f), scale);
+    for (auto& pv : lnee) ldot[pv.first] = ldot[pv.first] + c * pv.second;
+  }
+  void scatter(const VertexInfo& vi, V3 wo, double k) {
+    V3 f = bsdf_eval(vi.m, vi.wi, wo);
+    V3 nb = mul(beta, f) * k;
+    for (int p = 0; p < np; ++p) bdot[p] = mul(bdot[p], f) * k;
+    for (auto& pv : lbsdf) bdot[pv.first] = bdot[pv.first] + nb * pv.second;
+    beta = nb;
+  }
+  void scatter_delta(double w) {
+    beta = beta * w;
+    for (auto& b : bdot) b = b * w;
+  }
+  void roulette(double q) {
+    beta = beta * (1.0 / q);
+    for (auto& b : bdot) b = b * (1.0 / q);
   }
 };
 
@@ -1458,6 +1813,67 @@ int oracle_train_records(void* sc, const oracle_render_in* r, int cap, double* o
   return n;
 }
 
+static bool reparam_opts(const oracle_reparam_opts* o, ReparamOpts& op) {
+  if (!o || o->n_aux < 2 || !(o->kappa > 0) || !(o->kernel_scale >= 1) || !(o->eps > 0) || !(o->miss >= 0))
+    return false;
+  op.n_aux = o->n_aux;
+  op.kappa = o->kappa;
+  op.kernel_scale = o->kernel_scale;
+  op.power = o->power;
+  op.miss = o->miss;
+  op.eps = o->eps;
+  op.jackknife = o->jackknife;
+  op.border = o->border;
+  return o->border > 0;
+}
+
+// Reverse-mode-equivalent translation gradient by forward mode: g[s][a] =
+// sum over pixels and channels of grad_image * d image / d tau[s][a] for every
+// shape translation tau (the reparameterized estimator above; every random
+// number fixed, auxiliary ones from the stream initseq | 2^62).  Optionally the
+// image and its derivative along parameter `dot_param` (= 3 shape + axis).
+int oracle_grad_reparam(void* sc, const oracle_render_in* r, const double* grad_image, const oracle_reparam_opts* o,
+                        double* g_out, double* image, int dot_param, double* image_dot, int n_threads) {
+  const Scene& s = *(Scene*)sc;
+  Camera cam = make_camera(*r);
+  ReparamOpts op;
+  if (!reparam_opts(o, op)) return -1;
+  int x0, y0, cw, ch;
+  crop_of(*r, x0, y0, cw, ch);
+  const int np = 3 * (int)s.shapes.size();
+  std::vector<double> rows((size_t)ch * np, 0.0);
+  parallel_rows(y0, ch, n_threads, [&](int py) {
+    double* grow = &rows[(size_t)(py - y0) * np];
+    for (int px = x0; px < x0 + cw; ++px) {
+      size_t pi = (size_t)(py - y0) * cw + (px - x0);
+      double sum[3] = {0, 0, 0}, sum_dot[3] = {0, 0, 0};
+      const double* gi = grad_image ? grad_image + pi * 3 : nullptr;
+      for (int k = 0; k < r->spp; ++k) {
+        ReparamAcc acc;
+        acc.init(&s, &op, r->seed, cam);
+        V3 l = render_sample(s, cam, *r, px, py, k, acc, nullptr);
+        for (int c = 0; c < 3; ++c) sum[c] += l[c];
+        if (dot_param >= 0 && dot_param < np)
+          for (int c = 0; c < 3; ++c) sum_dot[c] += acc.ldot[dot_param][c];
+        if (gi)
+          for (int p = 0; p < np; ++p) grow[p] += (gi[0] * acc.ldot[p].x + gi[1] * acc.ldot[p].y +
+                                                   gi[2] * acc.ldot[p].z) / r->spp;
+      }
+      for (int c = 0; c < 3; ++c) {
+        if (image) image[pi * 3 + c] = sum[c] / r->spp;
+        if (image_dot) image_dot[pi * 3 + c] = sum_dot[c] / r->spp;
+      }
+    }
+  });
+  if (g_out)
+    for (int p = 0; p < np; ++p) {
+      double t = 0.0;
+      for (int y = 0; y < ch; ++y) t += rows[(size_t)y * np + p];
+      g_out[p] = t;
+    }
+  return 0;
+}
+
 // ---------------------------------------------------------------- unit-test hooks
 void oracle_pcg32(uint64_t initstate, uint64_t initseq, int n, uint32_t* out) {
   Pcg32 r;
@@ -1535,4 +1951,46 @@ int oracle_frame(const double* n, double* s_out, double* t_out) {
   return 0;
 }
 
+
+// Divergence on the sphere (gnomonic-chart duals) of analytic fields at u:
+// kind 0: V = e (constant ambient vector), 1: V = w x e, 2: V = (I - w w^T) e.
+double oracle_sphere_div(int kind, const double* u, const double* e) {
+  V3 uu(u[0], u[1], u[2]), ee(e[0], e[1], e[2]);
+  auto field = [&](VD w) -> VD {
+    if (kind == 0) return constant(ee);
+    if (kind == 1) return VD{w.z * ee.y * -1.0 + w.y * ee.z, w.x * ee.z * -1.0 + w.z * ee.x,
+                             w.y * ee.x * -1.0 + w.x * ee.y};
+    D2 we = dotd(w, ee);
+    return VD{D2{ee.x, 0, 0} - w.x * we, D2{ee.y, 0, 0} - w.y * we, D2{ee.z, 0, 0} - w.z * we};
+  };
+  return sphere_div(uu, field);
+}
+
+// One warp field at origin o and center u (uniforms: 2 n_aux values): the
+// field of parameter (param / 3, param % 3) for origin shape s_o evaluated at the
+// unit direction `at` (NULL: u) into V_out, its divergence at u, and the log
+// derivative with covector m (NULL: zero).  Returns the number of auxiliary hits.
+int oracle_warp(void* sc, const double* o, const double* u, int s_o, const double* uni, const oracle_reparam_opts* opt,
+                int param, const double* at, const double* m, double* V_out, double* div_out, double* logd_out) {
+  const Scene& s = *(Scene*)sc;
+  ReparamOpts op;
+  if (!reparam_opts(opt, op)) return -1;
+  V3 uu(u[0], u[1], u[2]);
+  WarpSamples ws = warp_samples(s, op, V3(o[0], o[1], o[2]), uu, uni);
+  const int ps = param / 3, pa = param % 3;
+  V3 w = at ? V3(at[0], at[1], at[2]) : uu;
+  VD V = warp_field(ws, s_o, ps, pa, constant(w));
+  V_out[0] = V.x.v;
+  V_out[1] = V.y.v;
+  V_out[2] = V.z.v;
+  *div_out = sphere_div(uu, [&](VD x) { return warp_field(ws, s_o, ps, pa, x); });
+  if (logd_out) {
+    std::vector<std::pair<int, double>> ld;
+    warp_log_derivs(ws, s_o, m ? V3(m[0], m[1], m[2]) : V3(), ld);
+    *logd_out = 0.0;
+    for (auto& pv : ld)
+      if (pv.first == param) *logd_out = pv.second;
+  }
+  return (int)ws.hits.size();
+}
 }  // extern "C"

@@ -76,6 +76,15 @@ class Scene:
     def n_shapes(self) -> int:
         return int(self.bsdf.shape[0])
 
+    def translated(self, offsets) -> "Scene":
+        """Copy with every shape's vertices moved by offsets[shape] ([S, 3])."""
+        import copy
+        off = np.asarray(offsets, np.float64).reshape(self.n_shapes, 3)
+        s = copy.copy(self)
+        v = self.vertices.astype(np.float64) + off[self.tri_shape][:, None, :]
+        s.vertices = np.ascontiguousarray(v, dtype=np.float32)
+        return s
+
     def with_params(self, albedo=None, textures=None, roughness=None) -> "Scene":
         import copy
         s = copy.copy(self)
@@ -541,6 +550,68 @@ def lit_plane(albedo: float = 0.6, env_radiance: float = 1.0, env_size=(64, 32),
                  tri_shape=np.zeros(2, np.int32), albedo=np.full((1, 3), albedo, np.float32),
                  textures=[], roughness=np.zeros(0, np.float32), env=env, cameras=[cam],
                  name="lit_plane", **st)
+
+
+def occluder_sky(center=(0.15, 0.1), depth=3.0, side=0.4, env_radiance=1.0, width=64, height=64,
+                 vfov_deg=40.0) -> Scene:
+    """A black square facing a pinhole camera under a uniform environment.
+
+    Camera at the origin looking along -z; the square (shape 0, two triangles)
+    spans center +- side/2 in x and y at z = -depth.  The image is the
+    environment radiance outside the square's projection and 0 inside, so the
+    summed image changes with the square's depth by a closed form (its projected
+    area is (side/depth)^2 on the image plane at unit distance) and not at all
+    with a move parallel to the image plane.
+    """
+    cx, cy = center
+    h = 0.5 * side
+    q = ((cx - h, cy - h, -depth), (cx + h, cy - h, -depth), (cx + h, cy + h, -depth), (cx - h, cy + h, -depth))
+    tris = _quad(*q)
+    st = _shape_table(1)
+    st["bsdf"][0] = BSDF_NONE
+    env = np.full((16, 32, 4), env_radiance, np.float32)
+    env[..., 3] = 1.0
+    cam = Camera((0.0, 0.0, 0.0), (0.0, 0.0, -1.0), (0.0, 1.0, 0.0), vfov_deg, width, height)
+    return Scene(vertices=np.asarray(tris, np.float32), uvs=np.asarray(_QUAD_UV, np.float32),
+                 tri_shape=np.zeros(2, np.int32), albedo=np.zeros((0, 3), np.float32), textures=[],
+                 roughness=np.zeros(0, np.float32), env=env, cameras=[cam], name="occluder_sky", **st)
+
+
+def shadow_scene(light=(-1.2, 2.0, 0.0), light_half=0.25, occluder=(-0.6, 0.8, 0.0), occluder_half=0.3,
+                 camera=((1.6, 0.5, 0.0), (-0.2, 0.0, 0.0)), vfov_deg=40.0, width=64, height=64,
+                 radiance=20.0) -> Scene:
+    """A diffuse floor, a square area light and a square occluder casting a shadow.
+
+    Shapes: 0 floor (y = 0, |x|,|z| <= 2, albedo row 0), 1 light (facing -y,
+    radiance `radiance`, black BSDF), 2 occluder (horizontal, albedo row 1).
+    Nothing else: rays that miss see black.
+    """
+    tris, uvs, shp = [], [], []
+
+    def add(corners, shape):
+        for t, uv in zip(_quad(*corners), _QUAD_UV):
+            tris.append(t)
+            uvs.append(uv)
+            shp.append(shape)
+
+    add(((-2, 0, 2), (2, 0, 2), (2, 0, -2), (-2, 0, -2)), 0)
+    lx, ly, lz = light
+    h = light_half
+    add(((lx - h, ly, lz - h), (lx + h, ly, lz - h), (lx + h, ly, lz + h), (lx - h, ly, lz + h)), 1)
+    ox, oy, oz = occluder
+    h = occluder_half
+    add(((ox - h, oy, oz + h), (ox + h, oy, oz + h), (ox + h, oy, oz - h), (ox - h, oy, oz - h)), 2)
+    st = _shape_table(3)
+    st["bsdf"][[0, 2]] = BSDF_DIFFUSE
+    st["albedo_index"][0] = 0
+    st["albedo_index"][2] = 1
+    st["bsdf"][1] = BSDF_NONE
+    st["emission"][1] = radiance
+    albedo = np.array([[0.7, 0.6, 0.5], [0.3, 0.5, 0.4]], np.float32)
+    cam = Camera(tuple(camera[0]), tuple(camera[1]), (0.0, 1.0, 0.0), vfov_deg, width, height)
+    return Scene(vertices=np.asarray(tris, np.float32), uvs=np.asarray(uvs, np.float32),
+                 tri_shape=np.asarray(shp, np.int32), albedo=albedo, textures=[],
+                 roughness=np.zeros(0, np.float32), env=None, cameras=[cam], name="shadow", **st)
 
 
 # ----------------------------------------------------------------------------

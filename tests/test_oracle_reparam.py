@@ -1,0 +1,121 @@
+"""Pins of the oracle's reparameterized translation derivative (Sec. 4.7).
+
+The estimator (warp field from auxiliary rays, Jacobian determinant, per-ray
+log-derivative factors) is defined in oracle.cpp.  It is pinned here against
+what the mathematics fixes independently of it:
+  * the divergence on the sphere of analytic fields (closed forms);
+  * the divergence of an actual warp field against central differences of the
+    field itself (samples held fixed);
+  * the expected derivative of a rendered image against closed forms (the
+    projected area of a square seen against a uniform sky) and against central
+    finite differences of the primal render, for moving occluders and lights.
+The warp estimator is consistent, not unbiased: the tolerances below state the
+bias measured at the default options (16 auxiliary rays).
+"""
+import numpy as np
+import pytest
+
+from paper_2202_01284_gb300 import scenes as S
+
+pytestmark = pytest.mark.filterwarnings("ignore")
+
+
+def test_sphere_divergence_closed_forms(oracle_mod):
+    rng = np.random.default_rng(1)
+    for _ in range(20):
+        u = rng.normal(size=3)
+        u /= np.linalg.norm(u)
+        e = rng.normal(size=3)
+        # constant ambient field and its tangential part: div = -2 e.u; rotation: 0
+        assert oracle_mod.sphere_div(0, u, e) == pytest.approx(-2 * e @ u, abs=1e-12)
+        assert oracle_mod.sphere_div(1, u, e) == pytest.approx(0.0, abs=1e-12)
+        assert oracle_mod.sphere_div(2, u, e) == pytest.approx(-2 * e @ u, abs=1e-12)
+
+
+def _chart_coords(V, w, u, t):
+    return (t @ V * (u @ w) - (t @ w) * (u @ V)) / (u @ w) ** 2
+
+
+@pytest.mark.parametrize("param", [0, 2])
+def test_warp_divergence_matches_finite_differences(oracle_mod, param):
+    sc = S.occluder_sky()
+    osc = oracle_mod.OracleScene(sc)
+    rng = np.random.default_rng(4)
+    o = np.zeros(3)
+    n_checked = 0
+    for trial in range(12):
+        # directions near the square's right edge (x = 0.35 at depth 3)
+        u = np.array([0.35 + rng.uniform(-0.05, 0.05), rng.uniform(-0.05, 0.25), -3.0])
+        u /= np.linalg.norm(u)
+        uni = rng.random(32)
+        opts = dict(jackknife=0)
+        V0, div, logd, n = oracle_mod.warp(osc, o, u, -1, uni, param, m=np.array([0.3, -0.2, 0.5]), **opts)
+        if n == 0 or not np.any(V0):
+            continue
+        t1, t2 = oracle_mod.frame(u)
+        h = 1e-5
+        fd = 0.0
+        for t in (t1, t2):
+            vals = []
+            for sgn in (1, -1):
+                w = u + sgn * h * t
+                w /= np.linalg.norm(w)
+                V, _, _, _ = oracle_mod.warp(osc, o, u, -1, uni, param, at=w, **opts)
+                vals.append(_chart_coords(V, w, u, t))
+            fd += (vals[0] - vals[1]) / (2 * h)
+        assert div == pytest.approx(fd, rel=1e-5, abs=1e-6 * max(1.0, abs(div)))
+        # log-derivative = m . (tangential part of V) + div V
+        vt = V0 - u * (u @ V0)
+        assert logd == pytest.approx(np.array([0.3, -0.2, 0.5]) @ vt + div, rel=1e-9, abs=1e-12)
+        n_checked += 1
+    assert n_checked >= 6
+
+
+def _sum_grad(oracle_mod, sc, spp, seed, **opts):
+    cam = sc.cameras[0]
+    r = oracle_mod.render_in(cam, spp, 2, seed, -1, True)
+    g, _, _ = oracle_mod.grad_reparam(oracle_mod.OracleScene(sc), r, np.ones((cam.height, cam.width, 3)), **opts)
+    return g
+
+
+def test_square_depth_and_lateral_closed_forms(oracle_mod):
+    """A black square (side s, depth d) over a sky of radiance 1: the summed image
+    is (image area - (s/d)^2) / pixel area per channel, so moving it toward the
+    camera changes the sum by -2 s^2 / d^3 / pixel area per channel and moving it
+    sideways not at all."""
+    sc = S.occluder_sky(center=(0.15, 0.1), depth=3.0, side=0.4, width=64, height=64)
+    th = np.tan(np.radians(20.0))
+    pix_area = (2 * th / 64) ** 2
+    exact_z = -3 * 2 * 0.4 ** 2 / 3.0 ** 3 / pix_area
+    g = np.mean([_sum_grad(oracle_mod, sc, 256, seed)[0] for seed in (7, 8)], axis=0)
+    print("square: reparameterized", g, "closed form z", exact_z)
+    assert g[2] / exact_z == pytest.approx(1.0, abs=0.08)  # measured 0.96 (consistent estimator, N = 16)
+    assert abs(g[0]) < 0.2 * abs(exact_z) and abs(g[1]) < 0.2 * abs(exact_z)
+    # more auxiliary rays approach the closed form
+    g32 = _sum_grad(oracle_mod, sc, 128, 9, n_aux=32)[0]
+    assert abs(g32[2] / exact_z - 1.0) < 0.06
+
+
+def test_shadow_scene_matches_finite_differences(oracle_mod):
+    """Moving the light and the occluder of a lit floor, against central finite
+    differences of the primal render (same random numbers on both sides of each
+    difference; 1024 samples per pixel)."""
+    sc = S.shadow_scene()
+    cam = sc.cameras[0]
+    g = _sum_grad(oracle_mod, sc, 64, 3)
+    rf = oracle_mod.render_in(cam, 512, 2, 5, -1, True)
+    h = 0.01
+    fd = np.zeros((3, 3))
+    for shape in (1, 2):
+        for axis in range(3):
+            off = np.zeros((3, 3))
+            off[shape, axis] = h
+            ip = oracle_mod.render(oracle_mod.OracleScene(sc.translated(off)), rf).sum()
+            im = oracle_mod.render(oracle_mod.OracleScene(sc.translated(-off)), rf).sum()
+            fd[shape, axis] = (ip - im) / (2 * h)
+    print("reparameterized\n", g, "\nfinite differences\n", fd)
+    for shape in (1, 2):
+        scale = np.abs(fd[shape]).max()
+        assert np.abs(g[shape] - fd[shape]).max() < 0.15 * scale
+    # a plain (not reparameterized) derivative would be zero for every translation
+    assert np.abs(g[1:]).max() > 0.5 * np.abs(fd[1:]).max()
