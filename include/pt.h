@@ -392,6 +392,53 @@ int pt_ckpt_forward(pt_scene* scene, const pt_render_desc* desc, const pt_params
 int pt_ckpt_backward(pt_scene* scene, const pt_render_desc* desc, const pt_params* params, pt_ckpt* ckpt,
                      const float* grad_image, const pt_grads* grads, void* stream);
 
+/* ------------------------------------------------------------------ reparameterized PRB
+ * Gradients with respect to shape TRANSLATIONS through visibility (Sec. 4.7,
+ * reparameterizations; Sec. 4.8, the derivative terms of moving vertices; warp
+ * field after Bangaru et al. 2020).  The parameters are one translation per
+ * shape (all of its vertices move together; a surface point keeps its
+ * barycentric coordinates).  Every traced ray -- the camera ray and, at DIFFUSE
+ * vertices, the light-sample ray and the BSDF-sampled ray -- is reparameterized:
+ * n_aux auxiliary rays in a von Mises-Fisher lobe (concentration kappa) around
+ * it estimate a warp field V that follows the geometry they hit (the closer
+ * surface dominating near silhouettes, escaping rays weighted `miss`), and the
+ * ray contributes R * (m.V + div V), R = grad_image . (radiance the ray carries),
+ * m = the ray's cosine (or, for camera rays, the pinhole's image-plane density)
+ * term.  Rays leaving non-diffuse vertices are not reparameterized (their
+ * directional terms stay detached; the paper notes that specular interfaces are
+ * an open problem).  The warp estimator is consistent, not unbiased: its ratio of
+ * sample sums is jackknife-corrected, and the camera warp is windowed to zero
+ * within `border` pixels of the image border (samples cannot leave the image).
+ * The camera is static.
+ *
+ * Each sample is traced once for its radiance and replayed (PRB) with the
+ * warps; auxiliary random numbers come from a second PCG32 stream of the sample
+ * (initseq | 2^62): 2 n_aux for the camera ray, then 4 n_aux at every vertex that
+ * draws its 8 path uniforms (light-sample ray first, then BSDF ray), used or not.
+ *
+ * grad_translation: device float [n_shapes][3], accumulated (+=).  rays: device
+ * counter of the rays traced (camera, continuation, shadow, auxiliary and the
+ * warps' own center rays), accumulated; NULL = not wanted.  desc: as for
+ * pt_render_backward (the seed is used for both passes); block_size must be 0 or
+ * 128; no cache, counters or per-sample outputs.  opts: NULL = defaults
+ * (pt_reparam_defaults).  Errors: PT_ERR_ARG (options out of range: 2 <= n_aux <=
+ * 32, 0 < kappa <= 1e6, kernel_scale >= 1, 0 <= power <= 16, miss >= 0, eps > 0,
+ * border > 0, jackknife 0/1), PT_ERR_STATE, PT_ERR_CUDA. */
+typedef struct {
+  int32_t n_aux;        /* auxiliary rays per reparameterized ray (16) */
+  float kappa;          /* vMF concentration of the auxiliary lobe (1000) */
+  float kernel_scale;   /* the weighting kernel is this many times more concentrated (8) */
+  float power;          /* depth-weight exponent: g = (t0 / t)^power (2) */
+  float miss;           /* weight of an auxiliary ray that escapes (0.01) */
+  float eps;            /* floor of the normaliser, per auxiliary ray (1e-4) */
+  float border;         /* camera-warp window width at the image border, pixels (4) */
+  int32_t jackknife;    /* leave-one-out correction of the ratio's 1/N bias (1) */
+} pt_reparam_opts;
+void pt_reparam_defaults(pt_reparam_opts* opts);
+int pt_render_backward_reparam(pt_scene* scene, const pt_render_desc* desc, const pt_params* params,
+                               const pt_reparam_opts* opts, const float* grad_image, float* grad_translation,
+                               unsigned long long* rays, void* stream);
+
 /* Reads (and clears) the scene's device status word after synchronising
  * `stream`: *out = PT_OK or the first PT_ERR_* a kernel recorded. */
 int pt_last_device_status(pt_scene* scene, void* stream, int* out);

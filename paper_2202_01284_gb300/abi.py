@@ -120,6 +120,11 @@ class pt_wavefront_opts(C.Structure):
     _fields_ = [("calls", C.c_int32), ("wave_paths", C.c_int32)]
 
 
+class pt_reparam_opts(C.Structure):
+    _fields_ = [("n_aux", C.c_int32), ("kappa", C.c_float), ("kernel_scale", C.c_float), ("power", C.c_float),
+                ("miss", C.c_float), ("eps", C.c_float), ("border", C.c_float), ("jackknife", C.c_int32)]
+
+
 _lib = None
 _lock = threading.Lock()
 
@@ -146,6 +151,10 @@ SIGNATURES = {
                          C.c_void_p], C.c_int),
     "pt_ckpt_backward": ([C.c_void_p, C.POINTER(pt_render_desc), C.POINTER(pt_params), C.c_void_p, C.c_void_p,
                           C.POINTER(pt_grads), C.c_void_p], C.c_int),
+    "pt_reparam_defaults": ([C.POINTER(pt_reparam_opts)], None),
+    "pt_render_backward_reparam": ([C.c_void_p, C.POINTER(pt_render_desc), C.POINTER(pt_params),
+                                    C.POINTER(pt_reparam_opts), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
+                                   C.c_int),
     "pt_last_device_status": ([C.c_void_p, C.c_void_p, C.POINTER(C.c_int)], C.c_int),
     "pt_status_string": ([C.c_int], C.c_char_p),
     "pt_cache_create": ([C.POINTER(pt_cache_desc), C.POINTER(C.c_void_p)], C.c_int),
@@ -382,6 +391,24 @@ def pt_ckpt_backward(handle: int, desc: pt_render_desc, params: pt_params, ckpt:
                      stream: int = 0) -> None:
     check("pt_ckpt_backward", load().pt_ckpt_backward(handle, C.byref(desc), C.byref(params), ckpt,
                                                       _ptr(grad_image), C.byref(grads), stream or None))
+
+
+def reparam_opts(**kw) -> pt_reparam_opts:
+    """pt_reparam_opts with the library's defaults, overridden by keyword."""
+    o = pt_reparam_opts()
+    load().pt_reparam_defaults(C.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise TypeError(f"unknown reparameterization option {k}")
+        setattr(o, k, v)
+    return o
+
+
+def pt_render_backward_reparam(handle: int, desc: pt_render_desc, params: pt_params, opts: pt_reparam_opts,
+                               grad_image, grad_translation, rays=None, stream: int = 0) -> None:
+    check("pt_render_backward_reparam",
+          load().pt_render_backward_reparam(handle, C.byref(desc), C.byref(params), C.byref(opts), _ptr(grad_image),
+                                            _ptr(grad_translation), _ptr(rays), stream or None))
 
 
 def pt_last_device_status(handle: int, stream: int = 0) -> int:

@@ -17,7 +17,8 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 LIB = os.path.join(HERE, "libptgb.so")
 OBJDIR = os.path.join(HERE, "_build")
 
-CU_SOURCES = ["pt_render.cu", "pt_scene.cu", "pt_nrc.cu", "pt_nrc_tc.cu", "pt_wavefront.cu", "pt_ckpt.cu"]
+CU_SOURCES = ["pt_render.cu", "pt_scene.cu", "pt_nrc.cu", "pt_nrc_tc.cu", "pt_wavefront.cu", "pt_ckpt.cu",
+              "pt_reparam.cu"]
 CPP_SOURCES = ["bvh_build.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -61,6 +61,7 @@ class DeviceScene:
         self.env = (torch.as_tensor(scene.env, dtype=torch.float32).to(dev).contiguous()
                     if scene.env is not None else None)
         self.cameras = list(scene.cameras)
+        self.n_shapes = scene.n_shapes
 
     def info(self) -> dict:
         return abi.pt_scene_get_info(self.handle)
@@ -113,6 +114,23 @@ class DeviceScene:
         desc = self._desc(cams, st, seed=seed, counters=counters)
         abi.pt_render_backward(self.handle, desc, p, grad_image.contiguous(), g,
                                torch.cuda.current_stream(grad_image.device).cuda_stream)
+
+    def backward_reparam(self, st: RenderSettings, grad_image, g_translation, cams=None, albedo=None,
+                         textures=None, roughness=None, env=None, seed=None, rays=None, **opts):
+        """pt_render_backward_reparam: accumulate into g_translation [n_shapes, 3] the
+        gradient of sum(grad_image * image) with respect to one translation per shape,
+        by reparameterized PRB (Sec. 4.7).  opts: pt_reparam_opts fields; rays: optional
+        int64 device counter of the rays traced."""
+        cams = list(cams) if cams is not None else self.cameras
+        p = abi.params_struct(self.albedo if albedo is None else albedo,
+                              self.textures if textures is None else textures,
+                              self.roughness if roughness is None else roughness, env)
+        desc = self._desc(cams, st, seed=seed)
+        if g_translation.dtype != torch.float32 or not g_translation.is_contiguous() or \
+                tuple(g_translation.shape) != (self.n_shapes, 3):
+            raise ValueError("g_translation must be a contiguous float32 [n_shapes, 3] tensor")
+        abi.pt_render_backward_reparam(self.handle, desc, p, abi.reparam_opts(**opts), grad_image.contiguous(),
+                                       g_translation, rays, torch.cuda.current_stream(grad_image.device).cuda_stream)
 
     # ------------------------------------------------------------------ wavefront variant
     def wavefront_forward(self, st: RenderSettings, calls: int = abi.PT_WF_TRACED, wave_paths: int = 0, cams=None,

@@ -1,0 +1,100 @@
+"""GPU parity of reparameterized PRB (translation gradients, Sec. 4.7) vs the FP64 oracle.
+
+The CUDA kernel computes the gradients in reverse mode (PRB replay, closed-form
+warp-field coefficients); the oracle computes the same estimator in forward mode
+(chart dual numbers for the warp divergence).  Same seeds, same options, same
+auxiliary random numbers.  FP32 against FP64 can flip an auxiliary ray's hit at a
+triangle edge, so the comparison is on the accumulated gradient vector.
+"""
+import numpy as np
+import pytest
+
+from paper_2202_01284_gb300 import scenes as S
+
+from parity import cosine
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2202_01284_gb300 import abi
+    abi.load()
+    return abi
+
+
+def _compare(oracle_mod, sc, spp, max_depth, seed, gi, rr_depth=-1, layout=1, **opts):
+    from paper_2202_01284_gb300.render import DeviceScene, RenderSettings
+    cam = sc.cameras[0]
+    ds = DeviceScene(sc, layout=layout)
+    st = RenderSettings(width=cam.width, height=cam.height, spp=spp, max_depth=max_depth, rr_depth=rr_depth,
+                        seed=seed)
+    g = torch.zeros((sc.n_shapes, 3), device="cuda")
+    rays = torch.zeros(1, dtype=torch.int64, device="cuda")
+    ds.backward_reparam(st, torch.as_tensor(gi[None], dtype=torch.float32, device="cuda"), g, rays=rays, **opts)
+    torch.cuda.synchronize()
+    assert ds.status() == 0
+    r = oracle_mod.render_in(cam, spp, max_depth, seed, rr_depth, True)
+    g_ref, _, _ = oracle_mod.grad_reparam(oracle_mod.OracleScene(sc), r, gi, **opts)
+    gg = g.cpu().numpy().astype(np.float64)
+    c = cosine(gg.ravel(), g_ref.ravel())
+    rel = np.abs(gg - g_ref).max() / np.abs(g_ref).max()
+    print(f"{sc.name}: cosine {c:.7f} max rel {rel:.2e} rays {int(rays.item())}\n gpu {gg.ravel()}\n ref {g_ref.ravel()}")
+    return gg, g_ref, c, rel, int(rays.item())
+
+
+def test_reparam_parity_shadow_scene(lib, oracle_mod):
+    sc = S.shadow_scene()
+    gi = np.random.default_rng(2).random((64, 64, 3)) + 0.5
+    gg, g_ref, c, rel, rays = _compare(oracle_mod, sc, 16, 3, 21, gi)
+    assert c >= 0.99999
+    assert rel < 1e-4  # measured 4e-6
+    assert rays > 64 * 64 * 16
+
+
+def test_reparam_parity_camera_rays(lib, oracle_mod):
+    """Camera-ray warps only (black occluder over a uniform sky), windowed at the border."""
+    sc = S.occluder_sky(center=(0.5, 0.2), side=0.6)   # near the right border: the window matters
+    gi = np.random.default_rng(3).random((64, 64, 3))
+    _, _, c, rel, _ = _compare(oracle_mod, sc, 16, 2, 5, gi)
+    assert c >= 0.99999
+    assert rel < 1e-4  # measured 9e-6
+
+
+def test_reparam_parity_cornell_multibounce(lib, oracle_mod):
+    """Six shapes, indirect bounces, no jackknife and other options: every path vertex warps."""
+    sc = S.cornell(width=48, height=48)
+    gi = np.random.default_rng(4).random((48, 48, 3))
+    _, _, c, rel, _ = _compare(oracle_mod, sc, 4, 4, 9, gi, layout=0, n_aux=8, kappa=2000.0, jackknife=0,
+                               power=4.0)
+    assert c >= 0.99999
+    assert rel < 1e-3  # measured 5e-5
+    _, _, c, rel, _ = _compare(oracle_mod, sc, 4, 4, 9, gi, rr_depth=2)
+    assert c >= 0.99999
+    assert rel < 1e-3
+
+
+def test_reparam_arguments(lib):
+    from paper_2202_01284_gb300.render import DeviceScene, RenderSettings
+    sc = S.shadow_scene(width=16, height=16)
+    ds = DeviceScene(sc)
+    st = RenderSettings(width=16, height=16, spp=2, max_depth=2, rr_depth=-1, seed=1)
+    gi = torch.ones((1, 16, 16, 3), device="cuda")
+    g = torch.zeros((3, 3), device="cuda")
+    for bad in (dict(n_aux=1), dict(n_aux=33), dict(kappa=0.0), dict(kernel_scale=0.5), dict(eps=0.0),
+                dict(miss=-1.0), dict(border=0.0), dict(jackknife=2), dict(power=-1.0)):
+        with pytest.raises(lib.PtError):
+            ds.backward_reparam(st, gi, g, **bad)
+    with pytest.raises(ValueError):
+        ds.backward_reparam(st, gi, torch.zeros((2, 3), device="cuda"))
+    from dataclasses import replace
+    with pytest.raises(lib.PtError):
+        ds.backward_reparam(replace(st, block_size=256), gi, g)
+    # zero loss gradient: nothing is accumulated
+    ds.backward_reparam(st, torch.zeros_like(gi), g)
+    torch.cuda.synchronize()
+    assert not g.any()
