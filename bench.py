@@ -75,6 +75,9 @@ def parse():
                     help="radiance-cache MLP inference throughput, tcgen05 vs mma.sync engines (own JSON line)")
     ap.add_argument("--ckpt", action="store_true",
                     help="PRB vs reverse mode with checkpoints, one gradient step each (own JSON line)")
+    ap.add_argument("--reparam", action="store_true",
+                    help="reparameterized PRB: shape-translation gradients through visibility (own JSON line)")
+    ap.add_argument("--reparam-spp", type=int, default=16)
     ap.add_argument("--peaks", action="store_true",
                     help="microbenchmarks of the memory-side roofs (L2-resident reads, atomics) as a JSON line")
     ap.add_argument("--small", action="store_true",
@@ -640,6 +643,110 @@ def run_ckpt_experiment(args):
     ck.close()
 
 
+def run_reparam_experiment(args):
+    """Reparameterized PRB (translation gradients of the 33 shapes through
+    visibility) on the throughput scene at --reparam-spp samples per pixel: one
+    gradient step = forward image, L2-loss image gradient, reparameterized
+    adjoint.  Rays = every ray the adjoint traces (path, shadow, auxiliary and
+    the warps' center rays), counted by the kernel itself.  Own JSON line."""
+    import torch
+
+    from paper_2202_01284_gb300 import abi
+    from paper_2202_01284_gb300.render import DeviceScene
+    from dataclasses import replace
+    abi.load()
+    dev = torch.device("cuda", 0)
+    sc, tgt_tex = make_workload(small=args.small)
+    layout = abi.PT_BVH_WIDE if args.bvh == "wide" else abi.PT_BVH_BINARY
+    ds = DeviceScene(sc, layout=layout, device=dev)
+    spp = 4 if args.small else args.reparam_spp
+    st = replace(settings(args, 11), spp=spp, block_size=0, prb_mode=0)
+    target = ds.forward(replace(st, seed=77), textures=[torch.as_tensor(tgt_tex, device=dev)]).clone()
+    img = torch.empty_like(target)
+    grad_img = torch.empty_like(target)
+    g_t = torch.zeros((sc.n_shapes, 3), device=dev)
+    rays = torch.zeros(1, dtype=torch.int64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(ev, count=None):
+        ev[0].record(stream)
+        ds.forward(st, out=img)
+        torch.sub(img, target, out=grad_img)
+        grad_img.mul_(2.0 / img.numel())
+        ev[1].record(stream)
+        ds.backward_reparam(replace(st, seed=12), grad_img, g_t, rays=count)
+        ev[2].record(stream)
+
+    dummy = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    for _ in range(max(3, args.warmup)):
+        step(dummy)
+    rays.zero_()
+    step(dummy, rays)
+    torch.cuda.synchronize()
+    rays_step = int(rays.item())
+    clocks = ClockSampler(0)
+    clocks.start()
+    evs = []
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        step(ev)
+        evs.append(ev)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    fwd_ms = statistics.mean(e[0].elapsed_time(e[1]) for e in evs)
+    rp_ms = statistics.mean(e[1].elapsed_time(e[2]) for e in evs)
+    # node / triangle visits of the same launch (instrumented variant, after timing)
+    cnt = torch.zeros(abi.PT_N_COUNTERS, dtype=torch.int64, device=dev)
+    gt2 = torch.zeros_like(g_t)
+    p = abi.params_struct(ds.albedo, ds.textures, ds.roughness, None)
+    desc = ds._desc(ds.cameras, replace(st, seed=12), counters=cnt)
+    abi.pt_render_backward_reparam(ds.handle, desc, p, abi.reparam_opts(), grad_img, gt2, None, stream.cuda_stream)
+    torch.cuda.synchronize()
+    c = cnt.cpu().numpy()
+    flops = FLOPS_PER_NODE[args.bvh] * int(c[3]) + FLOPS_PER_TRI * int(c[4])
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = clk.get("sm_mhz") or 1477.0
+    peak_tflops = sms * 128 * 2 * mhz * 1e6 / 1e12
+    achieved = flops / (rp_ms / 1e3) / 1e12
+    # the plain PRB adjoint of the same samples, for scale (texture + roughness gradients)
+    g_tex = torch.zeros_like(ds.textures[0])
+    g_rough = torch.zeros_like(ds.roughness)
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ds.backward(replace(st, seed=12), grad_img, g_textures=[g_tex], g_roughness=g_rough)
+    flush.fill_(0.0)
+    e[0].record(stream)
+    ds.backward(replace(st, seed=12), grad_img, g_textures=[g_tex], g_roughness=g_rough)
+    e[1].record(stream)
+    torch.cuda.synchronize()
+    plain_ms = e[0].elapsed_time(e[1])
+    opts = abi.reparam_opts()
+    line = {"metric": "reparameterized PRB (shape-translation gradients through visibility), Mrays/s",
+            "value": round(rays_step / rp_ms / 1e3, 2), "unit": "Mrays/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": round(fwd_ms + rp_ms, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": (f"spheres32x5120 + ground (196,608 tris, 33 shapes), {st.width}x{st.height}, "
+                                    f"{spp} spp, depth 8, RR from 3; translation gradients of all 33 shapes"),
+                       "l2": "flushed before each timed step", "forward_ms": round(fwd_ms, 3),
+                       "reparam_adjoint_ms": round(rp_ms, 3), "plain_prb_adjoint_ms": round(plain_ms, 3),
+                       "reparam_over_plain": round(rp_ms / plain_ms, 2), "rays_per_step": rays_step,
+                       "rays_per_sample": round(rays_step / (st.width * st.height * spp), 2),
+                       "node_visits_per_ray": round(int(c[3]) / max(rays_step, 1), 2),
+                       "tri_tests_per_ray": round(int(c[4]) / max(rays_step, 1), 2),
+                       "options": {k: getattr(opts, k) for k, _ in opts._fields_},
+                       "grad_translation_norm": float(g_t.norm().item())},
+            "roofline": {"bound": "alu", "kernel": "reparam_kernel", "achieved": round(achieved, 3),
+                         "peak": round(peak_tflops, 2), "unit": "TFLOP/s", "frac": round(achieved / peak_tflops, 4),
+                         "traffic": None,
+                         "work": f"{FLOPS_PER_NODE[args.bvh]}/node visit + {FLOPS_PER_TRI}/triangle test (counted "
+                                 "by the instrumented launch; warp-field arithmetic not counted)",
+                         "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 x median SM clock {mhz} MHz"},
+            "gpu_launches": 2 * args.steps,
+            "clocks": clk}
+    print(json.dumps(line), flush=True)
+
+
 MLP_FLOPS_PER_QUERY = 2 * (5 * 64 * 64 + 64 * 3)  # five 64x64 layers + the 64x3 head
 
 
@@ -941,6 +1048,8 @@ def main():
         run_wavefront_experiment(args)
     elif args.ckpt:
         run_ckpt_experiment(args)
+    elif args.reparam:
+        run_reparam_experiment(args)
     elif args.mlp:
         run_mlp_experiment(args)
     else:

@@ -45,15 +45,18 @@ namespace {
 constexpr int kMaxAux = 32;
 
 struct RpOpts {
-  int n_aux, jackknife, smem;
+  int n_aux, jackknife, smem, group;  // group: lanes per cooperative warp, a power of two >= n_aux
   float kappa, kk, power, miss, eps, border, e2k;
 };
 
-template <int LAYOUT>
-__device__ __forceinline__ Hit closest(const DevScene& S, float3 o, float3 d, float tmax, bool any,
-                                       Counters<false>& cnt) {
-  return LAYOUT == PT_BVH_WIDE ? trace_wide<false>(S, o, d, tmax, any, cnt)
-                               : trace_binary<false>(S, o, d, tmax, any, cnt);
+// One out-of-line traversal shared by all call sites (path, shadow, center and
+// auxiliary rays): inlining it at each of them multiplied the kernel's code and
+// its instruction-cache misses.
+template <int LAYOUT, bool INSTR>
+__device__ __noinline__ Hit closest(const DevScene& S, float3 o, float3 d, float tmax, bool any,
+                                    Counters<INSTR>& cnt) {
+  return LAYOUT == PT_BVH_WIDE ? trace_wide<INSTR>(S, o, d, tmax, any, cnt)
+                               : trace_binary<INSTR>(S, o, d, tmax, any, cnt);
 }
 
 __device__ __forceinline__ int tri_shape(const DevScene& S, int pos) {
@@ -109,111 +112,143 @@ struct GradOut {
   }
 };
 
-// One reparameterized ray: trace its N auxiliary rays and scatter R times the
-// coefficient of every shape's translation velocity.  Consumes 2N uniforms of
-// `rng` whether or not R is zero.  Returns the rays traced.
-template <int LAYOUT>
-__device__ __noinline__ unsigned warp_scatter(const LaunchArgs& A, const RpOpts& K, Pcg32& rng, float3 o, float3 u,
-                                              int s_o, float3 m, int cam, float R, GradOut& G) {
-  const Pcg32 r0 = rng;
-  for (int i = 0; i < 2 * K.n_aux; ++i) rng.next();
-  if (R == 0.0f) return 0;
-  const DevScene& S = A.scene;
-  Counters<false> cnt;
-  const Hit h0 = closest<LAYOUT>(S, o, u, INFINITY, false, cnt);
-  const float t0 = h0.pos >= 0 ? h0.t : INFINITY;
-  const Frame fr = make_frame(u);
-  const float dk = K.kk - K.kappa;
-  float alpha[kMaxAux], dist[kMaxAux];
-  int pos[kMaxAux];
-  float D = 0.0f;
-  float3 P = f3(0.f, 0.f, 0.f);
-  Pcg32 r = r0;
-  for (int i = 0; i < K.n_aux; ++i) {
-    const float a0 = r.uniform(), a1 = r.uniform();
-    float c1;
-    const float3 w = vmf_dir(fr, a0, a1, K, c1);
-    const Hit h = closest<LAYOUT>(S, o, w, INFINITY, false, cnt);
-    float g = K.miss;
-    if (h.pos >= 0) g = t0 < INFINITY ? powf(t0 / fmaxf(h.t, 1e-3f * t0), K.power) : 1.0f;
-    const float a = expf(dk * c1) * g;
-    alpha[i] = a;
-    pos[i] = h.pos;
-    dist[i] = h.t;
-    D += a;
-    P = P + (w - u * dot3(u, w)) * a;
+constexpr unsigned kFull = 0xffffffffu;
+
+// Jump a PCG32 stream ahead by `delta` draws in O(log delta) (Brown 1994,
+// "Random number generation with arbitrary strides": compose the LCG step).
+__device__ __forceinline__ void pcg_advance(Pcg32& r, unsigned long long delta) {
+  unsigned long long acc_mult = 1ull, acc_plus = 0ull, cur_mult = 6364136223846793005ull, cur_plus = r.inc;
+  while (delta) {
+    if (delta & 1ull) {
+      acc_mult *= cur_mult;
+      acc_plus = acc_plus * cur_mult + cur_plus;
+    }
+    cur_plus = (cur_mult + 1ull) * cur_plus;
+    cur_mult *= cur_mult;
+    delta >>= 1;
   }
-  D += K.n_aux * K.eps;
-  // leave-one-out sums: S1 = sum_j 1 / D_{-j}, SP = sum_j P_{-j} / D_{-j}^2
-  float S1 = 0.0f;
-  float3 SP = f3(0.f, 0.f, 0.f);
-  if (K.jackknife) {
-    r = r0;
-    for (int j = 0; j < K.n_aux; ++j) {
+  r.state = acc_mult * r.state + acc_plus;
+}
+
+// A reparameterized ray waiting for its warp: origin, direction, cosine/measure
+// covector, origin shape (-1: camera), camera index for the window (-1: none),
+// weight R, its own hit distance and the auxiliary stream at its first uniform.
+struct WarpRay {
+  float3 o, u, m;
+  int s_o, cam;
+  float R, t0;
+  unsigned long long st, inc;
+};
+
+__device__ __forceinline__ float3 shfl3(float3 v, int src) {
+  return f3(__shfl_sync(kFull, v.x, src), __shfl_sync(kFull, v.y, src), __shfl_sync(kFull, v.z, src));
+}
+// sum over the aligned group of `gs` lanes (gs a power of two)
+__device__ __forceinline__ float group_sum(float v, int gs) {
+  for (int off = gs >> 1; off > 0; off >>= 1) v += __shfl_xor_sync(kFull, v, off);
+  return v;
+}
+__device__ __forceinline__ float3 group_sum3(float3 v, int gs) {
+  return f3(group_sum(v.x, gs), group_sum(v.y, gs), group_sum(v.z, gs));
+}
+
+// Warp-cooperative warps: called by all 32 lanes together.  The lanes form
+// 32 / gs groups of gs >= N lanes; each round every group takes one pending ray
+// of some lane, and its lane j traces auxiliary ray j of that ray (the rays of a
+// lobe are coherent), so the reductions of the warp estimator are shuffles.
+template <int LAYOUT, bool INSTR>
+__device__ __noinline__ unsigned process_warps(const LaunchArgs& A, const RpOpts& K, bool has, const WarpRay& mine,
+                                               GradOut& G, Counters<INSTR>& cnt) {
+  const DevScene& S = A.scene;
+  const int lane = lane_id(), gs = K.group, grp = lane / gs, j = lane % gs;
+  const int ng = 32 / gs;
+  const float dk = K.kk - K.kappa, n = (float)K.n_aux;
+  unsigned rays = 0;
+  unsigned pend = __ballot_sync(kFull, has);
+  while (pend) {
+    unsigned p = pend;
+    for (int g = 0; g < grp && p; ++g) p &= p - 1;
+    const int src = p ? __ffs(p) - 1 : -1;
+    for (int g = 0; g < ng && pend; ++g) pend &= pend - 1;
+    const int sl = src >= 0 ? src : lane;
+    WarpRay w;
+    w.o = shfl3(mine.o, sl);
+    w.u = shfl3(mine.u, sl);
+    w.m = shfl3(mine.m, sl);
+    w.s_o = __shfl_sync(kFull, mine.s_o, sl);
+    w.cam = __shfl_sync(kFull, mine.cam, sl);
+    w.R = __shfl_sync(kFull, mine.R, sl);
+    w.t0 = __shfl_sync(kFull, mine.t0, sl);
+    w.st = __shfl_sync(kFull, mine.st, sl);
+    w.inc = __shfl_sync(kFull, mine.inc, sl);
+    const bool on = src >= 0 && j < K.n_aux;
+    float alpha = 0.0f, t = 0.0f;
+    int pos = -1;
+    float3 wi = w.u, pi = f3(0.f, 0.f, 0.f);
+    if (on) {
+      Pcg32 r;
+      r.state = w.st;
+      r.inc = w.inc;
+      pcg_advance(r, 2ull * (unsigned long long)j);
       const float a0 = r.uniform(), a1 = r.uniform();
       float c1;
-      const float3 w = vmf_dir(fr, a0, a1, K, c1);
-      const float Dj = D - alpha[j] - K.eps;
-      const float3 Pj = P - (w - u * dot3(u, w)) * alpha[j];
-      S1 += 1.0f / Dj;
-      SP = SP + Pj * (1.0f / (Dj * Dj));
-    }
-  }
-  float b = 1.0f;
-  float3 gb = f3(0.f, 0.f, 0.f);
-  if (cam >= 0) b = cam_window(A, A.cams[cam], u, K.border, gb);
-  const float3 mp = m - u * dot3(u, m);
-  const float n = (float)K.n_aux;
-  r = r0;
-  for (int i = 0; i < K.n_aux; ++i) {
-    const float a0 = r.uniform(), a1 = r.uniform();
-    if (pos[i] < 0) continue;
-    const int si = tri_shape(S, pos[i]);
-    if (si == s_o) continue;
-    float c1;
-    const float3 w = vmf_dir(fr, a0, a1, K, c1);
-    const float3 nrm = tri_normal(S, pos[i]);
-    const float nu = dot3(nrm, u);
-    const float di = dot3(nrm, w) * dist[i];
-    const float3 p = w - u * dot3(u, w);
-    // A_i: the part of H_i that does not depend on the sample set
-    const float3 Ai = (mp - u * 2.0f + p * K.kk) * (nu * b) + (nrm - u * nu) * b + gb * nu;
-    const float kb = K.kk * b * nu;
-    float3 coef = Ai * (1.0f / D) - P * (kb / (D * D));
-    if (K.jackknife) {
-      const float Dm = D - alpha[i] - K.eps;
-      const float3 Pm = P - p * alpha[i];
-      const float3 loo = Ai * (S1 - 1.0f / Dm) - (SP - Pm * (1.0f / (Dm * Dm))) * kb;
-      coef = coef * n - loo * ((n - 1.0f) / n);
-    }
-    const float3 g = coef * (R * alpha[i] / di);
-    G.add(si, g);
-    if (s_o >= 0) G.add(s_o, -g);
-  }
-  return 1u + (unsigned)K.n_aux;
-}
-
-template <int LAYOUT>
-__device__ __forceinline__ float3 sample_radiance(const LaunchArgs& A, PathState& P, const PixelOf& px, int si,
-                                                  GradSink& sink, Counters<false>& cnt, unsigned& rays) {
-  path_start<false>(A, P, A.seed, px.cam, px.px, px.py, si, px.pix, cnt);
-  P.Lrem = f3(0.f, 0.f, 0.f);
-  const float3 z = f3(0.f, 0.f, 0.f);
-  for (;;) {
-    const Hit hit = closest<LAYOUT>(A.scene, P.ro, P.rd, INFINITY, false, cnt);
-    ++rays;
-    if (!path_shade<false, false, false, PT_DISPATCH_SWITCH>(A, P, hit, false, z, sink, cnt)) break;
-    bool occ = false;
-    if (P.has_shadow) {
-      occ = closest<LAYOUT>(A.scene, P.so, P.sd, P.stmax, true, cnt).pos >= 0;
+      wi = vmf_dir(make_frame(w.u), a0, a1, K, c1);
+      const Hit h = closest<LAYOUT, INSTR>(S, w.o, wi, INFINITY, false, cnt);
       ++rays;
+      float g = K.miss;
+      if (h.pos >= 0) g = w.t0 < INFINITY ? powf(w.t0 / fmaxf(h.t, 1e-3f * w.t0), K.power) : 1.0f;
+      alpha = expf(dk * c1) * g;
+      pos = h.pos;
+      t = h.t;
+      pi = wi - w.u * dot3(w.u, wi);
     }
-    if (!path_finish<false, false, false>(A, P, occ, false, z, sink, cnt)) break;
+    const float D = group_sum(alpha, gs) + n * K.eps;
+    const float3 P = group_sum3(pi * alpha, gs);
+    float S1 = 0.0f;
+    float3 SP = f3(0.f, 0.f, 0.f);
+    if (K.jackknife) {
+      const float Dj = D - alpha - K.eps;
+      const float3 Pj = P - pi * alpha;
+      S1 = group_sum(on ? 1.0f / Dj : 0.0f, gs);
+      SP = group_sum3(on ? Pj * (1.0f / (Dj * Dj)) : f3(0.f, 0.f, 0.f), gs);
+    }
+    float3 gv = f3(0.f, 0.f, 0.f);
+    int si = -1;
+    if (on && pos >= 0) si = tri_shape(S, pos);
+    const bool contrib = si >= 0 && si != w.s_o;
+    if (contrib) {
+      float b = 1.0f;
+      float3 gb = f3(0.f, 0.f, 0.f);
+      if (w.cam >= 0) b = cam_window(A, A.cams[w.cam], w.u, K.border, gb);
+      const float3 mp = w.m - w.u * dot3(w.u, w.m);
+      const float3 nrm = tri_normal(S, pos);
+      const float nu = dot3(nrm, w.u);
+      const float di = dot3(nrm, wi) * t;
+      // A_i: the part of H_i that does not depend on the sample set
+      const float3 Ai = (mp - w.u * 2.0f + pi * K.kk) * (nu * b) + (nrm - w.u * nu) * b + gb * nu;
+      const float kb = K.kk * b * nu;
+      float3 coef = Ai * (1.0f / D) - P * (kb / (D * D));
+      if (K.jackknife) {
+        const float Dm = D - alpha - K.eps;
+        const float3 Pm = P - pi * alpha;
+        const float3 loo = Ai * (S1 - 1.0f / Dm) - (SP - Pm * (1.0f / (Dm * Dm))) * kb;
+        coef = coef * n - loo * ((n - 1.0f) / n);
+      }
+      gv = coef * (w.R * alpha / di);
+      float v[3] = {gv.x, gv.y, gv.z};
+      if (warp_aggregate<3>((unsigned)si, v)) G.add(si, f3(v[0], v[1], v[2]));
+    }
+    // the origin moves with its own shape: minus the group's total
+    const float3 go = group_sum3(gv, gs);
+    if (j == 0 && src >= 0 && w.s_o >= 0 && (go.x != 0.0f || go.y != 0.0f || go.z != 0.0f)) G.add(w.s_o, -go);
   }
-  return P.L;
+  return rays;
 }
 
-template <int LAYOUT>
+// Lockstep per-lane state machine: each iteration every lane advances its own
+// path by one vertex (radiance pass, then PRB replay of the same sample), then
+// the whole warp processes the reparameterized rays the lanes posted.
+template <int LAYOUT, bool INSTR>
 __global__ void __launch_bounds__(128) reparam_kernel(const __grid_constant__ LaunchArgs A, const RpOpts K,
                                                       float* __restrict__ grad_t, unsigned long long* rays_out) {
   extern __shared__ float s_grad[];
@@ -223,75 +258,150 @@ __global__ void __launch_bounds__(128) reparam_kernel(const __grid_constant__ La
     __syncthreads();
   }
   GradOut G{K.smem ? s_grad : grad_t};
+  const DevScene& S = A.scene;
   const long long unit = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   PixelOf px{};
   const bool valid = unit_pixel(A, unit, crop_tile(A), px);
   unsigned rays = 0;
+  Counters<INSTR> cnt;
+  if constexpr (INSTR)
+    for (int i = 0; i < 8; ++i) cnt.c[i] = 0;
+  const float3 z = f3(0.f, 0.f, 0.f);
+  float3 dl = z, fwd = z;
   if (valid) {
-    const int lane = (int)(unit & (A.lanes_per_pixel - 1));
     const float inv = 1.0f / (float)A.spp;
-    const float3 dl = f3(A.grad_image[3 * px.pix] * inv, A.grad_image[3 * px.pix + 1] * inv,
-                         A.grad_image[3 * px.pix + 2] * inv);
+    dl = f3(A.grad_image[3 * px.pix] * inv, A.grad_image[3 * px.pix + 1] * inv, A.grad_image[3 * px.pix + 2] * inv);
     const DevCamera& cam = A.cams[px.cam];
-    const float3 fwd = f3(cam.fx, cam.fy, cam.fz);
-    const float3 z = f3(0.f, 0.f, 0.f);
-    Counters<false> cnt;
-    GradSink sink;
-    PathState P;
-    for (int si = lane; si < A.spp; si += A.lanes_per_pixel) {
-      const float3 L = sample_radiance<LAYOUT>(A, P, px, si, sink, cnt, rays);
-      // replay with the same primary stream; auxiliary stream initseq | 2^62
-      path_start<false>(A, P, A.seed, px.cam, px.px, px.py, si, px.pix, cnt);
-      P.Lrem = L;
-      const unsigned long long pixel = (unsigned long long)px.py * (unsigned long long)A.width + px.px;
-      Pcg32 aux;
-      aux.seed(A.seed, ((unsigned long long)px.cam << 40) | (pixel << 12) | (unsigned long long)si | (1ull << 62));
-      rays += warp_scatter<LAYOUT>(A, K, aux, P.ro, P.rd, -1, fwd * (-3.0f / dot3(fwd, P.rd)), px.cam,
-                                   dot3(dl, L), G);
-      for (;;) {
-        const Hit hit = closest<LAYOUT>(A.scene, P.ro, P.rd, INFINITY, false, cnt);
-        ++rays;
-        const bool block = hit.pos >= 0 && P.depth < A.max_depth;
-        int s_o = -1;
-        float3 n_s = z;
-        if (hit.pos >= 0) {
-          s_o = tri_shape(A.scene, hit.pos);
-          const float3 ng = tri_normal(A.scene, hit.pos);
-          n_s = dot3(ng, P.rd) < 0.0f ? ng : -ng;
-        }
-        const bool alive = path_shade<false, false, false, PT_DISPATCH_SWITCH>(A, P, hit, false, z, sink, cnt);
-        Pcg32 aux_nee = aux, aux_bsdf = aux;
-        if (block) {
-          for (int i = 0; i < 2 * K.n_aux; ++i) aux_bsdf.next();
-          aux = aux_bsdf;
-          for (int i = 0; i < 2 * K.n_aux; ++i) aux.next();
-        }
-        if (!alive) break;
+    fwd = f3(cam.fx, cam.fy, cam.fz);
+  }
+  enum { RAD = 0, REPLAY = 1, DONE = 2 };
+  int phase = DONE;
+  int si = (int)(unit & (A.lanes_per_pixel - 1));
+  GradSink sink;
+  PathState P;
+  Pcg32 aux;
+  aux.state = aux.inc = 0ull;
+  float3 L_total = z;
+  bool cached = false;
+  Hit next{};
+  const unsigned long long n2 = 2ull * (unsigned long long)K.n_aux;
+  if (valid && si < A.spp) {
+    path_start<INSTR>(A, P, A.seed, px.cam, px.px, px.py, si, px.pix, cnt);
+    P.Lrem = z;
+    phase = RAD;
+  }
+  for (;;) {
+    if (!__any_sync(kFull, phase != DONE)) break;
+    WarpRay w0{}, w1{};
+    bool h0 = false, h1 = false;
+    if (phase == RAD) {
+      const Hit hit = closest<LAYOUT, INSTR>(S, P.ro, P.rd, INFINITY, false, cnt);
+      ++rays;
+      bool more = path_shade<false, false, INSTR, PT_DISPATCH_SWITCH>(A, P, hit, false, z, sink, cnt);
+      if (more) {
         bool occ = false;
         if (P.has_shadow) {
-          occ = closest<LAYOUT>(A.scene, P.so, P.sd, P.stmax, true, cnt).pos >= 0;
+          occ = closest<LAYOUT, INSTR>(S, P.so, P.sd, P.stmax, true, cnt).pos >= 0;
           ++rays;
         }
-        const bool diffuse = P.mtype == PT_BSDF_DIFFUSE;
-        if (block && diffuse && P.has_shadow && !occ)
-          rays += warp_scatter<LAYOUT>(A, K, aux_nee, P.so, P.sd, s_o, n_s * (1.0f / dot3(n_s, P.sd)), -1,
-                                       dot3(dl, P.c_nee), G);
-        const bool cont = path_finish<false, false, false>(A, P, occ, false, z, sink, cnt);
-        if (!cont) break;
-        if (block && diffuse) {
-          const float3 lr = f3(fmaxf(P.Lrem.x, 0.f), fmaxf(P.Lrem.y, 0.f), fmaxf(P.Lrem.z, 0.f));
-          rays += warp_scatter<LAYOUT>(A, K, aux_bsdf, P.ro, P.rd, s_o, n_s * (1.0f / dot3(n_s, P.rd)), -1,
-                                       dot3(dl, lr), G);
+        more = path_finish<false, false, INSTR>(A, P, occ, false, z, sink, cnt);
+      }
+      if (!more) {
+        // replay the sample: same primary stream, auxiliary stream initseq | 2^62
+        L_total = P.L;
+        path_start<INSTR>(A, P, A.seed, px.cam, px.px, px.py, si, px.pix, cnt);
+        P.Lrem = L_total;
+        const unsigned long long pixel = (unsigned long long)px.py * (unsigned long long)A.width + px.px;
+        aux.seed(A.seed, ((unsigned long long)px.cam << 40) | (pixel << 12) | (unsigned long long)si | (1ull << 62));
+        next = closest<LAYOUT, INSTR>(S, P.ro, P.rd, INFINITY, false, cnt);
+        ++rays;
+        cached = true;
+        const float R = dot3(dl, L_total);
+        if (R != 0.0f) {
+          w0 = WarpRay{P.ro, P.rd, fwd * (-3.0f / dot3(fwd, P.rd)), -1, px.cam, R,
+                       next.pos >= 0 ? next.t : INFINITY, aux.state, aux.inc};
+          h0 = true;
+        }
+        pcg_advance(aux, n2);
+        phase = REPLAY;
+      }
+    } else if (phase == REPLAY) {
+      Hit hit;
+      if (cached) {
+        hit = next;
+        cached = false;
+      } else {
+        hit = closest<LAYOUT, INSTR>(S, P.ro, P.rd, INFINITY, false, cnt);
+        ++rays;
+      }
+      const bool block = hit.pos >= 0 && P.depth < A.max_depth;
+      int s_o = -1;
+      float3 n_s = z;
+      if (hit.pos >= 0) {
+        s_o = tri_shape(S, hit.pos);
+        const float3 ng = tri_normal(S, hit.pos);
+        n_s = dot3(ng, P.rd) < 0.0f ? ng : -ng;
+      }
+      bool more = path_shade<false, false, INSTR, PT_DISPATCH_SWITCH>(A, P, hit, false, z, sink, cnt);
+      Pcg32 aux_nee = aux, aux_bsdf = aux;
+      if (block) {
+        pcg_advance(aux_bsdf, n2);
+        pcg_advance(aux, 2ull * n2);
+      }
+      if (more) {
+        bool occ = false;
+        if (P.has_shadow) {
+          occ = closest<LAYOUT, INSTR>(S, P.so, P.sd, P.stmax, true, cnt).pos >= 0;
+          ++rays;
+        }
+        const bool diffuse = block && P.mtype == PT_BSDF_DIFFUSE;
+        if (diffuse && P.has_shadow && !occ) {
+          const float R = dot3(dl, P.c_nee);
+          if (R != 0.0f) {
+            const Hit hl = closest<LAYOUT, INSTR>(S, P.so, P.sd, INFINITY, false, cnt);
+            ++rays;
+            w0 = WarpRay{P.so, P.sd, n_s * (1.0f / dot3(n_s, P.sd)), s_o, -1, R,
+                         hl.pos >= 0 ? hl.t : INFINITY, aux_nee.state, aux_nee.inc};
+            h0 = true;
+          }
+        }
+        more = path_finish<false, false, INSTR>(A, P, occ, false, z, sink, cnt);
+        if (more && diffuse) {
+          const float R = dot3(dl, f3(fmaxf(P.Lrem.x, 0.f), fmaxf(P.Lrem.y, 0.f), fmaxf(P.Lrem.z, 0.f)));
+          if (R != 0.0f) {
+            next = closest<LAYOUT, INSTR>(S, P.ro, P.rd, INFINITY, false, cnt);
+            ++rays;
+            cached = true;
+            w1 = WarpRay{P.ro, P.rd, n_s * (1.0f / dot3(n_s, P.rd)), s_o, -1, R,
+                         next.pos >= 0 ? next.t : INFINITY, aux_bsdf.state, aux_bsdf.inc};
+            h1 = true;
+          }
+        }
+      }
+      if (!more) {
+        si += A.lanes_per_pixel;
+        phase = DONE;
+        if (si < A.spp) {
+          path_start<INSTR>(A, P, A.seed, px.cam, px.px, px.py, si, px.pix, cnt);
+          P.Lrem = z;
+          phase = RAD;
         }
       }
     }
+    rays += process_warps<LAYOUT, INSTR>(A, K, h0, w0, G, cnt);
+    rays += process_warps<LAYOUT, INSTR>(A, K, h1, w1, G, cnt);
   }
   if (K.smem) {
     __syncthreads();
     for (int i = threadIdx.x; i < n3; i += blockDim.x)
       if (s_grad[i] != 0.0f) atomicAdd(&grad_t[i], s_grad[i]);
   }
-  if (rays_out && rays) atomicAdd(rays_out, (unsigned long long)rays);
+  if (rays_out) {
+    unsigned long long r = rays;
+    for (int off = 16; off > 0; off >>= 1) r += __shfl_xor_sync(kFull, r, off);
+    if (lane_id() == 0 && r) atomicAdd(rays_out, r);
+  }
+  flush_counters<INSTR>(A, cnt);
 }
 
 }  // namespace
@@ -325,7 +435,7 @@ extern "C" int pt_render_backward_reparam(pt_scene* s, const pt_render_desc* r, 
   LaunchArgs A;
   int st = fill_launch(s, r, p, A);
   if (st != PT_OK) return st;
-  if (r->cache || r->counters || r->dbg_sample_L || r->dbg_sample_hash) return PT_ERR_ARG;
+  if (r->cache || r->dbg_sample_L || r->dbg_sample_hash) return PT_ERR_ARG;
   A.grad_image = grad_image;
   RpOpts K;
   K.n_aux = o.n_aux;
@@ -337,6 +447,8 @@ extern "C" int pt_render_backward_reparam(pt_scene* s, const pt_render_desc* r, 
   K.eps = o.eps;
   K.border = o.border;
   K.e2k = expf(-2.0f * o.kappa);
+  K.group = 2;
+  while (K.group < o.n_aux) K.group *= 2;
   const size_t smem = (size_t)s->n_shapes * 3 * sizeof(float);
   K.smem = smem <= 32768 ? 1 : 0;
   pt_render_desc rd = *r;
@@ -347,9 +459,13 @@ extern "C" int pt_render_backward_reparam(pt_scene* s, const pt_render_desc* r, 
   if ((st = launch_dims(&rd, A, block, grid)) != PT_OK) return st;
   cudaStream_t cs = (cudaStream_t)stream;
   const size_t sm = K.smem ? smem : 0;
-  if (s->dev.layout == PT_BVH_WIDE)
-    reparam_kernel<PT_BVH_WIDE><<<(unsigned)grid, block, sm, cs>>>(A, K, grad_translation, rays);
-  else
-    reparam_kernel<PT_BVH_BINARY><<<(unsigned)grid, block, sm, cs>>>(A, K, grad_translation, rays);
+  const dim3 gd((unsigned)grid), bd(block);
+  if (s->dev.layout == PT_BVH_WIDE) {
+    if (A.counters) reparam_kernel<PT_BVH_WIDE, true><<<gd, bd, sm, cs>>>(A, K, grad_translation, rays);
+    else reparam_kernel<PT_BVH_WIDE, false><<<gd, bd, sm, cs>>>(A, K, grad_translation, rays);
+  } else {
+    if (A.counters) reparam_kernel<PT_BVH_BINARY, true><<<gd, bd, sm, cs>>>(A, K, grad_translation, rays);
+    else reparam_kernel<PT_BVH_BINARY, false><<<gd, bd, sm, cs>>>(A, K, grad_translation, rays);
+  }
   return cudaGetLastError() == cudaSuccess ? PT_OK : PT_ERR_CUDA;
 }
