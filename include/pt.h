@@ -211,7 +211,7 @@ typedef struct {
   float* tex[PT_MAX_TEX];     /* each [tex_h][tex_w][4] */
   float* roughness;           /* [n_rough] */
   float* env;                 /* [env_h][env_w][4] environment radiance (emitter gradients,
-                                 Sec. 5: PRB differentiating the environment map) */
+                                 Sec. 4.10: PRB differentiating the environment map) */
 } pt_grads;
 
 /* Primal render (Fig. 7, megakernel #1): image = mean over spp of the path
@@ -313,7 +313,7 @@ int pt_render_batch_noalloc(const pt_job* jobs, int n_jobs, const pt_batch_opts*
 int pt_render_jvp(pt_scene* scene, const pt_render_desc* desc, const pt_params* params, const pt_params* tangent,
                   float* image, float* image_dot, void* stream);
 
-/* Wavefront variant (Sec. 3.3 "wavefront-style evaluation", Sec. 5: the megakernel
+/* Wavefront variant (Sec. 3.4 "wavefront-style evaluation", Sec. 3.5: the megakernel
  * against wavefront execution).  The same estimator as pt_render_forward /
  * pt_render_backward (same random numbers and decisions), computed by one kernel per
  * stage with the path state in device memory: a wave of whole pixels runs max_depth
@@ -367,7 +367,7 @@ int pt_cache_set_state(pt_cache* cache, const float* weights, const float* m, co
 #define PT_CACHE_WAIT_LIMIT_DEFAULT (1u << 22)
 int pt_cache_set_wait_limit(pt_cache* cache, uint32_t limit);
 
-/* Reverse mode with checkpoints (Sec. 5: differentiating a standard path tracer
+/* Reverse mode with checkpoints (Sec. 4.10: differentiating a standard path tracer
  * whose loop keeps one checkpoint per scattering event, against PRB).
  * pt_ckpt_forward renders like pt_render_forward and stores, before every
  * closest-hit ray, the loop state of the path (PCG32 state, ray, throughput, MIS

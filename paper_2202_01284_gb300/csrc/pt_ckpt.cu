@@ -1,6 +1,6 @@
-// Reverse-mode differentiation of the path tracer with checkpoints (Sec. 5, the
+// Reverse-mode differentiation of the path tracer with checkpoints (Sec. 4.10, the
 // comparison of PRB with differentiating a standard path tracer whose loop keeps
-// one checkpoint per scattering event; Sec. 3.4 on loops).
+// one checkpoint per scattering event; Sec. 4.3 on loops).
 //
 // Forward: the megakernel stores the loop state at the start of every path vertex
 // (pt_ckpt_forward).  Reverse: each sample's vertices are recomputed from their

@@ -90,7 +90,7 @@ __device__ __forceinline__ void load_checkpoint(const LaunchArgs& A, long long s
 }
 
 // FEAT_CKPT (forward only): store a checkpoint before every closest-hit ray and
-// the vertex count of every sample (reverse mode with checkpoints, Sec. 5).
+// the vertex count of every sample (reverse mode with checkpoints, Sec. 4.10).
 template <bool ADJ, bool JVP, bool INSTR, int LAYOUT, int DISPATCH, int FEAT = 0>
 __device__ __forceinline__ void megakernel(const LaunchArgs& A, long long unit, const Tile& tile) {
   constexpr bool CKPT = (FEAT & FEAT_CKPT) != 0;

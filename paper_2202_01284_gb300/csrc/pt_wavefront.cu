@@ -1,5 +1,5 @@
-// Wavefront variant of the forward render and of the PRB adjoint (Sec. 3.3,
-// wavefront-style evaluation; Sec. 5 compares it with the megakernel).
+// Wavefront variant of the forward render and of the PRB adjoint (Sec. 3.4,
+// wavefront-style evaluation; Sec. 3.5 compares it with the megakernel).
 //
 // The per-path code is the megakernel's (path_start / path_shade / path_finish):
 // only the loop is unrolled into one kernel per stage, with the path state kept

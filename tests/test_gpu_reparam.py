@@ -98,3 +98,34 @@ def test_reparam_arguments(lib):
     ds.backward_reparam(st, torch.zeros_like(gi), g)
     torch.cuda.synchronize()
     assert not g.any()
+
+
+def test_reparam_fullsize_crop_parity(lib, oracle_mod):
+    """The bench's launch: 196,608-triangle sphere scene (33 shapes), 1024x1024, 16 spp,
+    depth 8, roulette from 3, wide BVH, whole-image launch.  dLoss/dI is non-zero on two
+    16x16 crops only, so the oracle's crops and the GPU's full image differentiate the
+    same sum."""
+    from paper_2202_01284_gb300.render import DeviceScene, RenderSettings
+    sc = S.spheres()
+    ds = DeviceScene(sc, layout=lib.PT_BVH_WIDE)
+    st = RenderSettings(width=1024, height=1024, spp=16, max_depth=8, rr_depth=3, seed=12)
+    crops = [(400, 540, 16, 16), (600, 600, 16, 16)]
+    rng = np.random.default_rng(8)
+    gi = np.zeros((1024, 1024, 3), np.float32)
+    osc = oracle_mod.OracleScene(sc)
+    g_ref = np.zeros((sc.n_shapes, 3))
+    for (x0, y0, w, h) in crops:
+        g = rng.random((h, w, 3)).astype(np.float32)
+        gi[y0:y0 + h, x0:x0 + w] = g
+        r = oracle_mod.render_in(sc.cameras[0], 16, 8, 12, 3, True, crop=(x0, y0, w, h))
+        g_ref += oracle_mod.grad_reparam(osc, r, g)[0]
+    gt = torch.zeros((sc.n_shapes, 3), device="cuda")
+    ds.backward_reparam(st, torch.as_tensor(gi[None], device="cuda"), gt)
+    torch.cuda.synchronize()
+    assert ds.status() == 0
+    gg = gt.cpu().numpy().astype(np.float64)
+    c = cosine(gg.ravel(), g_ref.ravel())
+    rel = np.abs(gg - g_ref).max() / np.abs(g_ref).max()
+    print(f"full-size reparam: cosine {c:.7f} max rel {rel:.2e}")
+    assert c >= 0.9999
+    assert rel < 1e-2
