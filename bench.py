@@ -647,8 +647,9 @@ def run_reparam_experiment(args):
     """Reparameterized PRB (translation gradients of the 33 shapes through
     visibility) on the throughput scene at --reparam-spp samples per pixel: one
     gradient step = forward image, L2-loss image gradient, reparameterized
-    adjoint.  Rays = every ray the adjoint traces (path, shadow, auxiliary and
-    the warps' center rays), counted by the kernel itself.  Own JSON line."""
+    adjoint (radiance pass + replay with the warps).  Rays = every ray the adjoint
+    traces (radiance pass, replay, shadow, auxiliary and the warps' center rays),
+    counted by the kernel.  Own JSON line."""
     import torch
 
     from paper_2202_01284_gb300 import abi
@@ -703,6 +704,8 @@ def run_reparam_experiment(args):
     p = abi.params_struct(ds.albedo, ds.textures, ds.roughness, None)
     desc = ds._desc(ds.cameras, replace(st, seed=12), counters=cnt)
     abi.pt_render_backward_reparam(ds.handle, desc, p, abi.reparam_opts(), grad_img, gt2, None, stream.cuda_stream)
+    # the radiance pass before the replay traces the forward's rays with the adjoint seed
+    ds.forward(replace(st, seed=12), out=img, counters=cnt)
     torch.cuda.synchronize()
     c = cnt.cpu().numpy()
     flops = FLOPS_PER_NODE[args.bvh] * int(c[3]) + FLOPS_PER_TRI * int(c[4])
@@ -740,7 +743,8 @@ def run_reparam_experiment(args):
                          "peak": round(peak_tflops, 2), "unit": "TFLOP/s", "frac": round(achieved / peak_tflops, 4),
                          "traffic": None,
                          "work": f"{FLOPS_PER_NODE[args.bvh]}/node visit + {FLOPS_PER_TRI}/triangle test (counted "
-                                 "by the instrumented launch; warp-field arithmetic not counted)",
+                                 "by instrumented launches of the replay and of the radiance pass; warp-field "
+                                 "arithmetic not counted); time = radiance pass + reparam_kernel",
                          "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 x median SM clock {mhz} MHz"},
             "gpu_launches": 2 * args.steps,
             "clocks": clk}

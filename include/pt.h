@@ -411,14 +411,19 @@ int pt_ckpt_backward(pt_scene* scene, const pt_render_desc* desc, const pt_param
  * within `border` pixels of the image border (samples cannot leave the image).
  * The camera is static.
  *
- * Each sample is traced once for its radiance and replayed (PRB) with the
- * warps; auxiliary random numbers come from a second PCG32 stream of the sample
+ * A radiance pass (as split PRB: the forward megakernel storing each sample's
+ * radiance, 12 B per sample, in scene-owned scratch grown with cudaMalloc, which
+ * synchronises the device) precedes a replay (PRB) with the warps in which the
+ * lanes of a warp trace the auxiliary rays of one or two rays together;
+ * auxiliary random numbers come from a second PCG32 stream of the sample
  * (initseq | 2^62): 2 n_aux for the camera ray, then 4 n_aux at every vertex that
  * draws its 8 path uniforms (light-sample ray first, then BSDF ray), used or not.
  *
  * grad_translation: device float [n_shapes][3], accumulated (+=).  rays: device
- * counter of the rays traced (camera, continuation, shadow, auxiliary and the
- * warps' own center rays), accumulated; NULL = not wanted.  desc: as for
+ * counter of the rays traced (radiance pass -- counted as the replay's path and
+ * shadow rays, which it repeats --, replay, auxiliary and the warps' own center
+ * rays), accumulated; NULL = not wanted.  desc.counters: node and triangle
+ * visits of the replay kernel only.  desc: as for
  * pt_render_backward (the seed is used for both passes); block_size must be 0 or
  * 128; no cache, counters or per-sample outputs.  opts: NULL = defaults
  * (pt_reparam_defaults).  Errors: PT_ERR_ARG (options out of range: 2 <= n_aux <=

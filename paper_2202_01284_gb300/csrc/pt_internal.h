@@ -127,6 +127,10 @@ CacheBuffers cache_buffers(pt_cache* c);
 // description and parameters into launch arguments; block and grid of a launch.
 int fill_launch(pt_scene* s, const pt_render_desc* r, const pt_params* p, LaunchArgs& A);
 int launch_dims(const pt_render_desc* r, const LaunchArgs& A, int& block, long long& grid);
+// Split-PRB radiance pass (the forward megakernel with seed_adj storing each sample's
+// radiance, 12 B per sample, into scene-owned scratch grown with cudaMalloc);
+// A.sample_L points at the scratch afterwards.
+int radiance_pass(pt_scene* s, const pt_render_desc* r, LaunchArgs& A, cudaStream_t cs);
 
 }  // namespace ptgb
 

@@ -253,6 +253,35 @@ bool instrumented(const pt_render_desc* r) { return r->dbg_sample_L || r->dbg_sa
 
 long long sample_slots(const LaunchArgs& A) { return (long long)A.n_cams * A.crop_w * A.crop_h * A.spp; }
 
+int radiance_pass(pt_scene* s, const pt_render_desc* r, LaunchArgs& A, cudaStream_t cs) {
+  // per-sample radiance scratch owned by the scene
+  const size_t need = (size_t)sample_slots(A) * 3 * sizeof(float);
+  if (s->sample_L_bytes < need) {
+    if (s->d_sample_L) cudaFree(s->d_sample_L);
+    s->d_sample_L = nullptr;
+    s->sample_L_bytes = 0;
+    if (cudaMalloc(&s->d_sample_L, need) != cudaSuccess) {
+      cudaGetLastError();
+      return PT_ERR_OOM;
+    }
+    s->sample_L_bytes = need;
+  }
+  int block;
+  long long grid;
+  int st = launch_dims(r, A, block, grid);
+  if (st != PT_OK) return st;
+  LaunchArgs F = A;
+  F.image = nullptr;
+  F.counters = nullptr;
+  F.dbg_L = nullptr;
+  F.dbg_hash = nullptr;
+  F.sample_L = A.sample_L = static_cast<float*>(s->d_sample_L);
+  const dim3 gd((unsigned)grid), bd(block);
+  if (s->dev.layout == PT_BVH_WIDE) radiance_kernel<PT_BVH_WIDE><<<gd, bd, 0, cs>>>(F);
+  else radiance_kernel<PT_BVH_BINARY><<<gd, bd, 0, cs>>>(F);
+  return cudaGetLastError() == cudaSuccess ? PT_OK : PT_ERR_CUDA;
+}
+
 }  // namespace ptgb
 
 namespace {
@@ -351,28 +380,9 @@ extern "C" int pt_render_backward(pt_scene* s, const pt_render_desc* r, const pt
   }
   if (r->prb_mode < PT_PRB_AUTO || r->prb_mode > PT_PRB_SPLIT) return PT_ERR_ARG;
   if (r->prb_mode != PT_PRB_FUSED && !instrumented(r)) {
-    // per-sample radiance scratch owned by the scene
-    const size_t need = (size_t)sample_slots(A) * 3 * sizeof(float);
-    if (s->sample_L_bytes < need) {
-      if (s->d_sample_L) cudaFree(s->d_sample_L);
-      s->d_sample_L = nullptr;
-      s->sample_L_bytes = 0;
-      if (cudaMalloc(&s->d_sample_L, need) != cudaSuccess) {
-        cudaGetLastError();
-        return PT_ERR_OOM;
-      }
-      s->sample_L_bytes = need;
-    }
-    LaunchArgs F = A;
-    F.image = nullptr;
-    F.sample_L = A.sample_L = static_cast<float*>(s->d_sample_L);
-    if (s->dev.layout == PT_BVH_WIDE) {
-      radiance_kernel<PT_BVH_WIDE><<<gd, bd, 0, cs>>>(F);
-      replay_kernel<PT_BVH_WIDE><<<gd, bd, 0, cs>>>(A);
-    } else {
-      radiance_kernel<PT_BVH_BINARY><<<gd, bd, 0, cs>>>(F);
-      replay_kernel<PT_BVH_BINARY><<<gd, bd, 0, cs>>>(A);
-    }
+    if ((st = radiance_pass(s, r, A, cs)) != PT_OK) return st;
+    if (s->dev.layout == PT_BVH_WIDE) replay_kernel<PT_BVH_WIDE><<<gd, bd, 0, cs>>>(A);
+    else replay_kernel<PT_BVH_BINARY><<<gd, bd, 0, cs>>>(A);
     return cudaGetLastError() == cudaSuccess ? PT_OK : PT_ERR_CUDA;
   }
   const int v = (instrumented(r) ? 4 : 0) | (s->dev.layout == PT_BVH_WIDE ? 2 : 0) | (A.dispatch == PT_DISPATCH_MATCH ? 1 : 0);

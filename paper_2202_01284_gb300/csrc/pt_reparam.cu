@@ -34,9 +34,10 @@
 // each Delta_i: it is added to shape_i's gradient and subtracted from the
 // origin shape's.
 //
-// Launch: one thread per (pixel, lane) as in the megakernel; each sample is
-// traced once for its radiance and replayed (PRB) with the warps.  Gradients
-// are accumulated per CTA in shared memory when the shape table fits.
+// Launch: the split-PRB radiance pass (each sample's radiance), then one thread per
+// (pixel, lane) replays its samples in lockstep with the other lanes of its warp,
+// which trace the auxiliary rays of the posted rays together.  Gradients are
+// accumulated per CTA in shared memory when the shape table fits.
 #include "pt_mega.cuh"
 
 namespace ptgb {
@@ -245,9 +246,10 @@ __device__ __noinline__ unsigned process_warps(const LaunchArgs& A, const RpOpts
   return rays;
 }
 
-// Lockstep per-lane state machine: each iteration every lane advances its own
-// path by one vertex (radiance pass, then PRB replay of the same sample), then
-// the whole warp processes the reparameterized rays the lanes posted.
+// Lockstep loop: each iteration every lane advances the PRB replay of its current
+// sample by one vertex (its radiance comes from the radiance pass launched before,
+// as in split PRB), then the whole warp processes the reparameterized rays the
+// lanes posted.
 template <int LAYOUT, bool INSTR>
 __global__ void __launch_bounds__(128) reparam_kernel(const __grid_constant__ LaunchArgs A, const RpOpts K,
                                                       float* __restrict__ grad_t, unsigned long long* rays_out) {
@@ -274,66 +276,47 @@ __global__ void __launch_bounds__(128) reparam_kernel(const __grid_constant__ La
     const DevCamera& cam = A.cams[px.cam];
     fwd = f3(cam.fx, cam.fy, cam.fz);
   }
-  enum { RAD = 0, REPLAY = 1, DONE = 2 };
-  int phase = DONE;
+  bool live = false;
   int si = (int)(unit & (A.lanes_per_pixel - 1));
   GradSink sink;
   PathState P;
   Pcg32 aux;
   aux.state = aux.inc = 0ull;
-  float3 L_total = z;
   bool cached = false;
   Hit next{};
   const unsigned long long n2 = 2ull * (unsigned long long)K.n_aux;
-  if (valid && si < A.spp) {
-    path_start<INSTR>(A, P, A.seed, px.cam, px.px, px.py, si, px.pix, cnt);
-    P.Lrem = z;
-    phase = RAD;
-  }
   for (;;) {
-    if (!__any_sync(kFull, phase != DONE)) break;
     WarpRay w0{}, w1{};
     bool h0 = false, h1 = false;
-    if (phase == RAD) {
-      const Hit hit = closest<LAYOUT, INSTR>(S, P.ro, P.rd, INFINITY, false, cnt);
+    if (!live && valid && si < A.spp) {
+      // start the replay of sample si: primary stream as the radiance pass,
+      // auxiliary stream initseq | 2^62; the camera ray is the first warp
+      path_start<INSTR>(A, P, A.seed, px.cam, px.px, px.py, si, px.pix, cnt);
+      const float* Ls = A.sample_L + 3 * P.slot;
+      P.Lrem = f3(Ls[0], Ls[1], Ls[2]);
+      const unsigned long long pixel = (unsigned long long)px.py * (unsigned long long)A.width + px.px;
+      aux.seed(A.seed, ((unsigned long long)px.cam << 40) | (pixel << 12) | (unsigned long long)si | (1ull << 62));
+      next = closest<LAYOUT, INSTR>(S, P.ro, P.rd, INFINITY, false, cnt);
       ++rays;
-      bool more = path_shade<false, false, INSTR, PT_DISPATCH_SWITCH>(A, P, hit, false, z, sink, cnt);
-      if (more) {
-        bool occ = false;
-        if (P.has_shadow) {
-          occ = closest<LAYOUT, INSTR>(S, P.so, P.sd, P.stmax, true, cnt).pos >= 0;
-          ++rays;
-        }
-        more = path_finish<false, false, INSTR>(A, P, occ, false, z, sink, cnt);
+      cached = true;
+      const float R = dot3(dl, P.Lrem);
+      if (R != 0.0f) {
+        w0 = WarpRay{P.ro, P.rd, fwd * (-3.0f / dot3(fwd, P.rd)), -1, px.cam, R,
+                     next.pos >= 0 ? next.t : INFINITY, aux.state, aux.inc};
+        h0 = true;
       }
-      if (!more) {
-        // replay the sample: same primary stream, auxiliary stream initseq | 2^62
-        L_total = P.L;
-        path_start<INSTR>(A, P, A.seed, px.cam, px.px, px.py, si, px.pix, cnt);
-        P.Lrem = L_total;
-        const unsigned long long pixel = (unsigned long long)px.py * (unsigned long long)A.width + px.px;
-        aux.seed(A.seed, ((unsigned long long)px.cam << 40) | (pixel << 12) | (unsigned long long)si | (1ull << 62));
-        next = closest<LAYOUT, INSTR>(S, P.ro, P.rd, INFINITY, false, cnt);
-        ++rays;
-        cached = true;
-        const float R = dot3(dl, L_total);
-        if (R != 0.0f) {
-          w0 = WarpRay{P.ro, P.rd, fwd * (-3.0f / dot3(fwd, P.rd)), -1, px.cam, R,
-                       next.pos >= 0 ? next.t : INFINITY, aux.state, aux.inc};
-          h0 = true;
-        }
-        pcg_advance(aux, n2);
-        phase = REPLAY;
-      }
-    } else if (phase == REPLAY) {
+      pcg_advance(aux, n2);
+      live = true;
+    } else if (live) {
       Hit hit;
-      if (cached) {
+      if (cached) {  // traced already as the center ray of the previous warp
         hit = next;
         cached = false;
       } else {
         hit = closest<LAYOUT, INSTR>(S, P.ro, P.rd, INFINITY, false, cnt);
         ++rays;
       }
+      ++rays;  // its twin in the radiance pass
       const bool block = hit.pos >= 0 && P.depth < A.max_depth;
       int s_o = -1;
       float3 n_s = z;
@@ -352,7 +335,7 @@ __global__ void __launch_bounds__(128) reparam_kernel(const __grid_constant__ La
         bool occ = false;
         if (P.has_shadow) {
           occ = closest<LAYOUT, INSTR>(S, P.so, P.sd, P.stmax, true, cnt).pos >= 0;
-          ++rays;
+          rays += 2;
         }
         const bool diffuse = block && P.mtype == PT_BSDF_DIFFUSE;
         if (diffuse && P.has_shadow && !occ) {
@@ -379,15 +362,11 @@ __global__ void __launch_bounds__(128) reparam_kernel(const __grid_constant__ La
         }
       }
       if (!more) {
+        live = false;
         si += A.lanes_per_pixel;
-        phase = DONE;
-        if (si < A.spp) {
-          path_start<INSTR>(A, P, A.seed, px.cam, px.px, px.py, si, px.pix, cnt);
-          P.Lrem = z;
-          phase = RAD;
-        }
       }
     }
+    if (!__any_sync(kFull, live || h0 || h1 || (valid && si < A.spp))) break;
     rays += process_warps<LAYOUT, INSTR>(A, K, h0, w0, G, cnt);
     rays += process_warps<LAYOUT, INSTR>(A, K, h1, w1, G, cnt);
   }
@@ -459,6 +438,7 @@ extern "C" int pt_render_backward_reparam(pt_scene* s, const pt_render_desc* r, 
   if ((st = launch_dims(&rd, A, block, grid)) != PT_OK) return st;
   cudaStream_t cs = (cudaStream_t)stream;
   const size_t sm = K.smem ? smem : 0;
+  if ((st = radiance_pass(s, &rd, A, cs)) != PT_OK) return st;
   const dim3 gd((unsigned)grid), bd(block);
   if (s->dev.layout == PT_BVH_WIDE) {
     if (A.counters) reparam_kernel<PT_BVH_WIDE, true><<<gd, bd, sm, cs>>>(A, K, grad_translation, rays);

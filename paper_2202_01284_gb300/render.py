@@ -291,6 +291,36 @@ def render(dscene: DeviceScene, st: RenderSettings, albedo, roughness, textures:
     return RenderFn.apply(dscene, st, albedo, roughness, env, *textures)
 
 
+class TranslateFn(torch.autograd.Function):
+    """image = render of `scene` with every shape moved by translations[shape]
+    ([n_shapes, 3]); backward = reparameterized PRB (pt_render_backward_reparam,
+    Sec. 4.7), the gradient with respect to the translations through visibility.
+    The translated geometry is uploaded (scene and BVH built) on every call."""
+
+    @staticmethod
+    def forward(ctx, scene: S.Scene, st: RenderSettings, layout: int, opts: dict, translations):
+        t = translations.detach().to("cpu", torch.float64).numpy()
+        ds = DeviceScene(scene.translated(t), layout=layout, device=translations.device)
+        ctx.ds, ctx.st, ctx.opts = ds, st, opts
+        return ds.forward(st)
+
+    @staticmethod
+    def backward(ctx, grad_img):
+        ds, st = ctx.ds, ctx.st
+        g = torch.zeros((ds.n_shapes, 3), device=grad_img.device, dtype=torch.float32)
+        seed = st.backward_seed if st.backward_seed is not None else st.seed
+        ds.backward_reparam(st, grad_img.contiguous(), g, seed=seed, **ctx.opts)
+        ds.close()  # pt_scene_destroy frees device memory, which waits for the launch
+        ctx.ds = None
+        return None, None, None, None, g
+
+
+def render_translated(scene: S.Scene, st: RenderSettings, translations, layout: int = abi.PT_BVH_BINARY,
+                      **reparam_opts):
+    """Differentiable render with respect to one translation per shape."""
+    return TranslateFn.apply(scene, st, layout, reparam_opts, translations)
+
+
 class RadianceCache:
     """Owner of a pt_cache (MLP weights, Adam state, query/record buffers)."""
 
