@@ -661,8 +661,8 @@ Camera make_camera(const oracle_render_in& r) {
 struct NoRayEvents {
   void camera_ray(uint64_t, V3, V3, V3) {}
   void vertex_block() {}
-  void nee_ray(V3, V3, int, V3, int) {}
-  void bsdf_ray(V3, V3, int, V3, int) {}
+  void nee_ray(V3, V3, int, double, double, V3, int) {}
+  void bsdf_ray(V3, V3, int, double, double, V3, int) {}
 };
 struct VertexInfo {
   Mat m;
@@ -865,7 +865,7 @@ V3 render_sample(const Scene& s, const Camera& cam, const oracle_render_in& r, i
             V3 scale = Le * s_env;             // everything but beta and f
             V3 c = mul(mul(beta, f), scale);
             L = L + c;
-            acc.nee_ray(so, dir, s.tri_shape[t], n, vi.m.bsdf);
+            acc.nee_ray(so, dir, t, hit.u, hit.v, n, vi.m.bsdf);
             acc.nee(vi, wl, scale, c, env_texel, mul(beta, f) * s_env, s_env);
           }
         }
@@ -899,7 +899,7 @@ V3 render_sample(const Scene& s, const Camera& cam, const oracle_render_in& r, i
       beta = mul(beta, f) * k;
       V3 wo = fr.to_world(wo_l);
       V3 ro_next = offset_origin(p, ng, wo);
-      acc.bsdf_ray(ro_next, wo, s.tri_shape[t], n, vi.m.bsdf);
+      acc.bsdf_ray(ro_next, wo, t, hit.u, hit.v, n, vi.m.bsdf);
       acc.scatter(vi, wo_l, k);
       prev_delta = false;
       prev_pdf = pdf;
@@ -1204,6 +1204,7 @@ struct AuxHit {
   int shape;
   V3 n;       // geometric normal of the hit triangle
   double d;   // n . (hit point - origin): the plane is {x : n.(x - o) = d}
+  int tri;    // hit triangle (-1: escaped)
 };
 struct WarpSamples {
   V3 u;
@@ -1239,12 +1240,12 @@ WarpSamples warp_samples(const Scene& s, const ReparamOpts& op, V3 o, V3 u, cons
     Hit h = closest_hit(s, o, w, INFINITY, false);
     if (h.prim < 0) {
       if (op.miss > 0)
-        ws.hits.push_back({w, INFINITY, op.miss / (Cq * std::exp(op.kappa * (dot(u, w) - 1.0))), -1, V3(), 1.0});
+        ws.hits.push_back({w, INFINITY, op.miss / (Cq * std::exp(op.kappa * (dot(u, w) - 1.0))), -1, V3(), 1.0, -1});
       continue;
     }
     double q = Cq * std::exp(op.kappa * (dot(u, w) - 1.0));
     V3 n = geo_normal(s, h.prim);
-    ws.hits.push_back({w, h.t, 1.0 / q, s.tri_shape[h.prim], n, dot(n, w) * h.t});
+    ws.hits.push_back({w, h.t, 1.0 / q, s.tri_shape[h.prim], n, dot(n, w) * h.t, h.prim});
   }
   // depth weights relative to the ray's own hit distance t0: g = (t0 / t)^m, so
   // a closer surface dominates a farther one near its silhouette; if the ray
@@ -1256,32 +1257,80 @@ WarpSamples warp_samples(const Scene& s, const ReparamOpts& op, V3 o, V3 u, cons
   return ws;
 }
 
-// Motion of auxiliary hit i relative to the origin for the unit tangent of
-// parameter (shape ps, axis pa): the hit's shape moves with tau[ps], the origin
-// with tau[s_o]; escaping rays (shape -1) see the static environment.
-V3 aux_motion(const AuxHit& h, int s_o, int ps, int pa) {
-  double m = (h.shape >= 0 && h.shape == ps ? 1.0 : 0.0) - (h.shape >= 0 && s_o == ps ? 1.0 : 0.0);
-  V3 e;
-  if (pa == 0) e.x = m;
-  else if (pa == 1) e.y = m;
-  else e.z = m;
-  return e;
+// Parameters: one translation per shape (param = 3 shape + axis) or every triangle
+// corner's position (param = 9 triangle + 3 corner + axis).  A surface point moves
+// with its barycentric coordinates: by tau[shape] or by sum_j b_j v'_j.
+struct Param {
+  bool vertex;
+  int index, corner, axis;  // shape or triangle; corner (vertex mode); axis
+};
+Param param_of(bool vertex, int p) {
+  return vertex ? Param{true, p / 9, (p / 3) % 3, p % 3} : Param{false, p / 3, 0, p % 3};
+}
+V3 axis_vec(int a, D2) { return a == 0 ? V3(1, 0, 0) : a == 1 ? V3(0, 1, 0) : V3(0, 0, 1); }
+
+// The ray's origin: the camera (tri < 0) or a point of triangle `tri` with
+// barycentric coordinates (1 - bu - bv, bu, bv) on shape `shape`.
+struct Origin {
+  int shape = -1, tri = -1;
+  double bu = 0, bv = 0;
+};
+
+// Motion of the origin for the unit tangent of parameter P.
+V3 origin_motion(const Scene& s, const Origin& og, const Param& P) {
+  if (og.tri < 0) return V3();
+  V3 e = axis_vec(P.axis, D2{});
+  if (!P.vertex) return og.shape == P.index ? e : V3();
+  if (og.tri != P.index) return V3();
+  const double b[3] = {1.0 - og.bu - og.bv, og.bu, og.bv};
+  return e * b[P.corner];
 }
 
-// The warp field of parameter (ps, pa) at direction w (fixed samples).
-VD warp_field(const WarpSamples& ws, int s_o, int ps, int pa, VD w, int skip = -1) {
+// Barycentric coordinate `corner` of the point where the ray (o, w) meets the
+// plane of triangle t (extended beyond its edges), from its definition with
+// signed areas: b1 = ((x - v0) x e2).c / c.c, b2 = (e1 x (x - v0)).c / c.c.
+D2 plane_barycentric(const Scene& s, int t, V3 o, VD w, int corner) {
+  V3 v0 = s.v0[t], e1 = s.v1[t] - s.v0[t], e2 = s.v2[t] - s.v0[t];
+  V3 c = cross(e1, e2);
+  D2 tt = D2{dot(c, v0 - o), 0, 0} / dotd(w, c);
+  VD x{D2{o.x - v0.x, 0, 0} + w.x * tt, D2{o.y - v0.y, 0, 0} + w.y * tt, D2{o.z - v0.z, 0, 0} + w.z * tt};
+  // (x x e2).c and (e1 x x).c are linear in x: (e2 x c).x and (c x e1).x
+  D2 b1 = dotd(x, cross(e2, c)) * (1.0 / dot(c, c));
+  D2 b2 = dotd(x, cross(c, e1)) * (1.0 / dot(c, c));
+  if (corner == 1) return b1;
+  if (corner == 2) return b2;
+  return D2{1, 0, 0} - b1 - b2;
+}
+
+// Velocity, seen along w, of the point where w meets the plane of auxiliary hit h
+// (distance d_h / (n_h . w)), relative to the origin, for the unit tangent of P.
+VD aux_velocity(const Scene& s, const AuxHit& h, V3 o, const Origin& og, const Param& P, VD w) {
+  if (h.tri < 0) return constant(V3());
+  V3 e = axis_vec(P.axis, D2{});
+  VD mv = constant(V3());  // motion of the plane point
+  if (!P.vertex) {
+    if (h.shape == P.index) mv = constant(e);
+  } else if (h.tri == P.index) {
+    D2 b = plane_barycentric(s, h.tri, o, w, P.corner);
+    mv = VD{b * e.x, b * e.y, b * e.z};
+  }
+  V3 om = origin_motion(s, og, P);
+  VD rel{mv.x - D2{om.x, 0, 0}, mv.y - D2{om.y, 0, 0}, mv.z - D2{om.z, 0, 0}};
+  D2 inv_t = dotd(w, h.n) * (1.0 / h.d);
+  D2 wr = dotd(w, rel);
+  return VD{(rel.x - w.x * wr) * inv_t, (rel.y - w.y * wr) * inv_t, (rel.z - w.z * wr) * inv_t};
+}
+
+// The warp field of parameter P at direction w (fixed samples; `skip` >= 0 leaves
+// that sample out, -2 leaves out an escaped sample that carries no weight).
+VD warp_field(const Scene& s, const WarpSamples& ws, V3 o, const Origin& og, const Param& P, VD w, int skip = -1) {
   VD num = constant(V3());
   D2 den{0, 0, 0};
   int idx = -1;
   for (const AuxHit& h : ws.hits) {
     if (++idx == skip) continue;
     D2 a = d2exp((dotd(w, h.w) - D2{1.0, 0, 0}) * (ws.kappa * ws.kscale)) * h.g_over_q;
-    // velocity seen along w of the point where w meets the plane of hit i
-    // (distance d_i / (n_i . w)), moving with the hit's shape relative to the origin
-    V3 e = aux_motion(h, s_o, ps, pa);
-    D2 inv_t = dotd(w, h.n) * (1.0 / h.d);
-    D2 we = dotd(w, e);
-    VD pc{(D2{e.x, 0, 0} - w.x * we) * inv_t, (D2{e.y, 0, 0} - w.y * we) * inv_t, (D2{e.z, 0, 0} - w.z * we) * inv_t};
+    VD pc = aux_velocity(s, h, o, og, P, w);
     num = num + VD{pc.x * a, pc.y * a, pc.z * a};
     den = den + a;
   }
@@ -1290,9 +1339,19 @@ VD warp_field(const WarpSamples& ws, int s_o, int ps, int pa, VD w, int skip = -
   return divided(VD{num.x * inv_n, num.y * inv_n, num.z * inv_n}, d);
 }
 
-// Log-derivative factor of one reparameterized ray for every translation
-// parameter that can move it: d/dtheta log(integrand * det) = m.(P u V) + div V,
-// with m the covector of the ray's measure/cosine term.  `out` gets (param, value).
+// Derivative of log|n . u| for the unit tangent of P, n the unit geometric normal of
+// the origin's triangle (vertex mode only; a translation does not turn a normal).
+double normal_derivative(const Scene& s, const Origin& og, const Param& P, V3 u) {
+  if (!P.vertex || og.tri < 0 || og.tri != P.index) return 0.0;
+  V3 e = axis_vec(P.axis, D2{});
+  VD v[3] = {constant(s.v0[og.tri]), constant(s.v1[og.tri]), constant(s.v2[og.tri])};
+  v[P.corner] = VD{D2{v[P.corner].x.v, e.x, 0}, D2{v[P.corner].y.v, e.y, 0}, D2{v[P.corner].z.v, e.z, 0}};
+  VD e1{v[1].x - v[0].x, v[1].y - v[0].y, v[1].z - v[0].z}, e2{v[2].x - v[0].x, v[2].y - v[0].y, v[2].z - v[0].z};
+  VD c{e1.y * e2.z - e1.z * e2.y, e1.z * e2.x - e1.x * e2.z, e1.x * e2.y - e1.y * e2.x};
+  D2 nu = dotd(c, u) / d2sqrt(dotd(c, c));
+  return nu.a / nu.v;
+}
+
 // Window of the camera-ray warp: 1 inside the image, falling to 0 at its border
 // over `border` pixels (smoothstep of the distance in pixels to the nearest image
 // edge), so that no sample is moved across the border of the image.
@@ -1315,20 +1374,39 @@ D2 window(const CamWindow& c, VD w) {
   return t * t * (D2{3, 0, 0} - t * 2.0);
 }
 
-void warp_log_derivs(const WarpSamples& ws, int s_o, V3 m, std::vector<std::pair<int, double>>& out,
-                     const CamWindow* win = nullptr) {
+// Log-derivative factor of one reparameterized ray for every parameter that can
+// move it: d/dtheta log(integrand * det) = m.(P_u V) + div V (+ the derivative of
+// the cosine's normal, (n' . u) / (n . u), when m is a cosine covector n / n.u and
+// the vertices move).  `out` gets (param, value).
+void warp_log_derivs(const Scene& s, const WarpSamples& ws, V3 o, const Origin& og, bool vertex, V3 m, V3 n_cos,
+                     std::vector<std::pair<int, double>>& out, const CamWindow* win = nullptr) {
   out.clear();
-  std::vector<int> shapes;
-  for (const AuxHit& h : ws.hits)
-    if (h.shape >= 0 && h.shape != s_o && std::find(shapes.begin(), shapes.end(), h.shape) == shapes.end())
-      shapes.push_back(h.shape);
-  if (!shapes.empty() && s_o >= 0) shapes.push_back(s_o);
+  // the parameters that can move this ray: those of the hit shapes / triangles and the origin
+  std::vector<int> ids;
+  auto add = [&](int id) {
+    if (id >= 0 && std::find(ids.begin(), ids.end(), id) == ids.end()) ids.push_back(id);
+  };
+  bool moving_hit = false;
+  for (const AuxHit& h : ws.hits) {
+    if (h.tri < 0) continue;
+    if (vertex) {
+      add(h.tri);
+      moving_hit = true;
+    } else if (h.shape != og.shape) {
+      add(h.shape);
+      moving_hit = true;
+    }
+  }
+  if (og.tri >= 0 && (moving_hit || vertex)) add(vertex ? og.tri : og.shape);
   const V3 u = ws.u;
-  for (int ps : shapes)
-    for (int pa = 0; pa < 3; ++pa) {
+  const int per = vertex ? 9 : 3;
+  for (int id : ids)
+    for (int k = 0; k < per; ++k) {
+      const int p = per * id + k;
+      const Param P = param_of(vertex, p);
       auto ld = [&](int skip) {
         auto field = [&](VD w) {
-          VD V = warp_field(ws, s_o, ps, pa, w, skip);
+          VD V = warp_field(s, ws, o, og, P, w, skip);
           if (!win) return V;
           D2 b = window(*win, w);
           return VD{V.x * b, V.y * b, V.z * b};
@@ -1348,7 +1426,8 @@ void warp_log_derivs(const WarpSamples& ws, int s_o, V3 m, std::vector<std::pair
         loo += (ws.n - nh) * ld(-2);
         full = ws.n * full - (ws.n - 1.0) / ws.n * loo;
       }
-      out.push_back({3 * ps + pa, full});
+      if (dot(n_cos, n_cos) > 0) full += normal_derivative(s, og, P, u);
+      out.push_back({p, full});
     }
 }
 
@@ -1364,7 +1443,9 @@ struct ReparamAcc {
   std::vector<V3> bdot, ldot;
   std::vector<std::pair<int, double>> lnee, lbsdf, tmp;
   CamWindow win;
-  void init(const Scene* sc, const ReparamOpts* o, uint64_t sd, const Camera& cam) {
+  bool vertex = false;
+  void init(const Scene* sc, const ReparamOpts* o, uint64_t sd, const Camera& cam, bool vert) {
+    vertex = vert;
     win.fwd = cam.fwd;
     win.right = cam.right;
     win.up = cam.up;
@@ -1376,7 +1457,7 @@ struct ReparamAcc {
     s = sc;
     op = o;
     seed = sd;
-    np = 3 * (int)sc->shapes.size();
+    np = vert ? 9 * sc->n_tris : 3 * (int)sc->shapes.size();
     bdot.assign(np, V3());
     ldot.assign(np, V3());
     block.assign(4 * o->n_aux, 0.0);
@@ -1386,22 +1467,26 @@ struct ReparamAcc {
     std::vector<double> uni(2 * op->n_aux);
     for (double& x : uni) x = aux.uniform();
     WarpSamples ws = warp_samples(*s, *op, o, d, uni.data());
-    warp_log_derivs(ws, -1, fwd * (-3.0 / dot(fwd, d)), tmp, &win);
+    warp_log_derivs(*s, ws, o, Origin{}, vertex, fwd * (-3.0 / dot(fwd, d)), V3(), tmp, &win);
     beta = V3(1, 1, 1);
     for (auto& pv : tmp) bdot[pv.first] = V3(1, 1, 1) * pv.second;
   }
   void vertex_block() {
     for (double& x : block) x = aux.uniform();
   }
-  void ray(V3 o, V3 d, int shape, V3 n, int bsdf, const double* uni, std::vector<std::pair<int, double>>& out) {
+  void ray(V3 o, V3 d, int tri, double bu, double bv, V3 n, int bsdf, const double* uni,
+           std::vector<std::pair<int, double>>& out) {
     out.clear();
     if (bsdf != BSDF_DIFFUSE) return;
     WarpSamples ws = warp_samples(*s, *op, o, d, uni);
-    warp_log_derivs(ws, shape, n * (1.0 / dot(n, d)), out);
+    Origin og{s->tri_shape[tri], tri, bu, bv};
+    warp_log_derivs(*s, ws, o, og, vertex, n * (1.0 / dot(n, d)), n, out);
   }
-  void nee_ray(V3 o, V3 d, int shape, V3 n, int bsdf) { ray(o, d, shape, n, bsdf, block.data(), lnee); }
-  void bsdf_ray(V3 o, V3 d, int shape, V3 n, int bsdf) {
-    ray(o, d, shape, n, bsdf, block.data() + 2 * op->n_aux, lbsdf);
+  void nee_ray(V3 o, V3 d, int tri, double bu, double bv, V3 n, int bsdf) {
+    ray(o, d, tri, bu, bv, n, bsdf, block.data(), lnee);
+  }
+  void bsdf_ray(V3 o, V3 d, int tri, double bu, double bv, V3 n, int bsdf) {
+    ray(o, d, tri, bu, bv, n, bsdf, block.data() + 2 * op->n_aux, lbsdf);
   }
   void emission(V3, V3 le_w, int, V3, double) {
     for (int p = 0; p < np; ++p) ldot[p] = ldot[p] + mul(bdot[p], le_w);
@@ -1827,20 +1912,22 @@ static bool reparam_opts(const oracle_reparam_opts* o, ReparamOpts& op) {
   return o->border > 0;
 }
 
-// Reverse-mode-equivalent translation gradient by forward mode: g[s][a] =
-// sum over pixels and channels of grad_image * d image / d tau[s][a] for every
-// shape translation tau (the reparameterized estimator above; every random
-// number fixed, auxiliary ones from the stream initseq | 2^62).  Optionally the
-// image and its derivative along parameter `dot_param` (= 3 shape + axis).
+// Reverse-mode-equivalent gradient by forward mode: g[p] = sum over pixels and
+// channels of grad_image * d image / d theta_p for every translation parameter
+// (vertex = 0: p = 3 shape + axis, g [n_shapes][3]) or every triangle corner
+// position (vertex = 1: p = 9 triangle + 3 corner + axis, g [n_tris][3][3]), by
+// the reparameterized estimator above (every random number fixed, auxiliary ones
+// from the stream initseq | 2^62).  Optionally the image and its derivative along
+// parameter `dot_param`.
 int oracle_grad_reparam(void* sc, const oracle_render_in* r, const double* grad_image, const oracle_reparam_opts* o,
-                        double* g_out, double* image, int dot_param, double* image_dot, int n_threads) {
+                        int vertex, double* g_out, double* image, int dot_param, double* image_dot, int n_threads) {
   const Scene& s = *(Scene*)sc;
   Camera cam = make_camera(*r);
   ReparamOpts op;
   if (!reparam_opts(o, op)) return -1;
   int x0, y0, cw, ch;
   crop_of(*r, x0, y0, cw, ch);
-  const int np = 3 * (int)s.shapes.size();
+  const int np = vertex ? 9 * s.n_tris : 3 * (int)s.shapes.size();
   std::vector<double> rows((size_t)ch * np, 0.0);
   parallel_rows(y0, ch, n_threads, [&](int py) {
     double* grow = &rows[(size_t)(py - y0) * np];
@@ -1850,7 +1937,7 @@ int oracle_grad_reparam(void* sc, const oracle_render_in* r, const double* grad_
       const double* gi = grad_image ? grad_image + pi * 3 : nullptr;
       for (int k = 0; k < r->spp; ++k) {
         ReparamAcc acc;
-        acc.init(&s, &op, r->seed, cam);
+        acc.init(&s, &op, r->seed, cam, vertex != 0);
         V3 l = render_sample(s, cam, *r, px, py, k, acc, nullptr);
         for (int c = 0; c < 3; ++c) sum[c] += l[c];
         if (dot_param >= 0 && dot_param < np)
@@ -1979,14 +2066,17 @@ int oracle_warp(void* sc, const double* o, const double* u, int s_o, const doubl
   WarpSamples ws = warp_samples(s, op, V3(o[0], o[1], o[2]), uu, uni);
   const int ps = param / 3, pa = param % 3;
   V3 w = at ? V3(at[0], at[1], at[2]) : uu;
-  VD V = warp_field(ws, s_o, ps, pa, constant(w));
+  Origin og{s_o, s_o >= 0 ? 0 : -1, 0.0, 0.0};
+  const Param P{false, ps, 0, pa};
+  const V3 oo(o[0], o[1], o[2]);
+  VD V = warp_field(s, ws, oo, og, P, constant(w));
   V_out[0] = V.x.v;
   V_out[1] = V.y.v;
   V_out[2] = V.z.v;
-  *div_out = sphere_div(uu, [&](VD x) { return warp_field(ws, s_o, ps, pa, x); });
+  *div_out = sphere_div(uu, [&](VD x) { return warp_field(s, ws, oo, og, P, x); });
   if (logd_out) {
     std::vector<std::pair<int, double>> ld;
-    warp_log_derivs(ws, s_o, m ? V3(m[0], m[1], m[2]) : V3(), ld);
+    warp_log_derivs(s, ws, oo, og, false, m ? V3(m[0], m[1], m[2]) : V3(), V3(), ld);
     *logd_out = 0.0;
     for (auto& pv : ld)
       if (pv.first == param) *logd_out = pv.second;

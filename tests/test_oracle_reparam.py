@@ -119,3 +119,74 @@ def test_shadow_scene_matches_finite_differences(oracle_mod):
         assert np.abs(g[shape] - fd[shape]).max() < 0.15 * scale
     # a plain (not reparameterized) derivative would be zero for every translation
     assert np.abs(g[1:]).max() > 0.5 * np.abs(fd[1:]).max()
+
+
+def test_vertex_gradients_sum_to_translation_gradients(oracle_mod):
+    """Moving every corner of a shape by the same vector is its translation: the
+    per-corner gradients of a shape sum to its translation gradient (the normal
+    terms cancel, the plane points' barycentric weights sum to one)."""
+    sc = S.shadow_scene(width=32, height=32)
+    osc = oracle_mod.OracleScene(sc)
+    r = oracle_mod.render_in(sc.cameras[0], 8, 3, 21, -1, True)
+    gi = np.random.default_rng(2).random((32, 32, 3)) + 0.5
+    gt, _, _ = oracle_mod.grad_reparam(osc, r, gi)
+    gv, _, _ = oracle_mod.grad_reparam(osc, r, gi, vertex=True)
+    sums = np.zeros_like(gt)
+    for t in range(sc.n_tris):
+        sums[sc.tri_shape[t]] += gv[t].sum(axis=0)
+    assert np.abs(sums - gt).max() <= 1e-9 * np.abs(gt).max()
+
+
+def _corner_field(sc, shape, fn):
+    """Per-corner displacement direction [n_tris, 3, 3]: fn(corner position) on `shape`."""
+    v = np.zeros((sc.n_tris, 3, 3))
+    for t in range(sc.n_tris):
+        if sc.tri_shape[t] == shape:
+            for k in range(3):
+                v[t, k] = fn(sc.vertices[t, k].astype(np.float64))
+    return v
+
+
+def test_square_scaling_closed_form(oracle_mod):
+    """Growing the square about its centre (corners move by eps (p - c)): its
+    projected area grows by 2 (s/d)^2 per unit eps, a non-rigid motion."""
+    sc = S.occluder_sky(center=(0.15, 0.1), depth=3.0, side=0.4, width=48, height=48)
+    th = np.tan(np.radians(20.0))
+    pix_area = (2 * th / 48) ** 2
+    exact = -3 * 2 * (0.4 / 3.0) ** 2 / pix_area
+    c = np.array([0.15, 0.1, -3.0])
+    v = _corner_field(sc, 0, lambda p: p - c)
+    r = oracle_mod.render_in(sc.cameras[0], 256, 2, 7, -1, True)
+    gv, _, _ = oracle_mod.grad_reparam(oracle_mod.OracleScene(sc), r, np.ones((48, 48, 3)), vertex=True)
+    got = float((gv * v).sum())
+    print("scaling: reparameterized", got, "closed form", exact)
+    assert got / exact == pytest.approx(1.0, abs=0.1)
+
+
+def _rotation_field(center, axis, sc, shape):
+    a = np.asarray(axis, np.float64)
+    a /= np.linalg.norm(a)
+    return _corner_field(sc, shape, lambda p: np.cross(a, p - np.asarray(center)))
+
+
+def test_tilting_light_and_occluder_match_finite_differences(oracle_mod):
+    """Tilting the light or the occluder (corners rotate about the centre, which turns
+    their normals) against central finite differences of the primal render."""
+    sc = S.shadow_scene(width=48, height=48)
+    cam = sc.cameras[0]
+    r = oracle_mod.render_in(cam, 32, 2, 3, -1, True)
+    gv, _, _ = oracle_mod.grad_reparam(oracle_mod.OracleScene(sc), r, np.ones((48, 48, 3)), vertex=True)
+    rf = oracle_mod.render_in(cam, 512, 2, 5, -1, True)
+    for shape, center, axis in ((1, (-1.2, 2.0, 0.0), (0, 0, 1)), (1, (-1.2, 2.0, 0.0), (1, 0, 0)),
+                                (2, (-0.6, 0.8, 0.0), (0, 0, 1)), (2, (-0.6, 0.8, 0.0), (1, 0, 0))):
+        v = _rotation_field(center, axis, sc, shape)
+        got = float((gv * v).sum())
+        h = 0.02
+        vals = []
+        for sgn in (1, -1):
+            moved = sc.translated(np.zeros((3, 3)))
+            moved.vertices = (sc.vertices.astype(np.float64) + sgn * h * v).astype(np.float32)
+            vals.append(oracle_mod.render(oracle_mod.OracleScene(moved), rf).sum())
+        fd = (vals[0] - vals[1]) / (2 * h)
+        print(f"tilt shape {shape} axis {axis}: reparameterized {got:.2f} finite differences {fd:.2f}")
+        assert abs(got - fd) < 0.15 * abs(fd) + 5.0
