@@ -713,6 +713,16 @@ def run_reparam_experiment(args):
     mhz = clk.get("sm_mhz") or 1477.0
     peak_tflops = sms * 128 * 2 * mhz * 1e6 / 1e12
     achieved = flops / (rp_ms / 1e3) / 1e12
+    # the same estimator with every triangle corner's position as a parameter
+    g_v = torch.zeros((sc.n_tris, 3, 3), device=dev)
+    ev_v = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ds.backward_reparam(replace(st, seed=12), grad_img, g_vertices=g_v)
+    flush.fill_(1.0)
+    ev_v[0].record(stream)
+    ds.backward_reparam(replace(st, seed=12), grad_img, g_vertices=g_v)
+    ev_v[1].record(stream)
+    torch.cuda.synchronize()
+    vert_ms = ev_v[0].elapsed_time(ev_v[1])
     # the plain PRB adjoint of the same samples, for scale (texture + roughness gradients)
     g_tex = torch.zeros_like(ds.textures[0])
     g_rough = torch.zeros_like(ds.roughness)
@@ -734,6 +744,8 @@ def run_reparam_experiment(args):
                        "l2": "flushed before each timed step", "forward_ms": round(fwd_ms, 3),
                        "reparam_adjoint_ms": round(rp_ms, 3), "plain_prb_adjoint_ms": round(plain_ms, 3),
                        "reparam_over_plain": round(rp_ms / plain_ms, 2), "rays_per_step": rays_step,
+                       "vertex_mode_ms": round(vert_ms, 3),
+                       "vertex_mode_mrays_s": round(rays_step / vert_ms / 1e3, 1),
                        "rays_per_sample": round(rays_step / (st.width * st.height * spp), 2),
                        "node_visits_per_ray": round(int(c[3]) / max(rays_step, 1), 2),
                        "tri_tests_per_ray": round(int(c[4]) / max(rays_step, 1), 2),

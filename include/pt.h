@@ -443,6 +443,18 @@ void pt_reparam_defaults(pt_reparam_opts* opts);
 int pt_render_backward_reparam(pt_scene* scene, const pt_render_desc* desc, const pt_params* params,
                                const pt_reparam_opts* opts, const float* grad_image, float* grad_translation,
                                unsigned long long* rays, void* stream);
+/* The same estimator with every triangle corner's position as a parameter (the
+ * paper's vertex-position optimisation, Sec. 4.10): a surface point moves with its
+ * barycentric weights, so the warp's plane points carry the barycentric
+ * coordinates of the (extended) hit triangle, and the cosine of a moving vertex
+ * adds the derivative of its triangle's normal.  grad_vertices: device float
+ * [n_tris][3][3] in the order of pt_scene_desc.vertices (corner k of triangle t at
+ * [t][k]), accumulated; shared positions are the caller's to sum.  The per-corner
+ * gradients of a shape sum to its translation gradient.  Same arguments, counters
+ * and errors as pt_render_backward_reparam. */
+int pt_render_backward_reparam_vertices(pt_scene* scene, const pt_render_desc* desc, const pt_params* params,
+                                        const pt_reparam_opts* opts, const float* grad_image, float* grad_vertices,
+                                        unsigned long long* rays, void* stream);
 
 /* Reads (and clears) the scene's device status word after synchronising
  * `stream`: *out = PT_OK or the first PT_ERR_* a kernel recorded. */

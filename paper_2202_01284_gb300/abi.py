@@ -155,6 +155,9 @@ SIGNATURES = {
     "pt_render_backward_reparam": ([C.c_void_p, C.POINTER(pt_render_desc), C.POINTER(pt_params),
                                     C.POINTER(pt_reparam_opts), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
                                    C.c_int),
+    "pt_render_backward_reparam_vertices": ([C.c_void_p, C.POINTER(pt_render_desc), C.POINTER(pt_params),
+                                             C.POINTER(pt_reparam_opts), C.c_void_p, C.c_void_p, C.c_void_p,
+                                             C.c_void_p], C.c_int),
     "pt_last_device_status": ([C.c_void_p, C.c_void_p, C.POINTER(C.c_int)], C.c_int),
     "pt_status_string": ([C.c_int], C.c_char_p),
     "pt_cache_create": ([C.POINTER(pt_cache_desc), C.POINTER(C.c_void_p)], C.c_int),
@@ -409,6 +412,14 @@ def pt_render_backward_reparam(handle: int, desc: pt_render_desc, params: pt_par
     check("pt_render_backward_reparam",
           load().pt_render_backward_reparam(handle, C.byref(desc), C.byref(params), C.byref(opts), _ptr(grad_image),
                                             _ptr(grad_translation), _ptr(rays), stream or None))
+
+
+def pt_render_backward_reparam_vertices(handle: int, desc: pt_render_desc, params: pt_params, opts: pt_reparam_opts,
+                                        grad_image, grad_vertices, rays=None, stream: int = 0) -> None:
+    check("pt_render_backward_reparam_vertices",
+          load().pt_render_backward_reparam_vertices(handle, C.byref(desc), C.byref(params), C.byref(opts),
+                                                     _ptr(grad_image), _ptr(grad_vertices), _ptr(rays),
+                                                     stream or None))
 
 
 def pt_last_device_status(handle: int, stream: int = 0) -> int:

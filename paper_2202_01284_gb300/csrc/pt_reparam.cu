@@ -139,7 +139,26 @@ struct WarpRay {
   int s_o, cam;
   float R, t0;
   unsigned long long st, inc;
+  int o_tri;         // vertex mode: original id of the origin's triangle (-1: camera)
+  float o_bu, o_bv;  // and the origin's barycentric coordinates on it
 };
+
+// Vertex mode output: corner k of original triangle t at [t][k][0..2].
+struct VertOut {
+  float* dst;
+  __device__ __forceinline__ void add(int t, const float3 (&g)[3]) {
+    float* d = dst + 9 * (size_t)t;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      atomicAdd(d + 3 * k, g[k].x);
+      atomicAdd(d + 3 * k + 1, g[k].y);
+      atomicAdd(d + 3 * k + 2, g[k].z);
+    }
+  }
+};
+__device__ __forceinline__ int tri_orig(const DevScene& S, int pos) {
+  return (int)__float_as_uint(__ldg(&S.tri_v[3 * pos]).w);
+}
 
 __device__ __forceinline__ float3 shfl3(float3 v, int src) {
   return f3(__shfl_sync(kFull, v.x, src), __shfl_sync(kFull, v.y, src), __shfl_sync(kFull, v.z, src));
@@ -157,9 +176,9 @@ __device__ __forceinline__ float3 group_sum3(float3 v, int gs) {
 // 32 / gs groups of gs >= N lanes; each round every group takes one pending ray
 // of some lane, and its lane j traces auxiliary ray j of that ray (the rays of a
 // lobe are coherent), so the reductions of the warp estimator are shuffles.
-template <int LAYOUT, bool INSTR>
+template <int LAYOUT, bool INSTR, bool VERT>
 __device__ __noinline__ unsigned process_warps(const LaunchArgs& A, const RpOpts& K, bool has, const WarpRay& mine,
-                                               GradOut& G, Counters<INSTR>& cnt) {
+                                               GradOut& G, VertOut& GV, Counters<INSTR>& cnt) {
   const DevScene& S = A.scene;
   const int lane = lane_id(), gs = K.group, grp = lane / gs, j = lane % gs;
   const int ng = 32 / gs;
@@ -182,6 +201,11 @@ __device__ __noinline__ unsigned process_warps(const LaunchArgs& A, const RpOpts
     w.t0 = __shfl_sync(kFull, mine.t0, sl);
     w.st = __shfl_sync(kFull, mine.st, sl);
     w.inc = __shfl_sync(kFull, mine.inc, sl);
+    if constexpr (VERT) {
+      w.o_tri = __shfl_sync(kFull, mine.o_tri, sl);
+      w.o_bu = __shfl_sync(kFull, mine.o_bu, sl);
+      w.o_bv = __shfl_sync(kFull, mine.o_bv, sl);
+    }
     const bool on = src >= 0 && j < K.n_aux;
     float alpha = 0.0f, t = 0.0f;
     int pos = -1;
@@ -213,35 +237,80 @@ __device__ __noinline__ unsigned process_warps(const LaunchArgs& A, const RpOpts
       S1 = group_sum(on ? 1.0f / Dj : 0.0f, gs);
       SP = group_sum3(on ? Pj * (1.0f / (Dj * Dj)) : f3(0.f, 0.f, 0.f), gs);
     }
-    float3 gv = f3(0.f, 0.f, 0.f);
+    float3 gv = f3(0.f, 0.f, 0.f);  // coefficient of the relative translation (origin part)
     int si = -1;
     if (on && pos >= 0) si = tri_shape(S, pos);
-    const bool contrib = si >= 0 && si != w.s_o;
+    const bool contrib = VERT ? pos >= 0 : (si >= 0 && si != w.s_o);
     if (contrib) {
       float b = 1.0f;
       float3 gb = f3(0.f, 0.f, 0.f);
       if (w.cam >= 0) b = cam_window(A, A.cams[w.cam], w.u, K.border, gb);
       const float3 mp = w.m - w.u * dot3(w.u, w.m);
       const float3 nrm = tri_normal(S, pos);
-      const float nu = dot3(nrm, w.u);
       const float di = dot3(nrm, wi) * t;
-      // A_i: the part of H_i that does not depend on the sample set
-      const float3 Ai = (mp - w.u * 2.0f + pi * K.kk) * (nu * b) + (nrm - w.u * nu) * b + gb * nu;
-      const float kb = K.kk * b * nu;
-      float3 coef = Ai * (1.0f / D) - P * (kb / (D * D));
+      const float3 base = (mp - w.u * 2.0f + pi * K.kk) * b;  // m_perp - 2u + kk p, windowed
+      float Dm = 0.0f;
+      float3 Pm = f3(0.f, 0.f, 0.f);
       if (K.jackknife) {
-        const float Dm = D - alpha - K.eps;
-        const float3 Pm = P - pi * alpha;
-        const float3 loo = Ai * (S1 - 1.0f / Dm) - (SP - Pm * (1.0f / (Dm * Dm))) * kb;
-        coef = coef * n - loo * ((n - 1.0f) / n);
+        Dm = D - alpha - K.eps;
+        Pm = P - pi * alpha;
       }
-      gv = coef * (w.R * alpha / di);
-      float v[3] = {gv.x, gv.y, gv.z};
-      if (warp_aggregate<3>((unsigned)si, v)) G.add(si, f3(v[0], v[1], v[2]));
+      // coefficient of a velocity field s(w) Delta with s linear in w: gradient g = (I - uu^T) grad s
+      auto coef_of = [&](float sv, float3 g) {
+        const float3 Ai = base * sv + g * b + gb * sv;
+        const float kb = K.kk * b * sv;
+        float3 c = Ai * (1.0f / D) - P * (kb / (D * D));
+        if (K.jackknife) {
+          const float3 loo = Ai * (S1 - 1.0f / Dm) - (SP - Pm * (1.0f / (Dm * Dm))) * kb;
+          c = c * n - loo * ((n - 1.0f) / n);
+        }
+        return c * (w.R * alpha);
+      };
+      // plane point seen along w: 1/t(w) = (n.w)/d; the origin moves as a whole
+      gv = coef_of(dot3(nrm, w.u) / di, (nrm - w.u * dot3(nrm, w.u)) * (1.0f / di));
+      if constexpr (VERT) {
+        // corner j of the hit triangle carries b_j(w)/t(w) = beta_j (n.w)/d + a_j.w with
+        // a_1 = (e2 x c)/c.c, a_2 = (c x e1)/c.c, a_0 = -(a_1 + a_2), beta_j = a_j.(o - v0) + [j = 0]
+        const float3 v0 = xyz(__ldg(&S.tri_v[3 * pos]));
+        const float3 e1 = xyz(__ldg(&S.tri_v[3 * pos + 1])), e2 = xyz(__ldg(&S.tri_v[3 * pos + 2]));
+        const float3 c = cross3(e1, e2);
+        const float icc = 1.0f / dot3(c, c);
+        const float3 a1 = cross3(e2, c) * icc, a2 = cross3(c, e1) * icc;
+        const float3 a0 = -(a1 + a2);
+        const float3 ov = w.o - v0;
+        const float nu = dot3(nrm, w.u) / di;
+        const float3 nperp = (nrm - w.u * dot3(nrm, w.u)) * (1.0f / di);
+        float3 gc[3];
+        const float3 aj[3] = {a0, a1, a2};
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          const float beta = dot3(aj[k], ov) + (k == 0 ? 1.0f : 0.0f);
+          gc[k] = coef_of(beta * nu + dot3(aj[k], w.u), nperp * beta + (aj[k] - w.u * dot3(aj[k], w.u)));
+        }
+        float v[9] = {gc[0].x, gc[0].y, gc[0].z, gc[1].x, gc[1].y, gc[1].z, gc[2].x, gc[2].y, gc[2].z};
+        const int to = tri_orig(S, pos);
+        if (warp_aggregate<9>((unsigned)to, v)) {
+          const float3 g3[3] = {f3(v[0], v[1], v[2]), f3(v[3], v[4], v[5]), f3(v[6], v[7], v[8])};
+          GV.add(to, g3);
+        }
+      } else {
+        float v[3] = {gv.x, gv.y, gv.z};
+        if (warp_aggregate<3>((unsigned)si, v)) G.add(si, f3(v[0], v[1], v[2]));
+      }
     }
-    // the origin moves with its own shape: minus the group's total
+    // the origin moves with its own shape (or triangle corners): minus the group's total
     const float3 go = group_sum3(gv, gs);
-    if (j == 0 && src >= 0 && w.s_o >= 0 && (go.x != 0.0f || go.y != 0.0f || go.z != 0.0f)) G.add(w.s_o, -go);
+    if (j == 0 && src >= 0 && (go.x != 0.0f || go.y != 0.0f || go.z != 0.0f)) {
+      if constexpr (VERT) {
+        if (w.o_tri >= 0) {
+          const float bo[3] = {1.0f - w.o_bu - w.o_bv, w.o_bu, w.o_bv};
+          const float3 g3[3] = {-go * bo[0], -go * bo[1], -go * bo[2]};
+          GV.add(w.o_tri, g3);
+        }
+      } else if (w.s_o >= 0) {
+        G.add(w.s_o, -go);
+      }
+    }
   }
   return rays;
 }
@@ -250,9 +319,27 @@ __device__ __noinline__ unsigned process_warps(const LaunchArgs& A, const RpOpts
 // sample by one vertex (its radiance comes from the radiance pass launched before,
 // as in split PRB), then the whole warp processes the reparameterized rays the
 // lanes posted.
-template <int LAYOUT, bool INSTR>
+// Gradient of log|n . u| with respect to the corners of the triangle at leaf
+// position pos (n its unit geometric normal): with c = e1 x e2 and
+// w = (u - n (n.u)) / |c|, d(n.u) = de1.(e2 x w) + de2.(w x e1).
+__device__ __forceinline__ void normal_log_grad(const DevScene& S, int pos, float3 u, float scale, float3 (&g)[3]) {
+  const float3 e1 = xyz(__ldg(&S.tri_v[3 * pos + 1])), e2 = xyz(__ldg(&S.tri_v[3 * pos + 2]));
+  const float3 c = cross3(e1, e2);
+  const float len = sqrtf(dot3(c, c));
+  const float3 nn = c * (1.0f / len);
+  const float nu = dot3(nn, u);
+  const float3 w = (u - nn * nu) * (scale / (len * nu));
+  g[1] = cross3(e2, w);
+  g[2] = cross3(w, e1);
+  g[0] = -(g[1] + g[2]);
+}
+
+// VERT: gradients of every triangle corner's position (grad_v [n_tris][3][3]);
+// otherwise of one translation per shape (grad_t [n_shapes][3]).
+template <int LAYOUT, bool INSTR, bool VERT>
 __global__ void __launch_bounds__(128) reparam_kernel(const __grid_constant__ LaunchArgs A, const RpOpts K,
-                                                      float* __restrict__ grad_t, unsigned long long* rays_out) {
+                                                      float* __restrict__ grad_t, float* __restrict__ grad_v,
+                                                      unsigned long long* rays_out) {
   extern __shared__ float s_grad[];
   const int n3 = 3 * A.scene.n_shapes;
   if (K.smem) {
@@ -260,6 +347,7 @@ __global__ void __launch_bounds__(128) reparam_kernel(const __grid_constant__ La
     __syncthreads();
   }
   GradOut G{K.smem ? s_grad : grad_t};
+  VertOut GV{grad_v};
   const DevScene& S = A.scene;
   const long long unit = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   PixelOf px{};
@@ -302,7 +390,7 @@ __global__ void __launch_bounds__(128) reparam_kernel(const __grid_constant__ La
       const float R = dot3(dl, P.Lrem);
       if (R != 0.0f) {
         w0 = WarpRay{P.ro, P.rd, fwd * (-3.0f / dot3(fwd, P.rd)), -1, px.cam, R,
-                     next.pos >= 0 ? next.t : INFINITY, aux.state, aux.inc};
+                     next.pos >= 0 ? next.t : INFINITY, aux.state, aux.inc, -1, 0.0f, 0.0f};
         h0 = true;
       }
       pcg_advance(aux, n2);
@@ -318,10 +406,11 @@ __global__ void __launch_bounds__(128) reparam_kernel(const __grid_constant__ La
       }
       ++rays;  // its twin in the radiance pass
       const bool block = hit.pos >= 0 && P.depth < A.max_depth;
-      int s_o = -1;
+      int s_o = -1, o_tri = -1;
       float3 n_s = z;
       if (hit.pos >= 0) {
         s_o = tri_shape(S, hit.pos);
+        o_tri = tri_orig(S, hit.pos);
         const float3 ng = tri_normal(S, hit.pos);
         n_s = dot3(ng, P.rd) < 0.0f ? ng : -ng;
       }
@@ -344,8 +433,13 @@ __global__ void __launch_bounds__(128) reparam_kernel(const __grid_constant__ La
             const Hit hl = closest<LAYOUT, INSTR>(S, P.so, P.sd, INFINITY, false, cnt);
             ++rays;
             w0 = WarpRay{P.so, P.sd, n_s * (1.0f / dot3(n_s, P.sd)), s_o, -1, R,
-                         hl.pos >= 0 ? hl.t : INFINITY, aux_nee.state, aux_nee.inc};
+                         hl.pos >= 0 ? hl.t : INFINITY, aux_nee.state, aux_nee.inc, o_tri, hit.u, hit.v};
             h0 = true;
+            if constexpr (VERT) {
+              float3 gn[3];
+              normal_log_grad(S, hit.pos, P.sd, R, gn);
+              GV.add(o_tri, gn);
+            }
           }
         }
         more = path_finish<false, false, INSTR>(A, P, occ, false, z, sink, cnt);
@@ -356,8 +450,13 @@ __global__ void __launch_bounds__(128) reparam_kernel(const __grid_constant__ La
             ++rays;
             cached = true;
             w1 = WarpRay{P.ro, P.rd, n_s * (1.0f / dot3(n_s, P.rd)), s_o, -1, R,
-                         next.pos >= 0 ? next.t : INFINITY, aux_bsdf.state, aux_bsdf.inc};
+                         next.pos >= 0 ? next.t : INFINITY, aux_bsdf.state, aux_bsdf.inc, o_tri, hit.u, hit.v};
             h1 = true;
+            if constexpr (VERT) {
+              float3 gn[3];
+              normal_log_grad(S, hit.pos, P.rd, R, gn);
+              GV.add(o_tri, gn);
+            }
           }
         }
       }
@@ -367,8 +466,8 @@ __global__ void __launch_bounds__(128) reparam_kernel(const __grid_constant__ La
       }
     }
     if (!__any_sync(kFull, live || h0 || h1 || (valid && si < A.spp))) break;
-    rays += process_warps<LAYOUT, INSTR>(A, K, h0, w0, G, cnt);
-    rays += process_warps<LAYOUT, INSTR>(A, K, h1, w1, G, cnt);
+    rays += process_warps<LAYOUT, INSTR, VERT>(A, K, h0, w0, G, GV, cnt);
+    rays += process_warps<LAYOUT, INSTR, VERT>(A, K, h1, w1, G, GV, cnt);
   }
   if (K.smem) {
     __syncthreads();
@@ -400,9 +499,9 @@ extern "C" void pt_reparam_defaults(pt_reparam_opts* o) {
   o->jackknife = 1;
 }
 
-extern "C" int pt_render_backward_reparam(pt_scene* s, const pt_render_desc* r, const pt_params* p,
-                                          const pt_reparam_opts* opts, const float* grad_image,
-                                          float* grad_translation, unsigned long long* rays, void* stream) {
+namespace {
+int reparam_launch(pt_scene* s, const pt_render_desc* r, const pt_params* p, const pt_reparam_opts* opts,
+                   const float* grad_image, float* grad_t, float* grad_v, unsigned long long* rays, void* stream) {
   pt_reparam_opts o;
   pt_reparam_defaults(&o);
   if (opts) o = *opts;
@@ -410,7 +509,7 @@ extern "C" int pt_render_backward_reparam(pt_scene* s, const pt_render_desc* r, 
       !(o.power >= 0.0f && o.power <= 16.0f) || !(o.miss >= 0.0f) || !(o.eps > 0.0f) || !(o.border > 0.0f) ||
       (o.jackknife != 0 && o.jackknife != 1))
     return PT_ERR_ARG;
-  if (!s || !r || !p || !grad_image || !grad_translation) return PT_ERR_ARG;
+  if (!s || !r || !p || !grad_image || (!grad_t && !grad_v)) return PT_ERR_ARG;
   LaunchArgs A;
   int st = fill_launch(s, r, p, A);
   if (st != PT_OK) return st;
@@ -428,8 +527,9 @@ extern "C" int pt_render_backward_reparam(pt_scene* s, const pt_render_desc* r, 
   K.e2k = expf(-2.0f * o.kappa);
   K.group = 2;
   while (K.group < o.n_aux) K.group *= 2;
+  const bool vert = grad_v != nullptr;
   const size_t smem = (size_t)s->n_shapes * 3 * sizeof(float);
-  K.smem = smem <= 32768 ? 1 : 0;
+  K.smem = (!vert && smem <= 32768) ? 1 : 0;
   pt_render_desc rd = *r;
   if (rd.block_size == 0) rd.block_size = 128;
   if (rd.block_size != 128) return PT_ERR_ARG;
@@ -440,12 +540,31 @@ extern "C" int pt_render_backward_reparam(pt_scene* s, const pt_render_desc* r, 
   const size_t sm = K.smem ? smem : 0;
   if ((st = radiance_pass(s, &rd, A, cs)) != PT_OK) return st;
   const dim3 gd((unsigned)grid), bd(block);
-  if (s->dev.layout == PT_BVH_WIDE) {
-    if (A.counters) reparam_kernel<PT_BVH_WIDE, true><<<gd, bd, sm, cs>>>(A, K, grad_translation, rays);
-    else reparam_kernel<PT_BVH_WIDE, false><<<gd, bd, sm, cs>>>(A, K, grad_translation, rays);
-  } else {
-    if (A.counters) reparam_kernel<PT_BVH_BINARY, true><<<gd, bd, sm, cs>>>(A, K, grad_translation, rays);
-    else reparam_kernel<PT_BVH_BINARY, false><<<gd, bd, sm, cs>>>(A, K, grad_translation, rays);
+  const int v = (s->dev.layout == PT_BVH_WIDE ? 4 : 0) | (A.counters ? 2 : 0) | (vert ? 1 : 0);
+  switch (v) {
+    case 0: reparam_kernel<PT_BVH_BINARY, false, false><<<gd, bd, sm, cs>>>(A, K, grad_t, grad_v, rays); break;
+    case 1: reparam_kernel<PT_BVH_BINARY, false, true><<<gd, bd, sm, cs>>>(A, K, grad_t, grad_v, rays); break;
+    case 2: reparam_kernel<PT_BVH_BINARY, true, false><<<gd, bd, sm, cs>>>(A, K, grad_t, grad_v, rays); break;
+    case 3: reparam_kernel<PT_BVH_BINARY, true, true><<<gd, bd, sm, cs>>>(A, K, grad_t, grad_v, rays); break;
+    case 4: reparam_kernel<PT_BVH_WIDE, false, false><<<gd, bd, sm, cs>>>(A, K, grad_t, grad_v, rays); break;
+    case 5: reparam_kernel<PT_BVH_WIDE, false, true><<<gd, bd, sm, cs>>>(A, K, grad_t, grad_v, rays); break;
+    case 6: reparam_kernel<PT_BVH_WIDE, true, false><<<gd, bd, sm, cs>>>(A, K, grad_t, grad_v, rays); break;
+    default: reparam_kernel<PT_BVH_WIDE, true, true><<<gd, bd, sm, cs>>>(A, K, grad_t, grad_v, rays); break;
   }
   return cudaGetLastError() == cudaSuccess ? PT_OK : PT_ERR_CUDA;
+}
+}  // namespace
+
+extern "C" int pt_render_backward_reparam(pt_scene* s, const pt_render_desc* r, const pt_params* p,
+                                          const pt_reparam_opts* opts, const float* grad_image,
+                                          float* grad_translation, unsigned long long* rays, void* stream) {
+  if (!grad_translation) return PT_ERR_ARG;
+  return reparam_launch(s, r, p, opts, grad_image, grad_translation, nullptr, rays, stream);
+}
+
+extern "C" int pt_render_backward_reparam_vertices(pt_scene* s, const pt_render_desc* r, const pt_params* p,
+                                                   const pt_reparam_opts* opts, const float* grad_image,
+                                                   float* grad_vertices, unsigned long long* rays, void* stream) {
+  if (!grad_vertices) return PT_ERR_ARG;
+  return reparam_launch(s, r, p, opts, grad_image, nullptr, grad_vertices, rays, stream);
 }

@@ -115,22 +115,33 @@ class DeviceScene:
         abi.pt_render_backward(self.handle, desc, p, grad_image.contiguous(), g,
                                torch.cuda.current_stream(grad_image.device).cuda_stream)
 
-    def backward_reparam(self, st: RenderSettings, grad_image, g_translation, cams=None, albedo=None,
-                         textures=None, roughness=None, env=None, seed=None, rays=None, **opts):
-        """pt_render_backward_reparam: accumulate into g_translation [n_shapes, 3] the
-        gradient of sum(grad_image * image) with respect to one translation per shape,
-        by reparameterized PRB (Sec. 4.7).  opts: pt_reparam_opts fields; rays: optional
-        int64 device counter of the rays traced."""
+    def backward_reparam(self, st: RenderSettings, grad_image, g_translation=None, cams=None, albedo=None,
+                         textures=None, roughness=None, env=None, seed=None, rays=None, g_vertices=None, **opts):
+        """Reparameterized PRB (Sec. 4.7): accumulate the gradient of sum(grad_image *
+        image) with respect to one translation per shape into g_translation
+        [n_shapes, 3] (pt_render_backward_reparam) and/or with respect to every
+        triangle corner's position into g_vertices [n_tris, 3, 3]
+        (pt_render_backward_reparam_vertices).  opts: pt_reparam_opts fields; rays:
+        optional int64 device counter of the rays traced."""
         cams = list(cams) if cams is not None else self.cameras
         p = abi.params_struct(self.albedo if albedo is None else albedo,
                               self.textures if textures is None else textures,
                               self.roughness if roughness is None else roughness, env)
         desc = self._desc(cams, st, seed=seed)
-        if g_translation.dtype != torch.float32 or not g_translation.is_contiguous() or \
-                tuple(g_translation.shape) != (self.n_shapes, 3):
-            raise ValueError("g_translation must be a contiguous float32 [n_shapes, 3] tensor")
-        abi.pt_render_backward_reparam(self.handle, desc, p, abi.reparam_opts(**opts), grad_image.contiguous(),
-                                       g_translation, rays, torch.cuda.current_stream(grad_image.device).cuda_stream)
+        stream = torch.cuda.current_stream(grad_image.device).cuda_stream
+        if g_translation is None and g_vertices is None:
+            raise ValueError("pass g_translation and/or g_vertices")
+        for g, shape, name in ((g_translation, (self.n_shapes, 3), "g_translation"),
+                               (g_vertices, (self.scene.n_tris, 3, 3), "g_vertices")):
+            if g is not None and (g.dtype != torch.float32 or not g.is_contiguous() or tuple(g.shape) != shape):
+                raise ValueError(f"{name} must be a contiguous float32 {list(shape)} tensor")
+        o = abi.reparam_opts(**opts)
+        if g_translation is not None:
+            abi.pt_render_backward_reparam(self.handle, desc, p, o, grad_image.contiguous(), g_translation, rays,
+                                           stream)
+        if g_vertices is not None:
+            abi.pt_render_backward_reparam_vertices(self.handle, desc, p, o, grad_image.contiguous(), g_vertices,
+                                                    rays, stream)
 
     # ------------------------------------------------------------------ wavefront variant
     def wavefront_forward(self, st: RenderSettings, calls: int = abi.PT_WF_TRACED, wave_paths: int = 0, cams=None,

@@ -158,3 +158,70 @@ def test_reparam_recovers_occluder_position(lib):
     print("recovered", t.detach().cpu().numpy()[2], "truth", truth[2], "loss", loss.item())
     assert np.abs(err[[0, 2]]).max() < 0.03   # started 0.15 / 0.08 away
     assert abs(err[1]) < 0.05
+
+
+def test_reparam_two_cameras_crop_and_lanes(lib, oracle_mod):
+    """Two cameras in one call, a ragged crop and every lane split: the gradient of the
+    call is the sum of the oracle's per-camera crops."""
+    from dataclasses import replace
+    from paper_2202_01284_gb300.render import DeviceScene, RenderSettings
+    sc = S.shadow_scene(width=40, height=30)
+    cam2 = S.Camera((1.2, 1.4, 1.0), (-0.4, 0.0, 0.0), (0.0, 1.0, 0.0), 50.0, 40, 30)
+    ds = DeviceScene(sc, layout=0)
+    crop = (5, 3, 29, 21)
+    gi = np.random.default_rng(7).random((2, 21, 29, 3)).astype(np.float32)
+    osc = oracle_mod.OracleScene(sc)
+    g_ref = np.zeros((3, 3))
+    for ci, cam in enumerate((sc.cameras[0], cam2)):
+        r = oracle_mod.render_in(cam, 6, 3, 13, 2, True, cam_index=ci, crop=crop)
+        g_ref += oracle_mod.grad_reparam(osc, r, gi[ci])[0]
+    base = RenderSettings(width=40, height=30, spp=6, max_depth=3, rr_depth=2, seed=13, crop=crop)
+    for lanes in (1, 2, 4, 8):
+        g = torch.zeros((3, 3), device="cuda")
+        ds.backward_reparam(replace(base, lanes_per_pixel=lanes), torch.as_tensor(gi, device="cuda"), g,
+                            cams=[sc.cameras[0], cam2])
+        torch.cuda.synchronize()
+        gg = g.cpu().numpy().astype(np.float64)
+        rel = np.abs(gg - g_ref).max() / np.abs(g_ref).max()
+        print("lanes", lanes, "max rel", rel)
+        assert rel < 1e-3
+
+
+def _compare_vertices(oracle_mod, sc, spp, max_depth, seed, gi, rr_depth=-1, layout=1, **opts):
+    from paper_2202_01284_gb300.render import DeviceScene, RenderSettings
+    cam = sc.cameras[0]
+    ds = DeviceScene(sc, layout=layout)
+    st = RenderSettings(width=cam.width, height=cam.height, spp=spp, max_depth=max_depth, rr_depth=rr_depth,
+                        seed=seed)
+    gv = torch.zeros((sc.n_tris, 3, 3), device="cuda")
+    gt = torch.zeros((sc.n_shapes, 3), device="cuda")
+    gim = torch.as_tensor(gi[None], dtype=torch.float32, device="cuda")
+    ds.backward_reparam(st, gim, gt, g_vertices=gv, **opts)
+    torch.cuda.synchronize()
+    assert ds.status() == 0
+    r = oracle_mod.render_in(cam, spp, max_depth, seed, rr_depth, True)
+    ref, _, _ = oracle_mod.grad_reparam(oracle_mod.OracleScene(sc), r, gi, vertex=True, **opts)
+    g = gv.cpu().numpy().astype(np.float64)
+    c = cosine(g.ravel(), ref.ravel())
+    rel = np.abs(g - ref).max() / np.abs(ref).max()
+    sums = np.zeros((sc.n_shapes, 3))
+    for t in range(sc.n_tris):
+        sums[sc.tri_shape[t]] += g[t].sum(axis=0)
+    gtn = gt.cpu().numpy().astype(np.float64)
+    srel = np.abs(sums - gtn).max() / np.abs(gtn).max()
+    print(f"{sc.name} vertices: cosine {c:.7f} max rel {rel:.2e}; corner sums vs translation {srel:.2e}")
+    return c, rel, srel
+
+
+def test_reparam_vertex_parity(lib, oracle_mod):
+    gi = np.random.default_rng(2).random((48, 48, 3)) + 0.5
+    c, rel, srel = _compare_vertices(oracle_mod, S.shadow_scene(width=48, height=48), 8, 3, 21, gi)
+    assert c >= 0.99999 and rel < 1e-3 and srel < 1e-4
+    gi = np.random.default_rng(3).random((48, 48, 3))
+    c, rel, srel = _compare_vertices(oracle_mod, S.occluder_sky(center=(0.5, 0.2), side=0.6, width=48, height=48),
+                                     8, 2, 5, gi)
+    assert c >= 0.99999 and rel < 1e-3 and srel < 1e-4
+    gi = np.random.default_rng(4).random((24, 24, 3))
+    c, rel, srel = _compare_vertices(oracle_mod, S.cornell(width=24, height=24), 2, 4, 9, gi, layout=0,
+                                     jackknife=0, n_aux=8)
+    assert c >= 0.9999 and rel < 1e-2 and srel < 1e-3
