@@ -1379,8 +1379,10 @@ D2 window(const CamWindow& c, VD w) {
 // the cosine's normal, (n' . u) / (n . u), when m is a cosine covector n / n.u and
 // the vertices move).  `out` gets (param, value).
 void warp_log_derivs(const Scene& s, const WarpSamples& ws, V3 o, const Origin& og, bool vertex, V3 m, V3 n_cos,
-                     std::vector<std::pair<int, double>>& out, const CamWindow* win = nullptr) {
+                     std::vector<std::pair<int, double>>& out, const CamWindow* win = nullptr,
+                     std::vector<std::pair<int, V3>>* wdot_out = nullptr) {
   out.clear();
+  if (wdot_out) wdot_out->clear();
   // the parameters that can move this ray: those of the hit shapes / triangles and the origin
   std::vector<int> ids;
   auto add = [&](int id) {
@@ -1415,21 +1417,78 @@ void warp_log_derivs(const Scene& s, const WarpSamples& ws, V3 o, const Origin& 
         VD V = field(constant(u));
         V3 v(V.x.v, V.y.v, V.z.v);
         V3 wdot = v - u * dot(u, v);
-        return dot(m, wdot) + div;
+        return std::make_pair(dot(m, wdot) + div, wdot);
       };
-      double full = ld(-1);
+      auto fv = ld(-1);
+      double full = fv.first;
+      V3 wd = fv.second;
       if (ws.jackknife && ws.n > 1) {
         // leave-one-out over all N samples (misses without weight contribute the full value)
         double loo = 0.0;
+        V3 wloo;
         int nh = (int)ws.hits.size();
-        for (int j = 0; j < nh; ++j) loo += ld(j);
-        loo += (ws.n - nh) * ld(-2);
+        for (int j = 0; j < nh; ++j) {
+          auto r = ld(j);
+          loo += r.first;
+          wloo = wloo + r.second;
+        }
+        auto r2 = ld(-2);
+        loo += (ws.n - nh) * r2.first;
+        wloo = wloo + r2.second * (double)(ws.n - nh);
         full = ws.n * full - (ws.n - 1.0) / ws.n * loo;
+        wd = wd * (double)ws.n - wloo * ((ws.n - 1.0) / ws.n);
       }
       if (dot(n_cos, n_cos) > 0) full += normal_derivative(s, og, P, u);
       out.push_back({p, full});
+      if (wdot_out) wdot_out->push_back({p, wd});
     }
 }
+
+// BSDF value with a direction in dual numbers (local frame, normal +z): diffuse,
+// GGX conductor and blend, the same formulas as bsdf_eval_t.
+void bsdf_value_dirs(const Mat& m, VD wi, VD wo, D2 out[3]) {
+  for (int c = 0; c < 3; ++c) out[c] = D2{};
+  D2 kd{0, 0, 0};
+  if (m.bsdf == BSDF_DIFFUSE || m.bsdf == BSDF_BLEND) {
+    const double w = m.bsdf == BSDF_DIFFUSE ? 1.0 : m.wd;
+    for (int c = 0; c < 3; ++c) out[c] = D2{m.albedo[c] * w / kPi, 0, 0};
+  }
+  if (m.bsdf == BSDF_CONDUCTOR || m.bsdf == BSDF_BLEND) {
+    VD sv{wi.x + wo.x, wi.y + wo.y, wi.z + wo.z};
+    VD h = divided(sv, d2sqrt(dotd(sv, sv)));
+    const double a2 = m.alpha * m.alpha;
+    D2 den = h.z * h.z * (a2 - 1.0) + D2{1, 0, 0};
+    D2 D = D2{a2 / kPi, 0, 0} / (den * den);
+    auto G1 = [&](D2 c) {
+      D2 tan2 = (D2{1, 0, 0} - c * c) / (c * c);
+      return D2{2, 0, 0} / (D2{1, 0, 0} + d2sqrt(D2{1, 0, 0} + tan2 * a2));
+    };
+    D2 G = G1(wi.z) * G1(wo.z);
+    D2 cd = dotd(wi, h);
+    D2 mcd = D2{1, 0, 0} - cd;
+    D2 m5 = mcd * mcd * mcd * mcd * mcd;
+    const double w = m.bsdf == BSDF_CONDUCTOR ? 1.0 : 1.0 - m.wd;
+    for (int c = 0; c < 3; ++c) {
+      D2 F = D2{m.f0[c], 0, 0} + m5 * (1.0 - m.f0[c]);
+      out[c] = out[c] + D * G * F / (wi.z * wo.z * 4.0) * w;
+    }
+  }
+}
+
+// Gradient (tangential, local frame) of log f_c with respect to the outgoing
+// (wrt_out) or incident direction, by chart duals around that direction.
+void bsdf_log_grad(const Mat& m, V3 wi, V3 wo, bool wrt_out, V3 g[3]) {
+  V3 d = wrt_out ? wo : wi;
+  Frame fr = make_frame(d);
+  VD dr{D2{d.x, fr.s.x, fr.t.x}, D2{d.y, fr.s.y, fr.t.y}, D2{d.z, fr.s.z, fr.t.z}};
+  VD dd = divided(dr, d2sqrt(dotd(dr, dr)));
+  D2 f[3];
+  bsdf_value_dirs(m, wrt_out ? constant(wi) : dd, wrt_out ? dd : constant(wo), f);
+  for (int c = 0; c < 3; ++c)
+    g[c] = f[c].v > 0 ? fr.s * (f[c].a / f[c].v) + fr.t * (f[c].b / f[c].v) : V3();
+}
+
+bool reparameterized(int bsdf) { return bsdf == BSDF_DIFFUSE || bsdf == BSDF_CONDUCTOR || bsdf == BSDF_BLEND; }
 
 // Forward-mode accumulator of the translation derivatives (all shapes at once).
 struct ReparamAcc {
@@ -1441,7 +1500,11 @@ struct ReparamAcc {
   std::vector<double> block;  // 4N uniforms of the current vertex: light ray, then BSDF ray
   V3 beta;
   std::vector<V3> bdot, ldot;
-  std::vector<std::pair<int, double>> lnee, lbsdf, tmp;
+  using Sparse = std::vector<std::pair<int, double>>;
+  using SparseV = std::vector<std::pair<int, V3>>;
+  Sparse lnee, lbsdf, tmp;
+  SparseV wnee, wbsdf, wprev;  // tangential direction change of the light ray, the BSDF ray, the previous ray
+  V3 nee_n, bsdf_n;            // world normal of the vertex the rays leave
   CamWindow win;
   bool vertex = false;
   void init(const Scene* sc, const ReparamOpts* o, uint64_t sd, const Camera& cam, bool vert) {
@@ -1467,26 +1530,60 @@ struct ReparamAcc {
     std::vector<double> uni(2 * op->n_aux);
     for (double& x : uni) x = aux.uniform();
     WarpSamples ws = warp_samples(*s, *op, o, d, uni.data());
-    warp_log_derivs(*s, ws, o, Origin{}, vertex, fwd * (-3.0 / dot(fwd, d)), V3(), tmp, &win);
+    warp_log_derivs(*s, ws, o, Origin{}, vertex, fwd * (-3.0 / dot(fwd, d)), V3(), tmp, &win, &wprev);
     beta = V3(1, 1, 1);
     for (auto& pv : tmp) bdot[pv.first] = V3(1, 1, 1) * pv.second;
   }
   void vertex_block() {
     for (double& x : block) x = aux.uniform();
   }
-  void ray(V3 o, V3 d, int tri, double bu, double bv, V3 n, int bsdf, const double* uni,
-           std::vector<std::pair<int, double>>& out) {
+  void ray(V3 o, V3 d, int tri, double bu, double bv, V3 n, int bsdf, const double* uni, Sparse& out, SparseV& wout) {
     out.clear();
-    if (bsdf != BSDF_DIFFUSE) return;
+    wout.clear();
+    if (!reparameterized(bsdf)) return;
     WarpSamples ws = warp_samples(*s, *op, o, d, uni);
     Origin og{s->tri_shape[tri], tri, bu, bv};
-    warp_log_derivs(*s, ws, o, og, vertex, n * (1.0 / dot(n, d)), n, out);
+    warp_log_derivs(*s, ws, o, og, vertex, n * (1.0 / dot(n, d)), n, out, nullptr, &wout);
   }
   void nee_ray(V3 o, V3 d, int tri, double bu, double bv, V3 n, int bsdf) {
-    ray(o, d, tri, bu, bv, n, bsdf, block.data(), lnee);
+    nee_n = n;
+    ray(o, d, tri, bu, bv, n, bsdf, block.data(), lnee, wnee);
   }
   void bsdf_ray(V3 o, V3 d, int tri, double bu, double bv, V3 n, int bsdf) {
-    ray(o, d, tri, bu, bv, n, bsdf, block.data() + 2 * op->n_aux, lbsdf);
+    bsdf_n = n;
+    ray(o, d, tri, bu, bv, n, bsdf, block.data() + 2 * op->n_aux, lbsdf, wbsdf);
+  }
+  // Per-channel log-derivative of one term of vertex `vi` leaving along wl (local):
+  // the ray's warp terms, plus the BSDF's dependence on the outgoing direction
+  // (turned by this ray's warp) and on the incident one (turned by the previous
+  // ray's warp; it points back along that ray).
+  std::vector<std::pair<int, V3>> term(const VertexInfo& vi, V3 wl, V3 n, const Sparse& l, const SparseV& w) {
+    std::vector<std::pair<int, V3>> out;
+    for (auto& pv : l) out.push_back({pv.first, V3(1, 1, 1) * pv.second});
+    if (vi.m.bsdf == BSDF_DIFFUSE) return out;
+    Frame fr = make_frame(n);
+    V3 go[3], gi[3];
+    bsdf_log_grad(vi.m, vi.wi, wl, true, go);
+    bsdf_log_grad(vi.m, vi.wi, wl, false, gi);
+    V3 gow[3], giw[3];
+    for (int c = 0; c < 3; ++c) {
+      gow[c] = fr.to_world(go[c]);
+      giw[c] = fr.to_world(gi[c]);
+    }
+    auto add = [&](int p, V3 v) {
+      for (auto& q : out)
+        if (q.first == p) {
+          q.second = q.second + v;
+          return;
+        }
+      out.push_back({p, v});
+    };
+    for (auto& pw : w) add(pw.first, V3(dot(gow[0], pw.second), dot(gow[1], pw.second), dot(gow[2], pw.second)));
+    for (auto& pw : wprev) {
+      V3 di = -pw.second;  // the incident direction points back along the previous ray
+      add(pw.first, V3(dot(giw[0], di), dot(giw[1], di), dot(giw[2], di)));
+    }
+    return out;
   }
   void emission(V3, V3 le_w, int, V3, double) {
     for (int p = 0; p < np; ++p) ldot[p] = ldot[p] + mul(bdot[p], le_w);
@@ -1494,18 +1591,20 @@ struct ReparamAcc {
   void nee(const VertexInfo& vi, V3 wl, V3 scale, V3 c, int, V3, double) {
     V3 f = bsdf_eval(vi.m, vi.wi, wl);
     for (int p = 0; p < np; ++p) ldot[p] = ldot[p] + mul(mul(bdot[p], f), scale);
-    for (auto& pv : lnee) ldot[pv.first] = ldot[pv.first] + c * pv.second;
+    for (auto& pv : term(vi, wl, nee_n, lnee, wnee)) ldot[pv.first] = ldot[pv.first] + mul(c, pv.second);
   }
   void scatter(const VertexInfo& vi, V3 wo, double k) {
     V3 f = bsdf_eval(vi.m, vi.wi, wo);
     V3 nb = mul(beta, f) * k;
     for (int p = 0; p < np; ++p) bdot[p] = mul(bdot[p], f) * k;
-    for (auto& pv : lbsdf) bdot[pv.first] = bdot[pv.first] + nb * pv.second;
+    for (auto& pv : term(vi, wo, bsdf_n, lbsdf, wbsdf)) bdot[pv.first] = bdot[pv.first] + mul(nb, pv.second);
     beta = nb;
+    wprev = wbsdf;
   }
   void scatter_delta(double w) {
     beta = beta * w;
     for (auto& b : bdot) b = b * w;
+    wprev.clear();  // a delta lobe's outgoing ray is not reparameterized
   }
   void roulette(double q) {
     beta = beta * (1.0 / q);

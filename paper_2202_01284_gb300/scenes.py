@@ -579,12 +579,13 @@ def occluder_sky(center=(0.15, 0.1), depth=3.0, side=0.4, env_radiance=1.0, widt
 
 def shadow_scene(light=(-1.2, 2.0, 0.0), light_half=0.25, occluder=(-0.6, 0.8, 0.0), occluder_half=0.3,
                  camera=((1.6, 0.5, 0.0), (-0.2, 0.0, 0.0)), vfov_deg=40.0, width=64, height=64,
-                 radiance=20.0) -> Scene:
-    """A diffuse floor, a square area light and a square occluder casting a shadow.
+                 radiance=20.0, floor_bsdf=BSDF_DIFFUSE, floor_alpha=0.3) -> Scene:
+    """A floor, a square area light and a square occluder casting a shadow.
 
-    Shapes: 0 floor (y = 0, |x|,|z| <= 2, albedo row 0), 1 light (facing -y,
-    radiance `radiance`, black BSDF), 2 occluder (horizontal, albedo row 1).
-    Nothing else: rays that miss see black.
+    Shapes: 0 floor (y = 0, |x|,|z| <= 2; diffuse with albedo row 0, or a GGX
+    conductor of roughness floor_alpha and F0 (0.9, 0.7, 0.5), or a blend), 1 light
+    (facing -y, radiance `radiance`, black BSDF), 2 occluder (horizontal, diffuse,
+    albedo row 1).  Nothing else: rays that miss see black.
     """
     tris, uvs, shp = [], [], []
 
@@ -603,6 +604,9 @@ def shadow_scene(light=(-1.2, 2.0, 0.0), light_half=0.25, occluder=(-0.6, 0.8, 0
     add(((ox - h, oy, oz + h), (ox + h, oy, oz + h), (ox + h, oy, oz - h), (ox - h, oy, oz - h)), 2)
     st = _shape_table(3)
     st["bsdf"][[0, 2]] = BSDF_DIFFUSE
+    st["bsdf"][0] = floor_bsdf
+    st["alpha"][0] = floor_alpha
+    st["f0"][0] = (0.9, 0.7, 0.5) if floor_bsdf == BSDF_CONDUCTOR else (0.04, 0.04, 0.04)
     st["albedo_index"][0] = 0
     st["albedo_index"][2] = 1
     st["bsdf"][1] = BSDF_NONE

@@ -190,3 +190,28 @@ def test_tilting_light_and_occluder_match_finite_differences(oracle_mod):
         fd = (vals[0] - vals[1]) / (2 * h)
         print(f"tilt shape {shape} axis {axis}: reparameterized {got:.2f} finite differences {fd:.2f}")
         assert abs(got - fd) < 0.15 * abs(fd) + 5.0
+
+
+@pytest.mark.parametrize("bsdf", [S.BSDF_CONDUCTOR, S.BSDF_BLEND])
+def test_glossy_receiver_matches_finite_differences(oracle_mod, bsdf):
+    """A glossy floor (GGX conductor, or the diffuse + GGX blend): its BSDF value
+    depends on both directions, so a ray's warp also turns the next vertex's
+    incident direction.  Moving the light and the occluder against central finite
+    differences of the primal render."""
+    sc = S.shadow_scene(width=48, height=48, floor_bsdf=bsdf, floor_alpha=0.3)
+    cam = sc.cameras[0]
+    r = oracle_mod.render_in(cam, 64, 2, 3, -1, True)
+    g, _, _ = oracle_mod.grad_reparam(oracle_mod.OracleScene(sc), r, np.ones((48, 48, 3)))
+    rf = oracle_mod.render_in(cam, 1024, 2, 5, -1, True)
+    h = 0.01
+    fd = np.zeros((3, 3))
+    for shape in (1, 2):
+        for axis in range(3):
+            off = np.zeros((3, 3))
+            off[shape, axis] = h
+            ip = oracle_mod.render(oracle_mod.OracleScene(sc.translated(off)), rf).sum()
+            im = oracle_mod.render(oracle_mod.OracleScene(sc.translated(-off)), rf).sum()
+            fd[shape, axis] = (ip - im) / (2 * h)
+    print("reparameterized\n", g, "\nfinite differences\n", fd)
+    for shape in (1, 2):
+        assert np.abs(g[shape] - fd[shape]).max() < 0.25 * np.abs(fd[shape]).max()
