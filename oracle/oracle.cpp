@@ -1378,6 +1378,10 @@ D2 window(const CamWindow& c, VD w) {
 // move it: d/dtheta log(integrand * det) = m.(P_u V) + div V (+ the derivative of
 // the cosine's normal, (n' . u) / (n . u), when m is a cosine covector n / n.u and
 // the vertices move).  `out` gets (param, value).
+struct LogDeriv {
+  double l;   // m . (tangential V) + div V
+  V3 wdot;    // tangential V: how the ray direction turns
+};
 void warp_log_derivs(const Scene& s, const WarpSamples& ws, V3 o, const Origin& og, bool vertex, V3 m, V3 n_cos,
                      std::vector<std::pair<int, double>>& out, const CamWindow* win = nullptr,
                      std::vector<std::pair<int, V3>>* wdot_out = nullptr) {
@@ -1417,24 +1421,24 @@ void warp_log_derivs(const Scene& s, const WarpSamples& ws, V3 o, const Origin& 
         VD V = field(constant(u));
         V3 v(V.x.v, V.y.v, V.z.v);
         V3 wdot = v - u * dot(u, v);
-        return std::make_pair(dot(m, wdot) + div, wdot);
+        return LogDeriv{dot(m, wdot) + div, wdot};
       };
-      auto fv = ld(-1);
-      double full = fv.first;
-      V3 wd = fv.second;
+      LogDeriv fv = ld(-1);
+      double full = fv.l;
+      V3 wd = fv.wdot;
       if (ws.jackknife && ws.n > 1) {
         // leave-one-out over all N samples (misses without weight contribute the full value)
         double loo = 0.0;
         V3 wloo;
         int nh = (int)ws.hits.size();
         for (int j = 0; j < nh; ++j) {
-          auto r = ld(j);
-          loo += r.first;
-          wloo = wloo + r.second;
+          LogDeriv r = ld(j);
+          loo += r.l;
+          wloo = wloo + r.wdot;
         }
-        auto r2 = ld(-2);
-        loo += (ws.n - nh) * r2.first;
-        wloo = wloo + r2.second * (double)(ws.n - nh);
+        LogDeriv r2 = ld(-2);
+        loo += (ws.n - nh) * r2.l;
+        wloo = wloo + r2.wdot * (double)(ws.n - nh);
         full = ws.n * full - (ws.n - 1.0) / ws.n * loo;
         wd = wd * (double)ws.n - wloo * ((ws.n - 1.0) / ws.n);
       }

@@ -131,9 +131,12 @@ __device__ __forceinline__ void pcg_advance(Pcg32& r, unsigned long long delta) 
   r.state = acc_mult * r.state + acc_plus;
 }
 
-// A reparameterized ray waiting for its warp: origin, direction, cosine/measure
-// covector, origin shape (-1: camera), camera index for the window (-1: none),
-// weight R, its own hit distance and the auxiliary stream at its first uniform.
+// A reparameterized ray waiting for its warp: origin, direction, the covector M of
+// its integrand's log-derivative in the ray direction weighted by the radiance it
+// carries (R times the cosine / measure term, plus the BSDF's directional terms),
+// origin shape (-1: camera), camera index for the window (-1: none), weight R =
+// dLoss/dI . radiance, its own hit distance and the auxiliary stream at its first
+// uniform.  Its derivative is M . V + R div V.
 struct WarpRay {
   float3 o, u, m;
   int s_o, cam;
@@ -248,7 +251,7 @@ __device__ __noinline__ unsigned process_warps(const LaunchArgs& A, const RpOpts
       const float3 mp = w.m - w.u * dot3(w.u, w.m);
       const float3 nrm = tri_normal(S, pos);
       const float di = dot3(nrm, wi) * t;
-      const float3 base = (mp - w.u * 2.0f + pi * K.kk) * b;  // m_perp - 2u + kk p, windowed
+      const float3 base = (mp + (pi * K.kk - w.u * 2.0f) * w.R) * b;  // M_perp + R (kk p - 2u), windowed
       float Dm = 0.0f;
       float3 Pm = f3(0.f, 0.f, 0.f);
       if (K.jackknife) {
@@ -257,14 +260,14 @@ __device__ __noinline__ unsigned process_warps(const LaunchArgs& A, const RpOpts
       }
       // coefficient of a velocity field s(w) Delta with s linear in w: gradient g = (I - uu^T) grad s
       auto coef_of = [&](float sv, float3 g) {
-        const float3 Ai = base * sv + g * b + gb * sv;
-        const float kb = K.kk * b * sv;
+        const float3 Ai = base * sv + (g * b + gb * sv) * w.R;
+        const float kb = K.kk * b * sv * w.R;
         float3 c = Ai * (1.0f / D) - P * (kb / (D * D));
         if (K.jackknife) {
           const float3 loo = Ai * (S1 - 1.0f / Dm) - (SP - Pm * (1.0f / (Dm * Dm))) * kb;
           c = c * n - loo * ((n - 1.0f) / n);
         }
-        return c * (w.R * alpha);
+        return c * alpha;
       };
       // plane point seen along w: 1/t(w) = (n.w)/d; the origin moves as a whole
       gv = coef_of(dot3(nrm, w.u) / di, (nrm - w.u * dot3(nrm, w.u)) * (1.0f / di));
@@ -319,6 +322,87 @@ __device__ __noinline__ unsigned process_warps(const LaunchArgs& A, const RpOpts
 // sample by one vertex (its radiance comes from the radiance pass launched before,
 // as in split PRB), then the whole warp processes the reparameterized rays the
 // lanes posted.
+// Gradients of log f_c with respect to the outgoing (go) and incident (gi)
+// directions, local frame (n = +z), for the glossy BSDFs: GGX conductor, and the
+// blend w albedo/pi + (1 - w) GGX; zero for diffuse.  With h = (wi + wo)/|wi + wo|,
+// f = F(c_d) D(c_h) G1(c_i) G1(c_o) / (4 c_i c_o), c_d = wi.h = |wi + wo|/2:
+// d log D / d c_h = -4 c_h (a^2 - 1) / (c_h^2 (a^2 - 1) + 1), d c_h / d w = (z - h c_h)/|wi + wo|,
+// d log G1 / d c = a^2 / (r c^3 (1 + r)) with r = sqrt(1 + a^2 (1 - c^2)/c^2),
+// d log F_c / d c_d = -5 (1 - F0_c)(1 - c_d)^4 / F_c with d c_d / d w = h/2 (tangentially).
+__device__ void glossy_log_grad(int type, float alpha, float3 f0, float wd, float3 albedo, float3 wi, float3 wo,
+                                float3 (&go)[3], float3 (&gi)[3]) {
+  for (int c = 0; c < 3; ++c) go[c] = gi[c] = f3(0.f, 0.f, 0.f);
+  if (type != PT_BSDF_CONDUCTOR && type != PT_BSDF_BLEND) return;
+  if (!(wi.z > 0.0f) || !(wo.z > 0.0f)) return;
+  const float3 zz = f3(0.f, 0.f, 1.f);
+  const float3 sv = wi + wo;
+  const float sl = sqrtf(dot3(sv, sv));
+  const float3 h = sv * (1.0f / sl);
+  const float ch = h.z, cd = 0.5f * sl, a2 = alpha * alpha;
+  const float den = ch * ch * (a2 - 1.0f) + 1.0f;
+  const float3 common = (zz - h * ch) * (-4.0f * ch * (a2 - 1.0f) / (den * sl));
+  auto G1 = [&](float c, float& dlog) {
+    const float r = sqrtf(1.0f + a2 * (1.0f - c * c) / (c * c));
+    dlog = a2 / (r * c * c * c * (1.0f + r));
+    return 2.0f / (1.0f + r);
+  };
+  float dgi, dgo;
+  const float G = G1(wi.z, dgi) * G1(wo.z, dgo);
+  const float3 bo = common + zz * (dgo - 1.0f / wo.z);
+  const float3 bi = common + zz * (dgi - 1.0f / wi.z);
+  const float k = a2 / (PT_PI * den * den) * G / (4.0f * wi.z * wo.z);
+  const float m = 1.0f - cd, m4 = m * m * m * m;
+  const float f0c[3] = {f0.x, f0.y, f0.z}, alb[3] = {albedo.x, albedo.y, albedo.z};
+  for (int c = 0; c < 3; ++c) {
+    const float F = f0c[c] + (1.0f - f0c[c]) * m4 * m;
+    const float3 gF = h * (F > 0.0f ? -2.5f * (1.0f - f0c[c]) * m4 / F : 0.0f);
+    float share = 1.0f;  // fraction of f_c that depends on the directions
+    if (type == PT_BSDF_BLEND) {
+      const float fg = (1.0f - wd) * k * F;
+      const float f = wd * alb[c] * PT_INV_PI + fg;
+      share = f > 0.0f ? fg / f : 0.0f;
+    }
+    go[c] = (bo + gF) * share;
+    gi[c] = (bi + gF) * share;
+  }
+}
+
+// The glossy parameters of the material at a hit (as path_shade resolves them).
+struct Gloss {
+  int type;
+  float alpha, wd;
+  float3 f0, albedo;
+};
+__device__ Gloss gloss_at(const LaunchArgs& A, const Hit& hit) {
+  const DevScene& S = A.scene;
+  Gloss g;
+  const float4 ta0 = __ldg(&S.tri_a[2 * hit.pos]);
+  const float4 ta1 = __ldg(&S.tri_a[2 * hit.pos + 1]);
+  const int4* shp = reinterpret_cast<const int4*>(&S.shapes[__float_as_int(ta1.z)]);
+  const int4 sw0 = __ldg(shp);
+  const float4 sw1 = __ldg(reinterpret_cast<const float4*>(shp + 1));
+  g.type = sw0.x;
+  g.alpha = sw0.w >= 0 ? __ldg(&A.params.rough[sw0.w]) : sw1.x;
+  g.wd = sw1.z;
+  g.f0 = xyz(__ldg(reinterpret_cast<const float4*>(shp + 2)));
+  g.albedo = f3(0.f, 0.f, 0.f);
+  if (g.type == PT_BSDF_BLEND) {
+    if (sw0.y >= 0) {
+      const float b0 = 1.0f - hit.u - hit.v;
+      const float tu = b0 * ta0.x + hit.u * ta0.z + hit.v * ta1.x;
+      const float tv = b0 * ta0.y + hit.u * ta0.w + hit.v * ta1.y;
+      const int w = A.params.tex_w[sw0.y], h = A.params.tex_h[sw0.y];
+      const int x = min((int)(fmaxf(tu, 0.0f) * (float)w), w - 1);
+      const int y = min((int)(fmaxf(tv, 0.0f) * (float)h), h - 1);
+      g.albedo = xyz(__ldg(&A.params.tex[sw0.y][y * w + x]));
+    } else if (sw0.z >= 0) {
+      const float* a = &A.params.albedo[3 * sw0.z];
+      g.albedo = f3(__ldg(a), __ldg(a + 1), __ldg(a + 2));
+    }
+  }
+  return g;
+}
+
 // Gradient of log|n . u| with respect to the corners of the triangle at leaf
 // position pos (n its unit geometric normal): with c = e1 x e2 and
 // w = (u - n (n.u)) / |c|, d(n.u) = de1.(e2 x w) + de2.(w x e1).
@@ -372,6 +456,10 @@ __global__ void __launch_bounds__(128) reparam_kernel(const __grid_constant__ La
   aux.state = aux.inc = 0ull;
   bool cached = false;
   Hit next{};
+  // The ray that arrives at the lane's next vertex (camera or BSDF ray): posted after
+  // that vertex, whose glossy BSDF may add terms for its incident direction.
+  WarpRay arr{};
+  bool has_arr = false;
   const unsigned long long n2 = 2ull * (unsigned long long)K.n_aux;
   for (;;) {
     WarpRay w0{}, w1{};
@@ -388,11 +476,9 @@ __global__ void __launch_bounds__(128) reparam_kernel(const __grid_constant__ La
       ++rays;
       cached = true;
       const float R = dot3(dl, P.Lrem);
-      if (R != 0.0f) {
-        w0 = WarpRay{P.ro, P.rd, fwd * (-3.0f / dot3(fwd, P.rd)), -1, px.cam, R,
-                     next.pos >= 0 ? next.t : INFINITY, aux.state, aux.inc, -1, 0.0f, 0.0f};
-        h0 = true;
-      }
+      arr = WarpRay{P.ro, P.rd, fwd * (-3.0f * R / dot3(fwd, P.rd)), -1, px.cam, R,
+                    next.pos >= 0 ? next.t : INFINITY, aux.state, aux.inc, -1, 0.0f, 0.0f};
+      has_arr = true;
       pcg_advance(aux, n2);
       live = true;
     } else if (live) {
@@ -408,6 +494,7 @@ __global__ void __launch_bounds__(128) reparam_kernel(const __grid_constant__ La
       const bool block = hit.pos >= 0 && P.depth < A.max_depth;
       int s_o = -1, o_tri = -1;
       float3 n_s = z;
+      const float3 wi_w = -P.rd;
       if (hit.pos >= 0) {
         s_o = tri_shape(S, hit.pos);
         o_tri = tri_orig(S, hit.pos);
@@ -420,20 +507,49 @@ __global__ void __launch_bounds__(128) reparam_kernel(const __grid_constant__ La
         pcg_advance(aux_bsdf, n2);
         pcg_advance(aux, 2ull * n2);
       }
+      float3 inc = z;  // covector of this vertex's terms in its incident direction (weighted)
+      WarpRay out{};
+      bool has_out = false;
       if (more) {
         bool occ = false;
         if (P.has_shadow) {
           occ = closest<LAYOUT, INSTR>(S, P.so, P.sd, P.stmax, true, cnt).pos >= 0;
           rays += 2;
         }
-        const bool diffuse = block && P.mtype == PT_BSDF_DIFFUSE;
-        if (diffuse && P.has_shadow && !occ) {
+        const int mt = P.mtype;
+        const bool warp = block && (mt == PT_BSDF_DIFFUSE || mt == PT_BSDF_CONDUCTOR || mt == PT_BSDF_BLEND);
+        const bool glossy = warp && mt != PT_BSDF_DIFFUSE;
+        Gloss gl{};
+        Frame fr{};
+        float3 wi_l = z;
+        if (glossy) {
+          gl = gloss_at(A, hit);
+          fr = make_frame(n_s);
+          wi_l = fr.to_local(wi_w);
+        }
+        // covector of the term C (per channel) leaving along d: R n/(n.d) plus, at a
+        // glossy vertex, sum_c dl_c C_c grad_out log f_c; adds to `inc` the incident part
+        auto covector = [&](float3 d, float3 C, float R) {
+          float3 M = n_s * (R / dot3(n_s, d));
+          if (glossy) {
+            float3 go[3], gi[3];
+            glossy_log_grad(gl.type, gl.alpha, gl.f0, gl.wd, gl.albedo, wi_l, fr.to_local(d), go, gi);
+            const float wc[3] = {dl.x * C.x, dl.y * C.y, dl.z * C.z};
+            for (int c = 0; c < 3; ++c) {
+              M = M + fr.to_world(go[c]) * wc[c];
+              inc = inc + fr.to_world(gi[c]) * wc[c];
+            }
+          }
+          return M;
+        };
+        if (warp && P.has_shadow && !occ) {
           const float R = dot3(dl, P.c_nee);
-          if (R != 0.0f) {
+          const float3 M = covector(P.sd, P.c_nee, R);
+          if (R != 0.0f || M.x != 0.0f || M.y != 0.0f || M.z != 0.0f) {
             const Hit hl = closest<LAYOUT, INSTR>(S, P.so, P.sd, INFINITY, false, cnt);
             ++rays;
-            w0 = WarpRay{P.so, P.sd, n_s * (1.0f / dot3(n_s, P.sd)), s_o, -1, R,
-                         hl.pos >= 0 ? hl.t : INFINITY, aux_nee.state, aux_nee.inc, o_tri, hit.u, hit.v};
+            w0 = WarpRay{P.so, P.sd, M, s_o, -1, R, hl.pos >= 0 ? hl.t : INFINITY, aux_nee.state, aux_nee.inc,
+                         o_tri, hit.u, hit.v};
             h0 = true;
             if constexpr (VERT) {
               float3 gn[3];
@@ -443,16 +559,18 @@ __global__ void __launch_bounds__(128) reparam_kernel(const __grid_constant__ La
           }
         }
         more = path_finish<false, false, INSTR>(A, P, occ, false, z, sink, cnt);
-        if (more && diffuse) {
-          const float R = dot3(dl, f3(fmaxf(P.Lrem.x, 0.f), fmaxf(P.Lrem.y, 0.f), fmaxf(P.Lrem.z, 0.f)));
-          if (R != 0.0f) {
-            next = closest<LAYOUT, INSTR>(S, P.ro, P.rd, INFINITY, false, cnt);
-            ++rays;
-            cached = true;
-            w1 = WarpRay{P.ro, P.rd, n_s * (1.0f / dot3(n_s, P.rd)), s_o, -1, R,
-                         next.pos >= 0 ? next.t : INFINITY, aux_bsdf.state, aux_bsdf.inc, o_tri, hit.u, hit.v};
-            h1 = true;
-            if constexpr (VERT) {
+        if (more && warp) {
+          const float3 C = f3(fmaxf(P.Lrem.x, 0.f), fmaxf(P.Lrem.y, 0.f), fmaxf(P.Lrem.z, 0.f));
+          const float R = dot3(dl, C);
+          const float3 M = covector(P.rd, C, R);
+          next = closest<LAYOUT, INSTR>(S, P.ro, P.rd, INFINITY, false, cnt);
+          ++rays;
+          cached = true;
+          out = WarpRay{P.ro, P.rd, M, s_o, -1, R, next.pos >= 0 ? next.t : INFINITY, aux_bsdf.state,
+                        aux_bsdf.inc, o_tri, hit.u, hit.v};
+          has_out = true;
+          if constexpr (VERT) {
+            if (R != 0.0f) {
               float3 gn[3];
               normal_log_grad(S, hit.pos, P.rd, R, gn);
               GV.add(o_tri, gn);
@@ -460,6 +578,16 @@ __global__ void __launch_bounds__(128) reparam_kernel(const __grid_constant__ La
           }
         }
       }
+      // the ray that arrived here: its direction is minus this vertex's incident one
+      if (has_arr) {
+        arr.m = arr.m - inc;
+        if (arr.R != 0.0f || arr.m.x != 0.0f || arr.m.y != 0.0f || arr.m.z != 0.0f) {
+          w1 = arr;
+          h1 = true;
+        }
+      }
+      arr = out;
+      has_arr = has_out;
       if (!more) {
         live = false;
         si += A.lanes_per_pixel;

@@ -225,3 +225,24 @@ def test_reparam_vertex_parity(lib, oracle_mod):
     c, rel, srel = _compare_vertices(oracle_mod, S.cornell(width=24, height=24), 2, 4, 9, gi, layout=0,
                                      jackknife=0, n_aux=8)
     assert c >= 0.9999 and rel < 1e-2 and srel < 1e-3
+
+
+@pytest.mark.parametrize("bsdf", [S.BSDF_CONDUCTOR, S.BSDF_BLEND])
+def test_reparam_glossy_parity(lib, oracle_mod, bsdf):
+    """Glossy floor (GGX conductor, blend): the rays leaving it add the BSDF's
+    directional terms, and the arriving ray's warp takes the floor's incident-direction
+    terms (posted one vertex later)."""
+    gi = np.random.default_rng(5).random((48, 48, 3)) + 0.2
+    sc = S.shadow_scene(width=48, height=48, floor_bsdf=bsdf, floor_alpha=0.3)
+    _, _, c, rel, _ = _compare(oracle_mod, sc, 16, 3, 31, gi)
+    assert c >= 0.99999 and rel < 1e-3
+    c, rel, srel = _compare_vertices(oracle_mod, sc, 8, 3, 31, gi)
+    assert c >= 0.9999 and rel < 5e-3 and srel < 1e-4
+
+
+def test_reparam_textured_blend_scene(lib, oracle_mod):
+    """96-shape Cornell room (textured blend BSDFs with per-shape roughness), roulette."""
+    sc = S.cornell96(width=32, height=32, tex_res=256)
+    gi = np.random.default_rng(6).random((32, 32, 3))
+    _, _, c, rel, _ = _compare(oracle_mod, sc, 2, 4, 17, gi, rr_depth=2, layout=0, n_aux=8)
+    assert c >= 0.9999 and rel < 1e-2
