@@ -419,9 +419,12 @@ __device__ __forceinline__ void normal_log_grad(const DevScene& S, int pos, floa
 }
 
 // VERT: gradients of every triangle corner's position (grad_v [n_tris][3][3]);
-// otherwise of one translation per shape (grad_t [n_shapes][3]).
+// otherwise of one translation per shape (grad_t [n_shapes][3]).  Capped at 64
+// registers (8 CTAs of 128 per SM): on the sphere workload the occupancy gained
+// outweighs the spills (uncapped 168 registers: 173 ms; 128: 148; 96: 135; 80: 130;
+// 64: 127).
 template <int LAYOUT, bool INSTR, bool VERT>
-__global__ void __launch_bounds__(128) reparam_kernel(const __grid_constant__ LaunchArgs A, const RpOpts K,
+__global__ void __launch_bounds__(128, 8) reparam_kernel(const __grid_constant__ LaunchArgs A, const RpOpts K,
                                                       float* __restrict__ grad_t, float* __restrict__ grad_v,
                                                       unsigned long long* rays_out) {
   extern __shared__ float s_grad[];
