@@ -1,43 +1,48 @@
-// Reparameterized Path Replay Backpropagation for shape translations (Sec. 4.7,
-// "Reparameterizations"; Sec. 4.8 on the derivative terms a moving vertex adds;
-// warp field after Bangaru et al. 2020).
+// Reparameterized Path Replay Backpropagation for geometry (Sec. 4.7,
+// "Reparameterizations"; Sec. 4.8 on the derivative terms of adjacent vertices;
+// Sec. 4.10's vertex-position benchmark; warp field after Bangaru et al. 2020).
 //
-// Parameters: one translation per shape (all of its vertices move together); a
+// Parameters: one translation per shape, or every triangle corner's position; a
 // surface point keeps its barycentric coordinates.  Every ray the path tracer
-// traces -- the camera ray and, at diffuse vertices, the light-sample ray and the
-// BSDF-sampled ray -- is reparameterized: in the primal nothing changes, in the
-// derivative the ray turns by a warp field V and its integrand is multiplied by
-// the Jacobian determinant 1 + div V.  A ray therefore contributes
-//     R * (m_perp . V(u) + div V(u))
-// to the derivative, where R = dLoss/dI . (radiance the ray carries) and m is the
-// covector of the ray's own measure or cosine term (camera: the pinhole's
-// image-plane density, -3 f / f.u; diffuse vertex: the cosine, n / n.u).
+// traces -- the camera ray and, at diffuse, GGX-conductor and blend vertices, the
+// light-sample ray and the BSDF-sampled ray -- is reparameterized: in the primal
+// nothing changes, in the derivative the ray turns by a warp field V and its
+// integrand is multiplied by the Jacobian determinant 1 + div V.  A ray therefore
+// contributes  M . V(u) + R div V(u),  where R = dLoss/dI . (radiance the ray
+// carries) and M the radiance-weighted covector of its integrand's log-derivative
+// in the ray direction: R times its measure or cosine term (camera: the pinhole's
+// image-plane density, -3 f / f.u; a vertex: the cosine, n / n.u), plus at a glossy
+// vertex the BSDF's outgoing-direction gradient, and for the ray that arrives at a
+// glossy vertex minus that vertex's incident-direction gradient (so the arriving
+// ray is posted one vertex later).
 //
 // The warp of a ray (origin o, direction u) comes from N auxiliary rays in a von
 // Mises-Fisher lobe around u (uniforms from the sample's auxiliary PCG32 stream,
 // initseq | 2^62): each one that hits a triangle of plane n_i.(x - o) = d_i says
 // that, seen along w, the plane point at distance d_i / (n_i.w) moves relative to
-// the origin with Delta_i = tau'(shape_i) - tau'(shape_o).  With per-sample weights
+// the origin with Delta_i = tau'(shape_i) - tau'(shape_o) (vertex positions: the
+// barycentric combination of the hit triangle's corner velocities at that point,
+// minus the origin's).  With per-sample weights
 //     alpha_i = exp((kk - kappa)(u.w_i - 1)) g_i,   g_i = (t0 / t_i)^m (1 if the
 // ray itself escapes; `miss` for escaping auxiliary rays, which do not move),
 // the normalised average C(w) = sum alpha_i(w) Delta_i (n_i.w)/d_i / (sum alpha_i(w)
 // + N eps) with alpha_i(w) proportional to exp(kk (w.w_i - 1)) gives the warp
 // V = (I - w w^T) C, and differentiating it at u (samples fixed) in closed form:
-//     m_perp.V + div V = sum_i alpha_i / (D d_i) * H_i . Delta_i,
-//     H_i = (n_i.u)(m_perp - 2u + kk p_i - kk P / D) + (I - u u^T) n_i,
+//     M.V + R div V = sum_i alpha_i / (D d_i) * H_i . Delta_i,
+//     H_i = (n_i.u)(M_perp + R (kk p_i - 2u - kk P / D)) + R (I - u u^T) n_i,
 // with p_i = (I - u u^T) w_i, P = sum alpha_j p_j, D = sum alpha_j + N eps.  The
 // ratio's O(1/N) bias is removed by the leave-one-out (jackknife) combination
 // N f(all) - (N-1)/N sum_j f(all but j), evaluated with two extra sums.  For the
 // camera ray the warp is multiplied by a window b that reaches 0 at the image
-// border, adding grad(b) . C.  Because every term is linear in the translation
-// velocities, the reverse-mode gradient of a ray is the coefficient vector of
-// each Delta_i: it is added to shape_i's gradient and subtracted from the
-// origin shape's.
+// border, adding R grad(b) . C.  Because every term is linear in the velocities,
+// the reverse-mode gradient of a ray is the coefficient vector of each Delta_i: it
+// is added to the hit's shape (or triangle corners) and subtracted from the
+// origin's.
 //
 // Launch: the split-PRB radiance pass (each sample's radiance), then one thread per
 // (pixel, lane) replays its samples in lockstep with the other lanes of its warp,
-// which trace the auxiliary rays of the posted rays together.  Gradients are
-// accumulated per CTA in shared memory when the shape table fits.
+// which trace the auxiliary rays of the posted rays together.  Translation
+// gradients are accumulated per CTA in shared memory when the shape table fits.
 #include "pt_mega.cuh"
 
 namespace ptgb {
