@@ -75,6 +75,9 @@ def parse():
                     help="radiance-cache MLP inference throughput, tcgen05 vs mma.sync engines (own JSON line)")
     ap.add_argument("--ckpt", action="store_true",
                     help="PRB vs reverse mode with checkpoints, one gradient step each (own JSON line)")
+    ap.add_argument("--texgrad", action="store_true",
+                    help="PRB adjoint of the 96-shape textured room (2048^2 atlas + 96 roughness values): "
+                         "Mrays/s and gradient atomics/s (own JSON line)")
     ap.add_argument("--reparam", action="store_true",
                     help="reparameterized PRB: shape-translation gradients through visibility (own JSON line)")
     ap.add_argument("--reparam-spp", type=int, default=16)
@@ -411,6 +414,83 @@ def run_ours(args):
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def run_texgrad_experiment(args):
+    """The texture-gradient configuration: the 96-shape Cornell room (blend BSDFs,
+    one 2048^2 RGBA atlas texture, 96 roughness values), 512x512, 16 spp, depth 6, no
+    roulette; one step = forward + PRB adjoint with the L2 gradient against the target
+    texture's render.  Reports the adjoint's Mrays/s and the gradient atomics it
+    issues per second (texel float4 and roughness atomics, before and after warp
+    aggregation, counted by an instrumented launch).  Own JSON line."""
+    import torch
+
+    from paper_2202_01284_gb300 import abi
+    from paper_2202_01284_gb300 import scenes as S
+    from paper_2202_01284_gb300.render import DeviceScene, RenderSettings
+    abi.load()
+    dev = torch.device("cuda", 0)
+    sc = S.cornell96(width=512, height=512)
+    ds = DeviceScene(sc, layout=abi.PT_BVH_WIDE if args.bvh == "wide" else abi.PT_BVH_BINARY, device=dev)
+    st = RenderSettings(width=512, height=512, spp=16, max_depth=6, rr_depth=-1, seed=11)
+    tgt = torch.as_tensor(S.cornell96_target_texture(sc.textures[0]), device=dev)
+    target = ds.forward(RenderSettings(width=512, height=512, spp=16, max_depth=6, rr_depth=-1, seed=77),
+                        textures=[tgt]).clone()
+    img = torch.empty_like(target)
+    gi = torch.empty_like(target)
+    g_tex = torch.zeros_like(ds.textures[0])
+    g_rough = torch.zeros_like(ds.roughness)
+    cf = torch.zeros(abi.PT_N_COUNTERS, dtype=torch.int64, device=dev)
+    cb = torch.zeros_like(cf)
+    ds.forward(st, out=img, counters=cf)
+    torch.sub(img, target, out=gi)
+    gi.mul_(2.0 / img.numel())
+    ds.backward(st, gi, g_textures=[g_tex], g_roughness=g_rough, seed=12, counters=cb)
+    torch.cuda.synchronize()
+    cf, cb = cf.cpu().numpy(), cb.cpu().numpy()
+    rays_f, rays_b = int(cf[1] + cf[2]), int(cb[1] + cb[2])
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(ev):
+        ev[0].record(stream)
+        ds.forward(st, out=img)
+        torch.sub(img, target, out=gi)
+        gi.mul_(2.0 / img.numel())
+        ev[1].record(stream)
+        ds.backward(st, gi, g_textures=[g_tex], g_roughness=g_rough, seed=12)
+        ev[2].record(stream)
+
+    dummy = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    for _ in range(max(3, args.warmup)):
+        step(dummy)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    clocks.start()
+    evs = []
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        step(ev)
+        evs.append(ev)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    fwd_ms = statistics.mean(e[0].elapsed_time(e[1]) for e in evs)
+    adj_ms = statistics.mean(e[1].elapsed_time(e[2]) for e in evs)
+    line = {"metric": "PRB adjoint of the textured 96-shape room: Mrays/s and gradient atomics/s",
+            "value": round(rays_b / adj_ms / 1e3, 2), "unit": "Mrays/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": round(fwd_ms + adj_ms, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "cornell96 (96 blend shapes, 2048^2 RGBA atlas, 96 roughness values), "
+                                   "512x512, 16 spp, depth 6, no roulette; forward + PRB adjoint",
+                       "l2": "flushed before each timed step", "forward_ms": round(fwd_ms, 3),
+                       "adjoint_ms": round(adj_ms, 3), "rays_fwd": rays_f, "rays_adj": rays_b,
+                       "fwd_mrays_s": round(rays_f / fwd_ms / 1e3, 1),
+                       "gradient_terms": int(cb[7]), "gradient_atomics": int(cb[6]),
+                       "gradient_terms_per_s_g": round(int(cb[7]) / adj_ms / 1e6, 3),
+                       "gradient_atomics_per_s_g": round(int(cb[6]) / adj_ms / 1e6, 3)},
+            "clocks": clk}
+    print(json.dumps(line), flush=True)
 
 
 def run_jvp_experiment(args):
@@ -1066,6 +1146,8 @@ def main():
         run_ckpt_experiment(args)
     elif args.reparam:
         run_reparam_experiment(args)
+    elif args.texgrad:
+        run_texgrad_experiment(args)
     elif args.mlp:
         run_mlp_experiment(args)
     else:
