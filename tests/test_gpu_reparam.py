@@ -246,3 +246,25 @@ def test_reparam_textured_blend_scene(lib, oracle_mod):
     gi = np.random.default_rng(6).random((32, 32, 3))
     _, _, c, rel, _ = _compare(oracle_mod, sc, 2, 4, 17, gi, rr_depth=2, layout=0, n_aux=8)
     assert c >= 0.9999 and rel < 1e-2
+
+
+def test_reparam_without_light_sampling_and_depth_one(lib, oracle_mod):
+    """BSDF sampling only (no light-sample rays) on the blend floor, and depth 1 (the
+    directly visible sky: camera warps only)."""
+    gi = np.random.default_rng(9).random((32, 32, 3))
+    from paper_2202_01284_gb300.render import DeviceScene, RenderSettings
+    for sc, nee, depth in ((S.shadow_scene(width=32, height=32, floor_bsdf=S.BSDF_BLEND), False, 3),
+                           (S.occluder_sky(width=32, height=32), True, 1)):
+        ds = DeviceScene(sc, layout=1)
+        n = sc.n_shapes
+        st = RenderSettings(width=32, height=32, spp=16, max_depth=depth, rr_depth=-1, seed=4, nee=nee)
+        g = torch.zeros((n, 3), device="cuda")
+        ds.backward_reparam(st, torch.as_tensor(gi[None], dtype=torch.float32, device="cuda"), g)
+        torch.cuda.synchronize()
+        r = oracle_mod.render_in(sc.cameras[0], 16, depth, 4, -1, nee)
+        ref, _, _ = oracle_mod.grad_reparam(oracle_mod.OracleScene(sc), r, gi)
+        gg = g.cpu().numpy().astype(np.float64)
+        scale = max(np.abs(ref).max(), 1e-6)
+        rel = np.abs(gg - ref).max() / scale
+        print(f"nee={nee} depth={depth}: max rel {rel:.2e}, |g| {np.abs(ref).max():.3g}")
+        assert np.abs(ref).max() > 1.0 and rel < 1e-3
