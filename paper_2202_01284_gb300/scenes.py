@@ -619,6 +619,78 @@ def shadow_scene(light=(-1.2, 2.0, 0.0), light_half=0.25, occluder=(-0.6, 0.8, 0
 
 
 # ----------------------------------------------------------------------------
+# user meshes
+# ----------------------------------------------------------------------------
+
+def load_obj(path_or_text: str):
+    """Minimal Wavefront OBJ reader: `v`, `vt`, `f` (polygons fanned into
+    triangles, negative indices allowed) and `o` / `g` groups.  Returns
+    (vertices [T,3,3] f32, uvs [T,3,2] f32, group [T] i32, group names).  No
+    materials, normals or other statements (they are ignored)."""
+    import os
+    text = open(path_or_text).read() if os.path.exists(path_or_text) else path_or_text
+    pos, uv, tris, tuvs, grp, names = [], [], [], [], [], []
+    current = -1
+    for line in text.splitlines():
+        parts = line.split("#", 1)[0].split()
+        if not parts:
+            continue
+        key = parts[0]
+        if key == "v":
+            pos.append([float(x) for x in parts[1:4]])
+        elif key == "vt":
+            uv.append([float(x) for x in parts[1:3]] + [0.0] * (2 - len(parts[1:3])))
+        elif key in ("o", "g"):
+            names.append(" ".join(parts[1:]) or f"group{len(names)}")
+            current = len(names) - 1
+        elif key == "f":
+            if current < 0:
+                names.append("default")
+                current = 0
+            corners = []
+            for c in parts[1:]:
+                idx = c.split("/")
+                vi = int(idx[0])
+                vi = vi - 1 if vi > 0 else len(pos) + vi
+                ti = None
+                if len(idx) > 1 and idx[1]:
+                    ti = int(idx[1])
+                    ti = ti - 1 if ti > 0 else len(uv) + ti
+                corners.append((vi, ti))
+            for k in range(1, len(corners) - 1):
+                tri = (corners[0], corners[k], corners[k + 1])
+                tris.append([pos[v] for v, _ in tri])
+                tuvs.append([uv[t] if t is not None else [0.0, 0.0] for _, t in tri])
+                grp.append(current)
+    if not tris:
+        raise ValueError("no faces in the OBJ input")
+    return (np.asarray(tris, np.float32), np.asarray(tuvs, np.float32), np.asarray(grp, np.int32), names)
+
+
+def mesh_scene(vertices, uvs=None, tri_shape=None, bsdf=None, albedo=None, emission=None, alpha=None,
+               env=None, cameras=(), name="mesh") -> Scene:
+    """A scene from user triangles: vertices [T,3,3], optional uvs [T,3,2] and a
+    shape id per triangle [T] (default: one shape).  Per shape: bsdf codes
+    (default diffuse), constant RGB albedos (default 0.5), emission, GGX alpha."""
+    v = np.ascontiguousarray(vertices, np.float32).reshape(-1, 3, 3)
+    t = v.shape[0]
+    ts = np.zeros(t, np.int32) if tri_shape is None else np.ascontiguousarray(tri_shape, np.int32)
+    n = int(ts.max()) + 1
+    st = _shape_table(n)
+    st["bsdf"][:] = BSDF_DIFFUSE if bsdf is None else np.asarray(bsdf, np.int32)
+    alb = np.full((n, 3), 0.5, np.float32) if albedo is None else np.asarray(albedo, np.float32).reshape(n, 3)
+    st["albedo_index"][:] = np.arange(n)
+    if emission is not None:
+        st["emission"][:] = np.asarray(emission, np.float32).reshape(n, 3)
+    if alpha is not None:
+        st["alpha"][:] = np.asarray(alpha, np.float32)
+    uv = np.zeros((t, 3, 2), np.float32) if uvs is None else np.ascontiguousarray(uvs, np.float32)
+    return Scene(vertices=v, uvs=uv, tri_shape=ts, albedo=alb, textures=[], roughness=np.zeros(0, np.float32),
+                 env=None if env is None else np.ascontiguousarray(env, np.float32), cameras=list(cameras),
+                 name=name, **st)
+
+
+# ----------------------------------------------------------------------------
 # batched-launch workload: many cameras of uneven size over several scenes
 # ----------------------------------------------------------------------------
 
