@@ -37,6 +37,22 @@ FLOPS_PER_NODE = {"binary": 44,   # two child slab tests: 12 FMA (24 flops), 10 
                                   # decode: 3 scale + 3 offset products excluded)
 FLOPS_PER_TRI = 45      # Moller-Trumbore: 2 cross, 4 dot, 1 div, 4 mul, 3 sub (FMA = 2 flops)
 NODE_BYTES = {"binary": 64, "wide": 80}  # bytes fetched per node visit
+
+
+def alu_roofline(kernel, counters, bvh, ms, clk, note=""):
+    """FP32-ALU roofline entry: traversal FLOPs of the counted node visits and
+    triangle tests (counters = PT_CNT_* array) over `ms`, against 152 SMs x 128 lanes
+    x 2 x the median SM clock sampled during the timed region."""
+    import torch
+    flops = FLOPS_PER_NODE[bvh] * int(counters[3]) + FLOPS_PER_TRI * int(counters[4])
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    mhz = (clk or {}).get("sm_mhz") or 1477.0
+    peak = sms * 128 * 2 * mhz * 1e6 / 1e12
+    achieved = flops / (ms / 1e3) / 1e12
+    return {"bound": "alu", "kernel": kernel, "achieved": round(achieved, 3), "peak": round(peak, 2),
+            "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": None,
+            "work": f"{FLOPS_PER_NODE[bvh]}/node visit + {FLOPS_PER_TRI}/triangle test (counted launch){note}",
+            "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 x median SM clock {mhz} MHz"}
 # DRAM bytes (read + write) per full-size launch of the production kernels, from one
 # one-pass ncu capture of this step (profiles/launches_spheres196k_1024px_64spp.md);
 # cleared whenever the kernels change until they are captured again.
@@ -489,6 +505,8 @@ def run_texgrad_experiment(args):
                        "gradient_terms": int(cb[7]), "gradient_atomics": int(cb[6]),
                        "gradient_terms_per_s_g": round(int(cb[7]) / adj_ms / 1e6, 3),
                        "gradient_atomics_per_s_g": round(int(cb[6]) / adj_ms / 1e6, 3)},
+            "roofline": alu_roofline("replay_kernel (after radiance_kernel)", cb, args.bvh, adj_ms, clk,
+                                     "; the adjoint's rays over radiance pass + replay"),
             "clocks": clk}
     print(json.dumps(line), flush=True)
 
@@ -642,6 +660,9 @@ def run_wavefront_experiment(args):
                            "grouped_fwd": round(avg["wavefront_grouped_fwd"] / avg["megakernel_fwd"], 3),
                            "traced_adj": round(avg["wavefront_traced_adj"] / avg["megakernel_adj"], 3),
                            "grouped_adj": round(avg["wavefront_grouped_adj"] / avg["megakernel_adj"], 3)}},
+            "roofline": alu_roofline("wavefront forward (wf_start, wf_trace, wf_shade, wf_finish, wf_film)", cf,
+                                     args.bvh, avg["wavefront_traced_fwd"], clk,
+                                     "; the megakernel forward's rays, whole wavefront forward time"),
             "clocks": clk}
     print(json.dumps(line), flush=True)
 
@@ -668,6 +689,11 @@ def run_ckpt_experiment(args):
     ck = Checkpoints(st.width * st.height * st.spp, st.max_depth)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
+    # node / triangle visits of the forward's rays: the reverse sweep recomputes exactly these
+    cf = torch.zeros(abi.PT_N_COUNTERS, dtype=torch.int64, device=dev)
+    ds.forward(st, out=img, counters=cf)
+    torch.cuda.synchronize()
+    cf = cf.cpu().numpy()
 
     def prb(ev):
         ev[0].record(stream)
@@ -718,6 +744,8 @@ def run_ckpt_experiment(args):
                        "ckpt_bytes": ck.nbytes, "prb_scratch_bytes": 0,
                        "prb_seed": "decorrelated (radiance pass + replay)",
                        "ckpt_seed": "the forward's (reverse sweep over stored vertices)"},
+            "roofline": alu_roofline("ckpt_reverse_kernel", cf, args.bvh, out["ckpt"]["reverse_ms"], clk,
+                                     "; the forward's rays, which the reverse sweep traces again"),
             "clocks": clk}
     print(json.dumps(line), flush=True)
     ck.close()
@@ -1075,7 +1103,10 @@ def run_batch_experiment(args):
                       use_cache=False, reset_grads=reset)
     b = B.Batch(jobs, tile=best["tile"], lanes_per_pixel=best["lanes_per_pixel"], ctas_per_sm=best["ctas_per_sm"])
     b.capture()
+    clocks = ClockSampler(0)
+    clocks.start()
     graph_ms = timed(b.replay)
+    clk = clocks.stop()
     direct_ms = timed(b.run)
     out = {"metric": "batched forward + adjoint: one persistent CUDA-graph launch vs 64 separate launches",
            "jobs": len(jobs), "scenes_tris": [ds.scene.n_tris for ds in scenes], "samples": samples, "rays": rays,
@@ -1086,6 +1117,10 @@ def run_batch_experiment(args):
            "gpu_launches": {"persistent": 3, "separate": 3 * len(jobs), "graph_launches": 1},
            "autotune": {k: v for k, v in best.items() if k != "candidates"},
            "autotune_candidates": best["candidates"]}
+    cnt = (cnt_f + cnt_b).cpu().numpy()
+    out["roofline"] = alu_roofline("batch_kernel (forward, radiance pass, replay)", cnt, "wide", graph_ms, clk,
+                                   "; every job's forward and adjoint rays over the graph's time")
+    out["clocks"] = clk
     print(json.dumps(out), flush=True)
 
 
