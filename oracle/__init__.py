@@ -104,6 +104,7 @@ def lib():
             L.oracle_grad_reparam.argtypes = [vp, C.POINTER(RenderIn), vp, C.POINTER(ReparamIn), ip, vp, vp, ip, vp,
                                               ip]
             L.oracle_grad_reparam.restype = ip
+            L.oracle_vmf.argtypes = [dp, dp, dp, vp]
             L.oracle_sphere_div.argtypes = [ip, vp, vp]
             L.oracle_sphere_div.restype = dp
             L.oracle_warp.argtypes = [vp, vp, vp, ip, vp, C.POINTER(ReparamIn), ip, vp, vp, vp, vp, vp]
@@ -298,6 +299,13 @@ def grad_reparam(osc: OracleScene, r: RenderIn, grad_image=None, dot_param=-1, t
     if rc != 0:
         raise ValueError("oracle_grad_reparam: bad options")
     return g, img, dot
+
+
+def vmf(u0: float, u1: float, kappa: float) -> np.ndarray:
+    """The auxiliary-ray sampler's local direction (lobe axis +z)."""
+    out = np.zeros(3)
+    lib().oracle_vmf(float(u0), float(u1), float(kappa), _ptr(out))
+    return out
 
 
 def sphere_div(kind: int, u, e) -> float:

@@ -2142,6 +2142,14 @@ int oracle_frame(const double* n, double* s_out, double* t_out) {
 }
 
 
+// The auxiliary-ray sampler: local vMF direction (lobe axis +z) for uniforms (u0, u1).
+void oracle_vmf(double u0, double u1, double kappa, double* out) {
+  V3 w = vmf_local(u0, u1, kappa);
+  out[0] = w.x;
+  out[1] = w.y;
+  out[2] = w.z;
+}
+
 // Divergence on the sphere (gnomonic-chart duals) of analytic fields at u:
 // kind 0: V = e (constant ambient vector), 1: V = w x e, 2: V = (I - w w^T) e.
 double oracle_sphere_div(int kind, const double* u, const double* e) {

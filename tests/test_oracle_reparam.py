@@ -215,3 +215,23 @@ def test_glossy_receiver_matches_finite_differences(oracle_mod, bsdf):
     print("reparameterized\n", g, "\nfinite differences\n", fd)
     for shape in (1, 2):
         assert np.abs(g[shape] - fd[shape]).max() < 0.25 * np.abs(fd[shape]).max()
+
+
+@pytest.mark.parametrize("kappa", [2.0, 50.0, 1000.0])
+def test_vmf_sampler_matches_the_distribution(oracle_mod, kappa):
+    """Auxiliary directions follow the von Mises-Fisher law p(w) ~ exp(kappa w.z):
+    cos(theta) has CDF (e^{kappa c} - e^{-kappa}) / (e^{kappa} - e^{-kappa}) and the
+    azimuth is uniform; the directions are unit vectors."""
+    rng = np.random.default_rng(int(kappa))
+    u = rng.random((20000, 2))
+    w = np.array([oracle_mod.vmf(a, b, kappa) for a, b in u])
+    assert np.allclose(np.linalg.norm(w, axis=1), 1.0, atol=1e-12)
+    c = np.sort(w[:, 2])
+    emp = np.arange(1, len(c) + 1) / len(c)
+    cdf = (np.exp(kappa * (c - 1.0)) - np.exp(-2 * kappa)) / (1.0 - np.exp(-2 * kappa))
+    assert np.abs(emp - cdf).max() < 0.015          # Kolmogorov-Smirnov distance
+    phi = np.arctan2(w[:, 1], w[:, 0])
+    hist, _ = np.histogram(phi, bins=8, range=(-np.pi, np.pi))
+    assert np.abs(hist / len(phi) - 1 / 8).max() < 0.01
+    # mean cosine: coth(kappa) - 1/kappa
+    assert w[:, 2].mean() == pytest.approx(1 / np.tanh(kappa) - 1 / kappa, abs=3 / np.sqrt(len(c)) * w[:, 2].std() + 1e-9)
