@@ -332,6 +332,27 @@ def render_translated(scene: S.Scene, st: RenderSettings, translations, layout: 
     return TranslateFn.apply(scene, st, layout, reparam_opts, translations)
 
 
+def save_pfm(path: str, image) -> None:
+    """Write an RGB float image ([rows, cols, 3], row 0 = top; tensor or array) as
+    a little-endian Portable Float Map."""
+    img = image.detach().cpu().numpy() if isinstance(image, torch.Tensor) else np.asarray(image)
+    img = np.ascontiguousarray(img, dtype="<f4").reshape(img.shape[-3], img.shape[-2], 3)
+    with open(path, "wb") as f:
+        f.write(b"PF\n%d %d\n-1.0\n" % (img.shape[1], img.shape[0]))
+        f.write(np.ascontiguousarray(img[::-1]).tobytes())  # PFM stores the bottom row first
+
+
+def load_pfm(path: str) -> np.ndarray:
+    """Read a colour Portable Float Map into [rows, cols, 3] float32, row 0 = top."""
+    with open(path, "rb") as f:
+        if f.readline().strip() != b"PF":
+            raise ValueError("not a colour PFM file")
+        w, h = (int(x) for x in f.readline().split())
+        scale = float(f.readline())
+        data = np.frombuffer(f.read(), dtype="<f4" if scale < 0 else ">f4", count=w * h * 3)
+    return np.ascontiguousarray(data.reshape(h, w, 3)[::-1], dtype=np.float32)
+
+
 class RadianceCache:
     """Owner of a pt_cache (MLP weights, Adam state, query/record buffers)."""
 

@@ -40,3 +40,14 @@ def test_mesh_scene_renders_on_the_oracle(oracle_mod):
     assert sc.n_shapes == 2 and sc.n_tris == 3
     img = oracle_mod.render(oracle_mod.OracleScene(sc), oracle_mod.render_in(cam, 4, 3, 1))
     assert img.shape == (8, 8, 3) and np.isfinite(img).all() and img.max() > 0
+
+
+def test_pfm_round_trip(tmp_path):
+    from paper_2202_01284_gb300.render import load_pfm, save_pfm
+    img = np.random.default_rng(0).random((5, 7, 3)).astype(np.float32)
+    p = str(tmp_path / "img.pfm")
+    save_pfm(p, img)
+    back = load_pfm(p)
+    assert back.shape == (5, 7, 3) and np.array_equal(back, img)
+    with open(p, "rb") as f:
+        assert f.readline() == b"PF\n" and f.readline() == b"7 5\n"
