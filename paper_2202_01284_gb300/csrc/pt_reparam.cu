@@ -323,10 +323,6 @@ __device__ __noinline__ unsigned process_warps(const LaunchArgs& A, const RpOpts
   return rays;
 }
 
-// Lockstep loop: each iteration every lane advances the PRB replay of its current
-// sample by one vertex (its radiance comes from the radiance pass launched before,
-// as in split PRB), then the whole warp processes the reparameterized rays the
-// lanes posted.
 // Gradients of log f_c with respect to the outgoing (go) and incident (gi)
 // directions, local frame (n = +z), for the glossy BSDFs: GGX conductor, and the
 // blend w albedo/pi + (1 - w) GGX; zero for diffuse.  With h = (wi + wo)/|wi + wo|,
@@ -423,6 +419,10 @@ __device__ __forceinline__ void normal_log_grad(const DevScene& S, int pos, floa
   g[0] = -(g[1] + g[2]);
 }
 
+// Lockstep loop: each iteration every lane advances the PRB replay of its current
+// sample by one vertex (its radiance comes from the radiance pass launched before,
+// as in split PRB), then the whole warp processes the reparameterized rays the
+// lanes posted.
 // VERT: gradients of every triangle corner's position (grad_v [n_tris][3][3]);
 // otherwise of one translation per shape (grad_t [n_shapes][3]).  Capped at 64
 // registers (8 CTAs of 128 per SM): on the sphere workload the occupancy gained
