@@ -332,6 +332,38 @@ def render_translated(scene: S.Scene, st: RenderSettings, translations, layout: 
     return TranslateFn.apply(scene, st, layout, reparam_opts, translations)
 
 
+class VerticesFn(torch.autograd.Function):
+    """image = render of `scene` with its triangle corners at `vertices` ([n_tris,
+    3, 3], absolute positions); backward = reparameterized PRB with every corner as
+    a parameter (pt_render_backward_reparam_vertices).  The geometry is uploaded on
+    every call; compose with torch for any parametrisation of the vertices."""
+
+    @staticmethod
+    def forward(ctx, scene: S.Scene, st: RenderSettings, layout: int, opts: dict, vertices):
+        import copy
+        moved = copy.copy(scene)
+        moved.vertices = np.ascontiguousarray(vertices.detach().to("cpu", torch.float32).numpy())
+        ds = DeviceScene(moved, layout=layout, device=vertices.device)
+        ctx.ds, ctx.st, ctx.opts = ds, st, opts
+        return ds.forward(st)
+
+    @staticmethod
+    def backward(ctx, grad_img):
+        ds, st = ctx.ds, ctx.st
+        g = torch.zeros((ds.scene.n_tris, 3, 3), device=grad_img.device, dtype=torch.float32)
+        seed = st.backward_seed if st.backward_seed is not None else st.seed
+        ds.backward_reparam(st, grad_img.contiguous(), g_vertices=g, seed=seed, **ctx.opts)
+        ds.close()
+        ctx.ds = None
+        return None, None, None, None, g
+
+
+def render_vertices(scene: S.Scene, st: RenderSettings, vertices, layout: int = abi.PT_BVH_BINARY,
+                    **reparam_opts):
+    """Differentiable render with respect to every triangle corner's position."""
+    return VerticesFn.apply(scene, st, layout, reparam_opts, vertices)
+
+
 def save_pfm(path: str, image) -> None:
     """Write an RGB float image ([rows, cols, 3], row 0 = top; tensor or array) as
     a little-endian Portable Float Map."""
