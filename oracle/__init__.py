@@ -62,7 +62,7 @@ class RenderIn(C.Structure):
 class ReparamIn(C.Structure):
     _fields_ = [("n_aux", C.c_int), ("kappa", C.c_double), ("kernel_scale", C.c_double), ("power", C.c_double),
                 ("miss", C.c_double), ("eps", C.c_double), ("jackknife", C.c_int),
-                ("border", C.c_double)]
+                ("border", C.c_double), ("edge_spp", C.c_int)]
 
 
 def lib():
@@ -269,15 +269,17 @@ def render_jvp(osc: OracleScene, r: RenderIn, t_albedo=None, t_textures=None, t_
 # traced ray, vMF concentration of their lobe, how much narrower the weighting
 # kernel is, depth-weight exponent, weight of escaping rays, normaliser floor,
 # leave-one-out correction on/off, width in pixels of the window that takes the
-# camera-ray warp to zero at the image border.
+# camera-ray warp to zero at the image border, paths per pixel edge for the term
+# of the pixels' own moving boundaries (0: off).
 REPARAM_DEFAULTS = dict(n_aux=16, kappa=1000.0, kernel_scale=8.0, power=2.0, miss=0.01, eps=1e-4,
-                        jackknife=1, border=4.0)
+                        jackknife=1, border=4.0, edge_spp=1)
 
 
 def _reparam_in(opts) -> ReparamIn:
     o = dict(REPARAM_DEFAULTS, **opts)
     return ReparamIn(int(o["n_aux"]), float(o["kappa"]), float(o["kernel_scale"]), float(o["power"]),
-                     float(o["miss"]), float(o["eps"]), int(o["jackknife"]), float(o["border"]))
+                     float(o["miss"]), float(o["eps"]), int(o["jackknife"]), float(o["border"]),
+                     int(o["edge_spp"]))
 
 
 def grad_reparam(osc: OracleScene, r: RenderIn, grad_image=None, dot_param=-1, threads=0, vertex=False, **opts):

@@ -227,6 +227,7 @@ typedef struct {
   double kappa, kernel_scale, power, miss, eps;
   int jackknife;
   double border;
+  int edge_spp;
 } oracle_reparam_opts;
 }
 
@@ -688,20 +689,35 @@ extern "C" void oracle_nrc_encode(int n, const double* raw, const double* box, d
 extern "C" void oracle_mlp_forward(const double* W, int n, const double* enc, double* out);
 namespace {
 
+// A path started on a pixel edge instead of inside a pixel (the reparameterized
+// derivative's pixel-edge term): its own stream, and the image-plane point (X, Y +
+// j0) on a vertical edge or (X + j0, Y) on a horizontal one, in pixel coordinates.
+struct EdgeStart {
+  uint64_t stream;
+  bool vertical;
+  int X, Y;
+};
+
 template <class Acc>
 V3 render_sample(const Scene& s, const Camera& cam, const oracle_render_in& r, int px, int py,
                  int spp_index, Acc& acc, uint32_t* hash_out, const CacheModel* cache = nullptr,
-                 std::vector<TrainRecord>* records = nullptr) {
+                 std::vector<TrainRecord>* records = nullptr, const EdgeStart* edge = nullptr) {
   // RNG stream of this sample: (camera << 40) | (pixel << 12) | sample
   Pcg32 rng;
   uint64_t pixel = (uint64_t)py * (uint64_t)r.width + (uint64_t)px;
   uint64_t stream = ((uint64_t)r.cam_index << 40) | (pixel << 12) | (uint64_t)spp_index;
+  if (edge) stream = edge->stream;
   rng.seed(r.seed, stream);
   DecisionHash dh;
 
   double j0 = rng.uniform(), j1 = rng.uniform();
-  double sx = (2.0 * (px + j0) / cam.w - 1.0) * cam.tan_half * cam.aspect;
-  double sy = (1.0 - 2.0 * (py + j1) / cam.h) * cam.tan_half;
+  double fx = px + j0, fy = py + j1;
+  if (edge) {
+    fx = edge->vertical ? edge->X : edge->X + j0;
+    fy = edge->vertical ? edge->Y + j0 : edge->Y;
+  }
+  double sx = (2.0 * fx / cam.w - 1.0) * cam.tan_half * cam.aspect;
+  double sy = (1.0 - 2.0 * fy / cam.h) * cam.tan_half;
   V3 ro = cam.o;
   V3 rd = normalize(cam.fwd + cam.right * sx + cam.up * sy);
   acc.camera_ray(stream, ro, rd, cam.fwd);
@@ -1146,6 +1162,7 @@ struct ReparamOpts {
   double eps = 1e-4;          // floor of the normaliser
   int jackknife = 1;          // leave-one-out correction of the ratio's 1/N bias
   double border = 4.0;        // camera-ray warp window at the image border, pixels
+  int edge_spp = 1;           // samples per pixel edge of the pixel-edge term (0: off)
 };
 
 // value and gradient in the two chart coordinates
@@ -1286,20 +1303,23 @@ V3 origin_motion(const Scene& s, const Origin& og, const Param& P) {
   return e * b[P.corner];
 }
 
-// Barycentric coordinate `corner` of the point where the ray (o, w) meets the
-// plane of triangle t (extended beyond its edges), from its definition with
-// signed areas: b1 = ((x - v0) x e2).c / c.c, b2 = (e1 x (x - v0)).c / c.c.
-D2 plane_barycentric(const Scene& s, int t, V3 o, VD w, int corner) {
+// Barycentric coordinate `corner` of the point x(w) = o + t(w) w where the ray meets
+// the plane of triangle t (extended beyond its edges), divided by t(w).  From the
+// definition with signed areas, b1 = ((x - v0) x e2).c / c.c = (x - v0).a1 and b2 =
+// (e1 x (x - v0)).c / c.c = (x - v0).a2 with a1 = (e2 x c) / c.c, a2 = (c x e1) / c.c,
+// b0 = 1 - b1 - b2; dividing by t(w), with 1 / t(w) = (w.c) / (c.(v0 - o)), gives
+// b_j / t = (o - v0).a_j / t + w.a_j, finite also where w runs parallel to the plane
+// (where b_j and t are not).
+D2 plane_barycentric_over_t(const Scene& s, int t, V3 o, VD w, int corner) {
   V3 v0 = s.v0[t], e1 = s.v1[t] - s.v0[t], e2 = s.v2[t] - s.v0[t];
   V3 c = cross(e1, e2);
-  D2 tt = D2{dot(c, v0 - o), 0, 0} / dotd(w, c);
-  VD x{D2{o.x - v0.x, 0, 0} + w.x * tt, D2{o.y - v0.y, 0, 0} + w.y * tt, D2{o.z - v0.z, 0, 0} + w.z * tt};
-  // (x x e2).c and (e1 x x).c are linear in x: (e2 x c).x and (c x e1).x
-  D2 b1 = dotd(x, cross(e2, c)) * (1.0 / dot(c, c));
-  D2 b2 = dotd(x, cross(c, e1)) * (1.0 / dot(c, c));
+  D2 inv_t = dotd(w, c) * (1.0 / dot(c, v0 - o));
+  V3 a1 = cross(e2, c) * (1.0 / dot(c, c)), a2 = cross(c, e1) * (1.0 / dot(c, c));
+  D2 b1 = inv_t * dot(o - v0, a1) + dotd(w, a1);
+  D2 b2 = inv_t * dot(o - v0, a2) + dotd(w, a2);
   if (corner == 1) return b1;
   if (corner == 2) return b2;
-  return D2{1, 0, 0} - b1 - b2;
+  return inv_t - b1 - b2;
 }
 
 // Velocity, seen along w, of the point where w meets the plane of auxiliary hit h
@@ -1307,18 +1327,17 @@ D2 plane_barycentric(const Scene& s, int t, V3 o, VD w, int corner) {
 VD aux_velocity(const Scene& s, const AuxHit& h, V3 o, const Origin& og, const Param& P, VD w) {
   if (h.tri < 0) return constant(V3());
   V3 e = axis_vec(P.axis, D2{});
-  VD mv = constant(V3());  // motion of the plane point
+  D2 inv_t = dotd(w, h.n) * (1.0 / h.d);
+  D2 mt{0, 0, 0};  // motion of the plane point along e, divided by its distance t(w)
   if (!P.vertex) {
-    if (h.shape == P.index) mv = constant(e);
+    if (h.shape == P.index) mt = inv_t;
   } else if (h.tri == P.index) {
-    D2 b = plane_barycentric(s, h.tri, o, w, P.corner);
-    mv = VD{b * e.x, b * e.y, b * e.z};
+    mt = plane_barycentric_over_t(s, h.tri, o, w, P.corner);
   }
   V3 om = origin_motion(s, og, P);
-  VD rel{mv.x - D2{om.x, 0, 0}, mv.y - D2{om.y, 0, 0}, mv.z - D2{om.z, 0, 0}};
-  D2 inv_t = dotd(w, h.n) * (1.0 / h.d);
+  VD rel{mt * e.x - inv_t * om.x, mt * e.y - inv_t * om.y, mt * e.z - inv_t * om.z};  // relative motion / t(w)
   D2 wr = dotd(w, rel);
-  return VD{(rel.x - w.x * wr) * inv_t, (rel.y - w.y * wr) * inv_t, (rel.z - w.z * wr) * inv_t};
+  return VD{rel.x - w.x * wr, rel.y - w.y * wr, rel.z - w.z * wr};
 }
 
 // The warp field of parameter P at direction w (fixed samples; `skip` >= 0 leaves
@@ -1617,6 +1636,38 @@ struct ReparamAcc {
 };
 
 // ---------------------------------------------------------------- parallel driver
+// A path through a pixel edge: only its camera ray's warp is needed (the radiance
+// it carries enters the edge term as a value, not differentiated).  The warp is
+// the windowed camera-ray warp of ReparamAcc, from the same auxiliary stream rule.
+struct EdgeAcc : NullAcc {
+  const Scene* s = nullptr;
+  const ReparamOpts* op = nullptr;
+  uint64_t seed = 0;
+  CamWindow win;
+  bool vertex = false;
+  V3 u;
+  std::vector<std::pair<int, double>> tmp;
+  std::vector<std::pair<int, V3>> wdot;  // per parameter: the tangential turn of the camera ray
+  void camera_ray(uint64_t stream, V3 o, V3 d, V3) {
+    Pcg32 aux;
+    aux.seed(seed, stream | (1ull << 62));
+    std::vector<double> uni(2 * op->n_aux);
+    for (double& x : uni) x = aux.uniform();
+    WarpSamples ws = warp_samples(*s, *op, o, d, uni.data());
+    u = d;
+    warp_log_derivs(*s, ws, o, Origin{}, vertex, V3(), V3(), tmp, &win, &wdot);
+  }
+};
+
+// Gradient of the image-plane pixel coordinate (px if `x`, else py) with respect
+// to the ray direction w of a pinhole camera: px = (w.right / w.fwd / (tan_half *
+// aspect) + 1) w / 2, py = (1 - w.up / w.fwd / tan_half) h / 2.
+V3 pixel_coord_grad(const Camera& c, V3 w, bool x) {
+  const double f = dot(w, c.fwd);
+  if (x) return (c.right * (1.0 / f) - c.fwd * (dot(w, c.right) / (f * f))) * (0.5 * c.w / (c.tan_half * c.aspect));
+  return (c.up * (1.0 / f) - c.fwd * (dot(w, c.up) / (f * f))) * (-0.5 * c.h / c.tan_half);
+}
+
 template <class F>
 void parallel_rows(int y0, int rows, int n_threads, F fn) {
   if (n_threads <= 0) n_threads = (int)std::max(1u, std::thread::hardware_concurrency());
@@ -2012,7 +2063,8 @@ static bool reparam_opts(const oracle_reparam_opts* o, ReparamOpts& op) {
   op.eps = o->eps;
   op.jackknife = o->jackknife;
   op.border = o->border;
-  return o->border > 0;
+  op.edge_spp = o->edge_spp;
+  return o->border > 0 && o->edge_spp >= 0;
 }
 
 // Reverse-mode-equivalent gradient by forward mode: g[p] = sum over pixels and
@@ -2031,7 +2083,75 @@ int oracle_grad_reparam(void* sc, const oracle_render_in* r, const double* grad_
   int x0, y0, cw, ch;
   crop_of(*r, x0, y0, cw, ch);
   const int np = vertex ? 9 * s.n_tris : 3 * (int)s.shapes.size();
-  std::vector<double> rows((size_t)ch * np, 0.0);
+  std::vector<double> rows((size_t)(ch + 1) * np, 0.0);
+  // Pixel-edge term.  The warp that fixes the discontinuities also moves the
+  // footprint of every pixel (a box of unit area in pixel coordinates): its
+  // boundary moves with minus the warp's image-plane velocity, so pixel p gains
+  // -integral over its boundary of L (v . n_out) ds.  An edge between pixels a
+  // (left / above) and b (right / below) adds -L v_n to a and +L v_n to b, v_n
+  // the velocity along +x (+y); one path through a uniform point of the edge
+  // estimates the integral.  Edges on the image border carry none (the window
+  // vanishes there); those on the crop's border count for the inside pixel.
+  std::vector<double> edge_dot((size_t)(ch + 1) * cw * 3, 0.0);  // horizontal edges: L v_n of dot_param
+  if (image_dot) std::fill(image_dot, image_dot + (size_t)cw * ch * 3, 0.0);
+  if (op.edge_spp > 0 && (grad_image || (image_dot && dot_param >= 0 && dot_param < np))) {
+    const double* gimg = grad_image;
+    parallel_rows(y0, ch + 1, n_threads, [&](int Y) {
+      double* grow = &rows[(size_t)(Y - y0) * np];
+      auto pixel_grad = [&](int X, int Yp) -> const double* {
+        if (!gimg || X < x0 || X >= x0 + cw || Yp < y0 || Yp >= y0 + ch) return nullptr;
+        return gimg + ((size_t)(Yp - y0) * cw + (X - x0)) * 3;
+      };
+      auto edge = [&](bool vertical, int X, int Yy, uint64_t id) {
+        const double* ga = vertical ? pixel_grad(X - 1, Yy) : pixel_grad(X, Yy - 1);
+        const double* gb = pixel_grad(X, Yy);
+        V3 sum_dot;
+        for (int k = 0; k < op.edge_spp; ++k) {
+          EdgeStart e{((uint64_t)r->cam_index << 40) | (id << 12) | (uint64_t)k | (1ull << 61), vertical, X, Yy};
+          EdgeAcc acc;
+          acc.s = &s;
+          acc.op = &op;
+          acc.seed = r->seed;
+          acc.vertex = vertex != 0;
+          acc.win = CamWindow{cam.fwd, cam.right, cam.up, cam.tan_half, cam.aspect, op.border, cam.w, cam.h};
+          V3 l = render_sample(s, cam, *r, 0, 0, k, acc, nullptr, nullptr, nullptr, &e);
+          V3 gp = pixel_coord_grad(cam, acc.u, vertical);
+          for (auto& pw : acc.wdot) {
+            const double vn = dot(gp, pw.second) / op.edge_spp;
+            double gl = 0.0;
+            for (int c = 0; c < 3; ++c) gl += ((gb ? gb[c] : 0.0) - (ga ? ga[c] : 0.0)) * l[c];
+            grow[pw.first] += gl * vn;
+            if (pw.first == dot_param) sum_dot = sum_dot + l * vn;
+          }
+        }
+        return sum_dot;
+      };
+      const uint64_t nv = (uint64_t)(r->width + 1) * r->height;  // vertical edges first, then horizontal
+      if (Y < y0 + ch)
+        for (int X = std::max(x0, 1); X <= std::min(x0 + cw, r->width - 1); ++X) {
+          V3 d = edge(true, X, Y, (uint64_t)Y * (r->width + 1) + X);
+          if (!image_dot) continue;
+          double* row = image_dot + (size_t)(Y - y0) * cw * 3;
+          for (int c = 0; c < 3; ++c) {
+            if (X - 1 >= x0) row[(X - 1 - x0) * 3 + c] -= d[c];
+            if (X < x0 + cw) row[(X - x0) * 3 + c] += d[c];
+          }
+        }
+      if (Y >= 1 && Y <= r->height - 1)
+        for (int X = x0; X < x0 + cw; ++X) {
+          V3 d = edge(false, X, Y, nv + (uint64_t)Y * r->width + X);
+          for (int c = 0; c < 3; ++c) edge_dot[((size_t)(Y - y0) * cw + (X - x0)) * 3 + c] = d[c];
+        }
+    });
+    if (image_dot)
+      for (int Y = y0; Y <= y0 + ch; ++Y)
+        for (int X = x0; X < x0 + cw; ++X)
+          for (int c = 0; c < 3; ++c) {
+            const double d = edge_dot[((size_t)(Y - y0) * cw + (X - x0)) * 3 + c];
+            if (Y - 1 >= y0) image_dot[((size_t)(Y - 1 - y0) * cw + (X - x0)) * 3 + c] -= d;
+            if (Y < y0 + ch) image_dot[((size_t)(Y - y0) * cw + (X - x0)) * 3 + c] += d;
+          }
+  }
   parallel_rows(y0, ch, n_threads, [&](int py) {
     double* grow = &rows[(size_t)(py - y0) * np];
     for (int px = x0; px < x0 + cw; ++px) {
@@ -2051,14 +2171,14 @@ int oracle_grad_reparam(void* sc, const oracle_render_in* r, const double* grad_
       }
       for (int c = 0; c < 3; ++c) {
         if (image) image[pi * 3 + c] = sum[c] / r->spp;
-        if (image_dot) image_dot[pi * 3 + c] = sum_dot[c] / r->spp;
+        if (image_dot) image_dot[pi * 3 + c] += sum_dot[c] / r->spp;
       }
     }
   });
   if (g_out)
     for (int p = 0; p < np; ++p) {
       double t = 0.0;
-      for (int y = 0; y < ch; ++y) t += rows[(size_t)y * np + p];
+      for (int y = 0; y <= ch; ++y) t += rows[(size_t)y * np + p];
       g_out[p] = t;
     }
   return 0;
