@@ -756,8 +756,9 @@ def run_reparam_experiment(args):
     visibility) on the throughput scene at --reparam-spp samples per pixel: one
     gradient step = forward image, L2-loss image gradient, reparameterized
     adjoint (radiance pass + replay with the warps).  Rays = every ray the adjoint
-    traces (radiance pass, replay, shadow, auxiliary and the warps' center rays),
-    counted by the kernel.  Own JSON line."""
+    traces (radiance pass, replay, shadow, auxiliary and the warps' center rays,
+    and the paths through pixel edges with their warps), counted by the kernels.
+    Own JSON line."""
     import torch
 
     from paper_2202_01284_gb300 import abi
@@ -863,8 +864,9 @@ def run_reparam_experiment(args):
                          "peak": round(peak_tflops, 2), "unit": "TFLOP/s", "frac": round(achieved / peak_tflops, 4),
                          "traffic": None,
                          "work": f"{FLOPS_PER_NODE[args.bvh]}/node visit + {FLOPS_PER_TRI}/triangle test (counted "
-                                 "by instrumented launches of the replay and of the radiance pass; warp-field "
-                                 "arithmetic not counted); time = radiance pass + reparam_kernel",
+                                 "by instrumented launches of the replay, the pixel-edge paths and the radiance "
+                                 "pass; warp-field arithmetic not counted); time = radiance pass + reparam_kernel "
+                                 "+ edge_kernel",
                          "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 x median SM clock {mhz} MHz"},
             "gpu_launches": 2 * args.steps,
             "clocks": clk}

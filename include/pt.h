@@ -397,19 +397,27 @@ int pt_ckpt_backward(pt_scene* scene, const pt_render_desc* desc, const pt_param
  * reparameterizations; Sec. 4.8, the derivative terms of moving vertices; warp
  * field after Bangaru et al. 2020).  The parameters are one translation per
  * shape (all of its vertices move together; a surface point keeps its
- * barycentric coordinates).  Every traced ray -- the camera ray and, at DIFFUSE
- * vertices, the light-sample ray and the BSDF-sampled ray -- is reparameterized:
- * n_aux auxiliary rays in a von Mises-Fisher lobe (concentration kappa) around
- * it estimate a warp field V that follows the geometry they hit (the closer
- * surface dominating near silhouettes, escaping rays weighted `miss`), and the
- * ray contributes R * (m.V + div V), R = grad_image . (radiance the ray carries),
- * m = the ray's cosine (or, for camera rays, the pinhole's image-plane density)
- * term.  Rays leaving non-diffuse vertices are not reparameterized (their
- * directional terms stay detached; the paper notes that specular interfaces are
- * an open problem).  The warp estimator is consistent, not unbiased: its ratio of
- * sample sums is jackknife-corrected, and the camera warp is windowed to zero
- * within `border` pixels of the image border (samples cannot leave the image).
- * The camera is static.
+ * barycentric coordinates).  Every traced ray -- the camera ray and, at diffuse,
+ * GGX-conductor and blend vertices, the light-sample ray and the BSDF-sampled ray
+ * -- is reparameterized: n_aux auxiliary rays in a von Mises-Fisher lobe
+ * (concentration kappa) around it estimate a warp field V that follows the
+ * geometry they hit (the closer surface dominating near silhouettes, escaping rays
+ * weighted `miss`), and the ray contributes m.V + R div V, R = grad_image .
+ * (radiance the ray carries), m = R times the ray's cosine (or, for camera rays,
+ * the pinhole's image-plane density) term plus, at glossy vertices, the BSDF's
+ * gradients in its two directions.  Rays leaving dielectric vertices are not
+ * reparameterized (their directional terms stay detached; the paper notes that
+ * specular interfaces are an open problem).  The warp estimator is consistent,
+ * not unbiased: its ratio of sample sums is jackknife-corrected, and the camera
+ * warp is windowed to zero within `border` pixels of the image border (samples
+ * cannot leave the image).  Because the camera warp also moves the pixels' own
+ * footprints (box filter), each edge between two pixels of the crop adds
+ * (grad_image right/below - left/above) . integral over the edge of L times the
+ * warp's image-plane velocity across it, estimated by edge_spp paths through
+ * uniform points of every edge (PCG32 stream camera << 40 | edge << 12 | sample |
+ * 2^61; edge = y (width + 1) + x for the vertical edge left of pixel (x, y), (width
+ * + 1) height + y width + x for the horizontal one above it; auxiliary stream
+ * | 2^62).  The camera is static.
  *
  * A radiance pass (as split PRB: the forward megakernel storing each sample's
  * radiance, 12 B per sample, in scene-owned scratch grown with cudaMalloc, which
@@ -428,7 +436,9 @@ int pt_ckpt_backward(pt_scene* scene, const pt_render_desc* desc, const pt_param
  * 128; no cache, counters or per-sample outputs.  opts: NULL = defaults
  * (pt_reparam_defaults).  Errors: PT_ERR_ARG (options out of range: 2 <= n_aux <=
  * 32, 0 < kappa <= 1e6, kernel_scale >= 1, 0 <= power <= 16, miss >= 0, eps > 0,
- * border > 0, jackknife 0/1), PT_ERR_STATE, PT_ERR_CUDA. */
+ * border > 0, jackknife 0/1, 0 <= edge_spp <= 4096; with edge_spp > 0 the image's
+ * edge count (width + 1) height + width (height + 1) below 2^28), PT_ERR_STATE,
+ * PT_ERR_CUDA. */
 typedef struct {
   int32_t n_aux;        /* auxiliary rays per reparameterized ray (16) */
   float kappa;          /* vMF concentration of the auxiliary lobe (1000) */
@@ -438,6 +448,7 @@ typedef struct {
   float eps;            /* floor of the normaliser, per auxiliary ray (1e-4) */
   float border;         /* camera-warp window width at the image border, pixels (4) */
   int32_t jackknife;    /* leave-one-out correction of the ratio's 1/N bias (1) */
+  int32_t edge_spp;     /* paths per pixel edge for the pixel-edge term, 0 = off (1) */
 } pt_reparam_opts;
 void pt_reparam_defaults(pt_reparam_opts* opts);
 int pt_render_backward_reparam(pt_scene* scene, const pt_render_desc* desc, const pt_params* params,

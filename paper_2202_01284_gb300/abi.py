@@ -122,7 +122,8 @@ class pt_wavefront_opts(C.Structure):
 
 class pt_reparam_opts(C.Structure):
     _fields_ = [("n_aux", C.c_int32), ("kappa", C.c_float), ("kernel_scale", C.c_float), ("power", C.c_float),
-                ("miss", C.c_float), ("eps", C.c_float), ("border", C.c_float), ("jackknife", C.c_int32)]
+                ("miss", C.c_float), ("eps", C.c_float), ("border", C.c_float), ("jackknife", C.c_int32),
+                ("edge_spp", C.c_int32)]
 
 
 _lib = None

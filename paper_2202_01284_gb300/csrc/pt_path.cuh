@@ -135,18 +135,14 @@ struct PathState {
   float3 beta_dot, L_dot, c_nee_dot, w_next_dot;
 };
 
+// The camera ray through image point (fx, fy) (pixel units, y down) and the path's
+// initial state; the RNG has drawn the point's two uniforms already.
 template <bool INSTR>
-__device__ __forceinline__ void path_start(const LaunchArgs& A, PathState& P, unsigned long long seed, int ci, int px,
-                                           int py, int si, long long pix, Counters<INSTR>& cnt) {
-  P.slot = pix * A.spp + si;
-  P.cache_done = false;
+__device__ __forceinline__ void path_start_at(const LaunchArgs& A, PathState& P, int ci, float fx, float fy,
+                                              Counters<INSTR>& cnt) {
   const DevCamera& cam = A.cams[ci];
-  unsigned long long pixel = (unsigned long long)py * (unsigned long long)A.width + (unsigned long long)px;
-  P.rng.seed(seed, ((unsigned long long)ci << 40) | (pixel << 12) | (unsigned long long)si);
-  P.fh.h = 2166136261u;
-  float j0 = P.rng.uniform(), j1 = P.rng.uniform();
-  float sx = 2.0f * (px + j0) / A.width - 1.0f;
-  float sy = 1.0f - 2.0f * (py + j1) / A.height;
+  float sx = 2.0f * fx / A.width - 1.0f;
+  float sy = 1.0f - 2.0f * fy / A.height;
   P.ro = f3(cam.ox, cam.oy, cam.oz);
   P.rd = normalize3(f3(cam.fx + cam.rx * sx + cam.ux * sy, cam.fy + cam.ry * sx + cam.uy * sy,
                        cam.fz + cam.rz * sx + cam.uz * sy));
@@ -158,6 +154,20 @@ __device__ __forceinline__ void path_start(const LaunchArgs& A, PathState& P, un
   P.prev_pdf = 0.0f;
   P.depth = 1;
   cnt.add(0, 1);
+}
+
+// Sample si of pixel (px, py) of camera ci: its PCG32 stream (camera << 40 |
+// pixel << 12 | sample) and a uniform point of the pixel.
+template <bool INSTR>
+__device__ __forceinline__ void path_start(const LaunchArgs& A, PathState& P, unsigned long long seed, int ci, int px,
+                                           int py, int si, long long pix, Counters<INSTR>& cnt) {
+  P.slot = pix * A.spp + si;
+  P.cache_done = false;
+  unsigned long long pixel = (unsigned long long)py * (unsigned long long)A.width + (unsigned long long)px;
+  P.rng.seed(seed, ((unsigned long long)ci << 40) | (pixel << 12) | (unsigned long long)si);
+  P.fh.h = 2166136261u;
+  float j0 = P.rng.uniform(), j1 = P.rng.uniform();
+  path_start_at<INSTR>(A, P, ci, px + j0, py + j1, cnt);
 }
 
 // Shading step after the closest hit.  Returns false if the path ended here.

@@ -53,6 +53,7 @@ constexpr int kMaxAux = 32;
 struct RpOpts {
   int n_aux, jackknife, smem, group;  // group: lanes per cooperative warp, a power of two >= n_aux
   float kappa, kk, power, miss, eps, border, e2k;
+  int edge_spp;
 };
 
 // One out-of-line traversal shared by all call sites (path, shadow, center and
@@ -83,17 +84,29 @@ __device__ __forceinline__ float3 vmf_dir(const Frame& fr, float u0, float u1, c
   return normalize3(fr.s * (st * cp) + fr.t * (st * sp) + fr.n * (1.0f + c1));
 }
 
-// Window of the camera warp: smoothstep of the distance in pixels to the nearest
-// image border over `border` pixels; b and its gradient on the sphere at u.
-__device__ __forceinline__ float cam_window(const LaunchArgs& A, const DevCamera& c, float3 u, float border,
-                                            float3& grad) {
+// Image-plane coordinates (pixels, y down) of direction u and their gradients with
+// respect to u (the camera's right / up vectors carry the half-extents of the
+// image plane at unit distance).
+__device__ __forceinline__ void pixel_coords(const LaunchArgs& A, const DevCamera& c, float3 u, float& px, float& py,
+                                             float3& gpx, float3& gpy) {
   const float3 f = f3(c.fx, c.fy, c.fz), rs = f3(c.rx, c.ry, c.rz), us = f3(c.ux, c.uy, c.uz);
   const float fw = dot3(f, u), rr = dot3(rs, rs), uu = dot3(us, us);
   const float sx = dot3(rs, u) / (fw * rr), sy = dot3(us, u) / (fw * uu);
   const float W = (float)A.width, H = (float)A.height;
-  const float px = (sx + 1.0f) * 0.5f * W, py = (1.0f - sy) * 0.5f * H;
-  const float3 gpx = (rs - f * (dot3(rs, u) / fw)) * (0.5f * W / (rr * fw));
-  const float3 gpy = (us - f * (dot3(us, u) / fw)) * (-0.5f * H / (uu * fw));
+  px = (sx + 1.0f) * 0.5f * W;
+  py = (1.0f - sy) * 0.5f * H;
+  gpx = (rs - f * (dot3(rs, u) / fw)) * (0.5f * W / (rr * fw));
+  gpy = (us - f * (dot3(us, u) / fw)) * (-0.5f * H / (uu * fw));
+}
+
+// Window of the camera warp: smoothstep of the distance in pixels to the nearest
+// image border over `border` pixels; b and its gradient on the sphere at u.
+__device__ __forceinline__ float cam_window(const LaunchArgs& A, const DevCamera& c, float3 u, float border,
+                                            float3& grad) {
+  const float W = (float)A.width, H = (float)A.height;
+  float px, py;
+  float3 gpx, gpy;
+  pixel_coords(A, c, u, px, py, gpx, gpy);
   float d = px;
   float3 gd = gpx;
   if (W - px < d) { d = W - px; gd = -gpx; }
@@ -618,6 +631,123 @@ __global__ void __launch_bounds__(128, 8) reparam_kernel(const __grid_constant__
   flush_counters<INSTR>(A, cnt);
 }
 
+// Edges of the crop that carry the pixel-edge term, per camera: vertical edges
+// x = xlo .. xlo + nvx - 1 of every crop row, then horizontal edges y = ylo .. ylo +
+// nhy - 1 of every crop column (image-border edges excluded).
+struct EdgeGrid {
+  int xlo, nvx, ylo, nhy;
+  long long per_cam;
+};
+
+// Pixel-edge term of the camera-ray warp (box pixel filter).  The warp that holds
+// the discontinuities still also moves every pixel's footprint, a unit box in pixel
+// coordinates: its boundary moves with minus the warp's image-plane velocity v, so
+// pixel p gains -integral over its boundary of L (v . n_out) ds.  An edge between
+// pixels a (left / above) and b (right / below) thus adds (dLoss/dI_b - dLoss/dI_a)
+// . integral of L v_e ds, v_e the velocity along +x (+y).  One thread per (edge,
+// sample): the path through a uniform point of the edge (PCG32 stream camera << 40
+// | edge << 12 | sample | 2^61) gives L, and its camera ray is posted as a warp with
+// R = 0 and M = (dLoss/dI_b - dLoss/dI_a) . L grad(px) (grad(py)), whose M . V is the
+// integrand.  Image-border edges carry nothing (the window is 0 there); on the
+// crop's border only the inside pixel's loss gradient counts.
+template <int LAYOUT, bool INSTR, bool VERT>
+__global__ void __launch_bounds__(128, 8) edge_kernel(const __grid_constant__ LaunchArgs A, const RpOpts K,
+                                                   const EdgeGrid E, float* __restrict__ grad_t,
+                                                   float* __restrict__ grad_v, unsigned long long* rays_out) {
+  extern __shared__ float s_grad[];
+  const int n3 = 3 * A.scene.n_shapes;
+  if (K.smem) {
+    for (int i = threadIdx.x; i < n3; i += blockDim.x) s_grad[i] = 0.0f;
+    __syncthreads();
+  }
+  GradOut G{K.smem ? s_grad : grad_t};
+  VertOut GV{grad_v};
+  const DevScene& S = A.scene;
+  Counters<INSTR> cnt;
+  if constexpr (INSTR)
+    for (int i = 0; i < 8; ++i) cnt.c[i] = 0;
+  const float3 z = f3(0.f, 0.f, 0.f);
+  const long long unit = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  unsigned rays = 0;
+  WarpRay w{};
+  bool has = false;
+  if (unit < (long long)A.n_cams * E.per_cam * K.edge_spp) {
+    const int k = (int)(unit % K.edge_spp);
+    const long long ea = unit / K.edge_spp;
+    const int ci = (int)(ea / E.per_cam);
+    long long e = ea - (long long)ci * E.per_cam;
+    const long long nv = (long long)A.crop_h * E.nvx;
+    const bool vertical = e < nv;
+    int X, Y;
+    unsigned long long id;
+    if (vertical) {
+      Y = A.crop_y0 + (int)(e / E.nvx);
+      X = E.xlo + (int)(e % E.nvx);
+      id = (unsigned long long)Y * (unsigned long long)(A.width + 1) + (unsigned long long)X;
+    } else {
+      e -= nv;
+      Y = E.ylo + (int)(e / A.crop_w);
+      X = A.crop_x0 + (int)(e % A.crop_w);
+      id = (unsigned long long)(A.width + 1) * (unsigned long long)A.height +
+           (unsigned long long)Y * (unsigned long long)A.width + (unsigned long long)X;
+    }
+    auto dl_at = [&](int x, int y) {
+      if (x < A.crop_x0 || x >= A.crop_x0 + A.crop_w || y < A.crop_y0 || y >= A.crop_y0 + A.crop_h) return z;
+      const long long pix = ((long long)ci * A.crop_h + (y - A.crop_y0)) * A.crop_w + (x - A.crop_x0);
+      return f3(A.grad_image[3 * pix], A.grad_image[3 * pix + 1], A.grad_image[3 * pix + 2]);
+    };
+    const float3 gd = dl_at(X, Y) - (vertical ? dl_at(X - 1, Y) : dl_at(X, Y - 1));
+    if (gd.x != 0.0f || gd.y != 0.0f || gd.z != 0.0f) {
+      const unsigned long long stream = ((unsigned long long)ci << 40) | (id << 12) | (unsigned long long)k | (1ull << 61);
+      PathState P;
+      P.slot = 0;
+      P.cache_done = false;
+      P.rng.seed(A.seed, stream);
+      P.fh.h = 2166136261u;
+      const float j0 = P.rng.uniform();
+      P.rng.uniform();  // the second coordinate's uniform, unused on an edge
+      path_start_at<INSTR>(A, P, ci, vertical ? (float)X : (float)X + j0, vertical ? (float)Y + j0 : (float)Y, cnt);
+      const float3 o = P.ro, u = P.rd;
+      float t0 = INFINITY;
+      GradSink sink;
+      for (bool first = true;; first = false) {
+        const Hit hit = closest<LAYOUT, INSTR>(S, P.ro, P.rd, INFINITY, false, cnt);
+        ++rays;
+        if (first && hit.pos >= 0) t0 = hit.t;
+        if (!path_shade<false, false, INSTR, PT_DISPATCH_SWITCH>(A, P, hit, false, z, sink, cnt)) break;
+        bool occ = false;
+        if (P.has_shadow) {
+          occ = closest<LAYOUT, INSTR>(S, P.so, P.sd, P.stmax, true, cnt).pos >= 0;
+          ++rays;
+        }
+        if (!path_finish<false, false, INSTR>(A, P, occ, false, z, sink, cnt)) break;
+      }
+      const float R = dot3(gd, P.L) / (float)K.edge_spp;
+      if (R != 0.0f) {
+        float px, py;
+        float3 gpx, gpy;
+        pixel_coords(A, A.cams[ci], u, px, py, gpx, gpy);
+        Pcg32 aux;
+        aux.seed(A.seed, stream | (1ull << 62));
+        w = WarpRay{o, u, (vertical ? gpx : gpy) * R, -1, ci, 0.0f, t0, aux.state, aux.inc, -1, 0.0f, 0.0f};
+        has = true;
+      }
+    }
+  }
+  rays += process_warps<LAYOUT, INSTR, VERT>(A, K, has, w, G, GV, cnt);
+  if (K.smem) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < n3; i += blockDim.x)
+      if (s_grad[i] != 0.0f) atomicAdd(&grad_t[i], s_grad[i]);
+  }
+  if (rays_out) {
+    unsigned long long r = rays;
+    for (int off = 16; off > 0; off >>= 1) r += __shfl_xor_sync(kFull, r, off);
+    if (lane_id() == 0 && r) atomicAdd(rays_out, r);
+  }
+  flush_counters<INSTR>(A, cnt);
+}
+
 }  // namespace
 }  // namespace ptgb
 
@@ -633,6 +763,7 @@ extern "C" void pt_reparam_defaults(pt_reparam_opts* o) {
   o->eps = 1e-4f;
   o->border = 4.0f;
   o->jackknife = 1;
+  o->edge_spp = 1;
 }
 
 namespace {
@@ -643,7 +774,7 @@ int reparam_launch(pt_scene* s, const pt_render_desc* r, const pt_params* p, con
   if (opts) o = *opts;
   if (!(o.n_aux >= 2 && o.n_aux <= kMaxAux) || !(o.kappa > 0.0f && o.kappa <= 1e6f) || !(o.kernel_scale >= 1.0f) ||
       !(o.power >= 0.0f && o.power <= 16.0f) || !(o.miss >= 0.0f) || !(o.eps > 0.0f) || !(o.border > 0.0f) ||
-      (o.jackknife != 0 && o.jackknife != 1))
+      (o.jackknife != 0 && o.jackknife != 1) || !(o.edge_spp >= 0 && o.edge_spp <= 4096))
     return PT_ERR_ARG;
   if (!s || !r || !p || !grad_image || (!grad_t && !grad_v)) return PT_ERR_ARG;
   LaunchArgs A;
@@ -660,6 +791,7 @@ int reparam_launch(pt_scene* s, const pt_render_desc* r, const pt_params* p, con
   K.miss = o.miss;
   K.eps = o.eps;
   K.border = o.border;
+  K.edge_spp = o.edge_spp;
   K.e2k = expf(-2.0f * o.kappa);
   K.group = 2;
   while (K.group < o.n_aux) K.group *= 2;
@@ -686,6 +818,35 @@ int reparam_launch(pt_scene* s, const pt_render_desc* r, const pt_params* p, con
     case 5: reparam_kernel<PT_BVH_WIDE, false, true><<<gd, bd, sm, cs>>>(A, K, grad_t, grad_v, rays); break;
     case 6: reparam_kernel<PT_BVH_WIDE, true, false><<<gd, bd, sm, cs>>>(A, K, grad_t, grad_v, rays); break;
     default: reparam_kernel<PT_BVH_WIDE, true, true><<<gd, bd, sm, cs>>>(A, K, grad_t, grad_v, rays); break;
+  }
+  if (cudaGetLastError() != cudaSuccess) return PT_ERR_CUDA;
+  if (o.edge_spp > 0) {
+    EdgeGrid E;
+    E.xlo = A.crop_x0 > 1 ? A.crop_x0 : 1;
+    const int xhi = A.crop_x0 + A.crop_w < A.width - 1 ? A.crop_x0 + A.crop_w : A.width - 1;
+    E.nvx = xhi >= E.xlo ? xhi - E.xlo + 1 : 0;
+    E.ylo = A.crop_y0 > 1 ? A.crop_y0 : 1;
+    const int yhi = A.crop_y0 + A.crop_h < A.height - 1 ? A.crop_y0 + A.crop_h : A.height - 1;
+    E.nhy = yhi >= E.ylo ? yhi - E.ylo + 1 : 0;
+    E.per_cam = (long long)A.crop_h * E.nvx + (long long)E.nhy * A.crop_w;
+    // edge ids (camera << 40 | edge << 12 | sample) need 28 bits for the edge
+    if ((unsigned long long)(A.width + 1) * A.height + (unsigned long long)A.width * (A.height + 1) >= (1ull << 28))
+      return PT_ERR_ARG;
+    const long long units = (long long)A.n_cams * E.per_cam * o.edge_spp;
+    if (units > 0) {
+      const dim3 eg((unsigned)((units + 127) / 128)), eb(128);
+      auto go = [&](auto kernel) { kernel<<<eg, eb, sm, cs>>>(A, K, E, grad_t, grad_v, rays); };
+      switch (v) {
+        case 0: go(edge_kernel<PT_BVH_BINARY, false, false>); break;
+        case 1: go(edge_kernel<PT_BVH_BINARY, false, true>); break;
+        case 2: go(edge_kernel<PT_BVH_BINARY, true, false>); break;
+        case 3: go(edge_kernel<PT_BVH_BINARY, true, true>); break;
+        case 4: go(edge_kernel<PT_BVH_WIDE, false, false>); break;
+        case 5: go(edge_kernel<PT_BVH_WIDE, false, true>); break;
+        case 6: go(edge_kernel<PT_BVH_WIDE, true, false>); break;
+        default: go(edge_kernel<PT_BVH_WIDE, true, true>); break;
+      }
+    }
   }
   return cudaGetLastError() == cudaSuccess ? PT_OK : PT_ERR_CUDA;
 }

@@ -86,7 +86,8 @@ def test_reparam_arguments(lib):
     gi = torch.ones((1, 16, 16, 3), device="cuda")
     g = torch.zeros((3, 3), device="cuda")
     for bad in (dict(n_aux=1), dict(n_aux=33), dict(kappa=0.0), dict(kernel_scale=0.5), dict(eps=0.0),
-                dict(miss=-1.0), dict(border=0.0), dict(jackknife=2), dict(power=-1.0)):
+                dict(miss=-1.0), dict(border=0.0), dict(jackknife=2), dict(power=-1.0), dict(edge_spp=-1),
+                dict(edge_spp=4097)):
         with pytest.raises(lib.PtError):
             ds.backward_reparam(st, gi, g, **bad)
     with pytest.raises(ValueError):
@@ -98,6 +99,43 @@ def test_reparam_arguments(lib):
     ds.backward_reparam(st, torch.zeros_like(gi), g)
     torch.cuda.synchronize()
     assert not g.any()
+
+
+def test_reparam_pixel_edge_term_parity(lib, oracle_mod):
+    """The pixel-edge term on its own (gradient with edge paths minus without), in
+    translation and vertex mode, on the whole image and on a ragged crop whose border
+    edges count for the inside pixel only."""
+    from paper_2202_01284_gb300.render import DeviceScene, RenderSettings
+    sc = S.occluder_sky(center=(0.15, 0.1), side=0.8, width=40, height=40)
+    cam = sc.cameras[0]
+    osc = oracle_mod.OracleScene(sc)
+    ds = DeviceScene(sc)
+    for crop in (None, (5, 7, 27, 22)):
+        h, w = (40, 40) if crop is None else (crop[3], crop[2])
+        gi = np.random.default_rng(11).random((h, w, 3)) - 0.5
+        st = RenderSettings(width=40, height=40, spp=4, max_depth=2, rr_depth=-1, seed=31, crop=crop)
+        r = oracle_mod.render_in(cam, 4, 2, 31, -1, True, crop=crop)
+        gim = torch.as_tensor(gi[None], dtype=torch.float32, device="cuda")
+        n_edges = 39 * 40 * 2 if crop is None else 28 * 22 + 23 * 27
+        for vertex in (False, True):
+            got, ref, n_rays = [], [], []
+            for edge_spp in (0, 8):
+                gt = torch.zeros((sc.n_shapes, 3), device="cuda")
+                gv = torch.zeros((sc.n_tris, 3, 3), device="cuda") if vertex else None
+                rays = torch.zeros(1, dtype=torch.int64, device="cuda")
+                ds.backward_reparam(st, gim, gt, g_vertices=gv, rays=rays, edge_spp=edge_spp)
+                torch.cuda.synchronize()
+                assert ds.status() == 0
+                got.append((gv if vertex else gt).cpu().numpy().astype(np.float64))
+                ref.append(oracle_mod.grad_reparam(osc, r, gi, vertex=vertex, edge_spp=edge_spp)[0])
+                n_rays.append(int(rays.item()))
+            assert n_rays[1] - n_rays[0] >= n_edges * 8  # at least the camera ray of every edge path
+            d, dr = got[1] - got[0], ref[1] - ref[0]
+            c = cosine(d.ravel(), dr.ravel())
+            rel = np.abs(d - dr).max() / np.abs(dr).max()
+            print(f"edge term crop={crop} vertex={vertex}: cosine {c:.7f} max rel {rel:.2e}, "
+                  f"{np.abs(dr).max() / np.abs(ref[0]).max():.2f} of the interior terms")
+            assert c >= 0.9999 and rel < 1e-3
 
 
 def test_reparam_fullsize_crop_parity(lib, oracle_mod):
@@ -308,4 +346,28 @@ def test_reparam_recovers_square_scale_through_vertices(lib):
         loss.backward()
         opt.step()
     print("recovered scale", s.item(), "truth", true_s)
+    assert abs(s.item() - true_s) < 0.03
+
+
+def test_reparam_recovers_square_scale_with_a_sharp_loss(lib):
+    """The same scale recovery with the plain per-pixel L2 loss, no blur: the
+    pixel-edge term gives the derivative of the box-filtered pixels themselves, so
+    the loss on a one-pixel-wide ring of disagreement pulls the right way."""
+    from paper_2202_01284_gb300.render import DeviceScene, RenderSettings, render_vertices
+    sc = S.occluder_sky(width=48, height=48)
+    base = torch.as_tensor(sc.vertices, dtype=torch.float32, device="cuda")
+    c = torch.tensor([0.15, 0.1, -3.0], device="cuda")
+    true_s = 1.25
+    target_sc = S.occluder_sky(width=48, height=48, side=0.4 * true_s)
+    target = DeviceScene(target_sc).forward(RenderSettings(width=48, height=48, spp=256, max_depth=2, seed=99))
+    s = torch.ones(1, device="cuda", requires_grad=True)
+    opt = torch.optim.Adam([s], lr=0.02)
+    for k in range(60):
+        st = RenderSettings(width=48, height=48, spp=16, max_depth=2, seed=100 + k, backward_seed=500 + k)
+        opt.zero_grad()
+        img = render_vertices(sc, st, c + s * (base - c), edge_spp=4)
+        loss = ((img - target) ** 2).mean()
+        loss.backward()
+        opt.step()
+    print("recovered scale (sharp loss)", s.item(), "truth", true_s)
     assert abs(s.item() - true_s) < 0.03
