@@ -85,6 +85,7 @@ def lib():
             L.oracle_bsdf_sample.argtypes = [ip, vp, vp, dp, dp, dp, vp]
             L.oracle_bsdf_sample.restype = ip
             L.oracle_bsdf_dfactors.argtypes = [ip, vp, vp, vp, vp]
+            L.oracle_bsdf_normal_dlog.argtypes = [ip, vp, vp, vp, vp, vp, vp]
             L.oracle_fresnel.argtypes = [dp, dp]
             L.oracle_fresnel.restype = dp
             L.oracle_env_pdf.argtypes = [vp, vp]
@@ -375,6 +376,16 @@ def bsdf_dfactors(bsdf, params, wi, wo):
     lib().oracle_bsdf_dfactors(bsdf, _ptr(params), _ptr(np.asarray(wi, np.float64)),
                                _ptr(np.asarray(wo, np.float64)), _ptr(out))
     return out[:3], out[3:]
+
+
+def bsdf_normal_dlog(bsdf, params, corners, n, wi, wo) -> np.ndarray:
+    """d log f_c / d corner coordinate [3 corners, 3 axes, 3 channels] through the unit
+    normal of the triangle `corners` [3, 3] (oriented like n); wi, wo world directions."""
+    out = np.zeros(27)
+    f64 = lambda a: np.ascontiguousarray(a, np.float64)
+    lib().oracle_bsdf_normal_dlog(bsdf, _ptr(params), _ptr(f64(corners)), _ptr(f64(n)), _ptr(f64(wi)),
+                                  _ptr(f64(wo)), _ptr(out))
+    return out.reshape(3, 3, 3)
 
 
 def fresnel(cos_i, eta):

@@ -1511,6 +1511,35 @@ void bsdf_log_grad(const Mat& m, V3 wi, V3 wo, bool wrt_out, V3 g[3]) {
     g[c] = f[c].v > 0 ? fr.s * (f[c].a / f[c].v) + fr.t * (f[c].b / f[c].v) : V3();
 }
 
+// Derivative of log f_c (per channel) at a glossy vertex with respect to the 9
+// coordinates of its triangle's corners v0, v1, v2 (index 3 corner + axis), through
+// the unit normal they define (oriented like n): the Duff et al. 2017 frame of the
+// normal in dual numbers gives the local directions of the fixed world directions
+// wi, wo, and f is evaluated on them (vertex mode: a non-rigid motion turns n).
+void bsdf_normal_log_derivs(V3 v0, V3 v1, V3 v2, V3 n, const Mat& m, V3 wi, V3 wo, V3 out[9]) {
+  for (int p = 0; p < 9; ++p) {
+    out[p] = V3();
+    if (m.bsdf == BSDF_DIFFUSE) continue;
+    const int k = p / 3;
+    const V3 e = axis_vec(p % 3, D2{});
+    VD v[3] = {constant(v0), constant(v1), constant(v2)};
+    v[k] = VD{D2{v[k].x.v, e.x, 0}, D2{v[k].y.v, e.y, 0}, D2{v[k].z.v, e.z, 0}};
+    VD e1{v[1].x - v[0].x, v[1].y - v[0].y, v[1].z - v[0].z}, e2{v[2].x - v[0].x, v[2].y - v[0].y, v[2].z - v[0].z};
+    VD c{e1.y * e2.z - e1.z * e2.y, e1.z * e2.x - e1.x * e2.z, e1.x * e2.y - e1.y * e2.x};
+    const double orient = dot(V3(c.x.v, c.y.v, c.z.v), n) < 0.0 ? -1.0 : 1.0;
+    VD nn = divided(c, d2sqrt(dotd(c, c)) * orient);
+    const double sg = nn.z.v >= 0.0 ? 1.0 : -1.0;
+    const D2 a = D2{-1, 0, 0} / (nn.z + D2{sg, 0, 0});
+    const D2 b = nn.x * nn.y * a;
+    VD fs{D2{1, 0, 0} + nn.x * nn.x * a * sg, b * sg, nn.x * (-sg)};
+    VD ft{b, D2{sg, 0, 0} + nn.y * nn.y * a, nn.y * -1.0};
+    VD wil{dotd(fs, wi), dotd(ft, wi), dotd(nn, wi)}, wol{dotd(fs, wo), dotd(ft, wo), dotd(nn, wo)};
+    D2 f[3];
+    bsdf_value_dirs(m, wil, wol, f);
+    for (int ch = 0; ch < 3; ++ch) out[p][ch] = f[ch].v > 0 ? f[ch].a / f[ch].v : 0.0;
+  }
+}
+
 bool reparameterized(int bsdf) { return bsdf == BSDF_DIFFUSE || bsdf == BSDF_CONDUCTOR || bsdf == BSDF_BLEND; }
 
 // Forward-mode accumulator of the translation derivatives (all shapes at once).
@@ -1528,6 +1557,7 @@ struct ReparamAcc {
   Sparse lnee, lbsdf, tmp;
   SparseV wnee, wbsdf, wprev;  // tangential direction change of the light ray, the BSDF ray, the previous ray
   V3 nee_n, bsdf_n;            // world normal of the vertex the rays leave
+  int nee_tri = -1, bsdf_tri = -1;  // and its triangle
   CamWindow win;
   bool vertex = false;
   void init(const Scene* sc, const ReparamOpts* o, uint64_t sd, const Camera& cam, bool vert) {
@@ -1570,17 +1600,21 @@ struct ReparamAcc {
   }
   void nee_ray(V3 o, V3 d, int tri, double bu, double bv, V3 n, int bsdf) {
     nee_n = n;
+    nee_tri = tri;
     ray(o, d, tri, bu, bv, n, bsdf, block.data(), lnee, wnee);
   }
   void bsdf_ray(V3 o, V3 d, int tri, double bu, double bv, V3 n, int bsdf) {
     bsdf_n = n;
+    bsdf_tri = tri;
     ray(o, d, tri, bu, bv, n, bsdf, block.data() + 2 * op->n_aux, lbsdf, wbsdf);
   }
-  // Per-channel log-derivative of one term of vertex `vi` leaving along wl (local):
-  // the ray's warp terms, plus the BSDF's dependence on the outgoing direction
-  // (turned by this ray's warp) and on the incident one (turned by the previous
-  // ray's warp; it points back along that ray).
-  std::vector<std::pair<int, V3>> term(const VertexInfo& vi, V3 wl, V3 n, const Sparse& l, const SparseV& w) {
+  // Per-channel log-derivative of one term of vertex `vi` (on triangle tri) leaving
+  // along wl (local): the ray's warp terms, plus the BSDF's dependence on the
+  // outgoing direction (turned by this ray's warp), on the incident one (turned by
+  // the previous ray's warp; it points back along that ray) and, with vertex
+  // positions as parameters, on the triangle's turning normal.
+  std::vector<std::pair<int, V3>> term(const VertexInfo& vi, V3 wl, V3 n, int tri, const Sparse& l,
+                                       const SparseV& w) {
     std::vector<std::pair<int, V3>> out;
     for (auto& pv : l) out.push_back({pv.first, V3(1, 1, 1) * pv.second});
     if (vi.m.bsdf == BSDF_DIFFUSE) return out;
@@ -1606,6 +1640,11 @@ struct ReparamAcc {
       V3 di = -pw.second;  // the incident direction points back along the previous ray
       add(pw.first, V3(dot(giw[0], di), dot(giw[1], di), dot(giw[2], di)));
     }
+    if (vertex && tri >= 0) {
+      V3 nd[9];
+      bsdf_normal_log_derivs(s->v0[tri], s->v1[tri], s->v2[tri], n, vi.m, fr.to_world(vi.wi), fr.to_world(wl), nd);
+      for (int q = 0; q < 9; ++q) add(9 * tri + q, nd[q]);
+    }
     return out;
   }
   void emission(V3, V3 le_w, int, V3, double) {
@@ -1614,13 +1653,13 @@ struct ReparamAcc {
   void nee(const VertexInfo& vi, V3 wl, V3 scale, V3 c, int, V3, double) {
     V3 f = bsdf_eval(vi.m, vi.wi, wl);
     for (int p = 0; p < np; ++p) ldot[p] = ldot[p] + mul(mul(bdot[p], f), scale);
-    for (auto& pv : term(vi, wl, nee_n, lnee, wnee)) ldot[pv.first] = ldot[pv.first] + mul(c, pv.second);
+    for (auto& pv : term(vi, wl, nee_n, nee_tri, lnee, wnee)) ldot[pv.first] = ldot[pv.first] + mul(c, pv.second);
   }
   void scatter(const VertexInfo& vi, V3 wo, double k) {
     V3 f = bsdf_eval(vi.m, vi.wi, wo);
     V3 nb = mul(beta, f) * k;
     for (int p = 0; p < np; ++p) bdot[p] = mul(bdot[p], f) * k;
-    for (auto& pv : term(vi, wo, bsdf_n, lbsdf, wbsdf)) bdot[pv.first] = bdot[pv.first] + mul(nb, pv.second);
+    for (auto& pv : term(vi, wo, bsdf_n, bsdf_tri, lbsdf, wbsdf)) bdot[pv.first] = bdot[pv.first] + mul(nb, pv.second);
     beta = nb;
     wprev = wbsdf;
   }
@@ -2221,6 +2260,17 @@ void oracle_bsdf_eval(int bsdf, const double* params, const double* wi, const do
   V3 f = bsdf_eval(m, a, b);
   for (int c = 0; c < 3; ++c) f_out[c] = f[c];
   *pdf_out = bsdf_pdf(m, a, b);
+}
+// d log f_c / d (corner k, axis a) at [3 (3 k + a) + c] through the normal of the
+// triangle v (9 doubles), oriented like n; wi, wo world directions.
+void oracle_bsdf_normal_dlog(int bsdf, const double* params, const double* v, const double* n, const double* wi,
+                             const double* wo, double* out27) {
+  Mat m = hook_mat(bsdf, params);
+  V3 d[9];
+  bsdf_normal_log_derivs(V3(v[0], v[1], v[2]), V3(v[3], v[4], v[5]), V3(v[6], v[7], v[8]), V3(n[0], n[1], n[2]), m,
+                         V3(wi[0], wi[1], wi[2]), V3(wo[0], wo[1], wo[2]), d);
+  for (int p = 0; p < 9; ++p)
+    for (int c = 0; c < 3; ++c) out27[3 * p + c] = d[p][c];
 }
 // Returns 1 and wo if sampling succeeded (non-delta BSDFs).
 int oracle_bsdf_sample(int bsdf, const double* params, const double* wi, double u3, double u4, double u5,
