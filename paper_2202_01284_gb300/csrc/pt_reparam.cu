@@ -417,16 +417,18 @@ __device__ Gloss gloss_at(const LaunchArgs& A, const Hit& hit) {
   return g;
 }
 
-// Gradient of log|n . u| with respect to the corners of the triangle at leaf
-// position pos (n its unit geometric normal): with c = e1 x e2 and
-// w = (u - n (n.u)) / |c|, d(n.u) = de1.(e2 x w) + de2.(w x e1).
-__device__ __forceinline__ void normal_log_grad(const DevScene& S, int pos, float3 u, float scale, float3 (&g)[3]) {
+// Vertex mode: gradient with respect to the corners of the triangle at leaf position
+// pos of scale log|n . u| + q . n, n its unit geometric normal (q: a covector on the
+// normal's change, here from a glossy BSDF).  With c = e1 x e2 and w = (p - n (n.p))
+// / |c|, p = scale u / (n.u) + q: d(...) = dn . p = de1.(e2 x w) + de2.(w x e1).
+__device__ __forceinline__ void normal_log_grad(const DevScene& S, int pos, float3 u, float scale, float3 q,
+                                                float3 (&g)[3]) {
   const float3 e1 = xyz(__ldg(&S.tri_v[3 * pos + 1])), e2 = xyz(__ldg(&S.tri_v[3 * pos + 2]));
   const float3 c = cross3(e1, e2);
   const float len = sqrtf(dot3(c, c));
   const float3 nn = c * (1.0f / len);
-  const float nu = dot3(nn, u);
-  const float3 w = (u - nn * nu) * (scale / (len * nu));
+  const float3 p = u * (scale / dot3(nn, u)) + q;
+  const float3 w = (p - nn * dot3(nn, p)) * (1.0f / len);
   g[1] = cross3(e2, w);
   g[2] = cross3(w, e1);
   g[0] = -(g[1] + g[2]);
@@ -514,12 +516,12 @@ __global__ void __launch_bounds__(128, 8) reparam_kernel(const __grid_constant__
       ++rays;  // its twin in the radiance pass
       const bool block = hit.pos >= 0 && P.depth < A.max_depth;
       int s_o = -1, o_tri = -1;
-      float3 n_s = z;
+      float3 n_s = z, ng = z;
       const float3 wi_w = -P.rd;
       if (hit.pos >= 0) {
         s_o = tri_shape(S, hit.pos);
         o_tri = tri_orig(S, hit.pos);
-        const float3 ng = tri_normal(S, hit.pos);
+        ng = tri_normal(S, hit.pos);
         n_s = dot3(ng, P.rd) < 0.0f ? ng : -ng;
       }
       bool more = path_shade<false, false, INSTR, PT_DISPATCH_SWITCH>(A, P, hit, false, z, sink, cnt);
@@ -549,17 +551,27 @@ __global__ void __launch_bounds__(128, 8) reparam_kernel(const __grid_constant__
           wi_l = fr.to_local(wi_w);
         }
         // covector of the term C (per channel) leaving along d: R n/(n.d) plus, at a
-        // glossy vertex, sum_c dl_c C_c grad_out log f_c; adds to `inc` the incident part
+        // glossy vertex, sum_c dl_c C_c grad_out log f_c; adds to `inc` the incident part.
+        // Vertex mode: the glossy value also depends on the turning normal; f is
+        // unchanged when n, wi and wo turn together, so for a turn n' = w x n (w = n x n')
+        // d log f = -w . (wi x grad_in + wo x grad_out) = n' . (n x J): qn = ng x J, the
+        // same for either orientation of the normal.
+        float3 qn = z;
         auto covector = [&](float3 d, float3 C, float R) {
           float3 M = n_s * (R / dot3(n_s, d));
+          qn = z;
           if (glossy) {
             float3 go[3], gi[3];
             glossy_log_grad(gl.type, gl.alpha, gl.f0, gl.wd, gl.albedo, wi_l, fr.to_local(d), go, gi);
             const float wc[3] = {dl.x * C.x, dl.y * C.y, dl.z * C.z};
+            float3 Go = z, Gi = z;
             for (int c = 0; c < 3; ++c) {
-              M = M + fr.to_world(go[c]) * wc[c];
-              inc = inc + fr.to_world(gi[c]) * wc[c];
+              Go = Go + fr.to_world(go[c]) * wc[c];
+              Gi = Gi + fr.to_world(gi[c]) * wc[c];
             }
+            M = M + Go;
+            inc = inc + Gi;
+            if constexpr (VERT) qn = cross3(ng, cross3(wi_w, Gi) + cross3(d, Go));
           }
           return M;
         };
@@ -574,7 +586,7 @@ __global__ void __launch_bounds__(128, 8) reparam_kernel(const __grid_constant__
             h0 = true;
             if constexpr (VERT) {
               float3 gn[3];
-              normal_log_grad(S, hit.pos, P.sd, R, gn);
+              normal_log_grad(S, hit.pos, P.sd, R, qn, gn);
               GV.add(o_tri, gn);
             }
           }
@@ -591,9 +603,9 @@ __global__ void __launch_bounds__(128, 8) reparam_kernel(const __grid_constant__
                         aux_bsdf.inc, o_tri, hit.u, hit.v};
           has_out = true;
           if constexpr (VERT) {
-            if (R != 0.0f) {
+            if (R != 0.0f || qn.x != 0.0f || qn.y != 0.0f || qn.z != 0.0f) {
               float3 gn[3];
-              normal_log_grad(S, hit.pos, P.rd, R, gn);
+              normal_log_grad(S, hit.pos, P.rd, R, qn, gn);
               GV.add(o_tri, gn);
             }
           }

@@ -269,7 +269,9 @@ def test_reparam_vertex_parity(lib, oracle_mod):
 def test_reparam_glossy_parity(lib, oracle_mod, bsdf):
     """Glossy floor (GGX conductor, blend): the rays leaving it add the BSDF's
     directional terms, and the arriving ray's warp takes the floor's incident-direction
-    terms (posted one vertex later)."""
+    terms (posted one vertex later); in vertex mode the BSDF value also follows the
+    floor triangles' turning normals (closed form on the GPU, dual-number frame in the
+    oracle)."""
     gi = np.random.default_rng(5).random((48, 48, 3)) + 0.2
     sc = S.shadow_scene(width=48, height=48, floor_bsdf=bsdf, floor_alpha=0.3)
     _, _, c, rel, _ = _compare(oracle_mod, sc, 16, 3, 31, gi)
@@ -284,6 +286,8 @@ def test_reparam_textured_blend_scene(lib, oracle_mod):
     gi = np.random.default_rng(6).random((32, 32, 3))
     _, _, c, rel, _ = _compare(oracle_mod, sc, 2, 4, 17, gi, rr_depth=2, layout=0, n_aux=8)
     assert c >= 0.9999 and rel < 1e-2
+    c, rel, srel = _compare_vertices(oracle_mod, sc, 2, 4, 17, gi, rr_depth=2, layout=0, n_aux=8)
+    assert c >= 0.999 and srel < 1e-3
 
 
 def test_reparam_without_light_sampling_and_depth_one(lib, oracle_mod):
