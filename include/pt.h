@@ -457,8 +457,9 @@ int pt_render_backward_reparam(pt_scene* scene, const pt_render_desc* desc, cons
 /* The same estimator with every triangle corner's position as a parameter (the
  * paper's vertex-position optimisation, Sec. 4.10): a surface point moves with its
  * barycentric weights, so the warp's plane points carry the barycentric
- * coordinates of the (extended) hit triangle, and the cosine of a moving vertex
- * adds the derivative of its triangle's normal.  grad_vertices: device float
+ * coordinates of the (extended) hit triangle, and the cosine and (glossy BSDFs)
+ * the BSDF value of a moving vertex add the derivative of its triangle's turning
+ * normal.  grad_vertices: device float
  * [n_tris][3][3] in the order of pt_scene_desc.vertices (corner k of triangle t at
  * [t][k]), accumulated; shared positions are the caller's to sum.  The per-corner
  * gradients of a shape sum to its translation gradient.  Same arguments, counters
