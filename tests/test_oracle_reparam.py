@@ -121,11 +121,13 @@ def test_shadow_scene_matches_finite_differences(oracle_mod):
     assert np.abs(g[1:]).max() > 0.5 * np.abs(fd[1:]).max()
 
 
-def test_vertex_gradients_sum_to_translation_gradients(oracle_mod):
+@pytest.mark.parametrize("floor", [S.BSDF_DIFFUSE, S.BSDF_CONDUCTOR])
+def test_vertex_gradients_sum_to_translation_gradients(oracle_mod, floor):
     """Moving every corner of a shape by the same vector is its translation: the
     per-corner gradients of a shape sum to its translation gradient (the normal
-    terms cancel, the plane points' barycentric weights sum to one)."""
-    sc = S.shadow_scene(width=32, height=32)
+    terms, of the cosine and of a glossy BSDF value, cancel; the plane points'
+    barycentric weights sum to one; the pixel-edge terms follow)."""
+    sc = S.shadow_scene(width=32, height=32, floor_bsdf=floor)
     osc = oracle_mod.OracleScene(sc)
     r = oracle_mod.render_in(sc.cameras[0], 8, 3, 21, -1, True)
     gi = np.random.default_rng(2).random((32, 32, 3)) + 0.5
