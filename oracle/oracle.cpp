@@ -1294,7 +1294,7 @@ struct Origin {
 };
 
 // Motion of the origin for the unit tangent of parameter P.
-V3 origin_motion(const Scene& s, const Origin& og, const Param& P) {
+V3 origin_motion(const Origin& og, const Param& P) {
   if (og.tri < 0) return V3();
   V3 e = axis_vec(P.axis, D2{});
   if (!P.vertex) return og.shape == P.index ? e : V3();
@@ -1334,7 +1334,7 @@ VD aux_velocity(const Scene& s, const AuxHit& h, V3 o, const Origin& og, const P
   } else if (h.tri == P.index) {
     mt = plane_barycentric_over_t(s, h.tri, o, w, P.corner);
   }
-  V3 om = origin_motion(s, og, P);
+  V3 om = origin_motion(og, P);
   VD rel{mt * e.x - inv_t * om.x, mt * e.y - inv_t * om.y, mt * e.z - inv_t * om.z};  // relative motion / t(w)
   D2 wr = dotd(w, rel);
   return VD{rel.x - w.x * wr, rel.y - w.y * wr, rel.z - w.z * wr};
@@ -1471,7 +1471,6 @@ void warp_log_derivs(const Scene& s, const WarpSamples& ws, V3 o, const Origin& 
 // GGX conductor and blend, the same formulas as bsdf_eval_t.
 void bsdf_value_dirs(const Mat& m, VD wi, VD wo, D2 out[3]) {
   for (int c = 0; c < 3; ++c) out[c] = D2{};
-  D2 kd{0, 0, 0};
   if (m.bsdf == BSDF_DIFFUSE || m.bsdf == BSDF_BLEND) {
     const double w = m.bsdf == BSDF_DIFFUSE ? 1.0 : m.wd;
     for (int c = 0; c < 3; ++c) out[c] = D2{m.albedo[c] * w / kPi, 0, 0};
