@@ -408,16 +408,19 @@ int pt_ckpt_backward(pt_scene* scene, const pt_render_desc* desc, const pt_param
  * gradients in its two directions.  Rays leaving dielectric vertices are not
  * reparameterized (their directional terms stay detached; the paper notes that
  * specular interfaces are an open problem).  The warp estimator is consistent,
- * not unbiased: its ratio of sample sums is jackknife-corrected, and the camera
- * warp is windowed to zero within `border` pixels of the image border (samples
- * cannot leave the image).  Because the camera warp also moves the pixels' own
- * footprints (box filter), each edge between two pixels of the crop adds
- * (grad_image right/below - left/above) . integral over the edge of L times the
- * warp's image-plane velocity across it, estimated by edge_spp paths through
- * uniform points of every edge (PCG32 stream camera << 40 | edge << 12 | sample |
- * 2^61; edge = y (width + 1) + x for the vertical edge left of pixel (x, y), (width
- * + 1) height + y width + x for the horizontal one above it; auxiliary stream
- * | 2^62).  The camera is static.
+ * not unbiased: its ratio of sample sums is jackknife-corrected.  Because the
+ * camera warp also moves the pixels' own footprints (box filter), each edge of a
+ * pixel of the crop adds (grad_image right/below - left/above, 0 outside the crop)
+ * . integral over the edge of L times the warp's image-plane velocity across it,
+ * estimated by edge_spp paths through uniform points of every edge (PCG32 stream
+ * camera << 40 | edge << 12 | sample | 2^61; edge = y (width + 1) + x for the
+ * vertical edge left of pixel (x, y), (width + 1) height + y width + x for the
+ * horizontal one above it; auxiliary stream | 2^62); on the image border this is
+ * the flux of radiance entering or leaving the image.  Optionally (border > 0)
+ * the camera warp is instead windowed to zero within `border` pixels of the image
+ * border, which biases whatever moves there.  The camera is static; its
+ * translation is minus the sum of all shapes' translations (the environment lies
+ * at infinity).
  *
  * A radiance pass (as split PRB: the forward megakernel storing each sample's
  * radiance, 12 B per sample, in scene-owned scratch grown with cudaMalloc, which
@@ -436,7 +439,7 @@ int pt_ckpt_backward(pt_scene* scene, const pt_render_desc* desc, const pt_param
  * 128; no cache, counters or per-sample outputs.  opts: NULL = defaults
  * (pt_reparam_defaults).  Errors: PT_ERR_ARG (options out of range: 2 <= n_aux <=
  * 32, 0 < kappa <= 1e6, kernel_scale >= 1, 0 <= power <= 16, miss >= 0, eps > 0,
- * border > 0, jackknife 0/1, 0 <= edge_spp <= 4096; with edge_spp > 0 the image's
+ * border >= 0, jackknife 0/1, 0 <= edge_spp <= 4096; with edge_spp > 0 the image's
  * edge count (width + 1) height + width (height + 1) below 2^28), PT_ERR_STATE,
  * PT_ERR_CUDA. */
 typedef struct {
@@ -446,7 +449,7 @@ typedef struct {
   float power;          /* depth-weight exponent: g = (t0 / t)^power (2) */
   float miss;           /* weight of an auxiliary ray that escapes (0.01) */
   float eps;            /* floor of the normaliser, per auxiliary ray (1e-4) */
-  float border;         /* camera-warp window width at the image border, pixels (4) */
+  float border;         /* camera-warp window width at the image border, pixels; 0 = none (0) */
   int32_t jackknife;    /* leave-one-out correction of the ratio's 1/N bias (1) */
   int32_t edge_spp;     /* paths per pixel edge for the pixel-edge term, 0 = off (1) */
 } pt_reparam_opts;

@@ -269,11 +269,11 @@ def render_jvp(osc: OracleScene, r: RenderIn, t_albedo=None, t_textures=None, t_
 # Options of the reparameterized translation derivative: auxiliary rays per
 # traced ray, vMF concentration of their lobe, how much narrower the weighting
 # kernel is, depth-weight exponent, weight of escaping rays, normaliser floor,
-# leave-one-out correction on/off, width in pixels of the window that takes the
-# camera-ray warp to zero at the image border, paths per pixel edge for the term
-# of the pixels' own moving boundaries (0: off).
+# leave-one-out correction on/off, width in pixels of an optional window that
+# takes the camera-ray warp to zero at the image border (0: none), paths per pixel
+# edge for the term of the pixels' own moving boundaries (0: off).
 REPARAM_DEFAULTS = dict(n_aux=16, kappa=1000.0, kernel_scale=8.0, power=2.0, miss=0.01, eps=1e-4,
-                        jackknife=1, border=4.0, edge_spp=1)
+                        jackknife=1, border=0.0, edge_spp=1)
 
 
 def _reparam_in(opts) -> ReparamIn:

@@ -1143,9 +1143,9 @@ struct JvpAcc : NoRayEvents {
 //
 // Each traced ray multiplies the integrand it carries by
 //   camera ray: 1 + theta (div(bV) - 3 f.(bV) / f.u), the image-plane measure of
-//               the pinhole (f = optical axis); b is a window that takes the warp
-//               to 0 within `border` pixels of the image border, where samples
-//               cannot be moved;
+//               the pinhole (f = optical axis); b = 1, or with border > 0 a window
+//               that takes the warp to 0 within `border` pixels of the image
+//               border (an option: the pixel-edge term below makes it unneeded);
 //   light and BSDF rays at a diffuse vertex: 1 + theta (div V + n.V / n.u), the
 //               cosine term.
 // Rays leaving non-diffuse vertices are not reparameterized (their directional
@@ -1161,7 +1161,7 @@ struct ReparamOpts {
   double miss = 0.01;         // weight of an auxiliary ray that escapes (velocity 0)
   double eps = 1e-4;          // floor of the normaliser
   int jackknife = 1;          // leave-one-out correction of the ratio's 1/N bias
-  double border = 4.0;        // camera-ray warp window at the image border, pixels
+  double border = 0.0;        // camera-ray warp window at the image border, pixels (0: none)
   int edge_spp = 1;           // samples per pixel edge of the pixel-edge term (0: off)
 };
 
@@ -1371,15 +1371,18 @@ double normal_derivative(const Scene& s, const Origin& og, const Param& P, V3 u)
   return nu.a / nu.v;
 }
 
-// Window of the camera-ray warp: 1 inside the image, falling to 0 at its border
-// over `border` pixels (smoothstep of the distance in pixels to the nearest image
-// edge), so that no sample is moved across the border of the image.
+// Window of the camera-ray warp (border > 0): 1 inside the image, falling to 0 at
+// its border over `border` pixels (smoothstep of the distance in pixels to the
+// nearest image edge), so that no sample is moved across the border of the image;
+// border = 0: no window (samples near the border move across it, and the
+// pixel-edge term on the image-border edges accounts for the flux).
 struct CamWindow {
   V3 fwd, right, up;
   double tan_half = 1, aspect = 1, border = 4;
   int w = 1, h = 1;
 };
 D2 window(const CamWindow& c, VD w) {
+  if (c.border <= 0.0) return D2{1, 0, 0};
   D2 fw = dotd(w, c.fwd);
   D2 sx = dotd(w, c.right) / fw * (1.0 / (c.tan_half * c.aspect));
   D2 sy = dotd(w, c.up) / fw * (1.0 / c.tan_half);
@@ -2102,7 +2105,7 @@ static bool reparam_opts(const oracle_reparam_opts* o, ReparamOpts& op) {
   op.jackknife = o->jackknife;
   op.border = o->border;
   op.edge_spp = o->edge_spp;
-  return o->border > 0 && o->edge_spp >= 0;
+  return o->border >= 0 && o->edge_spp >= 0;
 }
 
 // Reverse-mode-equivalent gradient by forward mode: g[p] = sum over pixels and
@@ -2128,8 +2131,9 @@ int oracle_grad_reparam(void* sc, const oracle_render_in* r, const double* grad_
   // -integral over its boundary of L (v . n_out) ds.  An edge between pixels a
   // (left / above) and b (right / below) adds -L v_n to a and +L v_n to b, v_n
   // the velocity along +x (+y); one path through a uniform point of the edge
-  // estimates the integral.  Edges on the image border carry none (the window
-  // vanishes there); those on the crop's border count for the inside pixel.
+  // estimates the integral.  Every edge of every pixel of the crop: on the crop's
+  // (or the image's) border only the inside pixel counts; with a border window the
+  // image-border edges carry nothing (the warp vanishes there).
   std::vector<double> edge_dot((size_t)(ch + 1) * cw * 3, 0.0);  // horizontal edges: L v_n of dot_param
   if (image_dot) std::fill(image_dot, image_dot + (size_t)cw * ch * 3, 0.0);
   if (op.edge_spp > 0 && (grad_image || (image_dot && dot_param >= 0 && dot_param < np))) {
@@ -2166,7 +2170,7 @@ int oracle_grad_reparam(void* sc, const oracle_render_in* r, const double* grad_
       };
       const uint64_t nv = (uint64_t)(r->width + 1) * r->height;  // vertical edges first, then horizontal
       if (Y < y0 + ch)
-        for (int X = std::max(x0, 1); X <= std::min(x0 + cw, r->width - 1); ++X) {
+        for (int X = x0; X <= x0 + cw; ++X) {
           V3 d = edge(true, X, Y, (uint64_t)Y * (r->width + 1) + X);
           if (!image_dot) continue;
           double* row = image_dot + (size_t)(Y - y0) * cw * 3;
@@ -2175,11 +2179,10 @@ int oracle_grad_reparam(void* sc, const oracle_render_in* r, const double* grad_
             if (X < x0 + cw) row[(X - x0) * 3 + c] += d[c];
           }
         }
-      if (Y >= 1 && Y <= r->height - 1)
-        for (int X = x0; X < x0 + cw; ++X) {
-          V3 d = edge(false, X, Y, nv + (uint64_t)Y * r->width + X);
-          for (int c = 0; c < 3; ++c) edge_dot[((size_t)(Y - y0) * cw + (X - x0)) * 3 + c] = d[c];
-        }
+      for (int X = x0; X < x0 + cw; ++X) {
+        V3 d = edge(false, X, Y, nv + (uint64_t)Y * r->width + X);
+        for (int c = 0; c < 3; ++c) edge_dot[((size_t)(Y - y0) * cw + (X - x0)) * 3 + c] = d[c];
+      }
     });
     if (image_dot)
       for (int Y = y0; Y <= y0 + ch; ++Y)

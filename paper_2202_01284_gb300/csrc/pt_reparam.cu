@@ -33,8 +33,8 @@
 // with p_i = (I - u u^T) w_i, P = sum alpha_j p_j, D = sum alpha_j + N eps.  The
 // ratio's O(1/N) bias is removed by the leave-one-out (jackknife) combination
 // N f(all) - (N-1)/N sum_j f(all but j), evaluated with two extra sums.  For the
-// camera ray the warp is multiplied by a window b that reaches 0 at the image
-// border, adding R grad(b) . C.  Because every term is linear in the velocities,
+// camera ray the warp may be multiplied by a window b that reaches 0 at the image
+// border (option), adding R grad(b) . C.  Because every term is linear in the velocities,
 // the reverse-mode gradient of a ray is the coefficient vector of each Delta_i: it
 // is added to the hit's shape (or triangle corners) and subtracted from the
 // origin's.
@@ -100,9 +100,15 @@ __device__ __forceinline__ void pixel_coords(const LaunchArgs& A, const DevCamer
 }
 
 // Window of the camera warp: smoothstep of the distance in pixels to the nearest
-// image border over `border` pixels; b and its gradient on the sphere at u.
+// image border over `border` pixels; b and its gradient on the sphere at u.  No
+// window (b = 1) for border = 0: the pixel-edge term then carries the flux through
+// the image border.
 __device__ __forceinline__ float cam_window(const LaunchArgs& A, const DevCamera& c, float3 u, float border,
                                             float3& grad) {
+  if (border <= 0.0f) {
+    grad = f3(0.f, 0.f, 0.f);
+    return 1.0f;
+  }
   const float W = (float)A.width, H = (float)A.height;
   float px, py;
   float3 gpx, gpy;
@@ -645,7 +651,7 @@ __global__ void __launch_bounds__(128, 8) reparam_kernel(const __grid_constant__
 
 // Edges of the crop that carry the pixel-edge term, per camera: vertical edges
 // x = xlo .. xlo + nvx - 1 of every crop row, then horizontal edges y = ylo .. ylo +
-// nhy - 1 of every crop column (image-border edges excluded).
+// nhy - 1 of every crop column (all edges of the crop's pixels).
 struct EdgeGrid {
   int xlo, nvx, ylo, nhy;
   long long per_cam;
@@ -660,8 +666,8 @@ struct EdgeGrid {
 // sample): the path through a uniform point of the edge (PCG32 stream camera << 40
 // | edge << 12 | sample | 2^61) gives L, and its camera ray is posted as a warp with
 // R = 0 and M = (dLoss/dI_b - dLoss/dI_a) . L grad(px) (grad(py)), whose M . V is the
-// integrand.  Image-border edges carry nothing (the window is 0 there); on the
-// crop's border only the inside pixel's loss gradient counts.
+// integrand.  On the crop's (or image's) border only the inside pixel's loss
+// gradient counts; with a border window the image-border edges carry nothing.
 template <int LAYOUT, bool INSTR, bool VERT>
 __global__ void __launch_bounds__(128, 8) edge_kernel(const __grid_constant__ LaunchArgs A, const RpOpts K,
                                                    const EdgeGrid E, float* __restrict__ grad_t,
@@ -773,7 +779,7 @@ extern "C" void pt_reparam_defaults(pt_reparam_opts* o) {
   o->power = 2.0f;
   o->miss = 0.01f;
   o->eps = 1e-4f;
-  o->border = 4.0f;
+  o->border = 0.0f;
   o->jackknife = 1;
   o->edge_spp = 1;
 }
@@ -785,7 +791,7 @@ int reparam_launch(pt_scene* s, const pt_render_desc* r, const pt_params* p, con
   pt_reparam_defaults(&o);
   if (opts) o = *opts;
   if (!(o.n_aux >= 2 && o.n_aux <= kMaxAux) || !(o.kappa > 0.0f && o.kappa <= 1e6f) || !(o.kernel_scale >= 1.0f) ||
-      !(o.power >= 0.0f && o.power <= 16.0f) || !(o.miss >= 0.0f) || !(o.eps > 0.0f) || !(o.border > 0.0f) ||
+      !(o.power >= 0.0f && o.power <= 16.0f) || !(o.miss >= 0.0f) || !(o.eps > 0.0f) || !(o.border >= 0.0f && o.border <= 1e6f) ||
       (o.jackknife != 0 && o.jackknife != 1) || !(o.edge_spp >= 0 && o.edge_spp <= 4096))
     return PT_ERR_ARG;
   if (!s || !r || !p || !grad_image || (!grad_t && !grad_v)) return PT_ERR_ARG;
@@ -834,12 +840,10 @@ int reparam_launch(pt_scene* s, const pt_render_desc* r, const pt_params* p, con
   if (cudaGetLastError() != cudaSuccess) return PT_ERR_CUDA;
   if (o.edge_spp > 0) {
     EdgeGrid E;
-    E.xlo = A.crop_x0 > 1 ? A.crop_x0 : 1;
-    const int xhi = A.crop_x0 + A.crop_w < A.width - 1 ? A.crop_x0 + A.crop_w : A.width - 1;
-    E.nvx = xhi >= E.xlo ? xhi - E.xlo + 1 : 0;
-    E.ylo = A.crop_y0 > 1 ? A.crop_y0 : 1;
-    const int yhi = A.crop_y0 + A.crop_h < A.height - 1 ? A.crop_y0 + A.crop_h : A.height - 1;
-    E.nhy = yhi >= E.ylo ? yhi - E.ylo + 1 : 0;
+    E.xlo = A.crop_x0;
+    E.nvx = A.crop_w + 1;
+    E.ylo = A.crop_y0;
+    E.nhy = A.crop_h + 1;
     E.per_cam = (long long)A.crop_h * E.nvx + (long long)E.nhy * A.crop_w;
     // edge ids (camera << 40 | edge << 12 | sample) need 28 bits for the edge
     if ((unsigned long long)(A.width + 1) * A.height + (unsigned long long)A.width * (A.height + 1) >= (1ull << 28))

@@ -304,14 +304,22 @@ def render(dscene: DeviceScene, st: RenderSettings, albedo, roughness, textures:
 
 class TranslateFn(torch.autograd.Function):
     """image = render of `scene` with every shape moved by translations[shape]
-    ([n_shapes, 3]); backward = reparameterized PRB (pt_render_backward_reparam,
-    Sec. 4.7), the gradient with respect to the translations through visibility.
-    The translated geometry is uploaded (scene and BVH built) on every call."""
+    ([n_shapes, 3]) and every camera by camera_offset ([3]); backward =
+    reparameterized PRB (pt_render_backward_reparam, Sec. 4.7), the gradient with
+    respect to the translations through visibility.  Moving the cameras is moving
+    every shape the opposite way (the environment lies at infinity), so the camera
+    offset's gradient is minus the sum of the shapes'.  The moved geometry is
+    uploaded (scene and BVH built) on every call."""
 
     @staticmethod
-    def forward(ctx, scene: S.Scene, st: RenderSettings, layout: int, opts: dict, translations):
-        t = translations.detach().to("cpu", torch.float64).numpy()
-        ds = DeviceScene(scene.translated(t), layout=layout, device=translations.device)
+    def forward(ctx, scene: S.Scene, st: RenderSettings, layout: int, opts: dict, translations, camera_offset):
+        ref = translations if translations is not None else camera_offset
+        sc = scene
+        if translations is not None:
+            sc = sc.translated(translations.detach().to("cpu", torch.float64).numpy())
+        if camera_offset is not None:
+            sc = sc.camera_moved(camera_offset.detach().to("cpu", torch.float64).numpy())
+        ds = DeviceScene(sc, layout=layout, device=ref.device)
         ctx.ds, ctx.st, ctx.opts = ds, st, opts
         return ds.forward(st)
 
@@ -323,13 +331,17 @@ class TranslateFn(torch.autograd.Function):
         ds.backward_reparam(st, grad_img.contiguous(), g, seed=seed, **ctx.opts)
         ds.close()  # pt_scene_destroy frees device memory, which waits for the launch
         ctx.ds = None
-        return None, None, None, None, g
+        g_cam = -g.sum(dim=0) if ctx.needs_input_grad[5] else None
+        return None, None, None, None, (g if ctx.needs_input_grad[4] else None), g_cam
 
 
-def render_translated(scene: S.Scene, st: RenderSettings, translations, layout: int = abi.PT_BVH_BINARY,
-                      **reparam_opts):
-    """Differentiable render with respect to one translation per shape."""
-    return TranslateFn.apply(scene, st, layout, reparam_opts, translations)
+def render_translated(scene: S.Scene, st: RenderSettings, translations=None, layout: int = abi.PT_BVH_BINARY,
+                      camera_offset=None, **reparam_opts):
+    """Differentiable render with respect to one translation per shape ([n_shapes,
+    3]) and / or one translation of the cameras ([3]); at least one is given."""
+    if translations is None and camera_offset is None:
+        raise ValueError("render_translated: give translations, camera_offset or both")
+    return TranslateFn.apply(scene, st, layout, reparam_opts, translations, camera_offset)
 
 
 class VerticesFn(torch.autograd.Function):

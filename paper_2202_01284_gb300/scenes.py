@@ -85,6 +85,17 @@ class Scene:
         s.vertices = np.ascontiguousarray(v, dtype=np.float32)
         return s
 
+    def camera_moved(self, offset) -> "Scene":
+        """Copy with every camera's origin and target moved by offset ([3])."""
+        import copy
+        import dataclasses
+        off = np.asarray(offset, np.float64).reshape(3)
+        s = copy.copy(self)
+        s.cameras = [dataclasses.replace(c, origin=tuple(float(x) for x in np.add(c.origin, off)),
+                                         target=tuple(float(x) for x in np.add(c.target, off)))
+                     for c in self.cameras]
+        return s
+
     def with_params(self, albedo=None, textures=None, roughness=None) -> "Scene":
         import copy
         s = copy.copy(self)

@@ -56,13 +56,15 @@ def test_reparam_parity_shadow_scene(lib, oracle_mod):
     assert rays > 64 * 64 * 16
 
 
-def test_reparam_parity_camera_rays(lib, oracle_mod):
-    """Camera-ray warps only (black occluder over a uniform sky), windowed at the border."""
-    sc = S.occluder_sky(center=(0.5, 0.2), side=0.6)   # near the right border: the window matters
+@pytest.mark.parametrize("border", [0.0, 4.0])
+def test_reparam_parity_camera_rays(lib, oracle_mod, border):
+    """Camera-ray warps only (black occluder over a uniform sky) across the right image
+    border: the flux through the image-border edges, or (option) the border window."""
+    sc = S.occluder_sky(center=(0.5, 0.2), side=0.6)
     gi = np.random.default_rng(3).random((64, 64, 3))
-    _, _, c, rel, _ = _compare(oracle_mod, sc, 16, 2, 5, gi)
+    _, _, c, rel, _ = _compare(oracle_mod, sc, 16, 2, 5, gi, border=border)
     assert c >= 0.99999
-    assert rel < 1e-4  # measured 9e-6
+    assert rel < 1e-4  # measured 9e-6 with the window
 
 
 def test_reparam_parity_cornell_multibounce(lib, oracle_mod):
@@ -86,7 +88,7 @@ def test_reparam_arguments(lib):
     gi = torch.ones((1, 16, 16, 3), device="cuda")
     g = torch.zeros((3, 3), device="cuda")
     for bad in (dict(n_aux=1), dict(n_aux=33), dict(kappa=0.0), dict(kernel_scale=0.5), dict(eps=0.0),
-                dict(miss=-1.0), dict(border=0.0), dict(jackknife=2), dict(power=-1.0), dict(edge_spp=-1),
+                dict(miss=-1.0), dict(border=-1.0), dict(jackknife=2), dict(power=-1.0), dict(edge_spp=-1),
                 dict(edge_spp=4097)):
         with pytest.raises(lib.PtError):
             ds.backward_reparam(st, gi, g, **bad)
@@ -116,7 +118,7 @@ def test_reparam_pixel_edge_term_parity(lib, oracle_mod):
         st = RenderSettings(width=40, height=40, spp=4, max_depth=2, rr_depth=-1, seed=31, crop=crop)
         r = oracle_mod.render_in(cam, 4, 2, 31, -1, True, crop=crop)
         gim = torch.as_tensor(gi[None], dtype=torch.float32, device="cuda")
-        n_edges = 39 * 40 * 2 if crop is None else 28 * 22 + 23 * 27
+        n_edges = 41 * 40 * 2 if crop is None else 28 * 22 + 23 * 27
         for vertex in (False, True):
             got, ref, n_rays = [], [], []
             for edge_spp in (0, 8):
@@ -375,3 +377,43 @@ def test_reparam_recovers_square_scale_with_a_sharp_loss(lib):
         opt.step()
     print("recovered scale (sharp loss)", s.item(), "truth", true_s)
     assert abs(s.item() - true_s) < 0.03
+
+
+def test_reparam_camera_translation(lib, oracle_mod):
+    """render_translated with a camera offset: its gradient is minus the sum of all
+    shapes' translation gradients (parity with the oracle's), and gradient descent on
+    the offset recovers a moved camera from its image alone.  Everything in view
+    slides when the camera moves, so this leans on the flux through the image-border
+    edges of the pixel-edge term."""
+    from paper_2202_01284_gb300.render import RenderSettings, render_translated
+    sc = S.shadow_scene(width=48, height=48)
+    st = RenderSettings(width=48, height=48, spp=8, max_depth=3, rr_depth=-1, seed=21)
+    gi = np.random.default_rng(9).random((48, 48, 3))
+    off = torch.zeros(3, device="cuda", requires_grad=True)
+    img = render_translated(sc, st, camera_offset=off)
+    (img * torch.as_tensor(gi[None], dtype=torch.float32, device="cuda")).sum().backward()
+    r = oracle_mod.render_in(sc.cameras[0], 8, 3, 21, -1, True)
+    g_ref = -oracle_mod.grad_reparam(oracle_mod.OracleScene(sc), r, gi)[0].sum(axis=0)
+    got = off.grad.cpu().numpy().astype(np.float64)
+    rel = np.abs(got - g_ref).max() / np.abs(g_ref).max()
+    print("camera offset gradient", got, "oracle", g_ref, "max rel", rel)
+    assert rel < 1e-3
+
+    truth = np.array([-0.08, 0.06, 0.1])
+    tsc = sc.camera_moved(truth)
+    from paper_2202_01284_gb300.render import DeviceScene
+    target = DeviceScene(tsc).forward(RenderSettings(width=48, height=48, spp=256, max_depth=2, seed=99))
+    off = torch.zeros(3, device="cuda", requires_grad=True)
+    opt = torch.optim.Adam([off], lr=0.01)
+    for k in range(60):
+        if k == 40:
+            for grp in opt.param_groups:
+                grp["lr"] = 0.003
+        st = RenderSettings(width=48, height=48, spp=16, max_depth=2, seed=1000 + k, backward_seed=5000 + k)
+        opt.zero_grad()
+        loss = ((render_translated(sc, st, camera_offset=off, edge_spp=4) - target) ** 2).mean()
+        loss.backward()
+        opt.step()
+    err = off.detach().cpu().numpy() - truth
+    print("recovered camera offset", off.detach().cpu().numpy(), "truth", truth, "loss", loss.item())
+    assert np.abs(err).max() < 0.025   # started 0.1 away
