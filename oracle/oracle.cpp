@@ -1679,7 +1679,8 @@ struct ReparamAcc {
 // ---------------------------------------------------------------- parallel driver
 // A path through a pixel edge: only its camera ray's warp is needed (the radiance
 // it carries enters the edge term as a value, not differentiated).  The warp is
-// the windowed camera-ray warp of ReparamAcc, from the same auxiliary stream rule.
+// the camera-ray warp of ReparamAcc (windowed or not), from the same auxiliary
+// stream rule.
 struct EdgeAcc : NullAcc {
   const Scene* s = nullptr;
   const ReparamOpts* op = nullptr;
