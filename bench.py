@@ -862,13 +862,14 @@ def run_reparam_experiment(args):
                        "grad_translation_norm": float(g_t.norm().item())},
             "roofline": {"bound": "alu", "kernel": "reparam_kernel", "achieved": round(achieved, 3),
                          "peak": round(peak_tflops, 2), "unit": "TFLOP/s", "frac": round(achieved / peak_tflops, 4),
-                         "traffic": None,
+                         "traffic": (DRAM_TRAFFIC_PER_LAUNCH.get(args.bvh, {}).get("reparam_kernel")
+                                     if not args.small else None),
                          "work": f"{FLOPS_PER_NODE[args.bvh]}/node visit + {FLOPS_PER_TRI}/triangle test (counted "
                                  "by instrumented launches of the replay, the pixel-edge paths and the radiance "
                                  "pass; warp-field arithmetic not counted); time = radiance pass + reparam_kernel "
                                  "+ edge_kernel",
                          "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 x median SM clock {mhz} MHz"},
-            "gpu_launches": 2 * args.steps,
+            "gpu_launches": (4 if opts.edge_spp > 0 else 3) * args.steps,  # forward, radiance pass, replay, edges
             "clocks": clk}
     print(json.dumps(line), flush=True)
 
