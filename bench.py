@@ -54,13 +54,16 @@ def alu_roofline(kernel, counters, bvh, ms, clk, note=""):
             "work": f"{FLOPS_PER_NODE[bvh]}/node visit + {FLOPS_PER_TRI}/triangle test (counted launch){note}",
             "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 x median SM clock {mhz} MHz"}
 # DRAM bytes (read + write) per full-size launch of the production kernels, from one
-# one-pass ncu capture of this step (profiles/launches_spheres196k_1024px_64spp.md);
+# one-pass ncu capture of the step (profiles/launches_spheres196k_1024px_64spp.md,
+# profiles/reparam_launches_spheres196k_1024px_16spp.md);
 # cleared whenever the kernels change until they are captured again.
-DRAM_TRAFFIC_PER_LAUNCH = {"wide": {"forward_kernel": 2_960_000_000 + 14_310_000_000,
+DRAM_TRAFFIC_PER_LAUNCH = {"wide": {"forward_kernel": 2_960_000_000 + 14_300_000_000,
                                     "replay_kernel": 2_030_000_000 + 4_620_000_000,
-                                    "radiance_kernel": 4_030_000_000 + 15_990_000_000,
+                                    "radiance_kernel": 4_190_000_000 + 16_060_000_000,
                                     "adjoint_kernel": 1_775_000_000 + 11_908_000_000,
-                                    "jvp_kernel": 1_325_000_000 + 7_153_000_000}}
+                                    "jvp_kernel": 1_325_000_000 + 7_153_000_000,
+                                    # bench.py --reparam (1024^2, 16 spp; profiles/reparam_launches_...)
+                                    "reparam_kernel": 12_440_000_000 + 23_310_000_000}}
 
 
 def parse():
