@@ -417,3 +417,50 @@ def test_reparam_camera_translation(lib, oracle_mod):
     err = off.detach().cpu().numpy() - truth
     print("recovered camera offset", off.detach().cpu().numpy(), "truth", truth, "loss", loss.item())
     assert np.abs(err).max() < 0.025   # started 0.1 away
+
+
+@pytest.mark.parametrize("n_aux", [2, 5, 32])
+def test_reparam_auxiliary_group_sizes(lib, oracle_mod, n_aux):
+    """Lobes of 2, 5 (groups of 8 lanes with 3 idle) and 32 auxiliary rays (one
+    lobe per warp round), jackknife on, vertex mode too."""
+    sc = S.shadow_scene(width=32, height=32)
+    gi = np.random.default_rng(12).random((32, 32, 3)) + 0.1
+    _, _, c, rel, _ = _compare(oracle_mod, sc, 4, 3, 41, gi, n_aux=n_aux)
+    assert c >= 0.99999 and rel < 1e-3
+    c, rel, srel = _compare_vertices(oracle_mod, sc, 4, 3, 41, gi, n_aux=n_aux)
+    assert c >= 0.9999 and rel < 5e-3 and srel < 1e-4
+
+
+def test_reparam_crops_on_the_image_border(lib, oracle_mod):
+    """Ragged crops that touch the image's corners: their outer edges lie on the image
+    border (flux through it), their inner edges count for the inside pixel only; the
+    four crops' gradients sum to the whole image's."""
+    from paper_2202_01284_gb300.render import DeviceScene, RenderSettings
+    sc = S.shadow_scene(width=40, height=30)
+    ds = DeviceScene(sc, layout=0)
+    osc = oracle_mod.OracleScene(sc)
+    gi_full = np.random.default_rng(13).random((30, 40, 3)) - 0.3
+    crops = [(0, 0, 17, 13), (17, 0, 23, 13), (0, 13, 17, 17), (17, 13, 23, 17)]
+    g_sum = np.zeros((3, 3))
+    for crop in crops:
+        x0, y0, w, h = crop
+        gi = np.ascontiguousarray(gi_full[y0:y0 + h, x0:x0 + w])
+        st = RenderSettings(width=40, height=30, spp=4, max_depth=3, rr_depth=-1, seed=23, crop=crop)
+        g = torch.zeros((3, 3), device="cuda")
+        ds.backward_reparam(st, torch.as_tensor(gi[None], dtype=torch.float32, device="cuda"), g, edge_spp=2)
+        torch.cuda.synchronize()
+        assert ds.status() == 0
+        r = oracle_mod.render_in(sc.cameras[0], 4, 3, 23, -1, True, crop=crop)
+        ref = oracle_mod.grad_reparam(osc, r, gi, edge_spp=2)[0]
+        gg = g.cpu().numpy().astype(np.float64)
+        rel = np.abs(gg - ref).max() / np.abs(ref).max()
+        print("crop", crop, "max rel", rel)
+        assert rel < 1e-3
+        g_sum += gg
+    st = RenderSettings(width=40, height=30, spp=4, max_depth=3, rr_depth=-1, seed=23)
+    g = torch.zeros((3, 3), device="cuda")
+    ds.backward_reparam(st, torch.as_tensor(gi_full[None], dtype=torch.float32, device="cuda"), g, edge_spp=2)
+    torch.cuda.synchronize()
+    whole = g.cpu().numpy().astype(np.float64)
+    print("sum of the crops", g_sum.ravel(), "whole image", whole.ravel())
+    assert np.abs(g_sum - whole).max() < 1e-4 * np.abs(whole).max()
