@@ -471,6 +471,25 @@ int pt_render_backward_reparam_vertices(pt_scene* scene, const pt_render_desc* d
                                         const pt_reparam_opts* opts, const float* grad_image, float* grad_vertices,
                                         unsigned long long* rays, void* stream);
 
+/* Forward mode of the same estimator (the paper's forward derivative of a
+ * translated mesh, Sec. 4.7, Fig. "bunny": without reparameterization the
+ * silhouettes' and reflections' derivatives are missing): image_dot = d image /
+ * d eps of the render with every shape s moved by eps * dir_translation[s], in one
+ * pass without a radiance pass.  Each reparameterized ray's warp returns its
+ * tangential value V and div V for the direction; the path carries the per-channel
+ * derivative of its log throughput, and the pixel-edge term's edge paths add
+ * their flux to the two pixels of their edge.  With the same seed, sum(grad_image *
+ * image_dot) equals <dir_translation, gradient of pt_render_backward_reparam> up
+ * to float rounding (the same estimator in the other mode).  dir_translation:
+ * device float [n_shapes][3]; image (NULL: not wanted) and image_dot: device float
+ * [n_cams][crop_h][crop_w][3], overwritten (zeroed on the stream, then
+ * accumulated).  rays: as pt_render_backward_reparam (path, shadow, auxiliary,
+ * center and edge rays).  desc: as pt_render_backward_reparam, no counters.
+ * Errors: as pt_render_backward_reparam. */
+int pt_render_jvp_reparam(pt_scene* scene, const pt_render_desc* desc, const pt_params* params,
+                          const pt_reparam_opts* opts, const float* dir_translation, float* image, float* image_dot,
+                          unsigned long long* rays, void* stream);
+
 /* Reads (and clears) the scene's device status word after synchronising
  * `stream`: *out = PT_OK or the first PT_ERR_* a kernel recorded. */
 int pt_last_device_status(pt_scene* scene, void* stream, int* out);

@@ -766,6 +766,400 @@ __global__ void __launch_bounds__(128, 8) edge_kernel(const __grid_constant__ La
   flush_counters<INSTR>(A, cnt);
 }
 
+// ---------------------------------------------------------------- forward mode
+// Forward-mode derivative images along a direction of shape translations (the
+// paper's forward derivative of a translated mesh, Fig. "bunny": without the
+// reparameterization the silhouettes' derivative is missing).  Every ray is
+// reparameterized as in the reverse mode; a posted ray gets back its warp's
+// tangential value V at u (windowed for camera rays) and div V, both linear in
+// the direction's relative velocities Delta_i = dir[shape_i] - dir[shape_o]:
+//     V = (I - u u^T) sum_i alpha_i b sv_i J Delta_i,  J = 1/D (jackknife:
+//         N/D - (N-1)/N (S1 - 1/D_-i)),
+//     div V = sum_i c_i . Delta_i, c_i the reverse mode's coefficient for M = 0,
+//         R = 1.
+// The path carries r = d(beta)/beta per channel (derivative of the log
+// throughput): a camera ray starts it at m.V + div V (m = -3 f / f.u); a term
+// C leaving a vertex along d adds its ray's m.V + div V with m = n / n.d, plus at a
+// glossy vertex grad_out log f_c . V + grad_in log f_c . (-V_arriving); emitted
+// radiance c adds r (.) c, a light sample c_nee adds (r + its term) (.) c_nee, the
+// sampled continuation adds its term to r.
+
+// Warps of the rays the lanes posted (called by all lanes together, as
+// process_warps): the lane that posted a ray receives V (tangential) and div V.
+template <int LAYOUT>
+__device__ __noinline__ unsigned warp_forward(const LaunchArgs& A, const RpOpts& K, bool has, const WarpRay& mine,
+                                              const float* __restrict__ dir_t, float3& V_out, float& div_out,
+                                              Counters<false>& cnt) {
+  const DevScene& S = A.scene;
+  const int lane = lane_id(), gs = K.group, grp = lane / gs, j = lane % gs;
+  const int ng = 32 / gs;
+  const float dk = K.kk - K.kappa, n = (float)K.n_aux;
+  unsigned rays = 0;
+  V_out = f3(0.f, 0.f, 0.f);
+  div_out = 0.0f;
+  unsigned pend = __ballot_sync(kFull, has);
+  while (pend) {
+    unsigned p = pend;
+    for (int g = 0; g < grp && p; ++g) p &= p - 1;
+    const int src = p ? __ffs(p) - 1 : -1;
+    // this lane's own ray is served this round by group `rank` if it is among the first ng pending
+    const int rank = __popc(pend & ((1u << lane) - 1u));
+    const bool served = ((pend >> lane) & 1u) && rank < ng;
+    for (int g = 0; g < ng && pend; ++g) pend &= pend - 1;
+    const int sl = src >= 0 ? src : lane;
+    WarpRay w;
+    w.o = shfl3(mine.o, sl);
+    w.u = shfl3(mine.u, sl);
+    w.s_o = __shfl_sync(kFull, mine.s_o, sl);
+    w.cam = __shfl_sync(kFull, mine.cam, sl);
+    w.t0 = __shfl_sync(kFull, mine.t0, sl);
+    w.st = __shfl_sync(kFull, mine.st, sl);
+    w.inc = __shfl_sync(kFull, mine.inc, sl);
+    const bool on = src >= 0 && j < K.n_aux;
+    float alpha = 0.0f, t = 0.0f;
+    int pos = -1;
+    float3 wi = w.u, pi = f3(0.f, 0.f, 0.f);
+    if (on) {
+      Pcg32 r;
+      r.state = w.st;
+      r.inc = w.inc;
+      pcg_advance(r, 2ull * (unsigned long long)j);
+      const float a0 = r.uniform(), a1 = r.uniform();
+      float c1;
+      wi = vmf_dir(make_frame(w.u), a0, a1, K, c1);
+      const Hit h = closest<LAYOUT, false>(S, w.o, wi, INFINITY, false, cnt);
+      ++rays;
+      float g = K.miss;
+      if (h.pos >= 0) g = w.t0 < INFINITY ? powf(w.t0 / fmaxf(h.t, 1e-3f * w.t0), K.power) : 1.0f;
+      alpha = expf(dk * c1) * g;
+      pos = h.pos;
+      t = h.t;
+      pi = wi - w.u * dot3(w.u, wi);
+    }
+    const float D = group_sum(alpha, gs) + n * K.eps;
+    const float3 P = group_sum3(pi * alpha, gs);
+    float S1 = 0.0f;
+    float3 SP = f3(0.f, 0.f, 0.f);
+    if (K.jackknife) {
+      const float Dj = D - alpha - K.eps;
+      const float3 Pj = P - pi * alpha;
+      S1 = group_sum(on ? 1.0f / Dj : 0.0f, gs);
+      SP = group_sum3(on ? Pj * (1.0f / (Dj * Dj)) : f3(0.f, 0.f, 0.f), gs);
+    }
+    float3 vs = f3(0.f, 0.f, 0.f);
+    float dv = 0.0f;
+    int si = -1;
+    if (on && pos >= 0) si = tri_shape(S, pos);
+    if (si >= 0 && si != w.s_o) {
+      const float3 vi = f3(__ldg(&dir_t[3 * si]), __ldg(&dir_t[3 * si + 1]), __ldg(&dir_t[3 * si + 2]));
+      const float3 vo = w.s_o >= 0 ? f3(__ldg(&dir_t[3 * w.s_o]), __ldg(&dir_t[3 * w.s_o + 1]),
+                                        __ldg(&dir_t[3 * w.s_o + 2]))
+                                   : f3(0.f, 0.f, 0.f);
+      const float3 delta = vi - vo;
+      float b = 1.0f;
+      float3 gb = f3(0.f, 0.f, 0.f);
+      if (w.cam >= 0) b = cam_window(A, A.cams[w.cam], w.u, K.border, gb);
+      const float3 nrm = tri_normal(S, pos);
+      const float di = dot3(nrm, wi) * t;
+      const float sv = dot3(nrm, w.u) / di;
+      const float3 g = (nrm - w.u * dot3(nrm, w.u)) * (1.0f / di);
+      float Dm = 0.0f;
+      float3 Pm = f3(0.f, 0.f, 0.f);
+      if (K.jackknife) {
+        Dm = D - alpha - K.eps;
+        Pm = P - pi * alpha;
+      }
+      const float Jm = K.jackknife ? n / D - (n - 1.0f) / n * (S1 - 1.0f / Dm) : 1.0f / D;
+      vs = delta * (alpha * b * sv * Jm);
+      // div part: the reverse coefficient with M = 0, R = 1
+      const float3 Ai = (pi * K.kk - w.u * 2.0f) * (b * sv) + g * b + gb * sv;
+      const float kb = K.kk * b * sv;
+      float3 c = Ai * (1.0f / D) - P * (kb / (D * D));
+      if (K.jackknife) {
+        const float3 loo = Ai * (S1 - 1.0f / Dm) - (SP - Pm * (1.0f / (Dm * Dm))) * kb;
+        c = c * n - loo * ((n - 1.0f) / n);
+      }
+      dv = dot3(c * alpha, delta);
+    }
+    vs = group_sum3(vs, gs);
+    dv = group_sum(dv, gs);
+    const int server = (rank < ng ? rank : 0) * gs;
+    const float3 vr = shfl3(vs, server);
+    const float dr = __shfl_sync(kFull, dv, server);
+    if (served) {
+      V_out = vr - mine.u * dot3(mine.u, vr);
+      div_out = dr;
+    }
+  }
+  return rays;
+}
+
+// Per-channel log-derivative of a term leaving a vertex along d: its ray's m.V +
+// div V, plus at a glossy vertex the BSDF's directional terms (V of this ray,
+// -V of the ray that arrived).
+__device__ __forceinline__ float3 fwd_term(float3 n_s, float3 d, float3 V, float dvg, bool glossy, const Gloss& gl,
+                                           const Frame& fr, float3 wi_l, float3 v_prev) {
+  const float l = dot3(n_s, V) / dot3(n_s, d) + dvg;
+  float3 t = f3(l, l, l);
+  if (glossy) {
+    float3 go[3], gi[3];
+    glossy_log_grad(gl.type, gl.alpha, gl.f0, gl.wd, gl.albedo, wi_l, fr.to_local(d), go, gi);
+    t.x += dot3(fr.to_world(go[0]), V) - dot3(fr.to_world(gi[0]), v_prev);
+    t.y += dot3(fr.to_world(go[1]), V) - dot3(fr.to_world(gi[1]), v_prev);
+    t.z += dot3(fr.to_world(go[2]), V) - dot3(fr.to_world(gi[2]), v_prev);
+  }
+  return t;
+}
+
+// One thread per (pixel, lane) as the reverse kernel; samples in lockstep, the
+// warps processed together after each vertex.  image / image_dot accumulate (the
+// caller zeroes them): the mean over the pixel's samples.
+template <int LAYOUT>
+__global__ void __launch_bounds__(128, 8) reparam_jvp_kernel(const __grid_constant__ LaunchArgs A, const RpOpts K,
+                                                          const float* __restrict__ dir_t, float* __restrict__ image,
+                                                          float* __restrict__ image_dot,
+                                                          unsigned long long* rays_out) {
+  const DevScene& S = A.scene;
+  const long long unit = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  PixelOf px{};
+  const bool valid = unit_pixel(A, unit, crop_tile(A), px);
+  unsigned rays = 0;
+  Counters<false> cnt;
+  const float3 z = f3(0.f, 0.f, 0.f);
+  float3 fwd = z;
+  if (valid) {
+    const DevCamera& cam = A.cams[px.cam];
+    fwd = f3(cam.fx, cam.fy, cam.fz);
+  }
+  bool live = false;
+  int si = (int)(unit & (A.lanes_per_pixel - 1));
+  GradSink sink;
+  PathState P;
+  Pcg32 aux;
+  aux.state = aux.inc = 0ull;
+  bool cached = false;
+  Hit next{};
+  float3 r = z, v_prev = z, ldot = z, sum_L = z, sum_dot = z;
+  const unsigned long long n2 = 2ull * (unsigned long long)K.n_aux;
+  for (;;) {
+    WarpRay w0{}, w1{};
+    bool h0 = false, h1 = false, start = false, done = false, glossy = false;
+    float3 n_s = z, c_nee = z, wi_l = z;
+    Gloss gl{};
+    Frame fr{};
+    if (!live && valid && si < A.spp) {
+      path_start<false>(A, P, A.seed, px.cam, px.px, px.py, si, px.pix, cnt);
+      const unsigned long long pixel = (unsigned long long)px.py * (unsigned long long)A.width + px.px;
+      aux.seed(A.seed, ((unsigned long long)px.cam << 40) | (pixel << 12) | (unsigned long long)si | (1ull << 62));
+      next = closest<LAYOUT, false>(S, P.ro, P.rd, INFINITY, false, cnt);
+      ++rays;
+      cached = true;
+      w0 = WarpRay{P.ro, P.rd, fwd * (-3.0f / dot3(fwd, P.rd)), -1, px.cam, 0.0f,
+                   next.pos >= 0 ? next.t : INFINITY, aux.state, aux.inc, -1, 0.0f, 0.0f};
+      h0 = true;
+      start = true;
+      pcg_advance(aux, n2);
+      live = true;
+    } else if (live) {
+      Hit hit;
+      if (cached) {
+        hit = next;
+        cached = false;
+      } else {
+        hit = closest<LAYOUT, false>(S, P.ro, P.rd, INFINITY, false, cnt);
+        ++rays;
+      }
+      const bool block = hit.pos >= 0 && P.depth < A.max_depth;
+      int s_o = -1;
+      const float3 wi_w = -P.rd;
+      if (hit.pos >= 0) {
+        s_o = tri_shape(S, hit.pos);
+        const float3 ng = tri_normal(S, hit.pos);
+        n_s = dot3(ng, P.rd) < 0.0f ? ng : -ng;
+      }
+      float3 L0 = P.L;
+      bool more = path_shade<false, false, false, PT_DISPATCH_SWITCH>(A, P, hit, false, z, sink, cnt);
+      ldot = ldot + r * (P.L - L0);  // emission reaching this vertex
+      Pcg32 aux_nee = aux, aux_bsdf = aux;
+      if (block) {
+        pcg_advance(aux_bsdf, n2);
+        pcg_advance(aux, 2ull * n2);
+      }
+      if (more) {
+        bool occ = false;
+        if (P.has_shadow) {
+          occ = closest<LAYOUT, false>(S, P.so, P.sd, P.stmax, true, cnt).pos >= 0;
+          ++rays;
+        }
+        const int mt = P.mtype;
+        const bool warp = block && (mt == PT_BSDF_DIFFUSE || mt == PT_BSDF_CONDUCTOR || mt == PT_BSDF_BLEND);
+        glossy = warp && mt != PT_BSDF_DIFFUSE;
+        if (glossy) {
+          gl = gloss_at(A, hit);
+          fr = make_frame(n_s);
+          wi_l = fr.to_local(wi_w);
+        }
+        if (warp && P.has_shadow && !occ) {
+          const Hit hl = closest<LAYOUT, false>(S, P.so, P.sd, INFINITY, false, cnt);
+          ++rays;
+          c_nee = P.c_nee;
+          w0 = WarpRay{P.so, P.sd, z, s_o, -1, 0.0f, hl.pos >= 0 ? hl.t : INFINITY, aux_nee.state, aux_nee.inc,
+                       -1, 0.0f, 0.0f};
+          h0 = true;
+        }
+        L0 = P.L;
+        more = path_finish<false, false, false>(A, P, occ, false, z, sink, cnt);
+        ldot = ldot + r * (P.L - L0);  // the light sample, with the path's tangent so far
+        if (more && warp) {
+          next = closest<LAYOUT, false>(S, P.ro, P.rd, INFINITY, false, cnt);
+          ++rays;
+          cached = true;
+          w1 = WarpRay{P.ro, P.rd, z, s_o, -1, 0.0f, next.pos >= 0 ? next.t : INFINITY, aux_bsdf.state,
+                       aux_bsdf.inc, -1, 0.0f, 0.0f};
+          h1 = true;
+        }
+      }
+      if (!more) done = true;
+    }
+    if (!__any_sync(kFull, live || h0 || h1 || (valid && si < A.spp))) break;
+    float3 V0, V1;
+    float d0, d1;
+    rays += warp_forward<LAYOUT>(A, K, h0, w0, dir_t, V0, d0, cnt);
+    rays += warp_forward<LAYOUT>(A, K, h1, w1, dir_t, V1, d1, cnt);
+    if (start) {
+      const float l = dot3(w0.m, V0) + d0;  // m: the pinhole's image-plane density term
+      r = f3(l, l, l);
+      v_prev = V0;
+    } else if (live) {
+      if (h0) ldot = ldot + c_nee * fwd_term(n_s, w0.u, V0, d0, glossy, gl, fr, wi_l, v_prev);
+      if (h1) {
+        r = r + fwd_term(n_s, w1.u, V1, d1, glossy, gl, fr, wi_l, v_prev);
+        v_prev = V1;
+      } else {
+        v_prev = z;  // a delta vertex: its continuation is not reparameterized
+      }
+      if (done) {
+        sum_L = sum_L + P.L;
+        sum_dot = sum_dot + ldot;
+        ldot = r = v_prev = z;
+        live = false;
+        si += A.lanes_per_pixel;
+      }
+    }
+  }
+  if (valid) {
+    const float inv = 1.0f / (float)A.spp;
+    if (image) {
+      atomicAdd(&image[3 * px.pix], sum_L.x * inv);
+      atomicAdd(&image[3 * px.pix + 1], sum_L.y * inv);
+      atomicAdd(&image[3 * px.pix + 2], sum_L.z * inv);
+    }
+    atomicAdd(&image_dot[3 * px.pix], sum_dot.x * inv);
+    atomicAdd(&image_dot[3 * px.pix + 1], sum_dot.y * inv);
+    atomicAdd(&image_dot[3 * px.pix + 2], sum_dot.z * inv);
+  }
+  if (rays_out) {
+    unsigned long long rr = rays;
+    for (int off = 16; off > 0; off >>= 1) rr += __shfl_xor_sync(kFull, rr, off);
+    if (lane_id() == 0 && rr) atomicAdd(rays_out, rr);
+  }
+}
+
+// Forward mode of the pixel-edge term: per (edge, sample) the path's radiance L and
+// its camera warp's velocity across the edge v_e; the pixel left of / above the
+// edge loses L v_e / edge_spp, the one right of / below it gains it (pixels of the
+// crop only).
+template <int LAYOUT>
+__global__ void __launch_bounds__(128, 8) edge_jvp_kernel(const __grid_constant__ LaunchArgs A, const RpOpts K,
+                                                       const EdgeGrid E, const float* __restrict__ dir_t,
+                                                       float* __restrict__ image_dot,
+                                                       unsigned long long* rays_out) {
+  const DevScene& S = A.scene;
+  Counters<false> cnt;
+  const float3 z = f3(0.f, 0.f, 0.f);
+  const long long unit = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  unsigned rays = 0;
+  WarpRay w{};
+  bool has = false, vertical = false;
+  int X = 0, Y = 0, ci = 0;
+  float3 L = z;
+  if (unit < (long long)A.n_cams * E.per_cam * K.edge_spp) {
+    const int k = (int)(unit % K.edge_spp);
+    const long long ea = unit / K.edge_spp;
+    ci = (int)(ea / E.per_cam);
+    long long e = ea - (long long)ci * E.per_cam;
+    const long long nv = (long long)A.crop_h * E.nvx;
+    vertical = e < nv;
+    unsigned long long id;
+    if (vertical) {
+      Y = A.crop_y0 + (int)(e / E.nvx);
+      X = E.xlo + (int)(e % E.nvx);
+      id = (unsigned long long)Y * (unsigned long long)(A.width + 1) + (unsigned long long)X;
+    } else {
+      e -= nv;
+      Y = E.ylo + (int)(e / A.crop_w);
+      X = A.crop_x0 + (int)(e % A.crop_w);
+      id = (unsigned long long)(A.width + 1) * (unsigned long long)A.height +
+           (unsigned long long)Y * (unsigned long long)A.width + (unsigned long long)X;
+    }
+    const unsigned long long stream = ((unsigned long long)ci << 40) | (id << 12) | (unsigned long long)k | (1ull << 61);
+    PathState P;
+    P.slot = 0;
+    P.cache_done = false;
+    P.rng.seed(A.seed, stream);
+    P.fh.h = 2166136261u;
+    const float j0 = P.rng.uniform();
+    P.rng.uniform();
+    path_start_at<false>(A, P, ci, vertical ? (float)X : (float)X + j0, vertical ? (float)Y + j0 : (float)Y, cnt);
+    const float3 o = P.ro, u = P.rd;
+    float t0 = INFINITY;
+    GradSink sink;
+    for (bool first = true;; first = false) {
+      const Hit hit = closest<LAYOUT, false>(S, P.ro, P.rd, INFINITY, false, cnt);
+      ++rays;
+      if (first && hit.pos >= 0) t0 = hit.t;
+      if (!path_shade<false, false, false, PT_DISPATCH_SWITCH>(A, P, hit, false, z, sink, cnt)) break;
+      bool occ = false;
+      if (P.has_shadow) {
+        occ = closest<LAYOUT, false>(S, P.so, P.sd, P.stmax, true, cnt).pos >= 0;
+        ++rays;
+      }
+      if (!path_finish<false, false, false>(A, P, occ, false, z, sink, cnt)) break;
+    }
+    L = P.L;
+    if (L.x != 0.0f || L.y != 0.0f || L.z != 0.0f) {
+      Pcg32 aux;
+      aux.seed(A.seed, stream | (1ull << 62));
+      w = WarpRay{o, u, z, -1, ci, 0.0f, t0, aux.state, aux.inc, -1, 0.0f, 0.0f};
+      has = true;
+    }
+  }
+  float3 V;
+  float dv;
+  rays += warp_forward<LAYOUT>(A, K, has, w, dir_t, V, dv, cnt);
+  if (has) {
+    float pxc, pyc;
+    float3 gpx, gpy;
+    pixel_coords(A, A.cams[ci], w.u, pxc, pyc, gpx, gpy);
+    const float3 d = L * (dot3(vertical ? gpx : gpy, V) / (float)K.edge_spp);
+    const int xa = vertical ? X - 1 : X, ya = vertical ? Y : Y - 1;
+    auto add = [&](int x, int y, float3 v) {
+      if (x < A.crop_x0 || x >= A.crop_x0 + A.crop_w || y < A.crop_y0 || y >= A.crop_y0 + A.crop_h) return;
+      const long long pix = ((long long)ci * A.crop_h + (y - A.crop_y0)) * A.crop_w + (x - A.crop_x0);
+      atomicAdd(&image_dot[3 * pix], v.x);
+      atomicAdd(&image_dot[3 * pix + 1], v.y);
+      atomicAdd(&image_dot[3 * pix + 2], v.z);
+    };
+    add(xa, ya, -d);
+    add(X, Y, d);
+  }
+  if (rays_out) {
+    unsigned long long rr = rays;
+    for (int off = 16; off > 0; off >>= 1) rr += __shfl_xor_sync(kFull, rr, off);
+    if (lane_id() == 0 && rr) atomicAdd(rays_out, rr);
+  }
+}
+
 }  // namespace
 }  // namespace ptgb
 
@@ -785,22 +1179,16 @@ extern "C" void pt_reparam_defaults(pt_reparam_opts* o) {
 }
 
 namespace {
-int reparam_launch(pt_scene* s, const pt_render_desc* r, const pt_params* p, const pt_reparam_opts* opts,
-                   const float* grad_image, float* grad_t, float* grad_v, unsigned long long* rays, void* stream) {
+// Options (NULL: defaults) checked and converted to the kernels' form.
+int rp_opts(const pt_reparam_opts* opts, RpOpts& K) {
   pt_reparam_opts o;
   pt_reparam_defaults(&o);
   if (opts) o = *opts;
   if (!(o.n_aux >= 2 && o.n_aux <= kMaxAux) || !(o.kappa > 0.0f && o.kappa <= 1e6f) || !(o.kernel_scale >= 1.0f) ||
-      !(o.power >= 0.0f && o.power <= 16.0f) || !(o.miss >= 0.0f) || !(o.eps > 0.0f) || !(o.border >= 0.0f && o.border <= 1e6f) ||
-      (o.jackknife != 0 && o.jackknife != 1) || !(o.edge_spp >= 0 && o.edge_spp <= 4096))
+      !(o.power >= 0.0f && o.power <= 16.0f) || !(o.miss >= 0.0f) || !(o.eps > 0.0f) ||
+      !(o.border >= 0.0f && o.border <= 1e6f) || (o.jackknife != 0 && o.jackknife != 1) ||
+      !(o.edge_spp >= 0 && o.edge_spp <= 4096))
     return PT_ERR_ARG;
-  if (!s || !r || !p || !grad_image || (!grad_t && !grad_v)) return PT_ERR_ARG;
-  LaunchArgs A;
-  int st = fill_launch(s, r, p, A);
-  if (st != PT_OK) return st;
-  if (r->cache || r->dbg_sample_L || r->dbg_sample_hash) return PT_ERR_ARG;
-  A.grad_image = grad_image;
-  RpOpts K;
   K.n_aux = o.n_aux;
   K.jackknife = o.jackknife;
   K.kappa = o.kappa;
@@ -813,6 +1201,35 @@ int reparam_launch(pt_scene* s, const pt_render_desc* r, const pt_params* p, con
   K.e2k = expf(-2.0f * o.kappa);
   K.group = 2;
   while (K.group < o.n_aux) K.group *= 2;
+  K.smem = 0;
+  return PT_OK;
+}
+
+// The pixel-edge term's edges (all edges of the crop's pixels); PT_ERR_ARG if the
+// edge ids do not fit their 28 bits.
+int edge_grid(const LaunchArgs& A, EdgeGrid& E) {
+  E.xlo = A.crop_x0;
+  E.nvx = A.crop_w + 1;
+  E.ylo = A.crop_y0;
+  E.nhy = A.crop_h + 1;
+  E.per_cam = (long long)A.crop_h * E.nvx + (long long)E.nhy * A.crop_w;
+  if ((unsigned long long)(A.width + 1) * A.height + (unsigned long long)A.width * (A.height + 1) >= (1ull << 28))
+    return PT_ERR_ARG;
+  return PT_OK;
+}
+
+int reparam_launch(pt_scene* s, const pt_render_desc* r, const pt_params* p, const pt_reparam_opts* opts,
+                   const float* grad_image, float* grad_t, float* grad_v, unsigned long long* rays, void* stream) {
+  RpOpts K;
+  if (rp_opts(opts, K) != PT_OK) return PT_ERR_ARG;
+  if (!s || !r || !p || !grad_image || (!grad_t && !grad_v)) return PT_ERR_ARG;
+  LaunchArgs A;
+  int st = fill_launch(s, r, p, A);
+  if (st != PT_OK) return st;
+  if (r->cache || r->dbg_sample_L || r->dbg_sample_hash) return PT_ERR_ARG;
+  A.grad_image = grad_image;
+  EdgeGrid E;
+  if (K.edge_spp > 0 && edge_grid(A, E) != PT_OK) return PT_ERR_ARG;
   const bool vert = grad_v != nullptr;
   const size_t smem = (size_t)s->n_shapes * 3 * sizeof(float);
   K.smem = (!vert && smem <= 32768) ? 1 : 0;
@@ -838,17 +1255,8 @@ int reparam_launch(pt_scene* s, const pt_render_desc* r, const pt_params* p, con
     default: reparam_kernel<PT_BVH_WIDE, true, true><<<gd, bd, sm, cs>>>(A, K, grad_t, grad_v, rays); break;
   }
   if (cudaGetLastError() != cudaSuccess) return PT_ERR_CUDA;
-  if (o.edge_spp > 0) {
-    EdgeGrid E;
-    E.xlo = A.crop_x0;
-    E.nvx = A.crop_w + 1;
-    E.ylo = A.crop_y0;
-    E.nhy = A.crop_h + 1;
-    E.per_cam = (long long)A.crop_h * E.nvx + (long long)E.nhy * A.crop_w;
-    // edge ids (camera << 40 | edge << 12 | sample) need 28 bits for the edge
-    if ((unsigned long long)(A.width + 1) * A.height + (unsigned long long)A.width * (A.height + 1) >= (1ull << 28))
-      return PT_ERR_ARG;
-    const long long units = (long long)A.n_cams * E.per_cam * o.edge_spp;
+  if (K.edge_spp > 0) {
+    const long long units = (long long)A.n_cams * E.per_cam * K.edge_spp;
     if (units > 0) {
       const dim3 eg((unsigned)((units + 127) / 128)), eb(128);
       auto go = [&](auto kernel) { kernel<<<eg, eb, sm, cs>>>(A, K, E, grad_t, grad_v, rays); };
@@ -880,4 +1288,42 @@ extern "C" int pt_render_backward_reparam_vertices(pt_scene* s, const pt_render_
                                                    float* grad_vertices, unsigned long long* rays, void* stream) {
   if (!grad_vertices) return PT_ERR_ARG;
   return reparam_launch(s, r, p, opts, grad_image, nullptr, grad_vertices, rays, stream);
+}
+
+extern "C" int pt_render_jvp_reparam(pt_scene* s, const pt_render_desc* r, const pt_params* p,
+                                     const pt_reparam_opts* opts, const float* dir_translation, float* image,
+                                     float* image_dot, unsigned long long* rays, void* stream) {
+  RpOpts K;
+  if (rp_opts(opts, K) != PT_OK) return PT_ERR_ARG;
+  if (!s || !r || !p || !dir_translation || !image_dot) return PT_ERR_ARG;
+  LaunchArgs A;
+  int st = fill_launch(s, r, p, A);
+  if (st != PT_OK) return st;
+  if (r->cache || r->dbg_sample_L || r->dbg_sample_hash || r->counters) return PT_ERR_ARG;
+  EdgeGrid E;
+  if (K.edge_spp > 0 && edge_grid(A, E) != PT_OK) return PT_ERR_ARG;
+  pt_render_desc rd = *r;
+  if (rd.block_size == 0) rd.block_size = 128;
+  if (rd.block_size != 128) return PT_ERR_ARG;
+  int block;
+  long long grid;
+  if ((st = launch_dims(&rd, A, block, grid)) != PT_OK) return st;
+  cudaStream_t cs = (cudaStream_t)stream;
+  const size_t bytes = (size_t)A.n_cams * A.crop_w * A.crop_h * 3 * sizeof(float);
+  if (image && cudaMemsetAsync(image, 0, bytes, cs) != cudaSuccess) return PT_ERR_CUDA;
+  if (cudaMemsetAsync(image_dot, 0, bytes, cs) != cudaSuccess) return PT_ERR_CUDA;
+  const bool wide = s->dev.layout == PT_BVH_WIDE;
+  const dim3 gd((unsigned)grid), bd(block);
+  if (wide) reparam_jvp_kernel<PT_BVH_WIDE><<<gd, bd, 0, cs>>>(A, K, dir_translation, image, image_dot, rays);
+  else reparam_jvp_kernel<PT_BVH_BINARY><<<gd, bd, 0, cs>>>(A, K, dir_translation, image, image_dot, rays);
+  if (cudaGetLastError() != cudaSuccess) return PT_ERR_CUDA;
+  if (K.edge_spp > 0) {
+    const long long units = (long long)A.n_cams * E.per_cam * K.edge_spp;
+    if (units > 0) {
+      const dim3 eg((unsigned)((units + 127) / 128)), eb(128);
+      if (wide) edge_jvp_kernel<PT_BVH_WIDE><<<eg, eb, 0, cs>>>(A, K, E, dir_translation, image_dot, rays);
+      else edge_jvp_kernel<PT_BVH_BINARY><<<eg, eb, 0, cs>>>(A, K, E, dir_translation, image_dot, rays);
+    }
+  }
+  return cudaGetLastError() == cudaSuccess ? PT_OK : PT_ERR_CUDA;
 }

@@ -143,6 +143,27 @@ class DeviceScene:
             abi.pt_render_backward_reparam_vertices(self.handle, desc, p, o, grad_image.contiguous(), g_vertices,
                                                     rays, stream)
 
+    def jvp_reparam(self, st: RenderSettings, dir_translation, cams=None, albedo=None, textures=None,
+                    roughness=None, env=None, seed=None, rays=None, with_image=True, **opts):
+        """Forward-mode reparameterized derivative (pt_render_jvp_reparam): (image or
+        None, image_dot), image_dot = d image / d eps with every shape moved by eps *
+        dir_translation[shape] ([n_shapes, 3]).  opts: pt_reparam_opts fields."""
+        cams = list(cams) if cams is not None else self.cameras
+        rows, cols = st.rows_cols()
+        dev = self.albedo.device
+        d = torch.as_tensor(dir_translation, dtype=torch.float32, device=dev).contiguous()
+        if tuple(d.shape) != (self.n_shapes, 3):
+            raise ValueError(f"dir_translation must be [{self.n_shapes}, 3]")
+        img = torch.empty((len(cams), rows, cols, 3), device=dev, dtype=torch.float32) if with_image else None
+        dot = torch.empty((len(cams), rows, cols, 3), device=dev, dtype=torch.float32)
+        p = abi.params_struct(self.albedo if albedo is None else albedo,
+                              self.textures if textures is None else textures,
+                              self.roughness if roughness is None else roughness, env)
+        desc = self._desc(cams, st, seed=seed)
+        abi.pt_render_jvp_reparam(self.handle, desc, p, abi.reparam_opts(**opts), d, img, dot, rays,
+                                  torch.cuda.current_stream(dev).cuda_stream)
+        return img, dot
+
     # ------------------------------------------------------------------ wavefront variant
     def wavefront_forward(self, st: RenderSettings, calls: int = abi.PT_WF_TRACED, wave_paths: int = 0, cams=None,
                           albedo=None, textures=None, roughness=None, out=None, per_sample=False, env=None):
