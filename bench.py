@@ -835,6 +835,17 @@ def run_reparam_experiment(args):
     ev_v[1].record(stream)
     torch.cuda.synchronize()
     vert_ms = ev_v[0].elapsed_time(ev_v[1])
+    # forward mode along a direction over all shapes' translations (pt_render_jvp_reparam)
+    direction = torch.ones((sc.n_shapes, 3), device=dev)
+    jrays = torch.zeros(1, dtype=torch.int64, device=dev)
+    ds.jvp_reparam(replace(st, seed=12), direction, with_image=False)
+    flush.fill_(2.0)
+    ev_j = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ev_j[0].record(stream)
+    ds.jvp_reparam(replace(st, seed=12), direction, with_image=False, rays=jrays)
+    ev_j[1].record(stream)
+    torch.cuda.synchronize()
+    jvp_ms = ev_j[0].elapsed_time(ev_j[1])
     # the plain PRB adjoint of the same samples, for scale (texture + roughness gradients)
     g_tex = torch.zeros_like(ds.textures[0])
     g_rough = torch.zeros_like(ds.roughness)
@@ -858,6 +869,8 @@ def run_reparam_experiment(args):
                        "reparam_over_plain": round(rp_ms / plain_ms, 2), "rays_per_step": rays_step,
                        "vertex_mode_ms": round(vert_ms, 3),
                        "vertex_mode_mrays_s": round(rays_step / vert_ms / 1e3, 1),
+                       "forward_mode_ms": round(jvp_ms, 3),
+                       "forward_mode_mrays_s": round(int(jrays.item()) / jvp_ms / 1e3, 1),
                        "rays_per_sample": round(rays_step / (st.width * st.height * spp), 2),
                        "node_visits_per_ray": round(int(c[3]) / max(rays_step, 1), 2),
                        "tri_tests_per_ray": round(int(c[4]) / max(rays_step, 1), 2),
