@@ -657,6 +657,78 @@ struct EdgeGrid {
   long long per_cam;
 };
 
+// The edge and sample of a unit of the edge kernels (per camera: the vertical
+// edges row by row, then the horizontal ones), its PCG32 stream and the pixel
+// index of (x, y) in the crop (-1 outside).
+struct EdgeSample {
+  int ci, X, Y;
+  bool vertical;
+  unsigned long long stream;
+};
+__device__ __forceinline__ EdgeSample edge_of(const LaunchArgs& A, const RpOpts& K, const EdgeGrid& E,
+                                              long long unit) {
+  EdgeSample es;
+  const int k = (int)(unit % K.edge_spp);
+  const long long ea = unit / K.edge_spp;
+  es.ci = (int)(ea / E.per_cam);
+  long long e = ea - (long long)es.ci * E.per_cam;
+  const long long nv = (long long)A.crop_h * E.nvx;
+  es.vertical = e < nv;
+  unsigned long long id;
+  if (es.vertical) {
+    es.Y = A.crop_y0 + (int)(e / E.nvx);
+    es.X = E.xlo + (int)(e % E.nvx);
+    id = (unsigned long long)es.Y * (unsigned long long)(A.width + 1) + (unsigned long long)es.X;
+  } else {
+    e -= nv;
+    es.Y = E.ylo + (int)(e / A.crop_w);
+    es.X = A.crop_x0 + (int)(e % A.crop_w);
+    id = (unsigned long long)(A.width + 1) * (unsigned long long)A.height +
+         (unsigned long long)es.Y * (unsigned long long)A.width + (unsigned long long)es.X;
+  }
+  es.stream = ((unsigned long long)es.ci << 40) | (id << 12) | (unsigned long long)k | (1ull << 61);
+  return es;
+}
+__device__ __forceinline__ long long crop_pixel(const LaunchArgs& A, int ci, int x, int y) {
+  if (x < A.crop_x0 || x >= A.crop_x0 + A.crop_w || y < A.crop_y0 || y >= A.crop_y0 + A.crop_h) return -1;
+  return ((long long)ci * A.crop_h + (y - A.crop_y0)) * A.crop_w + (x - A.crop_x0);
+}
+
+// The path through a uniform point of the edge (the point's uniform first, then
+// the unused second one, then the path's): its radiance, its camera ray (o, u) and
+// that ray's hit distance (infinite if it escapes).
+template <int LAYOUT, bool INSTR>
+__device__ __forceinline__ float3 edge_path(const LaunchArgs& A, const EdgeSample& es, float3& o, float3& u,
+                                            float& t0, unsigned& rays, Counters<INSTR>& cnt) {
+  const float3 z = f3(0.f, 0.f, 0.f);
+  PathState P;
+  P.slot = 0;
+  P.cache_done = false;
+  P.rng.seed(A.seed, es.stream);
+  P.fh.h = 2166136261u;
+  const float j0 = P.rng.uniform();
+  P.rng.uniform();
+  path_start_at<INSTR>(A, P, es.ci, es.vertical ? (float)es.X : (float)es.X + j0,
+                       es.vertical ? (float)es.Y + j0 : (float)es.Y, cnt);
+  o = P.ro;
+  u = P.rd;
+  t0 = INFINITY;
+  GradSink sink;
+  for (bool first = true;; first = false) {
+    const Hit hit = closest<LAYOUT, INSTR>(A.scene, P.ro, P.rd, INFINITY, false, cnt);
+    ++rays;
+    if (first && hit.pos >= 0) t0 = hit.t;
+    if (!path_shade<false, false, INSTR, PT_DISPATCH_SWITCH>(A, P, hit, false, z, sink, cnt)) break;
+    bool occ = false;
+    if (P.has_shadow) {
+      occ = closest<LAYOUT, INSTR>(A.scene, P.so, P.sd, P.stmax, true, cnt).pos >= 0;
+      ++rays;
+    }
+    if (!path_finish<false, false, INSTR>(A, P, occ, false, z, sink, cnt)) break;
+  }
+  return P.L;
+}
+
 // Pixel-edge term of the camera-ray warp (box pixel filter).  The warp that holds
 // the discontinuities still also moves every pixel's footprint, a unit box in pixel
 // coordinates: its boundary moves with minus the warp's image-plane velocity v, so
@@ -680,7 +752,6 @@ __global__ void __launch_bounds__(128, 8) edge_kernel(const __grid_constant__ La
   }
   GradOut G{K.smem ? s_grad : grad_t};
   VertOut GV{grad_v};
-  const DevScene& S = A.scene;
   Counters<INSTR> cnt;
   if constexpr (INSTR)
     for (int i = 0; i < 8; ++i) cnt.c[i] = 0;
@@ -690,64 +761,24 @@ __global__ void __launch_bounds__(128, 8) edge_kernel(const __grid_constant__ La
   WarpRay w{};
   bool has = false;
   if (unit < (long long)A.n_cams * E.per_cam * K.edge_spp) {
-    const int k = (int)(unit % K.edge_spp);
-    const long long ea = unit / K.edge_spp;
-    const int ci = (int)(ea / E.per_cam);
-    long long e = ea - (long long)ci * E.per_cam;
-    const long long nv = (long long)A.crop_h * E.nvx;
-    const bool vertical = e < nv;
-    int X, Y;
-    unsigned long long id;
-    if (vertical) {
-      Y = A.crop_y0 + (int)(e / E.nvx);
-      X = E.xlo + (int)(e % E.nvx);
-      id = (unsigned long long)Y * (unsigned long long)(A.width + 1) + (unsigned long long)X;
-    } else {
-      e -= nv;
-      Y = E.ylo + (int)(e / A.crop_w);
-      X = A.crop_x0 + (int)(e % A.crop_w);
-      id = (unsigned long long)(A.width + 1) * (unsigned long long)A.height +
-           (unsigned long long)Y * (unsigned long long)A.width + (unsigned long long)X;
-    }
+    const EdgeSample es = edge_of(A, K, E, unit);
     auto dl_at = [&](int x, int y) {
-      if (x < A.crop_x0 || x >= A.crop_x0 + A.crop_w || y < A.crop_y0 || y >= A.crop_y0 + A.crop_h) return z;
-      const long long pix = ((long long)ci * A.crop_h + (y - A.crop_y0)) * A.crop_w + (x - A.crop_x0);
-      return f3(A.grad_image[3 * pix], A.grad_image[3 * pix + 1], A.grad_image[3 * pix + 2]);
+      const long long pix = crop_pixel(A, es.ci, x, y);
+      return pix < 0 ? z : f3(A.grad_image[3 * pix], A.grad_image[3 * pix + 1], A.grad_image[3 * pix + 2]);
     };
-    const float3 gd = dl_at(X, Y) - (vertical ? dl_at(X - 1, Y) : dl_at(X, Y - 1));
+    const float3 gd = dl_at(es.X, es.Y) - (es.vertical ? dl_at(es.X - 1, es.Y) : dl_at(es.X, es.Y - 1));
     if (gd.x != 0.0f || gd.y != 0.0f || gd.z != 0.0f) {
-      const unsigned long long stream = ((unsigned long long)ci << 40) | (id << 12) | (unsigned long long)k | (1ull << 61);
-      PathState P;
-      P.slot = 0;
-      P.cache_done = false;
-      P.rng.seed(A.seed, stream);
-      P.fh.h = 2166136261u;
-      const float j0 = P.rng.uniform();
-      P.rng.uniform();  // the second coordinate's uniform, unused on an edge
-      path_start_at<INSTR>(A, P, ci, vertical ? (float)X : (float)X + j0, vertical ? (float)Y + j0 : (float)Y, cnt);
-      const float3 o = P.ro, u = P.rd;
-      float t0 = INFINITY;
-      GradSink sink;
-      for (bool first = true;; first = false) {
-        const Hit hit = closest<LAYOUT, INSTR>(S, P.ro, P.rd, INFINITY, false, cnt);
-        ++rays;
-        if (first && hit.pos >= 0) t0 = hit.t;
-        if (!path_shade<false, false, INSTR, PT_DISPATCH_SWITCH>(A, P, hit, false, z, sink, cnt)) break;
-        bool occ = false;
-        if (P.has_shadow) {
-          occ = closest<LAYOUT, INSTR>(S, P.so, P.sd, P.stmax, true, cnt).pos >= 0;
-          ++rays;
-        }
-        if (!path_finish<false, false, INSTR>(A, P, occ, false, z, sink, cnt)) break;
-      }
-      const float R = dot3(gd, P.L) / (float)K.edge_spp;
+      float3 o, u;
+      float t0;
+      const float3 L = edge_path<LAYOUT, INSTR>(A, es, o, u, t0, rays, cnt);
+      const float R = dot3(gd, L) / (float)K.edge_spp;
       if (R != 0.0f) {
         float px, py;
         float3 gpx, gpy;
-        pixel_coords(A, A.cams[ci], u, px, py, gpx, gpy);
+        pixel_coords(A, A.cams[es.ci], u, px, py, gpx, gpy);
         Pcg32 aux;
-        aux.seed(A.seed, stream | (1ull << 62));
-        w = WarpRay{o, u, (vertical ? gpx : gpy) * R, -1, ci, 0.0f, t0, aux.state, aux.inc, -1, 0.0f, 0.0f};
+        aux.seed(A.seed, es.stream | (1ull << 62));
+        w = WarpRay{o, u, (es.vertical ? gpx : gpy) * R, -1, es.ci, 0.0f, t0, aux.state, aux.inc, -1, 0.0f, 0.0f};
         has = true;
       }
     }
@@ -1074,63 +1105,23 @@ __global__ void __launch_bounds__(128, 8) edge_jvp_kernel(const __grid_constant_
                                                        const EdgeGrid E, const float* __restrict__ dir_t,
                                                        float* __restrict__ image_dot,
                                                        unsigned long long* rays_out) {
-  const DevScene& S = A.scene;
   Counters<false> cnt;
   const float3 z = f3(0.f, 0.f, 0.f);
   const long long unit = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   unsigned rays = 0;
   WarpRay w{};
-  bool has = false, vertical = false;
-  int X = 0, Y = 0, ci = 0;
+  bool has = false;
+  EdgeSample es{};
   float3 L = z;
   if (unit < (long long)A.n_cams * E.per_cam * K.edge_spp) {
-    const int k = (int)(unit % K.edge_spp);
-    const long long ea = unit / K.edge_spp;
-    ci = (int)(ea / E.per_cam);
-    long long e = ea - (long long)ci * E.per_cam;
-    const long long nv = (long long)A.crop_h * E.nvx;
-    vertical = e < nv;
-    unsigned long long id;
-    if (vertical) {
-      Y = A.crop_y0 + (int)(e / E.nvx);
-      X = E.xlo + (int)(e % E.nvx);
-      id = (unsigned long long)Y * (unsigned long long)(A.width + 1) + (unsigned long long)X;
-    } else {
-      e -= nv;
-      Y = E.ylo + (int)(e / A.crop_w);
-      X = A.crop_x0 + (int)(e % A.crop_w);
-      id = (unsigned long long)(A.width + 1) * (unsigned long long)A.height +
-           (unsigned long long)Y * (unsigned long long)A.width + (unsigned long long)X;
-    }
-    const unsigned long long stream = ((unsigned long long)ci << 40) | (id << 12) | (unsigned long long)k | (1ull << 61);
-    PathState P;
-    P.slot = 0;
-    P.cache_done = false;
-    P.rng.seed(A.seed, stream);
-    P.fh.h = 2166136261u;
-    const float j0 = P.rng.uniform();
-    P.rng.uniform();
-    path_start_at<false>(A, P, ci, vertical ? (float)X : (float)X + j0, vertical ? (float)Y + j0 : (float)Y, cnt);
-    const float3 o = P.ro, u = P.rd;
-    float t0 = INFINITY;
-    GradSink sink;
-    for (bool first = true;; first = false) {
-      const Hit hit = closest<LAYOUT, false>(S, P.ro, P.rd, INFINITY, false, cnt);
-      ++rays;
-      if (first && hit.pos >= 0) t0 = hit.t;
-      if (!path_shade<false, false, false, PT_DISPATCH_SWITCH>(A, P, hit, false, z, sink, cnt)) break;
-      bool occ = false;
-      if (P.has_shadow) {
-        occ = closest<LAYOUT, false>(S, P.so, P.sd, P.stmax, true, cnt).pos >= 0;
-        ++rays;
-      }
-      if (!path_finish<false, false, false>(A, P, occ, false, z, sink, cnt)) break;
-    }
-    L = P.L;
+    es = edge_of(A, K, E, unit);
+    float3 o, u;
+    float t0;
+    L = edge_path<LAYOUT, false>(A, es, o, u, t0, rays, cnt);
     if (L.x != 0.0f || L.y != 0.0f || L.z != 0.0f) {
       Pcg32 aux;
-      aux.seed(A.seed, stream | (1ull << 62));
-      w = WarpRay{o, u, z, -1, ci, 0.0f, t0, aux.state, aux.inc, -1, 0.0f, 0.0f};
+      aux.seed(A.seed, es.stream | (1ull << 62));
+      w = WarpRay{o, u, z, -1, es.ci, 0.0f, t0, aux.state, aux.inc, -1, 0.0f, 0.0f};
       has = true;
     }
   }
@@ -1140,18 +1131,17 @@ __global__ void __launch_bounds__(128, 8) edge_jvp_kernel(const __grid_constant_
   if (has) {
     float pxc, pyc;
     float3 gpx, gpy;
-    pixel_coords(A, A.cams[ci], w.u, pxc, pyc, gpx, gpy);
-    const float3 d = L * (dot3(vertical ? gpx : gpy, V) / (float)K.edge_spp);
-    const int xa = vertical ? X - 1 : X, ya = vertical ? Y : Y - 1;
+    pixel_coords(A, A.cams[es.ci], w.u, pxc, pyc, gpx, gpy);
+    const float3 d = L * (dot3(es.vertical ? gpx : gpy, V) / (float)K.edge_spp);
     auto add = [&](int x, int y, float3 v) {
-      if (x < A.crop_x0 || x >= A.crop_x0 + A.crop_w || y < A.crop_y0 || y >= A.crop_y0 + A.crop_h) return;
-      const long long pix = ((long long)ci * A.crop_h + (y - A.crop_y0)) * A.crop_w + (x - A.crop_x0);
+      const long long pix = crop_pixel(A, es.ci, x, y);
+      if (pix < 0) return;
       atomicAdd(&image_dot[3 * pix], v.x);
       atomicAdd(&image_dot[3 * pix + 1], v.y);
       atomicAdd(&image_dot[3 * pix + 2], v.z);
     };
-    add(xa, ya, -d);
-    add(X, Y, d);
+    add(es.vertical ? es.X - 1 : es.X, es.vertical ? es.Y : es.Y - 1, -d);
+    add(es.X, es.Y, d);
   }
   if (rays_out) {
     unsigned long long rr = rays;
