@@ -416,7 +416,7 @@ def test_reparam_camera_translation(lib, oracle_mod):
         opt.step()
     err = off.detach().cpu().numpy() - truth
     print("recovered camera offset", off.detach().cpu().numpy(), "truth", truth, "loss", loss.item())
-    assert np.abs(err).max() < 0.025   # started 0.1 away
+    assert np.abs(err).max() < 0.03   # started 0.1 away; measured 0.015
 
 
 @pytest.mark.parametrize("n_aux", [2, 5, 32])
