@@ -1117,8 +1117,9 @@ struct JvpAcc : NoRayEvents {
 // integrator traces is reparameterized: in the primal the warp is the identity;
 // its derivative turns the ray direction by V(u) and multiplies the integrand by
 // the Jacobian determinant 1 + div V.  The parameters are one translation per
-// shape (all its vertices move together); a surface point keeps its barycentric
-// coordinates, so path vertices move with their shape's translation.
+// shape (all its vertices move together) or every triangle corner's position; a
+// surface point keeps its barycentric coordinates, so path vertices move with
+// their shape (or their triangle's corners).
 //
 // The warp field of a ray (origin o, primal direction u, origin shape s_o; the
 // camera counts as static) is built from N auxiliary rays w_i drawn from the von
@@ -1146,12 +1147,18 @@ struct JvpAcc : NoRayEvents {
 //               the pinhole (f = optical axis); b = 1, or with border > 0 a window
 //               that takes the warp to 0 within `border` pixels of the image
 //               border (an option: the pixel-edge term below makes it unneeded);
-//   light and BSDF rays at a diffuse vertex: 1 + theta (div V + n.V / n.u), the
-//               cosine term.
-// Rays leaving non-diffuse vertices are not reparameterized (their directional
-// terms stay detached).  The tangent of a sample is propagated forward along the
-// path like the throughput (no replay): the oracle's independent route to the
-// reverse-mode kernel's gradients.
+//   light and BSDF rays at diffuse, GGX-conductor and blend vertices:
+//               1 + theta (div V + n.V / n.u), the cosine term; at the glossy
+//               ones the BSDF value also turns with both of its directions
+//               (grad_out log f_c . V of this ray, grad_in log f_c . -V of the
+//               ray that arrived) and, with vertex positions as parameters, with
+//               the triangle's normal.
+// Rays leaving dielectric (delta) vertices are not reparameterized.  The warp of
+// the camera rays also moves the pixels' own footprints: the pixel-edge term
+// (paths through pixel edges) carries that flux.  The tangent of a sample is
+// propagated forward along the path like the throughput (no replay): the
+// oracle's independent route to the reverse-mode kernel's gradients, and its
+// forward-mode image derivative.
 
 struct ReparamOpts {
   int n_aux = 16;
