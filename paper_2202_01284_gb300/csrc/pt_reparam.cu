@@ -43,6 +43,9 @@
 // (pixel, lane) replays its samples in lockstep with the other lanes of its warp,
 // which trace the auxiliary rays of the posted rays together.  Translation
 // gradients are accumulated per CTA in shared memory when the shape table fits.
+// Then one thread per (pixel edge, sample) adds the pixel-edge term: the camera
+// warp moves the box-filtered pixels' footprints too.  The forward mode (at the end
+// of the file) runs the same warps in one pass along a direction of translations.
 #include "pt_mega.cuh"
 
 namespace ptgb {
