@@ -489,6 +489,15 @@ int pt_render_backward_reparam_vertices(pt_scene* scene, const pt_render_desc* d
 int pt_render_jvp_reparam(pt_scene* scene, const pt_render_desc* desc, const pt_params* params,
                           const pt_reparam_opts* opts, const float* dir_translation, float* image, float* image_dot,
                           unsigned long long* rays, void* stream);
+/* The same along a direction of every triangle corner's position: dir_vertices,
+ * device float [n_tris][3][3] in the order of pt_scene_desc.vertices (corner k of
+ * triangle t at [t][k]); a surface point moves with its barycentric weights, and
+ * a moving vertex's cosine and glossy BSDF value follow its triangle's turning
+ * normal.  Pairs with pt_render_backward_reparam_vertices as the translation form
+ * with pt_render_backward_reparam.  Other arguments and errors as above. */
+int pt_render_jvp_reparam_vertices(pt_scene* scene, const pt_render_desc* desc, const pt_params* params,
+                                   const pt_reparam_opts* opts, const float* dir_vertices, float* image,
+                                   float* image_dot, unsigned long long* rays, void* stream);
 
 /* Reads (and clears) the scene's device status word after synchronising
  * `stream`: *out = PT_OK or the first PT_ERR_* a kernel recorded. */

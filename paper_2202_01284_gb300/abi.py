@@ -162,6 +162,9 @@ SIGNATURES = {
     "pt_render_jvp_reparam": ([C.c_void_p, C.POINTER(pt_render_desc), C.POINTER(pt_params),
                                C.POINTER(pt_reparam_opts), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                C.c_void_p], C.c_int),
+    "pt_render_jvp_reparam_vertices": ([C.c_void_p, C.POINTER(pt_render_desc), C.POINTER(pt_params),
+                                        C.POINTER(pt_reparam_opts), C.c_void_p, C.c_void_p, C.c_void_p,
+                                        C.c_void_p, C.c_void_p], C.c_int),
     "pt_last_device_status": ([C.c_void_p, C.c_void_p, C.POINTER(C.c_int)], C.c_int),
     "pt_status_string": ([C.c_int], C.c_char_p),
     "pt_cache_create": ([C.POINTER(pt_cache_desc), C.POINTER(C.c_void_p)], C.c_int),
@@ -431,6 +434,14 @@ def pt_render_jvp_reparam(handle: int, desc: pt_render_desc, params: pt_params, 
     check("pt_render_jvp_reparam",
           load().pt_render_jvp_reparam(handle, C.byref(desc), C.byref(params), C.byref(opts), _ptr(dir_translation),
                                        _ptr(image), _ptr(image_dot), _ptr(rays), stream or None))
+
+
+def pt_render_jvp_reparam_vertices(handle: int, desc: pt_render_desc, params: pt_params, opts: pt_reparam_opts,
+                                   dir_vertices, image, image_dot, rays=None, stream: int = 0) -> None:
+    check("pt_render_jvp_reparam_vertices",
+          load().pt_render_jvp_reparam_vertices(handle, C.byref(desc), C.byref(params), C.byref(opts),
+                                                _ptr(dir_vertices), _ptr(image), _ptr(image_dot), _ptr(rays),
+                                                stream or None))
 
 
 def pt_last_device_status(handle: int, stream: int = 0) -> int:

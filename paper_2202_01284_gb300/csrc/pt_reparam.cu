@@ -820,9 +820,13 @@ __global__ void __launch_bounds__(128, 8) edge_kernel(const __grid_constant__ La
 
 // Warps of the rays the lanes posted (called by all lanes together, as
 // process_warps): the lane that posted a ray receives V (tangential) and div V.
-template <int LAYOUT>
+// dir: [n_shapes][3] translation velocities, or (VERT) [n_tris][3][3] corner
+// velocities by original triangle id; a plane point then moves with the
+// barycentric combination of its triangle's corners (b_k(w) / t(w) = beta_k (n.w)
+// / d + a_k . w, as in the reverse mode) and the origin with its own.
+template <int LAYOUT, bool VERT>
 __device__ __noinline__ unsigned warp_forward(const LaunchArgs& A, const RpOpts& K, bool has, const WarpRay& mine,
-                                              const float* __restrict__ dir_t, float3& V_out, float& div_out,
+                                              const float* __restrict__ dir, float3& V_out, float& div_out,
                                               Counters<false>& cnt) {
   const DevScene& S = A.scene;
   const int lane = lane_id(), gs = K.group, grp = lane / gs, j = lane % gs;
@@ -849,6 +853,11 @@ __device__ __noinline__ unsigned warp_forward(const LaunchArgs& A, const RpOpts&
     w.t0 = __shfl_sync(kFull, mine.t0, sl);
     w.st = __shfl_sync(kFull, mine.st, sl);
     w.inc = __shfl_sync(kFull, mine.inc, sl);
+    if constexpr (VERT) {
+      w.o_tri = __shfl_sync(kFull, mine.o_tri, sl);
+      w.o_bu = __shfl_sync(kFull, mine.o_bu, sl);
+      w.o_bv = __shfl_sync(kFull, mine.o_bv, sl);
+    }
     const bool on = src >= 0 && j < K.n_aux;
     float alpha = 0.0f, t = 0.0f;
     int pos = -1;
@@ -884,19 +893,15 @@ __device__ __noinline__ unsigned warp_forward(const LaunchArgs& A, const RpOpts&
     float dv = 0.0f;
     int si = -1;
     if (on && pos >= 0) si = tri_shape(S, pos);
-    if (si >= 0 && si != w.s_o) {
-      const float3 vi = f3(__ldg(&dir_t[3 * si]), __ldg(&dir_t[3 * si + 1]), __ldg(&dir_t[3 * si + 2]));
-      const float3 vo = w.s_o >= 0 ? f3(__ldg(&dir_t[3 * w.s_o]), __ldg(&dir_t[3 * w.s_o + 1]),
-                                        __ldg(&dir_t[3 * w.s_o + 2]))
-                                   : f3(0.f, 0.f, 0.f);
-      const float3 delta = vi - vo;
+    const bool contrib = VERT ? (on && pos >= 0) : (si >= 0 && si != w.s_o);
+    if (contrib) {
       float b = 1.0f;
       float3 gb = f3(0.f, 0.f, 0.f);
       if (w.cam >= 0) b = cam_window(A, A.cams[w.cam], w.u, K.border, gb);
       const float3 nrm = tri_normal(S, pos);
       const float di = dot3(nrm, wi) * t;
-      const float sv = dot3(nrm, w.u) / di;
-      const float3 g = (nrm - w.u * dot3(nrm, w.u)) * (1.0f / di);
+      const float nu = dot3(nrm, w.u) / di;
+      const float3 nperp = (nrm - w.u * dot3(nrm, w.u)) * (1.0f / di);
       float Dm = 0.0f;
       float3 Pm = f3(0.f, 0.f, 0.f);
       if (K.jackknife) {
@@ -904,16 +909,52 @@ __device__ __noinline__ unsigned warp_forward(const LaunchArgs& A, const RpOpts&
         Pm = P - pi * alpha;
       }
       const float Jm = K.jackknife ? n / D - (n - 1.0f) / n * (S1 - 1.0f / Dm) : 1.0f / D;
-      vs = delta * (alpha * b * sv * Jm);
-      // div part: the reverse coefficient with M = 0, R = 1
-      const float3 Ai = (pi * K.kk - w.u * 2.0f) * (b * sv) + g * b + gb * sv;
-      const float kb = K.kk * b * sv;
-      float3 c = Ai * (1.0f / D) - P * (kb / (D * D));
-      if (K.jackknife) {
-        const float3 loo = Ai * (S1 - 1.0f / Dm) - (SP - Pm * (1.0f / (Dm * Dm))) * kb;
-        c = c * n - loo * ((n - 1.0f) / n);
+      // a velocity field s(w) Delta with s linear in w (gradient g on the sphere):
+      // its weight in V at u, and the reverse coefficient with M = 0, R = 1 (div part)
+      auto parts = [&](float sv, float3 g, float& vw, float3& cr) {
+        vw = alpha * b * sv * Jm;
+        const float3 Ai = (pi * K.kk - w.u * 2.0f) * (b * sv) + g * b + gb * sv;
+        const float kb = K.kk * b * sv;
+        float3 c = Ai * (1.0f / D) - P * (kb / (D * D));
+        if (K.jackknife) {
+          const float3 loo = Ai * (S1 - 1.0f / Dm) - (SP - Pm * (1.0f / (Dm * Dm))) * kb;
+          c = c * n - loo * ((n - 1.0f) / n);
+        }
+        cr = c * alpha;
+      };
+      auto vel = [&](int base) { return f3(__ldg(&dir[base]), __ldg(&dir[base + 1]), __ldg(&dir[base + 2])); };
+      float vw;
+      float3 cr;
+      parts(nu, nperp, vw, cr);
+      if constexpr (VERT) {
+        float3 vo = f3(0.f, 0.f, 0.f);  // the origin's velocity
+        if (w.o_tri >= 0) {
+          const size_t ob = 9 * (size_t)w.o_tri;
+          vo = vel(ob) * (1.0f - w.o_bu - w.o_bv) + vel(ob + 3) * w.o_bu + vel(ob + 6) * w.o_bv;
+        }
+        vs = -vo * vw;
+        dv = -dot3(cr, vo);
+        const float3 v0 = xyz(__ldg(&S.tri_v[3 * pos]));
+        const float3 e1 = xyz(__ldg(&S.tri_v[3 * pos + 1])), e2 = xyz(__ldg(&S.tri_v[3 * pos + 2]));
+        const float3 c = cross3(e1, e2);
+        const float icc = 1.0f / dot3(c, c);
+        const float3 a1 = cross3(e2, c) * icc, a2 = cross3(c, e1) * icc;
+        const float3 aj[3] = {-(a1 + a2), a1, a2};
+        const float3 ov = w.o - v0;
+        const size_t tb = 9 * (size_t)tri_orig(S, pos);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          const float beta = dot3(aj[k], ov) + (k == 0 ? 1.0f : 0.0f);
+          parts(beta * nu + dot3(aj[k], w.u), nperp * beta + (aj[k] - w.u * dot3(aj[k], w.u)), vw, cr);
+          const float3 vk = vel(tb + 3 * k);
+          vs = vs + vk * vw;
+          dv += dot3(cr, vk);
+        }
+      } else {
+        const float3 delta = vel(3 * si) - (w.s_o >= 0 ? vel(3 * w.s_o) : f3(0.f, 0.f, 0.f));
+        vs = delta * vw;
+        dv = dot3(cr, delta);
       }
-      dv = dot3(c * alpha, delta);
     }
     vs = group_sum3(vs, gs);
     dv = group_sum(dv, gs);
@@ -930,25 +971,52 @@ __device__ __noinline__ unsigned warp_forward(const LaunchArgs& A, const RpOpts&
 
 // Per-channel log-derivative of a term leaving a vertex along d: its ray's m.V +
 // div V, plus at a glossy vertex the BSDF's directional terms (V of this ray,
-// -V of the ray that arrived).
+// -V of the ray that arrived).  Vertex mode: ndot = the turn of the vertex's
+// unit geometric normal ng; the cosine adds ndot.d / ng.d and a glossy value
+// ndot . (ng x J_c), J_c = wi x grad_in log f_c + d x grad_out log f_c (f is
+// unchanged when the normal and both directions turn together).
 __device__ __forceinline__ float3 fwd_term(float3 n_s, float3 d, float3 V, float dvg, bool glossy, const Gloss& gl,
-                                           const Frame& fr, float3 wi_l, float3 v_prev) {
-  const float l = dot3(n_s, V) / dot3(n_s, d) + dvg;
+                                           const Frame& fr, float3 wi_l, float3 v_prev, float3 ng, float3 ndot,
+                                           float3 wi_w) {
+  const bool turns = ndot.x != 0.0f || ndot.y != 0.0f || ndot.z != 0.0f;
+  const float l = dot3(n_s, V) / dot3(n_s, d) + dvg + (turns ? dot3(ndot, d) / dot3(ng, d) : 0.0f);
   float3 t = f3(l, l, l);
   if (glossy) {
     float3 go[3], gi[3];
     glossy_log_grad(gl.type, gl.alpha, gl.f0, gl.wd, gl.albedo, wi_l, fr.to_local(d), go, gi);
-    t.x += dot3(fr.to_world(go[0]), V) - dot3(fr.to_world(gi[0]), v_prev);
-    t.y += dot3(fr.to_world(go[1]), V) - dot3(fr.to_world(gi[1]), v_prev);
-    t.z += dot3(fr.to_world(go[2]), V) - dot3(fr.to_world(gi[2]), v_prev);
+    float tc[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const float3 gow = fr.to_world(go[c]), giw = fr.to_world(gi[c]);
+      tc[c] = dot3(gow, V) - dot3(giw, v_prev) + dot3(ndot, cross3(ng, cross3(wi_w, giw) + cross3(d, gow)));
+    }
+    t = t + f3(tc[0], tc[1], tc[2]);
   }
   return t;
+}
+
+// Vertex mode: the turn of the unit geometric normal of the triangle at leaf
+// position pos when its corners move with dir[orig][k] (zero in translation mode).
+template <bool VERT>
+__device__ __forceinline__ float3 normal_turn(const DevScene& S, int pos, const float* __restrict__ dir) {
+  if constexpr (!VERT) {
+    return f3(0.f, 0.f, 0.f);
+  } else {
+    const float3 e1 = xyz(__ldg(&S.tri_v[3 * pos + 1])), e2 = xyz(__ldg(&S.tri_v[3 * pos + 2]));
+    const size_t b = 9 * (size_t)tri_orig(S, pos);
+    auto vel = [&](size_t i) { return f3(__ldg(&dir[i]), __ldg(&dir[i + 1]), __ldg(&dir[i + 2])); };
+    const float3 v0 = vel(b), d1 = vel(b + 3) - v0, d2 = vel(b + 6) - v0;
+    const float3 c = cross3(e1, e2), cd = cross3(d1, e2) + cross3(e1, d2);
+    const float il = 1.0f / sqrtf(dot3(c, c));
+    const float3 nn = c * il;
+    return (cd - nn * dot3(nn, cd)) * il;
+  }
 }
 
 // One thread per (pixel, lane) as the reverse kernel; samples in lockstep, the
 // warps processed together after each vertex.  image / image_dot accumulate (the
 // caller zeroes them): the mean over the pixel's samples.
-template <int LAYOUT>
+template <int LAYOUT, bool VERT>
 __global__ void __launch_bounds__(128, 8) reparam_jvp_kernel(const __grid_constant__ LaunchArgs A, const RpOpts K,
                                                           const float* __restrict__ dir_t, float* __restrict__ image,
                                                           float* __restrict__ image_dot,
@@ -978,7 +1046,7 @@ __global__ void __launch_bounds__(128, 8) reparam_jvp_kernel(const __grid_consta
   for (;;) {
     WarpRay w0{}, w1{};
     bool h0 = false, h1 = false, start = false, done = false, glossy = false;
-    float3 n_s = z, c_nee = z, wi_l = z;
+    float3 n_s = z, c_nee = z, wi_l = z, ng = z, ndot = z, wi_w = z;
     Gloss gl{};
     Frame fr{};
     if (!live && valid && si < A.spp) {
@@ -1004,12 +1072,14 @@ __global__ void __launch_bounds__(128, 8) reparam_jvp_kernel(const __grid_consta
         ++rays;
       }
       const bool block = hit.pos >= 0 && P.depth < A.max_depth;
-      int s_o = -1;
-      const float3 wi_w = -P.rd;
+      int s_o = -1, o_tri = -1;
+      wi_w = -P.rd;
       if (hit.pos >= 0) {
         s_o = tri_shape(S, hit.pos);
-        const float3 ng = tri_normal(S, hit.pos);
+        o_tri = tri_orig(S, hit.pos);
+        ng = tri_normal(S, hit.pos);
         n_s = dot3(ng, P.rd) < 0.0f ? ng : -ng;
+        ndot = normal_turn<VERT>(S, hit.pos, dir_t);
       }
       float3 L0 = P.L;
       bool more = path_shade<false, false, false, PT_DISPATCH_SWITCH>(A, P, hit, false, z, sink, cnt);
@@ -1038,7 +1108,7 @@ __global__ void __launch_bounds__(128, 8) reparam_jvp_kernel(const __grid_consta
           ++rays;
           c_nee = P.c_nee;
           w0 = WarpRay{P.so, P.sd, z, s_o, -1, 0.0f, hl.pos >= 0 ? hl.t : INFINITY, aux_nee.state, aux_nee.inc,
-                       -1, 0.0f, 0.0f};
+                       o_tri, hit.u, hit.v};
           h0 = true;
         }
         L0 = P.L;
@@ -1049,7 +1119,7 @@ __global__ void __launch_bounds__(128, 8) reparam_jvp_kernel(const __grid_consta
           ++rays;
           cached = true;
           w1 = WarpRay{P.ro, P.rd, z, s_o, -1, 0.0f, next.pos >= 0 ? next.t : INFINITY, aux_bsdf.state,
-                       aux_bsdf.inc, -1, 0.0f, 0.0f};
+                       aux_bsdf.inc, o_tri, hit.u, hit.v};
           h1 = true;
         }
       }
@@ -1058,16 +1128,16 @@ __global__ void __launch_bounds__(128, 8) reparam_jvp_kernel(const __grid_consta
     if (!__any_sync(kFull, live || h0 || h1 || (valid && si < A.spp))) break;
     float3 V0, V1;
     float d0, d1;
-    rays += warp_forward<LAYOUT>(A, K, h0, w0, dir_t, V0, d0, cnt);
-    rays += warp_forward<LAYOUT>(A, K, h1, w1, dir_t, V1, d1, cnt);
+    rays += warp_forward<LAYOUT, VERT>(A, K, h0, w0, dir_t, V0, d0, cnt);
+    rays += warp_forward<LAYOUT, VERT>(A, K, h1, w1, dir_t, V1, d1, cnt);
     if (start) {
       const float l = dot3(w0.m, V0) + d0;  // m: the pinhole's image-plane density term
       r = f3(l, l, l);
       v_prev = V0;
     } else if (live) {
-      if (h0) ldot = ldot + c_nee * fwd_term(n_s, w0.u, V0, d0, glossy, gl, fr, wi_l, v_prev);
+      if (h0) ldot = ldot + c_nee * fwd_term(n_s, w0.u, V0, d0, glossy, gl, fr, wi_l, v_prev, ng, ndot, wi_w);
       if (h1) {
-        r = r + fwd_term(n_s, w1.u, V1, d1, glossy, gl, fr, wi_l, v_prev);
+        r = r + fwd_term(n_s, w1.u, V1, d1, glossy, gl, fr, wi_l, v_prev, ng, ndot, wi_w);
         v_prev = V1;
       } else {
         v_prev = z;  // a delta vertex: its continuation is not reparameterized
@@ -1103,7 +1173,7 @@ __global__ void __launch_bounds__(128, 8) reparam_jvp_kernel(const __grid_consta
 // its camera warp's velocity across the edge v_e; the pixel left of / above the
 // edge loses L v_e / edge_spp, the one right of / below it gains it (pixels of the
 // crop only).
-template <int LAYOUT>
+template <int LAYOUT, bool VERT>
 __global__ void __launch_bounds__(128, 8) edge_jvp_kernel(const __grid_constant__ LaunchArgs A, const RpOpts K,
                                                        const EdgeGrid E, const float* __restrict__ dir_t,
                                                        float* __restrict__ image_dot,
@@ -1130,7 +1200,7 @@ __global__ void __launch_bounds__(128, 8) edge_jvp_kernel(const __grid_constant_
   }
   float3 V;
   float dv;
-  rays += warp_forward<LAYOUT>(A, K, has, w, dir_t, V, dv, cnt);
+  rays += warp_forward<LAYOUT, VERT>(A, K, has, w, dir_t, V, dv, cnt);
   if (has) {
     float pxc, pyc;
     float3 gpx, gpy;
@@ -1283,12 +1353,13 @@ extern "C" int pt_render_backward_reparam_vertices(pt_scene* s, const pt_render_
   return reparam_launch(s, r, p, opts, grad_image, nullptr, grad_vertices, rays, stream);
 }
 
-extern "C" int pt_render_jvp_reparam(pt_scene* s, const pt_render_desc* r, const pt_params* p,
-                                     const pt_reparam_opts* opts, const float* dir_translation, float* image,
-                                     float* image_dot, unsigned long long* rays, void* stream) {
+namespace {
+int jvp_reparam_launch(pt_scene* s, const pt_render_desc* r, const pt_params* p, const pt_reparam_opts* opts,
+                       const float* dir, bool vert, float* image, float* image_dot, unsigned long long* rays,
+                       void* stream) {
   RpOpts K;
   if (rp_opts(opts, K) != PT_OK) return PT_ERR_ARG;
-  if (!s || !r || !p || !dir_translation || !image_dot) return PT_ERR_ARG;
+  if (!s || !r || !p || !dir || !image_dot) return PT_ERR_ARG;
   LaunchArgs A;
   int st = fill_launch(s, r, p, A);
   if (st != PT_OK) return st;
@@ -1305,18 +1376,41 @@ extern "C" int pt_render_jvp_reparam(pt_scene* s, const pt_render_desc* r, const
   const size_t bytes = (size_t)A.n_cams * A.crop_w * A.crop_h * 3 * sizeof(float);
   if (image && cudaMemsetAsync(image, 0, bytes, cs) != cudaSuccess) return PT_ERR_CUDA;
   if (cudaMemsetAsync(image_dot, 0, bytes, cs) != cudaSuccess) return PT_ERR_CUDA;
-  const bool wide = s->dev.layout == PT_BVH_WIDE;
+  const int v = (s->dev.layout == PT_BVH_WIDE ? 2 : 0) | (vert ? 1 : 0);
   const dim3 gd((unsigned)grid), bd(block);
-  if (wide) reparam_jvp_kernel<PT_BVH_WIDE><<<gd, bd, 0, cs>>>(A, K, dir_translation, image, image_dot, rays);
-  else reparam_jvp_kernel<PT_BVH_BINARY><<<gd, bd, 0, cs>>>(A, K, dir_translation, image, image_dot, rays);
+  auto main = [&](auto kernel) { kernel<<<gd, bd, 0, cs>>>(A, K, dir, image, image_dot, rays); };
+  switch (v) {
+    case 0: main(reparam_jvp_kernel<PT_BVH_BINARY, false>); break;
+    case 1: main(reparam_jvp_kernel<PT_BVH_BINARY, true>); break;
+    case 2: main(reparam_jvp_kernel<PT_BVH_WIDE, false>); break;
+    default: main(reparam_jvp_kernel<PT_BVH_WIDE, true>); break;
+  }
   if (cudaGetLastError() != cudaSuccess) return PT_ERR_CUDA;
   if (K.edge_spp > 0) {
     const long long units = (long long)A.n_cams * E.per_cam * K.edge_spp;
     if (units > 0) {
       const dim3 eg((unsigned)((units + 127) / 128)), eb(128);
-      if (wide) edge_jvp_kernel<PT_BVH_WIDE><<<eg, eb, 0, cs>>>(A, K, E, dir_translation, image_dot, rays);
-      else edge_jvp_kernel<PT_BVH_BINARY><<<eg, eb, 0, cs>>>(A, K, E, dir_translation, image_dot, rays);
+      auto edges = [&](auto kernel) { kernel<<<eg, eb, 0, cs>>>(A, K, E, dir, image_dot, rays); };
+      switch (v) {
+        case 0: edges(edge_jvp_kernel<PT_BVH_BINARY, false>); break;
+        case 1: edges(edge_jvp_kernel<PT_BVH_BINARY, true>); break;
+        case 2: edges(edge_jvp_kernel<PT_BVH_WIDE, false>); break;
+        default: edges(edge_jvp_kernel<PT_BVH_WIDE, true>); break;
+      }
     }
   }
   return cudaGetLastError() == cudaSuccess ? PT_OK : PT_ERR_CUDA;
+}
+}  // namespace
+
+extern "C" int pt_render_jvp_reparam(pt_scene* s, const pt_render_desc* r, const pt_params* p,
+                                     const pt_reparam_opts* opts, const float* dir_translation, float* image,
+                                     float* image_dot, unsigned long long* rays, void* stream) {
+  return jvp_reparam_launch(s, r, p, opts, dir_translation, false, image, image_dot, rays, stream);
+}
+
+extern "C" int pt_render_jvp_reparam_vertices(pt_scene* s, const pt_render_desc* r, const pt_params* p,
+                                              const pt_reparam_opts* opts, const float* dir_vertices, float* image,
+                                              float* image_dot, unsigned long long* rays, void* stream) {
+  return jvp_reparam_launch(s, r, p, opts, dir_vertices, true, image, image_dot, rays, stream);
 }

@@ -143,25 +143,31 @@ class DeviceScene:
             abi.pt_render_backward_reparam_vertices(self.handle, desc, p, o, grad_image.contiguous(), g_vertices,
                                                     rays, stream)
 
-    def jvp_reparam(self, st: RenderSettings, dir_translation, cams=None, albedo=None, textures=None,
-                    roughness=None, env=None, seed=None, rays=None, with_image=True, **opts):
-        """Forward-mode reparameterized derivative (pt_render_jvp_reparam): (image or
-        None, image_dot), image_dot = d image / d eps with every shape moved by eps *
-        dir_translation[shape] ([n_shapes, 3]).  opts: pt_reparam_opts fields."""
+    def jvp_reparam(self, st: RenderSettings, dir_translation=None, cams=None, albedo=None, textures=None,
+                    roughness=None, env=None, seed=None, rays=None, with_image=True, dir_vertices=None, **opts):
+        """Forward-mode reparameterized derivative: (image or None, image_dot),
+        image_dot = d image / d eps with every shape moved by eps *
+        dir_translation[shape] ([n_shapes, 3], pt_render_jvp_reparam) or every
+        triangle corner by eps * dir_vertices[tri][corner] ([n_tris, 3, 3],
+        pt_render_jvp_reparam_vertices).  opts: pt_reparam_opts fields."""
         cams = list(cams) if cams is not None else self.cameras
         rows, cols = st.rows_cols()
         dev = self.albedo.device
-        d = torch.as_tensor(dir_translation, dtype=torch.float32, device=dev).contiguous()
-        if tuple(d.shape) != (self.n_shapes, 3):
-            raise ValueError(f"dir_translation must be [{self.n_shapes}, 3]")
+        if (dir_translation is None) == (dir_vertices is None):
+            raise ValueError("give exactly one of dir_translation and dir_vertices")
+        vert = dir_vertices is not None
+        shape = (self.scene.n_tris, 3, 3) if vert else (self.n_shapes, 3)
+        d = torch.as_tensor(dir_vertices if vert else dir_translation, dtype=torch.float32, device=dev).contiguous()
+        if tuple(d.shape) != shape:
+            raise ValueError(f"the direction must be {list(shape)}")
         img = torch.empty((len(cams), rows, cols, 3), device=dev, dtype=torch.float32) if with_image else None
         dot = torch.empty((len(cams), rows, cols, 3), device=dev, dtype=torch.float32)
         p = abi.params_struct(self.albedo if albedo is None else albedo,
                               self.textures if textures is None else textures,
                               self.roughness if roughness is None else roughness, env)
         desc = self._desc(cams, st, seed=seed)
-        abi.pt_render_jvp_reparam(self.handle, desc, p, abi.reparam_opts(**opts), d, img, dot, rays,
-                                  torch.cuda.current_stream(dev).cuda_stream)
+        fn = abi.pt_render_jvp_reparam_vertices if vert else abi.pt_render_jvp_reparam
+        fn(self.handle, desc, p, abi.reparam_opts(**opts), d, img, dot, rays, torch.cuda.current_stream(dev).cuda_stream)
         return img, dot
 
     # ------------------------------------------------------------------ wavefront variant

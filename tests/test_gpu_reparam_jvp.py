@@ -132,3 +132,60 @@ def test_jvp_reparam_translated_occluder_over_a_metallic_floor(lib):
     err = float((blur(dot) - blur(fd)).norm() / blur(fd).norm())
     print("forward derivative vs finite differences, relative L2 (1-pixel blur):", err)
     assert err < 0.35
+
+
+@pytest.mark.parametrize("name,tri,corner,axis", [("shadow", 4, 1, 0), ("shadow_conductor", 0, 2, 1),
+                                                  ("shadow_conductor", 1, 0, 0), ("occluder_sky_border", 1, 2, 0)])
+def test_jvp_reparam_vertices_parity_per_pixel(lib, oracle_mod, name, tri, corner, axis):
+    """Vertex mode: the per-pixel derivative along one corner coordinate (a
+    non-rigid motion: the triangle's normal turns, which the cosine and a glossy
+    floor's BSDF value follow) against the oracle's."""
+    from paper_2202_01284_gb300.render import DeviceScene, RenderSettings
+    sc = {"shadow": lambda: S.shadow_scene(width=32, height=32),
+          "shadow_conductor": lambda: S.shadow_scene(width=32, height=32, floor_bsdf=S.BSDF_CONDUCTOR),
+          "occluder_sky_border": lambda: S.occluder_sky(center=(0.5, 0.2), side=0.6, width=32, height=32)}[name]()
+    cam = sc.cameras[0]
+    d = np.zeros((sc.n_tris, 3, 3))
+    d[tri, corner, axis] = 1.0
+    st = RenderSettings(width=cam.width, height=cam.height, spp=8, max_depth=3, rr_depth=-1, seed=19)
+    ds = DeviceScene(sc)
+    _, dot = ds.jvp_reparam(st, dir_vertices=d, edge_spp=2)
+    torch.cuda.synchronize()
+    assert ds.status() == 0
+    dot = dot[0].cpu().numpy().astype(np.float64)
+    r = oracle_mod.render_in(cam, 8, 3, 19, -1, True)
+    _, _, ref = oracle_mod.grad_reparam(oracle_mod.OracleScene(sc), r, dot_param=9 * tri + 3 * corner + axis,
+                                        vertex=True, edge_spp=2)
+    c = cosine(dot.ravel(), ref.ravel())
+    rel = np.abs(dot - ref).max() / np.abs(ref).max()
+    print(f"{name} triangle {tri} corner {corner} axis {axis}: cosine {c:.7f} max rel {rel:.2e}")
+    assert c >= 0.9999 and rel < 5e-3
+
+
+def test_jvp_reparam_vertices_matches_reverse_mode_and_translations(lib):
+    """<grad_image, image_dot(direction)> against the reverse mode's <direction,
+    corner gradient> (same seed, glossy blend floor); and moving every corner of
+    each shape by that shape's vector gives the translation form's image."""
+    from paper_2202_01284_gb300.render import DeviceScene, RenderSettings
+    sc = S.shadow_scene(width=40, height=30, floor_bsdf=S.BSDF_BLEND)
+    ds = DeviceScene(sc)
+    st = RenderSettings(width=40, height=30, spp=6, max_depth=4, rr_depth=2, seed=37)
+    rng = np.random.default_rng(41)
+    dv = rng.normal(size=(sc.n_tris, 3, 3))
+    gi = rng.random((1, 30, 40, 3)).astype(np.float32) - 0.4
+    _, dot = ds.jvp_reparam(st, dir_vertices=dv, edge_spp=3)
+    g = torch.zeros((sc.n_tris, 3, 3), device="cuda")
+    gt = torch.zeros((3, 3), device="cuda")
+    ds.backward_reparam(st, torch.as_tensor(gi, device="cuda"), gt, g_vertices=g, edge_spp=3)
+    torch.cuda.synchronize()
+    lhs = float((dot.cpu().numpy().astype(np.float64) * gi).sum())
+    rhs = float((g.cpu().numpy().astype(np.float64) * dv).sum())
+    print("vertex mode: forward", lhs, "reverse", rhs)
+    assert abs(lhs - rhs) < 1e-4 * max(abs(lhs), abs(rhs))
+    dt = rng.normal(size=(3, 3))
+    _, dot_t = ds.jvp_reparam(st, dt, edge_spp=3)
+    _, dot_v = ds.jvp_reparam(st, dir_vertices=np.repeat(dt[sc.tri_shape][:, None, :], 3, axis=1), edge_spp=3)
+    torch.cuda.synchronize()
+    a, b = dot_t.cpu().numpy(), dot_v.cpu().numpy()
+    print("translations as corner motions: max diff", np.abs(a - b).max(), "scale", np.abs(a).max())
+    assert np.abs(a - b).max() < 1e-4 * np.abs(a).max()
