@@ -103,7 +103,7 @@ def lib():
             L.oracle_mlp_adam.argtypes = [vp, vp, vp, vp, ip, dp, dp, dp, dp, ip]
             L.oracle_nrc_encode.argtypes = [ip, vp, vp, vp]
             L.oracle_grad_reparam.argtypes = [vp, C.POINTER(RenderIn), vp, C.POINTER(ReparamIn), ip, vp, vp, ip, vp,
-                                              ip]
+                                              ip, vp]
             L.oracle_grad_reparam.restype = ip
             L.oracle_vmf.argtypes = [dp, dp, dp, vp]
             L.oracle_sphere_div.argtypes = [ip, vp, vp]
@@ -283,22 +283,27 @@ def _reparam_in(opts) -> ReparamIn:
                      int(o["edge_spp"]))
 
 
-def grad_reparam(osc: OracleScene, r: RenderIn, grad_image=None, dot_param=-1, threads=0, vertex=False, **opts):
+def grad_reparam(osc: OracleScene, r: RenderIn, grad_image=None, dot_param=-1, threads=0, vertex=False,
+                 dot_dir=None, **opts):
     """Gradients through reparameterized visibility, by forward mode.
 
     Returns (g, image [h, w, 3], image_dot [h, w, 3]): g = sum of grad_image * d image /
     d theta (zeros without grad_image) for one translation per shape (g [n_shapes, 3])
     or, with vertex=True, every triangle corner's position (g [n_tris, 3, 3]);
     image_dot = derivative along parameter `dot_param` (3 shape + axis, or 9 triangle +
-    3 corner + axis; zeros if < 0)."""
+    3 corner + axis; zeros if < 0), or along the direction dot_dir (the shape of g)."""
     o = _reparam_in(opts)
     h, w = _crop_shape(r)
     gi = None if grad_image is None else np.ascontiguousarray(grad_image, dtype=np.float64).reshape(h, w, 3)
     g = np.zeros((osc.scene.n_tris, 3, 3)) if vertex else np.zeros((osc.scene.n_shapes, 3))
     img = np.zeros((h, w, 3))
     dot = np.zeros((h, w, 3))
+    dd = None
+    if dot_dir is not None:
+        dd = np.ascontiguousarray(dot_dir, dtype=np.float64)
+        assert dd.shape == g.shape
     rc = lib().oracle_grad_reparam(osc.handle, C.byref(r), _ptr(gi), C.byref(o), int(bool(vertex)), _ptr(g),
-                                   _ptr(img), int(dot_param), _ptr(dot), threads)
+                                   _ptr(img), int(dot_param), _ptr(dot), threads, _ptr(dd))
     if rc != 0:
         raise ValueError("oracle_grad_reparam: bad options")
     return g, img, dot

@@ -2122,9 +2122,11 @@ static bool reparam_opts(const oracle_reparam_opts* o, ReparamOpts& op) {
 // position (vertex = 1: p = 9 triangle + 3 corner + axis, g [n_tris][3][3]), by
 // the reparameterized estimator above (every random number fixed, auxiliary ones
 // from the stream initseq | 2^62).  Optionally the image and its derivative along
-// parameter `dot_param`.
+// parameter `dot_param`, or (dot_dir non-NULL, one weight per parameter) along the
+// direction sum_p dot_dir[p] e_p.
 int oracle_grad_reparam(void* sc, const oracle_render_in* r, const double* grad_image, const oracle_reparam_opts* o,
-                        int vertex, double* g_out, double* image, int dot_param, double* image_dot, int n_threads) {
+                        int vertex, double* g_out, double* image, int dot_param, double* image_dot, int n_threads,
+                        const double* dot_dir) {
   const Scene& s = *(Scene*)sc;
   Camera cam = make_camera(*r);
   ReparamOpts op;
@@ -2133,6 +2135,9 @@ int oracle_grad_reparam(void* sc, const oracle_render_in* r, const double* grad_
   crop_of(*r, x0, y0, cw, ch);
   const int np = vertex ? 9 * s.n_tris : 3 * (int)s.shapes.size();
   std::vector<double> rows((size_t)(ch + 1) * np, 0.0);
+  // weight of parameter p in the image derivative
+  auto dot_w = [&](int p) { return dot_dir ? dot_dir[p] : (p == dot_param ? 1.0 : 0.0); };
+  const bool want_dot = image_dot && (dot_dir || (dot_param >= 0 && dot_param < np));
   // Pixel-edge term.  The warp that fixes the discontinuities also moves the
   // footprint of every pixel (a box of unit area in pixel coordinates): its
   // boundary moves with minus the warp's image-plane velocity, so pixel p gains
@@ -2144,7 +2149,7 @@ int oracle_grad_reparam(void* sc, const oracle_render_in* r, const double* grad_
   // image-border edges carry nothing (the warp vanishes there).
   std::vector<double> edge_dot((size_t)(ch + 1) * cw * 3, 0.0);  // horizontal edges: L v_n of dot_param
   if (image_dot) std::fill(image_dot, image_dot + (size_t)cw * ch * 3, 0.0);
-  if (op.edge_spp > 0 && (grad_image || (image_dot && dot_param >= 0 && dot_param < np))) {
+  if (op.edge_spp > 0 && (grad_image || want_dot)) {
     const double* gimg = grad_image;
     parallel_rows(y0, ch + 1, n_threads, [&](int Y) {
       double* grow = &rows[(size_t)(Y - y0) * np];
@@ -2171,7 +2176,7 @@ int oracle_grad_reparam(void* sc, const oracle_render_in* r, const double* grad_
             double gl = 0.0;
             for (int c = 0; c < 3; ++c) gl += ((gb ? gb[c] : 0.0) - (ga ? ga[c] : 0.0)) * l[c];
             grow[pw.first] += gl * vn;
-            if (pw.first == dot_param) sum_dot = sum_dot + l * vn;
+            sum_dot = sum_dot + l * (vn * dot_w(pw.first));
           }
         }
         return sum_dot;
@@ -2212,8 +2217,12 @@ int oracle_grad_reparam(void* sc, const oracle_render_in* r, const double* grad_
         acc.init(&s, &op, r->seed, cam, vertex != 0);
         V3 l = render_sample(s, cam, *r, px, py, k, acc, nullptr);
         for (int c = 0; c < 3; ++c) sum[c] += l[c];
-        if (dot_param >= 0 && dot_param < np)
-          for (int c = 0; c < 3; ++c) sum_dot[c] += acc.ldot[dot_param][c];
+        if (want_dot)
+          for (int p = 0; p < np; ++p) {
+            const double wp = dot_w(p);
+            if (wp != 0.0)
+              for (int c = 0; c < 3; ++c) sum_dot[c] += wp * acc.ldot[p][c];
+          }
         if (gi)
           for (int p = 0; p < np; ++p) grow[p] += (gi[0] * acc.ldot[p].x + gi[1] * acc.ldot[p].y +
                                                    gi[2] * acc.ldot[p].z) / r->spp;

@@ -221,6 +221,25 @@ def test_per_pixel_derivative_closed_form(oracle_mod, axis):
     assert e0 > 0.9
 
 
+def test_per_pixel_scaling_derivative_closed_form(oracle_mod):
+    """Vertex mode with a non-rigid motion: the square grows about its centre
+    (corner velocities p - c, the image derivative along that direction of all
+    corner coordinates); per pixel against the exact derivative of the coverage
+    image with respect to the side, times the side."""
+    cx, cy, depth, side, n = 0.15, 0.1, 3.0, 0.8, 32
+    sc = S.occluder_sky(center=(cx, cy), depth=depth, side=side, width=n, height=n)
+    c = np.array([cx, cy, -depth])
+    v = _corner_field(sc, 0, lambda p: p - c)
+    e = 1e-6
+    exact = side * (_SquareCoverage(n, n, side + e).image(cx, cy, depth)
+                    - _SquareCoverage(n, n, side - e).image(cx, cy, depth)) / (2 * e)
+    r = oracle_mod.render_in(sc.cameras[0], 1024, 4, 5, -1, True)
+    _, _, dot = oracle_mod.grad_reparam(oracle_mod.OracleScene(sc), r, vertex=True, dot_dir=v, edge_spp=256)
+    err = np.linalg.norm(dot[..., 0] - exact) / np.linalg.norm(exact)
+    print("scaling, per-pixel relative L2 error", err, "summed", dot[..., 0].sum(), exact.sum())
+    assert err < 0.15
+
+
 def test_per_pixel_derivative_across_the_image_border(oracle_mod):
     """A square that crosses the right image border and moves in depth: its edges
     slide through the image border, so the border pixels change by the flux through
