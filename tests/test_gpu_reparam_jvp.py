@@ -189,3 +189,26 @@ def test_jvp_reparam_vertices_matches_reverse_mode_and_translations(lib):
     a, b = dot_t.cpu().numpy(), dot_v.cpu().numpy()
     print("translations as corner motions: max diff", np.abs(a - b).max(), "scale", np.abs(a).max())
     assert np.abs(a - b).max() < 1e-4 * np.abs(a).max()
+
+
+@pytest.mark.parametrize("vertex", [False, True])
+def test_jvp_reparam_random_direction_parity(lib, oracle_mod, vertex):
+    """A random direction over every parameter (all shapes, or all corner coordinates:
+    the origins of vertex rays move too) against the oracle's derivative along the
+    same direction, per pixel."""
+    from paper_2202_01284_gb300.render import DeviceScene, RenderSettings
+    sc = S.shadow_scene(width=32, height=32, floor_bsdf=S.BSDF_BLEND)
+    cam = sc.cameras[0]
+    rng = np.random.default_rng(43)
+    d = rng.normal(size=(sc.n_tris, 3, 3) if vertex else (sc.n_shapes, 3))
+    st = RenderSettings(width=32, height=32, spp=6, max_depth=3, rr_depth=-1, seed=47)
+    ds = DeviceScene(sc)
+    _, dot = ds.jvp_reparam(st, dir_vertices=d, edge_spp=2) if vertex else ds.jvp_reparam(st, d, edge_spp=2)
+    torch.cuda.synchronize()
+    dot = dot[0].cpu().numpy().astype(np.float64)
+    r = oracle_mod.render_in(cam, 6, 3, 47, -1, True)
+    _, _, ref = oracle_mod.grad_reparam(oracle_mod.OracleScene(sc), r, vertex=vertex, dot_dir=d, edge_spp=2)
+    c = cosine(dot.ravel(), ref.ravel())
+    rel = np.abs(dot - ref).max() / np.abs(ref).max()
+    print(f"random direction (vertex={vertex}): cosine {c:.7f} max rel {rel:.2e}")
+    assert c >= 0.9999 and rel < 5e-3
