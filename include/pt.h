@@ -433,10 +433,10 @@ int pt_ckpt_backward(pt_scene* scene, const pt_render_desc* desc, const pt_param
  * grad_translation: device float [n_shapes][3], accumulated (+=).  rays: device
  * counter of the rays traced (radiance pass -- counted as the replay's path and
  * shadow rays, which it repeats --, replay, auxiliary and the warps' own center
- * rays), accumulated; NULL = not wanted.  desc.counters: node and triangle
- * visits of the replay kernel only.  desc: as for
- * pt_render_backward (the seed is used for both passes); block_size must be 0 or
- * 128; no cache, counters or per-sample outputs.  opts: NULL = defaults
+ * rays, the pixel-edge paths and their warps), accumulated; NULL = not wanted.
+ * desc.counters: node and triangle visits of the replay and pixel-edge kernels
+ * (not of the radiance pass).  desc: as for pt_render_backward (the seed is used
+ * for both passes); block_size must be 0 or 128; no cache or per-sample outputs.  opts: NULL = defaults
  * (pt_reparam_defaults).  Errors: PT_ERR_ARG (options out of range: 2 <= n_aux <=
  * 32, 0 < kappa <= 1e6, kernel_scale >= 1, 0 <= power <= 16, miss >= 0, eps > 0,
  * border >= 0, jackknife 0/1, 0 <= edge_spp <= 4096; with edge_spp > 0 the image's
