@@ -261,6 +261,24 @@ def test_per_pixel_derivative_across_the_image_border(oracle_mod):
     assert errs[4.0] > 0.2   # measured 0.25
 
 
+def test_moving_the_camera_is_moving_the_scene_the_other_way(oracle_mod):
+    """The identity behind the camera-translation gradient: with nothing at infinity
+    but a uniform (or no) environment, a render from a camera moved by d equals the
+    render of every shape moved by -d, sample for sample."""
+    sc = S.shadow_scene(width=24, height=24)
+    d = np.array([0.05, -0.03, 0.08])
+    a = oracle_mod.render(oracle_mod.OracleScene(sc), oracle_mod.render_in(sc.camera_moved(d).cameras[0], 8, 3, 11,
+                                                                             -1, True))
+    moved = sc.translated(-np.tile(d, (sc.n_shapes, 1)))
+    b = oracle_mod.render(oracle_mod.OracleScene(moved), oracle_mod.render_in(sc.cameras[0], 8, 3, 11, -1, True))
+    diff = np.abs(a - b)
+    print("camera vs scene motion: max diff", diff.max(), "pixels differing by > 1e-6:", int((diff > 1e-6).sum()))
+    # equal up to the float32 rounding of the moved vertices (measured 1.7e-8); a
+    # decision flipping at an edge would show as a few pixels far off
+    assert (diff > 1e-6).mean() < 0.01
+    assert np.median(diff) < 1e-7
+
+
 def test_camera_translation_matches_finite_differences(oracle_mod):
     """Moving the camera is moving every shape the opposite way (nothing lies at a
     finite distance outside the scene): minus the sum of all shapes' translation
