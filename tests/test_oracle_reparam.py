@@ -261,6 +261,18 @@ def test_per_pixel_derivative_across_the_image_border(oracle_mod):
     assert errs[4.0] > 0.2   # measured 0.25
 
 
+@pytest.mark.parametrize("vertex", [False, True])
+def test_reparameterization_is_the_identity_in_the_primal(oracle_mod, vertex):
+    """Sec. 4.7: a reparameterized ray returns the same direction in the primal, so
+    the image that comes with the reparameterized derivative is the plain render of
+    the same samples, exactly (its auxiliary rays draw from their own streams)."""
+    sc = S.shadow_scene(width=20, height=20, floor_bsdf=S.BSDF_BLEND)
+    r = oracle_mod.render_in(sc.cameras[0], 4, 4, 13, 2, True)
+    osc = oracle_mod.OracleScene(sc)
+    _, img, _ = oracle_mod.grad_reparam(osc, r, np.ones((20, 20, 3)), vertex=vertex)
+    np.testing.assert_array_equal(img, oracle_mod.render(osc, r))
+
+
 def test_moving_the_camera_is_moving_the_scene_the_other_way(oracle_mod):
     """The identity behind the camera-translation gradient: with nothing at infinity
     but a uniform (or no) environment, a render from a camera moved by d equals the
