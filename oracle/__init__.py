@@ -86,6 +86,7 @@ def lib():
             L.oracle_bsdf_sample.restype = ip
             L.oracle_bsdf_dfactors.argtypes = [ip, vp, vp, vp, vp]
             L.oracle_bsdf_normal_dlog.argtypes = [ip, vp, vp, vp, vp, vp, vp]
+            L.oracle_dual_toys.argtypes = [dp, ip, dp, vp]
             L.oracle_fresnel.argtypes = [dp, dp]
             L.oracle_fresnel.restype = dp
             L.oracle_env_pdf.argtypes = [vp, vp]
@@ -391,6 +392,13 @@ def bsdf_normal_dlog(bsdf, params, corners, n, wi, wo) -> np.ndarray:
     lib().oracle_bsdf_normal_dlog(bsdf, _ptr(params), _ptr(f64(corners)), _ptr(f64(n)), _ptr(f64(wi)),
                                   _ptr(f64(wo)), _ptr(out))
     return out.reshape(3, 3, 3)
+
+
+def dual_toys(x: float, n: int, a: float) -> np.ndarray:
+    """[x^n, its x-derivative, a exp(-a x), its a-derivative] by the dual-number classes."""
+    out = np.zeros(4)
+    lib().oracle_dual_toys(float(x), int(n), float(a), _ptr(out))
+    return out
 
 
 def fresnel(cos_i, eta):

@@ -2291,6 +2291,21 @@ void oracle_bsdf_normal_dlog(int bsdf, const double* params, const double* v, co
   for (int p = 0; p < 9; ++p)
     for (int c = 0; c < 3; ++c) out27[3 * p + c] = d[p][c];
 }
+// The dual-number classes on the paper's two toy programs (Fig. 1: x^n by repeated
+// multiplication; Fig. 6: the exponential density a exp(-a x) with x detached):
+// out = {x^n, d x^n / dx (Dual), a exp(-a x), d / da (D2)}.
+void oracle_dual_toys(double x, int n, double a, double* out) {
+  Dual dx(x, 1);
+  dx.d[0] = 1.0;
+  Dual y(1.0, 1);
+  for (int i = 0; i < n; ++i) y = y * dx;
+  out[0] = y.v;
+  out[1] = y.d[0];
+  D2 da{a, 1.0, 0.0};
+  D2 e = da * d2exp(da * (-x));
+  out[2] = e.v;
+  out[3] = e.a;
+}
 // Returns 1 and wo if sampling succeeded (non-delta BSDFs).
 int oracle_bsdf_sample(int bsdf, const double* params, const double* wi, double u3, double u4, double u5,
                        double* wo_out) {

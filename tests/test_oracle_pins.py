@@ -327,3 +327,16 @@ def test_texel_and_roughness_gradients(oracle_mod):
             vals.append((Lp - Lm) / (np.float64(tp[y, x, c]) - np.float64(tm[y, x, c])))
         rich = (4 * vals[1] - vals[0]) / 3
         assert abs(rich - g[y, x, c]) < 1e-7 * np.abs(flat).max()
+
+
+@pytest.mark.parametrize("x,n,a", [(1.7, 0, 0.5), (1.7, 1, 2.0), (-0.8, 5, 3.0), (2.5, 9, 0.1)])
+def test_dual_numbers_on_the_toy_programs(oracle_mod, x, n, a):
+    """The paper's AD toys (Fig. 1, x^n by repeated multiplication; Fig. 6, the
+    exponential density a exp(-a x) with x detached) through the oracle's dual
+    numbers, against their closed-form derivatives n x^(n-1) and
+    exp(-a x)(1 - a x)."""
+    y, dy, e, de = oracle_mod.dual_toys(x, n, a)
+    assert y == pytest.approx(x ** n, rel=1e-14)
+    assert dy == pytest.approx(n * x ** (n - 1) if n else 0.0, rel=1e-13, abs=1e-15)
+    assert e == pytest.approx(a * np.exp(-a * x), rel=1e-14)
+    assert de == pytest.approx(np.exp(-a * x) * (1.0 - a * x), rel=1e-13)
