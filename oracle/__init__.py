@@ -89,6 +89,9 @@ def lib():
             L.oracle_dual_toys.argtypes = [dp, ip, dp, vp]
             L.oracle_fresnel.argtypes = [dp, dp]
             L.oracle_fresnel.restype = dp
+            L.oracle_dielectric_sample.argtypes = [vp, vp, dp, dp, vp, vp]
+            L.oracle_dielectric_sample.restype = ip
+            L.oracle_ggx_terms.argtypes = [dp, dp, dp, vp]
             L.oracle_env_pdf.argtypes = [vp, vp]
             L.oracle_env_pdf.restype = dp
             L.oracle_frame.argtypes = [vp, vp, vp]
@@ -403,6 +406,22 @@ def dual_toys(x: float, n: int, a: float) -> np.ndarray:
 
 def fresnel(cos_i, eta):
     return lib().oracle_fresnel(cos_i, eta)
+
+
+def dielectric_sample(ng, wi, eta, u3):
+    """(refracted?, wo, radiance weight) of the integrator's dielectric event."""
+    wo = np.zeros(3)
+    w = np.zeros(1)
+    refr = lib().oracle_dielectric_sample(_ptr(np.asarray(ng, np.float64)), _ptr(np.asarray(wi, np.float64)),
+                                          float(eta), float(u3), _ptr(wo), _ptr(w))
+    return bool(refr), wo, float(w[0])
+
+
+def ggx_terms(alpha, cos_h, cos_w):
+    """(D(cos_h), G1(cos_w)) of the conductor lobe at roughness alpha."""
+    out = np.zeros(2)
+    lib().oracle_ggx_terms(float(alpha), float(cos_h), float(cos_w), _ptr(out))
+    return float(out[0]), float(out[1])
 
 
 def env_pdf(osc: OracleScene, d):

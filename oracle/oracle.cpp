@@ -556,6 +556,29 @@ double fresnel_dielectric(double cos_i, double eta, double& cos_t) {
   return 0.5 * (rs * rs + rp * rp);
 }
 
+// One scattering event at a smooth dielectric interface with geometric normal ng
+// (oriented outward, so that a ray arriving against it enters the medium of
+// relative index eta_shape) and incident direction wi_w (pointing away from the
+// surface).  Reflection is chosen with probability F (uniform u3 < F) and keeps
+// the radiance; refraction follows Snell's law and scales radiance by 1/eta^2,
+// eta being the index of the far side over the near side (radiance mode).
+// Returns true if the ray refracted; wo is the outgoing direction.
+bool dielectric_scatter(V3 ng, V3 wi_w, double eta_shape, double u3, V3& wo, double& weight) {
+  bool entering = dot(ng, wi_w) > 0.0;
+  V3 n = entering ? ng : -ng;
+  double eta = entering ? eta_shape : 1.0 / eta_shape;
+  double cos_i = dot(n, wi_w), cos_t;
+  double F = fresnel_dielectric(cos_i, eta, cos_t);
+  if (u3 < F) {
+    wo = n * (2.0 * cos_i) - wi_w;
+    weight = 1.0;
+    return false;
+  }
+  wo = -wi_w * (1.0 / eta) + n * (cos_i / eta - cos_t);
+  weight = 1.0 / (eta * eta);
+  return true;
+}
+
 // ---------------------------------------------------------------- emitters
 V3 env_lookup(const Scene& s, V3 d, int& px, int& py) {
   double phi = std::atan2(d.z, d.x);
@@ -800,22 +823,10 @@ V3 render_sample(const Scene& s, const Camera& cam, const oracle_render_in& r, i
     }
 
     if (sh.bsdf == BSDF_DIELECTRIC) {
-      bool entering = cos_front > 0.0;
-      V3 n = entering ? ng : -ng;
-      double eta = entering ? sh.eta : 1.0 / sh.eta;
-      double cos_i = dot(n, wi_w), cos_t;
-      double F = fresnel_dielectric(cos_i, eta, cos_t);
       V3 wo;
       double weight;
-      if (u[3] < F) {
-        wo = n * (2.0 * cos_i) - wi_w;
-        weight = 1.0;
-        dh.add(2);
-      } else {
-        wo = -wi_w * (1.0 / eta) + n * (cos_i / eta - cos_t);
-        weight = 1.0 / (eta * eta);
-        dh.add(3);
-      }
+      bool refracted = dielectric_scatter(ng, wi_w, sh.eta, u[3], wo, weight);
+      dh.add(refracted ? 3 : 2);
       dh.add(0xfffffffeu);  // no light sample at a delta vertex
       beta = beta * weight;
       acc.scatter_delta(weight);
@@ -2330,6 +2341,24 @@ void oracle_bsdf_dfactors(int bsdf, const double* params, const double* wi, cons
     out6[c] = df.d_alb[c];
     out6[3 + c] = df.d_alpha[c];
   }
+}
+// The dielectric scattering event of the integrator: returns 1 on refraction,
+// 0 on reflection; wo_out the outgoing direction, *weight_out the radiance factor.
+int oracle_dielectric_sample(const double* ng, const double* wi, double eta, double u3, double* wo_out,
+                             double* weight_out) {
+  V3 wo;
+  double w;
+  bool refr = dielectric_scatter(V3(ng[0], ng[1], ng[2]), V3(wi[0], wi[1], wi[2]), eta, u3, wo, w);
+  wo_out[0] = wo.x;
+  wo_out[1] = wo.y;
+  wo_out[2] = wo.z;
+  *weight_out = w;
+  return refr ? 1 : 0;
+}
+// The GGX terms of the conductor lobe: out2 = {D(cos_h), G1(cos_w)} (no sign tests).
+void oracle_ggx_terms(double alpha, double cos_h, double cos_w, double* out2) {
+  out2[0] = ggx_D<double>(alpha, cos_h);
+  out2[1] = ggx_G1<double>(alpha, cos_w);
 }
 double oracle_fresnel(double cos_i, double eta) {
   double ct;

@@ -563,6 +563,33 @@ def lit_plane(albedo: float = 0.6, env_radiance: float = 1.0, env_size=(64, 32),
                  name="lit_plane", **st)
 
 
+def glass_sphere(eta: float = 1.5, env_radiance: float = 1.0, inside: bool = False, level: int = 3,
+                 width=16, height=16) -> Scene:
+    """A closed smooth-dielectric icosphere of radius 1 (outward winding) at the
+    origin under a uniform environment of radiance L.
+
+    With `inside`, the camera sits at the centre, inside the glass; otherwise it
+    looks at the sphere from outside, so that the image shows the sphere and the
+    sky around it.  Transport through a lossless interface keeps L / n^2, so a
+    path that leaves into the sky carries L (camera outside) or eta^2 L (camera
+    inside the glass).
+    """
+    V, F = icosphere(level)
+    tris = V[F]
+    st = _shape_table(1)
+    st["bsdf"][0] = BSDF_DIELECTRIC
+    st["eta"][0] = eta
+    env = np.full((16, 32, 4), env_radiance, np.float32)
+    env[..., 3] = 1.0
+    if inside:
+        cam = Camera((0.0, 0.0, 0.0), (0.3, 0.2, -1.0), (0.0, 1.0, 0.0), 90.0, width, height)
+    else:
+        cam = Camera((0.0, 0.4, 3.5), (0.0, 0.0, 0.0), (0.0, 1.0, 0.0), 45.0, width, height)
+    return Scene(vertices=np.asarray(tris, np.float32), uvs=np.zeros((len(F), 3, 2), np.float32),
+                 tri_shape=np.zeros(len(F), np.int32), albedo=np.zeros((0, 3), np.float32), textures=[],
+                 roughness=np.zeros(0, np.float32), env=env, cameras=[cam], name="glass_sphere", **st)
+
+
 def occluder_sky(center=(0.15, 0.1), depth=3.0, side=0.4, env_radiance=1.0, width=64, height=64,
                  vfov_deg=40.0) -> Scene:
     """A black square facing a pinhole camera under a uniform environment.
