@@ -292,6 +292,9 @@ int pt_render_batch(const pt_job* jobs, int n_jobs, const pt_batch_opts* opts, v
  *   - The first call on a device (with that device current) looks up the array's
  *     device address with cudaGetSymbolAddress; make that first call before any
  *     stream capture.
+ *   - A `stream` that is capturing is refused with PT_ERR_STATE: the call copies its
+ *     tables from host memory that it frees on return.  pt_batch_create +
+ *     pt_batch_run is the form to capture.
  *   - Every call reuses the same array, which keeps the last call's contents; the
  *     work counters are cleared on `stream` before each launch.  Calls whose work
  *     overlaps on the GPU (other streams, or other host threads) race on the array:

@@ -658,6 +658,14 @@ int noalloc_scratch(void** out) {
 extern "C" int pt_render_batch_noalloc(const pt_job* jobs, int n_jobs, const pt_batch_opts* o, void* stream) {
   if (!jobs || n_jobs <= 0) return PT_ERR_ARG;
   if (n_jobs > PT_NOALLOC_MAX_JOBS) return PT_ERR_ARG;
+  // The tables below are copied from host vectors that die on return; recorded into
+  // a graph, those copies would point at freed host memory.
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing((cudaStream_t)stream, &cap) != cudaSuccess) {
+    cudaGetLastError();
+    return PT_ERR_CUDA;
+  }
+  if (cap != cudaStreamCaptureStatusNone) return PT_ERR_STATE;
   pt_batch_opts opts{4, 4, 4, 128};
   if (o) opts = *o;
   if (opts.tile < 1 || opts.tile > 256 || opts.ctas_per_sm < 1 || opts.ctas_per_sm > 8) return PT_ERR_ARG;
@@ -734,8 +742,10 @@ extern "C" int pt_render_batch_noalloc(const pt_job* jobs, int n_jobs, const pt_
   if (cudaMemcpyAsync(d_jobs, args.data(), sizeof(LaunchArgs) * n_jobs, cudaMemcpyHostToDevice, cs) != cudaSuccess ||
       cudaMemcpyAsync(d_items, sorted.data(), sizeof(BatchItem) * sorted.size(), cudaMemcpyHostToDevice, cs) !=
           cudaSuccess ||
-      cudaMemsetAsync(d_queue, 0, 2 * sizeof(unsigned), cs) != cudaSuccess)
+      cudaMemsetAsync(d_queue, 0, 2 * sizeof(unsigned), cs) != cudaSuccess) {
+    cudaGetLastError();  // clear it, so that the next call does not report it
     return PT_ERR_CUDA;
+  }
   int dev = 0, sms = 152;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);

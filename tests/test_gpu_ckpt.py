@@ -62,7 +62,7 @@ def test_ckpt_gradients_match_oracle_and_prb(lib, oracle_mod):
     c_t, c_r = cosine(gt.cpu().numpy()[..., :3], gt_ref[0][..., :3]), cosine(gr.cpu().numpy(), gr_ref)
     c_tp, c_rp = cosine(gt.cpu().numpy(), gt_p.cpu().numpy()), cosine(gr.cpu().numpy(), gr_p.cpu().numpy())
     print(f"ckpt vs oracle: tex {c_t:.7f} rough {c_r:.7f}; vs PRB: tex {c_tp:.9f} rough {c_rp:.9f}")
-    assert c_r >= GRAD_COSINE and c_t >= 0.999
+    assert c_r >= GRAD_COSINE and c_t >= GRAD_COSINE
     assert c_tp >= 0.99999 and c_rp >= 0.99999
     rel = (gr - gr_p).abs().max().item() / gr_p.abs().max().item()
     assert rel < 1e-3
@@ -89,7 +89,7 @@ def test_ckpt_env_gradients_and_roulette(lib, oracle_mod):
     c_t = cosine(gt.cpu().numpy()[..., :3], gt_ref[0][..., :3])
     c_r = cosine(gr.cpu().numpy(), gr_ref)
     print(f"spheres ckpt vs oracle: env {c_e:.8f} tex {c_t:.7f} rough {c_r:.7f}")
-    assert c_e >= GRAD_COSINE and c_r >= GRAD_COSINE and c_t >= 0.999
+    assert c_e >= GRAD_COSINE and c_r >= GRAD_COSINE and c_t >= GRAD_COSINE
 
 
 def test_ckpt_capacity_checks(lib):

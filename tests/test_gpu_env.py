@@ -101,7 +101,7 @@ def test_env_override_and_jvp(lib, oracle_mod):
     ok2 = rel_ok(img2[0].cpu().numpy(), ref2).all(axis=-1)
     okd = rel_ok(dot[0].cpu().numpy(), ref_dot).all(axis=-1)
     print("clean", clean.mean(), "override ok", ok2[clean].mean(), "env jvp ok", okd[clean].mean())
-    assert clean.mean() >= 0.99
+    assert ok2.mean() >= PIXEL_FRACTION and okd.mean() >= PIXEL_FRACTION  # all pixels
     assert ok2[clean].mean() >= PIXEL_FRACTION
     assert okd[clean].mean() >= PIXEL_FRACTION
 

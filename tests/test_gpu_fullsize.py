@@ -22,6 +22,15 @@ torch = pytest.importorskip("torch")
 
 CROPS = [(496, 40, 16, 16), (400, 540, 16, 16), (600, 600, 16, 16), (300, 720, 16, 16)]
 
+# Path-divergence budget at this workload (64 samples of up to 8 vertices per pixel):
+# measured 6 divergent pixels of 1024 (0.59 %), every one of them the only kind of
+# pixel that misses 1e-4; all pixels together 0.9941.  The 0.1 % budget holds on the
+# 36-triangle box (all pixels 1.0); here FP32-versus-FP64 decisions at triangle and
+# texel edges flip about 1 path in 10^4, and a pixel of 64 such paths takes one
+# flip with probability near 0.6 %.
+MAX_DIVERGENT_PIXELS = 12
+ALL_PIXEL_FRACTION = 0.99
+
 
 @pytest.fixture(scope="module")
 def full():
@@ -41,7 +50,7 @@ def test_fullsize_forward_parity_on_crops(full, oracle_mod):
     sc, ds, st = full
     img = ds.forward(st)[0].cpu().numpy()
     osc = oracle_mod.OracleScene(sc)
-    clean_ok, clean_n = 0, 0
+    clean_ok, clean_n, all_ok, all_n, divergent = 0, 0, 0, 0, 0
     for crop in CROPS:
         x0, y0, w, h = crop
         ref, _, refh = oracle_mod.render(osc, oracle_mod.render_in(sc.cameras[0], 64, 8, 11, 3, True, crop=crop),
@@ -49,11 +58,18 @@ def test_fullsize_forward_parity_on_crops(full, oracle_mod):
         _, _, gh = ds.forward(replace(st, crop=crop), per_sample=True)
         clean = (gh[0].cpu().numpy().view(np.uint32) == refh.astype(np.uint32)).all(axis=-1)
         ok = rel_ok(img[y0:y0 + h, x0:x0 + w], ref).all(axis=-1)
-        print(crop, "clean", clean.mean(), "ok on clean", ok[clean].mean(), "ok all", ok.mean())
-        assert clean.mean() >= 0.95
+        print(crop, "clean", clean.mean(), "ok on clean", ok[clean].mean(), "ok all", ok.mean(),
+              "divergent", int((~clean).sum()), "of", clean.size)
         clean_ok += int(ok[clean].sum())
         clean_n += int(clean.sum())
+        all_ok += int(ok.sum())
+        all_n += int(ok.size)
+        divergent += int((~clean).sum())
+    print(f"full-size forward: all pixels {all_ok / all_n:.5f}, clean pixels {clean_ok / clean_n:.5f}, "
+          f"divergent pixels {divergent} of {all_n}")
     assert clean_ok / clean_n >= PIXEL_FRACTION
+    assert divergent <= MAX_DIVERGENT_PIXELS
+    assert all_ok / all_n >= ALL_PIXEL_FRACTION
 
 
 def test_fullsize_adjoint_parity_on_crops(full, oracle_mod):
@@ -80,4 +96,4 @@ def test_fullsize_adjoint_parity_on_crops(full, oracle_mod):
     rel_r = np.abs(g_rough.cpu().numpy() - gr_ref).max() / np.abs(gr_ref).max()
     print(f"full-size adjoint: texture cosine {c_t:.7f}, roughness cosine {c_r:.9f} (max rel {rel_r:.2e})")
     assert c_r >= GRAD_COSINE
-    assert c_t >= 0.999  # texel-edge flips between FP32 and FP64 move single terms
+    assert c_t >= GRAD_COSINE  # measured 0.9999981

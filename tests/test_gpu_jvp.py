@@ -68,8 +68,9 @@ def test_cornell_albedo_jvp_parity(lib, oracle_mod, layout):
     clean = _clean_pixels(ds, sc, st, oracle_mod)
     ok_img = rel_ok(img, ref_img).all(axis=-1)
     ok_dot = rel_ok(dot, ref_dot).all(axis=-1)
-    print("clean", clean.mean(), "img ok", ok_img[clean].mean(), "dot ok", ok_dot[clean].mean())
-    assert clean.mean() >= 0.99
+    print("clean", clean.mean(), "img ok", ok_img[clean].mean(), "dot ok", ok_dot[clean].mean(),
+          "all pixels: img", ok_img.mean(), "dot", ok_dot.mean(), "divergent", int((~clean).sum()), "of", clean.size)
+    assert ok_img.mean() >= PIXEL_FRACTION and ok_dot.mean() >= PIXEL_FRACTION  # all pixels (measured 1.0)
     assert ok_img[clean].mean() >= PIXEL_FRACTION
     assert ok_dot[clean].mean() >= PIXEL_FRACTION
     # the primal of the JVP pass is the forward render
@@ -94,8 +95,10 @@ def test_cornell96_texel_and_roughness_jvp(lib, oracle_mod):
     _, ref_dot = oracle_mod.render_jvp(osc, r, t_albedo=va, t_textures=[vt])
     clean = _clean_pixels(ds, sc, st, oracle_mod)
     ok = rel_ok(dot, ref_dot).all(axis=-1)
-    print("texel jvp: clean", clean.mean(), "ok", ok[clean].mean())
-    assert clean.mean() >= 0.98
+    print("texel jvp: clean", clean.mean(), "ok", ok[clean].mean(), "all", ok.mean(),
+          "divergent", int((~clean).sum()), "of", clean.size)
+    # all pixels: measured 0.99557 (40 divergent of 7680: texel edges of the 2048^2 atlas at 8 spp x 6 vertices)
+    assert ok.mean() >= 0.99 and (~clean).sum() <= 80
     assert ok[clean].mean() >= PIXEL_FRACTION
     # roughness: signed derivative, judged by cosine over the crop
     vr = rng.normal(size=sc.roughness.shape)
@@ -125,8 +128,9 @@ def test_spheres_jvp_parity(lib, oracle_mod):
                                        t_textures=vt)
     clean = _clean_pixels(ds, sc, st, oracle_mod)
     ok = rel_ok(dot, ref_dot).all(axis=-1)
-    print("spheres jvp: clean", clean.mean(), "ok", ok[clean].mean())
-    assert clean.mean() >= 0.95
+    print("spheres jvp: clean", clean.mean(), "ok", ok[clean].mean(), "all", ok.mean(),
+          "divergent", int((~clean).sum()), "of", clean.size)
+    assert ok.mean() >= PIXEL_FRACTION  # all pixels (measured 0.99967, 1 divergent of 3072)
     assert ok[clean].mean() >= PIXEL_FRACTION
 
 

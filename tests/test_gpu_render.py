@@ -190,6 +190,9 @@ def test_cornell96_forward_and_gradients(lib, oracle_mod, layout):
     assert rep["matched_bad"] <= rep["n"] // 10000, rep
     assert rep["divergent_fraction"] <= 2e-3, rep
     assert rep["clean_pixel_fraction_ok"] >= PIXEL_FRACTION, rep
+    # all pixels: measured 0.99506 (186 divergent pixels of 16384, each one of them the
+    # only kind that misses 1e-4: 16 samples x 6 vertices of texel lookups per pixel)
+    assert rep["all_pixel_fraction_ok"] >= 0.99 and rep["divergent_pixels"] <= 300, rep
     # gradients: oracle tape on the same crop, correlated seed
     tgt = sc.with_params(textures=[S.cornell96_target_texture(sc.textures[0])])
     T = _oracle_render(oracle_mod, tgt, _settings(tgt, spp=16, max_depth=6, seed=23, crop=crop))
@@ -210,7 +213,7 @@ def test_cornell96_forward_and_gradients(lib, oracle_mod, layout):
         c_r = cosine(gr.cpu().numpy(), gr_ref)
         print(f"agg={agg} texture grad cosine {c_t:.7f} roughness grad cosine {c_r:.7f}")
         assert c_r >= GRAD_COSINE
-        assert c_t >= 0.999  # texel flips (path-divergence at texel edges) move single terms
+        assert c_t >= GRAD_COSINE  # measured 0.9999568: texel-edge flips move single terms
         assert np.all(gt.cpu().numpy()[..., 3] == 0)
 
 
@@ -227,6 +230,7 @@ def test_spheres_forward_parity(lib, oracle_mod, layout):
     assert rep["matched_bad"] <= max(2, rep["n"] // 10000), rep
     assert rep["divergent_fraction"] < 5e-3, rep
     assert rep["clean_pixel_fraction_ok"] >= PIXEL_FRACTION, rep
+    assert rep["all_pixel_fraction_ok"] >= PIXEL_FRACTION, rep  # measured 0.99967
 
 
 def test_counters_and_status(lib):
@@ -275,5 +279,5 @@ def test_split_prb_matches_fused_and_oracle(lib, oracle_mod, layout):
     c_t, c_r = cosine(gt1[..., :3], gt_ref[0][..., :3]), cosine(gr1, gr_ref)
     c_tf, c_rf = cosine(gt1, gt0), cosine(gr1, gr0)
     print(f"split PRB vs oracle: tex {c_t:.7f} rough {c_r:.7f}; vs fused: tex {c_tf:.9f} rough {c_rf:.9f}")
-    assert c_r >= GRAD_COSINE and c_t >= 0.999
+    assert c_r >= GRAD_COSINE and c_t >= GRAD_COSINE
     assert c_tf >= 0.99999 and c_rf >= 0.99999

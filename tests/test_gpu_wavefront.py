@@ -134,7 +134,7 @@ def test_wavefront_gradients(lib, oracle_mod):
         c_rm = cosine(gr.cpu().numpy(), gr_m.cpu().numpy())
         print(f"calls={calls}: vs oracle tex {c_t:.7f} rough {c_r:.7f}; vs megakernel tex {c_tm:.9f} rough {c_rm:.9f}")
         assert c_r >= GRAD_COSINE
-        assert c_t >= 0.999  # texel-edge flips between FP32 and FP64, as for the megakernel
+        assert c_t >= GRAD_COSINE  # measured 0.9999658 (texel-edge flips, as for the megakernel)
         assert c_tm >= 0.99999 and c_rm >= 0.99999
         assert np.all(gt.cpu().numpy()[..., 3] == 0)
 

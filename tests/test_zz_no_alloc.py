@@ -36,10 +36,28 @@ def _reset(jobs):
         for g in j.g_textures:
             g.zero_()
         j.g_roughness.zero_()
+        if j.g_env is not None:
+            j.g_env.zero_()
 
 
 def _snapshot(jobs):
-    return [(j.image.clone(), [g.clone() for g in j.g_textures], j.g_roughness.clone()) for j in jobs]
+    return [(j.image.clone(), [g.clone() for g in j.g_textures], j.g_roughness.clone(),
+             None if j.g_env is None else j.g_env.clone()) for j in jobs]
+
+
+def _cos(g, e):
+    return float((g * e).sum() / (g.norm() * e.norm() + 1e-30))
+
+
+def _check(jobs, want, tag):
+    for j, (img, gts, gr, ge) in zip(jobs, want):
+        assert torch.allclose(j.image, img, rtol=1e-6, atol=0), tag
+        for g, e in zip(j.g_textures, gts):
+            assert _cos(g, e) > 0.9999, (tag, _cos(g, e))
+        assert torch.allclose(j.g_roughness, gr, rtol=1e-3, atol=1e-7), tag
+        if ge is not None:
+            assert float(ge.abs().sum()) > 0
+            assert _cos(j.g_env, ge) > 0.9999, (tag, _cos(j.g_env, ge))
 
 
 def test_noalloc_batch_matches_allocating_batch():
@@ -56,13 +74,58 @@ def test_noalloc_batch_matches_allocating_batch():
         _reset(jobs)
         abi.pt_render_batch_noalloc([j.struct() for j in jobs], opts, stream)
         torch.cuda.synchronize()
-        for j, (img, gts, gr) in zip(jobs, want):
-            assert torch.allclose(j.image, img, rtol=1e-6, atol=0), call
-            for g, e in zip(j.g_textures, gts):
-                cos = float((g * e).sum() / (g.norm() * e.norm() + 1e-30))
-                assert cos > 0.9999, (call, cos)
-            assert torch.allclose(j.g_roughness, gr, rtol=1e-3, atol=1e-7), call
+        _check(jobs, want, call)
         assert float(sum(j.g_roughness.abs().sum() for j in jobs)) > 0
+
+
+def test_noalloc_small_call_after_large_and_env_gradients():
+    """A one-job call with a small image after the three-job call must not pick up
+    the larger call's job table or work lists left in the shared array; a job
+    with environment-map gradients takes the env-gradient kernel variant.  Once
+    warmed up, a call leaves the device's free memory unchanged."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2202_01284_gb300 import batch
+    abi, scenes, jobs = _setup()
+    opts = abi.pt_batch_opts(4, 4, 4, 128)
+    stream = torch.cuda.current_stream().cuda_stream
+    ds = scenes[1]
+    small = batch.Job(ds, S.Camera((0.5, 2.0, 6.0), (0.0, 0.4, 0.0), (0.0, 1.0, 0.0), 45.0, 9, 7), 4,
+                      seed=77, backward_seed=78, target=torch.full((7, 9, 3), 0.2, device="cuda"),
+                      g_textures=[torch.zeros_like(t) for t in ds.textures],
+                      g_roughness=torch.zeros_like(ds.roughness),
+                      g_env=torch.zeros((ds.scene.env.shape[0], ds.scene.env.shape[1], 4), device="cuda"))
+    _reset([small])
+    abi.pt_render_batch([small.struct()], opts, stream)
+    torch.cuda.synchronize()
+    want = _snapshot([small])
+    for _ in range(2):                      # large call, then the small one
+        abi.pt_render_batch_noalloc([j.struct() for j in jobs], opts, stream)
+        _reset([small])
+        abi.pt_render_batch_noalloc([small.struct()], opts, stream)
+        torch.cuda.synchronize()
+        _check([small], want, "small after large")
+    free0, _ = torch.cuda.mem_get_info()
+    abi.pt_render_batch_noalloc([j.struct() for j in jobs], opts, stream)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+
+
+def test_noalloc_refuses_a_capturing_stream():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    abi, scenes, jobs = _setup()
+    opts = abi.pt_batch_opts(4, 4, 4, 128)
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    codes = []
+    with torch.cuda.graph(g, stream=s):
+        try:
+            abi.pt_render_batch_noalloc([j.struct() for j in jobs], opts, s.cuda_stream)
+        except abi.PtError as e:
+            codes.append(e.code)
+    assert codes == [abi.PT_ERR_STATE]
 
 
 def test_noalloc_rejects_requests_beyond_its_limits():
