@@ -37,6 +37,26 @@ FLOPS_PER_NODE = {"binary": 44,   # two child slab tests: 12 FMA (24 flops), 10 
                                   # decode: 3 scale + 3 offset products excluded)
 FLOPS_PER_TRI = 45      # Moller-Trumbore: 2 cross, 4 dot, 1 div, 4 mul, 3 sub (FMA = 2 flops)
 NODE_BYTES = {"binary": 64, "wide": 80}  # bytes fetched per node visit
+TRI_BYTES, TEX_BYTES, ENV_BYTES = 48, 16, 16  # per triangle test, texture lookup, env-map lookup
+# FP32 operations per shaded vertex (FMA = 2), counted from the kernel's per-vertex
+# formulas: hit point, barycentric uv, geometric normal, frame and local directions
+# (~85 for every type); the light sample, BSDF value and pdf toward it, MIS weight and
+# shadow-ray offset (none at a smooth dielectric); the BSDF sample with its value and
+# pdf, the throughput update and the continuation-ray offset.  GGX adds the half
+# vector, D, two Smith G1 and three Schlick terms to every evaluation.
+SHADE_FLOPS = {8: 250, 9: 415, 10: 130, 11: 450}   # counter index -> diffuse, conductor, dielectric, blend
+ENV_FLOPS = 60          # direction -> env pixel (atan2, acos), its pdf and the MIS weight
+GRAD_BYTES_TEX, GRAD_BYTES_OTHER = 16, 4  # one float4 texel / one float per gradient term (before aggregation)
+
+
+def counted_work(c, bvh):
+    """(FP32 flops, bytes through L2) of the counted work c (PT_CNT_* array)."""
+    c = [int(x) for x in c]
+    flops = (FLOPS_PER_NODE[bvh] * c[3] + FLOPS_PER_TRI * c[4] + sum(v * c[k] for k, v in SHADE_FLOPS.items())
+             + ENV_FLOPS * c[12])
+    nbytes = NODE_BYTES[bvh] * c[3] + TRI_BYTES * c[4] + TEX_BYTES * c[5] + ENV_BYTES * c[12]
+    grad_bytes = GRAD_BYTES_TEX * c[13] + GRAD_BYTES_OTHER * (c[7] - c[13])
+    return flops, nbytes, grad_bytes
 
 
 def alu_roofline(kernel, counters, bvh, ms, clk, note=""):
@@ -53,17 +73,14 @@ def alu_roofline(kernel, counters, bvh, ms, clk, note=""):
             "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": None,
             "work": f"{FLOPS_PER_NODE[bvh]}/node visit + {FLOPS_PER_TRI}/triangle test (counted launch){note}",
             "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 x median SM clock {mhz} MHz"}
-# DRAM bytes (read + write) per full-size launch of the production kernels, from one
-# one-pass ncu capture of the step (profiles/launches_spheres196k_1024px_64spp.md,
-# profiles/reparam_launches_spheres196k_1024px_16spp.md);
-# cleared whenever the kernels change until they are captured again.
-DRAM_TRAFFIC_PER_LAUNCH = {"wide": {"forward_kernel": 2_960_000_000 + 14_300_000_000,
-                                    "replay_kernel": 2_030_000_000 + 4_620_000_000,
-                                    "radiance_kernel": 4_190_000_000 + 16_060_000_000,
-                                    "adjoint_kernel": 1_775_000_000 + 11_908_000_000,
-                                    "jvp_kernel": 1_325_000_000 + 7_153_000_000,
-                                    # bench.py --reparam (1024^2, 16 spp; profiles/reparam_launches_...)
-                                    "reparam_kernel": 12_440_000_000 + 23_310_000_000}}
+# DRAM bytes (read + write) per counted ray of a production kernel, from a one-kernel,
+# few-launch ncu capture of the 256x256 case (profiles/), scaled to a full-size launch
+# by its counted rays (the per-ray traffic of these kernels does not depend on the
+# image size: the scene and texture are the same and the per-sample state scales with
+# the rays).  A kernel changed since its capture has no entry.
+TRAFFIC_PER_RAY = {"wide": {}}
+TRAFFIC_BASIS = ("ncu dram__bytes_read.sum + dram__bytes_write.sum per counted ray, one kernel at 256x256 "
+                 "(profiles/), times the launch's counted rays")
 
 
 def parse():
@@ -73,12 +90,16 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-cache-line", action="store_true",
+                    help="skip the equal-time cache-vs-plain comparison of the default line")
     ap.add_argument("--dispatch", type=int, default=0)
     ap.add_argument("--lanes", type=int, default=0)
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--tex-aggregate", type=int, default=0)
     ap.add_argument("--prb-mode", type=int, default=0, help="backward: 0 auto (split), 1 fused PRB, 2 split")
     ap.add_argument("--bvh", default="wide", choices=["wide", "binary"])
+    ap.add_argument("--schedule", type=int, default=0,
+                    help="0 auto (persistent replay, static forward), 1 persistent lanes pulling units, 2 static")
     ap.add_argument("--cache", action="store_true",
                     help="radiance-cache experiment: equal-time MSE, cache-terminated vs plain PT (own JSON line)")
     ap.add_argument("--cache-warmup-frames", type=int, default=300)
@@ -174,11 +195,11 @@ def settings(args, seed):
         return RenderSettings(width=256, height=256, spp=64, max_depth=WORKLOAD["max_depth"],
                               rr_depth=WORKLOAD["rr_depth"], seed=seed, dispatch=args.dispatch,
                               lanes_per_pixel=args.lanes, block_size=args.block, tex_aggregate=args.tex_aggregate,
-                              prb_mode=args.prb_mode)
+                              prb_mode=args.prb_mode, schedule=args.schedule)
     return RenderSettings(width=WORKLOAD["width"], height=WORKLOAD["height"], spp=WORKLOAD["spp"],
                           max_depth=WORKLOAD["max_depth"], rr_depth=WORKLOAD["rr_depth"], seed=seed,
                           dispatch=args.dispatch, lanes_per_pixel=args.lanes, block_size=args.block,
-                          tex_aggregate=args.tex_aggregate, prb_mode=args.prb_mode)
+                          tex_aggregate=args.tex_aggregate, prb_mode=args.prb_mode, schedule=args.schedule)
 
 
 # Bounded samples of the workload for the FP64 oracle on the host cores: the
@@ -290,9 +311,10 @@ def run_ours(args):
     rays_f = int(cf[1] + cf[2])
     rays_b = int(cb[1] + cb[2])
     rays_step = rays_f + rays_b
-    fpn = FLOPS_PER_NODE[args.bvh]
-    flops_f = fpn * int(cf[3]) + FLOPS_PER_TRI * int(cf[4])
-    flops_b = fpn * int(cb[3]) + FLOPS_PER_TRI * int(cb[4])
+    flops_f, bytes_f, _ = counted_work(cf, args.bvh)
+    flops_b, bytes_b, grad_bytes_b = counted_work(cb, args.bvh)
+    # memory-side roofs with the library's own probes (before the timed region)
+    roofs = measure_roofs(torch, dev)
 
     for _ in range(args.warmup):
         step()
@@ -342,14 +364,18 @@ def run_ours(args):
         h_grough.copy_(g_rough, non_blocking=True)
     e2e_step()
     torch.cuda.synchronize()
+    # host wall clock around each call sequence, through the synchronisation that makes
+    # the results readable on the host (L2 flushed before each step, outside the clock)
     e_steps = max(2, min(args.steps, 5))
-    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a.record(stream)
-    for _ in range(e_steps):
+    e_times = []
+    for k in range(e_steps):
+        flush.fill_(float(k))
+        torch.cuda.synchronize()
+        t_a = time.perf_counter()
         e2e_step()
-    b.record(stream)
-    torch.cuda.synchronize()
-    e2e_ms = a.elapsed_time(b) / e_steps
+        torch.cuda.synchronize()
+        e_times.append(time.perf_counter() - t_a)
+    e2e_ms = 1e3 * statistics.mean(e_times)
     h2d = h_tex.numel() * 4 + h_rough.numel() * 4
     d2h = h_img.numel() * 4 + h_gtex.numel() * 4 + h_grough.numel() * 4
 
@@ -381,16 +407,60 @@ def run_ours(args):
         kern = {"forward_kernel": (fwd_avg, flops_f), "adjoint_kernel": (adj_avg, flops_b)}
     dom = max(kern, key=lambda k: kern[k][0])
     dom_ms, dom_flops = kern[dom]
-    # memory side of the same kernel: node and triangle bytes the traversal must
-    # fetch (through L2; the scene is L2-resident), per the counted visits
-    node_b, tri_b = NODE_BYTES[args.bvh], 48
-    bytes_f = node_b * int(cf[3]) + tri_b * int(cf[4])
-    bytes_b = node_b * int(cb[3]) + tri_b * int(cb[4])
-    dom_bytes = {"forward_kernel": bytes_f, "replay_kernel": bytes_b / 2, "adjoint_kernel": bytes_b}[dom]
+    # the same kernel's bytes through L2: node, triangle, texel and env fetches of the
+    # counted work, plus (replay / adjoint) the gradient scatter before aggregation
+    dom_bytes = {"forward_kernel": bytes_f, "replay_kernel": bytes_b / 2 + grad_bytes_b,
+                 "adjoint_kernel": bytes_b + grad_bytes_b}[dom]
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     mhz = clk.get("sm_mhz") or 1477.0
     peak_tflops = sms * 128 * 2 * mhz * 1e6 / 1e12
     achieved = dom_flops / (dom_ms / 1e3) / 1e12
+    achieved_gbs = dom_bytes / (dom_ms / 1e3) / 1e9
+    alu_frac = achieved / peak_tflops
+    l2_frac = achieved_gbs / roofs["l2_read_gbs"]
+    traffic = (TRAFFIC_PER_RAY.get(args.bvh, {}).get(dom, 0) * {"forward_kernel": rays_f, "replay_kernel": rays_b / 2,
+               "adjoint_kernel": rays_b}[dom]) or None
+    if l2_frac >= alu_frac:
+        head = {"bound": "l2", "achieved": round(achieved_gbs, 1), "peak": roofs["l2_read_gbs"], "unit": "GB/s",
+                "frac": round(l2_frac, 4)}
+    else:
+        head = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak_tflops, 2), "unit": "TFLOP/s",
+                "frac": round(alu_frac, 4)}
+    roofline = {**head, "kernel": dom, "traffic": round(traffic) if traffic else None,
+                "traffic_basis": TRAFFIC_BASIS if traffic else "no capture of the current kernel",
+                "alu": {"achieved_tflops": round(achieved, 3), "peak_tflops": round(peak_tflops, 2),
+                        "frac": round(alu_frac, 4),
+                        "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 x median SM clock {mhz} MHz",
+                        "work": f"{FLOPS_PER_NODE[args.bvh]}/node visit + {FLOPS_PER_TRI}/triangle test + "
+                                "shading per vertex (diffuse 250, conductor 415, dielectric 130, blend 450, "
+                                f"env lookup {ENV_FLOPS}), counted launch"},
+                "l2": {"achieved_gbs": round(achieved_gbs, 1), "peak_gbs": roofs["l2_read_gbs"],
+                       "frac": round(l2_frac, 4),
+                       "bytes": f"{NODE_BYTES[args.bvh]} B/node visit + {TRI_BYTES} B/triangle test + "
+                                f"{TEX_BYTES} B/texel + {ENV_BYTES} B/env lookup"
+                                + (" + 16 B/texel gradient term + 4 B/other term" if dom != "forward_kernel" else ""),
+                       "peak_basis": "pt_probe_read, L2-resident 16-B loads, measured in this run"},
+                "timing": ("replay = half of the counted fused adjoint; its time = adjoint stage minus the radiance "
+                           "pass timed alone" if dom == "replay_kernel" else "CUDA events around the launch")}
+    if dom != "forward_kernel":
+        terms = int(cb[7])
+        roofline["atomics"] = {"grad_terms_per_s_g": round(terms / (dom_ms / 1e3) / 1e9, 3),
+                               "issued_after_aggregation": int(cb[6]),
+                               "peak_f4_spread_gops": roofs["red_f4_spread_1M_gops"],
+                               "peak_f1_colliding_96_gops": roofs["red_f1_colliding_96_gops"]}
+    cache_line = None
+    if not args.no_cache_line and not args.small and world == 1:
+        try:
+            cc = cache_comparison(torch, warmup_frames=300, spps=(64, 96, 128, 192, 256, 320))
+            cache_line = {"workload": cc["workload"], "reference_spp": cc["reference_spp"],
+                          "plain": cc["plain"], "indirect_pixel_fraction": cc["indirect_pixel_fraction"]}
+            for k in ("cache_bounce1", "cache_bounce2"):
+                c = cc[k]
+                cache_line[k] = {kk: c[kk] for kk in ("equal_time_spp", "equal_time", "train_loss",
+                                                      "mse_indirect_ratio_plain_over_cache",
+                                                      "mse_ratio_plain_over_cache", "warmup_frames")}
+        except Exception as e:  # the throughput line stands without it
+            cache_line = {"error": str(e)[:300]}
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         try:
@@ -403,6 +473,8 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {**WORKLOAD, "l2": "flushed between timed steps (256 MB write)", "dispatch": args.dispatch,
+                   "schedule": ["auto: persistent replay, static forward", "persistent lanes", "static: one unit per thread"][
+                       args.schedule],
                    "bvh": f"{args.bvh} SAH", "bvh_nodes": info["n_nodes"], "rays_per_step": rays_step,
                    "rays_fwd": rays_f, "rays_adj": rays_b, "fwd_ms": round(fwd_avg, 3),
                    "adj_ms": round(adj_avg, 3), "prb": "split" if split else "fused",
@@ -412,20 +484,25 @@ def run_ours(args):
                    "adj_mrays_s": round(rays_b / adj_avg / 1e3, 1),
                    "node_visits_per_ray_fwd": round(int(cf[3]) / max(rays_f, 1), 2),
                    "tri_tests_per_ray_fwd": round(int(cf[4]) / max(rays_f, 1), 2),
-                   "grad_terms": int(cb[7]), "grad_atomics": int(cb[6])},
-        "roofline": {"bound": "alu", "kernel": dom, "achieved": round(achieved, 3),
-                     "peak": round(peak_tflops, 2), "unit": "TFLOP/s", "frac": round(achieved / peak_tflops, 4),
-                     "traffic": DRAM_TRAFFIC_PER_LAUNCH.get(args.bvh, {}).get(dom) if not args.small else None,
-                     "work": f"{FLOPS_PER_NODE[args.bvh]}/node visit + {FLOPS_PER_TRI}/triangle test (counted launch"
-                             + ("; replay = half of the counted fused adjoint, its time = adjoint stage minus "
-                                "the radiance pass timed alone)" if split else ")"),
-                     "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 x median SM clock {mhz} MHz",
-                     "l2_algorithmic_gbs": round(dom_bytes / (dom_ms / 1e3) / 1e9, 1),
-                     "l2_basis": f"{node_b} B per node visit + {tri_b} B per triangle test; compare the "
-                                 "L2-resident read probe of bench.py --peaks (4254 GB/s)"},
+                   "grad_terms": int(cb[7]), "grad_atomics": int(cb[6]),
+                   "paths_per_step": int(cf[0] + cb[0]) // (2 if split else 1),
+                   "mpaths_s_fwd": round(int(cf[0]) / fwd_avg / 1e3, 1),
+                   "shaded_vertices_fwd": {"diffuse": int(cf[8]), "conductor": int(cf[9]), "dielectric": int(cf[10]),
+                                           "blend": int(cf[11])},
+                   "env_lookups_fwd": int(cf[12]),
+                   "simt": {"traversal_lanes_per_node_step_fwd": round(32 * int(cf[3]) / max(32 * int(cf[14]), 1), 2),
+                            "rays_per_loop_step_fwd": round(32 * int(cf[1] + cf[2]) / max(32 * int(cf[15]), 1), 2),
+                            "traversal_lanes_per_node_step_adj": round(32 * int(cb[3]) / max(32 * int(cb[14]), 1), 2),
+                            "rays_per_loop_step_adj": round(32 * int(cb[1] + cb[2]) / max(32 * int(cb[15]), 1), 2),
+                            "basis": "counted launch: lanes per warp-level iteration (of 32)"},
+                   "measured_roofs": roofs},
+        "roofline": roofline,
         "cpu_baseline": cpu,
+        "cache_vs_plain": cache_line,
         "e2e": {"value": round(rays_step / (e2e_ms / 1e3) / 1e6, 2), "unit": "Mrays/s", "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h, "ms_per_step": round(e2e_ms, 3)},
+                "d2h_bytes_per_step": d2h, "ms_per_step": round(e2e_ms, 3),
+                "timing": "host wall clock per step through the C ABI calls and the final synchronisation; "
+                          "pinned host inputs copied in, image and gradients copied out"},
         "gpu_launches": (3 if split else 2) * args.steps,
         "clocks": clk,
         "wall_s": round(wall, 3),
@@ -582,7 +659,7 @@ def run_jvp_experiment(args):
                        "forward_mrays_s": round(rays / fwd_ms / 1e3, 1)},
             "roofline": {"bound": "alu", "kernel": "jvp_kernel", "achieved": round(achieved, 3), "peak": round(peak, 2),
                          "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
-                         "traffic": DRAM_TRAFFIC_PER_LAUNCH.get(args.bvh, {}).get("jvp_kernel")
+                         "traffic": None
                          if not args.small else None,
                          "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 x median SM clock {mhz} MHz"},
             "gpu_launches": 2 * args.steps, "clocks": clk}
@@ -954,19 +1031,20 @@ def run_mlp_experiment(args):
     print(json.dumps(line), flush=True)
 
 
-def run_cache_experiment(args):
-    """Cornell box at 1024^2, depth 4: plain PT at 64 spp vs cache-terminated PT (bounce 1
-    and 2) at the spp that fits the same per-frame time including one online training
-    update, after a warm-up of online training frames.  Reference: 4096-spp plain PT,
-    itself checked against the FP64 oracle on a 64^2 crop at 64 spp."""
-    import numpy as np
-    import torch
-
-    import oracle
+def cache_comparison(torch, warmup_frames=300, spps=(1, 2, 4, 8, 16, 32, 64, 96, 128, 192, 256, 320, 384),
+                     bounces=(1, 2), plain_spp=64, ref_batches=16):
+    """Cornell box at 1024^2, depth 4: plain PT at `plain_spp` vs cache-terminated PT
+    (bounce 1 and 2) at the spp that fits the same per-frame time including one online
+    training update, after `warmup_frames` online training frames.  The network state
+    (weights, Adam moments, step) after the warm-up is restored before every measured
+    frame, so that every spp is judged with the same network (one identical online
+    update inside each timed frame); without that, each measured frame trains on and
+    the comparison drifts with the order of the sweep.  Reference: ref_batches x 256
+    spp of plain PT with distinct seeds (the forward kernel, parity-tested against the
+    FP64 oracle)."""
     from paper_2202_01284_gb300 import abi, scenes as S
     from paper_2202_01284_gb300.render import DeviceScene, RadianceCache, RenderSettings
 
-    torch.cuda.set_device(0)
     W, H, D = 1024, 1024, 4
     sc = S.cornell(width=W, height=H)
     ds = DeviceScene(sc, layout=abi.PT_BVH_WIDE)
@@ -975,9 +1053,12 @@ def run_cache_experiment(args):
     def st(spp, seed, **kw):
         return RenderSettings(width=W, height=H, spp=spp, max_depth=D, seed=seed, **kw)
 
-    def timed(fn, reps=3):
-        ts = []
+    def timed(fn, reps=3, before=None):
+        ts, out = [], None
         for _ in range(reps):
+            if before:
+                before()
+            torch.cuda.synchronize()
             a, b = torch.cuda.Event(True), torch.cuda.Event(True)
             a.record()
             out = fn()
@@ -986,18 +1067,10 @@ def run_cache_experiment(args):
             ts.append(a.elapsed_time(b))
         return statistics.median(ts), out
 
-    # reference: 4096 spp as 16 x 256 spp with distinct seeds
     ref = torch.zeros((1, H, W, 3), device="cuda")
-    for k in range(16):
+    for k in range(ref_batches):
         ref += ds.forward(st(256, 50000 + k))
-    ref /= 16
-    # reference checked against the oracle on a 64^2 crop at 64 spp (same seed, same estimator)
-    crop = (480, 400, 64, 64)
-    g_crop = ds.forward(RenderSettings(width=W, height=H, spp=64, max_depth=D, seed=4242, crop=crop))[0].cpu().numpy()
-    o_crop = oracle.render(oracle.OracleScene(sc), oracle.render_in(sc.cameras[0], 64, D, 4242, crop=crop))
-    tau = 1e-3 * np.abs(o_crop).mean()
-    crop_frac = float(np.mean((np.abs(g_crop - o_crop) <= 1e-4 * np.maximum(np.abs(o_crop), tau)).all(-1)))
-
+    ref /= ref_batches
     # pixels that do not see the emitter (reference below 1): the light's edge pixels carry
     # anti-aliasing variance (radiance 15 vs ~0.2) that no cache can remove
     indirect = (ref.amax(dim=-1, keepdim=True) < 1.0).float()
@@ -1007,15 +1080,14 @@ def run_cache_experiment(args):
         d2 = (img - ref) ** 2
         return float(d2.mean()), float((d2 * indirect).sum()) / n_ind
 
-    t_plain, img_plain = timed(lambda: ds.forward(st(64, 7)))
+    t_plain, img_plain = timed(lambda: ds.forward(st(plain_spp, 7)))
     mp, mpi = mse(img_plain)
-    out = {"metric": "equal-time MSE vs 4096-spp reference, radiance cache vs plain PT",
-           "workload": f"cornell36, {W}x{H}, depth {D}", "reference_spp": 4096,
-           "reference_vs_oracle_crop": {"crop": crop, "spp": 64, "pixels_within_1e-4": crop_frac},
-           "indirect_pixel_fraction": n_ind / (3 * W * H),
-           "plain": {"spp": 64, "ms": round(t_plain, 3), "mse": mp, "mse_indirect": mpi}}
-    for bounce in (1, 2):
-        cache = RadianceCache(*box, batch=65536, max_queries=W * H * 384, max_records=2_000_000,
+    out = {"metric": "equal-time MSE vs the reference, radiance cache vs plain PT",
+           "workload": f"cornell36, {W}x{H}, depth {D}", "reference_spp": 256 * ref_batches,
+           "indirect_pixel_fraction": round(n_ind / (3 * W * H), 4),
+           "plain": {"spp": plain_spp, "ms": round(t_plain, 3), "mse": mp, "mse_indirect": mpi}}
+    for bounce in bounces:
+        cache = RadianceCache(*box, batch=65536, max_queries=W * H * max(spps), max_records=2_000_000,
                               max_paths=256 * 256, lr=5e-3, init_weights=S.mlp_init_weights(2022))
         train_st = RenderSettings(width=256, height=256, spp=1, max_depth=D, seed=0)
         train_cam = [S.cornell_camera(256, 256)]
@@ -1024,30 +1096,41 @@ def run_cache_experiment(args):
             train_st.seed = 900000 + i
             return cache.train(ds, train_st, steps=4, cams=train_cam)
         t0 = time.perf_counter()
-        for i in range(args.cache_warmup_frames):
+        for i in range(warmup_frames):
             train_frame(i)
         torch.cuda.synchronize()
         warm_s = time.perf_counter() - t0
         loss = cache.last_loss()
-        res = {}
-        best = None
-        for spp in (1, 2, 4, 8, 16, 32, 64, 96, 128, 192, 256, 320, 384):
-            t_frame, img = timed(lambda: (train_frame(10 ** 6 + spp),
-                                          ds.forward(st(spp, 8, cache=cache.handle, cache_bounce=bounce)))[1])
+        state = abi.pt_cache_get_state(cache.handle)
+
+        def restore():
+            abi.pt_cache_set_state(cache.handle, *state)
+        res, best = {}, None
+        for spp in spps:
+            t_frame, img = timed(lambda: (train_frame(10 ** 6),
+                                          ds.forward(st(spp, 8, cache=cache.handle, cache_bounce=bounce)))[1],
+                                 before=restore)
             m_all, m_ind = mse(img)
             res[spp] = {"ms": round(t_frame, 3), "mse": m_all, "mse_indirect": m_ind}
             if t_frame <= t_plain:
                 best = spp
         eq = res[best] if best else None
         out[f"cache_bounce{bounce}"] = {
-            "warmup_frames": args.cache_warmup_frames, "warmup_s": round(warm_s, 2), "train_loss": loss,
-            "per_frame": "one pt_cache_train (256^2 training paths, 1 spp, 4 Adam steps of 65,536) + render",
+            "warmup_frames": warmup_frames, "warmup_s": round(warm_s, 2), "train_loss": loss,
+            "per_frame": "one pt_cache_train (256^2 training paths, 1 spp, 4 Adam steps of 65,536) + render; "
+                         "network state restored before each measured frame",
             "equal_time_spp": best, "equal_time": eq,
-            "mse_ratio_plain_over_cache": (out["plain"]["mse"] / eq["mse"]) if eq else None,
-            "mse_indirect_ratio_plain_over_cache": (out["plain"]["mse_indirect"] / eq["mse_indirect"]) if eq else None,
+            "mse_indirect_ratio_plain_over_cache": (mpi / eq["mse_indirect"]) if eq else None,
+            "mse_ratio_plain_over_cache": (mp / eq["mse"]) if eq else None,
             "sweep": res}
         cache.close()
-    print(json.dumps(out), flush=True)
+    return out
+
+
+def run_cache_experiment(args):
+    import torch
+    torch.cuda.set_device(0)
+    print(json.dumps(cache_comparison(torch, warmup_frames=args.cache_warmup_frames)), flush=True)
 
 
 def run_batch_experiment(args):
@@ -1143,38 +1226,52 @@ def run_batch_experiment(args):
     print(json.dumps(out), flush=True)
 
 
-def run_peaks(args):
-    """L2-resident read bandwidth and float atomic throughput (spread vs colliding
-    addresses), measured with torch's reduction and index_add_ kernels."""
-    import torch
-    torch.cuda.set_device(0)
+def measure_roofs(torch, dev=0, l2_mb=48, reps=20):
+    """Memory-side roofs with the library's own probes (pt_probe_read / pt_probe_atomic),
+    timed with CUDA events on the stream they run on: L2-resident and HBM-sized 16-byte
+    reads, and fire-and-forget float / float4 atomic adds spread over the texture-gradient
+    buffer size (1M float4) or colliding on 96 floats (the roughness gradients)."""
+    from paper_2202_01284_gb300 import abi
+    stream = torch.cuda.current_stream(dev)
 
-    def t_ms(fn, reps=20):
+    def t_ms(fn, n=reps):
         fn()
-        torch.cuda.synchronize()
-        a, b = torch.cuda.Event(True), torch.cuda.Event(True)
-        a.record()
-        for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(n):
             fn()
-        b.record()
-        torch.cuda.synchronize()
-        return a.elapsed_time(b) / reps
-    out = {"metric": "memory-side roofs (own microbenchmarks)"}
-    x = torch.rand(16 * 1024 * 1024, device="cuda")            # 64 MB: L2 resident after the first pass
-    ms = t_ms(lambda: x.sum())
-    out["l2_read_gbs"] = round(x.numel() * 4 / ms / 1e6, 1)
-    big = torch.rand(1024 * 1024 * 1024 // 4 * 2, device="cuda")  # 2 GB: HBM
-    ms = t_ms(lambda: big.sum(), reps=5)
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        return a.elapsed_time(b) / n
+    sink = torch.zeros(1, device=dev)
+    out = {}
+    buf = torch.rand(l2_mb * (1 << 20) // 4, device=dev)
+    ms = t_ms(lambda: abi.pt_probe_read(buf, 4, sink, stream.cuda_stream))
+    out["l2_read_gbs"] = round(buf.numel() * 4 * 4 / ms / 1e6, 1)
+    del buf
+    big = torch.empty((4 << 30) // 4, device=dev)
+    big.fill_(1.0)
+    ms = t_ms(lambda: abi.pt_probe_read(big, 1, sink, stream.cuda_stream), n=5)
     out["hbm_read_gbs"] = round(big.numel() * 4 / ms / 1e6, 1)
     del big
     n = 1 << 24
-    vals = torch.rand(n, device="cuda")
-    for name, m in (("spread_16M_targets", n), ("spread_1M_targets", 1 << 20), ("colliding_96_targets", 96),
-                    ("colliding_15_targets", 15)):
-        idx = torch.randint(0, m, (n,), device="cuda")
-        dst = torch.zeros(m, device="cuda")
-        ms = t_ms(lambda: dst.index_add_(0, idx, vals))
-        out[f"atomic_add_f32_{name}_gops"] = round(n / ms / 1e6, 2)
+    dst = torch.zeros((1 << 20) * 4, device=dev)
+    ms = t_ms(lambda: abi.pt_probe_atomic(dst, 1 << 20, n, 4, stream.cuda_stream), n=5)
+    out["red_f4_spread_1M_gops"] = round(n / ms / 1e6, 2)
+    ms = t_ms(lambda: abi.pt_probe_atomic(dst, 1 << 20, n, 1, stream.cuda_stream), n=5)
+    out["red_f1_spread_1M_gops"] = round(n / ms / 1e6, 2)
+    ms = t_ms(lambda: abi.pt_probe_atomic(dst, 96, n, 1, stream.cuda_stream), n=3)
+    out["red_f1_colliding_96_gops"] = round(n / ms / 1e6, 2)
+    out["basis"] = (f"pt_probe_read: {l2_mb} MB x 4 passes (L2-resident), 4 GB x 1 pass (HBM), 16-B L2-only loads; "
+                    "pt_probe_atomic: 16M adds; CUDA events, mean of repeated launches")
+    return out
+
+
+def run_peaks(args):
+    """Memory-side roofs measured with the library's own probes."""
+    import torch
+    torch.cuda.set_device(0)
+    out = {"metric": "memory-side roofs (own microbenchmarks)", **measure_roofs(torch)}
     props = torch.cuda.get_device_properties(0)
     out["sms"] = props.multi_processor_count
     out["fp32_peak_tflops_at_2070mhz"] = round(props.multi_processor_count * 128 * 2 * 2070e6 / 1e12, 2)

@@ -148,6 +148,16 @@ enum {
   PT_CNT_TEX = 5,        /* texture lookups */
   PT_CNT_ATOMICS = 6,    /* gradient atomics issued after aggregation */
   PT_CNT_GRAD_TERMS = 7, /* gradient terms before aggregation */
+  PT_CNT_V_DIFFUSE = 8,  /* shaded vertices per BSDF type: diffuse, */
+  PT_CNT_V_CONDUCTOR = 9,   /* GGX conductor, */
+  PT_CNT_V_DIELECTRIC = 10, /* smooth dielectric, */
+  PT_CNT_V_BLEND = 11,      /* diffuse + GGX blend */
+  PT_CNT_ENV = 12,       /* environment-map lookups (escaped rays and env light samples) */
+  PT_CNT_TEX_TERMS = 13, /* texel gradient terms (float4) among PT_CNT_GRAD_TERMS */
+  PT_CNT_WARP_NODE_STEPS = 14, /* traversal node-loop iterations, counted once per warp: the
+                                  traversal's SIMT efficiency is PT_CNT_NODES / (32 x this) */
+  PT_CNT_WARP_LOOP_STEPS = 15, /* megakernel iterations, once per warp: lanes that traced a ray
+                                  are (PT_CNT_RAYS + PT_CNT_SHADOW) / (32 x this) */
   PT_N_COUNTERS = 16
 };
 
@@ -186,8 +196,19 @@ typedef struct {
    * plain adjoint (no cache, env gradients, texel aggregation or counters); the
    * others run fused. */
   int32_t prb_mode;
+  /* PT_SCHED_*: how threads take work.  PERSISTENT: a grid that fills the GPU once,
+   * each lane taking the next (pixel, lane) unit from a scene-owned counter when its
+   * unit has no samples left (the forward then adds lane sums into the image with
+   * float atomics when lanes_per_pixel > 1, so the image's last bits may vary from
+   * run to run); STATIC: one unit per thread.  PERSISTENT applies to the forward,
+   * split-PRB radiance pass and replay, and forward mode with switch dispatch and no
+   * cache or instrumentation (STATIC otherwise).  AUTO (0) = PERSISTENT for the replay,
+   * STATIC for the rest (measured faster that way).  Calls on one scene must not
+   * overlap on the GPU (the counter is per scene). */
+  int32_t schedule;
 } pt_render_desc;
 enum { PT_PRB_AUTO = 0, PT_PRB_FUSED = 1, PT_PRB_SPLIT = 2 };
+enum { PT_SCHED_AUTO = 0, PT_SCHED_PERSISTENT = 1, PT_SCHED_STATIC = 2 };
 
 /* Differentiable parameters: borrowed device pointers. */
 typedef struct {
@@ -563,6 +584,25 @@ int pt_cache_train(pt_cache* cache, pt_scene* scene, const pt_render_desc* desc,
  * pixel * spp + sample, depth of the vertex); any pointer may be NULL.
  * *n_out = min(cap, records kept). */
 int pt_cache_read_records(pt_cache* cache, int cap, float* raw, float* target, int* meta, int* n_out);
+
+/* ---------------------------------------------------------------- measurement probes
+ * The roofs that bound the traversal's node and triangle fetches (through L2; the
+ * paper's Sec. 3.5 finds the megakernel memory-latency bound) and the adjoint's
+ * gradient scatter (atomic scatter-adds, Sec. 4.1), which the driver's peak table
+ * does not hold.  Both calls are asynchronous on `stream`; time them with events.
+ *
+ * pt_probe_read: reads the device buffer buf [bytes] (16-byte aligned, bytes a
+ * multiple of 16) `passes` times with 16-byte loads cached in L2 only (keep it
+ * smaller than L2 to measure L2, larger to measure HBM) and adds the sum of all
+ * floats read to *sink (device float, accumulated).  Errors: PT_ERR_ARG.
+ *
+ * pt_probe_atomic: n_updates fire-and-forget atomic adds of 1.0 to the n_addr
+ * addresses of dst (device; width 1: floats, width 4: float4 elements, dst 16-byte
+ * aligned), update i going to element (i * 2654435761) mod n_addr -- spread over a
+ * large buffer, or colliding on a few elements.  Every element receives
+ * n_updates / n_addr (+1) adds.  Errors: PT_ERR_ARG. */
+int pt_probe_read(const void* buf, long long bytes, int passes, float* sink, void* stream);
+int pt_probe_atomic(float* dst, long long n_addr, long long n_updates, int width, void* stream);
 
 #ifdef __cplusplus
 }

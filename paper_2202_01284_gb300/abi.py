@@ -35,6 +35,9 @@ PT_DISPATCH_MATCH = 1
 PT_PRB_AUTO = 0
 PT_PRB_FUSED = 1
 PT_PRB_SPLIT = 2
+PT_SCHED_AUTO = 0
+PT_SCHED_PERSISTENT = 1
+PT_SCHED_STATIC = 2
 PT_WF_TRACED = 0
 PT_WF_GROUPED = 1
 PT_N_COUNTERS = 16
@@ -80,7 +83,8 @@ class pt_render_desc(C.Structure):
                 ("crop_x0", C.c_int32), ("crop_y0", C.c_int32), ("crop_w", C.c_int32), ("crop_h", C.c_int32),
                 ("lanes_per_pixel", C.c_int32), ("block_size", C.c_int32), ("tex_aggregate", C.c_int32),
                 ("dbg_sample_L", C.c_void_p), ("dbg_sample_hash", C.c_void_p), ("counters", C.c_void_p),
-                ("cache", C.c_void_p), ("cache_bounce", C.c_int32), ("prb_mode", C.c_int32)]
+                ("cache", C.c_void_p), ("cache_bounce", C.c_int32), ("prb_mode", C.c_int32),
+                ("schedule", C.c_int32)]
 
 
 class pt_params(C.Structure):
@@ -187,6 +191,8 @@ SIGNATURES = {
     "pt_batch_destroy": ([C.c_void_p], None),
     "pt_render_batch": ([C.c_void_p, C.c_int, C.POINTER(pt_batch_opts), C.c_void_p], C.c_int),
     "pt_render_batch_noalloc": ([C.c_void_p, C.c_int, C.POINTER(pt_batch_opts), C.c_void_p], C.c_int),
+    "pt_probe_read": ([C.c_void_p, C.c_longlong, C.c_int, C.c_void_p, C.c_void_p], C.c_int),
+    "pt_probe_atomic": ([C.c_void_p, C.c_longlong, C.c_longlong, C.c_int, C.c_void_p], C.c_int),
     "pt_cache_read_records": ([C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_int)],
                               C.c_int),
 }
@@ -272,7 +278,7 @@ def camera_struct(cam: "S.Camera") -> pt_camera:
 
 def render_desc(cams, width, height, spp, max_depth, seed, rr_depth=-1, nee=True, dispatch=PT_DISPATCH_SWITCH,
                 crop=None, lanes_per_pixel=0, block_size=0, tex_aggregate=0, dbg_L=None, dbg_hash=None,
-                counters=None, cache=None, cache_bounce=1, prb_mode=0):
+                counters=None, cache=None, cache_bounce=1, prb_mode=0, schedule=0):
     cams = list(cams)
     arr = (pt_camera * len(cams))(*[camera_struct(c) for c in cams])
     r = pt_render_desc()
@@ -289,6 +295,7 @@ def render_desc(cams, width, height, spp, max_depth, seed, rr_depth=-1, nee=True
     r.cache = cache
     r.cache_bounce = cache_bounce
     r.prb_mode = prb_mode
+    r.schedule = schedule
     r._keep = arr
     return r
 
@@ -589,3 +596,15 @@ def pt_render_batch_noalloc(jobs, opts, stream: int = 0) -> None:
     arr = (pt_job * len(jobs))(*jobs)
     check("pt_render_batch_noalloc", load().pt_render_batch_noalloc(C.cast(arr, C.c_void_p), len(jobs),
                                                                     C.byref(opts), stream or None))
+
+
+def pt_probe_read(buf, passes: int, sink, stream: int = 0) -> None:
+    """L2 / HBM read probe over the device tensor `buf` (sum added into `sink`)."""
+    check("pt_probe_read", load().pt_probe_read(_ptr(buf), buf.numel() * buf.element_size(), int(passes),
+                                                _ptr(sink), stream or None))
+
+
+def pt_probe_atomic(dst, n_addr: int, n_updates: int, width: int, stream: int = 0) -> None:
+    """Atomic-add probe: n_updates adds of 1.0 over the first n_addr elements of `dst`."""
+    check("pt_probe_atomic", load().pt_probe_atomic(_ptr(dst), int(n_addr), int(n_updates), int(width),
+                                                    stream or None))

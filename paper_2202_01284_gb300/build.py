@@ -18,7 +18,7 @@ LIB = os.path.join(HERE, "libptgb.so")
 OBJDIR = os.path.join(HERE, "_build")
 
 CU_SOURCES = ["pt_render.cu", "pt_scene.cu", "pt_nrc.cu", "pt_nrc_tc.cu", "pt_wavefront.cu", "pt_ckpt.cu",
-              "pt_reparam.cu"]
+              "pt_reparam.cu", "pt_probe.cu"]
 CPP_SOURCES = ["bvh_build.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

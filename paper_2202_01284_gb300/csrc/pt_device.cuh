@@ -21,6 +21,9 @@ namespace ptgb {
 #define PT_PI 3.14159265358979323846f
 #define PT_INV_PI 0.31830988618379067154f
 #define PT_STACK 64
+#ifndef PT_RSTACK
+#define PT_RSTACK 0  // 1: the wide traversal keeps its top four stack entries in registers
+#endif
 
 // ---------------------------------------------------------------- float3 helpers
 __device__ __forceinline__ float3 f3(float a, float b, float c) { return make_float3(a, b, c); }
@@ -36,6 +39,8 @@ __device__ __forceinline__ float3 cross3(float3 a, float3 b) {
 __device__ __forceinline__ float3 normalize3(float3 a) { return a * rsqrtf(dot3(a, a)); }
 __device__ __forceinline__ float max3f(float3 a) { return fmaxf(a.x, fmaxf(a.y, a.z)); }
 __device__ __forceinline__ float3 xyz(float4 a) { return f3(a.x, a.y, a.z); }
+
+__device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
 
 // ---------------------------------------------------------------- PCG32 (O'Neill 2014)
 struct Pcg32 {
@@ -65,13 +70,14 @@ struct Fnv {
 };
 
 // ---------------------------------------------------------------- instrumentation
+constexpr int kCounters = 16;  // PT_CNT_PATHS .. PT_CNT_WARP_LOOP_STEPS
 template <bool INSTR>
 struct Counters {
   __device__ __forceinline__ void add(int, unsigned) {}
 };
 template <>
 struct Counters<true> {
-  unsigned c[8];
+  unsigned c[kCounters];
   __device__ __forceinline__ void add(int i, unsigned v) { c[i] += v; }
 };
 
@@ -148,12 +154,15 @@ __device__ __forceinline__ Hit trace_binary(const DevScene& S, float3 ro, float3
   int sp = 0;
   int cur = 0;
   const float4* __restrict__ N = S.nodes;
-  unsigned n_nodes = 0, n_tris = 0;
+  unsigned n_nodes = 0, n_tris = 0, warp_steps = 0;
   const int kDone = 0x7fffffff;
   while (cur != kDone) {
     // ---- inner nodes
     while (cur >= 0 && cur != kDone) {
       ++n_nodes;
+      if constexpr (INSTR) {
+        if (lane_id() == __ffs(__activemask()) - 1) ++warp_steps;
+      }
       const float4 w0 = __ldg(&N[4 * cur]);
       const float4 w1 = __ldg(&N[4 * cur + 1]);
       const float4 w2 = __ldg(&N[4 * cur + 2]);
@@ -207,6 +216,7 @@ __device__ __forceinline__ Hit trace_binary(const DevScene& S, float3 ro, float3
   }
   cnt.add(3, n_nodes);
   cnt.add(4, n_tris);
+  cnt.add(14, warp_steps);
   return h;
 }
 
@@ -231,12 +241,22 @@ __device__ __forceinline__ Hit trace_wide(const DevScene& S, float3 ro, float3 r
   const float3 inv = safe_inv(rd);
   const uint32_t flip = (rd.x >= 0.0f ? 1u : 0u) | (rd.y >= 0.0f ? 2u : 0u) | (rd.z >= 0.0f ? 4u : 0u);
   const uint4* __restrict__ N = reinterpret_cast<const uint4*>(S.nodes);
+#if PT_RSTACK
+  // top four entries in registers (r0 = top), deeper ones in a local array
+  uint2 r0 = make_uint2(0u, 0u), r1 = r0, r2 = r0, r3 = r0;
+  uint2 ovf[28];
+#else
   uint2 stack[32];
+#endif
   int sp = 0;
   int node = 0;
   unsigned n_nodes = 0, n_tris = 0;
+  unsigned warp_steps = 0;
   for (;;) {
     ++n_nodes;
+    if constexpr (INSTR) {
+      if (lane_id() == __ffs(__activemask()) - 1) ++warp_steps;
+    }
     const uint4 w0 = __ldg(&N[5 * node]);
     const uint4 w1 = __ldg(&N[5 * node + 1]);
     const uint4 w2 = __ldg(&N[5 * node + 2]);
@@ -297,10 +317,20 @@ __device__ __forceinline__ Hit trace_wide(const DevScene& S, float3 ro, float3 r
     uint32_t base = w1.x, gmask = imask, hits = inner_hits;
     if (hits == 0u) {
       if (sp == 0) break;
-      base = stack[sp - 1].x;
-      gmask = stack[sp - 1].y & 0xffu;
-      hits = stack[sp - 1].y >> 8;
+#if PT_RSTACK
+      const uint2 e = r0;
+      r0 = r1;
+      r1 = r2;
+      r2 = r3;
       --sp;
+      if (sp >= 4) r3 = ovf[sp - 4];
+#else
+      const uint2 e = stack[sp - 1];
+      --sp;
+#endif
+      base = e.x;
+      gmask = e.y & 0xffu;
+      hits = e.y >> 8;
     }
     const int k = __ffs(hits) - 1;
     hits &= hits - 1;
@@ -311,11 +341,21 @@ __device__ __forceinline__ Hit trace_wide(const DevScene& S, float3 ro, float3 r
         set_status(S, PT_ERR_BVH);
         break;
       }
+#if PT_RSTACK
+      if (sp >= 4) ovf[sp - 4] = r3;
+      r3 = r2;
+      r2 = r1;
+      r1 = r0;
+      r0 = make_uint2(base, gmask | (hits << 8));
+      ++sp;
+#else
       stack[sp++] = make_uint2(base, gmask | (hits << 8));
+#endif
     }
   }
   cnt.add(3, n_nodes);
   cnt.add(4, n_tris);
+  cnt.add(14, warp_steps);
   return h;
 }
 
@@ -590,7 +630,6 @@ __device__ __forceinline__ float env_pdf_at(const DevScene& S, int x, int y, flo
 }
 
 // ---------------------------------------------------------------- gradient scatter
-__device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
 
 __device__ __forceinline__ int nth_set_bit(unsigned m, int n) {
   // smallest p with popc(m & bits[0..p]) > n

@@ -92,6 +92,9 @@ struct alignas(16) LaunchArgs {
   float* dbg_L;
   uint32_t* dbg_hash;
   unsigned long long* counters;
+  // persistent launches: work counter (units handed out so far), zeroed before the launch
+  unsigned long long* queue;
+  long long queue_pad_;
   // radiance cache: 0 off, 1 terminate + write queries, 2 terminate + read cache
   // radiance (adjoint), 3 full-length training paths writing records
   int cache_mode, cache_bounce;
@@ -161,7 +164,8 @@ struct pt_scene {
   void* d_light_guide = nullptr;
   void* d_env_marg_guide = nullptr;
   void* d_env_cond_guide = nullptr;
-  void* d_status = nullptr;
+  void* d_status = nullptr;     // 256 B: status word, then the work counter
+  unsigned long long* queue = nullptr;  // work counter of persistent launches (inside d_status)
   void* d_wf = nullptr;         // wavefront scratch (grown on demand)
   size_t wf_bytes = 0;
   void* d_sample_L = nullptr;   // split PRB: per-sample radiance (grown on demand)

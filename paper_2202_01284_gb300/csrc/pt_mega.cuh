@@ -13,7 +13,7 @@ __device__ __forceinline__ void flush_counters(const LaunchArgs& A, Counters<INS
   if constexpr (INSTR) {
     if (A.counters) {
 #pragma unroll
-      for (int i = 0; i < 8; ++i) {
+      for (int i = 0; i < kCounters; ++i) {
         unsigned long long v = cnt.c[i];
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
@@ -89,31 +89,68 @@ __device__ __forceinline__ void load_checkpoint(const LaunchArgs& A, long long s
   P.Lrem = f3(0.f, 0.f, 0.f);
 }
 
+// dLoss/dI of a pixel divided by spp (the adjoint's per-sample weight).
+__device__ __forceinline__ float3 pixel_dl(const LaunchArgs& A, long long pix) {
+  const float inv = 1.0f / (float)A.spp;
+  if (A.target) {  // batched jobs: L2 loss against the job's target
+    const float k = 2.0f * A.loss_scale * inv;
+    return f3((A.image[3 * pix] - A.target[3 * pix]) * k, (A.image[3 * pix + 1] - A.target[3 * pix + 1]) * k,
+              (A.image[3 * pix + 2] - A.target[3 * pix + 2]) * k);
+  }
+  return f3(A.grad_image[3 * pix] * inv, A.grad_image[3 * pix + 1] * inv, A.grad_image[3 * pix + 2] * inv);
+}
+
+// Film of a persistent launch: a unit's sample sum goes straight to its pixel with
+// one lane per pixel, else it is added to the (zeroed) image with float atomics.
+template <bool JVP>
+__device__ __forceinline__ void film_unit(const LaunchArgs& A, long long pix, float3 sum, float3 sum_dot) {
+  const float inv = 1.0f / (float)A.spp;
+  float* im = A.image + 3 * pix;
+  if (A.lanes_per_pixel == 1) {
+    im[0] = sum.x * inv;
+    im[1] = sum.y * inv;
+    im[2] = sum.z * inv;
+  } else {
+    atomicAdd(im, sum.x * inv);
+    atomicAdd(im + 1, sum.y * inv);
+    atomicAdd(im + 2, sum.z * inv);
+  }
+  if constexpr (JVP) {
+    float* d = A.image_dot + 3 * pix;
+    if (A.lanes_per_pixel == 1) {
+      d[0] = sum_dot.x * inv;
+      d[1] = sum_dot.y * inv;
+      d[2] = sum_dot.z * inv;
+    } else {
+      atomicAdd(d, sum_dot.x * inv);
+      atomicAdd(d + 1, sum_dot.y * inv);
+      atomicAdd(d + 2, sum_dot.z * inv);
+    }
+  }
+}
+
 // FEAT_CKPT (forward only): store a checkpoint before every closest-hit ray and
 // the vertex count of every sample (reverse mode with checkpoints, Sec. 4.10).
-template <bool ADJ, bool JVP, bool INSTR, int LAYOUT, int DISPATCH, int FEAT = 0>
+// PERSIST: the thread is one lane of a persistent grid: `unit` is ignored, and a
+// lane whose unit has no samples left takes the next unit from the launch's work
+// counter A.queue (one atomic per warp for all lanes that need one, so a warp's
+// new units are consecutive: neighbouring samples of the same pixels), until the
+// counter passes A.n_units.  Lanes never wait for the slowest unit of their warp
+// or block, only for the last units of the launch.
+template <bool ADJ, bool JVP, bool INSTR, int LAYOUT, int DISPATCH, int FEAT = 0, bool PERSIST = false>
 __device__ __forceinline__ void megakernel(const LaunchArgs& A, long long unit, const Tile& tile) {
   constexpr bool CKPT = (FEAT & FEAT_CKPT) != 0;
   PixelOf px{};
-  const bool valid = unit_pixel(A, unit, tile, px);
+  bool valid = PERSIST ? false : unit_pixel(A, unit, tile, px);
   Counters<INSTR> cnt;
   if constexpr (INSTR) {
-    for (int i = 0; i < 8; ++i) cnt.c[i] = 0;
+    for (int i = 0; i < kCounters; ++i) cnt.c[i] = 0;
   }
   GradSink sink;
-  const int lane_in_pix = (int)(unit & (A.lanes_per_pixel - 1));
+  int lane_in_pix = (int)(unit & (A.lanes_per_pixel - 1));
   float3 dl = f3(0.f, 0.f, 0.f);
-  if (valid) {
-    if constexpr (ADJ) {
-      const float inv = 1.0f / (float)A.spp;
-      if (A.target) {  // batched jobs: L2 loss against the job's target
-        const float k = 2.0f * A.loss_scale * inv;
-        dl = f3((A.image[3 * px.pix] - A.target[3 * px.pix]) * k, (A.image[3 * px.pix + 1] - A.target[3 * px.pix + 1]) * k,
-                (A.image[3 * px.pix + 2] - A.target[3 * px.pix + 2]) * k);
-      } else {
-        dl = f3(A.grad_image[3 * px.pix] * inv, A.grad_image[3 * px.pix + 1] * inv, A.grad_image[3 * px.pix + 2] * inv);
-      }
-    }
+  if constexpr (ADJ && !PERSIST) {
+    if (valid) dl = pixel_dl(A, px.pix);
   }
   float3 pix_sum = f3(0.f, 0.f, 0.f);
   float3 pix_sum_dot = f3(0.f, 0.f, 0.f);
@@ -121,11 +158,40 @@ __device__ __forceinline__ void megakernel(const LaunchArgs& A, long long unit, 
   int next_s = lane_in_pix;
   // FEAT_REPLAY: every sample is replayed once from the radiance the forward stored
   constexpr bool REPLAY = ADJ && (FEAT & FEAT_REPLAY) != 0;
+  constexpr bool FILM = !ADJ && (FEAT & FEAT_SAMPLE_L) == 0;
   int pass = REPLAY ? 1 : 0;
   bool has_path = false;
   bool want_shadow = false;  // the lane's next traversal is its pending shadow ray
+  bool retired = !PERSIST;   // persistent lanes: the work counter has run out
   PathState P;
   for (;;) {
+    if constexpr (PERSIST) {
+      const bool need = !has_path && !retired && !(valid && next_s < A.spp);
+      if (FILM && need && valid && A.image) film_unit<JVP>(A, px.pix, pix_sum, pix_sum_dot);
+      const unsigned m = __ballot_sync(0xffffffffu, need);
+      if (m) {
+        const int leader = __ffs(m) - 1;
+        unsigned long long base = 0;
+        if (lane_id() == leader) base = atomicAdd(A.queue, (unsigned long long)__popc(m));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        if (need) {
+          unit = (long long)(base + (unsigned long long)__popc(m & ((1u << lane_id()) - 1u)));
+          valid = false;
+          if (unit >= A.n_units) {
+            retired = true;
+          } else {
+            valid = unit_pixel(A, unit, tile, px);
+            lane_in_pix = (int)(unit & (A.lanes_per_pixel - 1));
+            next_s = lane_in_pix;
+            pix_sum = pix_sum_dot = L_pass0 = f3(0.f, 0.f, 0.f);
+            pass = REPLAY ? 1 : 0;
+            if constexpr (ADJ) {
+              if (valid) dl = pixel_dl(A, px.pix);
+            }
+          }
+        }
+      }
+    }
     if (!has_path && valid && next_s < A.spp) {
       // one call site for both passes: the replay starts from identical code
       // the split-PRB radiance pass traces the adjoint's samples
@@ -140,7 +206,10 @@ __device__ __forceinline__ void megakernel(const LaunchArgs& A, long long unit, 
       has_path = true;
       want_shadow = false;
     }
-    if (!__any_sync(0xffffffffu, has_path)) break;
+    if (!__any_sync(0xffffffffu, has_path || !retired)) break;
+    if constexpr (INSTR) {
+      if (lane_id() == 0) cnt.add(15, 1);
+    }
     if (has_path) {
       // one traversal per lane per iteration: its path ray or its shadow ray
       cnt.add(want_shadow ? 2 : 1, 1);
@@ -207,7 +276,7 @@ __device__ __forceinline__ void megakernel(const LaunchArgs& A, long long unit, 
       }
     }
   }
-  if constexpr (!ADJ) {
+  if constexpr (!ADJ && !PERSIST) {
     for (int off = 1; off < A.lanes_per_pixel; off <<= 1) {
       pix_sum.x += __shfl_xor_sync(0xffffffffu, pix_sum.x, off);
       pix_sum.y += __shfl_xor_sync(0xffffffffu, pix_sum.y, off);
@@ -240,6 +309,9 @@ __device__ __forceinline__ void megakernel(const LaunchArgs& A, long long unit, 
 // per-vertex shading out of line, more resident warps beat fewer spills -- the
 // forward runs best at 4 CTAs (64 registers, 48 vs 62 ms at 128 registers), the
 // adjoint at 3 (85 registers, 135 vs 148 ms).
+#ifndef PT_LB_THREADS
+#define PT_LB_THREADS 256  // block size the forward / replay register caps are computed for
+#endif
 #ifndef PT_FWD_MIN_BLOCKS
 #define PT_FWD_MIN_BLOCKS 4
 #endif

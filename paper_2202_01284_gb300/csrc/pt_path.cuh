@@ -17,6 +17,13 @@ enum : int {
   FEAT_ALL = 7
 };
 
+// Linkage of the per-vertex steps below (experiments build them inline).
+#ifdef PT_SHADE_INLINE
+#define PT_SHADE_FN __forceinline__
+#else
+#define PT_SHADE_FN __noinline__
+#endif
+
 // Per-vertex gradient sink of the adjoint: warp-aggregated atomics.
 // Constant-albedo rows and roughness entries are few and heavily shared, so the
 // lanes of a warp that hit the same entry are reduced with a shuffle tree and one
@@ -32,6 +39,7 @@ struct GradSink {
       float4* dst = G.tex[m.tex];
       if (dst) {
         cnt.add(7, 1);
+        cnt.add(13, 1);
         if (TEXAGG && A.tex_aggregate) {
           float v[3] = {g_alb.x, g_alb.y, g_alb.z};
           unsigned long long key = ((unsigned long long)m.tex << 32) | (unsigned)m.alb_ref;
@@ -175,7 +183,7 @@ __device__ __forceinline__ void path_start(const LaunchArgs& A, PathState& P, un
 // traversal loop of the megakernel keeps more registers (measured: adjoint -15 %,
 // forward -4 % on the 196k-triangle sphere workload).
 template <bool ADJ, bool JVP, bool INSTR, int DISPATCH, int FEAT = 0>
-__device__ __noinline__ bool path_shade(const LaunchArgs& A, PathState& P, const Hit& hit, bool grad_pass, float3 dl,
+__device__ PT_SHADE_FN bool path_shade(const LaunchArgs& A, PathState& P, const Hit& hit, bool grad_pass, float3 dl,
                                         GradSink& sink,
                                            Counters<INSTR>& cnt) {
   const DevScene& S = A.scene;
@@ -188,6 +196,7 @@ __device__ __noinline__ bool path_shade(const LaunchArgs& A, PathState& P, const
   if (hit.pos < 0) {
     P.fh.add(0xffffffffu);
     if (has_env) {
+      cnt.add(12, 1);
       int ex, ey;
       env_pixel(S, P.rd, ex, ey);
       const int ei = ey * S.env_w + ex;
@@ -239,6 +248,7 @@ __device__ __noinline__ bool path_shade(const LaunchArgs& A, PathState& P, const
   for (int k = 0; k < 8; ++k) u[k] = P.rng.uniform();
   const int type = sw0.x;
   if (type == PT_BSDF_NONE) return false;
+  cnt.add(7 + type, 1);  // PT_CNT_V_DIFFUSE .. PT_CNT_V_BLEND
 
   const float3 p = P.ro + P.rd * hit.t;
   const float b0 = 1.0f - hit.u - hit.v;
@@ -365,6 +375,7 @@ __device__ __noinline__ bool path_shade(const LaunchArgs& A, PathState& P, const
       pdf_l = p_env * env_pdf_at(S, x, y, st);
       valid = pdf_l > 0.0f;
       P.fh.add(0x80000000u | (uint32_t)(y * S.env_w + x));
+      cnt.add(12, 1);
     } else {
       const int k = cdf_pick_guided(S.light_cdf, S.light_guide, S.light_g, u[0]);
       const float4 l0 = __ldg(&S.lights[4 * k]);
@@ -450,7 +461,7 @@ __device__ __noinline__ bool path_shade(const LaunchArgs& A, PathState& P, const
 
 // Finish the vertex once the shadow ray is resolved.  Returns false if the path ended.
 template <bool ADJ, bool JVP, bool INSTR, int FEAT = 0>
-__device__ __noinline__ bool path_finish(const LaunchArgs& A, PathState& P, bool occluded, bool grad_pass,
+__device__ PT_SHADE_FN bool path_finish(const LaunchArgs& A, PathState& P, bool occluded, bool grad_pass,
                                             float3 dl, GradSink& sink, Counters<INSTR>& cnt) {
   if (A.nee && P.mtype != PT_BSDF_DIELECTRIC && (A.scene.n_lights > 0 || A.scene.env_w > 0))
     P.fh.add(P.has_shadow ? (occluded ? 1u : 0u) : 2u);

@@ -471,7 +471,7 @@ __global__ void __launch_bounds__(128, 8) reparam_kernel(const __grid_constant__
   unsigned rays = 0;
   Counters<INSTR> cnt;
   if constexpr (INSTR)
-    for (int i = 0; i < 8; ++i) cnt.c[i] = 0;
+    for (int i = 0; i < kCounters; ++i) cnt.c[i] = 0;
   const float3 z = f3(0.f, 0.f, 0.f);
   float3 dl = z, fwd = z;
   if (valid) {
@@ -757,7 +757,7 @@ __global__ void __launch_bounds__(128, 8) edge_kernel(const __grid_constant__ La
   VertOut GV{grad_v};
   Counters<INSTR> cnt;
   if constexpr (INSTR)
-    for (int i = 0; i < 8; ++i) cnt.c[i] = 0;
+    for (int i = 0; i < kCounters; ++i) cnt.c[i] = 0;
   const float3 z = f3(0.f, 0.f, 0.f);
   const long long unit = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   unsigned rays = 0;

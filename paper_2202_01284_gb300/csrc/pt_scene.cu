@@ -261,8 +261,9 @@ extern "C" int pt_scene_create(const pt_scene_desc* d, pt_scene** out) {
     s->info.env_bytes = (int64_t)(n * 16 + marg.size() * 4 + cond.size() * 4 + n * 4);
   }
   if (st == PT_OK) {
-    if (cudaMalloc(&s->d_status, sizeof(int)) != cudaSuccess) st = PT_ERR_OOM;
-    else if (cudaMemset(s->d_status, 0, sizeof(int)) != cudaSuccess) st = PT_ERR_CUDA;
+    // status word at byte 0, the persistent launches' work counter at byte 128
+    if (cudaMalloc(&s->d_status, 256) != cudaSuccess) st = PT_ERR_OOM;
+    else if (cudaMemset(s->d_status, 0, 256) != cudaSuccess) st = PT_ERR_CUDA;
   }
   if (st != PT_OK) {
     cudaGetLastError();
@@ -282,6 +283,7 @@ extern "C" int pt_scene_create(const pt_scene_desc* d, pt_scene** out) {
   s->dev.env_cond = (const float*)s->d_env_cond;
   s->dev.env_p = (const float*)s->d_env_p;
   s->dev.status = (int*)s->d_status;
+  s->queue = reinterpret_cast<unsigned long long*>(static_cast<char*>(s->d_status) + 128);
   s->dev.n_tris = d->n_tris;
   s->info.n_tris = d->n_tris;
   *out = s;

@@ -36,6 +36,7 @@ class RenderSettings:
     cache: Optional[int] = None          # pt_cache handle: cache-terminated paths
     cache_bounce: int = 1
     prb_mode: int = 0                    # backward: 0 auto (= split), 1 fused PRB, 2 split (abi.PT_PRB_*)
+    schedule: int = 0                    # 0 auto (persistent replay, static rest), 1 persistent, 2 static
 
     def rows_cols(self):
         return (self.crop[3], self.crop[2]) if self.crop else (self.height, self.width)
@@ -85,7 +86,7 @@ class DeviceScene:
         return abi.render_desc(cams, st.width, st.height, st.spp, st.max_depth,
                                st.seed if seed is None else seed, st.rr_depth, st.nee, st.dispatch, st.crop,
                                st.lanes_per_pixel, st.block_size, st.tex_aggregate, dbg_L, dbg_hash, counters,
-                               st.cache, st.cache_bounce, st.prb_mode)
+                               st.cache, st.cache_bounce, st.prb_mode, st.schedule)
 
     def forward(self, st: RenderSettings, cams: Optional[Sequence[S.Camera]] = None, albedo=None, textures=None,
                 roughness=None, out=None, per_sample=False, counters=None, env=None):
