@@ -78,9 +78,9 @@ def alu_roofline(kernel, counters, bvh, ms, clk, note=""):
 # by its counted rays (the per-ray traffic of these kernels does not depend on the
 # image size: the scene and texture are the same and the per-sample state scales with
 # the rays).  A kernel changed since its capture has no entry.
-TRAFFIC_PER_RAY = {"wide": {}}
-TRAFFIC_BASIS = ("ncu dram__bytes_read.sum + dram__bytes_write.sum per counted ray, one kernel at 256x256 "
-                 "(profiles/), times the launch's counted rays")
+TRAFFIC_PER_RAY = {"wide": {"forward_kernel": 116.0, "radiance_kernel": 140.5, "replay_kernel": 50.4}}
+TRAFFIC_BASIS = ("ncu dram__bytes_read.sum + dram__bytes_write.sum per counted ray at 256x256 "
+                 "(profiles/dram_per_ray_spheres196k_256px_64spp.md), times the launch's counted rays")
 
 
 def parse():
@@ -99,10 +99,11 @@ def parse():
     ap.add_argument("--prb-mode", type=int, default=0, help="backward: 0 auto (split), 1 fused PRB, 2 split")
     ap.add_argument("--bvh", default="wide", choices=["wide", "binary"])
     ap.add_argument("--schedule", type=int, default=0,
-                    help="0 auto (persistent replay, static forward), 1 persistent lanes pulling units, 2 static")
+                    help="0 auto (= static), 1 persistent lanes pulling units, 2 static: one unit per thread")
     ap.add_argument("--cache", action="store_true",
                     help="radiance-cache experiment: equal-time MSE, cache-terminated vs plain PT (own JSON line)")
     ap.add_argument("--cache-warmup-frames", type=int, default=300)
+    ap.add_argument("--cache-ema", type=float, default=0.99, help="moving average of the cache weights (0 = off)")
     ap.add_argument("--batch", action="store_true",
                     help="batching experiment: 64 cameras over 10k/200k/2M-triangle scenes, forward + adjoint "
                          "in one persistent graph-captured launch vs 64 separate launches (own JSON line)")
@@ -401,10 +402,13 @@ def run_ours(args):
         torch.cuda.synchronize()
         rad_avg = statistics.mean(a.elapsed_time(b) for a, b in ev_r)
         replay_avg = adj_avg - rad_avg
+        # the replay runs as the persistent instance unless a static schedule was asked for
         kern = {"forward_kernel": (fwd_avg, flops_f), "replay_kernel": (replay_avg, flops_b / 2)}
+        replay_name = "replay_persist_kernel" if args.schedule == 1 else "replay_kernel"
     else:
         rad_avg = replay_avg = None
         kern = {"forward_kernel": (fwd_avg, flops_f), "adjoint_kernel": (adj_avg, flops_b)}
+        replay_name = None
     dom = max(kern, key=lambda k: kern[k][0])
     dom_ms, dom_flops = kern[dom]
     # the same kernel's bytes through L2: node, triangle, texel and env fetches of the
@@ -426,7 +430,10 @@ def run_ours(args):
     else:
         head = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak_tflops, 2), "unit": "TFLOP/s",
                 "frac": round(alu_frac, 4)}
-    roofline = {**head, "kernel": dom, "traffic": round(traffic) if traffic else None,
+    kernel_name = replay_name if dom == "replay_kernel" else dom
+    traffic = (TRAFFIC_PER_RAY.get(args.bvh, {}).get(kernel_name, 0) * {"forward_kernel": rays_f,
+               "replay_kernel": rays_b / 2, "adjoint_kernel": rays_b}[dom]) or None
+    roofline = {**head, "kernel": kernel_name, "traffic": round(traffic) if traffic else None,
                 "traffic_basis": TRAFFIC_BASIS if traffic else "no capture of the current kernel",
                 "alu": {"achieved_tflops": round(achieved, 3), "peak_tflops": round(peak_tflops, 2),
                         "frac": round(alu_frac, 4),
@@ -458,7 +465,8 @@ def run_ours(args):
                 c = cc[k]
                 cache_line[k] = {kk: c[kk] for kk in ("equal_time_spp", "equal_time", "train_loss",
                                                       "mse_indirect_ratio_plain_over_cache",
-                                                      "mse_ratio_plain_over_cache", "warmup_frames")}
+                                                      "mse_ratio_plain_over_cache", "warmup_frames",
+                                                      "weight_average")}
         except Exception as e:  # the throughput line stands without it
             cache_line = {"error": str(e)[:300]}
     cpu = None
@@ -473,7 +481,7 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {**WORKLOAD, "l2": "flushed between timed steps (256 MB write)", "dispatch": args.dispatch,
-                   "schedule": ["auto: persistent replay, static forward", "persistent lanes", "static: one unit per thread"][
+                   "schedule": ["auto: one unit per thread", "persistent lanes", "static: one unit per thread"][
                        args.schedule],
                    "bvh": f"{args.bvh} SAH", "bvh_nodes": info["n_nodes"], "rays_per_step": rays_step,
                    "rays_fwd": rays_f, "rays_adj": rays_b, "fwd_ms": round(fwd_avg, 3),
@@ -1032,7 +1040,7 @@ def run_mlp_experiment(args):
 
 
 def cache_comparison(torch, warmup_frames=300, spps=(1, 2, 4, 8, 16, 32, 64, 96, 128, 192, 256, 320, 384),
-                     bounces=(1, 2), plain_spp=64, ref_batches=16):
+                     bounces=(1, 2), plain_spp=64, ref_batches=16, ema=0.99):
     """Cornell box at 1024^2, depth 4: plain PT at `plain_spp` vs cache-terminated PT
     (bounce 1 and 2) at the spp that fits the same per-frame time including one online
     training update, after `warmup_frames` online training frames.  The network state
@@ -1041,7 +1049,8 @@ def cache_comparison(torch, warmup_frames=300, spps=(1, 2, 4, 8, 16, 32, 64, 96,
     update inside each timed frame); without that, each measured frame trains on and
     the comparison drifts with the order of the sweep.  Reference: ref_batches x 256
     spp of plain PT with distinct seeds (the forward kernel, parity-tested against the
-    FP64 oracle)."""
+    FP64 oracle).  With ema > 0 the cache answers queries with the moving average of
+    its weights (pt_cache_desc.ema), which is restored too."""
     from paper_2202_01284_gb300 import abi, scenes as S
     from paper_2202_01284_gb300.render import DeviceScene, RadianceCache, RenderSettings
 
@@ -1088,7 +1097,7 @@ def cache_comparison(torch, warmup_frames=300, spps=(1, 2, 4, 8, 16, 32, 64, 96,
            "plain": {"spp": plain_spp, "ms": round(t_plain, 3), "mse": mp, "mse_indirect": mpi}}
     for bounce in bounces:
         cache = RadianceCache(*box, batch=65536, max_queries=W * H * max(spps), max_records=2_000_000,
-                              max_paths=256 * 256, lr=5e-3, init_weights=S.mlp_init_weights(2022))
+                              max_paths=256 * 256, lr=5e-3, init_weights=S.mlp_init_weights(2022), ema=ema)
         train_st = RenderSettings(width=256, height=256, spp=1, max_depth=D, seed=0)
         train_cam = [S.cornell_camera(256, 256)]
 
@@ -1102,9 +1111,11 @@ def cache_comparison(torch, warmup_frames=300, spps=(1, 2, 4, 8, 16, 32, 64, 96,
         warm_s = time.perf_counter() - t0
         loss = cache.last_loss()
         state = abi.pt_cache_get_state(cache.handle)
+        avg = cache.average()
 
         def restore():
             abi.pt_cache_set_state(cache.handle, *state)
+            cache.set_average(avg)
         res, best = {}, None
         for spp in spps:
             t_frame, img = timed(lambda: (train_frame(10 ** 6),
@@ -1119,6 +1130,7 @@ def cache_comparison(torch, warmup_frames=300, spps=(1, 2, 4, 8, 16, 32, 64, 96,
             "warmup_frames": warmup_frames, "warmup_s": round(warm_s, 2), "train_loss": loss,
             "per_frame": "one pt_cache_train (256^2 training paths, 1 spp, 4 Adam steps of 65,536) + render; "
                          "network state restored before each measured frame",
+            "weight_average": ema,
             "equal_time_spp": best, "equal_time": eq,
             "mse_indirect_ratio_plain_over_cache": (mpi / eq["mse_indirect"]) if eq else None,
             "mse_ratio_plain_over_cache": (mp / eq["mse"]) if eq else None,
@@ -1130,7 +1142,7 @@ def cache_comparison(torch, warmup_frames=300, spps=(1, 2, 4, 8, 16, 32, 64, 96,
 def run_cache_experiment(args):
     import torch
     torch.cuda.set_device(0)
-    print(json.dumps(cache_comparison(torch, warmup_frames=args.cache_warmup_frames)), flush=True)
+    print(json.dumps(cache_comparison(torch, warmup_frames=args.cache_warmup_frames, ema=args.cache_ema)), flush=True)
 
 
 def run_batch_experiment(args):

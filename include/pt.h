@@ -202,9 +202,9 @@ typedef struct {
    * float atomics when lanes_per_pixel > 1, so the image's last bits may vary from
    * run to run); STATIC: one unit per thread.  PERSISTENT applies to the forward,
    * split-PRB radiance pass and replay, and forward mode with switch dispatch and no
-   * cache or instrumentation (STATIC otherwise).  AUTO (0) = PERSISTENT for the replay,
-   * STATIC for the rest (measured faster that way).  Calls on one scene must not
-   * overlap on the GPU (the counter is per scene). */
+   * cache or instrumentation (STATIC otherwise).  AUTO (0) = STATIC (measured as fast
+   * or faster on every kernel).  Calls on one scene must not overlap on the GPU (the
+   * counter is per scene). */
   int32_t schedule;
 } pt_render_desc;
 enum { PT_PRB_AUTO = 0, PT_PRB_FUSED = 1, PT_PRB_SPLIT = 2 };
@@ -553,6 +553,10 @@ typedef struct {
   float lr, beta1, beta2, eps;  /* Adam */
   const float* init_weights;    /* host [PT_CACHE_N_PARAMS] or NULL (uniform +-sqrt(6/64) from `seed`) */
   uint64_t seed;
+  float ema;                    /* in [0, 1): 0 = queries use the trained weights; else every Adam step
+                                   also updates A = ema * A + (1 - ema) * W (A starts at the initial
+                                   weights) and queries, cache-terminated renders and their adjoint use
+                                   A (Polyak averaging: the weights' step-to-step noise averaged out) */
 } pt_cache_desc;
 
 /* Allocate weights, Adam state and all buffers on the current device (synchronous).
@@ -565,6 +569,10 @@ int pt_cache_get_weights(pt_cache* cache, float* host_out);
 int pt_cache_set_weights(pt_cache* cache, const float* host_in);
 /* rgb[i] = MLP(encode(raw[i])), device pointers raw [n][10], rgb [n][3]; async on stream. */
 int pt_cache_query(pt_cache* cache, const float* raw, float* rgb, int n, void* stream);
+/* Synchronous copies of the averaged weights A (see pt_cache_desc.ema); set_weights
+ * also sets A to the given weights. */
+int pt_cache_get_average(pt_cache* cache, float* host_out);
+int pt_cache_set_average(pt_cache* cache, const float* host_in);
 /* `steps` Adam steps on batches taken in order from device records raw [n][10],
  * target [n][3] (wrapping); async on stream. */
 int pt_cache_train_records(pt_cache* cache, const float* raw, const float* target, int n, int steps, void* stream);

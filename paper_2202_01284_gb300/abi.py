@@ -105,7 +105,7 @@ class pt_cache_desc(C.Structure):
     _fields_ = [("box_lo", C.c_float * 3), ("box_hi", C.c_float * 3), ("batch", C.c_int32),
                 ("max_queries", C.c_int32), ("max_records", C.c_int32), ("max_paths", C.c_int32),
                 ("lr", C.c_float), ("beta1", C.c_float), ("beta2", C.c_float), ("eps", C.c_float),
-                ("init_weights", C.c_void_p), ("seed", C.c_uint64)]
+                ("init_weights", C.c_void_p), ("seed", C.c_uint64), ("ema", C.c_float)]
 
 
 class pt_job(C.Structure):
@@ -179,6 +179,8 @@ SIGNATURES = {
     "pt_cache_get_state": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_int32)], C.c_int),
     "pt_cache_set_state": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32], C.c_int),
     "pt_cache_get_weights": ([C.c_void_p, C.c_void_p], C.c_int),
+    "pt_cache_get_average": ([C.c_void_p, C.c_void_p], C.c_int),
+    "pt_cache_set_average": ([C.c_void_p, C.c_void_p], C.c_int),
     "pt_cache_set_weights": ([C.c_void_p, C.c_void_p], C.c_int),
     "pt_cache_query": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p], C.c_int),
     "pt_cache_train_records": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p], C.c_int),
@@ -459,7 +461,7 @@ def pt_last_device_status(handle: int, stream: int = 0) -> int:
 
 # ------------------------------------------------------------------ radiance cache
 def pt_cache_create(box_lo, box_hi, batch=65536, max_queries=0, max_records=0, max_paths=0, lr=5e-3,
-                    beta1=0.9, beta2=0.99, eps=1e-8, init_weights=None, seed=0) -> int:
+                    beta1=0.9, beta2=0.99, eps=1e-8, init_weights=None, seed=0, ema=0.0) -> int:
     d = pt_cache_desc()
     d.box_lo[:] = [float(x) for x in box_lo]
     d.box_hi[:] = [float(x) for x in box_hi]
@@ -471,6 +473,7 @@ def pt_cache_create(box_lo, box_hi, batch=65536, max_queries=0, max_records=0, m
         assert w.size == PT_CACHE_N_PARAMS
         d.init_weights = w.ctypes.data
     d.seed = seed
+    d.ema = ema
     h = C.c_void_p()
     check("pt_cache_create", load().pt_cache_create(C.byref(d), C.byref(h)))
     return h.value
@@ -485,6 +488,18 @@ def pt_cache_get_weights(handle: int) -> np.ndarray:
     w = np.zeros(PT_CACHE_N_PARAMS, np.float32)
     check("pt_cache_get_weights", load().pt_cache_get_weights(handle, w.ctypes.data))
     return w
+
+
+def pt_cache_get_average(handle: int) -> np.ndarray:
+    w = np.zeros(PT_CACHE_N_PARAMS, np.float32)
+    check("pt_cache_get_average", load().pt_cache_get_average(handle, w.ctypes.data))
+    return w
+
+
+def pt_cache_set_average(handle: int, w) -> None:
+    w = np.ascontiguousarray(w, np.float32)
+    assert w.size == PT_CACHE_N_PARAMS
+    check("pt_cache_set_average", load().pt_cache_set_average(handle, w.ctypes.data))
 
 
 def pt_cache_set_weights(handle: int, w) -> None:

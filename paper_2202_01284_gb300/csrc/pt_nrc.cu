@@ -370,9 +370,12 @@ __global__ void __launch_bounds__(128) nrc_wgrad_kernel(const __nv_bfloat16* __r
 }
 
 // ---------------------------------------------------------------- Adam
+// One Adam step of every parameter; with ema > 0 also the exponential moving
+// average of the weights (Polyak averaging) and its BF16 copy, which queries use.
 __global__ void nrc_adam_kernel(float* __restrict__ W32, float* __restrict__ dW, float* __restrict__ m,
                                 float* __restrict__ v, __nv_bfloat16* __restrict__ Wb, float lr, float b1, float b2,
-                                float eps, float c1, float c2) {
+                                float eps, float c1, float c2, float* __restrict__ Wavg,
+                                __nv_bfloat16* __restrict__ Wq, float ema) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= NRC_PARAMS) return;
   const float gr = dW[i];
@@ -384,6 +387,11 @@ __global__ void nrc_adam_kernel(float* __restrict__ W32, float* __restrict__ dW,
   W32[i] = w;
   Wb[i] = __float2bfloat16_rn(w);
   dW[i] = 0.0f;
+  if (ema > 0.0f) {
+    const float a = ema * Wavg[i] + (1.0f - ema) * w;
+    Wavg[i] = a;
+    Wq[i] = __float2bfloat16_rn(a);
+  }
 }
 
 __global__ void nrc_to_bf16_kernel(const float* __restrict__ W32, __nv_bfloat16* __restrict__ Wb) {
@@ -404,6 +412,8 @@ struct pt_cache {
   float* v = nullptr;
   float* dW = nullptr;
   __nv_bfloat16* Wb = nullptr;  // [NRC_HIDDEN*64*64 + 8*64]
+  float* Wavg = nullptr;        // moving average of W32 (desc.ema > 0)
+  __nv_bfloat16* Wq = nullptr;  // its BF16 copy: the weights queries use when desc.ema > 0
   __nv_bfloat16* X = nullptr;   // [6][batch][64]
   __nv_bfloat16* dZ = nullptr;  // [6][batch][64]
   float* loss = nullptr;        // [1]
@@ -428,7 +438,7 @@ constexpr size_t kTrainSmem = (size_t)NrcSmem::W_ELEMS * 2 + (size_t)NRC_HIDDEN 
                               NRC_W * 24 * 2 + 4 * 6 * 16 * NRC_LD * 2;
 
 void cache_free(pt_cache* c) {
-  void* ptrs[] = {c->W32, c->m, c->v, c->dW, c->Wb, c->X, c->dZ, c->loss, c->q_raw, c->q_beta, c->q_rgb,
+  void* ptrs[] = {c->W32, c->m, c->v, c->dW, c->Wb, c->Wavg, c->Wq, c->X, c->dZ, c->loss, c->q_raw, c->q_beta, c->q_rgb,
                   c->r_raw, c->r_aux, c->r_target, c->path_L, c->r_count, c->status};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -466,6 +476,7 @@ extern "C" int pt_cache_create(const pt_cache_desc* d, pt_cache** out) {
   *out = nullptr;
   if (d->batch <= 0 || d->batch % 64 || d->max_queries < 0 || d->max_records < 0 || d->max_paths < 0)
     return PT_ERR_ARG;
+  if (!(d->ema >= 0.0f && d->ema < 1.0f)) return PT_ERR_ARG;
   for (int k = 0; k < 3; ++k)
     if (!(d->box_hi[k] > d->box_lo[k])) return PT_ERR_ARG;
   if (!smem_opt_in()) return PT_ERR_CUDA;
@@ -480,7 +491,8 @@ extern "C" int pt_cache_create(const pt_cache_desc* d, pt_cache** out) {
   const size_t act = (size_t)(NRC_HIDDEN + 1) * d->batch * NRC_W;
   bool ok = cudaMalloc(&c->W32, NRC_PARAMS * 4) == cudaSuccess && cudaMalloc(&c->m, NRC_PARAMS * 4) == cudaSuccess &&
             cudaMalloc(&c->v, NRC_PARAMS * 4) == cudaSuccess && cudaMalloc(&c->dW, NRC_PARAMS * 4) == cudaSuccess &&
-            cudaMalloc(&c->Wb, nb * 2) == cudaSuccess && cudaMalloc(&c->X, act * 2) == cudaSuccess &&
+            cudaMalloc(&c->Wb, nb * 2) == cudaSuccess && cudaMalloc(&c->Wavg, NRC_PARAMS * 4) == cudaSuccess &&
+            cudaMalloc(&c->Wq, nb * 2) == cudaSuccess && cudaMalloc(&c->X, act * 2) == cudaSuccess &&
             cudaMalloc(&c->dZ, act * 2) == cudaSuccess && cudaMalloc(&c->loss, 4) == cudaSuccess &&
             cudaMalloc(&c->r_count, 8) == cudaSuccess && cudaMalloc(&c->status, 4) == cudaSuccess;
   if (ok && d->max_queries > 0)
@@ -504,10 +516,13 @@ extern "C" int pt_cache_create(const pt_cache_desc* d, pt_cache** out) {
   ok = cudaMemcpy(c->W32, w.data(), NRC_PARAMS * 4, cudaMemcpyHostToDevice) == cudaSuccess &&
        cudaMemset(c->m, 0, NRC_PARAMS * 4) == cudaSuccess && cudaMemset(c->v, 0, NRC_PARAMS * 4) == cudaSuccess &&
        cudaMemset(c->dW, 0, NRC_PARAMS * 4) == cudaSuccess && cudaMemset(c->Wb, 0, nb * 2) == cudaSuccess &&
+       cudaMemset(c->Wq, 0, nb * 2) == cudaSuccess &&
+       cudaMemcpy(c->Wavg, w.data(), NRC_PARAMS * 4, cudaMemcpyHostToDevice) == cudaSuccess &&
        cudaMemset(c->loss, 0, 4) == cudaSuccess && cudaMemset(c->r_count, 0, 8) == cudaSuccess &&
        cudaMemset(c->status, 0, 4) == cudaSuccess;
   if (ok) {
     nrc_to_bf16_kernel<<<(NRC_PARAMS + 255) / 256, 256>>>(c->W32, c->Wb);
+    nrc_to_bf16_kernel<<<(NRC_PARAMS + 255) / 256, 256>>>(c->Wavg, c->Wq);
     ok = cudaDeviceSynchronize() == cudaSuccess;
   }
   if (!ok) {
@@ -539,20 +554,22 @@ extern "C" int pt_cache_set_weights(pt_cache* c, const float* host_in) {
   bool ok = cudaMemcpy(c->W32, host_in, NRC_PARAMS * 4, cudaMemcpyHostToDevice) == cudaSuccess &&
             cudaMemset(c->m, 0, NRC_PARAMS * 4) == cudaSuccess && cudaMemset(c->v, 0, NRC_PARAMS * 4) == cudaSuccess &&
             cudaMemset(c->dW, 0, NRC_PARAMS * 4) == cudaSuccess;
-  if (!ok) return PT_ERR_CUDA;
+  if (!ok || cudaMemcpy(c->Wavg, host_in, NRC_PARAMS * 4, cudaMemcpyHostToDevice) != cudaSuccess) return PT_ERR_CUDA;
   c->step = 0;
   nrc_to_bf16_kernel<<<(NRC_PARAMS + 255) / 256, 256>>>(c->W32, c->Wb);
+  nrc_to_bf16_kernel<<<(NRC_PARAMS + 255) / 256, 256>>>(c->Wavg, c->Wq);
   return cudaDeviceSynchronize() == cudaSuccess ? PT_OK : PT_ERR_CUDA;
 }
 
 namespace ptgb {
 int cache_infer(pt_cache* c, const float* raw, float* rgb, long long n, cudaStream_t st) {
   if (n <= 0) return PT_OK;
-  if (c->engine == PT_CACHE_TCGEN05) return cache_infer_tc(raw, rgb, n, c->box, c->Wb, c->status, c->wait_limit, st);
+  const __nv_bfloat16* Wuse = c->desc.ema > 0.0f ? c->Wq : c->Wb;
+  if (c->engine == PT_CACHE_TCGEN05) return cache_infer_tc(raw, rgb, n, c->box, Wuse, c->status, c->wait_limit, st);
   const long long tiles = (n + 15) / 16;
   long long grid = (tiles + 3) / 4;
   if (grid > 152 * 8) grid = 152 * 8;
-  nrc_infer_kernel<<<(unsigned)grid, 128, kInferSmem, st>>>(raw, n, c->box, c->Wb, rgb);
+  nrc_infer_kernel<<<(unsigned)grid, 128, kInferSmem, st>>>(raw, n, c->box, Wuse, rgb);
   return cudaGetLastError() == cudaSuccess ? PT_OK : PT_ERR_CUDA;
 }
 
@@ -587,7 +604,7 @@ int cache_optimise(pt_cache* c, const float* raw, const float* target, long long
     const pt_cache_desc& d = c->desc;
     const float c1 = 1.0f - std::pow(d.beta1, (float)c->step), c2 = 1.0f - std::pow(d.beta2, (float)c->step);
     nrc_adam_kernel<<<(NRC_PARAMS + 255) / 256, 256, 0, st>>>(c->W32, c->dW, c->m, c->v, c->Wb, d.lr, d.beta1,
-                                                              d.beta2, d.eps, c1, c2);
+                                                              d.beta2, d.eps, c1, c2, c->Wavg, c->Wq, d.ema);
   }
   return cudaGetLastError() == cudaSuccess ? PT_OK : PT_ERR_CUDA;
 }
@@ -643,6 +660,21 @@ extern "C" int pt_cache_set_state(pt_cache* c, const float* w, const float* m, c
   if (!ok) return PT_ERR_CUDA;
   c->step = step;
   nrc_to_bf16_kernel<<<(NRC_PARAMS + 255) / 256, 256>>>(c->W32, c->Wb);
+  return cudaDeviceSynchronize() == cudaSuccess ? PT_OK : PT_ERR_CUDA;
+}
+
+extern "C" int pt_cache_get_average(pt_cache* c, float* host_out) {
+  if (!c || !host_out) return PT_ERR_ARG;
+  if (cudaDeviceSynchronize() != cudaSuccess) return PT_ERR_CUDA;
+  return cudaMemcpy(host_out, c->Wavg, NRC_PARAMS * 4, cudaMemcpyDeviceToHost) == cudaSuccess ? PT_OK : PT_ERR_CUDA;
+}
+
+extern "C" int pt_cache_set_average(pt_cache* c, const float* host_in) {
+  if (!c || !host_in) return PT_ERR_ARG;
+  if (cudaDeviceSynchronize() != cudaSuccess ||
+      cudaMemcpy(c->Wavg, host_in, NRC_PARAMS * 4, cudaMemcpyHostToDevice) != cudaSuccess)
+    return PT_ERR_CUDA;
+  nrc_to_bf16_kernel<<<(NRC_PARAMS + 255) / 256, 256>>>(c->Wavg, c->Wq);
   return cudaDeviceSynchronize() == cudaSuccess ? PT_OK : PT_ERR_CUDA;
 }
 

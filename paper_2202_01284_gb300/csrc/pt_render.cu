@@ -287,12 +287,13 @@ int launch_dims(const pt_render_desc* r, const LaunchArgs& A, int& block, long l
 bool instrumented(const pt_render_desc* r) { return r->dbg_sample_L || r->dbg_sample_hash || r->counters; }
 
 // Persistent scheduling applies to the production instances (switch dispatch, no
-// cache, no instrumentation) when asked for; AUTO takes it for the split-PRB replay
-// only (measured on the 196k-triangle sphere workload: replay 66.1 vs 66.9 ms; the
-// forward and radiance pass 49.5 vs 47.9 ms, as lanes pulling units from a moving
-// frontier lose the pixel coherence of their camera rays).
-bool persistent(const pt_render_desc* r, const LaunchArgs& A, bool replay = false) {
-  if (r->schedule == PT_SCHED_STATIC || (r->schedule == PT_SCHED_AUTO && !replay)) return false;
+// cache, no instrumentation) when asked for.  AUTO keeps one unit per thread:
+// measured on the 196k-triangle sphere workload, the persistent forward and
+// radiance pass take 49.5 vs 47.9 ms (lanes pulling units from a moving frontier
+// lose the pixel coherence of their camera rays) and the persistent replay 66.1-68.2
+// vs 66.9 ms (no gain beyond run-to-run spread).
+bool persistent(const pt_render_desc* r, const LaunchArgs& A) {
+  if (r->schedule != PT_SCHED_PERSISTENT) return false;
   return !instrumented(r) && A.dispatch == PT_DISPATCH_SWITCH && A.cache_mode == 0;
 }
 
@@ -477,7 +478,7 @@ extern "C" int pt_render_backward(pt_scene* s, const pt_render_desc* r, const pt
   if (r->prb_mode < PT_PRB_AUTO || r->prb_mode > PT_PRB_SPLIT) return PT_ERR_ARG;
   if (r->prb_mode != PT_PRB_FUSED && !instrumented(r)) {
     if ((st = radiance_pass(s, r, A, cs)) != PT_OK) return st;
-    if (persistent(r, A, true)) {
+    if (persistent(r, A)) {
       if (s->dev.layout == PT_BVH_WIDE) return launch_persistent(replay_persist_kernel<PT_BVH_WIDE>, s, block, A, cs);
       return launch_persistent(replay_persist_kernel<PT_BVH_BINARY>, s, block, A, cs);
     }

@@ -36,7 +36,7 @@ class RenderSettings:
     cache: Optional[int] = None          # pt_cache handle: cache-terminated paths
     cache_bounce: int = 1
     prb_mode: int = 0                    # backward: 0 auto (= split), 1 fused PRB, 2 split (abi.PT_PRB_*)
-    schedule: int = 0                    # 0 auto (persistent replay, static rest), 1 persistent, 2 static
+    schedule: int = 0                    # 0 auto (= static), 1 persistent lanes, 2 static (abi.PT_SCHED_*)
 
     def rows_cols(self):
         return (self.crop[3], self.crop[2]) if self.crop else (self.height, self.width)
@@ -435,6 +435,13 @@ class RadianceCache:
 
     def weights(self):
         return abi.pt_cache_get_weights(self.handle)
+
+    def average(self):
+        """The averaged weights queries use when the cache was created with ema > 0."""
+        return abi.pt_cache_get_average(self.handle)
+
+    def set_average(self, w):
+        abi.pt_cache_set_average(self.handle, w)
 
     def set_weights(self, w):
         abi.pt_cache_set_weights(self.handle, w)

@@ -43,7 +43,8 @@ def c4():
 
 
 def _crop_of(cam):
-    return (cam.width // 2 - 8, cam.height // 3, 16, 16)
+    # the image centre looks at the spheres (every camera aims at their middle)
+    return (cam.width // 2 - 8, cam.height // 2 - 8, 16, 16)
 
 
 def _zero(jobs):
@@ -95,13 +96,28 @@ def test_c4_batch_gradients_match_oracle(c4, oracle_mod):
     abi.pt_render_batch([j.struct() for j in jobs], opts, stream)
     torch.cuda.synchronize()
     rng = np.random.default_rng(11)
+    n_div = 0
     for k in picks:
-        j = jobs[k]
-        x0, y0, w, h = _crop_of(cams[k].camera)
+        bc, j = cams[k], jobs[k]
+        crop = _crop_of(bc.camera)
+        x0, y0, w, h = crop
+        # pixels whose samples all take the oracle's decisions with the backward seed
+        # (the adjoint replays those paths); the others get target = image, i.e. no
+        # gradient on either side (a flipped texel or triangle choice between FP32 and
+        # FP64 moves whole gradient terms)
+        r = oracle_mod.render_in(bc.camera, bc.spp, 8, 2000 + k, 3, True, crop=crop)
+        _, _, refh = oracle_mod.render(oracle_mod.OracleScene(scenes[bc.scene]), r, per_sample=True)
+        st = render.RenderSettings(width=bc.camera.width, height=bc.camera.height, spp=bc.spp, max_depth=8,
+                                   rr_depth=3, seed=2000 + k, crop=crop)
+        _, _, gh = dss[bc.scene].forward(st, cams=[bc.camera], per_sample=True)
+        clean = (gh[0].cpu().numpy().view(np.uint32) == refh.astype(np.uint32)).all(axis=-1)
+        n_div += int((~clean).sum())
+        noise = rng.uniform(-0.2, 0.2, (h, w, 3)).astype(np.float32) * clean[..., None]
         t = j.image.clone()
-        t[y0:y0 + h, x0:x0 + w] += torch.as_tensor(rng.uniform(-0.2, 0.2, (h, w, 3)).astype(np.float32),
-                                                   device="cuda")
+        t[y0:y0 + h, x0:x0 + w] += torch.as_tensor(noise, device="cuda")
         j.target.copy_(t)
+    print(f"divergent pixels excluded from the gradient comparison: {n_div} of {16 * 16 * len(picks)}")
+    assert n_div <= 0.05 * 16 * 16 * len(picks)
     before = [j.image.clone() for j in jobs]
     _zero(jobs)
     abi.pt_render_batch([j.struct() for j in jobs], opts, stream)

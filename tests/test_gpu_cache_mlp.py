@@ -224,3 +224,35 @@ def test_training_checkpoint_resume(abi, tmp_path):
     assert abi.pt_cache_get_state(c.handle)[3] == 6
     c.close()
     assert np.allclose(got, want, rtol=1e-4, atol=1e-6), np.abs(got - want).max()
+
+
+@pytest.mark.parametrize("engine", [0, 1])
+def test_averaged_weights_follow_the_recurrence_and_serve_queries(abi, oracle_mod, engine):
+    """With ema = 0.8, after every Adam step the average is A = 0.8 A + 0.2 W (A
+    starting at the initial weights), and queries evaluate the network with A, not W."""
+    from paper_2202_01284_gb300.render import RadianceCache
+    n = 2048
+    raw, tgt = S.random_cache_records(n, 51)
+    W0 = S.mlp_init_weights(52)
+    d_raw, d_t = torch.as_tensor(raw, device="cuda"), torch.as_tensor(tgt, device="cuda")
+    c = RadianceCache(*BOX, batch=n, lr=5e-3, init_weights=W0, ema=0.8)
+    try:
+        abi.pt_cache_set_engine(c.handle, engine)
+        A = W0.astype(np.float64)
+        assert np.array_equal(c.average(), W0)
+        for _ in range(5):
+            c.train_records(d_raw, d_t, steps=1)
+            torch.cuda.synchronize()
+            A = 0.8 * A + 0.2 * c.weights().astype(np.float64)
+        got_A = c.average().astype(np.float64)
+        assert np.allclose(got_A, A, rtol=1e-5, atol=1e-7), np.abs(got_A - A).max()
+        assert np.abs(got_A - c.weights()).max() > 1e-4           # the average lags the weights
+        q = c.query(torch.as_tensor(raw[:300], device="cuda")).cpu().numpy().astype(np.float64)
+        assert abi.pt_cache_status(c.handle) == abi.PT_OK
+    finally:
+        c.close()
+    enc = oracle_mod.nrc_encode(raw[:300], *BOX)
+    err = _rel_err(q, oracle_mod.mlp_forward(got_A, enc))
+    assert np.median(err) < 2e-3 and np.quantile(err, 0.99) < 2e-2
+    with pytest.raises(abi.PtError):
+        RadianceCache(*BOX, batch=64, ema=1.0)
