@@ -200,7 +200,7 @@ __device__ __forceinline__ void megakernel(const LaunchArgs& A, long long unit, 
       if constexpr (REPLAY) {
         const float* l = A.sample_L + 3 * P.slot;
         P.Lrem = f3(l[0], l[1], l[2]);
-      } else {
+      } else if constexpr (ADJ) {
         P.Lrem = L_pass0;
       }
       has_path = true;

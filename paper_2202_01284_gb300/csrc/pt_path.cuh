@@ -14,6 +14,7 @@ namespace ptgb {
 // radiance, the adjoint replays only (no radiance pass of its own).
 enum : int {
   FEAT_EGRAD = 1, FEAT_CACHE = 2, FEAT_TEXAGG = 4, FEAT_CKPT = 8, FEAT_SAMPLE_L = 16, FEAT_REPLAY = 32,
+  FEAT_NOHASH = 64,  // no decision fingerprint (instances that never output it)
   FEAT_ALL = 7
 };
 
@@ -188,13 +189,14 @@ __device__ PT_SHADE_FN bool path_shade(const LaunchArgs& A, PathState& P, const 
                                            Counters<INSTR>& cnt) {
   const DevScene& S = A.scene;
   constexpr bool EGRAD = (FEAT & FEAT_EGRAD) != 0;
+  constexpr bool HASH = (FEAT & FEAT_NOHASH) == 0;
   const bool has_area = S.n_lights > 0;
   const bool has_env = S.env_w > 0;
   const float p_env = has_env ? (has_area ? 0.5f : 1.0f) : 0.0f;
   const float p_area = has_area ? 1.0f - p_env : 0.0f;
   P.has_shadow = false;
   if (hit.pos < 0) {
-    P.fh.add(0xffffffffu);
+    if constexpr (HASH) P.fh.add(0xffffffffu);
     if (has_env) {
       cnt.add(12, 1);
       int ex, ey;
@@ -208,7 +210,7 @@ __device__ PT_SHADE_FN bool path_shade(const LaunchArgs& A, PathState& P, const 
       }
       float3 c = P.beta * Le * w;
       P.L = P.L + c;
-      P.Lrem = P.Lrem - c;
+      if (ADJ) P.Lrem = P.Lrem - c;
       if (JVP) {
         P.L_dot = P.L_dot + P.beta_dot * Le * w;
         if (A.tangent.env) P.L_dot = P.L_dot + P.beta * xyz(__ldg(&A.tangent.env[ei])) * w;
@@ -220,7 +222,7 @@ __device__ PT_SHADE_FN bool path_shade(const LaunchArgs& A, PathState& P, const 
   const float4 tv0 = __ldg(&S.tri_v[3 * hit.pos]);
   const float4 tv1 = __ldg(&S.tri_v[3 * hit.pos + 1]);
   const float4 tv2 = __ldg(&S.tri_v[3 * hit.pos + 2]);
-  P.fh.add(__float_as_uint(tv0.w));
+  if constexpr (HASH) P.fh.add(__float_as_uint(tv0.w));
   const float4 ta0 = __ldg(&S.tri_a[2 * hit.pos]);
   const float4 ta1 = __ldg(&S.tri_a[2 * hit.pos + 1]);
   const int shape = __float_as_int(ta1.z);
@@ -239,7 +241,7 @@ __device__ PT_SHADE_FN bool path_shade(const LaunchArgs& A, PathState& P, const 
     }
     float3 c = P.beta * xyz(sw3) * w;
     P.L = P.L + c;
-    P.Lrem = P.Lrem - c;
+    if (ADJ) P.Lrem = P.Lrem - c;
     if (JVP) P.L_dot = P.L_dot + P.beta_dot * xyz(sw3) * w;
   }
   if (P.depth >= A.max_depth) return false;
@@ -287,7 +289,7 @@ __device__ PT_SHADE_FN bool path_shade(const LaunchArgs& A, PathState& P, const 
       m.alb_ref = sw0.z;
     }
   }
-  P.fh.add(texel_word);
+  if constexpr (HASH) P.fh.add(texel_word);
   // tangent of the differentiable inputs along the JVP direction
   float3 alb_dot = f3(0.f, 0.f, 0.f);
   float alpha_dot = 0.0f;
@@ -338,7 +340,7 @@ __device__ PT_SHADE_FN bool path_shade(const LaunchArgs& A, PathState& P, const 
         const float* q = A.q_rgb + P.slot * 3;
         const float3 c = P.beta * f3(fmaxf(q[0], 0.f), fmaxf(q[1], 0.f), fmaxf(q[2], 0.f));
         P.L = P.L + c;
-        P.Lrem = P.Lrem - c;
+        if (ADJ) P.Lrem = P.Lrem - c;
       }
       return false;
     }
@@ -348,7 +350,7 @@ __device__ PT_SHADE_FN bool path_shade(const LaunchArgs& A, PathState& P, const 
   P.c_nee = f3(0.f, 0.f, 0.f);
   if (EGRAD) P.nee_env = -1;
   if (JVP) P.c_nee_dot = f3(0.f, 0.f, 0.f);
-  P.r_nee_alb = P.r_nee_a = P.r_bsdf_alb = P.r_bsdf_a = f3(0.f, 0.f, 0.f);
+  if (ADJ) P.r_nee_alb = P.r_nee_a = P.r_bsdf_alb = P.r_bsdf_a = f3(0.f, 0.f, 0.f);
 
   // ---- next-event estimation: light sample + BSDF value toward it
   if (type != PT_BSDF_DIELECTRIC && A.nee && (has_area || has_env)) {
@@ -374,7 +376,7 @@ __device__ PT_SHADE_FN bool path_shade(const LaunchArgs& A, PathState& P, const 
       Le = xyz(__ldg(&(A.params.env ? A.params.env : S.env)[env_i]));
       pdf_l = p_env * env_pdf_at(S, x, y, st);
       valid = pdf_l > 0.0f;
-      P.fh.add(0x80000000u | (uint32_t)(y * S.env_w + x));
+      if constexpr (HASH) P.fh.add(0x80000000u | (uint32_t)(y * S.env_w + x));
       cnt.add(12, 1);
     } else {
       const int k = cdf_pick_guided(S.light_cdf, S.light_guide, S.light_g, u[0]);
@@ -395,7 +397,7 @@ __device__ PT_SHADE_FN bool path_shade(const LaunchArgs& A, PathState& P, const 
         pdf_l = p_area * dist * dist / (cos_l * S.light_area);
         valid = true;
       }
-      P.fh.add(__float_as_uint(l0.w));
+      if constexpr (HASH) P.fh.add(__float_as_uint(l0.w));
     }
     const float3 wl = fr.to_local(dir);
     BsdfEval ev;
@@ -435,7 +437,7 @@ __device__ PT_SHADE_FN bool path_shade(const LaunchArgs& A, PathState& P, const 
     if (bs.ok && !bs.delta)
       P.w_next_dot = (bs.ev.df_alb * alb_dot + bs.ev.df_alpha * alpha_dot) * (bs.wo.z / bs.pdf);
   }
-  P.lobe = bs.lobe;
+  if constexpr (HASH) P.lobe = bs.lobe;
   P.ok_next = bs.ok;
   P.delta_next = bs.delta;
   P.w_next = bs.weight;
@@ -450,12 +452,14 @@ __device__ PT_SHADE_FN bool path_shade(const LaunchArgs& A, PathState& P, const 
     P.no = offset_origin(p, ng, wo);
     P.nd = wo;
   }
-  P.alb_kind = m.alb_kind;
-  P.alb_ref = m.alb_ref;
-  P.tex = m.tex;
-  P.rough = m.rough;
-  P.mtype = type;
-  P.has_params = m.alb_kind != 0 || m.rough >= 0;
+  if (ADJ) {
+    P.alb_kind = m.alb_kind;
+    P.alb_ref = m.alb_ref;
+    P.tex = m.tex;
+    P.rough = m.rough;
+    P.has_params = m.alb_kind != 0 || m.rough >= 0;
+  }
+  if (ADJ || HASH) P.mtype = type;
   return true;
 }
 
@@ -463,18 +467,23 @@ __device__ PT_SHADE_FN bool path_shade(const LaunchArgs& A, PathState& P, const 
 template <bool ADJ, bool JVP, bool INSTR, int FEAT = 0>
 __device__ PT_SHADE_FN bool path_finish(const LaunchArgs& A, PathState& P, bool occluded, bool grad_pass,
                                             float3 dl, GradSink& sink, Counters<INSTR>& cnt) {
-  if (A.nee && P.mtype != PT_BSDF_DIELECTRIC && (A.scene.n_lights > 0 || A.scene.env_w > 0))
-    P.fh.add(P.has_shadow ? (occluded ? 1u : 0u) : 2u);
+  constexpr bool HASH = (FEAT & FEAT_NOHASH) == 0;
+  if constexpr (HASH) {
+    if (A.nee && P.mtype != PT_BSDF_DIELECTRIC && (A.scene.n_lights > 0 || A.scene.env_w > 0))
+      P.fh.add(P.has_shadow ? (occluded ? 1u : 0u) : 2u);
+  }
   const bool lit = P.has_shadow && !occluded;
   if (lit) {
     P.L = P.L + P.c_nee;
-    P.Lrem = P.Lrem - P.c_nee;
+    if (ADJ) P.Lrem = P.Lrem - P.c_nee;
     if (JVP) P.L_dot = P.L_dot + P.c_nee_dot;
     if (ADJ && (FEAT & FEAT_EGRAD) && grad_pass && P.nee_env >= 0)
       sink.add_env<INSTR>(A, P.nee_env, dl * P.nee_env_d, cnt);
   }
-  P.fh.add((uint32_t)P.lobe);
-  if (P.delta_next) P.fh.add(0xfffffffeu);
+  if constexpr (HASH) P.fh.add((uint32_t)P.lobe);
+  if constexpr (HASH) {
+    if (P.delta_next) P.fh.add(0xfffffffeu);
+  }
   if (ADJ && grad_pass && P.has_params) {
     const float3 cn = lit ? P.c_nee : f3(0.f, 0.f, 0.f);
     const float3 lr = P.ok_next ? f3(fmaxf(P.Lrem.x, 0.f), fmaxf(P.Lrem.y, 0.f), fmaxf(P.Lrem.z, 0.f))
@@ -499,7 +508,7 @@ __device__ PT_SHADE_FN bool path_finish(const LaunchArgs& A, PathState& P, bool 
   if (A.rr_depth >= 0 && P.depth >= A.rr_depth) {
     const float q = fminf(max3f(P.beta), 0.95f);
     const bool cont = P.u6 < q;
-    P.fh.add(cont ? 1u : 0u);
+    if constexpr (HASH) P.fh.add(cont ? 1u : 0u);
     if (!cont) return false;
     P.beta = P.beta * (1.0f / q);
     if (JVP) P.beta_dot = P.beta_dot * (1.0f / q);
