@@ -79,6 +79,9 @@ def alu_roofline(kernel, counters, bvh, ms, clk, note=""):
 # image size: the scene and texture are the same and the per-sample state scales with
 # the rays).  A kernel changed since its capture has no entry.
 TRAFFIC_PER_RAY = {"wide": {"forward_kernel": 116.0, "radiance_kernel": 140.5, "replay_kernel": 50.4}}
+# reparam_kernel (translation mode): DRAM bytes per sample of the same kind of capture
+# (439 MB per 256x256 x 4 spp launch).
+REPARAM_TRAFFIC_PER_SAMPLE = 1675.0
 TRAFFIC_BASIS = ("ncu dram__bytes_read.sum + dram__bytes_write.sum per counted ray at 256x256 "
                  "(profiles/dram_per_ray_spheres196k_256px_64spp.md), times the launch's counted rays")
 
@@ -963,8 +966,10 @@ def run_reparam_experiment(args):
                        "grad_translation_norm": float(g_t.norm().item())},
             "roofline": {"bound": "alu", "kernel": "reparam_kernel", "achieved": round(achieved, 3),
                          "peak": round(peak_tflops, 2), "unit": "TFLOP/s", "frac": round(achieved / peak_tflops, 4),
-                         "traffic": (DRAM_TRAFFIC_PER_LAUNCH.get(args.bvh, {}).get("reparam_kernel")
-                                     if not args.small else None),
+                         "traffic": round(REPARAM_TRAFFIC_PER_SAMPLE * st.width * st.height * spp)
+                                    if args.bvh == "wide" else None,
+                         "traffic_basis": "ncu DRAM read + write per sample of reparam_kernel<1,0,0> at 256x256, "
+                                          "4 spp (profiles/reparam_launches_spheres196k_256px_4spp.md), x samples",
                          "work": f"{FLOPS_PER_NODE[args.bvh]}/node visit + {FLOPS_PER_TRI}/triangle test (counted "
                                  "by instrumented launches of the replay, the pixel-edge paths and the radiance "
                                  "pass; warp-field arithmetic not counted); time = radiance pass + reparam_kernel "

@@ -230,7 +230,10 @@ __device__ __forceinline__ void megakernel(const LaunchArgs& A, long long unit, 
         occ = hit.pos >= 0;
         want_shadow = false;
       }
-      if (finish) alive = path_finish<ADJ, JVP, INSTR, FEAT>(A, P, occ, grad_pass, dl, sink, cnt);
+      if (finish) {
+        if constexpr (ADJ) alive = path_finish_body<ADJ, JVP, INSTR, FEAT>(A, P, occ, grad_pass, dl, sink, cnt);
+        else alive = path_finish<ADJ, JVP, INSTR, FEAT>(A, P, occ, grad_pass, dl, sink, cnt);
+      }
       if (!alive) {
         has_path = false;
         if constexpr (CKPT) A.ck_count[P.slot] = P.depth;
@@ -307,13 +310,18 @@ __device__ __forceinline__ void megakernel(const LaunchArgs& A, long long unit, 
 // Minimum resident CTAs of 256 threads per SM requested from ptxas (register cap).
 // Measured on the 196k-triangle sphere workload (forward + adjoint step): with the
 // per-vertex shading out of line, more resident warps beat fewer spills -- the
-// forward runs best at 4 CTAs (64 registers, 48 vs 62 ms at 128 registers), the
-// adjoint at 3 (85 registers, 135 vs 148 ms).
+// forward runs best at 5 CTAs (48 registers: 45.6 ms; 46.4 at 64, 62 at 128) once
+// the production instances carry no fingerprint or adjoint-only state, the adjoint
+// and the replay at 3 (80 registers: replay 62.6 ms; 64.2 at 64, 69.3 at 128).
 #ifndef PT_LB_THREADS
 #define PT_LB_THREADS 256  // block size the forward / replay register caps are computed for
 #endif
 #ifndef PT_FWD_MIN_BLOCKS
-#define PT_FWD_MIN_BLOCKS 4
+#define PT_FWD_MIN_BLOCKS 5
+#endif
+// The checkpointing forward and the batched forward keep 64 registers (measured there).
+#ifndef PT_OTHER_FWD_MIN_BLOCKS
+#define PT_OTHER_FWD_MIN_BLOCKS 4
 #endif
 #ifndef PT_ADJ_MIN_BLOCKS
 #define PT_ADJ_MIN_BLOCKS 3

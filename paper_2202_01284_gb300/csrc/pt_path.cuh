@@ -24,6 +24,11 @@ enum : int {
 #else
 #define PT_SHADE_FN __noinline__
 #endif
+#ifdef PT_FINISH_INLINE
+#define PT_FINISH_FN __forceinline__
+#else
+#define PT_FINISH_FN PT_SHADE_FN
+#endif
 
 // Per-vertex gradient sink of the adjoint: warp-aggregated atomics.
 // Constant-albedo rows and roughness entries are few and heavily shared, so the
@@ -190,6 +195,13 @@ __device__ PT_SHADE_FN bool path_shade(const LaunchArgs& A, PathState& P, const 
   const DevScene& S = A.scene;
   constexpr bool EGRAD = (FEAT & FEAT_EGRAD) != 0;
   constexpr bool HASH = (FEAT & FEAT_NOHASH) == 0;
+  constexpr bool KEEP_L = !(ADJ && (FEAT & FEAT_REPLAY));  // the replay works from the stored radiance
+  // the remaining radiance: the adjoint's, and the reparameterized kernels' (they call
+  // this step without ADJ); not the production forward instances'
+  constexpr bool KEEP_LREM = ADJ || (FEAT & FEAT_NOHASH) == 0;
+  // production instances write the continuation ray straight into the path's ray
+  // (nothing reads the old one between this step and path_finish there)
+  constexpr bool DIRECT_NEXT = (FEAT & FEAT_NOHASH) != 0;
   const bool has_area = S.n_lights > 0;
   const bool has_env = S.env_w > 0;
   const float p_env = has_env ? (has_area ? 0.5f : 1.0f) : 0.0f;
@@ -209,8 +221,8 @@ __device__ PT_SHADE_FN bool path_shade(const LaunchArgs& A, PathState& P, const 
         w = power_heuristic(P.prev_pdf, p_env * env_pdf_at(S, ex, ey, st));
       }
       float3 c = P.beta * Le * w;
-      P.L = P.L + c;
-      if (ADJ) P.Lrem = P.Lrem - c;
+      if constexpr (KEEP_L) P.L = P.L + c;
+      if constexpr (KEEP_LREM) P.Lrem = P.Lrem - c;
       if (JVP) {
         P.L_dot = P.L_dot + P.beta_dot * Le * w;
         if (A.tangent.env) P.L_dot = P.L_dot + P.beta * xyz(__ldg(&A.tangent.env[ei])) * w;
@@ -240,8 +252,8 @@ __device__ PT_SHADE_FN bool path_shade(const LaunchArgs& A, PathState& P, const 
       w = power_heuristic(P.prev_pdf, pdf_l);
     }
     float3 c = P.beta * xyz(sw3) * w;
-    P.L = P.L + c;
-    if (ADJ) P.Lrem = P.Lrem - c;
+    if constexpr (KEEP_L) P.L = P.L + c;
+    if constexpr (KEEP_LREM) P.Lrem = P.Lrem - c;
     if (JVP) P.L_dot = P.L_dot + P.beta_dot * xyz(sw3) * w;
   }
   if (P.depth >= A.max_depth) return false;
@@ -339,15 +351,14 @@ __device__ PT_SHADE_FN bool path_shade(const LaunchArgs& A, PathState& P, const 
       } else {
         const float* q = A.q_rgb + P.slot * 3;
         const float3 c = P.beta * f3(fmaxf(q[0], 0.f), fmaxf(q[1], 0.f), fmaxf(q[2], 0.f));
-        P.L = P.L + c;
-        if (ADJ) P.Lrem = P.Lrem - c;
+        if constexpr (KEEP_L) P.L = P.L + c;
+        if constexpr (KEEP_LREM) P.Lrem = P.Lrem - c;
       }
       return false;
     }
   }
   const Frame fr = make_frame(n_s);
   const float3 wi = fr.to_local(wi_w);
-  P.c_nee = f3(0.f, 0.f, 0.f);
   if (EGRAD) P.nee_env = -1;
   if (JVP) P.c_nee_dot = f3(0.f, 0.f, 0.f);
   if (ADJ) P.r_nee_alb = P.r_nee_a = P.r_bsdf_alb = P.r_bsdf_a = f3(0.f, 0.f, 0.f);
@@ -449,8 +460,13 @@ __device__ PT_SHADE_FN bool path_shade(const LaunchArgs& A, PathState& P, const 
   }
   if (bs.ok) {
     const float3 wo = fr.to_world(bs.wo);
-    P.no = offset_origin(p, ng, wo);
-    P.nd = wo;
+    if constexpr (DIRECT_NEXT) {
+      P.ro = offset_origin(p, ng, wo);
+      P.rd = wo;
+    } else {
+      P.no = offset_origin(p, ng, wo);
+      P.nd = wo;
+    }
   }
   if (ADJ) {
     P.alb_kind = m.alb_kind;
@@ -465,17 +481,19 @@ __device__ PT_SHADE_FN bool path_shade(const LaunchArgs& A, PathState& P, const 
 
 // Finish the vertex once the shadow ray is resolved.  Returns false if the path ended.
 template <bool ADJ, bool JVP, bool INSTR, int FEAT = 0>
-__device__ PT_SHADE_FN bool path_finish(const LaunchArgs& A, PathState& P, bool occluded, bool grad_pass,
-                                            float3 dl, GradSink& sink, Counters<INSTR>& cnt) {
+__device__ __forceinline__ bool path_finish_body(const LaunchArgs& A, PathState& P, bool occluded, bool grad_pass,
+                                                 float3 dl, GradSink& sink, Counters<INSTR>& cnt) {
   constexpr bool HASH = (FEAT & FEAT_NOHASH) == 0;
+  constexpr bool KEEP_L = !(ADJ && (FEAT & FEAT_REPLAY));
+  constexpr bool KEEP_LREM = ADJ || (FEAT & FEAT_NOHASH) == 0;
   if constexpr (HASH) {
     if (A.nee && P.mtype != PT_BSDF_DIELECTRIC && (A.scene.n_lights > 0 || A.scene.env_w > 0))
       P.fh.add(P.has_shadow ? (occluded ? 1u : 0u) : 2u);
   }
   const bool lit = P.has_shadow && !occluded;
   if (lit) {
-    P.L = P.L + P.c_nee;
-    if (ADJ) P.Lrem = P.Lrem - P.c_nee;
+    if constexpr (KEEP_L) P.L = P.L + P.c_nee;
+    if constexpr (KEEP_LREM) P.Lrem = P.Lrem - P.c_nee;
     if (JVP) P.L_dot = P.L_dot + P.c_nee_dot;
     if (ADJ && (FEAT & FEAT_EGRAD) && grad_pass && P.nee_env >= 0)
       sink.add_env<INSTR>(A, P.nee_env, dl * P.nee_env_d, cnt);
@@ -503,8 +521,10 @@ __device__ PT_SHADE_FN bool path_finish(const LaunchArgs& A, PathState& P, bool 
   P.beta = P.beta * P.w_next;
   P.prev_delta = P.delta_next;
   P.prev_pdf = P.pdf_next;
-  P.ro = P.no;
-  P.rd = P.nd;
+  if constexpr ((FEAT & FEAT_NOHASH) == 0) {
+    P.ro = P.no;
+    P.rd = P.nd;
+  }
   if (A.rr_depth >= 0 && P.depth >= A.rr_depth) {
     const float q = fminf(max3f(P.beta), 0.95f);
     const bool cont = P.u6 < q;
@@ -515,6 +535,14 @@ __device__ PT_SHADE_FN bool path_finish(const LaunchArgs& A, PathState& P, bool 
   }
   ++P.depth;
   return true;
+}
+
+// Out of line, except where the megakernel calls the body directly (the adjoint
+// instances: measured replay 61.7 vs 62.8 ms inline; the forward is faster out of line).
+template <bool ADJ, bool JVP, bool INSTR, int FEAT = 0>
+__device__ PT_FINISH_FN bool path_finish(const LaunchArgs& A, PathState& P, bool occluded, bool grad_pass,
+                                         float3 dl, GradSink& sink, Counters<INSTR>& cnt) {
+  return path_finish_body<ADJ, JVP, INSTR, FEAT>(A, P, occluded, grad_pass, dl, sink, cnt);
 }
 
 }  // namespace ptgb

@@ -142,7 +142,7 @@ constexpr int kJobBytes = (int)((offsetof(LaunchArgs, cams) + sizeof(DevCamera) 
 // Two kernels rather than one keep each at the register footprint of its
 // single-job counterpart (one kernel holding both megakernels spills).
 template <bool ADJ, int LAYOUT, int FEAT = 0>
-__global__ void __launch_bounds__(256, ADJ ? PT_ADJ_MIN_BLOCKS : PT_FWD_MIN_BLOCKS)
+__global__ void __launch_bounds__(256, ADJ ? PT_ADJ_MIN_BLOCKS : PT_OTHER_FWD_MIN_BLOCKS)
     batch_kernel(const LaunchArgs* __restrict__ jobs, const BatchItem* __restrict__ items, int n_items, int tile,
                  unsigned* __restrict__ queue) {
   extern __shared__ __align__(16) unsigned char job_smem[];
