@@ -78,10 +78,10 @@ def alu_roofline(kernel, counters, bvh, ms, clk, note=""):
 # by its counted rays (the per-ray traffic of these kernels does not depend on the
 # image size: the scene and texture are the same and the per-sample state scales with
 # the rays).  A kernel changed since its capture has no entry.
-TRAFFIC_PER_RAY = {"wide": {"forward_kernel": 116.0, "radiance_kernel": 140.5, "replay_kernel": 50.4}}
+TRAFFIC_PER_RAY = {"wide": {"forward_kernel": 130.6, "radiance_kernel": 161.6, "replay_kernel": 44.8}}
 # reparam_kernel (translation mode): DRAM bytes per sample of the same kind of capture
-# (439 MB per 256x256 x 4 spp launch).
-REPARAM_TRAFFIC_PER_SAMPLE = 1675.0
+# (409 MB per 256x256 x 4 spp launch).
+REPARAM_TRAFFIC_PER_SAMPLE = 1560.0
 TRAFFIC_BASIS = ("ncu dram__bytes_read.sum + dram__bytes_write.sum per counted ray at 256x256 "
                  "(profiles/dram_per_ray_spheres196k_256px_64spp.md), times the launch's counted rays")
 
