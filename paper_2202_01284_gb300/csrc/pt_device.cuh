@@ -21,9 +21,6 @@ namespace ptgb {
 #define PT_PI 3.14159265358979323846f
 #define PT_INV_PI 0.31830988618379067154f
 #define PT_STACK 64
-#ifndef PT_TRI_T_FIRST
-#define PT_TRI_T_FIRST 0  // 1: the triangle test computes t first and rejects farther hits early
-#endif
 #ifndef PT_RSTACK
 #define PT_RSTACK 0  // 1: the wide traversal keeps its top four stack entries in registers
 #endif
@@ -117,17 +114,6 @@ __device__ __forceinline__ bool tri_test(const float4* __restrict__ tv, int pos,
   if (det == 0.0f) return false;
   float inv = 1.0f / det;
   float3 s = r.o - v0;
-#if PT_TRI_T_FIRST
-  // the same values in another order: a hit beyond the closest one so far is
-  // rejected before its barycentrics are computed
-  float3 q = cross3(s, e1);
-  float t = dot3(e2, q) * inv;
-  if (!(t > 0.0f) || t > best_t) return false;
-  float u = dot3(s, p) * inv;
-  if (u < 0.0f || u > 1.0f) return false;
-  float v = dot3(r.d, q) * inv;
-  if (v < 0.0f || u + v > 1.0f) return false;
-#else
   float u = dot3(s, p) * inv;
   if (u < 0.0f || u > 1.0f) return false;
   float3 q = cross3(s, e1);
@@ -135,7 +121,6 @@ __device__ __forceinline__ bool tri_test(const float4* __restrict__ tv, int pos,
   if (v < 0.0f || u + v > 1.0f) return false;
   float t = dot3(e2, q) * inv;
   if (!(t > 0.0f)) return false;
-#endif
   uint32_t orig = __float_as_uint(a.w);
   if (t < best_t || (best_pos >= 0 && t == best_t && orig < best_orig)) {
     best_t = t;
@@ -483,14 +468,14 @@ __device__ __forceinline__ BsdfEval bsdf_eval(const Material& m, float3 wi, floa
 // (Sec. 3.1): phi = 2 pi u4, sin^2(theta) = u5.
 __device__ __forceinline__ float3 cosine_sample(float u4, float u5) {
   float s, c;
-  sincosf(2.0f * PT_PI * u4, &s, &c);
+  sincospif(2.0f * u4, &s, &c);  // the angle 2 pi u4 without rounding 2 pi u4 first
   float r = sqrtf(u5);
   return f3(c * r, s * r, sqrtf(1.0f - u5));
 }
 // Walter et al. 2007: phi = 2 pi u4, tan^2(theta_h) = a^2 u5 / (1 - u5).
 __device__ __forceinline__ bool ggx_sample(float a, float3 wi, float u4, float u5, float3& wo) {
   float s, c;
-  sincosf(2.0f * PT_PI * u4, &s, &c);
+  sincospif(2.0f * u4, &s, &c);  // the angle 2 pi u4 without rounding 2 pi u4 first
   float tan2 = a * a * u5 / (1.0f - u5);
   float ct = rsqrtf(1.0f + tan2);
   float st = sqrtf(fmaxf(0.0f, 1.0f - ct * ct));

@@ -15,6 +15,8 @@ namespace ptgb {
 enum : int {
   FEAT_EGRAD = 1, FEAT_CACHE = 2, FEAT_TEXAGG = 4, FEAT_CKPT = 8, FEAT_SAMPLE_L = 16, FEAT_REPLAY = 32,
   FEAT_NOHASH = 64,  // no decision fingerprint (instances that never output it)
+  FEAT_LEAN = 128,   // production megakernel instances: no remaining radiance outside the
+                     // adjoint, the continuation ray written straight into the path's ray
   FEAT_ALL = 7
 };
 
@@ -105,9 +107,13 @@ struct GradSink {
   }
 };
 
-__device__ __forceinline__ float3 ratio_grad(float3 dl, float3 x, float3 df, float3 f) {
-  return f3(f.x > 0.0f ? dl.x * x.x * df.x / f.x : 0.0f, f.y > 0.0f ? dl.y * x.y * df.y / f.y : 0.0f,
-            f.z > 0.0f ? dl.z * x.z * df.z / f.z : 0.0f);
+// Both log-derivative factors of one BSDF value, (df_alb / f, df_alpha / f) per
+// channel, from one reciprocal of f (0 where f is 0).
+__device__ __forceinline__ void log_derivs(float3 df_alb, float3 df_alpha, float3 f, float3& r_alb, float3& r_a) {
+  const float3 inv = f3(f.x > 0.0f ? 1.0f / f.x : 0.0f, f.y > 0.0f ? 1.0f / f.y : 0.0f,
+                        f.z > 0.0f ? 1.0f / f.z : 0.0f);
+  r_alb = df_alb * inv;
+  r_a = df_alpha * inv;
 }
 
 __device__ __forceinline__ float3 offset_origin(float3 p, float3 ng, float3 d) {
@@ -198,10 +204,10 @@ __device__ PT_SHADE_FN bool path_shade(const LaunchArgs& A, PathState& P, const 
   constexpr bool KEEP_L = !(ADJ && (FEAT & FEAT_REPLAY));  // the replay works from the stored radiance
   // the remaining radiance: the adjoint's, and the reparameterized kernels' (they call
   // this step without ADJ); not the production forward instances'
-  constexpr bool KEEP_LREM = ADJ || (FEAT & FEAT_NOHASH) == 0;
+  constexpr bool KEEP_LREM = ADJ || (FEAT & FEAT_LEAN) == 0;
   // production instances write the continuation ray straight into the path's ray
   // (nothing reads the old one between this step and path_finish there)
-  constexpr bool DIRECT_NEXT = (FEAT & FEAT_NOHASH) != 0;
+  constexpr bool DIRECT_NEXT = (FEAT & FEAT_LEAN) != 0;
   const bool has_area = S.n_lights > 0;
   const bool has_env = S.env_w > 0;
   const float p_env = has_env ? (has_area ? 0.5f : 1.0f) : 0.0f;
@@ -378,10 +384,10 @@ __device__ PT_SHADE_FN bool path_shade(const LaunchArgs& A, PathState& P, const 
       const float c0 = __ldg(&cond[x]), c1 = __ldg(&cond[x + 1]);
       const float fv = (u[1] - m0) / (m1 - m0);
       const float fu = (u[2] - c0) / (c1 - c0);
-      const float theta = PT_PI * (y + fv) / S.env_h, phi = 2.0f * PT_PI * (x + fu) / S.env_w;
+      // theta = pi (y + fv) / H, phi = 2 pi (x + fu) / W, through sin/cos of pi * a
       float st, ct, sp, cp;
-      sincosf(theta, &st, &ct);
-      sincosf(phi, &sp, &cp);
+      sincospif((y + fv) / S.env_h, &st, &ct);
+      sincospif(2.0f * (x + fu) / S.env_w, &sp, &cp);
       dir = f3(st * cp, ct, st * sp);
       env_i = y * S.env_w + x;
       Le = xyz(__ldg(&(A.params.env ? A.params.env : S.env)[env_i]));
@@ -435,8 +441,7 @@ __device__ PT_SHADE_FN bool path_shade(const LaunchArgs& A, PathState& P, const 
         P.nee_env_d = P.beta * ev.f * s_env;
       }
       if (ADJ && grad_pass) {
-        P.r_nee_alb = ratio_grad(f3(1.f, 1.f, 1.f), f3(1.f, 1.f, 1.f), ev.df_alb, ev.f);
-        P.r_nee_a = ratio_grad(f3(1.f, 1.f, 1.f), f3(1.f, 1.f, 1.f), ev.df_alpha, ev.f);
+        log_derivs(ev.df_alb, ev.df_alpha, ev.f, P.r_nee_alb, P.r_nee_a);
       }
     }
   }
@@ -455,8 +460,7 @@ __device__ PT_SHADE_FN bool path_shade(const LaunchArgs& A, PathState& P, const 
   P.pdf_next = bs.pdf;
   P.u6 = u[6];
   if (ADJ && grad_pass && bs.ok && !bs.delta) {
-    P.r_bsdf_alb = ratio_grad(f3(1.f, 1.f, 1.f), f3(1.f, 1.f, 1.f), bs.ev.df_alb, bs.ev.f);
-    P.r_bsdf_a = ratio_grad(f3(1.f, 1.f, 1.f), f3(1.f, 1.f, 1.f), bs.ev.df_alpha, bs.ev.f);
+    log_derivs(bs.ev.df_alb, bs.ev.df_alpha, bs.ev.f, P.r_bsdf_alb, P.r_bsdf_a);
   }
   if (bs.ok) {
     const float3 wo = fr.to_world(bs.wo);
@@ -475,7 +479,7 @@ __device__ PT_SHADE_FN bool path_shade(const LaunchArgs& A, PathState& P, const 
     P.rough = m.rough;
     P.has_params = m.alb_kind != 0 || m.rough >= 0;
   }
-  if (ADJ || HASH) P.mtype = type;
+  if constexpr (ADJ || HASH || (FEAT & FEAT_LEAN) == 0) P.mtype = type;
   return true;
 }
 
@@ -485,7 +489,7 @@ __device__ __forceinline__ bool path_finish_body(const LaunchArgs& A, PathState&
                                                  float3 dl, GradSink& sink, Counters<INSTR>& cnt) {
   constexpr bool HASH = (FEAT & FEAT_NOHASH) == 0;
   constexpr bool KEEP_L = !(ADJ && (FEAT & FEAT_REPLAY));
-  constexpr bool KEEP_LREM = ADJ || (FEAT & FEAT_NOHASH) == 0;
+  constexpr bool KEEP_LREM = ADJ || (FEAT & FEAT_LEAN) == 0;
   if constexpr (HASH) {
     if (A.nee && P.mtype != PT_BSDF_DIELECTRIC && (A.scene.n_lights > 0 || A.scene.env_w > 0))
       P.fh.add(P.has_shadow ? (occluded ? 1u : 0u) : 2u);
@@ -521,7 +525,7 @@ __device__ __forceinline__ bool path_finish_body(const LaunchArgs& A, PathState&
   P.beta = P.beta * P.w_next;
   P.prev_delta = P.delta_next;
   P.prev_pdf = P.pdf_next;
-  if constexpr ((FEAT & FEAT_NOHASH) == 0) {
+  if constexpr ((FEAT & FEAT_LEAN) == 0) {
     P.ro = P.no;
     P.rd = P.nd;
   }

@@ -15,14 +15,14 @@ namespace ptgb {
 // Production instances carry no optional features; instrumented ones carry all.
 template <bool INSTR, int LAYOUT, int DISPATCH>
 __global__ void __launch_bounds__(PT_LB_THREADS, PT_FWD_MIN_BLOCKS) forward_kernel(const __grid_constant__ LaunchArgs A) {
-  megakernel<false, false, INSTR, LAYOUT, DISPATCH, INSTR ? FEAT_ALL : FEAT_NOHASH>(
+  megakernel<false, false, INSTR, LAYOUT, DISPATCH, INSTR ? FEAT_ALL : FEAT_NOHASH | FEAT_LEAN>(
       A, (long long)blockIdx.x * blockDim.x + threadIdx.x, crop_tile(A));
 }
 
 // The forward with the radiance-cache modes compiled in.
 template <int LAYOUT>
 __global__ void __launch_bounds__(PT_LB_THREADS, PT_FWD_MIN_BLOCKS) forward_full_kernel(const __grid_constant__ LaunchArgs A) {
-  megakernel<false, false, false, LAYOUT, PT_DISPATCH_SWITCH, FEAT_ALL | FEAT_NOHASH>(
+  megakernel<false, false, false, LAYOUT, PT_DISPATCH_SWITCH, FEAT_ALL | FEAT_NOHASH | FEAT_LEAN>(
       A, (long long)blockIdx.x * blockDim.x + threadIdx.x, crop_tile(A));
 }
 
@@ -33,13 +33,13 @@ __global__ void __launch_bounds__(PT_LB_THREADS, PT_FWD_MIN_BLOCKS) forward_full
 #endif
 template <int LAYOUT>
 __global__ void __launch_bounds__(256, PT_JVP_MIN_BLOCKS) jvp_kernel(const __grid_constant__ LaunchArgs A) {
-  megakernel<false, true, false, LAYOUT, PT_DISPATCH_SWITCH, FEAT_NOHASH>(
+  megakernel<false, true, false, LAYOUT, PT_DISPATCH_SWITCH, FEAT_NOHASH | FEAT_LEAN>(
       A, (long long)blockIdx.x * blockDim.x + threadIdx.x, crop_tile(A));
 }
 
 template <bool INSTR, int LAYOUT, int DISPATCH>
 __global__ void __launch_bounds__(256, PT_ADJ_MIN_BLOCKS) adjoint_kernel(const __grid_constant__ LaunchArgs A) {
-  megakernel<true, false, INSTR, LAYOUT, DISPATCH, INSTR ? FEAT_ALL : FEAT_NOHASH>(
+  megakernel<true, false, INSTR, LAYOUT, DISPATCH, INSTR ? FEAT_ALL : FEAT_NOHASH | FEAT_LEAN>(
       A, (long long)blockIdx.x * blockDim.x + threadIdx.x, crop_tile(A));
 }
 
@@ -47,7 +47,7 @@ __global__ void __launch_bounds__(256, PT_ADJ_MIN_BLOCKS) adjoint_kernel(const _
 // the replay-only adjoint reading it.
 template <int LAYOUT>
 __global__ void __launch_bounds__(PT_LB_THREADS, PT_FWD_MIN_BLOCKS) radiance_kernel(const __grid_constant__ LaunchArgs A) {
-  megakernel<false, false, false, LAYOUT, PT_DISPATCH_SWITCH, FEAT_SAMPLE_L | FEAT_NOHASH>(
+  megakernel<false, false, false, LAYOUT, PT_DISPATCH_SWITCH, FEAT_SAMPLE_L | FEAT_NOHASH | FEAT_LEAN>(
       A, (long long)blockIdx.x * blockDim.x + threadIdx.x, crop_tile(A));
 }
 #ifndef PT_REPLAY_MIN_BLOCKS
@@ -55,7 +55,7 @@ __global__ void __launch_bounds__(PT_LB_THREADS, PT_FWD_MIN_BLOCKS) radiance_ker
 #endif
 template <int LAYOUT>
 __global__ void __launch_bounds__(PT_LB_THREADS, PT_REPLAY_MIN_BLOCKS) replay_kernel(const __grid_constant__ LaunchArgs A) {
-  megakernel<true, false, false, LAYOUT, PT_DISPATCH_SWITCH, FEAT_REPLAY | FEAT_NOHASH>(
+  megakernel<true, false, false, LAYOUT, PT_DISPATCH_SWITCH, FEAT_REPLAY | FEAT_NOHASH | FEAT_LEAN>(
       A, (long long)blockIdx.x * blockDim.x + threadIdx.x, crop_tile(A));
 }
 
@@ -65,28 +65,28 @@ __global__ void __launch_bounds__(PT_LB_THREADS, PT_REPLAY_MIN_BLOCKS) replay_ke
 template <int LAYOUT>
 __global__ void __launch_bounds__(PT_LB_THREADS, PT_FWD_MIN_BLOCKS)
     forward_persist_kernel(const __grid_constant__ LaunchArgs A) {
-  megakernel<false, false, false, LAYOUT, PT_DISPATCH_SWITCH, FEAT_NOHASH, true>(A, 0, crop_tile(A));
+  megakernel<false, false, false, LAYOUT, PT_DISPATCH_SWITCH, FEAT_NOHASH | FEAT_LEAN, true>(A, 0, crop_tile(A));
 }
 template <int LAYOUT>
 __global__ void __launch_bounds__(PT_LB_THREADS, PT_FWD_MIN_BLOCKS)
     radiance_persist_kernel(const __grid_constant__ LaunchArgs A) {
-  megakernel<false, false, false, LAYOUT, PT_DISPATCH_SWITCH, FEAT_SAMPLE_L | FEAT_NOHASH, true>(A, 0, crop_tile(A));
+  megakernel<false, false, false, LAYOUT, PT_DISPATCH_SWITCH, FEAT_SAMPLE_L | FEAT_NOHASH | FEAT_LEAN, true>(A, 0, crop_tile(A));
 }
 template <int LAYOUT>
 __global__ void __launch_bounds__(PT_LB_THREADS, PT_REPLAY_MIN_BLOCKS)
     replay_persist_kernel(const __grid_constant__ LaunchArgs A) {
-  megakernel<true, false, false, LAYOUT, PT_DISPATCH_SWITCH, FEAT_REPLAY | FEAT_NOHASH, true>(A, 0, crop_tile(A));
+  megakernel<true, false, false, LAYOUT, PT_DISPATCH_SWITCH, FEAT_REPLAY | FEAT_NOHASH | FEAT_LEAN, true>(A, 0, crop_tile(A));
 }
 template <int LAYOUT>
 __global__ void __launch_bounds__(256, PT_JVP_MIN_BLOCKS) jvp_persist_kernel(const __grid_constant__ LaunchArgs A) {
-  megakernel<false, true, false, LAYOUT, PT_DISPATCH_SWITCH, FEAT_NOHASH, true>(A, 0, crop_tile(A));
+  megakernel<false, true, false, LAYOUT, PT_DISPATCH_SWITCH, FEAT_NOHASH | FEAT_LEAN, true>(A, 0, crop_tile(A));
 }
 
 // The adjoint with every optional feature: environment-radiance (emitter)
 // gradients, the cache-terminated replay, warp-aggregated texel atomics.
 template <int LAYOUT>
 __global__ void __launch_bounds__(256, PT_ADJ_MIN_BLOCKS) adjoint_full_kernel(const __grid_constant__ LaunchArgs A) {
-  megakernel<true, false, false, LAYOUT, PT_DISPATCH_SWITCH, FEAT_ALL | FEAT_NOHASH>(
+  megakernel<true, false, false, LAYOUT, PT_DISPATCH_SWITCH, FEAT_ALL | FEAT_NOHASH | FEAT_LEAN>(
       A, (long long)blockIdx.x * blockDim.x + threadIdx.x, crop_tile(A));
 }
 

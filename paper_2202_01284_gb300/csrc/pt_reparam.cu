@@ -533,7 +533,7 @@ __global__ void __launch_bounds__(128, 8) reparam_kernel(const __grid_constant__
         ng = tri_normal(S, hit.pos);
         n_s = dot3(ng, P.rd) < 0.0f ? ng : -ng;
       }
-      bool more = path_shade<false, false, INSTR, PT_DISPATCH_SWITCH>(A, P, hit, false, z, sink, cnt);
+      bool more = path_shade<false, false, INSTR, PT_DISPATCH_SWITCH, FEAT_NOHASH>(A, P, hit, false, z, sink, cnt);
       Pcg32 aux_nee = aux, aux_bsdf = aux;
       if (block) {
         pcg_advance(aux_bsdf, n2);
@@ -600,7 +600,7 @@ __global__ void __launch_bounds__(128, 8) reparam_kernel(const __grid_constant__
             }
           }
         }
-        more = path_finish<false, false, INSTR>(A, P, occ, false, z, sink, cnt);
+        more = path_finish<false, false, INSTR, FEAT_NOHASH>(A, P, occ, false, z, sink, cnt);
         if (more && warp) {
           const float3 C = f3(fmaxf(P.Lrem.x, 0.f), fmaxf(P.Lrem.y, 0.f), fmaxf(P.Lrem.z, 0.f));
           const float R = dot3(dl, C);
@@ -721,13 +721,13 @@ __device__ __forceinline__ float3 edge_path(const LaunchArgs& A, const EdgeSampl
     const Hit hit = closest<LAYOUT, INSTR>(A.scene, P.ro, P.rd, INFINITY, false, cnt);
     ++rays;
     if (first && hit.pos >= 0) t0 = hit.t;
-    if (!path_shade<false, false, INSTR, PT_DISPATCH_SWITCH>(A, P, hit, false, z, sink, cnt)) break;
+    if (!path_shade<false, false, INSTR, PT_DISPATCH_SWITCH, FEAT_NOHASH>(A, P, hit, false, z, sink, cnt)) break;
     bool occ = false;
     if (P.has_shadow) {
       occ = closest<LAYOUT, INSTR>(A.scene, P.so, P.sd, P.stmax, true, cnt).pos >= 0;
       ++rays;
     }
-    if (!path_finish<false, false, INSTR>(A, P, occ, false, z, sink, cnt)) break;
+    if (!path_finish<false, false, INSTR, FEAT_NOHASH>(A, P, occ, false, z, sink, cnt)) break;
   }
   return P.L;
 }
@@ -1082,7 +1082,7 @@ __global__ void __launch_bounds__(128, 8) reparam_jvp_kernel(const __grid_consta
         ndot = normal_turn<VERT>(S, hit.pos, dir_t);
       }
       float3 L0 = P.L;
-      bool more = path_shade<false, false, false, PT_DISPATCH_SWITCH>(A, P, hit, false, z, sink, cnt);
+      bool more = path_shade<false, false, false, PT_DISPATCH_SWITCH, FEAT_NOHASH>(A, P, hit, false, z, sink, cnt);
       ldot = ldot + r * (P.L - L0);  // emission reaching this vertex
       Pcg32 aux_nee = aux, aux_bsdf = aux;
       if (block) {
@@ -1112,7 +1112,7 @@ __global__ void __launch_bounds__(128, 8) reparam_jvp_kernel(const __grid_consta
           h0 = true;
         }
         L0 = P.L;
-        more = path_finish<false, false, false>(A, P, occ, false, z, sink, cnt);
+        more = path_finish<false, false, false, FEAT_NOHASH>(A, P, occ, false, z, sink, cnt);
         ldot = ldot + r * (P.L - L0);  // the light sample, with the path's tangent so far
         if (more && warp) {
           next = closest<LAYOUT, false>(S, P.ro, P.rd, INFINITY, false, cnt);
