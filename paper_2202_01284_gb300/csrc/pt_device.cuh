@@ -21,6 +21,16 @@ namespace ptgb {
 #define PT_PI 3.14159265358979323846f
 #define PT_INV_PI 0.31830988618379067154f
 #define PT_STACK 64
+// 1/x through the correctly rounded reciprocal: the same value as the IEEE
+// division 1.0f / x, without the division's general code path.
+#ifndef PT_FAST_RCP
+#define PT_FAST_RCP 1
+#endif
+#if PT_FAST_RCP
+#define PT_RCP(x) __frcp_rn(x)
+#else
+#define PT_RCP(x) (1.0f / (x))
+#endif
 #ifndef PT_RSTACK
 #define PT_RSTACK 0  // 1: the wide traversal keeps its top four stack entries in registers
 #endif
@@ -96,9 +106,9 @@ struct Hit {
 
 __device__ __forceinline__ float3 safe_inv(float3 d) {
   const float eps = 1e-20f;
-  return f3(1.0f / (fabsf(d.x) > eps ? d.x : copysignf(eps, d.x)),
-            1.0f / (fabsf(d.y) > eps ? d.y : copysignf(eps, d.y)),
-            1.0f / (fabsf(d.z) > eps ? d.z : copysignf(eps, d.z)));
+  return f3(PT_RCP(fabsf(d.x) > eps ? d.x : copysignf(eps, d.x)),
+            PT_RCP(fabsf(d.y) > eps ? d.y : copysignf(eps, d.y)),
+            PT_RCP(fabsf(d.z) > eps ? d.z : copysignf(eps, d.z)));
 }
 
 // Moller-Trumbore in FP32 (edges inclusive, det == 0 misses).  Updates the
@@ -112,7 +122,7 @@ __device__ __forceinline__ bool tri_test(const float4* __restrict__ tv, int pos,
   float3 p = cross3(r.d, e2);
   float det = dot3(e1, p);
   if (det == 0.0f) return false;
-  float inv = 1.0f / det;
+  float inv = PT_RCP(det);
   float3 s = r.o - v0;
   float u = dot3(s, p) * inv;
   if (u < 0.0f || u > 1.0f) return false;
@@ -368,7 +378,7 @@ struct Frame {
 };
 __device__ __forceinline__ Frame make_frame(float3 n) {
   float sign = n.z >= 0.0f ? 1.0f : -1.0f;
-  float a = -1.0f / (sign + n.z);
+  float a = -PT_RCP(sign + n.z);
   float b = n.x * n.y * a;
   Frame f;
   f.n = n;
@@ -406,7 +416,7 @@ __device__ __forceinline__ float ggx_G1(float a, float c, float* dlog) {
   float T = (1.0f - c * c) / (c * c);
   float s = sqrtf(1.0f + a * a * T);
   if (dlog) *dlog = -(a * T / s) / (1.0f + s);
-  return 2.0f / (1.0f + s);
+  return 2.0f * PT_RCP(1.0f + s);  // 2 / (1 + s) exactly: scaling by 2 is exact
 }
 __device__ __forceinline__ float schlick(float f0, float cd) {
   float m = 1.0f - cd;
@@ -516,7 +526,7 @@ __device__ __forceinline__ BsdfSample bsdf_sample(const Material& m, float3 wi, 
   s.lobe = 0;
   s.weight = f3(0.f, 0.f, 0.f);
   if (T == PT_BSDF_DIELECTRIC) {
-    float eta = entering ? m.eta : 1.0f / m.eta;
+    float eta = entering ? m.eta : PT_RCP(m.eta);
     float cos_t;
     float F = fresnel_dielectric(wi.z, eta, cos_t);
     s.delta = true;
@@ -525,7 +535,7 @@ __device__ __forceinline__ BsdfSample bsdf_sample(const Material& m, float3 wi, 
       s.weight = f3(1.f, 1.f, 1.f);
       s.lobe = 2;
     } else {
-      float ie = 1.0f / eta;
+      float ie = PT_RCP(eta);
       s.wo = f3(-wi.x * ie, -wi.y * ie, -cos_t);
       float k = ie * ie;
       s.weight = f3(k, k, k);
