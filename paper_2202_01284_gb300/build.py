@@ -21,12 +21,13 @@ CU_SOURCES = ["pt_render.cu", "pt_scene.cu", "pt_nrc.cu", "pt_nrc_tc.cu", "pt_wa
               "pt_reparam.cu", "pt_probe.cu"]
 CPP_SOURCES = ["bvh_build.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-# In the megakernel sources, device divisions a / b are the approximate division (at
-# most 2 ulp): the shading's divisions were a measured 3.4 % of the path tracer's step.
-# Reciprocals that decide traversal (ray inverse direction, the triangle test's
-# 1 / det) use __frcp_rn explicitly and stay correctly rounded.  The reparameterized
-# warp estimator (ratios of sums) and the cache MLP keep IEEE division.
-DEVICE_FLAGS = ["-prec-div=false"]
+# In the megakernel sources, device divisions a / b and square roots are the
+# approximate ones (at most 2 ulp / the hardware square root): measured 3.4 % and
+# 1.7 % of the path tracer's step.  Reciprocals that decide traversal (ray inverse
+# direction, the triangle test's 1 / det) use __frcp_rn explicitly and stay
+# correctly rounded.  The reparameterized warp estimator (ratios of sums) and the
+# cache MLP keep IEEE division and square root.
+DEVICE_FLAGS = ["-prec-div=false", "-prec-sqrt=false"]
 FAST_DIV_SOURCES = {"pt_render.cu", "pt_wavefront.cu", "pt_ckpt.cu"}
 
 

@@ -68,6 +68,24 @@ def test_lit_plane_gpu_exact(lib):
     assert np.allclose(L, np.float32(0.6) * 1.5, rtol=2e-6)
 
 
+@pytest.mark.parametrize("inside", [False, True])
+def test_glass_furnace_gpu(lib, inside):
+    """A closed glass icosphere under a uniform sky: every path that leaves into the
+    sky carries L seen from outside and eta^2 L from a camera inside the glass (the
+    radiance theorem); the rest are paths cut off inside by the depth limit (zeros).
+    The 1/eta^2 and eta^2 factors of a path are FP32 products here."""
+    L, eta = 1.3, 1.5
+    sc = S.glass_sphere(eta=eta, env_radiance=L, inside=inside, level=3, width=24, height=24)
+    for layout in (0, 1):
+        st = _settings(sc, spp=16, max_depth=48, seed=31, nee=True)
+        _, _, Ls, _ = _gpu_forward(lib, sc, st, layout=layout)
+        x = Ls.reshape(-1, 3)
+        esc = x[:, 0] > 0
+        want = float(np.float32(L)) * (eta * eta if inside else 1.0)
+        assert np.allclose(x[esc], want, rtol=2e-6, atol=0), (layout, np.abs(x[esc] / want - 1).max())
+        assert esc.mean() > 0.99
+
+
 # ---------------------------------------------------------------- tiny Cornell box (36 tris)
 @pytest.mark.parametrize("dispatch,layout", [(0, 0), (1, 0), (0, 1), (1, 1)])
 def test_cornell_forward_parity(lib, oracle_mod, dispatch, layout):
