@@ -31,9 +31,6 @@ namespace ptgb {
 #else
 #define PT_RCP(x) (1.0f / (x))
 #endif
-#ifndef PT_RSTACK
-#define PT_RSTACK 0  // 1: the wide traversal keeps its top four stack entries in registers
-#endif
 
 // ---------------------------------------------------------------- float3 helpers
 __device__ __forceinline__ float3 f3(float a, float b, float c) { return make_float3(a, b, c); }
@@ -251,13 +248,7 @@ __device__ __forceinline__ Hit trace_wide(const DevScene& S, float3 ro, float3 r
   const float3 inv = safe_inv(rd);
   const uint32_t flip = (rd.x >= 0.0f ? 1u : 0u) | (rd.y >= 0.0f ? 2u : 0u) | (rd.z >= 0.0f ? 4u : 0u);
   const uint4* __restrict__ N = reinterpret_cast<const uint4*>(S.nodes);
-#if PT_RSTACK
-  // top four entries in registers (r0 = top), deeper ones in a local array
-  uint2 r0 = make_uint2(0u, 0u), r1 = r0, r2 = r0, r3 = r0;
-  uint2 ovf[28];
-#else
   uint2 stack[32];
-#endif
   int sp = 0;
   int node = 0;
   unsigned n_nodes = 0, n_tris = 0;
@@ -327,17 +318,8 @@ __device__ __forceinline__ Hit trace_wide(const DevScene& S, float3 ro, float3 r
     uint32_t base = w1.x, gmask = imask, hits = inner_hits;
     if (hits == 0u) {
       if (sp == 0) break;
-#if PT_RSTACK
-      const uint2 e = r0;
-      r0 = r1;
-      r1 = r2;
-      r2 = r3;
-      --sp;
-      if (sp >= 4) r3 = ovf[sp - 4];
-#else
       const uint2 e = stack[sp - 1];
       --sp;
-#endif
       base = e.x;
       gmask = e.y & 0xffu;
       hits = e.y >> 8;
@@ -351,16 +333,7 @@ __device__ __forceinline__ Hit trace_wide(const DevScene& S, float3 ro, float3 r
         set_status(S, PT_ERR_BVH);
         break;
       }
-#if PT_RSTACK
-      if (sp >= 4) ovf[sp - 4] = r3;
-      r3 = r2;
-      r2 = r1;
-      r1 = r0;
-      r0 = make_uint2(base, gmask | (hits << 8));
-      ++sp;
-#else
       stack[sp++] = make_uint2(base, gmask | (hits << 8));
-#endif
     }
   }
   cnt.add(3, n_nodes);
