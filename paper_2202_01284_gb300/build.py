@@ -21,14 +21,17 @@ CU_SOURCES = ["pt_render.cu", "pt_scene.cu", "pt_nrc.cu", "pt_nrc_tc.cu", "pt_wa
               "pt_reparam.cu", "pt_probe.cu"]
 CPP_SOURCES = ["bvh_build.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-# In the megakernel sources, device divisions a / b and square roots are the
-# approximate ones (at most 2 ulp / the hardware square root): measured 3.4 % and
-# 1.7 % of the path tracer's step.  Reciprocals that decide traversal (ray inverse
-# direction, the triangle test's 1 / det) use __frcp_rn explicitly and stay
-# correctly rounded.  The reparameterized warp estimator (ratios of sums) and the
-# cache MLP keep IEEE division and square root.
-DEVICE_FLAGS = ["-prec-div=false", "-prec-sqrt=false"]
-FAST_DIV_SOURCES = {"pt_render.cu", "pt_wavefront.cu", "pt_ckpt.cu"}
+# Per-source floating-point flags.  In the megakernel sources device divisions a / b
+# and square roots are the approximate ones (at most 2 ulp / the hardware square root):
+# measured 3.4 % and 1.7 % of the path tracer's step.  Reciprocals that decide
+# traversal (ray inverse direction, the triangle test's 1 / det) use __frcp_rn
+# everywhere.  The reparameterized source keeps IEEE division: with the approximate
+# one its glossy log-derivatives and vertex-mode tangents moved by up to 1.6e-3
+# relative against the FP64 reference (the warp estimator's own ratios of sums,
+# written as __fdiv_rn / __frcp_rn, were not the cause).  The cache MLP keeps IEEE
+# division and square root.
+_MEGA_FLAGS = ["-prec-div=false", "-prec-sqrt=false"]
+SOURCE_FLAGS = {"pt_render.cu": _MEGA_FLAGS, "pt_wavefront.cu": _MEGA_FLAGS, "pt_ckpt.cu": _MEGA_FLAGS}
 
 
 def _nvcc():
@@ -70,7 +73,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_verbose: bool = Fals
     def compile_one(src):
         obj = os.path.join(OBJDIR, os.path.basename(src) + ".o")
         if src.endswith(".cu"):
-            flags = DEVICE_FLAGS if os.path.basename(src) in FAST_DIV_SOURCES else []
+            flags = SOURCE_FLAGS.get(os.path.basename(src), [])
             cmd = [nvcc, *ARCH, "-lineinfo", "--expt-relaxed-constexpr", *flags, *common, "-c", src, "-o", obj]
             if ptxas_verbose:
                 cmd += ["-Xptxas", "-v"]

@@ -131,6 +131,10 @@ __device__ __forceinline__ float cam_window(const LaunchArgs& A, const DevCamera
   return t * t * (3.0f - 2.0f * t);
 }
 
+// (t0 / t)^power of the warp's depth weight; the default power 2 as one product (the
+// correctly rounded square; powf is only guaranteed within a few ulp of it)
+__device__ __forceinline__ float depth_weight(float q, float power) { return power == 2.0f ? q * q : powf(q, power); }
+
 struct GradOut {
   float* dst;  // shared (per CTA) or global [n_shapes][3]
   __device__ __forceinline__ void add(int s, float3 g) {
@@ -251,7 +255,7 @@ __device__ __noinline__ unsigned process_warps(const LaunchArgs& A, const RpOpts
       const Hit h = closest<LAYOUT, INSTR>(S, w.o, wi, INFINITY, false, cnt);
       ++rays;
       float g = K.miss;
-      if (h.pos >= 0) g = w.t0 < INFINITY ? powf(w.t0 / fmaxf(h.t, 1e-3f * w.t0), K.power) : 1.0f;
+      if (h.pos >= 0) g = w.t0 < INFINITY ? depth_weight(__fdiv_rn(w.t0, fmaxf(h.t, 1e-3f * w.t0)), K.power) : 1.0f;
       alpha = expf(dk * c1) * g;
       pos = h.pos;
       t = h.t;
@@ -264,8 +268,8 @@ __device__ __noinline__ unsigned process_warps(const LaunchArgs& A, const RpOpts
     if (K.jackknife) {
       const float Dj = D - alpha - K.eps;
       const float3 Pj = P - pi * alpha;
-      S1 = group_sum(on ? 1.0f / Dj : 0.0f, gs);
-      SP = group_sum3(on ? Pj * (1.0f / (Dj * Dj)) : f3(0.f, 0.f, 0.f), gs);
+      S1 = group_sum(on ? PT_RCP(Dj) : 0.0f, gs);
+      SP = group_sum3(on ? Pj * PT_RCP(Dj * Dj) : f3(0.f, 0.f, 0.f), gs);
     }
     float3 gv = f3(0.f, 0.f, 0.f);  // coefficient of the relative translation (origin part)
     int si = -1;
@@ -289,27 +293,27 @@ __device__ __noinline__ unsigned process_warps(const LaunchArgs& A, const RpOpts
       auto coef_of = [&](float sv, float3 g) {
         const float3 Ai = base * sv + (g * b + gb * sv) * w.R;
         const float kb = K.kk * b * sv * w.R;
-        float3 c = Ai * (1.0f / D) - P * (kb / (D * D));
+        float3 c = Ai * PT_RCP(D) - P * __fdiv_rn(kb, D * D);
         if (K.jackknife) {
-          const float3 loo = Ai * (S1 - 1.0f / Dm) - (SP - Pm * (1.0f / (Dm * Dm))) * kb;
-          c = c * n - loo * ((n - 1.0f) / n);
+          const float3 loo = Ai * (S1 - PT_RCP(Dm)) - (SP - Pm * PT_RCP(Dm * Dm)) * kb;
+          c = c * n - loo * __fdiv_rn(n - 1.0f, n);
         }
         return c * alpha;
       };
       // plane point seen along w: 1/t(w) = (n.w)/d; the origin moves as a whole
-      gv = coef_of(dot3(nrm, w.u) / di, (nrm - w.u * dot3(nrm, w.u)) * (1.0f / di));
+      gv = coef_of(__fdiv_rn(dot3(nrm, w.u), di), (nrm - w.u * dot3(nrm, w.u)) * PT_RCP(di));
       if constexpr (VERT) {
         // corner j of the hit triangle carries b_j(w)/t(w) = beta_j (n.w)/d + a_j.w with
         // a_1 = (e2 x c)/c.c, a_2 = (c x e1)/c.c, a_0 = -(a_1 + a_2), beta_j = a_j.(o - v0) + [j = 0]
         const float3 v0 = xyz(__ldg(&S.tri_v[3 * pos]));
         const float3 e1 = xyz(__ldg(&S.tri_v[3 * pos + 1])), e2 = xyz(__ldg(&S.tri_v[3 * pos + 2]));
         const float3 c = cross3(e1, e2);
-        const float icc = 1.0f / dot3(c, c);
+        const float icc = PT_RCP(dot3(c, c));
         const float3 a1 = cross3(e2, c) * icc, a2 = cross3(c, e1) * icc;
         const float3 a0 = -(a1 + a2);
         const float3 ov = w.o - v0;
-        const float nu = dot3(nrm, w.u) / di;
-        const float3 nperp = (nrm - w.u * dot3(nrm, w.u)) * (1.0f / di);
+        const float nu = __fdiv_rn(dot3(nrm, w.u), di);
+        const float3 nperp = (nrm - w.u * dot3(nrm, w.u)) * PT_RCP(di);
         float3 gc[3];
         const float3 aj[3] = {a0, a1, a2};
 #pragma unroll
@@ -873,7 +877,7 @@ __device__ __noinline__ unsigned warp_forward(const LaunchArgs& A, const RpOpts&
       const Hit h = closest<LAYOUT, false>(S, w.o, wi, INFINITY, false, cnt);
       ++rays;
       float g = K.miss;
-      if (h.pos >= 0) g = w.t0 < INFINITY ? powf(w.t0 / fmaxf(h.t, 1e-3f * w.t0), K.power) : 1.0f;
+      if (h.pos >= 0) g = w.t0 < INFINITY ? depth_weight(__fdiv_rn(w.t0, fmaxf(h.t, 1e-3f * w.t0)), K.power) : 1.0f;
       alpha = expf(dk * c1) * g;
       pos = h.pos;
       t = h.t;
@@ -886,8 +890,8 @@ __device__ __noinline__ unsigned warp_forward(const LaunchArgs& A, const RpOpts&
     if (K.jackknife) {
       const float Dj = D - alpha - K.eps;
       const float3 Pj = P - pi * alpha;
-      S1 = group_sum(on ? 1.0f / Dj : 0.0f, gs);
-      SP = group_sum3(on ? Pj * (1.0f / (Dj * Dj)) : f3(0.f, 0.f, 0.f), gs);
+      S1 = group_sum(on ? PT_RCP(Dj) : 0.0f, gs);
+      SP = group_sum3(on ? Pj * PT_RCP(Dj * Dj) : f3(0.f, 0.f, 0.f), gs);
     }
     float3 vs = f3(0.f, 0.f, 0.f);
     float dv = 0.0f;
@@ -900,25 +904,25 @@ __device__ __noinline__ unsigned warp_forward(const LaunchArgs& A, const RpOpts&
       if (w.cam >= 0) b = cam_window(A, A.cams[w.cam], w.u, K.border, gb);
       const float3 nrm = tri_normal(S, pos);
       const float di = dot3(nrm, wi) * t;
-      const float nu = dot3(nrm, w.u) / di;
-      const float3 nperp = (nrm - w.u * dot3(nrm, w.u)) * (1.0f / di);
+      const float nu = __fdiv_rn(dot3(nrm, w.u), di);
+      const float3 nperp = (nrm - w.u * dot3(nrm, w.u)) * PT_RCP(di);
       float Dm = 0.0f;
       float3 Pm = f3(0.f, 0.f, 0.f);
       if (K.jackknife) {
         Dm = D - alpha - K.eps;
         Pm = P - pi * alpha;
       }
-      const float Jm = K.jackknife ? n / D - (n - 1.0f) / n * (S1 - 1.0f / Dm) : 1.0f / D;
+      const float Jm = K.jackknife ? __fdiv_rn(n, D) - __fdiv_rn(n - 1.0f, n) * (S1 - PT_RCP(Dm)) : PT_RCP(D);
       // a velocity field s(w) Delta with s linear in w (gradient g on the sphere):
       // its weight in V at u, and the reverse coefficient with M = 0, R = 1 (div part)
       auto parts = [&](float sv, float3 g, float& vw, float3& cr) {
         vw = alpha * b * sv * Jm;
         const float3 Ai = (pi * K.kk - w.u * 2.0f) * (b * sv) + g * b + gb * sv;
         const float kb = K.kk * b * sv;
-        float3 c = Ai * (1.0f / D) - P * (kb / (D * D));
+        float3 c = Ai * PT_RCP(D) - P * __fdiv_rn(kb, D * D);
         if (K.jackknife) {
-          const float3 loo = Ai * (S1 - 1.0f / Dm) - (SP - Pm * (1.0f / (Dm * Dm))) * kb;
-          c = c * n - loo * ((n - 1.0f) / n);
+          const float3 loo = Ai * (S1 - PT_RCP(Dm)) - (SP - Pm * PT_RCP(Dm * Dm)) * kb;
+          c = c * n - loo * __fdiv_rn(n - 1.0f, n);
         }
         cr = c * alpha;
       };
@@ -937,7 +941,7 @@ __device__ __noinline__ unsigned warp_forward(const LaunchArgs& A, const RpOpts&
         const float3 v0 = xyz(__ldg(&S.tri_v[3 * pos]));
         const float3 e1 = xyz(__ldg(&S.tri_v[3 * pos + 1])), e2 = xyz(__ldg(&S.tri_v[3 * pos + 2]));
         const float3 c = cross3(e1, e2);
-        const float icc = 1.0f / dot3(c, c);
+        const float icc = PT_RCP(dot3(c, c));
         const float3 a1 = cross3(e2, c) * icc, a2 = cross3(c, e1) * icc;
         const float3 aj[3] = {-(a1 + a2), a1, a2};
         const float3 ov = w.o - v0;
