@@ -569,6 +569,17 @@ int pt_cache_get_weights(pt_cache* cache, float* host_out);
 int pt_cache_set_weights(pt_cache* cache, const float* host_in);
 /* rgb[i] = MLP(encode(raw[i])), device pointers raw [n][10], rgb [n][3]; async on stream. */
 int pt_cache_query(pt_cache* cache, const float* raw, float* rgb, int n, void* stream);
+/* The input encoding both inference engines feed to the first layer, as BF16 bits:
+ * features [n][64] (device, 16-byte aligned) from raw [n][10] (device); async on
+ * stream.  The frequency encoding of the radiance cache above (Mueller et al. 2021;
+ * the paper names caches only as an open direction, Sec. 3.2): position normalised
+ * to the box, sin and cos of 2^k pi x for k = 0..5 per axis (features 0..35, sin at
+ * even indices); inputs outside [-2^15, 2^15] after normalisation are clamped to it;
+ * direction and normal mapped to [0, 1] with k = 0, 1 (36..47, 48..59); roughness
+ * (60); the constant 1 (61..63).  Each value is rounded to BF16 from FP32 sin / cos
+ * evaluations within 2 ulp.  Errors: PT_ERR_ARG (null pointers with n > 0, n < 0,
+ * unaligned output), PT_ERR_CUDA (launch). */
+int pt_cache_encode(pt_cache* cache, const float* raw, uint16_t* features, int n, void* stream);
 /* Synchronous copies of the averaged weights A (see pt_cache_desc.ema); set_weights
  * also sets A to the given weights. */
 int pt_cache_get_average(pt_cache* cache, float* host_out);

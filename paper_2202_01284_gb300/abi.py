@@ -183,6 +183,7 @@ SIGNATURES = {
     "pt_cache_set_average": ([C.c_void_p, C.c_void_p], C.c_int),
     "pt_cache_set_weights": ([C.c_void_p, C.c_void_p], C.c_int),
     "pt_cache_query": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p], C.c_int),
+    "pt_cache_encode": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p], C.c_int),
     "pt_cache_train_records": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p], C.c_int),
     "pt_cache_last_loss": ([C.c_void_p, C.c_void_p, C.POINTER(C.c_float)], C.c_int),
     "pt_cache_train": ([C.c_void_p, C.c_void_p, C.POINTER(pt_render_desc), C.POINTER(pt_params), C.c_int,
@@ -546,6 +547,11 @@ def pt_cache_status(handle: int, stream: int = 0) -> int:
 
 def pt_cache_query(handle: int, raw, rgb, n: int, stream: int = 0) -> None:
     check("pt_cache_query", load().pt_cache_query(handle, _ptr(raw), _ptr(rgb), n, stream or None))
+
+
+def pt_cache_encode(handle: int, raw, features, n: int, stream: int = 0) -> None:
+    """features: device int16/uint16 [n][64] receiving the BF16 bits of the encoding."""
+    check("pt_cache_encode", load().pt_cache_encode(handle, _ptr(raw), _ptr(features), n, stream or None))
 
 
 def pt_cache_train_records(handle: int, raw, target, n: int, steps: int, stream: int = 0) -> None:

@@ -60,14 +60,7 @@ __device__ __forceinline__ void encode_tile(const float* __restrict__ raw, long 
   }
   uint32_t* dst = reinterpret_cast<uint32_t*>(tile + r * NRC_LD + 32 * half);
 #pragma unroll 4
-  for (int j = 0; j < 32; j += 2) {
-    float a = 0.f, b = 0.f;
-    if (rec < n) {
-      a = nrc_feature(32 * half + j, rr, lo, inv_ext);
-      b = nrc_feature(32 * half + j + 1, rr, lo, inv_ext);
-    }
-    dst[j >> 1] = pack_bf16(a, b);
-  }
+  for (int m = 0; m < 16; ++m) dst[m] = rec < n ? nrc_feature_pair(16 * half + m, rr, lo, inv_ext) : 0u;
 }
 
 // A fragments of the four 16-wide k-tiles of a 16x64 BF16 tile in shared memory.
@@ -631,6 +624,30 @@ CacheBuffers cache_buffers(pt_cache* c) {
 extern "C" int pt_cache_query(pt_cache* c, const float* raw, float* rgb, int n, void* stream) {
   if (!c || n < 0 || (n > 0 && (!raw || !rgb))) return PT_ERR_ARG;
   return cache_infer(c, raw, rgb, n, (cudaStream_t)stream);
+}
+
+// The BF16 features both inference engines feed to the first layer: one thread per
+// record, words[i][m] = nrc_feature_pair(m, raw[i]).
+__global__ void __launch_bounds__(256) nrc_encode_kernel(const float* __restrict__ raw, long long n, NrcBox box,
+                                                         uint4* __restrict__ out) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float rr[NRC_RAW];
+#pragma unroll
+  for (int k = 0; k < NRC_RAW; ++k) rr[k] = raw[i * NRC_RAW + k];
+  uint32_t w[32];
+  nrc_encode_packed(rr, box.lo, box.inv_ext, true, w);
+#pragma unroll
+  for (int c = 0; c < 8; ++c) out[i * 8 + c] = make_uint4(w[4 * c], w[4 * c + 1], w[4 * c + 2], w[4 * c + 3]);
+}
+
+extern "C" int pt_cache_encode(pt_cache* c, const float* raw, uint16_t* features, int n, void* stream) {
+  if (!c || n < 0 || (n > 0 && (!raw || !features))) return PT_ERR_ARG;
+  if ((reinterpret_cast<uintptr_t>(features) & 15u) != 0) return PT_ERR_ARG;
+  if (n == 0) return PT_OK;
+  nrc_encode_kernel<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(raw, n, c->box,
+                                                                                  reinterpret_cast<uint4*>(features));
+  return cudaGetLastError() == cudaSuccess ? PT_OK : PT_ERR_CUDA;
 }
 
 extern "C" int pt_cache_set_engine(pt_cache* c, int engine) {

@@ -63,30 +63,93 @@ __device__ __forceinline__ void ldmatrix_x4_trans(uint32_t (&r)[4], const void* 
                : "r"(addr));
 }
 
-// One encoded feature j (0..63) of a raw record; p is normalised to the box.
-// j <  36: position, axis j/12, frequency 2^((j%12)/2) pi, sin (even j) / cos (odd j)
-// j <  48: direction mapped to [0,1], axis (j-36)/4, frequency 2^(((j-36)%4)/2) pi
-// j <  60: normal, same layout from 48
-// j == 60: roughness; j > 60: constant 1
-__device__ __forceinline__ float nrc_feature(int j, const float* raw, const float* lo, const float* inv_ext) {
+// sin(pi t / 2) and cos(pi t / 2) for |t| <= 2^21, the frequency encoding's only
+// transcendental.  Reduction (exact): q = t rounded to the nearest integer (adding
+// 1.5 * 2^23 leaves q mod 4 in the low bits of the sum), u = t - q in [-1/2, 1/2].
+// Then sin(pi u / 2) = u S(u^2) and cos(pi u / 2) = C(u^2) with S and C of degree 3:
+// near-minimax relative-error fits on |u| <= 1/2 made for this encoding
+// (reweighted least squares on a dense grid, coefficients rounded to FP32; fit
+// error 3.3e-9 and 3.9e-8, FP32 evaluation within 1.7 ulp of sin and 1.5 ulp of
+// cos over the whole interval).  The quadrant q mod 4 swaps the pair and sets the
+// signs: sin(pi t / 2) = sin(q pi / 2 + pi u / 2).
+__device__ __forceinline__ void nrc_sincospi_half(float t, float& s, float& c) {
+  const float m = t + 12582912.0f;
+  const float q = m - 12582912.0f;
+  const float u = t - q;
+  const float v = u * u;
+  const float ps = fmaf(fmaf(fmaf(-4.601703025e-3f, v, 7.968004793e-2f), v, -0.6459634900f), v, 1.570796371f) * u;
+  const float pc = fmaf(fmaf(fmaf(-2.041752636e-2f, v, 0.2536032796f), v, -1.233697653f), v, 1.0f);
+  const uint32_t i = __float_as_uint(m);
+  const float a = (i & 1u) ? pc : ps, b = (i & 1u) ? ps : pc;
+  s = __uint_as_float(__float_as_uint(a) ^ ((i << 30) & 0x80000000u));
+  c = __uint_as_float(__float_as_uint(b) ^ (((i + 1u) << 30) & 0x80000000u));
+}
+
+// x limited to [-2^15, 2^15] (NaN stays NaN), so that every octave's 2^(k+1) x lies
+// in nrc_sincospi_half's domain; inside the box x is in [0, 1].
+__device__ __forceinline__ float nrc_clamp(float x) {
+  float y;
+  asm("max.NaN.f32 %0, %1, 0fC7000000;\n\tmin.NaN.f32 %0, %0, 0f47000000;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// The 64-d encoding of one raw record as 32 BF16 pairs (feature 2m in the low half
+// of word m).  Features:
+//  0..35  position normalised to the box, axis j / 12, sin (even j) / cos (odd j)
+//         of 2^((j % 12) / 2) pi x: six octaves per axis;
+//  36..47 direction mapped to [0, 1] (x = (w + 1) / 2), axis (j - 36) / 4, two
+//         octaves (pi x, 2 pi x);
+//  48..59 the normal, same layout from 48;
+//  60     roughness; 61..63 the constant 1.
+// Word m of the encoding (0..31).
+__device__ __forceinline__ uint32_t nrc_feature_pair(int m, const float* raw, const float* lo,
+                                                     const float* inv_ext) {
   float x;
   int k;
-  if (j < 36) {
-    const int a = j / 12;
-    k = (j % 12) >> 1;
+  if (m < 18) {
+    const int a = m / 6;
+    k = m % 6;
     x = (raw[a] - lo[a]) * inv_ext[a];
-  } else if (j < 60) {
-    const int v = j < 48 ? 0 : 1;
-    const int jj = j - (v ? 48 : 36);
-    const int a = jj >> 2;
-    k = (jj & 3) >> 1;
-    x = 0.5f * (raw[3 + 3 * v + a] + 1.0f);
+  } else if (m < 30) {
+    const int mm = m - 18;  // 0..11: direction axes 0..2, then the normal's
+    k = mm & 1;
+    x = 0.5f * (raw[3 + (mm >> 1)] + 1.0f);
   } else {
-    return j == 60 ? raw[9] : 1.0f;
+    return pack_bf16(m == 30 ? raw[9] : 1.0f, 1.0f);
   }
   float s, c;
-  sincospif(ldexpf(x, k), &s, &c);
-  return (j & 1) ? c : s;
+  nrc_sincospi_half(nrc_clamp(x) * (float)(2 << k), s, c);
+  return pack_bf16(s, c);
+}
+
+// All 32 words of one record (zeros when !live), unrolled: one reduction and one
+// polynomial pair per octave.
+__device__ __forceinline__ void nrc_encode_packed(const float* raw, const float* lo, const float* inv_ext, bool live,
+                                                  uint32_t (&w)[32]) {
+  float s, c;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const float x = nrc_clamp((raw[a] - lo[a]) * inv_ext[a]);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      nrc_sincospi_half(x * (float)(2 << k), s, c);
+      w[6 * a + k] = pack_bf16(s, c);
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < 6; ++a) {
+    const float x = nrc_clamp(0.5f * (raw[3 + a] + 1.0f));
+    nrc_sincospi_half(x * 2.0f, s, c);
+    w[18 + 2 * a] = pack_bf16(s, c);
+    nrc_sincospi_half(x * 4.0f, s, c);
+    w[19 + 2 * a] = pack_bf16(s, c);
+  }
+  w[30] = pack_bf16(raw[9], 1.0f);
+  w[31] = pack_bf16(1.0f, 1.0f);
+  if (!live) {
+#pragma unroll
+    for (int i = 0; i < 32; ++i) w[i] = 0u;
+  }
 }
 
 }  // namespace ptgb

@@ -128,31 +128,6 @@ __device__ __forceinline__ void group_sync(int g) {
   asm volatile("barrier.cta.sync %0, 128;" ::"r"(1 + g) : "memory");
 }
 
-// The 64 encoded features of one query: nrc_feature's encoding, one sincospif per
-// octave (as the mma.sync kernels, so both engines see identical BF16 features;
-// double-angle recurrences were 20 % faster here but flip ~0.6 % of the queries'
-// BF16 features against the FP64 oracle).
-__device__ __forceinline__ void encode_row(const float* rr, const NrcBox& box, float (&f)[64]) {
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {  // position: 6 octaves
-    const float x = (rr[a] - box.lo[a]) * box.inv_ext[a];
-#pragma unroll
-    for (int k = 0; k < 6; ++k) sincospif(ldexpf(x, k), &f[12 * a + 2 * k], &f[12 * a + 2 * k + 1]);
-  }
-#pragma unroll
-  for (int v = 0; v < 2; ++v) {  // direction, normal: 2 octaves of x = (w + 1) / 2
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      const float x = 0.5f * (rr[3 + 3 * v + a] + 1.0f);
-      const int j = 36 + 12 * v + 4 * a;
-      sincospif(x, &f[j], &f[j + 1]);
-      sincospif(ldexpf(x, 1), &f[j + 2], &f[j + 3]);
-    }
-  }
-  f[60] = rr[9];
-  f[61] = f[62] = f[63] = 1.0f;
-}
-
 __global__ void __launch_bounds__(128 * kGroups, 1)
     nrc_infer_tc_kernel(const float* __restrict__ raw, long long n, NrcBox box, const __nv_bfloat16* __restrict__ W,
                         float* __restrict__ out, int* __restrict__ status, unsigned limit) {
@@ -201,16 +176,12 @@ __global__ void __launch_bounds__(128 * kGroups, 1)
 #pragma unroll
     for (int k = 0; k < NRC_RAW; ++k) rr[k] = row < n ? raw[row * NRC_RAW + k] : 0.0f;
     {
-      float f[64];
-      encode_row(rr, box, f);
+      uint32_t w[32];
+      nrc_encode_packed(rr, box.lo, box.inv_ext, row < n, w);
 #pragma unroll
-      for (int c8 = 0; c8 < 8; ++c8) {
-        const float* p = f + 8 * c8;
-        const uint4 q = row < n ? make_uint4(pack_bf16(p[0], p[1]), pack_bf16(p[2], p[3]), pack_bf16(p[4], p[5]),
-                                             pack_bf16(p[6], p[7]))
-                                : make_uint4(0u, 0u, 0u, 0u);
-        *reinterpret_cast<uint4*>(X + core_off(r, 8 * c8)) = q;
-      }
+      for (int c8 = 0; c8 < 8; ++c8)
+        *reinterpret_cast<uint4*>(X + core_off(r, 8 * c8)) =
+            make_uint4(w[4 * c8], w[4 * c8 + 1], w[4 * c8 + 2], w[4 * c8 + 3]);
     }
     fence_async_smem();
     tc_fence_before();
@@ -390,16 +361,12 @@ __global__ void __launch_bounds__(128 * kTrGroups, 1)
       float rr[NRC_RAW];
 #pragma unroll
       for (int k = 0; k < NRC_RAW; ++k) rr[k] = live ? raw[row * NRC_RAW + k] : 0.0f;
-      float f[64];
-      encode_row(rr, box, f);
+      uint32_t w[32];
+      nrc_encode_packed(rr, box.lo, box.inv_ext, live, w);
 #pragma unroll
-      for (int c8 = 0; c8 < 8; ++c8) {
-        const float* p = f + 8 * c8;
-        const uint4 q = live ? make_uint4(pack_bf16(p[0], p[1]), pack_bf16(p[2], p[3]), pack_bf16(p[4], p[5]),
-                                          pack_bf16(p[6], p[7]))
-                             : make_uint4(0u, 0u, 0u, 0u);
-        put_chunk(Xt, r, c8, q, live ? X + row * NRC_W : nullptr);
-      }
+      for (int c8 = 0; c8 < 8; ++c8)
+        put_chunk(Xt, r, c8, make_uint4(w[4 * c8], w[4 * c8 + 1], w[4 * c8 + 2], w[4 * c8 + 3]),
+                  live ? X + row * NRC_W : nullptr);
     }
     fence_async_smem();
     tc_fence_before();
