@@ -5,7 +5,9 @@
 // own: a binned surface-area-heuristic build (cost = 1 per traversal step + 1
 // per triangle test), laid out either as a 2-wide tree with float boxes or as
 // an 8-wide tree with 8-bit quantised child boxes (80-byte nodes, five
-// 16-byte loads per node).
+// 16-byte loads per node).  The 8-wide tree is collapsed from a binary tree
+// built down to single triangles by a cost-optimal dynamic programme that also
+// forms its leaves (up to three triangles).
 #include "bvh_build.h"
 
 #include <algorithm>
@@ -272,11 +274,143 @@ void collapse_children(const BuildTree& t, int b, std::vector<int>& out) {
   }
 }
 
+// Cost-optimal collapse of the binary tree into 8-wide nodes (dynamic programming
+// after Ylitie, Karras and Laine 2017).  A ray that reaches a box pays c_node if the
+// box is a wide node (its eight child tests) or c_tri per triangle if it is a leaf;
+// the chance of reaching a box is proportional to its surface area.  For a binary
+// node m and i = 1..8, slots(m, i) is the cheapest way to put m's subtree into at
+// most i child slots of the parent: one slot holding m itself (a leaf of all its
+// triangles if they are at most max_leaf, or a new wide node), or the slots split
+// between m's two children.  A wide node at m costs c_node A(m) plus the cheapest
+// split of its two children over 8 slots.
+#ifndef PT_WIDE_NODE_COST
+#define PT_WIDE_NODE_COST 1.0
+#endif
+#ifndef PT_WIDE_TRI_COST
+#define PT_WIDE_TRI_COST 0.5
+#endif
+#ifndef PT_WIDE_COLLAPSE_DP
+#define PT_WIDE_COLLAPSE_DP 1
+#endif
+#ifndef PT_WIDE_BUILD_LEAF
+#define PT_WIDE_BUILD_LEAF 1
+#endif
+struct WidePlan {
+  std::vector<int> first, count;           // subtree triangle range in t.order
+  std::vector<float> slots;                // [node][8]: slots(m, i + 1)
+  std::vector<int8_t> how;                 // [node][8]: 0 = m in one slot, k > 0 = k slots left
+  std::vector<uint8_t> leaf;               // m as one slot is a leaf (else a wide node)
+  std::vector<int8_t> split;               // wide node at m: slots given to the left child
+};
+
+WidePlan plan_wide(const BuildTree& t, int max_leaf) {
+  const int n = (int)t.nodes.size();
+  WidePlan p;
+  p.first.assign(n, 0);
+  p.count.assign(n, 0);
+  p.slots.assign((size_t)n * 8, 0.0f);
+  p.how.assign((size_t)n * 8, 0);
+  p.leaf.assign(n, 0);
+  p.split.assign(n, 0);
+  const double cn = PT_WIDE_NODE_COST, ct = PT_WIDE_TRI_COST;
+  // children are created after their parent, so a reverse sweep visits them first
+  for (int m = n - 1; m >= 0; --m) {
+    const BuildNode& b = t.nodes[m];
+    Box bx;
+    std::memcpy(bx.lo, b.lo, sizeof bx.lo);
+    std::memcpy(bx.hi, b.hi, sizeof bx.hi);
+    const double a = bx.area();
+    float* S = &p.slots[(size_t)m * 8];
+    int8_t* H = &p.how[(size_t)m * 8];
+    if (b.left < 0) {
+      p.first[m] = b.first;
+      p.count[m] = b.count;
+      p.leaf[m] = 1;
+      for (int i = 0; i < 8; ++i) S[i] = (float)(ct * b.count * a);
+      continue;
+    }
+    const int l = b.left, r = b.right;
+    p.first[m] = p.first[l];
+    p.count[m] = p.count[l] + p.count[r];
+    const float* SL = &p.slots[(size_t)l * 8];
+    const float* SR = &p.slots[(size_t)r * 8];
+    // wide node at m: the two children over at most 8 slots
+    double best = INFINITY;
+    int bk = 1;
+    for (int k = 1; k < 8; ++k) {
+      const double c = (double)SL[k - 1] + SR[8 - k - 1];
+      if (c < best) {
+        best = c;
+        bk = k;
+      }
+    }
+    const double inner = cn * a + best;
+    const double as_leaf = p.count[m] <= max_leaf ? ct * p.count[m] * a : INFINITY;
+    p.split[m] = (int8_t)bk;
+    p.leaf[m] = as_leaf <= inner ? 1 : 0;
+    const double one = std::min(as_leaf, inner);
+    S[0] = (float)one;
+    H[0] = 0;
+    for (int i = 2; i <= 8; ++i) {
+      double c = S[i - 2];
+      int h = H[i - 2];
+      for (int k = 1; k < i; ++k) {
+        const double d = (double)SL[k - 1] + SR[i - k - 1];
+        if (d < c) {
+          c = d;
+          h = k;
+        }
+      }
+      S[i - 1] = (float)c;
+      H[i - 1] = (int8_t)h;
+    }
+  }
+  return p;
+}
+
+// The child slots of the wide node at binary node m under plan p.
+void plan_slots(const BuildTree& t, const WidePlan& p, int m, int i, std::vector<int>& out) {
+  const int h = p.how[(size_t)m * 8 + i - 1];
+  if (h == 0 || t.nodes[m].left < 0) {
+    out.push_back(m);
+    return;
+  }
+  plan_slots(t, p, t.nodes[m].left, h, out);
+  plan_slots(t, p, t.nodes[m].right, i - h, out);
+}
+void plan_children(const BuildTree& t, const WidePlan& p, int m, std::vector<int>& out) {
+  out.clear();
+  if (t.nodes[m].left < 0) {
+    out.push_back(m);
+    return;
+  }
+  const int k = p.split[m];
+  plan_slots(t, p, t.nodes[m].left, k, out);
+  plan_slots(t, p, t.nodes[m].right, 8 - k, out);
+}
+// Depth of the wide tree the plan makes (levels of wide nodes).
+int plan_depth(const BuildTree& t, const WidePlan& p) {
+  int depth = 0;
+  std::vector<std::pair<int, int>> st{{0, 1}};
+  std::vector<int> kids;
+  while (!st.empty()) {
+    auto [m, d] = st.back();
+    st.pop_back();
+    depth = std::max(depth, d);
+    plan_children(t, p, m, kids);
+    for (int c : kids)
+      if (t.nodes[c].left >= 0 && !p.leaf[c]) st.push_back({c, d + 1});
+  }
+  return depth;
+}
+
 uint32_t pack4(const uint8_t* b) {
   return (uint32_t)b[0] | ((uint32_t)b[1] << 8) | ((uint32_t)b[2] << 16) | ((uint32_t)b[3] << 24);
 }
 
 }  // namespace
+
+int wide_build_leaf(int max_leaf) { return PT_WIDE_COLLAPSE_DP ? std::min(PT_WIDE_BUILD_LEAF, max_leaf) : max_leaf; }
 
 void layout_wide(const BuildTree& t, std::vector<uint32_t>& words, std::vector<int>& order_out, int max_leaf) {
   (void)max_leaf;
@@ -290,9 +424,17 @@ void layout_wide(const BuildTree& t, std::vector<uint32_t>& words, std::vector<i
   words.assign(20, 0u);
   order_out.clear();
   std::vector<int> kids;
+  const WidePlan plan = plan_wide(t, max_leaf);
+  // the traversal keeps one stack entry per wide level: the greedy collapse (at
+  // least two binary levels per wide level) stays the fallback for deep trees
+  const bool use_plan = PT_WIDE_COLLAPSE_DP && plan_depth(t, plan) <= 30;
+  auto inner = [&](int c) { return t.nodes[c].left >= 0 && !(use_plan && plan.leaf[c]); };
   while (head < queue.size()) {
     Item it = queue[head++];
-    collapse_children(t, it.b, kids);
+    if (use_plan)
+      plan_children(t, plan, it.b, kids);
+    else
+      collapse_children(t, it.b, kids);
     // node box = union of the (padded) child boxes
     float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
     std::vector<std::array<float, 6>> cb(kids.size());
@@ -353,7 +495,6 @@ void layout_wide(const BuildTree& t, std::vector<uint32_t>& words, std::vector<i
     for (int sl = 0; sl < 8; ++sl) {
       int i = slot_child[sl];
       if (i < 0) continue;
-      const BuildNode& c = t.nodes[kids[i]];
       for (int k = 0; k < 3; ++k) {
         int q0 = (int)std::floor((cb[i][k] - lo[k]) / scale[k]);
         int q1 = (int)std::ceil((cb[i][3 + k] - lo[k]) / scale[k]);
@@ -364,15 +505,16 @@ void layout_wide(const BuildTree& t, std::vector<uint32_t>& words, std::vector<i
         qlo[k][sl] = (uint8_t)q0;
         qhi[k][sl] = (uint8_t)q1;
       }
-      if (c.left >= 0) {
+      if (inner(kids[i])) {
         imask |= (uint8_t)(1u << sl);
         meta[sl] = (uint8_t)(0x20 | sl);  // non-zero marker; the child index comes from imask ranks
         queue.push_back({kids[i], (int)child_base + inner_rank});
         ++inner_rank;
       } else {
         int off = (int)(order_out.size() - tri_base);
-        for (int k = 0; k < c.count; ++k) order_out.push_back(t.order[c.first + k]);
-        meta[sl] = (uint8_t)((c.count << 5) | off);
+        const int first = plan.first[kids[i]], count = plan.count[kids[i]];
+        for (int k = 0; k < count; ++k) order_out.push_back(t.order[first + k]);
+        meta[sl] = (uint8_t)((count << 5) | off);
       }
     }
     n_wide += inner_rank;

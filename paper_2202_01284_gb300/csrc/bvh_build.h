@@ -33,6 +33,10 @@ BuildTree build_sah(const float* tri_vertices, int n, int max_leaf, int n_bins);
 // `order` (leaf order of triangles) is the one of the build tree.
 void layout_binary(const BuildTree& t, std::vector<float>& words /* 16 floats per node */);
 
+// Leaf size of the binary build that layout_wide collapses (the collapse forms the
+// wide tree's leaves of up to max_leaf triangles itself).
+int wide_build_leaf(int max_leaf);
+
 // 8-wide compressed layout (80 bytes per node = five 16-byte words):
 //   w0 = (origin.x, origin.y, origin.z, exps)  exps = e_x | e_y << 8 | e_z << 16 | imask << 24
 //   w1 = (child_base, tri_base, meta[0..3], meta[4..7])
@@ -40,12 +44,14 @@ void layout_binary(const BuildTree& t, std::vector<float>& words /* 16 floats pe
 //   w3 = (qlo_z[0..3], qlo_z[4..7], qhi_x[0..3], qhi_x[4..7])
 //   w4 = (qhi_y[0..3], qhi_y[4..7], qhi_z[0..3], qhi_z[4..7])
 // A child box is origin + [q_lo, q_hi] * 2^(e - 127) per axis (conservative).
-// meta[k] = 0 for an empty slot; inner child: (1 << 5) | (24 + rank) where rank is
-// the child's position among the node's inner children (they are stored
-// consecutively from child_base); leaf child: ((1 << count) - 1) << 5 | tri_offset
-// with tri_offset relative to tri_base (triangles of all leaf children of a node
-// are consecutive).  imask bit k set = slot k is an inner node.  Reorders
-// `order_out` into the layout's triangle order.
+// meta[k] = 0 for an empty slot; inner child: (1 << 5) | k (non-zero; the child is
+// node child_base + the number of inner slots below k, from imask); leaf child:
+// count << 5 | tri_offset (count 1..3, tri_offset < 32 relative to tri_base: the
+// triangles of all leaf children of a node are consecutive).  imask bit k set = slot
+// k is an inner node.  The children come from a cost-optimal collapse of the binary
+// tree (plan_wide), or the greedy largest-area collapse where that plan's tree would
+// be deeper than the traversal stack.  Reorders `order_out` into the layout's
+// triangle order.
 void layout_wide(const BuildTree& t, std::vector<uint32_t>& words /* 20 words per node */,
                  std::vector<int>& order_out, int max_leaf);
 

@@ -307,7 +307,8 @@ extern "C" int pt_bvh_build(pt_scene* s, const pt_bvh_opts* o) {
   if (n_bins < 4 || n_bins > 64) return PT_ERR_ARG;
   if (opts.layout == PT_BVH_BINARY && max_leaf > 8) return PT_ERR_ARG;
   if (opts.layout == PT_BVH_WIDE && max_leaf > 3) return PT_ERR_ARG;
-  BuildTree tree = build_sah(s->h_vertices, s->n_tris, max_leaf, n_bins);
+  BuildTree tree = build_sah(s->h_vertices, s->n_tris, opts.layout == PT_BVH_WIDE ? wide_build_leaf(max_leaf) : max_leaf,
+                             n_bins);
   std::vector<int> order = tree.order;
   std::vector<float> node_words;
   std::vector<uint32_t> wide_words;
