@@ -150,9 +150,11 @@ int check_bvh(const float* V, int n, const float* rays, int n_rays, int max_leaf
   BuildTree t = build_sah(V, n, max_leaf, 32);
   std::vector<float> bin;
   layout_binary(t, bin);
+  // the 8-wide tree as pt_bvh_build makes it: collapsed from its own binary build
+  BuildTree tw = build_sah(V, n, wide_build_leaf(max_leaf), 32);
   std::vector<uint32_t> W;
   std::vector<int> order;
-  layout_wide(t, W, order, max_leaf);
+  layout_wide(tw, W, order, max_leaf);
   int bad = 0;
   // permutation
   std::vector<int> seen(n, 0);

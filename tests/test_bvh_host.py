@@ -14,10 +14,14 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(os.path.dirname(HERE), "paper_2202_01284_gb300", "csrc")
 
 
-@pytest.fixture(scope="module")
-def harness():
+@pytest.fixture(scope="module", params=["dp", "greedy"])
+def harness(request):
+    """The builder as shipped (8-wide tree by the cost-optimal collapse) and with the
+    greedy largest-area collapse it falls back to for trees deeper than the traversal
+    stack."""
+    flags = [] if request.param == "dp" else ["-DPT_WIDE_COLLAPSE_DP=0"]
     out = os.path.join(tempfile.mkdtemp(prefix="bvhh"), "libbvhh.so")
-    subprocess.run(["g++", "-O2", "-std=c++17", "-fPIC", "-shared", "-I", CSRC, "-o", out,
+    subprocess.run(["g++", "-O2", "-std=c++17", "-fPIC", "-shared", "-I", CSRC, *flags, "-o", out,
                     os.path.join(HERE, "bvh_harness.cpp"), os.path.join(CSRC, "bvh_build.cpp")], check=True)
     lib = ctypes.CDLL(out)
     lib.check_bvh.restype = ctypes.c_int
