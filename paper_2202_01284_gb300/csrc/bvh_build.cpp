@@ -486,6 +486,11 @@ void layout_wide(const BuildTree& t, std::vector<uint32_t>& words, std::vector<i
       e = std::min(std::max(e, -126), 127);
       ebits[k] = e + 127;
       scale[k] = std::ldexp(1.0f, e);
+      // keep 1/256 of a step between each child box and its quantised planes (the
+      // traversal's plane decode rounds by up to 1/512 of a step): the origin moves out
+      // by that much (where FP32 can represent the move; otherwise the step is below
+      // 2^-15 of the coordinate and the boxes' relative padding covers the rounding)
+      lo[k] -= std::ldexp(1.0f, e - 8);
     }
     uint8_t meta[8] = {0}, qlo[3][8] = {{0}}, qhi[3][8] = {{0}};
     uint8_t imask = 0;
@@ -500,8 +505,9 @@ void layout_wide(const BuildTree& t, std::vector<uint32_t>& words, std::vector<i
         int q1 = (int)std::ceil((cb[i][3 + k] - lo[k]) / scale[k]);
         q0 = std::min(std::max(q0, 0), 255);
         q1 = std::min(std::max(q1, 0), 255);
-        while (q0 > 0 && lo[k] + (float)q0 * scale[k] > cb[i][k]) --q0;
-        while (q1 < 255 && lo[k] + (float)q1 * scale[k] < cb[i][3 + k]) ++q1;
+        const float margin = std::ldexp(scale[k], -8);
+        while (q0 > 0 && lo[k] + (float)q0 * scale[k] > cb[i][k] - margin) --q0;
+        while (q1 < 255 && lo[k] + (float)q1 * scale[k] < cb[i][3 + k] + margin) ++q1;
         qlo[k][sl] = (uint8_t)q0;
         qhi[k][sl] = (uint8_t)q1;
       }

@@ -271,6 +271,12 @@ __device__ __forceinline__ Hit trace_wide(const DevScene& S, float3 ro, float3 r
     const float bx = (__uint_as_float(w0.x) - ro.x) * inv.x;
     const float by = (__uint_as_float(w0.y) - ro.y) * inv.y;
     const float bz = (__uint_as_float(w0.z) - ro.z) * inv.z;
+    // a plane byte q enters as the float 1 + q 2^-15 (one byte permute builds it), so that
+    // q a + b = (1 + q 2^-15) A + B with A = 2^15 a and B = b - A: one FMA per plane.  B's
+    // rounding moves a plane by at most 2^-9 of a quantisation step; the builder keeps
+    // 2^-8 of a step between every child box and its planes.
+    const float Ax = ax * 32768.0f, Ay = ay * 32768.0f, Az = az * 32768.0f;
+    const float Bx = bx - Ax, By = by - Ay, Bz = bz - Az;
     // near / far plane bytes per axis (lo planes are near for a positive direction)
     const uint32_t nx0 = rd.x >= 0.0f ? w2.x : w3.z, nx1 = rd.x >= 0.0f ? w2.y : w3.w;
     const uint32_t fx0 = rd.x >= 0.0f ? w3.z : w2.x, fx1 = rd.x >= 0.0f ? w3.w : w2.y;
@@ -282,17 +288,17 @@ __device__ __forceinline__ Hit trace_wide(const DevScene& S, float3 ro, float3 r
 #pragma unroll
     for (int sl = 0; sl < 8; ++sl) {
       const uint32_t meta = ((sl < 4 ? w1.z : w1.w) >> (8 * (sl & 3))) & 0xffu;
-      // byte q of a plane word -> float q: one byte permute builds 2^23 + q, then
-      // subtract 2^23 (both exact), instead of a shift/mask and an int->float convert
-      const uint32_t sel = 0x7540u | (uint32_t)(sl & 3);
-      const float qnx = __uint_as_float(__byte_perm(sl < 4 ? nx0 : nx1, 0x4B000000u, sel)) - 8388608.0f;
-      const float qfx = __uint_as_float(__byte_perm(sl < 4 ? fx0 : fx1, 0x4B000000u, sel)) - 8388608.0f;
-      const float qny = __uint_as_float(__byte_perm(sl < 4 ? ny0 : ny1, 0x4B000000u, sel)) - 8388608.0f;
-      const float qfy = __uint_as_float(__byte_perm(sl < 4 ? fy0 : fy1, 0x4B000000u, sel)) - 8388608.0f;
-      const float qnz = __uint_as_float(__byte_perm(sl < 4 ? nz0 : nz1, 0x4B000000u, sel)) - 8388608.0f;
-      const float qfz = __uint_as_float(__byte_perm(sl < 4 ? fz0 : fz1, 0x4B000000u, sel)) - 8388608.0f;
-      const float tn = fmaxf(fmaxf(fmaf(qnx, ax, bx), fmaf(qny, ay, by)), fmaxf(fmaf(qnz, az, bz), 0.0f));
-      const float tf = fminf(fminf(fmaf(qfx, ax, bx), fmaf(qfy, ay, by)), fminf(fmaf(qfz, az, bz), h.t));
+      // byte q of a plane word -> the float 1 + q 2^-15 (bits 0x3F80qq00): one byte
+      // permute, no shift/mask and no int->float convert
+      const uint32_t sel = 0x7604u | ((uint32_t)(sl & 3) << 4);
+      const float qnx = __uint_as_float(__byte_perm(sl < 4 ? nx0 : nx1, 0x3F800000u, sel));
+      const float qfx = __uint_as_float(__byte_perm(sl < 4 ? fx0 : fx1, 0x3F800000u, sel));
+      const float qny = __uint_as_float(__byte_perm(sl < 4 ? ny0 : ny1, 0x3F800000u, sel));
+      const float qfy = __uint_as_float(__byte_perm(sl < 4 ? fy0 : fy1, 0x3F800000u, sel));
+      const float qnz = __uint_as_float(__byte_perm(sl < 4 ? nz0 : nz1, 0x3F800000u, sel));
+      const float qfz = __uint_as_float(__byte_perm(sl < 4 ? fz0 : fz1, 0x3F800000u, sel));
+      const float tn = fmaxf(fmaxf(fmaf(qnx, Ax, Bx), fmaf(qny, Ay, By)), fmaxf(fmaf(qnz, Az, Bz), 0.0f));
+      const float tf = fminf(fminf(fmaf(qfx, Ax, Bx), fmaf(qfy, Ay, By)), fminf(fmaf(qfz, Az, Bz), h.t));
       if (meta != 0u && tn <= tf) {
         if ((imask >> sl) & 1u) inner_hits |= 1u << (sl ^ flip);
         else leaf_hits |= 1u << sl;

@@ -91,6 +91,12 @@ int trace_wide(Ctx& c, const std::vector<uint32_t>& W, const float* o, const flo
       a[k] = sc * inv[k];
       b[k] = (p[k] - o[k]) * inv[k];
     }
+    // as the kernel: plane q enters as 1 + q 2^-15 against A = 2^15 a and B = b - A
+    float A[3], B[3];
+    for (int k = 0; k < 3; ++k) {
+      A[k] = a[k] * 32768.0f;
+      B[k] = b[k] - A[k];
+    }
     auto byte_of = [&](int word0, int sl) { return (w[word0 + (sl >> 2)] >> (8 * (sl & 3))) & 0xffu; };
     const int lo_w[3] = {8, 10, 12}, hi_w[3] = {14, 16, 18};
     uint32_t inner_hits = 0;
@@ -100,8 +106,8 @@ int trace_wide(Ctx& c, const std::vector<uint32_t>& W, const float* o, const flo
       for (int k = 0; k < 3; ++k) {
         float qn = (float)byte_of(d[k] >= 0 ? lo_w[k] : hi_w[k], sl);
         float qf = (float)byte_of(d[k] >= 0 ? hi_w[k] : lo_w[k], sl);
-        tn = std::max(tn, std::fma(qn, a[k], b[k]));
-        tf = std::min(tf, std::fma(qf, a[k], b[k]));
+        tn = std::max(tn, std::fma(1.0f + qn * (1.0f / 32768.0f), A[k], B[k]));
+        tf = std::min(tf, std::fma(1.0f + qf * (1.0f / 32768.0f), A[k], B[k]));
       }
       if (meta == 0u || !(tn <= tf)) continue;
       if ((imask >> sl) & 1u) {
