@@ -492,7 +492,11 @@ void layout_wide(const BuildTree& t, std::vector<uint32_t>& words, std::vector<i
       // 2^-15 of the coordinate and the boxes' relative padding covers the rounding)
       lo[k] -= std::ldexp(1.0f, e - 8);
     }
-    uint8_t meta[8] = {0}, qlo[3][8] = {{0}}, qhi[3][8] = {{0}};
+    // empty slots get inverted boxes (low planes 255, high planes 0), which every slab
+    // test rejects: the traversal needs no separate empty-slot test
+    uint8_t meta[8] = {0}, qlo[3][8], qhi[3][8];
+    std::memset(qlo, 0xff, sizeof qlo);
+    std::memset(qhi, 0, sizeof qhi);
     uint8_t imask = 0;
     uint32_t child_base = (uint32_t)n_wide;
     uint32_t tri_base = (uint32_t)order_out.size();

@@ -284,10 +284,12 @@ __device__ __forceinline__ Hit trace_wide(const DevScene& S, float3 ro, float3 r
     const uint32_t fy0 = rd.y >= 0.0f ? w4.x : w2.z, fy1 = rd.y >= 0.0f ? w4.y : w2.w;
     const uint32_t nz0 = rd.z >= 0.0f ? w3.x : w4.z, nz1 = rd.z >= 0.0f ? w3.y : w4.w;
     const uint32_t fz0 = rd.z >= 0.0f ? w4.z : w3.x, fz1 = rd.z >= 0.0f ? w4.w : w3.y;
-    uint32_t inner_hits = 0, leaf_hits = 0;
+    // hit slots in slot order; empty slots hold inverted boxes that the slab test rejects
+    // (and one that passes anyway, a degenerate box below FP32 resolution, is a leaf of
+    // zero triangles), so no per-slot bookkeeping beyond one compare and one OR
+    uint32_t hitm = 0;
 #pragma unroll
     for (int sl = 0; sl < 8; ++sl) {
-      const uint32_t meta = ((sl < 4 ? w1.z : w1.w) >> (8 * (sl & 3))) & 0xffu;
       // byte q of a plane word -> the float 1 + q 2^-15 (bits 0x3F80qq00): one byte
       // permute, no shift/mask and no int->float convert
       const uint32_t sel = 0x7604u | ((uint32_t)(sl & 3) << 4);
@@ -299,11 +301,14 @@ __device__ __forceinline__ Hit trace_wide(const DevScene& S, float3 ro, float3 r
       const float qfz = __uint_as_float(__byte_perm(sl < 4 ? fz0 : fz1, 0x3F800000u, sel));
       const float tn = fmaxf(fmaxf(fmaf(qnx, Ax, Bx), fmaf(qny, Ay, By)), fmaxf(fmaf(qnz, Az, Bz), 0.0f));
       const float tf = fminf(fminf(fmaf(qfx, Ax, Bx), fmaf(qfy, Ay, By)), fminf(fmaf(qfz, Az, Bz), h.t));
-      if (meta != 0u && tn <= tf) {
-        if ((imask >> sl) & 1u) inner_hits |= 1u << (sl ^ flip);
-        else leaf_hits |= 1u << sl;
-      }
+      if (tn <= tf) hitm |= 1u << sl;
     }
+    uint32_t leaf_hits = hitm & ~imask;
+    uint32_t inner_hits = hitm & imask;
+    // inner hits in octant order: slot sl -> bit sl ^ flip (three masked swaps)
+    inner_hits = (flip & 1u) ? ((inner_hits & 0x55u) << 1) | ((inner_hits >> 1) & 0x55u) : inner_hits;
+    inner_hits = (flip & 2u) ? ((inner_hits & 0x33u) << 2) | ((inner_hits >> 2) & 0x33u) : inner_hits;
+    inner_hits = (flip & 4u) ? ((inner_hits & 0x0Fu) << 4) | ((inner_hits >> 4) & 0x0Fu) : inner_hits;
     // triangles of the hit leaf children
     bool stop = false;
     while (leaf_hits) {

@@ -109,7 +109,7 @@ int trace_wide(Ctx& c, const std::vector<uint32_t>& W, const float* o, const flo
         tn = std::max(tn, std::fma(1.0f + qn * (1.0f / 32768.0f), A[k], B[k]));
         tf = std::min(tf, std::fma(1.0f + qf * (1.0f / 32768.0f), A[k], B[k]));
       }
-      if (meta == 0u || !(tn <= tf)) continue;
+      if (!(tn <= tf)) continue;  // as the kernel: an empty slot that passes is a leaf of zero triangles
       if ((imask >> sl) & 1u) {
         inner_hits |= 1u << (sl ^ flip);
       } else {
