@@ -483,8 +483,8 @@ void layout_wide(const BuildTree& t, std::vector<uint32_t>& words, std::vector<i
     for (int k = 0; k < 3; ++k) {
       float ext = std::max(hi[k] - lo[k], 1e-30f);
       int e = (int)std::ceil(std::log2(ext / 254.0f));
-      e = std::min(std::max(e, -126), 127);
-      ebits[k] = e + 127;
+      e = std::min(std::max(e, -126), 112);
+      ebits[k] = e + 127 + 15;  // stored as the FP32 exponent of 2^15 times the step
       scale[k] = std::ldexp(1.0f, e);
       // keep 1/256 of a step between each child box and its quantised planes (the
       // traversal's plane decode rounds by up to 1/512 of a step): the origin moves out

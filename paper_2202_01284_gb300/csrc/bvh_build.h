@@ -43,7 +43,8 @@ int wide_build_leaf(int max_leaf);
 //   w2 = (qlo_x[0..3], qlo_x[4..7], qlo_y[0..3], qlo_y[4..7])
 //   w3 = (qlo_z[0..3], qlo_z[4..7], qhi_x[0..3], qhi_x[4..7])
 //   w4 = (qhi_y[0..3], qhi_y[4..7], qhi_z[0..3], qhi_z[4..7])
-// A child box is origin + [q_lo, q_hi] * 2^(e - 127) per axis (conservative, with
+// The exponent byte e of an axis is the FP32 exponent of 2^15 times its step: a
+// child box is origin + [q_lo, q_hi] * 2^(e - 142) per axis (conservative, with
 // 2^-8 of a step between the planes and the padded child box where FP32 allows).
 // meta[k] = 0 for an empty slot; inner child: (1 << 5) | k (non-zero; the child is
 // node child_base + the number of inner slots below k, from imask); leaf child:

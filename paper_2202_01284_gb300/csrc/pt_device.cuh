@@ -265,18 +265,18 @@ __device__ __forceinline__ Hit trace_wide(const DevScene& S, float3 ro, float3 r
     const uint4 w4 = __ldg(&N[5 * node + 4]);
     const uint32_t ex = w0.w & 0xffu, ey = (w0.w >> 8) & 0xffu, ez = (w0.w >> 16) & 0xffu;
     const uint32_t imask = w0.w >> 24;
-    const float ax = __uint_as_float(ex << 23) * inv.x;
-    const float ay = __uint_as_float(ey << 23) * inv.y;
-    const float az = __uint_as_float(ez << 23) * inv.z;
-    const float bx = (__uint_as_float(w0.x) - ro.x) * inv.x;
-    const float by = (__uint_as_float(w0.y) - ro.y) * inv.y;
-    const float bz = (__uint_as_float(w0.z) - ro.z) * inv.z;
-    // a plane byte q enters as the float 1 + q 2^-15 (one byte permute builds it), so that
-    // q a + b = (1 + q 2^-15) A + B with A = 2^15 a and B = b - A: one FMA per plane.  B's
-    // rounding moves a plane by at most 2^-9 of a quantisation step; the builder keeps
-    // 2^-8 of a step between every child box and its planes.
-    const float Ax = ax * 32768.0f, Ay = ay * 32768.0f, Az = az * 32768.0f;
-    const float Bx = bx - Ax, By = by - Ay, Bz = bz - Az;
+    // plane q of an axis with step s sits at t = q a + b, a = s / d, b = (origin - o) / d.
+    // A plane byte enters as the float 1 + q 2^-15 (one byte permute builds it), so that
+    // q a + b = (1 + q 2^-15) A + B with A = 2^15 a (the node stores the exponent of
+    // 2^15 s) and B = b - A in one FMA: one FMA per plane.  B's rounding moves a plane by
+    // at most 2^-9 of a step; the builder keeps 2^-8 of a step between every child box
+    // and its planes.
+    const float Ax = __uint_as_float(ex << 23) * inv.x;
+    const float Ay = __uint_as_float(ey << 23) * inv.y;
+    const float Az = __uint_as_float(ez << 23) * inv.z;
+    const float Bx = fmaf(__uint_as_float(w0.x) - ro.x, inv.x, -Ax);
+    const float By = fmaf(__uint_as_float(w0.y) - ro.y, inv.y, -Ay);
+    const float Bz = fmaf(__uint_as_float(w0.z) - ro.z, inv.z, -Az);
     // near / far plane bytes per axis (lo planes are near for a positive direction)
     const uint32_t nx0 = rd.x >= 0.0f ? w2.x : w3.z, nx1 = rd.x >= 0.0f ? w2.y : w3.w;
     const uint32_t fx0 = rd.x >= 0.0f ? w3.z : w2.x, fx1 = rd.x >= 0.0f ? w3.w : w2.y;

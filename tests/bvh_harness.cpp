@@ -83,19 +83,15 @@ int trace_wide(Ctx& c, const std::vector<uint32_t>& W, const float* o, const flo
     uint32_t e = w[3], imask = e >> 24;
     float p[3];
     std::memcpy(p, w, 12);
-    float a[3], b[3];
+    // as the kernel: plane q enters as 1 + q 2^-15 against A = 2^15 a (the stored
+    // exponent is that of 2^15 times the step) and B = b - A in one FMA
+    float A[3], B[3];
     for (int k = 0; k < 3; ++k) {
       uint32_t bits = ((e >> (8 * k)) & 0xffu) << 23;
       float sc;
       std::memcpy(&sc, &bits, 4);
-      a[k] = sc * inv[k];
-      b[k] = (p[k] - o[k]) * inv[k];
-    }
-    // as the kernel: plane q enters as 1 + q 2^-15 against A = 2^15 a and B = b - A
-    float A[3], B[3];
-    for (int k = 0; k < 3; ++k) {
-      A[k] = a[k] * 32768.0f;
-      B[k] = b[k] - A[k];
+      A[k] = sc * inv[k];
+      B[k] = std::fma(p[k] - o[k], inv[k], -A[k]);
     }
     auto byte_of = [&](int word0, int sl) { return (w[word0 + (sl >> 2)] >> (8 * (sl & 3))) & 0xffu; };
     const int lo_w[3] = {8, 10, 12}, hi_w[3] = {14, 16, 18};
@@ -190,6 +186,7 @@ int check_bvh(const float* V, int n, const float* rays, int n_rays, int max_leaf
     for (int k = 0; k < 3; ++k) {
       uint32_t bits = ((e >> (8 * k)) & 0xffu) << 23;
       std::memcpy(&sc[k], &bits, 4);
+      sc[k] *= 1.0f / 32768.0f;  // the step itself
     }
     for (int sl = 0; sl < 8; ++sl) {
       uint32_t meta = (w[6 + (sl >> 2)] >> (8 * (sl & 3))) & 0xffu;
