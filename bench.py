@@ -81,7 +81,7 @@ def alu_roofline(kernel, counters, bvh, ms, clk, note=""):
 TRAFFIC_PER_RAY = {"wide": {"forward_kernel": 84.8, "radiance_kernel": 109.9, "replay_kernel": 34.9}}
 # reparam_kernel (translation mode): DRAM bytes per sample of the same kind of capture
 # (409 MB per 256x256 x 4 spp launch).
-REPARAM_TRAFFIC_PER_SAMPLE = 1560.0
+REPARAM_TRAFFIC_PER_SAMPLE = 1535.0
 TRAFFIC_BASIS = ("ncu dram__bytes_read.sum + dram__bytes_write.sum per counted ray at 256x256 "
                  "(profiles/dram_per_ray_spheres196k_256px_64spp.md), times the launch's counted rays")
 
