@@ -23,9 +23,9 @@ CPP_SOURCES = ["bvh_build.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # Per-source floating-point flags.  In the megakernel sources device divisions a / b
 # and square roots are the approximate ones (at most 2 ulp / the hardware square root):
-# measured 3.4 % and 1.7 % of the path tracer's step.  Reciprocals that decide
-# traversal (ray inverse direction, the triangle test's 1 / det) use __frcp_rn
-# everywhere.  The reparameterized source keeps IEEE division: with the approximate
+# measured 3.4 % and 1.7 % of the path tracer's step.  The triangle test's 1 / det
+# uses __frcp_rn everywhere (hit decisions as under IEEE division); the ray's inverse
+# direction, which only the padded box tests use, the hardware reciprocal.  The reparameterized source keeps IEEE division: with the approximate
 # one its glossy log-derivatives and vertex-mode tangents moved by up to 1.6e-3
 # relative against the FP64 reference (the warp estimator's own ratios of sums,
 # written as __fdiv_rn / __frcp_rn, were not the cause).  The cache MLP keeps IEEE

@@ -23,14 +23,9 @@ namespace ptgb {
 #define PT_STACK 64
 // 1/x through the correctly rounded reciprocal: the same value as the IEEE
 // division 1.0f / x, without the division's general code path.
-#ifndef PT_FAST_RCP
-#define PT_FAST_RCP 1
-#endif
-#if PT_FAST_RCP
+// Correctly rounded reciprocal (the same bits as 1.0f / x under IEEE division, whatever
+// a source's division flags)
 #define PT_RCP(x) __frcp_rn(x)
-#else
-#define PT_RCP(x) (1.0f / (x))
-#endif
 
 // ---------------------------------------------------------------- float3 helpers
 __device__ __forceinline__ float3 f3(float a, float b, float c) { return make_float3(a, b, c); }
@@ -101,11 +96,19 @@ struct Hit {
   float t, u, v;
 };
 
+// The ray's inverse direction for the box tests (only they use it): the hardware
+// reciprocal, within 1 ulp; the boxes' padding (3e-6 relative plus the absolute pad and
+// the 8-wide layout's 2^-8-step margin) is far wider than that.
+__device__ __forceinline__ float rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
 __device__ __forceinline__ float3 safe_inv(float3 d) {
   const float eps = 1e-20f;
-  return f3(PT_RCP(fabsf(d.x) > eps ? d.x : copysignf(eps, d.x)),
-            PT_RCP(fabsf(d.y) > eps ? d.y : copysignf(eps, d.y)),
-            PT_RCP(fabsf(d.z) > eps ? d.z : copysignf(eps, d.z)));
+  return f3(rcp_approx(fabsf(d.x) > eps ? d.x : copysignf(eps, d.x)),
+            rcp_approx(fabsf(d.y) > eps ? d.y : copysignf(eps, d.y)),
+            rcp_approx(fabsf(d.z) > eps ? d.z : copysignf(eps, d.z)));
 }
 
 // Moller-Trumbore in FP32 (edges inclusive, det == 0 misses).  Updates the
