@@ -311,15 +311,18 @@ __device__ __forceinline__ void megakernel(const LaunchArgs& A, long long unit, 
 // Measured on the 196k-triangle sphere workload (forward + adjoint step): with the
 // per-vertex shading out of line, more resident warps beat fewer spills -- the
 // forward runs best at 5 CTAs (48 registers: 45.6 ms; 46.4 at 64, 62 at 128) once
-// the production instances carry no fingerprint or adjoint-only state, the adjoint
-// and the replay at 3 (80 registers: replay 62.6 ms; 64.2 at 64, 69.3 at 128).
+// the production instances carry no fingerprint or adjoint-only state, the fused
+// adjoint at 3 (80 registers; the batched kernels measured 381 ms there, 387 at 64).
+// With the shorter node visit (one FMA per box plane, a hit mask per node) the forward
+// still prefers 5 CTAs (37.3 ms; 38.1 at 64 registers, 39.9 at 40), while the split-PRB
+// replay and the forward-mode kernel moved to 4 (their own caps in pt_render.cu).
 #ifndef PT_LB_THREADS
 #define PT_LB_THREADS 256  // block size the forward / replay register caps are computed for
 #endif
 #ifndef PT_FWD_MIN_BLOCKS
 #define PT_FWD_MIN_BLOCKS 5
 #endif
-// The checkpointing forward and the batched forward keep 64 registers (measured there).
+// The batched forward keeps 64 registers (measured there).
 #ifndef PT_OTHER_FWD_MIN_BLOCKS
 #define PT_OTHER_FWD_MIN_BLOCKS 4
 #endif
