@@ -523,6 +523,21 @@ int pt_render_jvp_reparam_vertices(pt_scene* scene, const pt_render_desc* desc, 
                                    const pt_reparam_opts* opts, const float* dir_vertices, float* image,
                                    float* image_dot, unsigned long long* rays, void* stream);
 
+/* Ray queries against the scene's BVH, through the same traversal the path tracer runs
+ * (the scene-intersection call of the paper's rendering API, Sec. 3.1, which Mitsuba 3
+ * hands to Embree or OptiX; here the library's own 2- or 8-wide BVH).  Asynchronous on
+ * stream.  rays: device [n][6] floats (origin xyz, direction xyz; t is measured in units
+ * of the direction, which need not be unit length); tmax: device [n] or NULL (no limit);
+ * any_hit = 0: the closest hit with 0 < t < tmax (ties in t go to the smaller triangle
+ * index); any_hit = 1: some hit with 0 < t < tmax (shadow-ray semantics).  Outputs
+ * (device): t [n] (INFINITY on a miss), prim [n] (the input index of the hit triangle as
+ * given to pt_scene_create, -1 on a miss), uv [n][2] or NULL (barycentric coordinates of
+ * the hit on that triangle: p = (1 - u - v) v0 + u v1 + v v2).  Errors: PT_ERR_ARG (n <
+ * 0, null pointers with n > 0), PT_ERR_STATE (no BVH built), PT_ERR_CUDA (launch); a
+ * traversal stack overflow is reported later by pt_last_device_status as PT_ERR_BVH. */
+int pt_trace_rays(pt_scene* scene, const float* rays, const float* tmax, int n, int any_hit, float* t, int* prim,
+                  float* uv, void* stream);
+
 /* Reads (and clears) the scene's device status word after synchronising
  * `stream`: *out = PT_OK or the first PT_ERR_* a kernel recorded. */
 int pt_last_device_status(pt_scene* scene, void* stream, int* out);

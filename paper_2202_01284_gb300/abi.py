@@ -184,6 +184,8 @@ SIGNATURES = {
     "pt_cache_set_weights": ([C.c_void_p, C.c_void_p], C.c_int),
     "pt_cache_query": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p], C.c_int),
     "pt_cache_encode": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p], C.c_int),
+    "pt_trace_rays": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
+                       C.c_void_p], C.c_int),
     "pt_cache_train_records": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p], C.c_int),
     "pt_cache_last_loss": ([C.c_void_p, C.c_void_p, C.POINTER(C.c_float)], C.c_int),
     "pt_cache_train": ([C.c_void_p, C.c_void_p, C.POINTER(pt_render_desc), C.POINTER(pt_params), C.c_int,
@@ -547,6 +549,13 @@ def pt_cache_status(handle: int, stream: int = 0) -> int:
 
 def pt_cache_query(handle: int, raw, rgb, n: int, stream: int = 0) -> None:
     check("pt_cache_query", load().pt_cache_query(handle, _ptr(raw), _ptr(rgb), n, stream or None))
+
+
+def pt_trace_rays(scene: int, rays, n: int, t, prim, tmax=None, uv=None, any_hit: bool = False,
+                  stream: int = 0) -> None:
+    """rays: device float32 [n][6]; t: float32 [n]; prim: int32 [n]; tmax, uv optional."""
+    check("pt_trace_rays", load().pt_trace_rays(scene, _ptr(rays), _ptr(tmax), n, int(bool(any_hit)), _ptr(t),
+                                               _ptr(prim), _ptr(uv), stream or None))
 
 
 def pt_cache_encode(handle: int, raw, features, n: int, stream: int = 0) -> None:

@@ -895,3 +895,45 @@ extern "C" int pt_render_jvp(pt_scene* s, const pt_render_desc* r, const pt_para
   else jvp_kernel<PT_BVH_BINARY><<<(unsigned)grid, block, 0, cs>>>(A);
   return cudaGetLastError() == cudaSuccess ? PT_OK : PT_ERR_CUDA;
 }
+
+// ---------------------------------------------------------------- ray queries
+namespace ptgb {
+namespace {
+// One thread per ray through the megakernels' own traversal (same source, same
+// compile flags): closest hit, or any hit before tmax.
+template <int LAYOUT>
+__global__ void __launch_bounds__(128) trace_rays_kernel(DevScene S, const float* __restrict__ rays,
+                                                         const float* __restrict__ tmax, int n, int any_hit,
+                                                         float* __restrict__ t_out, int* __restrict__ prim_out,
+                                                         float* __restrict__ uv_out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float3 o = f3(rays[6 * i], rays[6 * i + 1], rays[6 * i + 2]);
+  const float3 d = f3(rays[6 * i + 3], rays[6 * i + 4], rays[6 * i + 5]);
+  const float tm = tmax ? tmax[i] : INFINITY;
+  Counters<false> cnt;
+  const Hit h = LAYOUT == PT_BVH_WIDE ? trace_wide<false>(S, o, d, tm, any_hit != 0, cnt)
+                                      : trace_binary<false>(S, o, d, tm, any_hit != 0, cnt);
+  t_out[i] = h.pos >= 0 ? h.t : INFINITY;
+  prim_out[i] = h.pos >= 0 ? (int)__float_as_uint(__ldg(&S.tri_v[3 * h.pos]).w) : -1;
+  if (uv_out) {
+    uv_out[2 * i] = h.pos >= 0 ? h.u : 0.0f;
+    uv_out[2 * i + 1] = h.pos >= 0 ? h.v : 0.0f;
+  }
+}
+}  // namespace
+}  // namespace ptgb
+
+extern "C" int pt_trace_rays(pt_scene* s, const float* rays, const float* tmax, int n, int any_hit, float* t,
+                             int* prim, float* uv, void* stream) {
+  if (!s || n < 0 || (n > 0 && (!rays || !t || !prim))) return PT_ERR_ARG;
+  if (!s->has_bvh) return PT_ERR_STATE;
+  if (n == 0) return PT_OK;
+  const cudaStream_t cs = (cudaStream_t)stream;
+  const unsigned grid = (unsigned)((n + 127) / 128);
+  if (s->dev.layout == PT_BVH_WIDE)
+    trace_rays_kernel<PT_BVH_WIDE><<<grid, 128, 0, cs>>>(s->dev, rays, tmax, n, any_hit, t, prim, uv);
+  else
+    trace_rays_kernel<PT_BVH_BINARY><<<grid, 128, 0, cs>>>(s->dev, rays, tmax, n, any_hit, t, prim, uv);
+  return cudaGetLastError() == cudaSuccess ? PT_OK : PT_ERR_CUDA;
+}
