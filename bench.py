@@ -119,6 +119,9 @@ def parse():
                     help="radiance-cache MLP inference throughput, tcgen05 vs mma.sync engines (own JSON line)")
     ap.add_argument("--ckpt", action="store_true",
                     help="PRB vs reverse mode with checkpoints, one gradient step each (own JSON line)")
+    ap.add_argument("--trace", action="store_true",
+                    help="ray queries alone (pt_trace_rays) on the sphere scene: coherent camera rays and "
+                         "incoherent surface rays, closest and any hit, G rays/s (own JSON line)")
     ap.add_argument("--texgrad", action="store_true",
                     help="PRB adjoint of the 96-shape textured room (2048^2 atlas + 96 roughness values): "
                          "Mrays/s and gradient atomics/s (own JSON line)")
@@ -521,6 +524,90 @@ def run_ours(args):
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def run_trace_experiment(args):
+    """Ray queries alone, through the megakernels' traversal (pt_trace_rays), on the
+    sphere scene's 8-wide BVH: 2048^2 jittered camera rays (coherent) and as many rays
+    leaving random surface points in uniform hemisphere directions (incoherent, like
+    the path tracer's bounces), closest hit, and the incoherent set again as any-hit
+    queries without a distance limit.  Rays are made on the device from a seeded
+    torch generator; 100 MB of rays per set, the L2 flushed before every launch.  The
+    megakernel's rays/s include shading and sampling; these are the traversal's.
+    Own JSON line."""
+    import math
+
+    import torch
+
+    from paper_2202_01284_gb300 import abi
+    from paper_2202_01284_gb300 import scenes as S
+    from paper_2202_01284_gb300.render import DeviceScene
+    abi.load()
+    dev = torch.device("cuda", 0)
+    sc = S.spheres()
+    ds = DeviceScene(sc, layout=abi.PT_BVH_WIDE, device=dev)
+    w = 512 if args.small else 2048
+    n = w * w
+    g = torch.Generator(device=dev).manual_seed(2022)
+    cam = sc.cameras[0]
+    o = torch.tensor(cam.origin, dtype=torch.float32, device=dev)
+    f = torch.tensor(cam.target, dtype=torch.float32, device=dev) - o
+    f = f / f.norm()
+    r = torch.linalg.cross(f, torch.tensor(cam.up, dtype=torch.float32, device=dev))
+    r = r / r.norm()
+    u = torch.linalg.cross(r, f)
+    th = math.tan(math.radians(cam.vfov_deg) / 2)
+    iy, ix = torch.meshgrid(torch.arange(w, device=dev), torch.arange(w, device=dev), indexing="ij")
+    jit = torch.rand((w, w, 2), device=dev, generator=g)
+    sx = (2 * (ix + jit[..., 0]) / w - 1).reshape(-1, 1) * th * cam.width / cam.height
+    sy = (1 - 2 * (iy + jit[..., 1]) / w).reshape(-1, 1) * th
+    d = f + sx * r + sy * u
+    cam_rays = torch.cat([o.expand(n, 3), d / d.norm(dim=1, keepdim=True)], 1).contiguous()
+    V = torch.as_tensor(sc.vertices, dtype=torch.float32, device=dev)
+    ti = torch.randint(0, V.shape[0], (n,), device=dev, generator=g)
+    b = -torch.log(torch.rand((n, 3), device=dev, generator=g).clamp_min(1e-12))  # rand may return 0
+    b = b / b.sum(1, keepdim=True)
+    p = (b[:, :, None] * V[ti]).sum(1)
+    nrm = torch.linalg.cross(V[ti, 1] - V[ti, 0], V[ti, 2] - V[ti, 0])
+    nrm = nrm / nrm.norm(dim=1, keepdim=True).clamp_min(1e-30)
+    dd = torch.randn((n, 3), device=dev, generator=g)
+    dd = dd / dd.norm(dim=1, keepdim=True)
+    dd = torch.where((dd * nrm).sum(1, keepdim=True) < 0, -dd, dd)
+    eps = 1e-4 * max(1.0, float(V.abs().max()))
+    sec_rays = torch.cat([p + eps * nrm, dd], 1).contiguous()
+    t = torch.empty(n, device=dev)
+    prim = torch.empty(n, dtype=torch.int32, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    res = {}
+    clocks = ClockSampler(0)
+    clocks.start()
+    for name, rays, any_hit in (("camera_closest", cam_rays, False), ("surface_closest", sec_rays, False),
+                                ("surface_any", sec_rays, True)):
+        for _ in range(max(3, args.warmup)):
+            abi.pt_trace_rays(ds.handle, rays, n, t, prim, any_hit=any_hit, stream=stream.cuda_stream)
+        ms = []
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            abi.pt_trace_rays(ds.handle, rays, n, t, prim, any_hit=any_hit, stream=stream.cuda_stream)
+            e.record(stream)
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(e))
+        hit = float((prim >= 0).float().mean())
+        res[name] = {"ms": round(statistics.mean(ms), 4), "grays_s": round(n / statistics.mean(ms) / 1e6, 3),
+                     "hit_fraction": round(hit, 4)}
+    clk = clocks.stop()
+    assert ds.status() == 0
+    line = {"metric": "ray queries through the path tracer's traversal, G rays/s (surface rays, closest hit)",
+            "value": res["surface_closest"]["grays_s"], "unit": "G rays/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": max(3, args.warmup), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"spheres32x5120 + ground (196,608 tris), 8-wide BVH, {n} rays per set",
+                       "l2": "flushed before each launch", "sets": res},
+            "gpu_launches": 3 * args.steps, "clocks": clk}
+    print(json.dumps(line), flush=True)
 
 
 def run_texgrad_experiment(args):
@@ -1314,6 +1401,8 @@ def main():
         run_ckpt_experiment(args)
     elif args.reparam:
         run_reparam_experiment(args)
+    elif args.trace:
+        run_trace_experiment(args)
     elif args.texgrad:
         run_texgrad_experiment(args)
     elif args.mlp:

@@ -532,7 +532,8 @@ int pt_render_jvp_reparam_vertices(pt_scene* scene, const pt_render_desc* desc, 
  * index); any_hit = 1: some hit with 0 < t < tmax (shadow-ray semantics).  Outputs
  * (device): t [n] (INFINITY on a miss), prim [n] (the input index of the hit triangle as
  * given to pt_scene_create, -1 on a miss), uv [n][2] or NULL (barycentric coordinates of
- * the hit on that triangle: p = (1 - u - v) v0 + u v1 + v v2).  Errors: PT_ERR_ARG (n <
+ * the hit on that triangle: p = (1 - u - v) v0 + u v1 + v v2).  A ray with a non-finite
+ * component or a zero direction misses.  Errors: PT_ERR_ARG (n <
  * 0, null pointers with n > 0), PT_ERR_STATE (no BVH built), PT_ERR_CUDA (launch); a
  * traversal stack overflow is reported later by pt_last_device_status as PT_ERR_BVH. */
 int pt_trace_rays(pt_scene* scene, const float* rays, const float* tmax, int n, int any_hit, float* t, int* prim,

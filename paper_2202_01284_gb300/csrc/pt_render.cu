@@ -912,8 +912,17 @@ __global__ void __launch_bounds__(128) trace_rays_kernel(DevScene S, const float
   const float3 d = f3(rays[6 * i + 3], rays[6 * i + 4], rays[6 * i + 5]);
   const float tm = tmax ? tmax[i] : INFINITY;
   Counters<false> cnt;
-  const Hit h = LAYOUT == PT_BVH_WIDE ? trace_wide<false>(S, o, d, tm, any_hit != 0, cnt)
-                                      : trace_binary<false>(S, o, d, tm, any_hit != 0, cnt);
+  Hit h;
+  h.pos = -1;
+  h.t = INFINITY;
+  h.u = h.v = 0.0f;
+  // a ray with a non-finite component misses (its box tests would otherwise pass
+  // everywhere: min / max drop a NaN)
+  const bool finite = isfinite(o.x) && isfinite(o.y) && isfinite(o.z) && isfinite(d.x) && isfinite(d.y) &&
+                      isfinite(d.z) && (d.x != 0.0f || d.y != 0.0f || d.z != 0.0f);
+  if (finite)
+    h = LAYOUT == PT_BVH_WIDE ? trace_wide<false>(S, o, d, tm, any_hit != 0, cnt)
+                              : trace_binary<false>(S, o, d, tm, any_hit != 0, cnt);
   t_out[i] = h.pos >= 0 ? h.t : INFINITY;
   prim_out[i] = h.pos >= 0 ? (int)__float_as_uint(__ldg(&S.tri_v[3 * h.pos]).w) : -1;
   if (uv_out) {

@@ -267,3 +267,18 @@ def test_trace_argument_checks(lib):
         lib.pt_trace_rays(ds.handle, rays, -1, t, p)
     with pytest.raises(lib.PtError):
         lib.pt_trace_rays(ds.handle, None, 4, t, p)
+
+
+def test_non_finite_and_zero_rays_miss(lib):
+    """NaN or infinite components and a zero direction are misses (t = INFINITY, prim
+    -1), next to ordinary rays in the same launch that still hit."""
+    from paper_2202_01284_gb300.render import DeviceScene
+    sc = S.cornell()
+    ds = DeviceScene(sc, layout=lib.PT_BVH_WIDE)
+    good = _rays(sc, 16, 3)[:16]
+    bad = np.array([[np.nan, 1, 3.5, 0, 0, -1], [0, 1, 3.5, np.nan, 0, -1], [0, 1, 3.5, 0, np.inf, -1],
+                    [np.inf, 1, 3.5, 0, 0, -1], [0, 1, 3.5, 0, 0, 0]], np.float32)
+    rays = np.concatenate([good, bad])
+    t_g, p_g, _ = _gpu_trace(lib, ds, rays)
+    assert np.all(p_g[-5:] == -1) and np.all(np.isinf(t_g[-5:]))
+    assert np.any(p_g[:16] >= 0)
