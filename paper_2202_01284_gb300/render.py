@@ -55,6 +55,7 @@ class DeviceScene:
             self.handle = None
             raise
         dev = torch.device(device)
+        self.device = dev
         self.albedo = torch.as_tensor(scene.albedo, dtype=torch.float32).reshape(-1, 3).to(dev).contiguous()
         self.textures = [torch.as_tensor(t, dtype=torch.float32).to(dev).contiguous() for t in scene.textures]
         self.roughness = torch.as_tensor(scene.roughness, dtype=torch.float32).to(dev).contiguous()
@@ -230,6 +231,21 @@ class DeviceScene:
 
     def status(self) -> int:
         return abi.pt_last_device_status(self.handle, torch.cuda.current_stream().cuda_stream)
+
+    def trace(self, origins: torch.Tensor, directions: torch.Tensor, tmax: torch.Tensor = None,
+              any_hit: bool = False):
+        """Ray queries through the path tracer's traversal (pt_trace_rays): closest hit
+        (or any hit before tmax) of each ray.  origins, directions: [n, 3] on this
+        device.  Returns (t [n], prim [n] int32: input triangle index or -1, uv [n, 2])."""
+        rays = torch.cat([origins, directions], 1).to(device=self.device, dtype=torch.float32).contiguous()
+        n = rays.shape[0]
+        t = torch.empty(n, device=self.device)
+        prim = torch.empty(n, dtype=torch.int32, device=self.device)
+        uv = torch.empty((n, 2), device=self.device)
+        tm = None if tmax is None else tmax.to(device=self.device, dtype=torch.float32).contiguous()
+        abi.pt_trace_rays(self.handle, rays, n, t, prim, tmax=tm, uv=uv, any_hit=any_hit,
+                          stream=torch.cuda.current_stream(self.device).cuda_stream)
+        return t, prim, uv
 
 
 class Checkpoints:

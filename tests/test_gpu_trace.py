@@ -282,3 +282,8 @@ def test_non_finite_and_zero_rays_miss(lib):
     t_g, p_g, _ = _gpu_trace(lib, ds, rays)
     assert np.all(p_g[-5:] == -1) and np.all(np.isinf(t_g[-5:]))
     assert np.any(p_g[:16] >= 0)
+    # the same through DeviceScene.trace
+    r = torch.as_tensor(rays, device="cuda")
+    t2, p2, _ = ds.trace(r[:, :3], r[:, 3:])
+    torch.cuda.synchronize()
+    assert np.array_equal(p2.cpu().numpy(), p_g) and np.array_equal(t2.cpu().numpy().astype(np.float64), t_g)
