@@ -237,147 +237,123 @@ __device__ __forceinline__ Hit trace_binary(const DevScene& S, float3 ro, float3
 // the ray direction), intersects the triangles of hit leaf children at once, and
 // pushes the remaining hit inner children as one (base, mask) group.  Children
 // are visited in the order of the slot octants relative to the ray direction.
-// The state of one ray's traversal of the 8-wide BVH.
-struct WideTrav {
-  Ray r;
-  Hit h;
-  float3 inv;
-  uint32_t flip, best_orig;
-  int sp, node;
-};
-// The traversal stack lives in its own array (a dynamically indexed member would put the
-// whole state in local memory): groups of (child base, inner-slot mask | hit mask << 8).
-typedef uint2 WideStack[32];
-
-__device__ __forceinline__ void wide_begin(WideTrav& w, float3 ro, float3 rd, float tmax) {
-  w.h.pos = -1;
-  w.h.t = tmax;
-  w.h.u = w.h.v = 0.0f;
-  w.r.o = ro;
-  w.r.d = rd;
-  w.best_orig = 0xffffffffu;
-  w.inv = safe_inv(rd);
-  w.flip = (rd.x >= 0.0f ? 1u : 0u) | (rd.y >= 0.0f ? 2u : 0u) | (rd.z >= 0.0f ? 4u : 0u);
-  w.sp = 0;
-  w.node = 0;
-}
-
-// One node visit of the ray's traversal: its eight child boxes, the triangles of the hit
-// leaf children, then the next node; false once the traversal is over (w.h holds the
-// result).
-template <bool INSTR>
-__device__ __forceinline__ bool wide_step(const DevScene& S, WideTrav& w, WideStack& stack, bool any_hit,
-                                          unsigned& n_nodes, unsigned& n_tris, unsigned& warp_steps) {
-  const uint4* __restrict__ N = reinterpret_cast<const uint4*>(S.nodes);
-  ++n_nodes;
-  if constexpr (INSTR) {
-    if (lane_id() == __ffs(__activemask()) - 1) ++warp_steps;
-  }
-  const uint4 w0 = __ldg(&N[5 * w.node]);
-  const uint4 w1 = __ldg(&N[5 * w.node + 1]);
-  const uint4 w2 = __ldg(&N[5 * w.node + 2]);
-  const uint4 w3 = __ldg(&N[5 * w.node + 3]);
-  const uint4 w4 = __ldg(&N[5 * w.node + 4]);
-  const uint32_t ex = w0.w & 0xffu, ey = (w0.w >> 8) & 0xffu, ez = (w0.w >> 16) & 0xffu;
-  const uint32_t imask = w0.w >> 24;
-  // plane q of an axis with step s sits at t = q a + b, a = s / d, b = (origin - o) / d.
-  // A plane byte enters as the float 1 + q 2^-15 (one byte permute builds it), so that
-  // q a + b = (1 + q 2^-15) A + B with A = 2^15 a (the node stores the exponent of
-  // 2^15 s) and B = b - A in one FMA: one FMA per plane.  B's rounding moves a plane by
-  // at most 2^-9 of a step; the builder keeps 2^-8 of a step between every child box
-  // and its planes.
-  const float Ax = __uint_as_float(ex << 23) * w.inv.x;
-  const float Ay = __uint_as_float(ey << 23) * w.inv.y;
-  const float Az = __uint_as_float(ez << 23) * w.inv.z;
-  const float Bx = fmaf(__uint_as_float(w0.x) - w.r.o.x, w.inv.x, -Ax);
-  const float By = fmaf(__uint_as_float(w0.y) - w.r.o.y, w.inv.y, -Ay);
-  const float Bz = fmaf(__uint_as_float(w0.z) - w.r.o.z, w.inv.z, -Az);
-  // near / far plane bytes per axis (lo planes are near for a positive direction)
-  const uint32_t nx0 = w.r.d.x >= 0.0f ? w2.x : w3.z, nx1 = w.r.d.x >= 0.0f ? w2.y : w3.w;
-  const uint32_t fx0 = w.r.d.x >= 0.0f ? w3.z : w2.x, fx1 = w.r.d.x >= 0.0f ? w3.w : w2.y;
-  const uint32_t ny0 = w.r.d.y >= 0.0f ? w2.z : w4.x, ny1 = w.r.d.y >= 0.0f ? w2.w : w4.y;
-  const uint32_t fy0 = w.r.d.y >= 0.0f ? w4.x : w2.z, fy1 = w.r.d.y >= 0.0f ? w4.y : w2.w;
-  const uint32_t nz0 = w.r.d.z >= 0.0f ? w3.x : w4.z, nz1 = w.r.d.z >= 0.0f ? w3.y : w4.w;
-  const uint32_t fz0 = w.r.d.z >= 0.0f ? w4.z : w3.x, fz1 = w.r.d.z >= 0.0f ? w4.w : w3.y;
-  // hit slots in slot order; empty slots hold inverted boxes that the slab test rejects
-  // (and one that passes anyway, a degenerate box below FP32 resolution, is a leaf of
-  // zero triangles), so no per-slot bookkeeping beyond one compare and one OR
-  uint32_t hitm = 0;
-#pragma unroll
-  for (int sl = 0; sl < 8; ++sl) {
-    // byte q of a plane word -> the float 1 + q 2^-15 (bits 0x3F80qq00): one byte
-    // permute, no shift/mask and no int->float convert
-    const uint32_t sel = 0x7604u | ((uint32_t)(sl & 3) << 4);
-    const float qnx = __uint_as_float(__byte_perm(sl < 4 ? nx0 : nx1, 0x3F800000u, sel));
-    const float qfx = __uint_as_float(__byte_perm(sl < 4 ? fx0 : fx1, 0x3F800000u, sel));
-    const float qny = __uint_as_float(__byte_perm(sl < 4 ? ny0 : ny1, 0x3F800000u, sel));
-    const float qfy = __uint_as_float(__byte_perm(sl < 4 ? fy0 : fy1, 0x3F800000u, sel));
-    const float qnz = __uint_as_float(__byte_perm(sl < 4 ? nz0 : nz1, 0x3F800000u, sel));
-    const float qfz = __uint_as_float(__byte_perm(sl < 4 ? fz0 : fz1, 0x3F800000u, sel));
-    const float tn = fmaxf(fmaxf(fmaf(qnx, Ax, Bx), fmaf(qny, Ay, By)), fmaxf(fmaf(qnz, Az, Bz), 0.0f));
-    const float tf = fminf(fminf(fmaf(qfx, Ax, Bx), fmaf(qfy, Ay, By)), fminf(fmaf(qfz, Az, Bz), w.h.t));
-    if (tn <= tf) hitm |= 1u << sl;
-  }
-  uint32_t leaf_hits = hitm & ~imask;
-  uint32_t inner_hits = hitm & imask;
-  // inner hits in octant order: slot sl -> bit sl ^ flip (three masked swaps)
-  inner_hits = (w.flip & 1u) ? ((inner_hits & 0x55u) << 1) | ((inner_hits >> 1) & 0x55u) : inner_hits;
-  inner_hits = (w.flip & 2u) ? ((inner_hits & 0x33u) << 2) | ((inner_hits >> 2) & 0x33u) : inner_hits;
-  inner_hits = (w.flip & 4u) ? ((inner_hits & 0x0Fu) << 4) | ((inner_hits >> 4) & 0x0Fu) : inner_hits;
-  // triangles of the hit leaf children
-  bool stop = false;
-  while (leaf_hits) {
-    const int sl = __ffs(leaf_hits) - 1;
-    leaf_hits &= leaf_hits - 1;
-    const uint32_t meta = ((sl < 4 ? w1.z : w1.w) >> (8 * (sl & 3))) & 0xffu;
-    const int count = (int)(meta >> 5), first = (int)w1.y + (int)(meta & 31u);
-    n_tris += count;
-    bool found = false;
-    for (int i = 0; i < count; ++i)
-      found |= tri_test(S.tri_v, first + i, w.r, w.h.t, w.h.pos, w.best_orig, w.h.u, w.h.v);
-    if (found && any_hit) {
-      stop = true;
-      break;
-    }
-  }
-  if (stop) return false;
-  // next node: nearest-octant hit child, the rest stays on the stack as one group
-  uint32_t base = w1.x, gmask = imask, hits = inner_hits;
-  if (hits == 0u) {
-    if (w.sp == 0) return false;
-    const uint2 e = stack[w.sp - 1];
-    --w.sp;
-    base = e.x;
-    gmask = e.y & 0xffu;
-    hits = e.y >> 8;
-  }
-  const int k = __ffs(hits) - 1;
-  hits &= hits - 1;
-  const int sl = k ^ (int)w.flip;
-  w.node = (int)base + __popc(gmask & ((1u << sl) - 1u));
-  if (hits) {
-    if (w.sp >= 32) {
-      set_status(S, PT_ERR_BVH);
-      return false;
-    }
-    stack[w.sp++] = make_uint2(base, gmask | (hits << 8));
-  }
-  return true;
-}
-
 template <bool INSTR>
 __device__ __forceinline__ Hit trace_wide(const DevScene& S, float3 ro, float3 rd, float tmax, bool any_hit,
                                           Counters<INSTR>& cnt) {
-  WideTrav w;
-  WideStack stack;
-  wide_begin(w, ro, rd, tmax);
-  unsigned n_nodes = 0, n_tris = 0, warp_steps = 0;
-  while (wide_step<INSTR>(S, w, stack, any_hit, n_nodes, n_tris, warp_steps)) {
+  Hit h;
+  h.pos = -1;
+  h.t = tmax;
+  h.u = h.v = 0.0f;
+  Ray r;
+  r.o = ro;
+  r.d = rd;
+  uint32_t best_orig = 0xffffffffu;
+  const float3 inv = safe_inv(rd);
+  const uint32_t flip = (rd.x >= 0.0f ? 1u : 0u) | (rd.y >= 0.0f ? 2u : 0u) | (rd.z >= 0.0f ? 4u : 0u);
+  const uint4* __restrict__ N = reinterpret_cast<const uint4*>(S.nodes);
+  uint2 stack[32];
+  int sp = 0;
+  int node = 0;
+  unsigned n_nodes = 0, n_tris = 0;
+  unsigned warp_steps = 0;
+  for (;;) {
+    ++n_nodes;
+    if constexpr (INSTR) {
+      if (lane_id() == __ffs(__activemask()) - 1) ++warp_steps;
+    }
+    const uint4 w0 = __ldg(&N[5 * node]);
+    const uint4 w1 = __ldg(&N[5 * node + 1]);
+    const uint4 w2 = __ldg(&N[5 * node + 2]);
+    const uint4 w3 = __ldg(&N[5 * node + 3]);
+    const uint4 w4 = __ldg(&N[5 * node + 4]);
+    const uint32_t ex = w0.w & 0xffu, ey = (w0.w >> 8) & 0xffu, ez = (w0.w >> 16) & 0xffu;
+    const uint32_t imask = w0.w >> 24;
+    // plane q of an axis with step s sits at t = q a + b, a = s / d, b = (origin - o) / d.
+    // A plane byte enters as the float 1 + q 2^-15 (one byte permute builds it), so that
+    // q a + b = (1 + q 2^-15) A + B with A = 2^15 a (the node stores the exponent of
+    // 2^15 s) and B = b - A in one FMA: one FMA per plane.  B's rounding moves a plane by
+    // at most 2^-9 of a step; the builder keeps 2^-8 of a step between every child box
+    // and its planes.
+    const float Ax = __uint_as_float(ex << 23) * inv.x;
+    const float Ay = __uint_as_float(ey << 23) * inv.y;
+    const float Az = __uint_as_float(ez << 23) * inv.z;
+    const float Bx = fmaf(__uint_as_float(w0.x) - ro.x, inv.x, -Ax);
+    const float By = fmaf(__uint_as_float(w0.y) - ro.y, inv.y, -Ay);
+    const float Bz = fmaf(__uint_as_float(w0.z) - ro.z, inv.z, -Az);
+    // near / far plane bytes per axis (lo planes are near for a positive direction)
+    const uint32_t nx0 = rd.x >= 0.0f ? w2.x : w3.z, nx1 = rd.x >= 0.0f ? w2.y : w3.w;
+    const uint32_t fx0 = rd.x >= 0.0f ? w3.z : w2.x, fx1 = rd.x >= 0.0f ? w3.w : w2.y;
+    const uint32_t ny0 = rd.y >= 0.0f ? w2.z : w4.x, ny1 = rd.y >= 0.0f ? w2.w : w4.y;
+    const uint32_t fy0 = rd.y >= 0.0f ? w4.x : w2.z, fy1 = rd.y >= 0.0f ? w4.y : w2.w;
+    const uint32_t nz0 = rd.z >= 0.0f ? w3.x : w4.z, nz1 = rd.z >= 0.0f ? w3.y : w4.w;
+    const uint32_t fz0 = rd.z >= 0.0f ? w4.z : w3.x, fz1 = rd.z >= 0.0f ? w4.w : w3.y;
+    // hit slots in slot order; empty slots hold inverted boxes that the slab test rejects
+    // (and one that passes anyway, a degenerate box below FP32 resolution, is a leaf of
+    // zero triangles), so no per-slot bookkeeping beyond one compare and one OR
+    uint32_t hitm = 0;
+#pragma unroll
+    for (int sl = 0; sl < 8; ++sl) {
+      // byte q of a plane word -> the float 1 + q 2^-15 (bits 0x3F80qq00): one byte
+      // permute, no shift/mask and no int->float convert
+      const uint32_t sel = 0x7604u | ((uint32_t)(sl & 3) << 4);
+      const float qnx = __uint_as_float(__byte_perm(sl < 4 ? nx0 : nx1, 0x3F800000u, sel));
+      const float qfx = __uint_as_float(__byte_perm(sl < 4 ? fx0 : fx1, 0x3F800000u, sel));
+      const float qny = __uint_as_float(__byte_perm(sl < 4 ? ny0 : ny1, 0x3F800000u, sel));
+      const float qfy = __uint_as_float(__byte_perm(sl < 4 ? fy0 : fy1, 0x3F800000u, sel));
+      const float qnz = __uint_as_float(__byte_perm(sl < 4 ? nz0 : nz1, 0x3F800000u, sel));
+      const float qfz = __uint_as_float(__byte_perm(sl < 4 ? fz0 : fz1, 0x3F800000u, sel));
+      const float tn = fmaxf(fmaxf(fmaf(qnx, Ax, Bx), fmaf(qny, Ay, By)), fmaxf(fmaf(qnz, Az, Bz), 0.0f));
+      const float tf = fminf(fminf(fmaf(qfx, Ax, Bx), fmaf(qfy, Ay, By)), fminf(fmaf(qfz, Az, Bz), h.t));
+      if (tn <= tf) hitm |= 1u << sl;
+    }
+    uint32_t leaf_hits = hitm & ~imask;
+    uint32_t inner_hits = hitm & imask;
+    // inner hits in octant order: slot sl -> bit sl ^ flip (three masked swaps)
+    inner_hits = (flip & 1u) ? ((inner_hits & 0x55u) << 1) | ((inner_hits >> 1) & 0x55u) : inner_hits;
+    inner_hits = (flip & 2u) ? ((inner_hits & 0x33u) << 2) | ((inner_hits >> 2) & 0x33u) : inner_hits;
+    inner_hits = (flip & 4u) ? ((inner_hits & 0x0Fu) << 4) | ((inner_hits >> 4) & 0x0Fu) : inner_hits;
+    // triangles of the hit leaf children
+    bool stop = false;
+    while (leaf_hits) {
+      const int sl = __ffs(leaf_hits) - 1;
+      leaf_hits &= leaf_hits - 1;
+      const uint32_t meta = ((sl < 4 ? w1.z : w1.w) >> (8 * (sl & 3))) & 0xffu;
+      const int count = (int)(meta >> 5), first = (int)w1.y + (int)(meta & 31u);
+      n_tris += count;
+      bool found = false;
+      for (int i = 0; i < count; ++i) found |= tri_test(S.tri_v, first + i, r, h.t, h.pos, best_orig, h.u, h.v);
+      if (found && any_hit) {
+        stop = true;
+        break;
+      }
+    }
+    if (stop) break;
+    // next node: nearest-octant hit child, the rest stays on the stack as one group
+    uint32_t base = w1.x, gmask = imask, hits = inner_hits;
+    if (hits == 0u) {
+      if (sp == 0) break;
+      const uint2 e = stack[sp - 1];
+      --sp;
+      base = e.x;
+      gmask = e.y & 0xffu;
+      hits = e.y >> 8;
+    }
+    const int k = __ffs(hits) - 1;
+    hits &= hits - 1;
+    const int sl = k ^ (int)flip;
+    node = (int)base + __popc(gmask & ((1u << sl) - 1u));
+    if (hits) {
+      if (sp >= 32) {
+        set_status(S, PT_ERR_BVH);
+        break;
+      }
+      stack[sp++] = make_uint2(base, gmask | (hits << 8));
+    }
   }
   cnt.add(3, n_nodes);
   cnt.add(4, n_tris);
   cnt.add(14, warp_steps);
-  return w.h;
+  return h;
 }
 
 // ---------------------------------------------------------------- shading frame
