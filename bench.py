@@ -1068,6 +1068,9 @@ def run_reparam_experiment(args):
 
 
 MLP_FLOPS_PER_QUERY = 2 * (5 * 64 * 64 + 64 * 3)  # five 64x64 layers + the 64x3 head
+# one training record: the forward, the head's and four hidden layers' input gradients
+# (the encoding's is not needed) and all weight gradients
+MLP_TRAIN_FLOPS_PER_RECORD = MLP_FLOPS_PER_QUERY + 2 * (64 * 3 + 4 * 64 * 64) + 2 * (5 * 64 * 64 + 64 * 3)
 
 
 def measured_peak(key, fallback):
@@ -1080,7 +1083,8 @@ def measured_peak(key, fallback):
 
 def run_mlp_experiment(args):
     """Radiance-cache MLP inference throughput: the tcgen05 engine (UMMA, TMEM
-    accumulators) against the mma.sync engine on the same queries.  Own JSON line."""
+    accumulators) against the mma.sync engine on the same queries; then training
+    throughput (Adam steps on 65,536-record batches) of both engines.  Own JSON line."""
     import numpy as np
     import torch
 
@@ -1114,8 +1118,35 @@ def run_mlp_experiment(args):
         t = statistics.mean(ms)
         res[name] = {"ms": round(t, 4), "gqueries_s": round(n / t / 1e6, 3),
                      "tflops": round(n * MLP_FLOPS_PER_QUERY / t / 1e9, 1)}
-    clk = clocks.stop()
     abi.pt_cache_destroy(h)
+    # training: Adam steps on batches of 65,536 records (forward, backward deltas, weight
+    # gradients, Adam), both engines, on the first 16 M records of the same set
+    batch, tsteps = 65536, 16
+    n_rec = batch * tsteps
+    _, tgt = S.random_cache_records(min(n_rec, 1 << 20), 3, *box)
+    tgt = np.tile(tgt, (n_rec // tgt.shape[0], 1))
+    d_tgt = torch.as_tensor(tgt, device="cuda")
+    train = {}
+    for name, eng in (("tcgen05", abi.PT_CACHE_TCGEN05), ("mma_sync", abi.PT_CACHE_MMA_SYNC)):
+        ht = abi.pt_cache_create(*box, batch=batch, init_weights=S.mlp_init_weights(12))
+        abi.pt_cache_set_engine(ht, eng)
+        for _ in range(max(3, args.warmup)):
+            abi.pt_cache_train_records(ht, d_raw, d_tgt, n_rec, tsteps)
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(args.steps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            abi.pt_cache_train_records(ht, d_raw, d_tgt, n_rec, tsteps)
+            b.record()
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+        assert abi.pt_cache_status(ht) == abi.PT_OK
+        abi.pt_cache_destroy(ht)
+        t = statistics.mean(ms)
+        train[name] = {"ms_per_adam_step": round(t / tsteps, 4), "mrecords_s": round(n_rec / t / 1e3, 1),
+                       "tflops": round(n_rec * MLP_TRAIN_FLOPS_PER_RECORD / t / 1e9, 1)}
+    clk = clocks.stop()
     peak, basis = measured_peak("bf16_tflops", 1900.0)
     ach = res["tcgen05"]["tflops"]
     line = {"metric": "radiance-cache MLP inference, queries/s (tcgen05 vs mma.sync)",
@@ -1123,7 +1154,9 @@ def run_mlp_experiment(args):
             "warmup": max(3, args.warmup), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "bf16 (FP32 accumulate)", "data": "synthetic",
             "config": {"workload": f"{n} queries, 64-d encoding, 5x64 ReLU + 64x3, BF16 weights", "engines": res,
-                       "speedup_over_mma_sync": round(res["mma_sync"]["ms"] / res["tcgen05"]["ms"], 2)},
+                       "speedup_over_mma_sync": round(res["mma_sync"]["ms"] / res["tcgen05"]["ms"], 2),
+                       "training": {"batch": batch, "adam_steps": tsteps, "engines": train,
+                                    "flops_per_record": MLP_TRAIN_FLOPS_PER_RECORD}},
             "roofline": {"bound": "tensor", "kernel": "nrc_infer_tc_kernel", "achieved": ach, "peak": peak,
                          "unit": "TFLOP/s", "frac": round(ach / peak, 4), "traffic": None,
                          "peak_basis": f"bf16 dense, {basis} (cuBLAS burst); includes the encoding on CUDA cores"},
