@@ -47,20 +47,26 @@ __device__ __forceinline__ void load_weights_smem(const __nv_bfloat16* __restric
   }
 }
 
-// Encode 16 records (rows) of a warp tile into padded shared rows (BF16).
+// Encode 16 records (rows) of a warp tile into padded shared rows (BF16): lanes
+// 0..15 write words 0..17 (position) of rows 0..15, lanes 16..31 words 18..31.
 __device__ __forceinline__ void encode_tile(const float* __restrict__ raw, long long row0, long long n,
                                             const float* lo, const float* inv_ext, __nv_bfloat16* tile) {
   const int lane = threadIdx.x & 31;
   const int r = lane & 15, half = lane >> 4;
   const long long rec = row0 + r;
-  float rr[NRC_RAW];
+  uint32_t* dst = reinterpret_cast<uint32_t*>(tile + r * NRC_LD);
   if (rec < n) {
+    float rr[NRC_RAW];
 #pragma unroll
     for (int k = 0; k < NRC_RAW; ++k) rr[k] = raw[rec * NRC_RAW + k];
+    if (half == 0)
+      nrc_encode_position(rr, lo, inv_ext, dst);
+    else
+      nrc_encode_direction(rr, dst + 18);
+  } else {
+    const int m0 = half ? 18 : 0, m1 = half ? 32 : 18;
+    for (int m = m0; m < m1; ++m) dst[m] = 0u;
   }
-  uint32_t* dst = reinterpret_cast<uint32_t*>(tile + r * NRC_LD + 32 * half);
-#pragma unroll 4
-  for (int m = 0; m < 16; ++m) dst[m] = rec < n ? nrc_feature_pair(16 * half + m, rr, lo, inv_ext) : 0u;
 }
 
 // A fragments of the four 16-wide k-tiles of a 16x64 BF16 tile in shared memory.
@@ -627,7 +633,7 @@ extern "C" int pt_cache_query(pt_cache* c, const float* raw, float* rgb, int n, 
 }
 
 // The BF16 features both inference engines feed to the first layer: one thread per
-// record, words[i][m] = nrc_feature_pair(m, raw[i]).
+// record, words[i] = nrc_encode_packed(raw[i]).
 __global__ void __launch_bounds__(256) nrc_encode_kernel(const float* __restrict__ raw, long long n, NrcBox box,
                                                          uint4* __restrict__ out) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;

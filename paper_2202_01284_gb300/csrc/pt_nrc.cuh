@@ -93,6 +93,18 @@ __device__ __forceinline__ float nrc_clamp(float x) {
   return y;
 }
 
+// One octave up: (sin a, cos a) -> (sin 2a, cos 2a) = (2 s c, c^2 - s^2).  In the
+// form c^2 - s^2 (not 1 - 2 s^2) the step's Jacobian is twice a rotation, so an
+// error already in the pair grows by exactly a factor 2 per octave, and each step
+// adds at most 2^-25 to s and 2^-24 to c of FP32 rounding.  From the pair of
+// nrc_sincospi_half (each within 2^-23), after k steps the pair is within
+// 2^k * 4 * 2^-24 (Euclidean) of the exact pair of the same FP32 argument.
+__device__ __forceinline__ void nrc_double_angle(float& s, float& c) {
+  const float s2 = (s + s) * c;
+  c = fmaf(c, c, -(s * s));
+  s = s2;
+}
+
 // The 64-d encoding of one raw record as 32 BF16 pairs (feature 2m in the low half
 // of word m).  Features:
 //  0..35  position normalised to the box, axis j / 12, sin (even j) / cos (odd j)
@@ -101,51 +113,44 @@ __device__ __forceinline__ float nrc_clamp(float x) {
 //         octaves (pi x, 2 pi x);
 //  48..59 the normal, same layout from 48;
 //  60     roughness; 61..63 the constant 1.
-// Word m of the encoding (0..31).
-__device__ __forceinline__ uint32_t nrc_feature_pair(int m, const float* raw, const float* lo,
-                                                     const float* inv_ext) {
-  float x;
-  int k;
-  if (m < 18) {
-    const int a = m / 6;
-    k = m % 6;
-    x = (raw[a] - lo[a]) * inv_ext[a];
-  } else if (m < 30) {
-    const int mm = m - 18;  // 0..11: direction axes 0..2, then the normal's
-    k = mm & 1;
-    x = 0.5f * (raw[3 + (mm >> 1)] + 1.0f);
-  } else {
-    return pack_bf16(m == 30 ? raw[9] : 1.0f, 1.0f);
-  }
-  float s, c;
-  nrc_sincospi_half(nrc_clamp(x) * (float)(2 << k), s, c);
-  return pack_bf16(s, c);
-}
-
-// All 32 words of one record (zeros when !live), unrolled: one reduction and one
-// polynomial pair per octave.
-__device__ __forceinline__ void nrc_encode_packed(const float* raw, const float* lo, const float* inv_ext, bool live,
-                                                  uint32_t (&w)[32]) {
-  float s, c;
+// Octave 0 of every coordinate comes from nrc_sincospi_half, the higher octaves
+// from nrc_double_angle.
+//
+// Words 0..17: the position's octaves.
+__device__ __forceinline__ void nrc_encode_position(const float* raw, const float* lo, const float* inv_ext,
+                                                    uint32_t* w) {
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    const float x = nrc_clamp((raw[a] - lo[a]) * inv_ext[a]);
+    float s, c;
+    nrc_sincospi_half(nrc_clamp((raw[a] - lo[a]) * inv_ext[a]) * 2.0f, s, c);
+    w[6 * a] = pack_bf16(s, c);
 #pragma unroll
-    for (int k = 0; k < 6; ++k) {
-      nrc_sincospi_half(x * (float)(2 << k), s, c);
+    for (int k = 1; k < 6; ++k) {
+      nrc_double_angle(s, c);
       w[6 * a + k] = pack_bf16(s, c);
     }
   }
+}
+
+// Words 18..31 (written to w[0..13]): direction and normal octaves, roughness, ones.
+__device__ __forceinline__ void nrc_encode_direction(const float* raw, uint32_t* w) {
 #pragma unroll
   for (int a = 0; a < 6; ++a) {
-    const float x = nrc_clamp(0.5f * (raw[3 + a] + 1.0f));
-    nrc_sincospi_half(x * 2.0f, s, c);
-    w[18 + 2 * a] = pack_bf16(s, c);
-    nrc_sincospi_half(x * 4.0f, s, c);
-    w[19 + 2 * a] = pack_bf16(s, c);
+    float s, c;
+    nrc_sincospi_half(nrc_clamp(0.5f * (raw[3 + a] + 1.0f)) * 2.0f, s, c);
+    w[2 * a] = pack_bf16(s, c);
+    nrc_double_angle(s, c);
+    w[2 * a + 1] = pack_bf16(s, c);
   }
-  w[30] = pack_bf16(raw[9], 1.0f);
-  w[31] = pack_bf16(1.0f, 1.0f);
+  w[12] = pack_bf16(raw[9], 1.0f);
+  w[13] = pack_bf16(1.0f, 1.0f);
+}
+
+// All 32 words of one record (zeros when !live).
+__device__ __forceinline__ void nrc_encode_packed(const float* raw, const float* lo, const float* inv_ext, bool live,
+                                                  uint32_t (&w)[32]) {
+  nrc_encode_position(raw, lo, inv_ext, w);
+  nrc_encode_direction(raw, w + 18);
   if (!live) {
 #pragma unroll
     for (int i = 0; i < 32; ++i) w[i] = 0u;

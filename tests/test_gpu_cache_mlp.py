@@ -26,6 +26,69 @@ def _rel_err(a, b):
     return np.abs(a - b) / (np.abs(b) + 0.05 * scale)
 
 
+# Octave of each encoded feature: position octave k at features 12 a + 2 k (+1),
+# direction and normal octaves 0 and 1, none for roughness and the constants.
+OCTAVE = np.zeros(64)
+OCTAVE[:36] = np.tile(np.repeat(np.arange(6), 2), 3)
+OCTAVE[36:60] = np.tile(np.repeat(np.arange(2), 2), 6)
+
+
+def _bf16(v):
+    """Values of the BF16 roundings (to FP32 nearest, then BF16 nearest even)."""
+    f = np.asarray(v, np.float32).view(np.uint32).astype(np.uint64)
+    b = (((f + 0x7FFF + ((f >> 16) & 1)) >> 16) << 16).astype(np.uint32)
+    return b.view(np.float32).astype(np.float64)
+
+
+def _unique_records(raw, oracle_enc, box=BOX):
+    """Records whose 64 BF16 features the kernel and the oracle decide alike.
+
+    Each feature is a quantised code chosen by floating point: the kernel rounds an
+    FP32 sin / cos of an FP32 coordinate (within 2^k * 4 * 2^-24 of the exact pair of
+    that coordinate at octave k), the oracle an FP64 one.  Where the FP64 value lies
+    within the two sides' difference (2^k * (pi + 1) * 4 * 2^-24: the FP32 rounding of
+    the coordinate amplified by the octave, plus the kernel's bound) of a BF16
+    rounding boundary, both codes are correct, and the network's output differs by
+    what one step of that feature makes of it.  The FP64 features here only locate
+    those boundaries; they are checked against the oracle's rounded features first.
+    The test records lie inside the box (no clamping)."""
+    lo, hi = np.asarray(box[0], np.float64), np.asarray(box[1], np.float64)
+    raw = raw.astype(np.float64)
+    x = (raw[:, :3] - lo) / (hi - lo)
+    xd = 0.5 * (raw[:, 3:9] + 1.0)
+    v = np.empty((raw.shape[0], 64))
+    for a in range(3):
+        for k in range(6):
+            v[:, 12 * a + 2 * k] = np.sin(2.0 ** k * np.pi * x[:, a])
+            v[:, 12 * a + 2 * k + 1] = np.cos(2.0 ** k * np.pi * x[:, a])
+    for a in range(6):
+        for k in range(2):
+            v[:, 36 + 4 * a + 2 * k] = np.sin(2.0 ** k * np.pi * xd[:, a])
+            v[:, 37 + 4 * a + 2 * k] = np.cos(2.0 ** k * np.pi * xd[:, a])
+    v[:, 60] = raw[:, 9]
+    v[:, 61:] = 1.0
+    m = 2.0 ** OCTAVE * (np.pi + 1) * 4 * 2.0 ** -24
+    either_way = _bf16(v - m) != _bf16(v + m)
+    assert np.all((_bf16(v) == oracle_enc) | either_way)
+    return ~either_way.any(1)
+
+
+def _check_outputs(got, ref, unique, tag=""):
+    """All records: finite, median error of a BF16 network.  Records with unique
+    features: the 99th percentile at FP32 accumulation-order level (measured near
+    3e-7).  The others: bounded by a few feature steps."""
+    err = _rel_err(got, ref)
+    print(f"{tag} median rel err {np.median(err):.2e}; unique-feature records {unique.mean():.2f}, "
+          f"p99 {np.quantile(err[unique], 0.99) if unique.any() else 0:.2e}; "
+          f"others max {err[~unique].max() if (~unique).any() else 0:.2e}")
+    assert np.all(np.isfinite(got))
+    assert np.median(err) < 2e-3
+    if unique.any():
+        assert np.quantile(err[unique], 0.99) < 1e-4
+    if (~unique).any():
+        assert err[~unique].max() < 0.5
+
+
 @pytest.mark.parametrize("engine", [0, 1])
 @pytest.mark.parametrize("n", [1, 17, 127, 128, 129, 5000])
 def test_inference_matches_oracle(abi, oracle_mod, n, engine):
@@ -46,11 +109,7 @@ def test_inference_matches_oracle(abi, oracle_mod, n, engine):
         abi.pt_cache_destroy(h)
     enc = oracle_mod.nrc_encode(raw, *BOX)
     ref = oracle_mod.mlp_forward(W.astype(np.float64), enc)
-    err = _rel_err(got, ref)
-    print(f"n={n} median rel err {np.median(err):.2e} p99 {np.quantile(err, 0.99):.2e} max {err.max():.2e}")
-    assert np.all(np.isfinite(got))
-    assert np.median(err) < 2e-3
-    assert np.quantile(err, 0.99) < 2e-2
+    _check_outputs(got, ref, _unique_records(raw, enc), f"n={n}")
 
 
 def test_gradient_and_loss_match_oracle(abi, oracle_mod):
@@ -252,7 +311,6 @@ def test_averaged_weights_follow_the_recurrence_and_serve_queries(abi, oracle_mo
     finally:
         c.close()
     enc = oracle_mod.nrc_encode(raw[:300], *BOX)
-    err = _rel_err(q, oracle_mod.mlp_forward(got_A, enc))
-    assert np.median(err) < 2e-3 and np.quantile(err, 0.99) < 2e-2
+    _check_outputs(q, oracle_mod.mlp_forward(got_A, enc), _unique_records(raw[:300], enc))
     with pytest.raises(abi.PtError):
         RadianceCache(*BOX, batch=64, ema=1.0)
