@@ -104,7 +104,9 @@ __device__ __forceinline__ uint32_t core_off(int row, int k) {
 // into shared memory once per CTA.
 constexpr int kGroups = 8;
 constexpr uint32_t kSmW = 0, kSmH = 5 * 8192, kSmX = kSmH + 2048;
-constexpr uint32_t kSmBar = kSmX + kGroups * 16384, kSmSlot = kSmBar + 8 * kGroups;
+constexpr uint32_t kRawTile = 128 * NRC_RAW * 4;  // one tile's raw records: 5120 bytes
+constexpr uint32_t kSmRaw = kSmX + kGroups * 16384;
+constexpr uint32_t kSmBar = kSmRaw + kGroups * kRawTile, kSmSlot = kSmBar + 8 * kGroups;
 constexpr uint32_t kTcSmem = kSmSlot + 8 + 1024;  // + alignment slack
 constexpr uint32_t kTmemCols = 64 * kGroups;      // 512: the whole tensor memory of the SM
 // Bounded waits: per MMA step `limit` polls (the cache's wait limit, by default
@@ -126,6 +128,28 @@ __device__ __forceinline__ bool group_sync_and(int g, bool pred) {
 }
 __device__ __forceinline__ void group_sync(int g) {
   asm volatile("barrier.cta.sync %0, 128;" ::"r"(1 + g) : "memory");
+}
+
+// Asynchronous 4-byte copies from global to shared memory (no registers held while
+// they are in flight); a thread's copies are complete after cp_async_wait_all, and
+// visible to the other threads after a barrier that follows it.
+__device__ __forceinline__ void cp_async4(uint32_t dst, const float* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Thread r's share of tile `tile`'s raw records into a group's staging buffer:
+// floats r, r + 128, ..., r + 1152 of the tile's 1280 (each warp copies 128
+// contiguous bytes at a time).  Floats past the end of the input are not copied;
+// their rows are not live.
+__device__ __forceinline__ void stage_raw(uint32_t stage_s, const float* raw, long long tile, long long n, int r) {
+  const long long base = tile * (128LL * NRC_RAW), end = n * NRC_RAW;
+#pragma unroll
+  for (int j = 0; j < NRC_RAW; ++j) {
+    const long long e = base + r + 128 * j;
+    if (e < end) cp_async4(stage_s + 4u * (uint32_t)(r + 128 * j), raw + e);
+  }
+  asm volatile("cp.async.commit_group;" ::: "memory");
 }
 
 __global__ void __launch_bounds__(128 * kGroups, 1)
@@ -151,6 +175,14 @@ __global__ void __launch_bounds__(128 * kGroups, 1)
     *reinterpret_cast<unsigned short*>(sm + kSmH + core_off(o, i)) =
         o < NRC_OUT ? gw[NRC_HIDDEN * NRC_W * NRC_W + o * NRC_W + i] : (unsigned short)0;
   }
+  // The group's raw records go through a staging buffer: each tile's are copied
+  // while the previous tile runs through the layers.
+  const float* stage = reinterpret_cast<const float*>(sm + kSmRaw + g * kRawTile);
+  const uint32_t stage_s = smem_addr(stage);
+  const long long n_tiles = (n + 127) / 128, stride = (long long)gridDim.x * kGroups;
+  long long tile = (long long)blockIdx.x * kGroups + g;
+  if (tile < n_tiles) stage_raw(stage_s, raw, tile, n, r);
+  cp_async_wait_all();
   if (r == 0) mbar_init(bar, 1);
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(slot)),
@@ -167,14 +199,16 @@ __global__ void __launch_bounds__(128 * kGroups, 1)
   const uint32_t t_lane = tmem + ((uint32_t)((warp & 3) * 32) << 16);  // this warp's 32 TMEM lanes
   uint32_t phase = 0, last = 0;  // last: parity of the latest wait
   bool ok = true;
-  const long long n_tiles = (n + 127) / 128;
-  for (long long tile = (long long)blockIdx.x * kGroups + g; tile < n_tiles && ok;
-       tile += (long long)gridDim.x * kGroups) {
-    // ---- encode this thread's query (row r of the tile)
+  for (; tile < n_tiles && ok; tile += stride) {
+    // ---- encode this thread's query (row r of the tile), from the staged records
     const long long row = tile * 128 + r;
     float rr[NRC_RAW];
 #pragma unroll
-    for (int k = 0; k < NRC_RAW; ++k) rr[k] = row < n ? raw[row * NRC_RAW + k] : 0.0f;
+    for (int k = 0; k < NRC_RAW; k += 2) {
+      const float2 v = row < n ? reinterpret_cast<const float2*>(stage + r * NRC_RAW)[k >> 1] : make_float2(0.f, 0.f);
+      rr[k] = v.x;
+      rr[k + 1] = v.y;
+    }
     {
       uint32_t w[32];
       nrc_encode_packed(rr, box.lo, box.inv_ext, row < n, w);
@@ -186,6 +220,8 @@ __global__ void __launch_bounds__(128 * kGroups, 1)
     fence_async_smem();
     tc_fence_before();
     group_sync(g);
+    // every thread of the group has read its record: stage the next tile's
+    if (tile + stride < n_tiles) stage_raw(stage_s, raw, tile + stride, n, r);
     // ---- five hidden layers and the head
     for (int l = 0; l <= NRC_HIDDEN; ++l) {
       const bool head = l == NRC_HIDDEN;
@@ -230,12 +266,14 @@ __global__ void __launch_bounds__(128 * kGroups, 1)
           out[row * 3 + 1] = v[1];
           out[row * 3 + 2] = v[2];
         }
+        cp_async_wait_all();  // the next tile's records, visible to the group after the barrier
       }
       tc_fence_before();
       ok = group_sync_and(g, done);
       if (!ok) break;
     }
   }
+  cp_async_wait_all();  // no copy in flight past a loop left early
   if (!ok) {
     if (r == 0) atomicCAS(status, 0, PT_ERR_TIMEOUT);
     // let an MMA still in flight finish before the tensor memory is released
