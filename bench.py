@@ -78,7 +78,7 @@ def alu_roofline(kernel, counters, bvh, ms, clk, note=""):
 # by its counted rays (the per-ray traffic of these kernels does not depend on the
 # image size: the scene and texture are the same and the per-sample state scales with
 # the rays).  A kernel changed since its capture has no entry.
-TRAFFIC_PER_RAY = {"wide": {"forward_kernel": 82.7, "radiance_kernel": 108.8, "replay_kernel": 148.3}}
+TRAFFIC_PER_RAY = {"wide": {"forward_kernel": 52.2, "radiance_kernel": 71.0, "replay_kernel": 146.5}}
 # reparam_kernel (translation mode): DRAM bytes per sample of the same kind of capture
 # (409 MB per 256x256 x 4 spp launch).
 REPARAM_TRAFFIC_PER_SAMPLE = 1535.0

@@ -230,10 +230,37 @@ __device__ __forceinline__ Hit trace_binary(const DevScene& S, float3 ro, float3
   return h;
 }
 
+// Three-input FP32 minimum / maximum (one instruction on sm_100 and later; exact, so
+// the same values as two chained fminf / fmaxf).
+__device__ __forceinline__ float min3f(float a, float b, float c) {
+  float d;
+  asm("min.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+  return d;
+}
+__device__ __forceinline__ float max3f(float a, float b, float c) {
+  float d;
+  asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+  return d;
+}
+// Both lanes of a packed pair in one 64-bit register.
+__device__ __forceinline__ uint64_t pack_f32x2(float lo, float hi) {
+  uint64_t r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+// (qn A + B, qf A + B) with AA = (A, A), BB = (B, B): one packed FP32 FMA (sm_100 and
+// later), rounded per lane exactly as two fmaf.
+__device__ __forceinline__ void plane_pair(float qn, float qf, uint64_t AA, uint64_t BB, float& tn, float& tf) {
+  asm("{\n .reg .b64 q, d;\n mov.b64 q, {%2, %3};\n fma.rn.f32x2 d, q, %4, %5;\n mov.b64 {%0, %1}, d;\n}"
+      : "=f"(tn), "=f"(tf)
+      : "f"(qn), "f"(qf), "l"(AA), "l"(BB));
+}
+
 // Closest hit / any hit on the 8-wide compressed BVH (80-byte nodes: origin,
 // per-axis power-of-two steps, inner-child mask, child and triangle bases, and
 // 8-bit child box planes; see bvh_build.h).  Each visited node tests its eight
-// child boxes with one FMA per plane (near/far planes picked once per node from
+// child boxes with one FMA per plane, the near and far planes of an axis as one packed
+// FMA (near/far planes picked once per node from
 // the ray direction), intersects the triangles of hit leaf children at once, and
 // pushes the remaining hit inner children as one (base, mask) group.  Children
 // are visited in the order of the slot octants relative to the ray direction.
@@ -280,6 +307,8 @@ __device__ __forceinline__ Hit trace_wide(const DevScene& S, float3 ro, float3 r
     const float Bx = fmaf(__uint_as_float(w0.x) - ro.x, inv.x, -Ax);
     const float By = fmaf(__uint_as_float(w0.y) - ro.y, inv.y, -Ay);
     const float Bz = fmaf(__uint_as_float(w0.z) - ro.z, inv.z, -Az);
+    const uint64_t AAx = pack_f32x2(Ax, Ax), AAy = pack_f32x2(Ay, Ay), AAz = pack_f32x2(Az, Az);
+    const uint64_t BBx = pack_f32x2(Bx, Bx), BBy = pack_f32x2(By, By), BBz = pack_f32x2(Bz, Bz);
     // near / far plane bytes per axis (lo planes are near for a positive direction)
     const uint32_t nx0 = rd.x >= 0.0f ? w2.x : w3.z, nx1 = rd.x >= 0.0f ? w2.y : w3.w;
     const uint32_t fx0 = rd.x >= 0.0f ? w3.z : w2.x, fx1 = rd.x >= 0.0f ? w3.w : w2.y;
@@ -302,8 +331,14 @@ __device__ __forceinline__ Hit trace_wide(const DevScene& S, float3 ro, float3 r
       const float qfy = __uint_as_float(__byte_perm(sl < 4 ? fy0 : fy1, 0x3F800000u, sel));
       const float qnz = __uint_as_float(__byte_perm(sl < 4 ? nz0 : nz1, 0x3F800000u, sel));
       const float qfz = __uint_as_float(__byte_perm(sl < 4 ? fz0 : fz1, 0x3F800000u, sel));
-      const float tn = fmaxf(fmaxf(fmaf(qnx, Ax, Bx), fmaf(qny, Ay, By)), fmaxf(fmaf(qnz, Az, Bz), 0.0f));
-      const float tf = fminf(fminf(fmaf(qfx, Ax, Bx), fmaf(qfy, Ay, By)), fminf(fmaf(qfz, Az, Bz), h.t));
+      // near and far plane of an axis in one packed FMA; entry and exit in two
+      // three-input min / max each
+      float tnx, tfx, tny, tfy, tnz, tfz;
+      plane_pair(qnx, qfx, AAx, BBx, tnx, tfx);
+      plane_pair(qny, qfy, AAy, BBy, tny, tfy);
+      plane_pair(qnz, qfz, AAz, BBz, tnz, tfz);
+      const float tn = max3f(fmaxf(tnx, 0.0f), tny, tnz);
+      const float tf = min3f(fminf(tfx, h.t), tfy, tfz);
       if (tn <= tf) hitm |= 1u << sl;
     }
     uint32_t leaf_hits = hitm & ~imask;

@@ -316,12 +316,20 @@ __device__ __forceinline__ void megakernel(const LaunchArgs& A, long long unit, 
 // With the shorter node visit (one FMA per box plane, a hit mask per node) the forward
 // still prefers 5 CTAs (37.3 ms; 38.1 at 64 registers, 39.9 at 40), while the split-PRB
 // replay and the forward-mode kernel moved to 4 (their own caps in pt_render.cu).
+// With two box planes per packed FMA the forward and the radiance pass run best at 56
+// registers (36.0 ms each; 36.5 at 48, 37.1 at 64), a cap that no CTA count of 256
+// threads gives, so those kernels take it directly (PT_FWD_REGS, any block size up to
+// 256 threads); the checkpointed forward keeps PT_FWD_MIN_BLOCKS.
 #ifndef PT_LB_THREADS
-#define PT_LB_THREADS 256  // block size the forward / replay register caps are computed for
+#define PT_LB_THREADS 256  // block size the replay register cap is computed for
 #endif
 #ifndef PT_FWD_MIN_BLOCKS
 #define PT_FWD_MIN_BLOCKS 5
 #endif
+#ifndef PT_FWD_REGS
+#define PT_FWD_REGS 56
+#endif
+#define PT_FWD_BOUNDS __maxnreg__(PT_FWD_REGS)
 // The batched forward keeps 64 registers (measured there).
 #ifndef PT_OTHER_FWD_MIN_BLOCKS
 #define PT_OTHER_FWD_MIN_BLOCKS 4

@@ -14,14 +14,14 @@ namespace ptgb {
 
 // Production instances carry no optional features; instrumented ones carry all.
 template <bool INSTR, int LAYOUT, int DISPATCH>
-__global__ void __launch_bounds__(PT_LB_THREADS, PT_FWD_MIN_BLOCKS) forward_kernel(const __grid_constant__ LaunchArgs A) {
+__global__ void PT_FWD_BOUNDS forward_kernel(const __grid_constant__ LaunchArgs A) {
   megakernel<false, false, INSTR, LAYOUT, DISPATCH, INSTR ? FEAT_ALL : FEAT_NOHASH | FEAT_LEAN>(
       A, (long long)blockIdx.x * blockDim.x + threadIdx.x, crop_tile(A));
 }
 
 // The forward with the radiance-cache modes compiled in.
 template <int LAYOUT>
-__global__ void __launch_bounds__(PT_LB_THREADS, PT_FWD_MIN_BLOCKS) forward_full_kernel(const __grid_constant__ LaunchArgs A) {
+__global__ void PT_FWD_BOUNDS forward_full_kernel(const __grid_constant__ LaunchArgs A) {
   megakernel<false, false, false, LAYOUT, PT_DISPATCH_SWITCH, FEAT_ALL | FEAT_NOHASH | FEAT_LEAN>(
       A, (long long)blockIdx.x * blockDim.x + threadIdx.x, crop_tile(A));
 }
@@ -46,7 +46,7 @@ __global__ void __launch_bounds__(256, PT_ADJ_MIN_BLOCKS) adjoint_kernel(const _
 // Split PRB: the radiance pass as a forward kernel storing each sample's L, and
 // the replay-only adjoint reading it.
 template <int LAYOUT>
-__global__ void __launch_bounds__(PT_LB_THREADS, PT_FWD_MIN_BLOCKS) radiance_kernel(const __grid_constant__ LaunchArgs A) {
+__global__ void PT_FWD_BOUNDS radiance_kernel(const __grid_constant__ LaunchArgs A) {
   megakernel<false, false, false, LAYOUT, PT_DISPATCH_SWITCH, FEAT_SAMPLE_L | FEAT_NOHASH | FEAT_LEAN>(
       A, (long long)blockIdx.x * blockDim.x + threadIdx.x, crop_tile(A));
 }
@@ -63,12 +63,12 @@ __global__ void __launch_bounds__(PT_LB_THREADS, PT_REPLAY_MIN_BLOCKS) replay_ke
 // radiance pass and replay, and forward mode: a grid of resident CTAs whose lanes
 // pull (pixel, lane) units from A.queue.
 template <int LAYOUT>
-__global__ void __launch_bounds__(PT_LB_THREADS, PT_FWD_MIN_BLOCKS)
+__global__ void PT_FWD_BOUNDS
     forward_persist_kernel(const __grid_constant__ LaunchArgs A) {
   megakernel<false, false, false, LAYOUT, PT_DISPATCH_SWITCH, FEAT_NOHASH | FEAT_LEAN, true>(A, 0, crop_tile(A));
 }
 template <int LAYOUT>
-__global__ void __launch_bounds__(PT_LB_THREADS, PT_FWD_MIN_BLOCKS)
+__global__ void PT_FWD_BOUNDS
     radiance_persist_kernel(const __grid_constant__ LaunchArgs A) {
   megakernel<false, false, false, LAYOUT, PT_DISPATCH_SWITCH, FEAT_SAMPLE_L | FEAT_NOHASH | FEAT_LEAN, true>(A, 0, crop_tile(A));
 }
