@@ -63,7 +63,7 @@ def up_to_date() -> bool:
 
 def build(force: bool = False, verbose: bool = False, ptxas_verbose: bool = False, defines=()) -> str:
     """defines: extra preprocessor definitions ("NAME=value"), e.g. the register caps
-    PT_FWD_MIN_BLOCKS / PT_ADJ_MIN_BLOCKS / PT_REPLAY_MIN_BLOCKS for tuning."""
+    PT_FWD_REGS / PT_ADJ_MIN_BLOCKS / PT_REPLAY_MIN_BLOCKS for tuning."""
     if not force and not defines and up_to_date():
         return LIB
     nvcc = _nvcc()

@@ -27,7 +27,7 @@ namespace {
 
 template <int LAYOUT>
 // the plain forward's cap (48 registers: 39.9 ms against 40.6 at 64)
-__global__ void __launch_bounds__(256, PT_FWD_MIN_BLOCKS) ckpt_forward_kernel(const __grid_constant__ LaunchArgs A) {
+__global__ void PT_FWD_BOUNDS ckpt_forward_kernel(const __grid_constant__ LaunchArgs A) {
   megakernel<false, false, false, LAYOUT, PT_DISPATCH_SWITCH, FEAT_CKPT>(
       A, (long long)blockIdx.x * blockDim.x + threadIdx.x, crop_tile(A));
 }

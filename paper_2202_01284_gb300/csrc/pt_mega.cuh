@@ -319,12 +319,9 @@ __device__ __forceinline__ void megakernel(const LaunchArgs& A, long long unit, 
 // With two box planes per packed FMA the forward and the radiance pass run best at 56
 // registers (36.0 ms each; 36.5 at 48, 37.1 at 64), a cap that no CTA count of 256
 // threads gives, so those kernels take it directly (PT_FWD_REGS, any block size up to
-// 256 threads); the checkpointed forward keeps PT_FWD_MIN_BLOCKS.
+// 256 threads); so does the checkpointed forward (38.6 ms against 39.3 at 48).
 #ifndef PT_LB_THREADS
 #define PT_LB_THREADS 256  // block size the replay register cap is computed for
-#endif
-#ifndef PT_FWD_MIN_BLOCKS
-#define PT_FWD_MIN_BLOCKS 5
 #endif
 #ifndef PT_FWD_REGS
 #define PT_FWD_REGS 56
