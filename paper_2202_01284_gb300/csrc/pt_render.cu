@@ -28,11 +28,13 @@ __global__ void PT_FWD_BOUNDS forward_full_kernel(const __grid_constant__ Launch
 
 // Forward mode (Sec. 4, forward-mode derivatives of the paper's AD layer): the
 // image and its derivative along a parameter direction in one pass.
-#ifndef PT_JVP_MIN_BLOCKS
-#define PT_JVP_MIN_BLOCKS 4  // 64 registers: 40.3 ms against 42.7 at the adjoint's 80
+// Register cap: 56 (39.4 ms against 39.7 at 64 with two box planes per packed FMA;
+// before that 64 registers ran 40.3 ms against 42.7 at the adjoint's 80).
+#ifndef PT_JVP_REGS
+#define PT_JVP_REGS 56
 #endif
 template <int LAYOUT>
-__global__ void __launch_bounds__(256, PT_JVP_MIN_BLOCKS) jvp_kernel(const __grid_constant__ LaunchArgs A) {
+__global__ void __maxnreg__(PT_JVP_REGS) jvp_kernel(const __grid_constant__ LaunchArgs A) {
   megakernel<false, true, false, LAYOUT, PT_DISPATCH_SWITCH, FEAT_NOHASH | FEAT_LEAN>(
       A, (long long)blockIdx.x * blockDim.x + threadIdx.x, crop_tile(A));
 }
@@ -51,7 +53,7 @@ __global__ void PT_FWD_BOUNDS radiance_kernel(const __grid_constant__ LaunchArgs
       A, (long long)blockIdx.x * blockDim.x + threadIdx.x, crop_tile(A));
 }
 #ifndef PT_REPLAY_MIN_BLOCKS
-#define PT_REPLAY_MIN_BLOCKS 4  // 64 registers: 41.4 ms against 43.5 at 80 and 41.6 at 48
+#define PT_REPLAY_MIN_BLOCKS 4  // 64 registers: 41.4 ms against 43.5 at 80 and 41.6 at 48; 40.3 at 64 and at 56 with the packed FMA
 #endif
 template <int LAYOUT>
 __global__ void __launch_bounds__(PT_LB_THREADS, PT_REPLAY_MIN_BLOCKS) replay_kernel(const __grid_constant__ LaunchArgs A) {
@@ -78,7 +80,7 @@ __global__ void __launch_bounds__(PT_LB_THREADS, PT_REPLAY_MIN_BLOCKS)
   megakernel<true, false, false, LAYOUT, PT_DISPATCH_SWITCH, FEAT_REPLAY | FEAT_NOHASH | FEAT_LEAN, true>(A, 0, crop_tile(A));
 }
 template <int LAYOUT>
-__global__ void __launch_bounds__(256, PT_JVP_MIN_BLOCKS) jvp_persist_kernel(const __grid_constant__ LaunchArgs A) {
+__global__ void __maxnreg__(PT_JVP_REGS) jvp_persist_kernel(const __grid_constant__ LaunchArgs A) {
   megakernel<false, true, false, LAYOUT, PT_DISPATCH_SWITCH, FEAT_NOHASH | FEAT_LEAN, true>(A, 0, crop_tile(A));
 }
 
