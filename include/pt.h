@@ -592,8 +592,10 @@ int pt_cache_query(pt_cache* cache, const float* raw, float* rgb, int n, void* s
  * to the box, sin and cos of 2^k pi x for k = 0..5 per axis (features 0..35, sin at
  * even indices); inputs outside [-2^15, 2^15] after normalisation are clamped to it;
  * direction and normal mapped to [0, 1] with k = 0, 1 (36..47, 48..59); roughness
- * (60); the constant 1 (61..63).  Each value is rounded to BF16 from FP32 sin / cos
- * evaluations within 2 ulp.  Errors: PT_ERR_ARG (null pointers with n > 0, n < 0,
+ * (60); the constant 1 (61..63).  Octave k = 0 of each coordinate is an FP32 sin /
+ * cos within 2 ulp, octave k > 0 follows by k double-angle steps and lies within
+ * 2^k * 4 * 2^-24 (absolute) of the exact pair; each value is then rounded to BF16.
+ * Errors: PT_ERR_ARG (null pointers with n > 0, n < 0,
  * unaligned output), PT_ERR_CUDA (launch). */
 int pt_cache_encode(pt_cache* cache, const float* raw, uint16_t* features, int n, void* stream);
 /* Synchronous copies of the averaged weights A (see pt_cache_desc.ema); set_weights
